@@ -1,0 +1,26 @@
+"""FP64 CPU oracle of the quasi-static PIC slice loop (arXiv:2109.10277, Sec. 2-3).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product package imports, links or runs
+anything here; only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may use it.
+
+The oracle is a plain, slow restatement of the paper's method in PyTorch CPU
+float64 ops (``torch.matmul`` is the only library primitive used as a step, for
+the dense DST-I).  It shares no code with the CUDA path.  Because every step is
+written with differentiable torch ops, running it under ``torch.autograd`` is the
+oracle's taped FP64 adjoint.
+
+Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
+  dst / poisson_solve  pinned: eigenmodes, S.S = (N/2) I, brute-force sums, 5-point residual
+  ddx / ddy            pinned: exact on quadratics, orientation
+  shape / deposit      pinned: partition of unity, charge conservation, brute-force B-spline
+  gather               pinned: affine reproduction, transpose identity with deposit
+  derivs               pinned: Lorentz-force chain rule, invariant Psi - psi(x_p)
+  ab5 step             pinned: exact on quartic derivatives, order-5 convergence
+  sweep                pinned: zero-beam invariant, symmetry, Ez ~ -d(psi)/d(zeta),
+                       conservation of sum(rho - Jz), discrete linear wake
+  beam binning         pinned: brute-force bin membership
+  beam push            pinned: uniform-B gyration, uniform-E energy gain, time reversibility
+  blowout-regime physics (cfg 512^2 n_b=5): parity unpinned beyond the checks above
+"""
+from .qsa import *  # noqa: F401,F403

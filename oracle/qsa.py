@@ -1,0 +1,518 @@
+"""Plain FP64 restatement of the quasi-static PIC slice loop of arXiv:2109.10277.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): the product path never
+imports this module.
+
+Units are the paper's normalized units (Sec. 5): lengths in 1/k_p, fields in
+E0 = m c omega_p / e, densities in n0, c = eps0 = mu0 = 1.  Plasma electrons have
+q = -1, M = 1; ions are immobile.
+
+Everything is written with differentiable torch ops on CPU float64, so running
+``sweep`` under autograd gives the oracle's taped adjoint.
+
+Readings of the paper (it is silent or only cites a reference on these points):
+  * grid: nodes x_j = xmin + j dx, j = 0..nx; nodes 0 and nx lie on the Dirichlet
+    wall and are zero.  Arrays are (ny, nx) over nodes 0..n-1 with row/col 0 zero.
+    The interior is transformed by the DST-I of Sec. 3.2 (fast Poisson solver),
+    i.e. S_jk = sin(pi j k / n); the 5-point Laplacian is the operator DST-I
+    diagonalises exactly.
+  * transverse derivatives are second-order central differences on interior
+    nodes; d(J_perp)/d(zeta) is central between slices zeta+dzeta and zeta-dzeta
+    (Sec. 3.2, predictor-corrector).
+  * shapes are cardinal B-splines of order 0-3 (Sec. 3.2 deposition), used for
+    both gather and deposit; weight landing outside nodes 1..n-1 is discarded
+    (deposit) or reads zero (gather).
+  * a macroparticle represents a fixed flux, so its density is w*gamma/((1+Psi)A);
+    with gamma - u_z = 1 + Psi (Eq. for gamma_p) this gives rho - J_z = q w S / A.
+  * chi = q^2 w S / (M (1+Psi) A) (the explicit solver's susceptibility; output only).
+  * ions: minus the electron charge deposited once from the initial positions.
+  * predictor-corrector: guess B(i) = 2 B(i-1) - B(i-2) (B = 0 before the box),
+    fixed n_pc iterations with mixing weight pc_mix, no early exit.
+  * a particle is removed (weight to zero, state frozen) when after a full step
+    1 + Psi < psi_guard, it leaves the open box, or a value is not finite; a trial
+    state failing the same test is skipped in the trial deposit.
+  * beam push: drift-kick-drift with a Boris kick (second order, time
+    reversible), fields of the particle's own slice (order-0 longitudinal).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import torch
+
+DT = torch.float64
+DEV = torch.device("cpu")
+
+# Fifth-order Adams-Bashforth weights (Sec. 3.2 plasma push): beta_k for f_{i-k}.
+AB5 = (1901.0 / 720.0, -2774.0 / 720.0, 2616.0 / 720.0, -1274.0 / 720.0, 251.0 / 720.0)
+
+FIELD_NAMES = ("rho", "jx", "jy", "jz", "chi", "psi", "exmby", "eypbx", "ez", "bx", "by", "bz")
+
+
+@dataclass
+class GridSpec:
+    """Transverse Dirichlet box, zeta range and plasma/solver parameters (Sec. 2, 3.2)."""
+    nx: int
+    ny: int
+    nzeta: int
+    xmin: float
+    xmax: float
+    ymin: float
+    ymax: float
+    zeta_min: float
+    zeta_max: float
+    shape_order: int = 1
+    ppc_x: int = 1
+    ppc_y: int = 1
+    radial_profile: Optional[Sequence[float]] = None
+    profile_rmax: float = 0.0
+    n0_scale: float = 1.0
+    n_pc_iter: int = 5
+    pc_mix: float = 0.05
+    psi_guard: float = 0.02
+
+    @property
+    def dx(self) -> float:
+        return (self.xmax - self.xmin) / self.nx
+
+    @property
+    def dy(self) -> float:
+        return (self.ymax - self.ymin) / self.ny
+
+    @property
+    def dzeta(self) -> float:
+        return (self.zeta_max - self.zeta_min) / self.nzeta
+
+
+# ----------------------------------------------------------------------------
+# Fast Poisson solver (Sec. 3.2: DST-I, Dirichlet boundary)
+# ----------------------------------------------------------------------------
+
+def dst_matrix(n: int) -> torch.Tensor:
+    """S_jk = sin(pi j k / n), j, k = 0..n-1 (row/col 0 are zero): DST-I with a zero border."""
+    j = torch.arange(n, dtype=torch.int64)
+    m = torch.remainder(torch.outer(j, j), 2 * n)  # exact argument reduction
+    return torch.sin(math.pi * m.to(DT) / n)
+
+
+def laplace_eigs(spec: GridSpec) -> torch.Tensor:
+    """Eigenvalues lambda[l, k] of the 5-point Laplacian for DST-I mode (k in x, l in y)."""
+    k = torch.arange(spec.nx, dtype=DT)
+    l = torch.arange(spec.ny, dtype=DT)
+    ex = -(4.0 / spec.dx ** 2) * torch.sin(math.pi * k / (2 * spec.nx)) ** 2
+    ey = -(4.0 / spec.dy ** 2) * torch.sin(math.pi * l / (2 * spec.ny)) ** 2
+    return ey[:, None] + ex[None, :]
+
+
+def dst2(spec: GridSpec, a: torch.Tensor) -> torch.Tensor:
+    """Unnormalised 2D DST-I of the interior: S_y a S_x."""
+    return dst_matrix(spec.ny) @ a @ dst_matrix(spec.nx)
+
+
+def poisson_solve(spec: GridSpec, s: torch.Tensor) -> torch.Tensor:
+    """f = L^{-1} s with L the 5-point Laplacian and f = 0 on the wall (Sec. 3.2).
+
+    f_hat = (S_y s S_x) / lambda;  f = (2/nx)(2/ny) S_y f_hat S_x.
+    """
+    lam = laplace_eigs(spec)
+    inv = torch.zeros_like(lam)
+    inv[1:, 1:] = 1.0 / lam[1:, 1:]
+    f_hat = dst2(spec, s) * inv
+    return (4.0 / (spec.nx * spec.ny)) * dst2(spec, f_hat)
+
+
+def _wall_mask(spec: GridSpec) -> torch.Tensor:
+    m = torch.ones(spec.ny, spec.nx, dtype=DT)
+    m[0, :] = 0.0
+    m[:, 0] = 0.0
+    return m
+
+
+def ddx(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
+    """Central x-derivative on interior nodes; node nx (wall) reads 0, wall outputs are 0."""
+    fp = torch.cat([f, torch.zeros_like(f[..., :1])], dim=-1)  # columns 0..nx
+    d = torch.zeros_like(f)
+    d = torch.cat([d[..., :1], (fp[..., 2:] - fp[..., :-2]) / (2.0 * spec.dx)], dim=-1)
+    return d * _wall_mask(spec)
+
+
+def ddy(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
+    """Central y-derivative on interior nodes; node ny (wall) reads 0, wall outputs are 0."""
+    fp = torch.cat([f, torch.zeros_like(f[..., :1, :])], dim=-2)
+    d = torch.cat([torch.zeros_like(f[..., :1, :]), (fp[..., 2:, :] - fp[..., :-2, :]) / (2.0 * spec.dy)], dim=-2)
+    return d * _wall_mask(spec)
+
+
+# ----------------------------------------------------------------------------
+# Shapes, deposition and gather (Sec. 3.2: order 0 longitudinal, 0-3 transverse)
+# ----------------------------------------------------------------------------
+
+def shape_1d(u: torch.Tensor, order: int):
+    """B-spline weights of order `order` at node coordinate u (nodes at integers).
+
+    Returns (j0, [w_0..w_p]): node j0 + a carries weight w_a.
+    """
+    if order == 0:
+        j0 = torch.floor(u + 0.5)
+        return j0.to(torch.int64), [torch.ones_like(u)]
+    if order == 1:
+        j0 = torch.floor(u)
+        d = u - j0
+        return j0.to(torch.int64), [1.0 - d, d]
+    if order == 2:
+        jc = torch.floor(u + 0.5)
+        d = u - jc
+        return (jc - 1).to(torch.int64), [0.5 * (0.5 - d) ** 2, 0.75 - d * d, 0.5 * (0.5 + d) ** 2]
+    if order == 3:
+        jf = torch.floor(u)
+        d = u - jf
+        return (jf - 1).to(torch.int64), [
+            (1.0 - d) ** 3 / 6.0,
+            (4.0 - 6.0 * d * d + 3.0 * d ** 3) / 6.0,
+            (1.0 + 3.0 * d + 3.0 * d * d - 3.0 * d ** 3) / 6.0,
+            d ** 3 / 6.0,
+        ]
+    raise ValueError("shape order must be 0..3")
+
+
+def _stencil(spec: GridSpec, x: torch.Tensor, y: torch.Tensor, order: int):
+    """Yield (flat node index, weight) for every stencil node; invalid nodes get weight 0."""
+    jx0, wx = shape_1d((x - spec.xmin) / spec.dx, order)
+    jy0, wy = shape_1d((y - spec.ymin) / spec.dy, order)
+    for b in range(order + 1):
+        jy = jy0 + b
+        vy = (jy >= 1) & (jy <= spec.ny - 1)
+        for a in range(order + 1):
+            jx = jx0 + a
+            valid = vy & (jx >= 1) & (jx <= spec.nx - 1)
+            idx = torch.where(valid, jy * spec.nx + jx, torch.zeros_like(jx))
+            yield idx, torch.where(valid, wx[a] * wy[b], torch.zeros_like(wx[a]))
+
+
+def deposit(spec: GridSpec, x, y, values: Sequence[torch.Tensor], order: int):
+    """Scatter per-particle `values` onto the node grid with shape `order`."""
+    outs = [torch.zeros(spec.ny * spec.nx, dtype=DT) for _ in values]
+    for idx, wgt in _stencil(spec, x, y, order):
+        outs = [o.index_add(0, idx, wgt * v) for o, v in zip(outs, values)]
+    return [o.reshape(spec.ny, spec.nx) for o in outs]
+
+
+def gather(spec: GridSpec, x, y, fields: Sequence[torch.Tensor], order: int):
+    """Interpolate node `fields` to particle positions with shape `order`."""
+    flat = [f.reshape(-1) for f in fields]
+    outs = [torch.zeros_like(x) for _ in fields]
+    for idx, wgt in _stencil(spec, x, y, order):
+        outs = [o + wgt * f[idx] for o, f in zip(outs, flat)]
+    return outs
+
+
+# ----------------------------------------------------------------------------
+# Plasma push (Sec. 3.2, Eqs. for d(x_perp)/d(zeta), d(u_perp)/d(zeta), d(Psi)/d(zeta))
+# ----------------------------------------------------------------------------
+
+def derivs(q_over_m: float, ux, uy, psi, F):
+    """zeta-derivatives (dx, dy, dux, duy, dpsi) of a plasma particle.
+
+    F = (ExmBy, EypBx, Ez, Bx, By, Bz) gathered at the particle; q/M in units e/m_e.
+    """
+    exmby, eypbx, ez, bx, by, bz = F
+    opp = 1.0 + psi
+    g = 1.0 / opp
+    gam = (1.0 + ux * ux + uy * uy + opp * opp) * 0.5 * g
+    dxz = -ux * g
+    dyz = -uy * g
+    dux = -q_over_m * (gam * g * exmby + by + bz * g * uy)
+    duy = -q_over_m * (gam * g * eypbx - bx - bz * g * ux)
+    dpsi = -q_over_m * (g * (ux * exmby + uy * eypbx) - ez)
+    return (dxz, dyz, dux, duy, dpsi)
+
+
+def ab5_step(y: Sequence[torch.Tensor], fs: Sequence[Sequence[torch.Tensor]], dzeta: float):
+    """One step zeta -> zeta - dzeta: y - dzeta * sum_k beta_k f_{i-k}; fs = [f_i, f_{i-1}, ..]."""
+    out = []
+    for c in range(len(y)):
+        acc = AB5[0] * fs[0][c]
+        for k in range(1, 5):
+            acc = acc + AB5[k] * fs[k][c]
+        out.append(y[c] - dzeta * acc)
+    return out
+
+
+def gamma_of(ux, uy, psi):
+    opp = 1.0 + psi
+    return (1.0 + ux * ux + uy * uy + opp * opp) / (2.0 * opp)
+
+
+# ----------------------------------------------------------------------------
+# Plasma state and deposits
+# ----------------------------------------------------------------------------
+
+PLASMA_Q = -1.0
+PLASMA_M = 1.0
+
+
+def plasma_init(spec: GridSpec, n0_scale: Optional[torch.Tensor] = None,
+                radial_profile: Optional[torch.Tensor] = None):
+    """ppc_x x ppc_y electrons per cell at sub-cell centres, at rest (Sec. 2).
+
+    Ordering: cell row-major (iy, ix), then sub-particle (sy, sx).
+    w = n0_scale * n(r) * dx * dy / ppc with n(r) linearly interpolated from the
+    radial profile over [0, profile_rmax] (uniform if no profile).
+    """
+    px, py = spec.ppc_x, spec.ppc_y
+    iy, ix, sy, sx = torch.meshgrid(torch.arange(spec.ny), torch.arange(spec.nx),
+                                    torch.arange(py), torch.arange(px), indexing="ij")
+    x = spec.xmin + (ix.to(DT) + (sx.to(DT) + 0.5) / px) * spec.dx
+    y = spec.ymin + (iy.to(DT) + (sy.to(DT) + 0.5) / py) * spec.dy
+    x = x.reshape(-1)
+    y = y.reshape(-1)
+    if n0_scale is None:
+        n0_scale = torch.tensor(spec.n0_scale, dtype=DT)
+    dens = torch.ones_like(x)
+    prof = radial_profile
+    if prof is None and spec.radial_profile is not None:
+        prof = torch.tensor(list(spec.radial_profile), dtype=DT)
+    if prof is not None:
+        npf = prof.shape[0]
+        r = torch.sqrt(x * x + y * y)
+        t = torch.clamp(r / spec.profile_rmax * (npf - 1), 0.0, float(npf - 1))
+        k0 = torch.clamp(torch.floor(t).to(torch.int64), 0, npf - 2)
+        fr = t - k0.to(DT)
+        dens = prof[k0] * (1.0 - fr) + prof[k0 + 1] * fr
+    w = n0_scale * dens * (spec.dx * spec.dy / (px * py))
+    z = torch.zeros_like(x)
+    return dict(x=x, y=y, ux=z.clone(), uy=z.clone(), psi=z.clone(), w=w,
+                alive=torch.ones_like(x, dtype=torch.bool))
+
+
+def plasma_deposit_full(spec: GridSpec, st, q=PLASMA_Q, m=PLASMA_M):
+    """rho, Jx, Jy, Jz, chi of the plasma slice (Sec. 2 step 2; densities per reading above)."""
+    A = spec.dx * spec.dy
+    opp = 1.0 + st["psi"]
+    g = 1.0 / opp
+    gam = (1.0 + st["ux"] ** 2 + st["uy"] ** 2 + opp * opp) * 0.5 * g
+    uz = (1.0 + st["ux"] ** 2 + st["uy"] ** 2 - opp * opp) * 0.5 * g
+    qw = torch.where(st["alive"], q * st["w"], torch.zeros_like(st["w"])) / A
+    vals = [qw * gam * g, qw * st["ux"] * g, qw * st["uy"] * g, qw * uz * g, qw * q * g / m]
+    return deposit(spec, st["x"], st["y"], vals, spec.shape_order)
+
+
+def _state_ok(spec: GridSpec, x, y, psi):
+    fin = torch.isfinite(x) & torch.isfinite(y) & torch.isfinite(psi)
+    inside = (x > spec.xmin) & (x < spec.xmax) & (y > spec.ymin) & (y < spec.ymax)
+    return fin & inside & (1.0 + psi >= spec.psi_guard)
+
+
+def plasma_deposit_jperp(spec: GridSpec, x, y, ux, uy, psi, w, ok, q=PLASMA_Q):
+    """Jx, Jy of (trial) particles; particles with ok == False contribute nothing."""
+    A = spec.dx * spec.dy
+    one = torch.ones_like(psi)
+    safe = lambda t, fill: torch.where(ok, t, fill)  # noqa: E731
+    xs, ys = safe(x, torch.full_like(x, spec.xmin)), safe(y, torch.full_like(y, spec.ymin))
+    g = 1.0 / safe(1.0 + psi, one)
+    qw = torch.where(ok, q * w, torch.zeros_like(w)) / A
+    return deposit(spec, xs, ys, [qw * safe(ux, 0 * one) * g, qw * safe(uy, 0 * one) * g],
+                   spec.shape_order)
+
+
+def ion_background(spec: GridSpec, st0, q=PLASMA_Q):
+    """Immobile ions: minus the initial electron charge density, deposited with the same shape."""
+    A = spec.dx * spec.dy
+    (rho_e,) = deposit(spec, st0["x"], st0["y"], [q * st0["w"] / A], spec.shape_order)
+    return -rho_e
+
+
+# ----------------------------------------------------------------------------
+# Beams (Sec. 3.1: beam particles sorted per slice; order-0 longitudinal deposit)
+# ----------------------------------------------------------------------------
+
+def beam_bins(spec: GridSpec, zeta: torch.Tensor) -> torch.Tensor:
+    """Slice index floor((zeta_max - zeta)/dzeta); -1 for particles outside [0, nzeta)."""
+    t = torch.floor((spec.zeta_max - zeta) / spec.dzeta)
+    ok = torch.isfinite(t) & (t >= 0) & (t < spec.nzeta)
+    return torch.where(ok, t, torch.full_like(t, -1.0)).to(torch.int64)
+
+
+def beam_csr(spec: GridSpec, bins: torch.Tensor):
+    """Counting-sort offsets: particles of slice i are order[off[i]:off[i+1]] (stable)."""
+    counts = torch.bincount(bins[bins >= 0], minlength=spec.nzeta)
+    off = torch.zeros(spec.nzeta + 1, dtype=torch.int64)
+    off[1:] = torch.cumsum(counts, 0)
+    sel = torch.nonzero(bins >= 0).reshape(-1)
+    order = sel[torch.argsort(bins[sel], stable=True)]
+    return off, order
+
+
+def beam_deposit_slice(spec: GridSpec, beam, sel: torch.Tensor, channels=("rho", "jx", "jy", "jz")):
+    """Beam rho, J of the particles `sel` (one slice): rho = q w S/(dx dy dzeta), J = rho u/gamma."""
+    x, y = beam["x"][sel], beam["y"][sel]
+    ux, uy, uz, w = beam["ux"][sel], beam["uy"][sel], beam["uz"][sel], beam["w"][sel]
+    gam = torch.sqrt(1.0 + ux * ux + uy * uy + uz * uz)
+    r = beam["charge"] * w / (spec.dx * spec.dy * spec.dzeta)
+    table = dict(rho=r, jx=r * ux / gam, jy=r * uy / gam, jz=r * uz / gam)
+    return deposit(spec, x, y, [table[c] for c in channels], spec.shape_order)
+
+
+def beam_push(spec: GridSpec, beam, sel, F, dt: float):
+    """Drift-kick-drift (Boris kick) step of length dt for beam particles `sel`.
+
+    F = slice fields (ExmBy, EypBx, Ez, Bx, By, Bz); E = (ExmBy + By, EypBx - Bx, Ez),
+    B = (Bx, By, Bz).  zeta advances with v_z - 1.  Returns updated copies of the arrays.
+    """
+    qm = beam["charge"] / beam["mass"]
+    x, y, z = beam["x"][sel], beam["y"][sel], beam["zeta"][sel]
+    ux, uy, uz = beam["ux"][sel], beam["uy"][sel], beam["uz"][sel]
+    h = 0.5 * dt
+
+    def drift(x, y, z, ux, uy, uz):
+        ig = 1.0 / torch.sqrt(1.0 + ux * ux + uy * uy + uz * uz)
+        return x + h * ux * ig, y + h * uy * ig, z + h * (uz * ig - 1.0)
+
+    x, y, z = drift(x, y, z, ux, uy, uz)
+    exmby, eypbx, ez, bx, by, bz = gather(spec, x, y, F, spec.shape_order)
+    ex, ey = exmby + by, eypbx - bx
+    # Boris: half electric kick, magnetic rotation, half electric kick
+    ux, uy, uz = ux + qm * h * ex, uy + qm * h * ey, uz + qm * h * ez
+    ig = 1.0 / torch.sqrt(1.0 + ux * ux + uy * uy + uz * uz)
+    tx, ty, tz = qm * h * bx * ig, qm * h * by * ig, qm * h * bz * ig
+    s = 2.0 / (1.0 + tx * tx + ty * ty + tz * tz)
+    px = ux + (uy * tz - uz * ty)
+    py = uy + (uz * tx - ux * tz)
+    pz = uz + (ux * ty - uy * tx)
+    ux = ux + s * (py * tz - pz * ty)
+    uy = uy + s * (pz * tx - px * tz)
+    uz = uz + s * (px * ty - py * tx)
+    ux, uy, uz = ux + qm * h * ex, uy + qm * h * ey, uz + qm * h * ez
+    x, y, z = drift(x, y, z, ux, uy, uz)
+    out = dict(beam)
+    for k, v in (("x", x), ("y", y), ("zeta", z), ("ux", ux), ("uy", uy), ("uz", uz)):
+        out[k] = beam[k].index_copy(0, sel, v)
+    return out
+
+
+def as_beam(arrays: dict, charge: float = -1.0, mass: float = 1.0):
+    """Convert a dict of numpy/torch arrays (x, y, zeta, ux, uy, uz, w) to float64 tensors."""
+    out = {k: torch.as_tensor(arrays[k], dtype=DT) for k in ("x", "y", "zeta", "ux", "uy", "uz", "w")}
+    out["charge"] = float(arrays.get("charge", charge))
+    out["mass"] = float(arrays.get("mass", mass))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# The slice loop (Sec. 2 enumerate, Fig. 1; Sec. 3.2 predictor-corrector)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class SweepResult:
+    fields: dict = field(default_factory=dict)      # name -> (n_slices, ny, nx)
+    pc_residual: list = field(default_factory=list)  # per slice, last P-C iteration
+    removed: int = 0
+    plasma: dict = field(default_factory=dict)       # plasma state after the last slice
+    beams: list = field(default_factory=list)        # beams after the push (dt != 0)
+    witness: dict = field(default_factory=dict)      # beam index -> (sum qw, sum qw Ez, sum qw Ez^2)
+    plasma_at: dict = field(default_factory=dict)    # slice -> plasma state at that slice
+
+
+def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
+          n_slices: Optional[int] = None, record: Sequence[str] = FIELD_NAMES,
+          witness: Sequence[int] = (), record_plasma_at: Sequence[int] = (),
+          n0_scale: Optional[torch.Tensor] = None, radial_profile: Optional[torch.Tensor] = None,
+          ) -> SweepResult:
+    """One quasi-static sweep head -> tail (Sec. 2), slices i = 0 .. n_slices-1.
+
+    Per slice (Sec. 2 steps 1-7 and the Sec. 3.2 predictor-corrector):
+      deposit plasma + ions + beam(i); solve psi -> ExmBy, EypBx; Ez; Bz;
+      predictor-corrector for Bx, By; final gather; push plasma to i+1.
+    dt != 0 also advances every beam particle once with its own slice's fields.
+    """
+    ns = spec.nzeta if n_slices is None else n_slices
+    dz = spec.dzeta
+    qm = PLASMA_Q / PLASMA_M
+    st = plasma_init(spec, n0_scale, radial_profile)
+    rho_ion = ion_background(spec, st)
+    zero = torch.zeros(spec.ny, spec.nx, dtype=DT)
+    hist = [(torch.zeros_like(st["x"]),) * 5 for _ in range(4)]  # f_{i-1} .. f_{i-4}
+    beams = [dict(b) for b in beams]
+    csr = [beam_csr(spec, beam_bins(spec, b["zeta"])) for b in beams]
+    sel_of = lambda bi, i: csr[bi][1][csr[bi][0][i]:csr[bi][0][i + 1]]  # noqa: E731
+
+    res = SweepResult()
+    rec = {k: [] for k in record}
+    wit = {bi: [torch.zeros((), dtype=DT)] * 3 for bi in witness}
+    jx_prev, jy_prev = zero, zero
+    b1 = (zero, zero)
+    b2 = (zero, zero)
+    src = plasma_deposit_full(spec, st)
+    for i in range(ns):
+        if i in record_plasma_at:
+            res.plasma_at[i] = {k: v.detach().clone() for k, v in st.items()}
+        rho, jx, jy, jz, chi = src
+        rho = rho + rho_ion
+        for bi, b in enumerate(beams):
+            brho, bjx, bjy, bjz = beam_deposit_slice(spec, b, sel_of(bi, i))
+            rho, jx, jy, jz = rho + brho, jx + bjx, jy + bjy, jz + bjz
+        psi = poisson_solve(spec, -(rho - jz))
+        exmby, eypbx = -ddx(spec, psi), -ddy(spec, psi)
+        ez = poisson_solve(spec, ddx(spec, jx) + ddy(spec, jy))
+        bz = poisson_solve(spec, ddy(spec, jx) - ddx(spec, jy))
+        bx, by = 2.0 * b1[0] - b2[0], 2.0 * b1[1] - b2[1]
+        sbx0, sby0 = -ddy(spec, jz), ddx(spec, jz)
+        njx, njy = zero, zero
+        if i + 1 < spec.nzeta:
+            for bi, b in enumerate(beams):
+                tjx, tjy = beam_deposit_slice(spec, b, sel_of(bi, i + 1), ("jx", "jy"))
+                njx, njy = njx + tjx, njy + tjy
+        resid = 0.0
+        for _m in range(spec.n_pc_iter):
+            F = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bx, by, bz), spec.shape_order)
+            f = derivs(qm, st["ux"], st["uy"], st["psi"], F)
+            tx, ty, tux, tuy, tpsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
+                                              [f] + hist, dz)
+            ok = st["alive"] & _state_ok(spec, tx, ty, tpsi)
+            pjx, pjy = plasma_deposit_jperp(spec, tx, ty, tux, tuy, tpsi, st["w"], ok)
+            jx1, jy1 = pjx + njx, pjy + njy
+            dzjx, dzjy = (jx_prev - jx1) / (2.0 * dz), (jy_prev - jy1) / (2.0 * dz)
+            bxs = poisson_solve(spec, sbx0 + dzjy)
+            bys = poisson_solve(spec, sby0 - dzjx)
+            nbx = spec.pc_mix * bxs + (1.0 - spec.pc_mix) * bx
+            nby = spec.pc_mix * bys + (1.0 - spec.pc_mix) * by
+            num = torch.sqrt(((nbx - bx) ** 2).sum() + ((nby - by) ** 2).sum())
+            den = torch.sqrt((nbx ** 2).sum() + (nby ** 2).sum())
+            resid = float(num / den) if float(den) > 0 else 0.0
+            bx, by = nbx, nby
+        res.pc_residual.append(resid)
+        Fs = (exmby, eypbx, ez, bx, by, bz)
+        F = gather(spec, st["x"], st["y"], Fs, spec.shape_order)
+        f = derivs(qm, st["ux"], st["uy"], st["psi"], F)
+        out = dict(rho=rho, jx=jx, jy=jy, jz=jz, chi=chi, psi=psi, exmby=exmby, eypbx=eypbx,
+                   ez=ez, bx=bx, by=by, bz=bz)
+        for k in record:
+            rec[k].append(out[k])
+        for bi in witness:
+            sel = sel_of(bi, i)
+            (ezw,) = gather(spec, beams[bi]["x"][sel], beams[bi]["y"][sel], (ez,), spec.shape_order)
+            qw = beams[bi]["charge"] * beams[bi]["w"][sel]
+            s0, s1, s2 = wit[bi]
+            wit[bi] = [s0 + qw.sum(), s1 + (qw * ezw).sum(), s2 + (qw * ezw * ezw).sum()]
+        if dt != 0.0:
+            for bi in range(len(beams)):
+                beams[bi] = beam_push(spec, beams[bi], sel_of(bi, i), Fs, dt)
+        # final AB5 step to slice i+1 with the converged fields, then removal and deposit
+        nx_, ny_, nux, nuy, npsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
+                                            [f] + hist, dz)
+        hist = [f] + hist[:3]
+        alive = st["alive"] & _state_ok(spec, nx_, ny_, npsi)
+        keep = lambda new, old: torch.where(alive, new, old)  # noqa: E731
+        st = dict(x=keep(nx_, st["x"]), y=keep(ny_, st["y"]), ux=keep(nux, st["ux"]),
+                  uy=keep(nuy, st["uy"]), psi=keep(npsi, st["psi"]), w=st["w"], alive=alive)
+        src = plasma_deposit_full(spec, st)
+        jx_prev, jy_prev = jx, jy
+        b2, b1 = b1, (bx, by)
+    res.fields = {k: torch.stack(v) for k, v in rec.items()}
+    res.removed = int((~st["alive"]).sum())
+    res.plasma = st
+    res.beams = beams
+    res.witness = {bi: tuple(v) for bi, v in wit.items()}
+    return res

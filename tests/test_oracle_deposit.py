@@ -1,0 +1,108 @@
+"""Pins for the oracle's shapes, deposition and gather (Sec. 3.2, orders 0-3 transverse).
+
+The brute-force reference evaluates the centred cardinal B-spline from its
+truncated-power closed form, a different formula from the oracle's local
+"floor + polynomial pieces" weights.
+"""
+import math
+
+import pytest
+import torch
+
+import oracle as O
+
+
+def spec(nx=14, ny=12, order=1):
+    return O.GridSpec(nx=nx, ny=ny, nzeta=4, xmin=-2.0, xmax=2.2, ymin=-1.5, ymax=1.5,
+                      zeta_min=0.0, zeta_max=1.0, shape_order=order)
+
+
+def bspline(t, p):
+    """Centred cardinal B-spline of degree p via truncated powers."""
+    if p == 0:
+        return 1.0 if -0.5 <= t < 0.5 else 0.0
+    s = 0.0
+    for k in range(p + 2):
+        v = t + (p + 1) / 2.0 - k
+        if v > 0:
+            s += (-1) ** k * math.comb(p + 1, k) * v ** p
+    return s / math.factorial(p)
+
+
+def rand_particles(sp, n, margin, seed):
+    g = torch.Generator().manual_seed(seed)
+    x = sp.xmin + (margin + (sp.nx - 2 * margin) * torch.rand(n, generator=g, dtype=torch.float64)) * sp.dx
+    y = sp.ymin + (margin + (sp.ny - 2 * margin) * torch.rand(n, generator=g, dtype=torch.float64)) * sp.dy
+    v = torch.randn(n, generator=g, dtype=torch.float64)
+    return x, y, v
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_deposit_brute_force(order):
+    sp = spec(nx=9, ny=8, order=order)
+    x, y, v = rand_particles(sp, 40, 0.0, 11 + order)
+    (got,) = O.deposit(sp, x, y, [v], order)
+    ref = torch.zeros(sp.ny, sp.nx, dtype=torch.float64)
+    for p in range(x.shape[0]):
+        ux = (float(x[p]) - sp.xmin) / sp.dx
+        uy = (float(y[p]) - sp.ymin) / sp.dy
+        for i in range(1, sp.ny):
+            for j in range(1, sp.nx):
+                ref[i, j] += float(v[p]) * bspline(ux - j, order) * bspline(uy - i, order)
+    assert torch.allclose(got, ref, atol=1e-13)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_charge_conservation(order):
+    sp = spec(order=order)
+    x, y, v = rand_particles(sp, 500, 2.5, 5 + order)  # >= 2.5 cells from the wall
+    (rho,) = O.deposit(sp, x, y, [v], order)
+    assert abs(float(rho.sum()) - float(v.sum())) <= 1e-13 * float(v.abs().sum())
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+@pytest.mark.parametrize("ppc", [(1, 1), (2, 1), (2, 2)])
+def test_partition_of_unity(order, ppc):
+    sp = spec(order=order)
+    sp.ppc_x, sp.ppc_y = ppc
+    st = O.plasma_init(sp)
+    (n,) = O.deposit(sp, st["x"], st["y"], [st["w"] / (sp.dx * sp.dy)], order)
+    inner = n[3:-3, 3:-3]
+    assert torch.allclose(inner, torch.ones_like(inner), atol=1e-14)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_gather_reproduces_affine(order):
+    sp = spec(order=order)
+    xs = sp.xmin + torch.arange(sp.nx, dtype=torch.float64) * sp.dx
+    ys = sp.ymin + torch.arange(sp.ny, dtype=torch.float64) * sp.dy
+    F = 0.3 + 1.7 * xs[None, :] - 0.9 * ys[:, None]
+    x, y, _ = rand_particles(sp, 300, 2.5, 21)
+    (g,) = O.gather(sp, x, y, [F], order)
+    assert torch.allclose(g, 0.3 + 1.7 * x - 0.9 * y, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_gather_is_deposit_transpose(order):
+    sp = spec(order=order)
+    x, y, w = rand_particles(sp, 200, 0.0, 31)  # includes particles touching the wall
+    g = torch.Generator().manual_seed(9)
+    F = torch.randn(sp.ny, sp.nx, generator=g, dtype=torch.float64)
+    (D,) = O.deposit(sp, x, y, [w], order)
+    (G,) = O.gather(sp, x, y, [F], order)
+    lhs, rhs = float((F * D).sum()), float((w * G).sum())
+    assert abs(lhs - rhs) <= 1e-13 * (abs(lhs) + 1.0)
+
+
+def test_rho_minus_jz_identity():
+    sp = spec(order=2)
+    x, y, _ = rand_particles(sp, 300, 1.0, 41)
+    g = torch.Generator().manual_seed(4)
+    st = dict(x=x, y=y, ux=0.3 * torch.randn(300, generator=g, dtype=torch.float64),
+              uy=0.3 * torch.randn(300, generator=g, dtype=torch.float64),
+              psi=0.5 * torch.rand(300, generator=g, dtype=torch.float64) - 0.4,
+              w=torch.rand(300, generator=g, dtype=torch.float64),
+              alive=torch.ones(300, dtype=torch.bool))
+    rho, jx, jy, jz, chi = O.plasma_deposit_full(sp, st)
+    (ref,) = O.deposit(sp, x, y, [O.PLASMA_Q * st["w"] / (sp.dx * sp.dy)], 2)
+    assert torch.allclose(rho - jz, ref, atol=1e-13)

@@ -1,0 +1,158 @@
+"""Whole-loop pins for the oracle's quasi-static sweep (Sec. 2 slice routine, Fig. 1).
+
+  * no beam: every field but chi is exactly zero and the plasma does not move;
+  * an on-axis beam on a symmetric grid gives the mirror/swap parities;
+  * Ez and -d(psi)/d(zeta), solved independently, agree to O(dzeta^2, dx^2);
+  * sum over nodes of the plasma (rho - Jz) is conserved slice to slice;
+  * a weak driver reproduces the discrete linear wake, Phi_hat = rho_hat_b/(lambda - 1),
+    Ez = int cos(zeta' - zeta) Phi dzeta', with the error falling as dx shrinks;
+  * beam binning matches a brute-force per-particle floor.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2109_10277_gb300 import inputs as I
+
+
+def linear_grid(nx=32, nz=32, order=1, npc=5, **kw):
+    g = dict(nx=nx, ny=nx, nzeta=nz, xmin=-6.0, xmax=6.0, ymin=-6.0, ymax=6.0,
+             zeta_min=-7.0, zeta_max=5.0, shape_order=order, n_pc_iter=npc, pc_mix=0.05)
+    g.update(kw)
+    return g
+
+
+def test_zero_beam_invariant():
+    g = linear_grid(nx=24, nz=12, order=2)
+    sp = O.GridSpec(**g)
+    r = O.sweep(sp, [])
+    for k, v in r.fields.items():
+        if k != "chi":
+            assert torch.all(v == 0), k
+    st0 = O.plasma_init(sp)
+    for k in ("x", "y", "ux", "uy", "psi"):
+        assert torch.equal(r.plasma[k], st0[k]), k
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_symmetry_on_axis_beam(order):
+    g = linear_grid(nx=32, nz=24, order=order)
+    sp = O.GridSpec(**g)
+    beam = O.as_beam(I.fixed_ppc_beam(g, 0.8, 1.0, 0.5))
+    r = O.sweep(sp, [beam])
+    N = sp.nx
+    mx = lambda F: torch.cat([F[..., :1], F[..., 1:].flip(-1)], -1)  # noqa: E731  node j -> N-j
+    my = lambda F: torch.cat([F[..., :1, :], F[..., 1:, :].flip(-2)], -2)  # noqa: E731
+    sw = lambda F: F.transpose(-1, -2)  # noqa: E731
+    f = r.fields
+    tol = lambda F: 1e-10 * float(F.abs().max()) + 1e-300  # noqa: E731
+    for k in ("rho", "jz", "psi", "ez", "chi"):
+        assert float((f[k] - mx(f[k])).abs().max()) <= tol(f[k]), k
+        assert float((f[k] - my(f[k])).abs().max()) <= tol(f[k]), k
+        assert float((f[k] - sw(f[k])).abs().max()) <= tol(f[k]), k
+    assert float((f["bx"] + my(f["bx"])).abs().max()) <= tol(f["bx"])
+    assert float((f["bx"] - mx(f["bx"])).abs().max()) <= tol(f["bx"])
+    assert float((f["by"] + mx(f["by"])).abs().max()) <= tol(f["by"])
+    assert float((f["bx"] + sw(f["by"])).abs().max()) <= tol(f["bx"])
+    assert float((f["exmby"] + mx(f["exmby"])).abs().max()) <= tol(f["exmby"])
+    assert float((f["eypbx"] - sw(f["exmby"])).abs().max()) <= tol(f["exmby"])
+    # curl(J_perp) is odd in x, odd in y and antisymmetric under x <-> y (zero only in the continuum)
+    assert float((f["bz"] + mx(f["bz"])).abs().max()) <= tol(f["bz"])
+    assert float((f["bz"] + my(f["bz"])).abs().max()) <= tol(f["bz"])
+    assert float((f["bz"] + sw(f["bz"])).abs().max()) <= tol(f["bz"])
+    assert float(f["ez"].abs().max()) > 0
+
+
+def test_ez_is_minus_dzeta_psi():
+    errs = []
+    for nz in (32, 64):
+        g = linear_grid(nx=32, nz=nz, npc=20)
+        sp = O.GridSpec(**g)
+        beam = O.as_beam(I.fixed_ppc_beam(g, 1.0, 1.0, 1e-3))
+        r = O.sweep(sp, [beam], record=("ez", "psi"))
+        ez, psi = r.fields["ez"], r.fields["psi"]
+        dpsi = -(psi[:-2] - psi[2:]) / (2 * sp.dzeta)
+        e = ez[1:-1]
+        errs.append(float(torch.linalg.norm(e - dpsi) / torch.linalg.norm(e)))
+    assert errs[0] < 0.05 and errs[1] < errs[0], errs
+
+
+def test_plasma_rho_minus_jz_conserved():
+    # plasma column that ends 1.7 k_p^-1 inside the wall, so no weighted particle deposits on it
+    prof = [1.0 if k <= 7 else 0.0 for k in range(17)]
+    g = linear_grid(nx=32, nz=32, order=2, radial_profile=prof, profile_rmax=6.0 * math.sqrt(2.0))
+    sp = O.GridSpec(**g)
+    beam = O.as_beam(I.fixed_ppc_beam(g, 0.6, 1.0, 0.2))
+    r = O.sweep(sp, [beam], record=("rho", "jz"))
+    st0 = O.plasma_init(sp)
+    ion = O.ion_background(sp, st0)
+    csr = O.beam_csr(sp, O.beam_bins(sp, beam["zeta"]))
+    sums = []
+    for i in range(sp.nzeta):
+        brho, bjz = O.beam_deposit_slice(sp, beam, csr[1][csr[0][i]:csr[0][i + 1]], ("rho", "jz"))
+        plasma = r.fields["rho"][i] - r.fields["jz"][i] - ion - (brho - bjz)
+        sums.append(float(plasma.sum()))
+    expect = O.PLASMA_Q * float(st0["w"].sum()) / (sp.dx * sp.dy)
+    assert max(abs(s - expect) for s in sums) <= 1e-12 * abs(expect)
+    assert float(r.fields["jz"].abs().max()) > 1e-3  # the plasma did respond
+
+
+def linear_wake_error(nx, nz, nb0, npc=40, sr=1.0, sz=1.0):
+    g = linear_grid(nx=nx, nz=nz, npc=npc)
+    sp = O.GridSpec(**g)
+    beam = O.as_beam(I.fixed_ppc_beam(g, sr, sz, nb0))
+    r = O.sweep(sp, [beam], record=("ez",))
+    ez = r.fields["ez"][:, nx // 2, nx // 2].numpy()
+    lam = O.laplace_eigs(sp)
+    dz = sp.dzeta
+    zc = sp.zeta_max - (np.arange(nz) + 0.5) * dz
+    off, order = O.beam_csr(sp, O.beam_bins(sp, beam["zeta"]))
+    phi = np.zeros(nz)
+    for i in range(nz):
+        (rb,) = O.beam_deposit_slice(sp, beam, order[off[i]:off[i + 1]], ("rho",))
+        hat = O.dst2(sp, rb) / (lam - 1.0)
+        hat[0, :] = 0.0
+        hat[:, 0] = 0.0
+        phi[i] = float((4.0 / (nx * nx) * O.dst2(sp, hat))[nx // 2, nx // 2])
+    lin = np.zeros(nz)
+    for i in range(nz):
+        for k in range(i + 1):  # Phi constant over each slice; integrate cos(z' - zeta_i) from zeta_i up
+            hi = zc[k] + dz / 2
+            lo = max(zc[k] - dz / 2, zc[i])
+            lin[i] += phi[k] * (math.sin(hi - zc[i]) - math.sin(lo - zc[i]))
+    win = zc >= -2 * math.pi  # head of the box to one plasma period behind the driver centre
+    return float(np.sqrt(((ez - lin)[win] ** 2).sum() / (lin[win] ** 2).sum()))
+
+
+def test_linear_wake_closed_form():
+    e64 = linear_wake_error(64, 64, 1e-3)
+    assert e64 < 5e-2, e64
+
+
+@pytest.mark.slow
+def test_linear_wake_converges_in_dx():
+    e64 = linear_wake_error(64, 64, 1e-3)
+    e128 = linear_wake_error(128, 128, 1e-3)
+    assert e128 < 0.6 * e64, (e64, e128)
+
+
+def test_beam_binning_brute_force():
+    g = linear_grid(nx=16, nz=40)
+    sp = O.GridSpec(**g)
+    b = I.random_beam(3000, 0.5, 0.5, 3.0, 1.0, zeta0=-1.0)
+    beam = O.as_beam(b)
+    bins = O.beam_bins(sp, beam["zeta"])
+    off, order = O.beam_csr(sp, bins)
+    ref = []
+    for z in b["zeta"]:
+        t = math.floor((sp.zeta_max - float(z)) / sp.dzeta)
+        ref.append(t if 0 <= t < sp.nzeta else -1)
+    ref = np.array(ref)
+    assert np.array_equal(bins.numpy(), ref)
+    for i in range(sp.nzeta):
+        members = sorted(order[off[i]:off[i + 1]].tolist())
+        assert members == sorted(np.nonzero(ref == i)[0].tolist())
+    assert int(off[-1]) == int((ref >= 0).sum())
