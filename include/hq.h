@@ -1,0 +1,177 @@
+/*
+ * hq.h -- C ABI of a GB300 (sm_103a) implementation of the quasi-static PIC
+ * per-slice loop of arXiv:2109.10277 (HiPACE++), Sec. 2 and Sec. 3.
+ *
+ * Units are the paper's normalized units (Sec. 5, "normalized units"): lengths
+ * in 1/k_p, fields in E0 = m c omega_p / e, densities in n0, c = eps0 = mu0 = 1.
+ * Plasma electrons have charge -1 and mass 1; ions are immobile.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named "device" must point to CUDA device memory (for example the
+ *    data of a torch CUDA tensor); the caller owns them and keeps them alive
+ *    until the work queued on the grid's stream has finished.
+ *  - Calls are asynchronous on the stream given to hq_grid_create.  Argument and
+ *    ordering errors are reported synchronously by the return value; faults seen
+ *    inside kernels (a bounded wait that ran out, a non-finite field) set a device
+ *    status word that hq_sync reports.
+ *  - No C++ exception crosses this boundary.  After a non-OK status,
+ *    hq_last_error(grid) returns a message (valid until the next call on the grid).
+ *  - A grid is used by one host thread at a time.
+ *
+ * Data layout: a transverse field slice is ny x nx values, row-major, row = y.
+ * Node (iy, ix) sits at (xmin + ix*dx, ymin + iy*dy); nodes 0 and nx (ny) lie on
+ * the Dirichlet wall, so row 0 and column 0 of every field are zero.  Field
+ * values are double for HQ_PREC_FP64 grids and float for HQ_PREC_FP32_BF16X3.
+ * Beam arrays are always double.
+ */
+#ifndef HQ_H
+#define HQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HQ_OK = 0,
+  HQ_ERR_ARG = 1,      /* invalid argument (null pointer, size out of range)          */
+  HQ_ERR_CUDA = 2,     /* a CUDA runtime call failed                                   */
+  HQ_ERR_OOM = 3,      /* a device allocation failed                                   */
+  HQ_ERR_NUMERIC = 4,  /* a non-finite value reached the field solve                  */
+  HQ_ERR_TIMEOUT = 5,  /* a bounded device-side wait ran out (kernel returned early)   */
+  HQ_ERR_STATE = 6,    /* call out of order (slices must be visited 0, 1, 2, ...)      */
+  HQ_ERR_UNSUPPORTED = 7
+} hq_status;
+
+typedef enum {
+  /* everything in FP64, DST-I by an FP64 FFT */
+  HQ_PREC_FP64 = 0,
+  /* push/gather/deposit in FP32 with FP64 position and Psi accumulators; the DST-I
+     as dense products on the tensor cores with each FP32 operand split into two
+     bf16 terms (3 products, FP32 accumulation) */
+  HQ_PREC_FP32_BF16X3 = 1
+} hq_precision;
+
+/* Grid, plasma and solver description; every field is copied by hq_grid_create.
+ * Sec. 2 (slice loop), Sec. 3.2 (push, deposition, Poisson and P-C solvers). */
+typedef struct {
+  int32_t nx, ny, nzeta;            /* cells; 8 <= nx, ny <= 4096, nzeta >= 1          */
+  double xmin, xmax, ymin, ymax;    /* Dirichlet box                                   */
+  double zeta_min, zeta_max;        /* slice i covers zeta_max - (i+1) dz .. - i dz    */
+  int32_t shape_order;              /* transverse B-spline order 0..3 (Sec. 3.2)       */
+  int32_t ppc_x, ppc_y;             /* plasma particles per cell, at sub-cell centres  */
+  const double* radial_profile;     /* host; n_profile entries over r in [0, rmax],
+                                       linearly interpolated; NULL = uniform           */
+  int32_t n_profile;
+  double profile_rmax;
+  double n0_scale;                  /* multiplies plasma (and ion) density            */
+  int32_t n_pc_iter;                /* predictor-corrector iterations (fixed count)   */
+  double pc_mix;                    /* B <- pc_mix * B_solved + (1 - pc_mix) * B      */
+  double psi_guard;                 /* particle removed when 1 + Psi < psi_guard      */
+  int32_t precision;                /* hq_precision                                   */
+} hq_grid_desc;
+
+/* One beam species, structure of arrays in DEVICE memory (double), n particles.
+ * x, y, zeta and ux, uy, uz (normalized momenta) are updated in place by the
+ * beam push; w is the number of physical particles per macroparticle in units
+ * of n0 / k_p^3. */
+typedef struct {
+  int64_t n;
+  double *x, *y, *zeta, *ux, *uy, *uz, *w;
+  double charge, mass;              /* units of e and m_e                              */
+} hq_beam_view;
+
+/* Per-slice field outputs, DEVICE arrays of nzeta x ny x nx elements of the grid's
+ * field type (see top); a NULL member is not written.  rho and J are totals
+ * (plasma + ions + beams); exmby = Ex - By, eypbx = Ey + Bx (Eq. exmby). */
+typedef struct {
+  void *rho, *jx, *jy, *jz, *chi, *psi, *exmby, *eypbx, *ez, *bx, *by, *bz;
+} hq_field_out;
+
+/* Read-only DEVICE views of the plasma slice (library-owned memory, valid until
+ * hq_grid_destroy).  x, y, psi are double; ux, uy, w are of the field type;
+ * alive is uint8 (0 once a particle is removed). */
+typedef struct {
+  int64_t n;
+  const double *x, *y, *psi;
+  const void *ux, *uy, *w;
+  const uint8_t* alive;
+} hq_plasma_view;
+
+typedef struct hq_grid_s* hq_grid_t;
+
+/* Creates a grid: validates desc, allocates the plasma slice, field slices and
+ * transform scratch on the current device, and builds the DST tables.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: HQ_ERR_ARG (bad desc), HQ_ERR_OOM, HQ_ERR_CUDA, HQ_ERR_UNSUPPORTED
+ * (HQ_PREC_FP32_BF16X3 needs a compute capability 10.x device). */
+hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t* out);
+
+/* Frees everything the grid owns (synchronizes its stream first). NULL is a no-op. */
+hq_status hq_grid_destroy(hq_grid_t grid);
+
+/* Sec. 2 step 1-2: for slice 0, resets the plasma to its unperturbed state ahead of
+ * the beams (Sec. 2, "a slice of unperturbed plasma is initialized ahead of the
+ * beams") and deposits it.  For slice i > 0, gathers the converged fields of slice
+ * i-1, takes the final AB5 step (Sec. 3.2 plasma push) to slice i, applies the
+ * removal rule, and deposits rho, J, chi of slice i.  Requires hq_solve_fields(i-1)
+ * (HQ_ERR_STATE otherwise). */
+hq_status hq_advance_slice(hq_grid_t grid, int32_t slice);
+
+/* Sec. 2 step 3 and Sec. 3.1 (beams sorted per slice): adds the charge and
+ * current of the beam particles whose zeta falls in slice i (order 0
+ * longitudinally), and stores J_perp of slice i+1 for the predictor-corrector.
+ * On slice 0 the beams are binned by slice (counting sort on the device); later
+ * slices of the same sweep must pass the same views (HQ_ERR_STATE otherwise).
+ * At most 4 beams.  Requires hq_advance_slice(i). */
+hq_status hq_beam_deposit(hq_grid_t grid, const hq_beam_view* beams, int32_t nbeams, int32_t slice);
+
+/* Sec. 2 steps 4-7 and Sec. 3.2 (fast Poisson solver, predictor-corrector):
+ * solves psi and ExmBy, EypBx = -grad psi (Eq. psi, exmby), Ez (Eq. ez), Bz (Eq. bz),
+ * then n_pc_iter predictor-corrector iterations for Bx, By (Eq. bxby).
+ * Requires hq_beam_deposit(i) (nbeams may be 0). */
+hq_status hq_solve_fields(hq_grid_t grid, int32_t slice);
+
+/* Copies the fields of the last solved slice into out at element offset
+ * slot * ny * nx (Sec. 3.1: per-slice diagnostics). */
+hq_status hq_store_fields(hq_grid_t grid, const hq_field_out* out, int64_t slot);
+
+/* Sec. 3.2 (beam pusher): advances the particles of slice i of each beam by dt
+ * with a second-order drift-kick-drift step (Boris kick) in the fields of the last
+ * solved slice, which must be i.  Positions and momenta are updated in place. */
+hq_status hq_push_beams(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, int32_t slice, double dt);
+
+/* Adds sum(q w), sum(q w Ez), sum(q w Ez^2) over the particles of slice i of
+ * `beam` (Ez gathered with the grid's shape) to sums[0..2] (DEVICE double[3]). */
+hq_status hq_witness_accumulate(hq_grid_t grid, const hq_beam_view* beam, int32_t slice, double* sums);
+
+/* One full quasi-static sweep head -> tail (Sec. 2, Fig. 1): for every slice,
+ * advance, beam deposit, field solve, then optionally store the fields (out may be
+ * NULL), push the beams (dt != 0), and accumulate witness sums (witness_beam >= 0,
+ * witness_sums a DEVICE double[3], zeroed by the caller).  After the last slice the
+ * plasma is advanced once more, so hq_plasma_state shows the state past the box. */
+hq_status hq_sweep_step(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, double dt,
+                        const hq_field_out* out, int32_t witness_beam, double* witness_sums);
+
+/* Solves nrhs (1..5) Dirichlet Poisson problems L f = s with the grid's DST-I
+ * backend (Sec. 3.2, fast Poisson solver): src and dst are DEVICE arrays of
+ * nrhs x ny x nx field-type values (row/col 0 of src are ignored). */
+hq_status hq_poisson_solve(hq_grid_t grid, const void* src, void* dst, int32_t nrhs);
+
+/* Fills *out with views of the plasma slice (state after the last advance). */
+hq_status hq_plasma_state(hq_grid_t grid, hq_plasma_view* out);
+
+/* Waits for the grid's stream, then reports device status: HQ_ERR_TIMEOUT or
+ * HQ_ERR_NUMERIC if a kernel flagged one (the flag is cleared), else HQ_OK.
+ * removed (may be NULL) receives the number of plasma particles removed so far. */
+hq_status hq_sync(hq_grid_t grid, int64_t* removed);
+
+/* Message for the last non-OK status on this grid (or a global message when
+ * grid is NULL, e.g. after a failed hq_grid_create). */
+const char* hq_last_error(hq_grid_t grid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HQ_H */

@@ -1,0 +1,551 @@
+// C ABI of libhq (declared in include/hq.h): grid lifecycle, the per-slice
+// steps of the quasi-static loop (Sec. 2 enumerate; Sec. 3.1 per-slice beam
+// work; Sec. 3.2 push, deposition, Poisson and predictor-corrector solvers)
+// and the full sweep.  Host code only orders launches on the grid's stream.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "hq_internal.cuh"
+
+using namespace hq;
+
+namespace {
+
+thread_local std::string g_global_err;
+
+hq_status fail(hq_grid_s* g, hq_status st, const std::string& msg) {
+  if (g) g->err = msg;
+  else g_global_err = msg;
+  return st;
+}
+
+#define HQ_CUDA(g, call)                                                                         \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail((g), e_ == cudaErrorMemoryAllocation ? HQ_ERR_OOM : HQ_ERR_CUDA, \
+                                       std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+void free_all(hq_grid_s* g) {
+  auto F = [](void* p) { if (p) cudaFree(p); };
+  for (hq::Plasma<double>* p : {&g->p64}) {
+    F(p->x); F(p->y); F(p->psi); F(p->ux); F(p->uy); F(p->w); F(p->alive); F(p->hist);
+  }
+  {
+    hq::Plasma<float>& p = g->p32;
+    if (!g->fp64) {
+      // x, y, psi, alive are shared with p64 storage (freed above); free the typed arrays
+      F(p.ux); F(p.uy); F(p.w); F(p.hist); F(p.cell); F(p.fx); F(p.fy); F(p.opp);
+    }
+  }
+  for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); }
+  F(g->rho_ion); F(g->tj); F(g->bjn); F(g->gf); F(g->psi); F(g->bprev1); F(g->bprev2); F(g->solved);
+  F(g->f64_a); F(g->f64_b); F(g->f64_scale); F(g->tw_x); F(g->tw_y); F(g->sin_x); F(g->sin_y);
+  F(g->sx_hi); F(g->sx_lo); F(g->sy_hi); F(g->sy_lo); F(g->f32_scale);
+  for (int b = 0; b < kMaxBeams; ++b) {
+    F(g->bins[b].bin); F(g->bins[b].count); F(g->bins[b].offset); F(g->bins[b].cursor); F(g->bins[b].perm);
+  }
+  F(g->d_profile); F(g->d_status); F(g->d_removed); F(g->d_scratch_int);
+  if (g->tmaps) dst_tc_free(g);
+}
+
+// (2/nx)(2/ny) / lambda_kl for the 5-point Laplacian; zero on mode 0 (wall).
+std::vector<double> scale_table(const hq_grid_s* g, int rows, int cols) {
+  std::vector<double> t((size_t)rows * cols, 0.0);
+  const double pi = M_PI;
+  for (int l = 1; l < g->ny; ++l) {
+    const double sy = std::sin(pi * l / (2.0 * g->ny));
+    for (int k = 1; k < g->nx; ++k) {
+      const double sx = std::sin(pi * k / (2.0 * g->nx));
+      const double lam = -(4.0 / (g->geom.dx * g->geom.dx)) * sx * sx - (4.0 / (g->geom.dy * g->geom.dy)) * sy * sy;
+      t[(size_t)l * cols + k] = (4.0 / ((double)g->nx * g->ny)) / lam;
+    }
+  }
+  return t;
+}
+
+// sin(pi j k / n) with exact argument reduction.
+double sin_jk(int64_t j, int64_t k, int n) {
+  const int64_t m = (j * k) % (2 * (int64_t)n);
+  return std::sin(M_PI * (double)m / (double)n);
+}
+
+template <typename T> void* plasma_ptr(hq_grid_s* g);
+
+template <typename T>
+hq_status solve_fields_impl(hq_grid_s* g, int slice) {
+  cudaStream_t s = g->stream;
+  void* cur = g->dep[slice & 1];
+  void* prev = g->dep[(slice + 1) & 1];
+  launch_src_main<T>(g, cur, s);
+  if (g->fp64) dst_solve_f64(g, 3, s);
+  else dst_solve_tc(g, 3, s);
+  launch_finish_main<T>(g, g->solved, s);
+  launch_bguess<T>(g, s);
+  for (int m = 0; m < g->d.n_pc_iter; ++m) {
+    launch_zero<T>(g->tj, 2 * g->nnode, s);
+    launch_trial_pass<T>(g, slice, s);
+    launch_src_bperp<T>(g, cur, prev, s);
+    if (g->fp64) dst_solve_f64(g, 2, s);
+    else dst_solve_tc(g, 2, s);
+    launch_finish_bperp<T>(g, g->solved, s);
+  }
+  launch_bshift<T>(g, s);
+  return HQ_OK;
+}
+
+template <typename T>
+void advance_impl(hq_grid_s* g, int slice) {
+  cudaStream_t s = g->stream;
+  void* dst = g->dep[slice & 1];
+  void* dchi = g->chi[slice & 1];
+  launch_reset_dep<T>(g, dst, dchi, s);
+  if (slice == 0) {
+    launch_plasma_init<T>(g, s);
+    launch_deposit_initial<T>(g, dst, dchi, 0, s);
+    launch_zero<T>(g->dep[1], 4 * g->nnode, s);   // J(-1) = 0 ahead of the box
+    launch_zero<T>(g->bprev1, 2 * g->nnode, s);
+    launch_zero<T>(g->bprev2, 2 * g->nnode, s);
+  } else {
+    launch_final_pass<T>(g, slice - 1, dst, dchi, s);
+  }
+}
+
+bool same_view(const hq_beam_view& a, const hq_beam_view& b) {
+  return a.n == b.n && a.x == b.x && a.y == b.y && a.zeta == b.zeta && a.ux == b.ux && a.uy == b.uy && a.uz == b.uz &&
+         a.w == b.w && a.charge == b.charge && a.mass == b.mass;
+}
+
+hq_status check_views(hq_grid_s* g, const hq_beam_view* beams, int nb) {
+  if (nb < 0 || nb > kMaxBeams) return fail(g, HQ_ERR_ARG, "nbeams must be 0..4");
+  if (nb > 0 && !beams) return fail(g, HQ_ERR_ARG, "beams is NULL");
+  for (int b = 0; b < nb; ++b) {
+    const hq_beam_view& v = beams[b];
+    if (v.n < 0 || v.n > 0x7fffffffLL) return fail(g, HQ_ERR_ARG, "beam size out of range");
+    if (v.n > 0 && (!v.x || !v.y || !v.zeta || !v.ux || !v.uy || !v.uz || !v.w))
+      return fail(g, HQ_ERR_ARG, "beam array is NULL");
+    if (!(v.mass > 0.0) || !std::isfinite(v.charge)) return fail(g, HQ_ERR_ARG, "beam charge/mass invalid");
+  }
+  return HQ_OK;
+}
+
+template <typename T>
+hq_status beam_deposit_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int slice) {
+  cudaStream_t s = g->stream;
+  if (slice == 0) {
+    for (int b = 0; b < nb; ++b) {
+      BeamBins& bb = g->bins[b];
+      if (bb.cap < beams[b].n) {
+        if (bb.bin) cudaFree(bb.bin);
+        if (bb.perm) cudaFree(bb.perm);
+        bb.bin = bb.perm = nullptr;
+        bb.cap = 0;
+        HQ_CUDA(g, dalloc(&bb.bin, sizeof(int32_t) * beams[b].n));
+        HQ_CUDA(g, dalloc(&bb.perm, sizeof(int32_t) * beams[b].n));
+        bb.cap = beams[b].n;
+      }
+      g->bound[b] = beams[b];
+      launch_beam_bin(g, b, beams[b], s);
+    }
+    g->nbound = nb;
+  } else {
+    if (nb != g->nbound) return fail(g, HQ_ERR_STATE, "beams differ from those binned at slice 0");
+    for (int b = 0; b < nb; ++b)
+      if (!same_view(beams[b], g->bound[b])) return fail(g, HQ_ERR_STATE, "beams differ from those binned at slice 0");
+  }
+  launch_zero<T>(g->bjn, 2 * g->nnode, s);
+  for (int b = 0; b < nb; ++b) {
+    if (beams[b].n > 0) launch_beam_deposit<T>(g, b, beams[b], slice, g->dep[slice & 1], g->bjn, s);
+  }
+  return HQ_OK;
+}
+
+int bound_index(const hq_grid_s* g, const hq_beam_view* v) {
+  for (int b = 0; b < g->nbound; ++b)
+    if (same_view(*v, g->bound[b])) return b;
+  return -1;
+}
+
+hq_status check_launch(hq_grid_s* g) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(g, HQ_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return HQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t* out) {
+  if (!desc || !out) return fail(nullptr, HQ_ERR_ARG, "desc and out must not be NULL");
+  *out = nullptr;
+  const hq_grid_desc& d = *desc;
+  if (d.nx < 8 || d.ny < 8 || d.nx > 4096 || d.ny > 4096) return fail(nullptr, HQ_ERR_ARG, "nx, ny must be in 8..4096");
+  if (d.nzeta < 1) return fail(nullptr, HQ_ERR_ARG, "nzeta must be >= 1");
+  if (!(d.xmax > d.xmin) || !(d.ymax > d.ymin) || !(d.zeta_max > d.zeta_min) || !std::isfinite(d.xmin) ||
+      !std::isfinite(d.xmax) || !std::isfinite(d.ymin) || !std::isfinite(d.ymax) || !std::isfinite(d.zeta_min) ||
+      !std::isfinite(d.zeta_max))
+    return fail(nullptr, HQ_ERR_ARG, "box bounds must be finite with max > min");
+  if (d.shape_order < 0 || d.shape_order > 3) return fail(nullptr, HQ_ERR_ARG, "shape_order must be 0..3");
+  if (d.ppc_x < 1 || d.ppc_y < 1 || d.ppc_x > 16 || d.ppc_y > 16) return fail(nullptr, HQ_ERR_ARG, "ppc must be 1..16");
+  if (d.n_pc_iter < 0 || d.n_pc_iter > 1000) return fail(nullptr, HQ_ERR_ARG, "n_pc_iter must be 0..1000");
+  if (!std::isfinite(d.pc_mix) || !std::isfinite(d.psi_guard) || !std::isfinite(d.n0_scale))
+    return fail(nullptr, HQ_ERR_ARG, "pc_mix, psi_guard and n0_scale must be finite");
+  if (d.precision != HQ_PREC_FP64 && d.precision != HQ_PREC_FP32_BF16X3)
+    return fail(nullptr, HQ_ERR_ARG, "unknown precision");
+  if (d.radial_profile && (d.n_profile < 2 || !(d.profile_rmax > 0.0)))
+    return fail(nullptr, HQ_ERR_ARG, "radial profile needs n_profile >= 2 and profile_rmax > 0");
+  const int64_t np = (int64_t)d.nx * d.ny * d.ppc_x * d.ppc_y;
+  if (np > (1LL << 31) - 1) return fail(nullptr, HQ_ERR_ARG, "too many plasma particles");
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, HQ_ERR_CUDA, "no CUDA device");
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return fail(nullptr, HQ_ERR_CUDA, "cudaGetDeviceProperties failed");
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(nullptr, HQ_ERR_UNSUPPORTED, "libhq is built for sm_103a (GB300) only; device is sm_" +
+                                                 std::to_string(prop.major) + std::to_string(prop.minor));
+
+  hq_grid_s* g = new (std::nothrow) hq_grid_s();
+  if (!g) return fail(nullptr, HQ_ERR_OOM, "host allocation failed");
+  g->d = d;
+  if (d.radial_profile) g->profile.assign(d.radial_profile, d.radial_profile + d.n_profile);
+  g->d.radial_profile = nullptr;
+  g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  g->dev = dev;
+  g->fp64 = d.precision == HQ_PREC_FP64;
+  g->nx = d.nx; g->ny = d.ny; g->nz = d.nzeta;
+  g->nnode = (int64_t)d.nx * d.ny;
+  g->np = np;
+  g->tsize = g->fp64 ? sizeof(double) : sizeof(float);
+  Geom& gm = g->geom;
+  gm.nx = d.nx; gm.ny = d.ny;
+  gm.xmin = d.xmin; gm.ymin = d.ymin; gm.xmax = d.xmax; gm.ymax = d.ymax;
+  gm.dx = (d.xmax - d.xmin) / d.nx;
+  gm.dy = (d.ymax - d.ymin) / d.ny;
+  gm.inv_dx = 1.0 / gm.dx; gm.inv_dy = 1.0 / gm.dy;
+  gm.dzeta = (d.zeta_max - d.zeta_min) / d.nzeta;
+  gm.inv_area = 1.0 / (gm.dx * gm.dy);
+  g->last_adv = g->last_beam = g->last_solved = -1;
+
+  auto bail = [&](hq_status st) {
+    std::string msg = g->err;
+    free_all(g);
+    delete g;
+    return fail(nullptr, st, msg);
+  };
+#define HQ_ALLOC(ptr, bytes)                                                                                   \
+  do {                                                                                                         \
+    cudaError_t e_ = dalloc(&(ptr), (bytes));                                                                  \
+    if (e_ != cudaSuccess) {                                                                                   \
+      g->err = std::string("cudaMalloc(" #ptr "): ") + cudaGetErrorString(e_);                                 \
+      return bail(e_ == cudaErrorMemoryAllocation ? HQ_ERR_OOM : HQ_ERR_CUDA);                                 \
+    }                                                                                                          \
+  } while (0)
+
+  const size_t ts = g->tsize, nn = (size_t)g->nnode;
+  // plasma (x, y, psi and alive are shared between the two typed views)
+  HQ_ALLOC(g->p64.x, 8 * np);
+  HQ_ALLOC(g->p64.y, 8 * np);
+  HQ_ALLOC(g->p64.psi, 8 * np);
+  HQ_ALLOC(g->p64.alive, np);
+  g->p64.n = g->p32.n = np;
+  g->p32.x = g->p64.x; g->p32.y = g->p64.y; g->p32.psi = g->p64.psi; g->p32.alive = g->p64.alive;
+  if (g->fp64) {
+    HQ_ALLOC(g->p64.ux, 8 * np); HQ_ALLOC(g->p64.uy, 8 * np); HQ_ALLOC(g->p64.w, 8 * np);
+    HQ_ALLOC(g->p64.hist, 8 * np * kRing * 5);
+  } else {
+    HQ_ALLOC(g->p32.ux, 4 * np); HQ_ALLOC(g->p32.uy, 4 * np); HQ_ALLOC(g->p32.w, 4 * np);
+    HQ_ALLOC(g->p32.hist, 4 * np * kRing * 5);
+    HQ_ALLOC(g->p32.cell, 4 * np); HQ_ALLOC(g->p32.fx, 4 * np); HQ_ALLOC(g->p32.fy, 4 * np); HQ_ALLOC(g->p32.opp, 4 * np);
+  }
+  // fields
+  for (int i = 0; i < 2; ++i) { HQ_ALLOC(g->dep[i], 4 * ts * nn); HQ_ALLOC(g->chi[i], ts * nn); }
+  HQ_ALLOC(g->rho_ion, ts * nn);
+  HQ_ALLOC(g->tj, 2 * ts * nn);
+  HQ_ALLOC(g->bjn, 2 * ts * nn);
+  HQ_ALLOC(g->gf, kGF * ts * nn);
+  HQ_ALLOC(g->psi, ts * nn);
+  HQ_ALLOC(g->bprev1, 2 * ts * nn);
+  HQ_ALLOC(g->bprev2, 2 * ts * nn);
+  HQ_ALLOC(g->solved, kMaxRhs * ts * nn);
+  HQ_ALLOC(g->d_status, sizeof(int));
+  HQ_ALLOC(g->d_removed, sizeof(unsigned long long));
+  for (int b = 0; b < kMaxBeams; ++b) {
+    HQ_ALLOC(g->bins[b].count, sizeof(int32_t) * (g->nz + 1));
+    HQ_ALLOC(g->bins[b].offset, sizeof(int32_t) * (g->nz + 1));
+    HQ_ALLOC(g->bins[b].cursor, sizeof(int32_t) * (g->nz + 1));
+  }
+  if (!g->profile.empty()) {
+    HQ_ALLOC(g->d_profile, 8 * g->profile.size());
+    if (cudaMemcpy(g->d_profile, g->profile.data(), 8 * g->profile.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      g->err = "profile upload failed";
+      return bail(HQ_ERR_CUDA);
+    }
+  }
+  // zero everything the kernels accumulate into or read before writing
+  for (void* p : {g->dep[0], g->dep[1]}) cudaMemset(p, 0, 4 * ts * nn);
+  for (void* p : {g->chi[0], g->chi[1], g->rho_ion, g->psi}) cudaMemset(p, 0, ts * nn);
+  for (void* p : {g->tj, g->bjn, g->bprev1, g->bprev2}) cudaMemset(p, 0, 2 * ts * nn);
+  cudaMemset(g->gf, 0, kGF * ts * nn);
+  cudaMemset(g->solved, 0, kMaxRhs * ts * nn);
+  cudaMemset(g->d_status, 0, sizeof(int));
+  cudaMemset(g->d_removed, 0, sizeof(unsigned long long));
+
+  // DST tables
+  if (g->fp64) {
+    HQ_ALLOC(g->f64_a, 8 * kMaxRhs * nn);
+    HQ_ALLOC(g->f64_b, 8 * kMaxRhs * nn);
+    cudaMemset(g->f64_a, 0, 8 * kMaxRhs * nn);
+    std::vector<double> sc = scale_table(g, g->ny, g->nx);
+    HQ_ALLOC(g->f64_scale, 8 * nn);
+    cudaMemcpy(g->f64_scale, sc.data(), 8 * nn, cudaMemcpyHostToDevice);
+    auto tables = [&](int n, double** tw, double** sn) -> hq_status {
+      if (is_pow2(n)) {
+        std::vector<double> t(2 * (size_t)n);
+        for (int k = 0; k < n; ++k) {
+          t[2 * k] = std::cos(M_PI * k / n);
+          t[2 * k + 1] = -std::sin(M_PI * k / n);
+        }
+        if (dalloc(tw, 8 * t.size()) != cudaSuccess) return HQ_ERR_OOM;
+        cudaMemcpy(*tw, t.data(), 8 * t.size(), cudaMemcpyHostToDevice);
+      } else {
+        std::vector<double> t((size_t)n * n);
+        for (int j = 0; j < n; ++j)
+          for (int k = 0; k < n; ++k) t[(size_t)j * n + k] = sin_jk(j, k, n);
+        if (dalloc(sn, 8 * t.size()) != cudaSuccess) return HQ_ERR_OOM;
+        cudaMemcpy(*sn, t.data(), 8 * t.size(), cudaMemcpyHostToDevice);
+      }
+      return HQ_OK;
+    };
+    if (tables(g->nx, &g->tw_x, &g->sin_x) != HQ_OK || tables(g->ny, &g->tw_y, &g->sin_y) != HQ_OK) {
+      g->err = "DST table allocation failed";
+      return bail(HQ_ERR_OOM);
+    }
+  } else {
+    g->nxp = (int)round_up(g->nx, 128);
+    g->nyp = (int)round_up(g->ny, 128);
+    const size_t opn = (size_t)kMaxRhs * g->nxp * g->nyp;
+    for (int i = 0; i < 2; ++i) {
+      HQ_ALLOC(g->op_hi[i], 2 * opn);
+      HQ_ALLOC(g->op_lo[i], 2 * opn);
+      cudaMemset(g->op_hi[i], 0, 2 * opn);
+      cudaMemset(g->op_lo[i], 0, 2 * opn);
+    }
+    auto smat = [&](int n, int np_, __nv_bfloat16** hi, __nv_bfloat16** lo) -> hq_status {
+      std::vector<__nv_bfloat16> h((size_t)np_ * np_), l((size_t)np_ * np_);
+      for (int k = 0; k < np_; ++k)
+        for (int j = 0; j < np_; ++j) {
+          const float v = (j < n && k < n) ? (float)sin_jk(j, k, n) : 0.0f;
+          const __nv_bfloat16 vh = __float2bfloat16_rn(v);
+          h[(size_t)k * np_ + j] = vh;
+          l[(size_t)k * np_ + j] = __float2bfloat16_rn(v - __bfloat162float(vh));
+        }
+      if (dalloc(hi, 2 * h.size()) != cudaSuccess || dalloc(lo, 2 * l.size()) != cudaSuccess) return HQ_ERR_OOM;
+      cudaMemcpy(*hi, h.data(), 2 * h.size(), cudaMemcpyHostToDevice);
+      cudaMemcpy(*lo, l.data(), 2 * l.size(), cudaMemcpyHostToDevice);
+      return HQ_OK;
+    };
+    if (smat(g->nx, g->nxp, &g->sx_hi, &g->sx_lo) != HQ_OK || smat(g->ny, g->nyp, &g->sy_hi, &g->sy_lo) != HQ_OK) {
+      g->err = "DST matrix allocation failed";
+      return bail(HQ_ERR_OOM);
+    }
+    std::vector<double> sc = scale_table(g, g->nyp, g->nxp);
+    std::vector<float> scf(sc.begin(), sc.end());
+    HQ_ALLOC(g->f32_scale, 4 * scf.size());
+    cudaMemcpy(g->f32_scale, scf.data(), 4 * scf.size(), cudaMemcpyHostToDevice);
+    std::string err;
+    if (dst_tc_init(g, err)) {
+      g->err = err;
+      return bail(HQ_ERR_CUDA);
+    }
+  }
+  // ion background from the initial plasma
+  if (g->fp64) {
+    launch_plasma_init<double>(g, g->stream);
+    launch_deposit_initial<double>(g, nullptr, nullptr, 1, g->stream);
+  } else {
+    launch_plasma_init<float>(g, g->stream);
+    launch_deposit_initial<float>(g, nullptr, nullptr, 1, g->stream);
+  }
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g->err = std::string("grid initialization: ") + cudaGetErrorString(e);
+    return bail(HQ_ERR_CUDA);
+  }
+#undef HQ_ALLOC
+  *out = g;
+  return HQ_OK;
+}
+
+hq_status hq_grid_destroy(hq_grid_t g) {
+  if (!g) return HQ_OK;
+  cudaStreamSynchronize(g->stream);
+  free_all(g);
+  delete g;
+  return HQ_OK;
+}
+
+hq_status hq_advance_slice(hq_grid_t g, int32_t slice) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (slice < 0 || slice >= g->nz) return fail(g, HQ_ERR_ARG, "slice out of range");
+  if (slice > 0 && !(g->last_solved == slice - 1 && g->last_adv == slice - 1))
+    return fail(g, HQ_ERR_STATE, "hq_advance_slice(i) needs hq_solve_fields(i-1) first");
+  if (g->fp64) advance_impl<double>(g, slice);
+  else advance_impl<float>(g, slice);
+  g->last_adv = slice;
+  g->last_beam = -1;
+  if (slice == 0) g->last_solved = -1;
+  return check_launch(g);
+}
+
+hq_status hq_beam_deposit(hq_grid_t g, const hq_beam_view* beams, int32_t nbeams, int32_t slice) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (slice < 0 || slice >= g->nz) return fail(g, HQ_ERR_ARG, "slice out of range");
+  if (g->last_adv != slice || g->last_beam == slice || g->last_solved == slice)
+    return fail(g, HQ_ERR_STATE, "hq_beam_deposit(i) needs hq_advance_slice(i) first, once");
+  hq_status st = check_views(g, beams, nbeams);
+  if (st != HQ_OK) return st;
+  st = g->fp64 ? beam_deposit_impl<double>(g, beams, nbeams, slice) : beam_deposit_impl<float>(g, beams, nbeams, slice);
+  if (st != HQ_OK) return st;
+  g->last_beam = slice;
+  return check_launch(g);
+}
+
+hq_status hq_solve_fields(hq_grid_t g, int32_t slice) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (slice < 0 || slice >= g->nz) return fail(g, HQ_ERR_ARG, "slice out of range");
+  if (g->last_beam != slice || g->last_solved == slice)
+    return fail(g, HQ_ERR_STATE, "hq_solve_fields(i) needs hq_beam_deposit(i) first");
+  if (g->fp64) solve_fields_impl<double>(g, slice);
+  else solve_fields_impl<float>(g, slice);
+  g->last_solved = slice;
+  return check_launch(g);
+}
+
+hq_status hq_store_fields(hq_grid_t g, const hq_field_out* out, int64_t slot) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (!out || slot < 0) return fail(g, HQ_ERR_ARG, "out is NULL or slot < 0");
+  if (g->last_solved < 0) return fail(g, HQ_ERR_STATE, "no slice solved yet");
+  const int i = g->last_solved;
+  if (g->fp64) launch_store<double>(g, out, slot, g->dep[i & 1], g->chi[i & 1], g->stream);
+  else launch_store<float>(g, out, slot, g->dep[i & 1], g->chi[i & 1], g->stream);
+  return check_launch(g);
+}
+
+hq_status hq_push_beams(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, int32_t slice, double dt) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (g->last_solved != slice) return fail(g, HQ_ERR_STATE, "hq_push_beams(i) needs hq_solve_fields(i)");
+  hq_status st = check_views(g, beams, nbeams);
+  if (st != HQ_OK) return st;
+  if (!std::isfinite(dt)) return fail(g, HQ_ERR_ARG, "dt must be finite");
+  for (int b = 0; b < nbeams; ++b) {
+    const int k = bound_index(g, &beams[b]);
+    if (k < 0) return fail(g, HQ_ERR_STATE, "beam was not binned at slice 0 of this sweep");
+    if (beams[b].n == 0) continue;
+    if (g->fp64) launch_beam_push<double>(g, k, beams[b], slice, dt, g->stream);
+    else launch_beam_push<float>(g, k, beams[b], slice, dt, g->stream);
+  }
+  return check_launch(g);
+}
+
+hq_status hq_witness_accumulate(hq_grid_t g, const hq_beam_view* beam, int32_t slice, double* sums) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (!beam || !sums) return fail(g, HQ_ERR_ARG, "beam and sums must not be NULL");
+  if (g->last_solved != slice) return fail(g, HQ_ERR_STATE, "hq_witness_accumulate(i) needs hq_solve_fields(i)");
+  const int k = bound_index(g, beam);
+  if (k < 0) return fail(g, HQ_ERR_STATE, "beam was not binned at slice 0 of this sweep");
+  if (beam->n == 0) return HQ_OK;
+  if (g->fp64) launch_witness<double>(g, k, *beam, slice, sums, g->stream);
+  else launch_witness<float>(g, k, *beam, slice, sums, g->stream);
+  return check_launch(g);
+}
+
+hq_status hq_sweep_step(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, double dt, const hq_field_out* out,
+                        int32_t witness_beam, double* witness_sums) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  hq_status st = check_views(g, beams, nbeams);
+  if (st != HQ_OK) return st;
+  if (witness_beam >= nbeams || (witness_beam >= 0 && !witness_sums))
+    return fail(g, HQ_ERR_ARG, "witness_beam must index a beam and witness_sums must be given");
+  if (!std::isfinite(dt)) return fail(g, HQ_ERR_ARG, "dt must be finite");
+  for (int i = 0; i < g->nz; ++i) {
+    if ((st = hq_advance_slice(g, i)) != HQ_OK) return st;
+    if ((st = hq_beam_deposit(g, beams, nbeams, i)) != HQ_OK) return st;
+    if ((st = hq_solve_fields(g, i)) != HQ_OK) return st;
+    if (out && (st = hq_store_fields(g, out, i)) != HQ_OK) return st;
+    if (witness_beam >= 0 && (st = hq_witness_accumulate(g, &beams[witness_beam], i, witness_sums)) != HQ_OK) return st;
+    if (dt != 0.0 && (st = hq_push_beams(g, beams, nbeams, i, dt)) != HQ_OK) return st;
+  }
+  // advance once past the tail so the plasma state matches a completed sweep
+  const int nz = g->nz;
+  if (g->fp64) {
+    launch_reset_dep<double>(g, g->dep[nz & 1], g->chi[nz & 1], g->stream);
+    launch_final_pass<double>(g, nz - 1, g->dep[nz & 1], g->chi[nz & 1], g->stream);
+  } else {
+    launch_reset_dep<float>(g, g->dep[nz & 1], g->chi[nz & 1], g->stream);
+    launch_final_pass<float>(g, nz - 1, g->dep[nz & 1], g->chi[nz & 1], g->stream);
+  }
+  g->last_adv = nz;
+  return check_launch(g);
+}
+
+hq_status hq_poisson_solve(hq_grid_t g, const void* src, void* dst, int32_t nrhs) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (!src || !dst || nrhs < 1 || nrhs > kMaxRhs) return fail(g, HQ_ERR_ARG, "src/dst NULL or nrhs not in 1..5");
+  cudaStream_t s = g->stream;
+  if (g->fp64) {
+    launch_src_copy<double>(g, src, nrhs, s);
+    dst_solve_f64(g, nrhs, s);
+  } else {
+    launch_src_copy<float>(g, src, nrhs, s);
+    dst_solve_tc(g, nrhs, s);
+  }
+  HQ_CUDA(g, cudaMemcpyAsync(dst, g->solved, (size_t)nrhs * g->nnode * g->tsize, cudaMemcpyDeviceToDevice, s));
+  return check_launch(g);
+}
+
+hq_status hq_plasma_state(hq_grid_t g, hq_plasma_view* out) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (!out) return fail(g, HQ_ERR_ARG, "out is NULL");
+  out->n = g->np;
+  out->x = g->p64.x;
+  out->y = g->p64.y;
+  out->psi = g->p64.psi;
+  out->alive = g->p64.alive;
+  if (g->fp64) { out->ux = g->p64.ux; out->uy = g->p64.uy; out->w = g->p64.w; }
+  else { out->ux = g->p32.ux; out->uy = g->p32.uy; out->w = g->p32.w; }
+  return HQ_OK;
+}
+
+hq_status hq_sync(hq_grid_t g, int64_t* removed) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  HQ_CUDA(g, cudaStreamSynchronize(g->stream));
+  int status = 0;
+  unsigned long long rm = 0;
+  HQ_CUDA(g, cudaMemcpy(&status, g->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  HQ_CUDA(g, cudaMemcpy(&rm, g->d_removed, sizeof(rm), cudaMemcpyDeviceToHost));
+  if (removed) *removed = (int64_t)rm;
+  if (status) {
+    HQ_CUDA(g, cudaMemset(g->d_status, 0, sizeof(int)));
+    if (status & DEV_TIMEOUT) return fail(g, HQ_ERR_TIMEOUT, "a bounded device wait ran out (tensor-core DST)");
+    if (status & DEV_NONFINITE) return fail(g, HQ_ERR_NUMERIC, "a non-finite value reached the field solve");
+  }
+  return HQ_OK;
+}
+
+const char* hq_last_error(hq_grid_t g) { return g ? g->err.c_str() : g_global_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,201 @@
+// Internal declarations shared by the CUDA translation units of libhq.
+// Quasi-static PIC slice loop of arXiv:2109.10277 (Sec. 2, Sec. 3.2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/hq.h"
+
+namespace hq {
+
+// ---------------------------------------------------------------- device status bits
+enum : int {
+  DEV_TIMEOUT = 1,   // a bounded wait ran out
+  DEV_NONFINITE = 2, // a non-finite value reached a field
+};
+
+constexpr int kMaxBeams = 4;
+constexpr int kMaxRhs = 5;
+constexpr int kRing = 4;  // AB5 history slots f_{i-1} .. f_{i-4}
+
+// Fifth-order Adams-Bashforth weights (Sec. 3.2 plasma push): beta_k for f_{i-k}.
+__host__ __device__ constexpr double ab5(int k) {
+  return k == 0 ? 1901.0 / 720.0 : k == 1 ? -2774.0 / 720.0 : k == 2 ? 2616.0 / 720.0
+       : k == 3 ? -1274.0 / 720.0 : 251.0 / 720.0;
+}
+
+// Plain-value geometry passed to kernels.
+struct Geom {
+  int nx, ny;
+  double xmin, ymin, dx, dy, inv_dx, inv_dy, dzeta;
+  double xmax, ymax;
+  double inv_area;  // 1 / (dx dy)
+};
+
+template <typename T> struct V4 { T a, b, c, d; };   // packed rho, jx, jy, jz
+template <typename T> struct V2 { T a, b; };          // packed jx, jy or bx, by
+// Gather fields packed per node: ExmBy, EypBx, Ez, Bx, By, Bz, pad, pad.
+constexpr int kGF = 8;
+
+// Plasma slice, structure of arrays.  x, y, psi are FP64 accumulators in both
+// modes; the rest is of the field type T.
+template <typename T> struct Plasma {
+  int64_t n;
+  double *x, *y, *psi;
+  T *ux, *uy, *w;
+  uint8_t* alive;
+  T* hist;           // [kRing][5][n]
+  // FP32 mode: per-particle cell coordinates of the current slice, written by the
+  // final pass so trial passes need no FP64 work (unused in FP64 mode).
+  int32_t* cell;     // (iy << 16) | ix of floor(node coordinate)
+  float* fx;         // fractional node coordinate in x, [0, 1)
+  float* fy;
+  float* opp;        // 1 + Psi, formed in FP64, rounded once
+};
+
+// Per-beam slice binning (counting sort by slice, Sec. 3.1).
+struct BeamBins {
+  int32_t* bin;      // per particle, -1 outside the box
+  int32_t* count;    // nzeta + 1
+  int32_t* offset;   // nzeta + 1 (exclusive scan)
+  int32_t* cursor;   // nzeta
+  int32_t* perm;     // particle indices grouped by slice
+  int64_t cap;
+};
+
+struct TensorMaps;  // opaque, defined in the tensor-core DST unit
+
+}  // namespace hq
+
+// ---------------------------------------------------------------- grid object
+struct hq_grid_s {
+  hq_grid_desc d;
+  std::vector<double> profile;
+  cudaStream_t stream;
+  int dev;
+  int fp64;            // 1: FP64 everywhere; 0: FP32 + bf16x3 tensor-core DST
+  int nx, ny, nz;
+  int64_t nnode, np;
+  hq::Geom geom;
+  size_t tsize;        // sizeof field type
+
+  // plasma
+  void* plasma;        // hq::Plasma<T>* host struct (typed by fp64)
+  hq::Plasma<double> p64;
+  hq::Plasma<float> p32;
+
+  // fields (void* typed by fp64)
+  void* dep[2];        // V4 per node: rho, jx, jy, jz   (ping-pong by slice parity)
+  void* chi[2];
+  void* rho_ion;
+  void* tj;            // V2: trial plasma J_perp of slice i+1
+  void* bjn;           // V2: beam J_perp of slice i+1
+  void* gf;            // kGF per node (gather fields of the current slice)
+  void* psi;
+  void* bprev1;        // V2: B_perp of slice i-1
+  void* bprev2;        // V2: B_perp of slice i-2
+  void* solved;        // kMaxRhs x nnode: DST results
+
+  // DST, FP64: [kMaxRhs][nnode] ping-pong buffers, per-mode scale, twiddles, sine tables
+  double *f64_a, *f64_b, *f64_scale, *tw_x, *tw_y, *sin_x, *sin_y;
+  // DST, FP32/bf16x3: padded operand buffers and sine matrices
+  int nxp, nyp;
+  __nv_bfloat16 *op_hi[2], *op_lo[2];       // ping-pong [kMaxRhs * max(nxp,nyp)^2]
+  __nv_bfloat16 *sx_hi, *sx_lo, *sy_hi, *sy_lo;
+  float* f32_scale;                          // [nyp][nxp] (1/lambda)(4/(nx ny))
+  hq::TensorMaps* tmaps;
+
+  // beams
+  hq::BeamBins bins[hq::kMaxBeams];
+  hq_beam_view bound[hq::kMaxBeams];
+  int nbound;
+
+  double* d_profile;   // radial density profile (device copy)
+  int* d_status;
+  unsigned long long* d_removed;
+  int* d_scratch_int;
+
+  int last_adv, last_beam, last_solved;
+  std::string err;
+};
+
+namespace hq {
+
+// ---------------------------------------------------------------- launchers (kernels in *.cu)
+// particles
+template <typename T> void launch_plasma_init(const hq_grid_s* g, cudaStream_t s);
+template <typename T> void launch_deposit_initial(const hq_grid_s* g, void* dep, void* chi, int ion_only, cudaStream_t s);
+template <typename T> void launch_trial_pass(const hq_grid_s* g, int slice, cudaStream_t s);
+template <typename T> void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cudaStream_t s);
+// fields
+template <typename T> void launch_reset_dep(const hq_grid_s* g, void* dep, void* chi, cudaStream_t s);
+template <typename T> void launch_src_main(const hq_grid_s* g, const void* dep, cudaStream_t s);
+template <typename T> void launch_src_bperp(const hq_grid_s* g, const void* dep_cur, const void* dep_prev, cudaStream_t s);
+template <typename T> void launch_src_copy(const hq_grid_s* g, const void* src, int nrhs, cudaStream_t s);
+template <typename T> void launch_finish_main(const hq_grid_s* g, const void* res, cudaStream_t s);
+template <typename T> void launch_finish_bperp(const hq_grid_s* g, const void* res, cudaStream_t s);
+template <typename T> void launch_bguess(const hq_grid_s* g, cudaStream_t s);
+template <typename T> void launch_bshift(const hq_grid_s* g, cudaStream_t s);
+template <typename T> void launch_store(const hq_grid_s* g, const hq_field_out* out, int64_t slot, const void* dep, const void* chi, cudaStream_t s);
+template <typename T> void launch_zero(void* p, int64_t n, cudaStream_t s);
+// DST backends: transform the nrhs sources prepared by the src kernels into g->solved
+void dst_solve_f64(hq_grid_s* g, int nrhs, cudaStream_t s);
+void dst_solve_tc(hq_grid_s* g, int nrhs, cudaStream_t s);
+int dst_tc_init(hq_grid_s* g, std::string& err);   // builds tensor maps; 0 on success
+void dst_tc_free(hq_grid_s* g);
+// beams
+void launch_beam_bin(hq_grid_s* g, int b, const hq_beam_view& v, cudaStream_t s);
+template <typename T> void launch_beam_deposit(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, void* dep, void* bjn, cudaStream_t s);
+template <typename T> void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double dt, cudaStream_t s);
+template <typename T> void launch_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double* sums, cudaStream_t s);
+
+}  // namespace hq
+
+// ---------------------------------------------------------------- device helpers
+namespace hq {
+
+// B-spline weights of order P from the cell index jf = floor(u) and the fraction
+// d = u - jf in [0, 1).  Node j0 + a carries weight w[a] (Sec. 3.2 deposition, orders 0-3).
+template <int P, typename T>
+__device__ __forceinline__ int shape_weights(int jf, T d, T* w) {
+  if constexpr (P == 0) {
+    w[0] = T(1);
+    return jf + (d >= T(0.5) ? 1 : 0);
+  } else if constexpr (P == 1) {
+    w[0] = T(1) - d;
+    w[1] = d;
+    return jf;
+  } else if constexpr (P == 2) {
+    const bool up = d >= T(0.5);
+    const T e = up ? d - T(1) : d;           // offset from the nearest node, [-0.5, 0.5)
+    const T a = T(0.5) - e, b = T(0.5) + e;
+    w[0] = T(0.5) * a * a;
+    w[1] = T(0.75) - e * e;
+    w[2] = T(0.5) * b * b;
+    return jf + (up ? 1 : 0) - 1;
+  } else {
+    const T d2 = d * d, d3 = d2 * d, om = T(1) - d;
+    w[0] = om * om * om * T(1.0 / 6.0);
+    w[1] = (T(4) - T(6) * d2 + T(3) * d3) * T(1.0 / 6.0);
+    w[2] = (T(1) + T(3) * d + T(3) * d2 - T(3) * d3) * T(1.0 / 6.0);
+    w[3] = d3 * T(1.0 / 6.0);
+    return jf - 1;
+  }
+}
+
+// Node coordinate u = (x - x0) / dx split into floor and fraction, in FP64.
+__device__ __forceinline__ void split_coord(double x, double x0, double dx, int& jf, double& d) {
+  const double u = (x - x0) / dx;
+  const double f = floor(u);
+  jf = (int)f;
+  d = u - f;
+}
+
+__device__ __forceinline__ bool in_interior(int j, int n) { return j >= 1 && j <= n - 1; }
+
+}  // namespace hq

@@ -1,0 +1,324 @@
+// DST-I as dense matrix products on the 5th-generation tensor cores (tcgen05),
+// for the FP32 path of the fast Poisson solver (Sec. 3.2: "fast Poisson solvers
+// based on a Discrete Sine Transform of the first type").
+//
+// A Dirichlet solve is f = (2/nx)(2/ny) S_y [ (S_y s S_x) / lambda ] S_x.  With
+// every operand kept K-major, each of the four products is a "TN" GEMM
+//   D[m][n] = sum_k A[m][k] S[n][k]          (S symmetric)
+// whose epilogue stores D transposed, so that the next product again reads its
+// operand K-major: two such products give S_y s S_x.  R right-hand sides are
+// stacked along m (R * 128-padded rows), so one launch transforms them all.
+//
+// Precision ("bf16x3"): every FP32 operand a is carried as a_hi + a_lo with
+// a_hi = bf16(a), a_lo = bf16(a - a_hi) (16 significant bits); a product uses
+// a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32 in tensor memory.
+// The epilogue of each product re-splits its FP32 result for the next one and
+// fuses the 1/lambda scaling (second product) or the final FP32 store (fourth).
+//
+// Kernel structure (one 128 x 128 output tile per CTA, 4 warps):
+//   warp 0 lane 0  TMA producer: 128B-swizzled 128x64 bf16 boxes of A_hi, A_lo,
+//                  S_hi, S_lo per stage (64 KB), 3-stage mbarrier ring;
+//   warp 1 lane 0  MMA issuer: 12 tcgen05.mma (M=128, N=128, K=16) per stage,
+//                  tcgen05.commit releases the stage, a final commit signals
+//                  the epilogue;
+//   warps 0-3      epilogue: tcgen05.ld 32x32b (lane = row), transposed store.
+// Every wait on an mbarrier is bounded; on expiry the kernel sets a status bit,
+// still drains its MMAs, frees its tensor memory and returns.
+#include "hq_internal.cuh"
+
+namespace hq {
+
+struct TensorMaps {
+  CUtensorMap a0_hi, a0_lo;   // op[0] as [kMaxRhs * nyp][nxp]
+  CUtensorMap a1_hi, a1_lo;   // op[1] as [kMaxRhs * nxp][nyp]
+  CUtensorMap sx_hi, sx_lo;   // [nxp][nxp]
+  CUtensorMap sy_hi, sy_lo;   // [nyp][nyp]
+};
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 2;            // 16 KB per bf16 box
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;        // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr uint32_t TMEM_COLS = BN;
+
+struct Epi {
+  int mode;          // 0: split + transposed bf16 store; 1: scale, split, store; 2: FP32 transposed store
+  int P1;            // rows per right-hand side (padded), i.e. m extent per rhs
+  int P2;            // padded n extent
+  __nv_bfloat16* out_hi;
+  __nv_bfloat16* out_lo;
+  const float* scale;   // [P2][P1]
+  float* out_f32;       // [R][n_real][m_real]
+  int m_real, n_real;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P1;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait (about two seconds of SM clock); false and a status bit on expiry.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (4ll << 30)) {
+      atomicOr(status, DEV_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile, 128B swizzle: rows of 64 bf16 (128 B), 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address, 16 B units
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                      // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                      // layout: SWIZZLE_128B
+  return d;
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M = BM, N = BN.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_dst_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+               const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo, int K, Epi ep,
+               int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* basep = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(basep + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int nk = K / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ((kb / STAGES) - 1) & 1, status)) break;
+      const uint32_t st = base + s * STAGE_BYTES;
+      const uint32_t fb = full0 + 8 * s;
+      mbar_expect_tx(fb, STAGE_BYTES);
+      tma_load_2d(st, &ta_hi, kb * BK, m0, fb);
+      tma_load_2d(st + TILE_BYTES, &ta_lo, kb * BK, m0, fb);
+      tma_load_2d(st + 2 * TILE_BYTES, &tb_hi, kb * BK, n0, fb);
+      tma_load_2d(st + 3 * TILE_BYTES, &tb_lo, kb * BK, n0, fb);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, status)) break;
+      tc_fence_after();
+      const uint32_t st = base + s * STAGE_BYTES;
+      const uint64_t ah = desc_k_sw128(st), al = desc_k_sw128(st + TILE_BYTES);
+      const uint64_t bh = desc_k_sw128(st + 2 * TILE_BYTES), bl = desc_k_sw128(st + 3 * TILE_BYTES);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k) {
+        const uint64_t off = (uint64_t)((k * 32) >> 4);  // 16 bf16 = 32 B along K inside the swizzle row
+        mma_bf16(tmem, ah + off, bh + off, (kb | k) != 0 ? 1u : 0u);
+        mma_bf16(tmem, ah + off, bl + off, 1u);
+        mma_bf16(tmem, al + off, bh + off, 1u);
+      }
+      mma_commit(empty0 + 8 * s);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  mbar_wait(done, 0, status);
+  tc_fence_after();
+
+  // ---------------------------------------------------------------- epilogue
+  const int row = warp * 32 + lane;
+  const int m = m0 + row;
+  const int r = m / ep.P1, ml = m - r * ep.P1;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    uint32_t v[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (ep.mode == 2) {
+      if (ml < ep.m_real) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < ep.n_real) ep.out_f32[((int64_t)r * ep.n_real + n) * ep.m_real + ml] = __uint_as_float(v[j]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int n = n0 + c0 + j;
+        float x = __uint_as_float(v[j]);
+        if (ep.mode == 1) x *= __ldg(ep.scale + (int64_t)n * ep.P1 + ml);
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+        const int64_t o = ((int64_t)r * ep.P2 + n) * ep.P1 + ml;
+        ep.out_hi[o] = h;
+        ep.out_lo[o] = l;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                              const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int make_map(EncodeFn enc, CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols, std::string& err) {
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {BK, 128};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult rc = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (rc != CUDA_SUCCESS) {
+    err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)rc) + ")";
+    return 1;
+  }
+  return 0;
+}
+
+void gemm(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl, int M, int N, int K,
+          const Epi& ep, int* status, cudaStream_t s) {
+  dim3 grid((unsigned)(M / BM), (unsigned)(N / BN));
+  k_dst_gemm<<<grid, 128, SMEM_BYTES, s>>>(ah, al, bh, bl, K, ep, status);
+}
+
+}  // namespace
+
+int dst_tc_init(hq_grid_s* g, std::string& err) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      fn == nullptr || q != cudaDriverEntryPointSuccess) {
+    err = "cuTensorMapEncodeTiled not available from the driver";
+    return 1;
+  }
+  EncodeFn enc = reinterpret_cast<EncodeFn>(fn);
+  if (cudaFuncSetAttribute(k_dst_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+    err = "cannot raise the shared-memory limit of the DST GEMM";
+    return 1;
+  }
+  g->tmaps = new TensorMaps();
+  TensorMaps& t = *g->tmaps;
+  const uint64_t nxp = g->nxp, nyp = g->nyp;
+  int bad = 0;
+  bad |= make_map(enc, &t.a0_hi, g->op_hi[0], kMaxRhs * nyp, nxp, err);
+  bad |= make_map(enc, &t.a0_lo, g->op_lo[0], kMaxRhs * nyp, nxp, err);
+  bad |= make_map(enc, &t.a1_hi, g->op_hi[1], kMaxRhs * nxp, nyp, err);
+  bad |= make_map(enc, &t.a1_lo, g->op_lo[1], kMaxRhs * nxp, nyp, err);
+  bad |= make_map(enc, &t.sx_hi, g->sx_hi, nxp, nxp, err);
+  bad |= make_map(enc, &t.sx_lo, g->sx_lo, nxp, nxp, err);
+  bad |= make_map(enc, &t.sy_hi, g->sy_hi, nyp, nyp, err);
+  bad |= make_map(enc, &t.sy_lo, g->sy_lo, nyp, nyp, err);
+  return bad;
+}
+
+void dst_tc_free(hq_grid_s* g) {
+  delete g->tmaps;
+  g->tmaps = nullptr;
+}
+
+// sources (split) in op[0] [R][nyp][nxp] -> FP32 solution in g->solved [R][ny][nx]
+void dst_solve_tc(hq_grid_s* g, int R, cudaStream_t s) {
+  const TensorMaps& t = *g->tmaps;
+  const int nxp = g->nxp, nyp = g->nyp;
+  Epi e{};
+  // 1: (s S_x)^T -> op[1] [R][nxp][nyp]
+  e = Epi{0, nyp, nxp, g->op_hi[1], g->op_lo[1], nullptr, nullptr, 0, 0};
+  gemm(t.a0_hi, t.a0_lo, t.sx_hi, t.sx_lo, R * nyp, nxp, nxp, e, g->d_status, s);
+  // 2: S_y s S_x, scaled by (4/(nx ny))/lambda -> op[0] [R][nyp][nxp]
+  e = Epi{1, nxp, nyp, g->op_hi[0], g->op_lo[0], g->f32_scale, nullptr, 0, 0};
+  gemm(t.a1_hi, t.a1_lo, t.sy_hi, t.sy_lo, R * nxp, nyp, nyp, e, g->d_status, s);
+  // 3: (f_hat S_x)^T -> op[1]
+  e = Epi{0, nyp, nxp, g->op_hi[1], g->op_lo[1], nullptr, nullptr, 0, 0};
+  gemm(t.a0_hi, t.a0_lo, t.sx_hi, t.sx_lo, R * nyp, nxp, nxp, e, g->d_status, s);
+  // 4: S_y f_hat S_x -> FP32 [R][ny][nx]
+  e = Epi{2, nxp, nyp, nullptr, nullptr, nullptr, reinterpret_cast<float*>(g->solved), g->nx, g->ny};
+  gemm(t.a1_hi, t.a1_lo, t.sy_hi, t.sy_lo, R * nxp, nyp, nyp, e, g->d_status, s);
+}
+
+}  // namespace hq

@@ -1,0 +1,280 @@
+// Field-slice kernels around the Poisson solves (Sec. 2 steps 4-7, Eqs. psi,
+// exmby, ez, bxby, bz): source assembly with second-order central differences,
+// -grad(psi), the predictor-corrector mixing, the B_perp guess/shift and the
+// per-slice output copy.  All are HBM/L2-streaming elementwise kernels over the
+// ny x nx slice (one thread per node, consecutive threads along x).
+//
+// Sources are written through a "sink": FP64 mode writes doubles in the solver's
+// [rhs][ny][nx] layout; FP32 mode writes each source already split into two bf16
+// terms (hi + lo) in the zero-padded [rhs][nyp][nxp] operand layout of the
+// tensor-core DST, so no separate conversion pass is needed.
+#include "hq_internal.cuh"
+
+namespace hq {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct SinkF64 {
+  double* p;
+  int nx, ny;
+  __device__ void put(int r, int iy, int ix, double v) const { p[((int64_t)r * ny + iy) * nx + ix] = v; }
+};
+
+struct SinkBF16 {
+  __nv_bfloat16 *hi, *lo;
+  int nxp, nyp;
+  __device__ void put(int r, int iy, int ix, float v) const {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    const int64_t o = ((int64_t)r * nyp + iy) * nxp + ix;
+    hi[o] = h;
+    lo[o] = l;
+  }
+};
+
+// Central difference helpers with wall nodes (index 0 and n) reading zero; the
+// result on wall rows/columns is zero (matching the field layout convention).
+template <typename A>
+__device__ __forceinline__ auto dxc(const A& f, int iy, int ix, int nx, double inv2dx) -> decltype(f(0, 0)) {
+  using T = decltype(f(0, 0));
+  const T r = ix + 1 < nx ? f(iy, ix + 1) : T(0);
+  const T l = f(iy, ix - 1);
+  return (r - l) * T(inv2dx);
+}
+template <typename A>
+__device__ __forceinline__ auto dyc(const A& f, int iy, int ix, int ny, double inv2dy) -> decltype(f(0, 0)) {
+  using T = decltype(f(0, 0));
+  const T u = iy + 1 < ny ? f(iy + 1, ix) : T(0);
+  const T d = f(iy - 1, ix);
+  return (u - d) * T(inv2dy);
+}
+
+template <typename T>
+__global__ void k_reset_dep(V4<T>* dep, T* chi, const T* rho_ion, int64_t nn) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  dep[i] = V4<T>{rho_ion[i], T(0), T(0), T(0)};
+  chi[i] = T(0);
+}
+
+// psi: -(rho - Jz);  Ez: dx Jx + dy Jy;  Bz: dy Jx - dx Jy.
+template <typename T, typename Sink>
+__global__ void k_src_main(const V4<T>* __restrict__ dep, Geom gm, Sink sink) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+  if (ix >= gm.nx) return;
+  const int nx = gm.nx;
+  auto jx = [&](int y, int x) { return dep[(int64_t)y * nx + x].b; };
+  auto jy = [&](int y, int x) { return dep[(int64_t)y * nx + x].c; };
+  T s0 = T(0), s1 = T(0), s2 = T(0);
+  if (ix > 0 && iy > 0) {
+    const V4<T> c = dep[(int64_t)iy * nx + ix];
+    const double i2x = 0.5 / gm.dx, i2y = 0.5 / gm.dy;
+    s0 = -(c.a - c.d);
+    s1 = dxc(jx, iy, ix, nx, i2x) + dyc(jy, iy, ix, gm.ny, i2y);
+    s2 = dyc(jx, iy, ix, gm.ny, i2y) - dxc(jy, iy, ix, nx, i2x);
+  }
+  sink.put(0, iy, ix, s0);
+  sink.put(1, iy, ix, s1);
+  sink.put(2, iy, ix, s2);
+}
+
+// Bx: -dy Jz + dzeta Jy;  By: dx Jz - dzeta Jx, with dzeta J = (J(i-1) - J(i+1)) / (2 dzeta)
+// and J(i+1) = trial plasma + beam of slice i+1 (Sec. 3.2 predictor-corrector).
+template <typename T, typename Sink>
+__global__ void k_src_bperp(const V4<T>* __restrict__ cur, const V4<T>* __restrict__ prev,
+                            const V2<T>* __restrict__ tj, const V2<T>* __restrict__ bjn, Geom gm, Sink sink) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+  if (ix >= gm.nx) return;
+  const int nx = gm.nx;
+  auto jz = [&](int y, int x) { return cur[(int64_t)y * nx + x].d; };
+  T s0 = T(0), s1 = T(0);
+  if (ix > 0 && iy > 0) {
+    const int64_t o = (int64_t)iy * nx + ix;
+    const T i2z = T(0.5 / gm.dzeta);
+    const V4<T> pv = prev[o];
+    const V2<T> t = tj[o], b = bjn[o];
+    const T dzjx = (pv.b - (t.a + b.a)) * i2z;
+    const T dzjy = (pv.c - (t.b + b.b)) * i2z;
+    s0 = -dyc(jz, iy, ix, gm.ny, 0.5 / gm.dy) + dzjy;
+    s1 = dxc(jz, iy, ix, nx, 0.5 / gm.dx) - dzjx;
+  }
+  sink.put(0, iy, ix, s0);
+  sink.put(1, iy, ix, s1);
+}
+
+template <typename T, typename Sink>
+__global__ void k_src_copy(const T* __restrict__ src, int nrhs, Geom gm, Sink sink) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+  if (ix >= gm.nx) return;
+  for (int r = 0; r < nrhs; ++r) {
+    const T v = (ix > 0 && iy > 0) ? src[((int64_t)r * gm.ny + iy) * gm.nx + ix] : T(0);
+    sink.put(r, iy, ix, v);
+  }
+}
+
+// psi -> psi array and gf[0..1] = -grad psi; Ez -> gf[2]; Bz -> gf[5].
+template <typename T>
+__global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, Geom gm, int* status) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+  if (ix >= gm.nx) return;
+  const int nx = gm.nx;
+  const int64_t nn = (int64_t)nx * gm.ny;
+  const int64_t o = (int64_t)iy * nx + ix;
+  auto ps = [&](int y, int x) { return res[(int64_t)y * nx + x]; };
+  T ex = T(0), ey = T(0);
+  if (ix > 0 && iy > 0) {
+    ex = -dxc(ps, iy, ix, nx, 0.5 / gm.dx);
+    ey = -dyc(ps, iy, ix, gm.ny, 0.5 / gm.dy);
+  }
+  const T p = res[o], ez = res[nn + o], bz = res[2 * nn + o];
+  if (!(isfinite(p) && isfinite(ez) && isfinite(bz))) atomicOr(status, DEV_NONFINITE);
+  psi[o] = p;
+  T* q = gf + o * kGF;
+  q[0] = ex;
+  q[1] = ey;
+  q[2] = ez;
+  q[5] = bz;
+}
+
+// B <- w B_solved + (1 - w) B  (predictor-corrector mixing), into gf[3..4].
+template <typename T>
+__global__ void k_finish_bperp(const T* __restrict__ res, T* gf, int64_t nn, T w, int* status) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nn) return;
+  const T bx = res[o], by = res[nn + o];
+  if (!(isfinite(bx) && isfinite(by))) atomicOr(status, DEV_NONFINITE);
+  T* q = gf + o * kGF;
+  q[3] = w * bx + (T(1) - w) * q[3];
+  q[4] = w * by + (T(1) - w) * q[4];
+}
+
+// Initial guess B(i) = 2 B(i-1) - B(i-2).
+template <typename T>
+__global__ void k_bguess(const V2<T>* b1, const V2<T>* b2, T* gf, int64_t nn) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nn) return;
+  const V2<T> p1 = b1[o], p2 = b2[o];
+  T* q = gf + o * kGF;
+  q[3] = T(2) * p1.a - p2.a;
+  q[4] = T(2) * p1.b - p2.b;
+}
+
+template <typename T>
+__global__ void k_bshift(V2<T>* b1, V2<T>* b2, const T* gf, int64_t nn) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nn) return;
+  b2[o] = b1[o];
+  const T* q = gf + o * kGF;
+  b1[o] = V2<T>{q[3], q[4]};
+}
+
+template <typename T>
+__global__ void k_store(hq_field_out out, int64_t base, const V4<T>* dep, const T* chi, const T* psi,
+                        const T* gf, int64_t nn) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nn) return;
+  const V4<T> d = dep[o];
+  const T* q = gf + o * kGF;
+  const int64_t t = base + o;
+  if (out.rho) reinterpret_cast<T*>(out.rho)[t] = d.a;
+  if (out.jx) reinterpret_cast<T*>(out.jx)[t] = d.b;
+  if (out.jy) reinterpret_cast<T*>(out.jy)[t] = d.c;
+  if (out.jz) reinterpret_cast<T*>(out.jz)[t] = d.d;
+  if (out.chi) reinterpret_cast<T*>(out.chi)[t] = chi[o];
+  if (out.psi) reinterpret_cast<T*>(out.psi)[t] = psi[o];
+  if (out.exmby) reinterpret_cast<T*>(out.exmby)[t] = q[0];
+  if (out.eypbx) reinterpret_cast<T*>(out.eypbx)[t] = q[1];
+  if (out.ez) reinterpret_cast<T*>(out.ez)[t] = q[2];
+  if (out.bx) reinterpret_cast<T*>(out.bx)[t] = q[3];
+  if (out.by) reinterpret_cast<T*>(out.by)[t] = q[4];
+  if (out.bz) reinterpret_cast<T*>(out.bz)[t] = q[5];
+}
+
+template <typename T>
+__global__ void k_zero(T* p, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = T(0);
+}
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+inline dim3 grid2d(const hq_grid_s* g) { return dim3((unsigned)((g->nx + 127) / 128), (unsigned)g->ny); }
+
+template <typename T> struct SinkOf;
+template <> struct SinkOf<double> {
+  static SinkF64 make(const hq_grid_s* g) { return SinkF64{g->f64_a, g->nx, g->ny}; }
+};
+template <> struct SinkOf<float> {
+  static SinkBF16 make(const hq_grid_s* g) { return SinkBF16{g->op_hi[0], g->op_lo[0], g->nxp, g->nyp}; }
+};
+
+}  // namespace
+
+template <typename T>
+void launch_reset_dep(const hq_grid_s* g, void* dep, void* chi, cudaStream_t s) {
+  k_reset_dep<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(reinterpret_cast<V4<T>*>(dep), reinterpret_cast<T*>(chi),
+                                                         reinterpret_cast<const T*>(g->rho_ion), g->nnode);
+}
+template <typename T>
+void launch_src_main(const hq_grid_s* g, const void* dep, cudaStream_t s) {
+  k_src_main<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const V4<T>*>(dep), g->geom, SinkOf<T>::make(g));
+}
+template <typename T>
+void launch_src_bperp(const hq_grid_s* g, const void* cur, const void* prev, cudaStream_t s) {
+  k_src_bperp<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const V4<T>*>(cur), reinterpret_cast<const V4<T>*>(prev),
+                                          reinterpret_cast<const V2<T>*>(g->tj), reinterpret_cast<const V2<T>*>(g->bjn),
+                                          g->geom, SinkOf<T>::make(g));
+}
+template <typename T>
+void launch_src_copy(const hq_grid_s* g, const void* src, int nrhs, cudaStream_t s) {
+  k_src_copy<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const T*>(src), nrhs, g->geom, SinkOf<T>::make(g));
+}
+template <typename T>
+void launch_finish_main(const hq_grid_s* g, const void* res, cudaStream_t s) {
+  k_finish_main<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const T*>(res), reinterpret_cast<T*>(g->psi),
+                                            reinterpret_cast<T*>(g->gf), g->geom, g->d_status);
+}
+template <typename T>
+void launch_finish_bperp(const hq_grid_s* g, const void* res, cudaStream_t s) {
+  k_finish_bperp<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(reinterpret_cast<const T*>(res), reinterpret_cast<T*>(g->gf),
+                                                            g->nnode, T(g->d.pc_mix), g->d_status);
+}
+template <typename T>
+void launch_bguess(const hq_grid_s* g, cudaStream_t s) {
+  k_bguess<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(reinterpret_cast<const V2<T>*>(g->bprev1),
+                                                       reinterpret_cast<const V2<T>*>(g->bprev2),
+                                                       reinterpret_cast<T*>(g->gf), g->nnode);
+}
+template <typename T>
+void launch_bshift(const hq_grid_s* g, cudaStream_t s) {
+  k_bshift<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(reinterpret_cast<V2<T>*>(g->bprev1), reinterpret_cast<V2<T>*>(g->bprev2),
+                                                       reinterpret_cast<const T*>(g->gf), g->nnode);
+}
+template <typename T>
+void launch_store(const hq_grid_s* g, const hq_field_out* out, int64_t slot, const void* dep, const void* chi, cudaStream_t s) {
+  k_store<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(*out, slot * g->nnode, reinterpret_cast<const V4<T>*>(dep),
+                                                      reinterpret_cast<const T*>(chi), reinterpret_cast<const T*>(g->psi),
+                                                      reinterpret_cast<const T*>(g->gf), g->nnode);
+}
+template <typename T>
+void launch_zero(void* p, int64_t n, cudaStream_t s) {
+  if (n > 0) k_zero<T><<<blocks_for(n), kThreads, 0, s>>>(reinterpret_cast<T*>(p), n);
+}
+
+#define HQ_INST(T)                                                                              \
+  template void launch_reset_dep<T>(const hq_grid_s*, void*, void*, cudaStream_t);             \
+  template void launch_src_main<T>(const hq_grid_s*, const void*, cudaStream_t);               \
+  template void launch_src_bperp<T>(const hq_grid_s*, const void*, const void*, cudaStream_t); \
+  template void launch_src_copy<T>(const hq_grid_s*, const void*, int, cudaStream_t);          \
+  template void launch_finish_main<T>(const hq_grid_s*, const void*, cudaStream_t);            \
+  template void launch_finish_bperp<T>(const hq_grid_s*, const void*, cudaStream_t);           \
+  template void launch_bguess<T>(const hq_grid_s*, cudaStream_t);                              \
+  template void launch_bshift<T>(const hq_grid_s*, cudaStream_t);                              \
+  template void launch_store<T>(const hq_grid_s*, const hq_field_out*, int64_t, const void*, const void*, cudaStream_t); \
+  template void launch_zero<T>(void*, int64_t, cudaStream_t);
+HQ_INST(float)
+HQ_INST(double)
+#undef HQ_INST
+
+}  // namespace hq

@@ -1,0 +1,452 @@
+// Plasma particle kernels: initialization, deposition (Sec. 3.2, "current
+// deposition": order 0 longitudinally, orders 0-3 transversely, atomics to global
+// memory), field gather and the fifth-order Adams-Bashforth push (Sec. 3.2,
+// equations for d(x_perp)/d(zeta), d(u_perp)/d(zeta), d(Psi)/d(zeta)).
+//
+// Layout: structure of arrays, one thread per particle, consecutive threads take
+// consecutive particles (coalesced streams).  Deposits go to a packed per-node
+// (rho, Jx, Jy, Jz) record with one vector atomic per node in FP32 mode.
+//
+// FP32 mode keeps x, y and Psi as FP64 accumulators.  The final pass, which
+// advances the state, derives each particle's cell index and fractional node
+// coordinate (and 1 + Psi, formed in FP64 and rounded once) and caches them, so
+// the n_pc trial passes of the predictor-corrector run without FP64 work.
+#include "hq_internal.cuh"
+
+namespace hq {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void atomic_add4(V4<float>* p, float a, float b, float c, float d) {
+  atomicAdd(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
+}
+__device__ __forceinline__ void atomic_add4(V4<double>* p, double a, double b, double c, double d) {
+  atomicAdd(&p->a, a);
+  atomicAdd(&p->b, b);
+  atomicAdd(&p->c, c);
+  atomicAdd(&p->d, d);
+}
+__device__ __forceinline__ void atomic_add2(V2<float>* p, float a, float b) {
+  atomicAdd(reinterpret_cast<float2*>(p), make_float2(a, b));
+}
+__device__ __forceinline__ void atomic_add2(V2<double>* p, double a, double b) {
+  atomicAdd(&p->a, a);
+  atomicAdd(&p->b, b);
+}
+
+// Six gathered fields: ExmBy, EypBx, Ez, Bx, By, Bz.
+template <typename T> struct F6 { T v[6]; };
+
+__device__ __forceinline__ void load_gf(const float* q, float* o) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(q));
+  const float2 b = __ldg(reinterpret_cast<const float2*>(q + 4));
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
+}
+__device__ __forceinline__ void load_gf(const double* q, double* o) {
+#pragma unroll
+  for (int c = 0; c < 6; c += 2) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(q + c));
+    o[c] = a.x; o[c + 1] = a.y;
+  }
+}
+
+// Interpolate the packed fields at a particle whose x/y stencils start at ix0/iy0.
+template <int P, typename T>
+__device__ __forceinline__ F6<T> gather6(const T* __restrict__ gf, int nx, int ny, int ix0, int iy0,
+                                         const T* wx, const T* wy) {
+  F6<T> F;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) F.v[c] = T(0);
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const int iy = iy0 + b;
+    if (!in_interior(iy, ny)) continue;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      const int ix = ix0 + a;
+      if (!in_interior(ix, nx)) continue;
+      T q[6];
+      load_gf(gf + ((int64_t)iy * nx + ix) * kGF, q);
+      const T wgt = wx[a] * wy[b];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) F.v[c] += wgt * q[c];
+    }
+  }
+  return F;
+}
+
+// zeta-derivatives of an electron (q/M = -1), Sec. 3.2; opp = 1 + Psi.
+template <typename T>
+__device__ __forceinline__ void derivs(T ux, T uy, T opp, const F6<T>& F, T* f) {
+  const T g = T(1) / opp;
+  const T gam = (T(1) + ux * ux + uy * uy + opp * opp) * T(0.5) * g;
+  const T exmby = F.v[0], eypbx = F.v[1], ez = F.v[2], bx = F.v[3], by = F.v[4], bz = F.v[5];
+  f[0] = -ux * g;
+  f[1] = -uy * g;
+  f[2] = gam * g * exmby + by + bz * g * uy;      // -(q/M)[...] with q/M = -1
+  f[3] = gam * g * eypbx - bx - bz * g * ux;
+  f[4] = g * (ux * exmby + uy * eypbx) - ez;
+}
+
+// AB5 combination sum_k beta_k f_{i-k} for component c; history slots hold f_{i-1..i-4}.
+template <typename T>
+__device__ __forceinline__ T ab5_comb(const T* __restrict__ hist, int64_t n, int64_t p, int slice,
+                                      int c, T f0) {
+  T acc = T(ab5(0)) * f0;
+#pragma unroll
+  for (int k = 1; k <= 4; ++k) {
+    const int slot = ((slice - k) % kRing + kRing) % kRing;
+    acc += T(ab5(k)) * hist[((int64_t)slot * 5 + c) * n + p];
+  }
+  return acc;
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void deposit_full(V4<T>* dep, T* chi, int nx, int ny, int ix0, int iy0,
+                                             const T* wx, const T* wy, T rho, T jx, T jy, T jz, T ch) {
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const int iy = iy0 + b;
+    if (!in_interior(iy, ny)) continue;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      const int ix = ix0 + a;
+      if (!in_interior(ix, nx)) continue;
+      const T wgt = wx[a] * wy[b];
+      const int64_t node = (int64_t)iy * nx + ix;
+      atomic_add4(dep + node, wgt * rho, wgt * jx, wgt * jy, wgt * jz);
+      if (chi) atomicAdd(chi + node, wgt * ch);
+    }
+  }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void deposit_perp(V2<T>* tj, int nx, int ny, int ix0, int iy0,
+                                             const T* wx, const T* wy, T jx, T jy) {
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const int iy = iy0 + b;
+    if (!in_interior(iy, ny)) continue;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      const int ix = ix0 + a;
+      if (!in_interior(ix, nx)) continue;
+      const T wgt = wx[a] * wy[b];
+      atomic_add2(tj + (int64_t)iy * nx + ix, wgt * jx, wgt * jy);
+    }
+  }
+}
+
+// Stencil of a position given in FP64 (exact division, as in the oracle).
+template <int P, typename T>
+__device__ __forceinline__ void stencil_f64(const Geom& gm, double x, double y, int& ix0, int& iy0, T* wx, T* wy) {
+  int jx, jy;
+  double fx, fy;
+  split_coord(x, gm.xmin, gm.dx, jx, fx);
+  split_coord(y, gm.ymin, gm.dy, jy, fy);
+  ix0 = shape_weights<P, T>(jx, T(fx), wx);
+  iy0 = shape_weights<P, T>(jy, T(fy), wy);
+}
+
+// Removal rule (a reading; the paper is silent): finite, inside the open box,
+// 1 + Psi >= psi_guard.
+__device__ __forceinline__ bool state_ok(const Geom& gm, double x, double y, double opp, double guard) {
+  return isfinite(x) && isfinite(y) && isfinite(opp) && x > gm.xmin && x < gm.xmax && y > gm.ymin &&
+         y < gm.ymax && opp >= guard;
+}
+
+// ---------------------------------------------------------------- init
+template <typename T>
+__global__ void k_plasma_init(Plasma<T> pl, Geom gm, int ppx, int ppy, const double* prof, int npf,
+                              double rmax, double n0s) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pl.n) return;
+  const int ppc = ppx * ppy;
+  const int64_t c = p / ppc;
+  const int sub = (int)(p - c * ppc);
+  const int ix = (int)(c % gm.nx), iy = (int)(c / gm.nx);
+  const int sx = sub % ppx, sy = sub / ppx;
+  const double x = gm.xmin + ((double)ix + ((double)sx + 0.5) / ppx) * gm.dx;
+  const double y = gm.ymin + ((double)iy + ((double)sy + 0.5) / ppy) * gm.dy;
+  double dens = 1.0;
+  if (prof) {
+    const double r = sqrt(x * x + y * y);
+    double t = r / rmax * (npf - 1);
+    t = fmin(fmax(t, 0.0), (double)(npf - 1));
+    int k0 = (int)floor(t);
+    k0 = k0 < 0 ? 0 : (k0 > npf - 2 ? npf - 2 : k0);
+    const double fr = t - (double)k0;
+    dens = prof[k0] * (1.0 - fr) + prof[k0 + 1] * fr;
+  }
+  pl.x[p] = x;
+  pl.y[p] = y;
+  pl.psi[p] = 0.0;
+  pl.ux[p] = T(0);
+  pl.uy[p] = T(0);
+  pl.w[p] = T(n0s * dens * (gm.dx * gm.dy / (double)ppc));
+  pl.alive[p] = 1;
+  for (int k = 0; k < kRing * 5; ++k) pl.hist[(int64_t)k * pl.n + p] = T(0);
+  if (pl.cell) {
+    int jx, jy;
+    double fx, fy;
+    jx = (int)floor((x - gm.xmin) * gm.inv_dx);
+    jy = (int)floor((y - gm.ymin) * gm.inv_dy);
+    fx = (x - gm.xmin) * gm.inv_dx - jx;
+    fy = (y - gm.ymin) * gm.inv_dy - jy;
+    pl.cell[p] = (jy << 16) | jx;
+    pl.fx[p] = (float)fx;
+    pl.fy[p] = (float)fy;
+    pl.opp[p] = 1.0f;
+  }
+}
+
+// Deposit of the current plasma state (slice 0), or of the ion background
+// rho_ion = -(q w / A) deposited from the initial positions (ion_only).
+template <int P, typename T>
+__global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* rho_ion) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pl.n || !pl.alive[p]) return;
+  T wx[P + 1], wy[P + 1];
+  int ix0, iy0;
+  stencil_f64<P, T>(gm, pl.x[p], pl.y[p], ix0, iy0, wx, wy);
+  const T qw = T(-1.0) * pl.w[p] * T(gm.inv_area);
+  if (rho_ion) {
+#pragma unroll
+    for (int b = 0; b <= P; ++b) {
+      const int iy = iy0 + b;
+      if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        const int ix = ix0 + a;
+        if (!in_interior(ix, gm.nx)) continue;
+        atomicAdd(rho_ion + (int64_t)iy * gm.nx + ix, -(wx[a] * wy[b] * qw));
+      }
+    }
+    return;
+  }
+  const T ux = pl.ux[p], uy = pl.uy[p];
+  const T opp = T(1.0 + pl.psi[p]);
+  const T g = T(1) / opp;
+  const T u2 = ux * ux + uy * uy;
+  const T gam = (T(1) + u2 + opp * opp) * T(0.5) * g;
+  const T uz = (T(1) + u2 - opp * opp) * T(0.5) * g;
+  deposit_full<P, T>(dep, chi, gm.nx, gm.ny, ix0, iy0, wx, wy, qw * gam * g, qw * ux * g, qw * uy * g,
+                     qw * uz * g, qw * T(-1) * g);
+}
+
+// ---------------------------------------------------------------- trial pass (predictor-corrector)
+// Gather with B^(m-1), AB5 trial step to slice i+1, deposit J_perp of the trial
+// particles into tj (Sec. 3.2, predictor-corrector field solver).
+template <int P, typename T, bool CACHE>
+__global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf,
+                                                         V2<T>* tj, int slice, double guard) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pl.n || !pl.alive[p]) return;
+  const int64_t n = pl.n;
+  T wx[P + 1], wy[P + 1];
+  int ix0, iy0;
+  T opp;
+  int jx = 0, jy = 0;
+  T fxr = T(0), fyr = T(0);
+  if constexpr (CACHE) {
+    const int cell = pl.cell[p];
+    jx = cell & 0xFFFF;
+    jy = cell >> 16;
+    fxr = T(pl.fx[p]);
+    fyr = T(pl.fy[p]);
+    ix0 = shape_weights<P, T>(jx, fxr, wx);
+    iy0 = shape_weights<P, T>(jy, fyr, wy);
+    opp = T(pl.opp[p]);
+  } else {
+    stencil_f64<P, T>(gm, pl.x[p], pl.y[p], ix0, iy0, wx, wy);
+    opp = T(1.0 + pl.psi[p]);
+  }
+  const T ux = pl.ux[p], uy = pl.uy[p];
+  const F6<T> F = gather6<P, T>(gf, gm.nx, gm.ny, ix0, iy0, wx, wy);
+  T f[5];
+  derivs<T>(ux, uy, opp, F, f);
+  const T dz = T(gm.dzeta);
+  const T cx = ab5_comb<T>(pl.hist, n, p, slice, 0, f[0]);
+  const T cy = ab5_comb<T>(pl.hist, n, p, slice, 1, f[1]);
+  const T tux = ux - dz * ab5_comb<T>(pl.hist, n, p, slice, 2, f[2]);
+  const T tuy = uy - dz * ab5_comb<T>(pl.hist, n, p, slice, 3, f[3]);
+  const T cpsi = ab5_comb<T>(pl.hist, n, p, slice, 4, f[4]);
+  T twx[P + 1], twy[P + 1];
+  int tix0, tiy0;
+  T topp;
+  if constexpr (CACHE) {
+    // trial step in cell-relative coordinates (FP32 only)
+    T ux_ = fxr - T(gm.dzeta * gm.inv_dx) * cx;
+    T uy_ = fyr - T(gm.dzeta * gm.inv_dy) * cy;
+    const T flx = floor(ux_), fly = floor(uy_);
+    const int tjx = jx + (int)flx, tjy = jy + (int)fly;
+    ux_ -= flx;
+    uy_ -= fly;
+    topp = opp - dz * cpsi;
+    const T ax = T(tjx) + ux_, ay = T(tjy) + uy_;
+    const bool ok = isfinite(ax) && isfinite(ay) && isfinite(topp) && ax > T(0) && ax < T(gm.nx) &&
+                    ay > T(0) && ay < T(gm.ny) && topp >= T(guard);
+    if (!ok) return;
+    tix0 = shape_weights<P, T>(tjx, ux_, twx);
+    tiy0 = shape_weights<P, T>(tjy, uy_, twy);
+  } else {
+    const double tx = pl.x[p] - (double)dz * (double)cx;
+    const double ty = pl.y[p] - (double)dz * (double)cy;
+    const double tpsi = pl.psi[p] - (double)dz * (double)cpsi;
+    if (!state_ok(gm, tx, ty, 1.0 + tpsi, guard)) return;
+    topp = T(1.0 + tpsi);
+    stencil_f64<P, T>(gm, tx, ty, tix0, tiy0, twx, twy);
+  }
+  const T qw = T(-1.0) * pl.w[p] * T(gm.inv_area);
+  const T tg = T(1) / topp;
+  deposit_perp<P, T>(tj, gm.nx, gm.ny, tix0, tiy0, twx, twy, qw * tux * tg, qw * tuy * tg);
+}
+
+// ---------------------------------------------------------------- final pass
+// Gather with the converged fields of slice i, store f_i in the AB5 history,
+// advance to slice i+1, apply the removal rule and deposit rho, J, chi there.
+template <int P, typename T, bool CACHE>
+__global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf,
+                                                         V4<T>* dep, T* chi, int slice, double guard,
+                                                         unsigned long long* removed) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pl.n || !pl.alive[p]) return;
+  const int64_t n = pl.n;
+  T wx[P + 1], wy[P + 1];
+  int ix0, iy0;
+  T opp;
+  if constexpr (CACHE) {
+    const int cell = pl.cell[p];
+    ix0 = shape_weights<P, T>(cell & 0xFFFF, T(pl.fx[p]), wx);
+    iy0 = shape_weights<P, T>(cell >> 16, T(pl.fy[p]), wy);
+    opp = T(pl.opp[p]);
+  } else {
+    stencil_f64<P, T>(gm, pl.x[p], pl.y[p], ix0, iy0, wx, wy);
+    opp = T(1.0 + pl.psi[p]);
+  }
+  const T ux = pl.ux[p], uy = pl.uy[p];
+  const F6<T> F = gather6<P, T>(gf, gm.nx, gm.ny, ix0, iy0, wx, wy);
+  T f[5];
+  derivs<T>(ux, uy, opp, F, f);
+  T comb[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) comb[c] = ab5_comb<T>(pl.hist, n, p, slice, c, f[c]);
+  const int slot = slice % kRing;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) pl.hist[((int64_t)slot * 5 + c) * n + p] = f[c];
+  const double dz = gm.dzeta;
+  const double nxp = pl.x[p] - dz * (double)comb[0];
+  const double nyp = pl.y[p] - dz * (double)comb[1];
+  const double npsi = pl.psi[p] - dz * (double)comb[4];
+  const T nux = ux - T(dz) * comb[2];
+  const T nuy = uy - T(dz) * comb[3];
+  const double nopp = 1.0 + npsi;
+  if (!state_ok(gm, nxp, nyp, nopp, guard)) {
+    pl.alive[p] = 0;
+    atomicAdd(removed, 1ull);
+    return;
+  }
+  pl.x[p] = nxp;
+  pl.y[p] = nyp;
+  pl.psi[p] = npsi;
+  pl.ux[p] = nux;
+  pl.uy[p] = nuy;
+  T topp;
+  if constexpr (CACHE) {
+    const double ux_ = (nxp - gm.xmin) * gm.inv_dx, uy_ = (nyp - gm.ymin) * gm.inv_dy;
+    const double flx = floor(ux_), fly = floor(uy_);
+    const int jx = (int)flx, jy = (int)fly;
+    const float frx = (float)(ux_ - flx), fry = (float)(uy_ - fly);
+    pl.cell[p] = (jy << 16) | jx;
+    pl.fx[p] = frx;
+    pl.fy[p] = fry;
+    topp = (float)nopp;
+    pl.opp[p] = topp;
+    ix0 = shape_weights<P, T>(jx, T(frx), wx);
+    iy0 = shape_weights<P, T>(jy, T(fry), wy);
+  } else {
+    topp = T(nopp);
+    stencil_f64<P, T>(gm, nxp, nyp, ix0, iy0, wx, wy);
+  }
+  const T qw = T(-1.0) * pl.w[p] * T(gm.inv_area);
+  const T g = T(1) / topp;
+  const T u2 = nux * nux + nuy * nuy;
+  const T gam = (T(1) + u2 + topp * topp) * T(0.5) * g;
+  const T uz = (T(1) + u2 - topp * topp) * T(0.5) * g;
+  deposit_full<P, T>(dep, chi, gm.nx, gm.ny, ix0, iy0, wx, wy, qw * gam * g, qw * nux * g, qw * nuy * g,
+                     qw * uz * g, qw * T(-1) * g);
+}
+
+template <typename T> Plasma<T> plasma_of(const hq_grid_s* g);
+template <> Plasma<double> plasma_of<double>(const hq_grid_s* g) { return g->p64; }
+template <> Plasma<float> plasma_of<float>(const hq_grid_s* g) { return g->p32; }
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+template <typename T>
+void launch_plasma_init(const hq_grid_s* g, cudaStream_t s) {
+  k_plasma_init<T><<<blocks_for(g->np), kThreads, 0, s>>>(
+      plasma_of<T>(g), g->geom, g->d.ppc_x, g->d.ppc_y, g->profile.empty() ? nullptr : g->d_profile,
+      (int)g->profile.size(), g->d.profile_rmax, g->d.n0_scale);
+}
+
+template <typename T>
+void launch_deposit_initial(const hq_grid_s* g, void* dep, void* chi, int ion_only, cudaStream_t s) {
+  const unsigned nb = blocks_for(g->np);
+  V4<T>* d = reinterpret_cast<V4<T>*>(dep);
+  T* c = reinterpret_cast<T*>(chi);
+  T* ion = ion_only ? reinterpret_cast<T*>(g->rho_ion) : nullptr;
+  switch (g->d.shape_order) {
+    case 0: k_deposit_initial<0, T><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, d, c, ion); break;
+    case 1: k_deposit_initial<1, T><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, d, c, ion); break;
+    case 2: k_deposit_initial<2, T><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, d, c, ion); break;
+    default: k_deposit_initial<3, T><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, d, c, ion); break;
+  }
+}
+
+template <typename T>
+void launch_trial_pass(const hq_grid_s* g, int slice, cudaStream_t s) {
+  const unsigned nb = blocks_for(g->np);
+  const T* gf = reinterpret_cast<const T*>(g->gf);
+  V2<T>* tj = reinterpret_cast<V2<T>*>(g->tj);
+  constexpr bool C = sizeof(T) == 4;
+  const double gd = g->d.psi_guard;
+  switch (g->d.shape_order) {
+    case 0: k_trial_pass<0, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
+    case 1: k_trial_pass<1, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
+    case 2: k_trial_pass<2, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
+    default: k_trial_pass<3, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
+  }
+}
+
+template <typename T>
+void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cudaStream_t s) {
+  const unsigned nb = blocks_for(g->np);
+  const T* gf = reinterpret_cast<const T*>(g->gf);
+  V4<T>* d = reinterpret_cast<V4<T>*>(dep);
+  T* c = reinterpret_cast<T*>(chi);
+  constexpr bool C = sizeof(T) == 4;
+  const double gd = g->d.psi_guard;
+  unsigned long long* rm = g->d_removed;
+  switch (g->d.shape_order) {
+    case 0: k_final_pass<0, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
+    case 1: k_final_pass<1, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
+    case 2: k_final_pass<2, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
+    default: k_final_pass<3, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
+  }
+}
+
+template void launch_plasma_init<float>(const hq_grid_s*, cudaStream_t);
+template void launch_plasma_init<double>(const hq_grid_s*, cudaStream_t);
+template void launch_deposit_initial<float>(const hq_grid_s*, void*, void*, int, cudaStream_t);
+template void launch_deposit_initial<double>(const hq_grid_s*, void*, void*, int, cudaStream_t);
+template void launch_trial_pass<float>(const hq_grid_s*, int, cudaStream_t);
+template void launch_trial_pass<double>(const hq_grid_s*, int, cudaStream_t);
+template void launch_final_pass<float>(const hq_grid_s*, int, void*, void*, cudaStream_t);
+template void launch_final_pass<double>(const hq_grid_s*, int, void*, void*, cudaStream_t);
+
+}  // namespace hq

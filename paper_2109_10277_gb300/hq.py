@@ -1,0 +1,241 @@
+"""Python binding of libhq (include/hq.h): argument marshalling only.
+
+Every step of the quasi-static slice loop runs in the CUDA kernels of libhq.so;
+PyTorch provides device memory (tensors) and the stream.  There is no fallback:
+if the library is missing or the device is not sm_103a the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhq.so")
+
+HQ_PREC_FP64 = 0
+HQ_PREC_FP32_BF16X3 = 1
+STATUS = {0: "HQ_OK", 1: "HQ_ERR_ARG", 2: "HQ_ERR_CUDA", 3: "HQ_ERR_OOM", 4: "HQ_ERR_NUMERIC",
+          5: "HQ_ERR_TIMEOUT", 6: "HQ_ERR_STATE", 7: "HQ_ERR_UNSUPPORTED"}
+FIELDS = ("rho", "jx", "jy", "jz", "chi", "psi", "exmby", "eypbx", "ez", "bx", "by", "bz")
+EXPORTS = ("hq_grid_create", "hq_grid_destroy", "hq_advance_slice", "hq_beam_deposit", "hq_solve_fields",
+           "hq_store_fields", "hq_push_beams", "hq_witness_accumulate", "hq_sweep_step", "hq_poisson_solve",
+           "hq_plasma_state", "hq_sync", "hq_last_error")
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nzeta", C.c_int32),
+                ("xmin", C.c_double), ("xmax", C.c_double), ("ymin", C.c_double), ("ymax", C.c_double),
+                ("zeta_min", C.c_double), ("zeta_max", C.c_double),
+                ("shape_order", C.c_int32), ("ppc_x", C.c_int32), ("ppc_y", C.c_int32),
+                ("radial_profile", C.POINTER(C.c_double)), ("n_profile", C.c_int32), ("profile_rmax", C.c_double),
+                ("n0_scale", C.c_double), ("n_pc_iter", C.c_int32), ("pc_mix", C.c_double),
+                ("psi_guard", C.c_double), ("precision", C.c_int32)]
+
+
+class BeamView(C.Structure):
+    _fields_ = [("n", C.c_int64)] + [(k, C.c_void_p) for k in ("x", "y", "zeta", "ux", "uy", "uz", "w")] + \
+               [("charge", C.c_double), ("mass", C.c_double)]
+
+
+class FieldOut(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in FIELDS]
+
+
+class PlasmaView(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p), ("psi", C.c_void_p),
+                ("ux", C.c_void_p), ("uy", C.c_void_p), ("w", C.c_void_p), ("alive", C.c_void_p)]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libhq.so (built in-tree by paper_2109_10277_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2109_10277_gb300.build`")
+        lib = C.CDLL(LIB_PATH)
+        P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "hq_grid_create": (C.POINTER(GridDesc), P, C.POINTER(P)),
+            "hq_grid_destroy": (P,),
+            "hq_advance_slice": (P, I32),
+            "hq_beam_deposit": (P, C.POINTER(BeamView), I32, I32),
+            "hq_solve_fields": (P, I32),
+            "hq_store_fields": (P, C.POINTER(FieldOut), I64),
+            "hq_push_beams": (P, C.POINTER(BeamView), I32, I32, D),
+            "hq_witness_accumulate": (P, C.POINTER(BeamView), I32, P),
+            "hq_sweep_step": (P, C.POINTER(BeamView), I32, D, C.POINTER(FieldOut), I32, P),
+            "hq_poisson_solve": (P, P, P, I32),
+            "hq_plasma_state": (P, C.POINTER(PlasmaView)),
+            "hq_sync": (P, C.POINTER(I64)),
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = list(args)
+            fn.restype = C.c_int
+        lib.hq_last_error.argtypes = [P]
+        lib.hq_last_error.restype = C.c_char_p
+        _lib = lib
+    return _lib
+
+
+class HQError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st: int, handle) -> None:
+    if st != 0:
+        msg = load().hq_last_error(handle)
+        raise HQError(st, msg.decode() if msg else "")
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class _CudaArray:
+    """Zero-copy view of library-owned device memory (for hq_plasma_state)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+class Beam:
+    """One beam species: float64 CUDA tensors x, y, zeta, ux, uy, uz, w (updated in place by pushes)."""
+
+    def __init__(self, arrays: dict, device: str = "cuda", charge: Optional[float] = None,
+                 mass: Optional[float] = None):
+        self.t = {k: torch.as_tensor(arrays[k], dtype=torch.float64, device=device).contiguous()
+                  for k in ("x", "y", "zeta", "ux", "uy", "uz", "w")}
+        self.charge = float(arrays.get("charge", -1.0) if charge is None else charge)
+        self.mass = float(arrays.get("mass", 1.0) if mass is None else mass)
+
+    @property
+    def n(self) -> int:
+        return int(self.t["x"].numel())
+
+    def view(self) -> BeamView:
+        return BeamView(self.n, *[self.t[k].data_ptr() for k in ("x", "y", "zeta", "ux", "uy", "uz", "w")],
+                        self.charge, self.mass)
+
+
+def _beam_array(beams: Sequence[Beam]):
+    arr = (BeamView * max(1, len(beams)))()
+    for i, b in enumerate(beams):
+        arr[i] = b.view()
+    return arr
+
+
+class Grid:
+    """A quasi-static grid (plasma slice, field slices, DST scratch) on the current CUDA device."""
+
+    def __init__(self, params: dict, precision: str = "fp64", stream: Optional[torch.cuda.Stream] = None):
+        lib = load()
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        prof = params.get("radial_profile")
+        self._prof = (C.c_double * len(prof))(*prof) if prof is not None else None
+        d = GridDesc(
+            int(params["nx"]), int(params["ny"]), int(params["nzeta"]),
+            float(params["xmin"]), float(params["xmax"]), float(params["ymin"]), float(params["ymax"]),
+            float(params["zeta_min"]), float(params["zeta_max"]),
+            int(params.get("shape_order", 1)), int(params.get("ppc_x", 1)), int(params.get("ppc_y", 1)),
+            C.cast(self._prof, C.POINTER(C.c_double)) if self._prof is not None else None,
+            len(prof) if prof is not None else 0, float(params.get("profile_rmax", 0.0)),
+            float(params.get("n0_scale", 1.0)), int(params.get("n_pc_iter", 5)), float(params.get("pc_mix", 0.05)),
+            float(params.get("psi_guard", 0.02)),
+            HQ_PREC_FP64 if precision == "fp64" else HQ_PREC_FP32_BF16X3)
+        self.params = dict(params)
+        self.nx, self.ny, self.nzeta = d.nx, d.ny, d.nzeta
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib.hq_grid_create(C.byref(d), C.c_void_p(self.stream.cuda_stream), C.byref(h)), None)
+        self.h = h
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().hq_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, out: Optional[dict]):
+        if out is None:
+            return None
+        fo = FieldOut()
+        for k in FIELDS:
+            t = out.get(k)
+            if t is not None:
+                assert t.dtype == self.dtype and t.is_cuda and t.is_contiguous()
+                setattr(fo, k, t.data_ptr())
+        return fo
+
+    def alloc_out(self, names: Sequence[str] = FIELDS, nslots: Optional[int] = None) -> dict:
+        n = self.nzeta if nslots is None else nslots
+        return {k: torch.zeros((n, self.ny, self.nx), dtype=self.dtype, device="cuda") for k in names}
+
+    # fine-grained steps (Sec. 2 enumerate)
+    def advance(self, slice_: int) -> None:
+        _check(load().hq_advance_slice(self.h, slice_), self.h)
+
+    def beam_deposit(self, beams: Sequence[Beam], slice_: int) -> None:
+        self._beams = _beam_array(beams)
+        _check(load().hq_beam_deposit(self.h, self._beams, len(beams), slice_), self.h)
+
+    def solve(self, slice_: int) -> None:
+        _check(load().hq_solve_fields(self.h, slice_), self.h)
+
+    def store(self, out: dict, slot: int) -> None:
+        fo = self._out(out)
+        _check(load().hq_store_fields(self.h, C.byref(fo), slot), self.h)
+
+    def push_beams(self, beams: Sequence[Beam], slice_: int, dt: float) -> None:
+        arr = _beam_array(beams)
+        _check(load().hq_push_beams(self.h, arr, len(beams), slice_, float(dt)), self.h)
+
+    def witness_accumulate(self, beam: Beam, slice_: int, sums: torch.Tensor) -> None:
+        v = beam.view()
+        _check(load().hq_witness_accumulate(self.h, C.byref(v), slice_, C.c_void_p(sums.data_ptr())), self.h)
+
+    def sweep(self, beams: Sequence[Beam] = (), dt: float = 0.0, out: Optional[dict] = None,
+              witness: int = -1, witness_sums: Optional[torch.Tensor] = None) -> None:
+        arr = _beam_array(beams)
+        fo = self._out(out)
+        _check(load().hq_sweep_step(self.h, arr, len(beams), float(dt), C.byref(fo) if fo is not None else None,
+                                    int(witness), C.c_void_p(_ptr(witness_sums)) if witness_sums is not None else None),
+               self.h)
+
+    def poisson_solve(self, src: torch.Tensor) -> torch.Tensor:
+        assert src.dtype == self.dtype and src.is_cuda and src.is_contiguous() and src.dim() == 3
+        dst = torch.empty_like(src)
+        _check(load().hq_poisson_solve(self.h, C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr()),
+                                       src.shape[0]), self.h)
+        return dst
+
+    def plasma_state(self) -> dict:
+        """Copies of the plasma slice arrays (synchronizes the grid's stream)."""
+        v = PlasmaView()
+        _check(load().hq_plasma_state(self.h, C.byref(v)), self.h)
+        self.sync()
+        ft = "<f8" if self.precision == "fp64" else "<f4"
+        n = int(v.n)
+        out = {}
+        for k, ts in (("x", "<f8"), ("y", "<f8"), ("psi", "<f8"), ("ux", ft), ("uy", ft), ("w", ft), ("alive", "|u1")):
+            out[k] = torch.as_tensor(_CudaArray(getattr(v, k), n, ts), device="cuda").clone()
+        return out
+
+    def sync(self) -> int:
+        rm = C.c_int64()
+        _check(load().hq_sync(self.h, C.byref(rm)), self.h)
+        return int(rm.value)

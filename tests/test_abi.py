@@ -1,0 +1,67 @@
+"""Host-side checks of the C ABI: the library builds, loads, exports every entry
+point declared in include/hq.h, and refuses to run without an sm_103a device
+(no CPU fallback).  No compute call is made here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "hq.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:hq_status|const char\*)\s+(hq_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2109_10277_gb300 import build, hq
+    if not os.path.exists(hq.LIB_PATH):
+        build.build()
+    return hq.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("hq_grid_create", "hq_beam_deposit", "hq_advance_slice", "hq_solve_fields", "hq_sweep_step"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2109_10277_gb300 import hq
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+    assert set(declared_symbols()) == set(hq.EXPORTS)
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.hq_grid_create(None, None, None) == 1  # HQ_ERR_ARG
+    assert b"NULL" in lib.hq_last_error(None)
+    assert lib.hq_advance_slice(None, 0) == 1
+    assert lib.hq_sync(None, None) == 1
+
+
+def test_bad_descriptor_is_rejected(lib):
+    from paper_2109_10277_gb300 import hq
+    d = hq.GridDesc(4, 64, 8, -1, 1, -1, 1, 0, 1, 1, 1, 1, None, 0, 0.0, 1.0, 5, 0.05, 0.02, 0)
+    h = C.c_void_p()
+    assert lib.hq_grid_create(C.byref(d), None, C.byref(h)) == 1
+    assert b"nx" in lib.hq_last_error(None)
+    d = hq.GridDesc(64, 64, 8, -1, 1, -1, 1, 0, 1, 7, 1, 1, None, 0, 0.0, 1.0, 5, 0.05, 0.02, 0)
+    assert lib.hq_grid_create(C.byref(d), None, C.byref(h)) == 1
+    assert b"shape_order" in lib.hq_last_error(None)
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU refusal")
+def test_no_device_fails_loudly(lib):
+    from paper_2109_10277_gb300 import hq
+    d = hq.GridDesc(64, 64, 8, -1, 1, -1, 1, 0, 1, 1, 1, 1, None, 0, 0.0, 1.0, 5, 0.05, 0.02, 0)
+    h = C.c_void_p()
+    st = lib.hq_grid_create(C.byref(d), None, C.byref(h))
+    assert st in (2, 7)  # HQ_ERR_CUDA / HQ_ERR_UNSUPPORTED, never a silent CPU path
+    assert not h.value
+    with pytest.raises(RuntimeError):  # HQError or torch refusing the stream
+        hq.Grid(dict(nx=64, ny=64, nzeta=8, xmin=-1, xmax=1, ymin=-1, ymax=1, zeta_min=0, zeta_max=1))
