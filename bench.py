@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Throughput of the quasi-static sweep (arXiv:2109.10277, Sec. 2) on GB300.
+
+Metric: plasma particle-slice pushes per second, i.e. plasma particles per slice
+x slices x sweeps / time of hq_sweep_step (predictor-corrector trial passes are
+not counted; the raw pass count is reported beside it).  The workload is the
+512^2 x 1024-slice blowout sweep: +-8 box, 1 particle per cell (262,144 per
+slice), quadratic shape, 5 predictor-corrector iterations, a seeded 1e6-particle
+Gaussian driver (sigma_r = 0.2, sigma_z = 1.4, n_b = 5).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hq|reference]
+
+One JSON line on rank 0.  N > 1 runs N independent replicas (one per GPU, the
+sweep does not shard), value = all replicas' particle-slices / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "plasma particle-slice pushes/s, FP32-split vs FP64 on 1 GB300; adjoint/forward time"
+UNIT = "particle-slices/s"
+WORKLOAD = "blowout512"
+WORKLOAD_DESC = ("512x512 grid on +-8 k_p^-1 x 1024 slices over zeta in [-13, 7]; 1 plasma particle per cell "
+                 "(262144 per slice), quadratic shape; seeded 1e6-particle Gaussian driver sigma_r=0.2, "
+                 "sigma_z=1.4, n_b/n0=5; predictor-corrector 5 iterations, mixing 0.05")
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+# algorithmic bytes per particle of the FP32 particle passes (reads + writes)
+BYTES_TRIAL = 109   # ux, uy, w (12) + AB5 history 4x5x4 (80) + cell/frac/1+Psi cache (16) + alive (1)
+BYTES_FINAL = 201   # reads: x, y, Psi (24) + 12 + 80 + 16 + 1; writes: x, y, Psi (24), ux, uy (8), f_i (20), cache (16)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("hq", "reference"), default="hq")
+    ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison sweep")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-slices", type=int, default=12, help="oracle sample: slices of the workload")
+    ap.add_argument("--case", choices=("sweep", "poisson"), default="sweep",
+                    help="poisson: only repeated 3-RHS Dirichlet solves on the workload grid (for ncu captures)")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    def __init__(self, dev: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            cols = [c.strip() for c in line.split(",")]
+            if len(cols) < 9:
+                continue
+            try:
+                sm.append(float(cols[1]))
+                mx = float(cols[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, cols[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(backend: str):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v: float, device) -> float:
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(n_slices: int) -> dict:
+    """The oracle as it stands on the first n_slices of the workload (host cores)."""
+    import torch
+
+    import oracle as O
+    from paper_2109_10277_gb300 import inputs as I
+    g = I.grid_params(WORKLOAD)
+    beams = [O.as_beam(b) for b in I.workload_beams(WORKLOAD)]
+    sp = O.GridSpec(**g)
+    t0 = time.perf_counter()
+    O.sweep(sp, beams, n_slices=n_slices, record=())
+    dt = time.perf_counter() - t0
+    p = g["nx"] * g["ny"] * g["ppc_x"] * g["ppc_y"]
+    return {"value": p * n_slices / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"first {n_slices} of 1024 slices of the {WORKLOAD} sweep ({p} particles/slice, "
+                      f"full 1e6-particle driver binned), FP64 torch-CPU oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    import torch
+    world, rank, _ = dist_setup("gloo")
+    if rank != 0:
+        return
+    n = max(1, min(args.cpu_slices, 4))
+    for _ in range(args.warmup):
+        oracle_sample(n)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = oracle_sample(n)
+        times.append(time.perf_counter() - t0)
+    from paper_2109_10277_gb300 import inputs as I
+    g = I.grid_params(WORKLOAD)
+    p = g["nx"] * g["ny"]
+    value = p * n * args.steps / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "sample_slices_per_step": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def dst_flops_per_sweep(g: dict) -> float:
+    """Executed bf16 flops of the tensor-core DST-I per sweep: per solve of R right-hand
+    sides, 4 products of 2 M N K with M = R x padded rows, times 3 (bf16x3)."""
+    nxp = -(-g["nx"] // 128) * 128
+    nyp = -(-g["ny"] // 128) * 128
+    per_rhs = 2 * (2.0 * nyp * nxp * nxp) + 2 * (2.0 * nxp * nyp * nyp)
+    rhs_per_slice = 3 + 2 * g["n_pc_iter"]
+    return 3.0 * per_rhs * rhs_per_slice * g["nzeta"]
+
+
+def run_hq(args):
+    import torch
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2109_10277_gb300 import hq
+    from paper_2109_10277_gb300 import inputs as I
+    peaks, peak_src = load_peaks()
+
+    g = I.grid_params(WORKLOAD)
+    beams_np = I.workload_beams(WORKLOAD)
+    p = g["nx"] * g["ny"] * g["ppc_x"] * g["ppc_y"]
+    nz = g["nzeta"]
+    stream = torch.cuda.current_stream()
+    grid = hq.Grid(g, precision=args.precision, stream=stream)
+    hb = [hq.Beam(b) for b in beams_np]
+    sums = torch.zeros(3, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    def step():
+        sums.zero_()
+        grid.sweep(hb, witness=0, witness_sums=sums)
+
+    for _ in range(args.warmup):
+        step()
+    grid.sync()
+
+    # ---- timed region: K sweeps, inputs resident in HBM, L2 flushed between sweeps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    t_host = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_host = time.perf_counter() - t_host
+    clocks = clk.stop()
+    removed = grid.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms = allmax(world, ms, dev)
+    value = p * nz * args.steps * world / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers: H2D beams, sweep, D2H result
+    host = [{k: b.t[k].cpu().pin_memory() for k in b.t} for b in hb]
+    res_host = torch.zeros(3, dtype=torch.float64).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    h2d = sum(t.numel() * t.element_size() for hbuf in host for t in hbuf.values())
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e2e_ev[k][0].record(stream)
+        for b, hbuf in zip(hb, host):
+            for key, t in hbuf.items():
+                b.t[key].copy_(t, non_blocking=True)
+        step()
+        res_host.copy_(sums, non_blocking=True)
+        e2e_ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = allmax(world, sum(a.elapsed_time(b) for a, b in e2e_ev), dev)
+    e2e_value = p * nz * args.steps * world / (e2e_ms / 1e3)
+
+    # ---- one more sweep with per-kernel-class CUDA events (launch stream) for the roofline
+    grid.profile(True)
+    step()
+    prof = grid.profile_read()
+    grid.profile(False)
+    launches_per_sweep = sum(v[1] for v in prof.values())
+    shares = {k: v[0] for k, v in prof.items()}
+    tot = sum(shares.values()) or 1.0
+    dom = max(shares, key=shares.get)
+    roofs = {}
+    if prof["dst"][0] > 0:
+        fl = dst_flops_per_sweep(g) if args.precision == "fp32" else None
+        if fl:
+            ach = fl / (prof["dst"][0] / 1e3) / 1e12
+            pk = peaks["bf16_tflops_sustained"]
+            roofs["dst"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                            "traffic": None, "avg_launch_us": 1e3 * prof["dst"][0] / max(1, prof["dst"][1]),
+                            "peak_src": f"bf16 sustained, {peak_src}"}
+    for k, nb in (("trial", BYTES_TRIAL), ("final", BYTES_FINAL)):
+        if prof[k][0] > 0 and args.precision == "fp32":
+            nl = max(1, prof[k][1])
+            ach = nb * p * nl / (prof[k][0] / 1e3) / 1e9
+            pk = peaks["hbm_gbs"]
+            roofs[k] = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+                        "traffic": None, "avg_launch_us": 1e3 * prof[k][0] / nl, "peak_src": f"hbm copy, {peak_src}"}
+    roof = dict(roofs.get(dom, next(iter(roofs.values()), {})))
+    if roof:
+        roof["kernel"] = dom
+
+    # ---- FP64 GPU path on the same workload (speedup of FP32/bf16x3 over plain FP64)
+    fp64 = None
+    if not args.no_fp64 and args.precision == "fp32":
+        g64 = hq.Grid(g, precision="fp64", stream=stream)
+        sums64 = torch.zeros(3, dtype=torch.float64, device=dev)
+        g64.sweep(hb, witness=0, witness_sums=sums64)
+        g64.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        a.record(stream)
+        g64.sweep(hb, witness=0, witness_sums=sums64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)
+        fp64 = {"value": p * nz / (ms64 / 1e3), "ms_per_step": ms64,
+                "fp32_speedup": (p * nz * args.steps / (ms / 1e3)) / (p * nz / (ms64 / 1e3))}
+        g64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(args.cpu_slices)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}",
+                       "precision": "FP32 push/gather/deposit, FP64 x/y/Psi accumulators, bf16x3 tensor-core DST-I"
+                       if args.precision == "fp32" else "FP64 everywhere, FP64 FFT DST-I",
+                       "particles_per_slice": p, "slices": nz, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                       "raw_particle_passes_per_s": value * (1 + g["n_pc_iter"]),
+                       "host_wall_s": t_host},
+            "roofline": roof, "rooflines": roofs,
+            "kernel_ms_per_sweep": {k: round(v[0], 3) for k, v in prof.items()},
+            "kernel_share": {k: round(v / tot, 4) for k, v in shares.items()},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
+            "gpu_launches": launches_per_sweep * args.steps,
+            "fp64": fp64, "cpu_baseline": cpu, "removed_particles": removed,
+        }
+        print(json.dumps(line), flush=True)
+    grid.close()
+
+
+def run_poisson_case(args):
+    """A few 3-right-hand-side solves on the workload grid: the DST kernels alone."""
+    import torch
+    from paper_2109_10277_gb300 import hq
+    from paper_2109_10277_gb300 import inputs as I
+    g = I.grid_params(WORKLOAD)
+    grid = hq.Grid(g, precision=args.precision)
+    dt = torch.float32 if args.precision == "fp32" else torch.float64
+    src = torch.randn(3, g["ny"], g["nx"], dtype=dt, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        grid.poisson_solve(src)
+    grid.sync()
+    grid.close()
+    print(json.dumps({"case": "poisson", "solves": args.warmup + args.steps}))
+
+
+def main():
+    args = parse()
+    if args.case == "poisson":
+        run_poisson_case(args)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_hq(args)
+
+
+if __name__ == "__main__":
+    main()

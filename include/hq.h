@@ -162,6 +162,29 @@ hq_status hq_poisson_solve(hq_grid_t grid, const void* src, void* dst, int32_t n
 /* Fills *out with views of the plasma slice (state after the last advance). */
 hq_status hq_plasma_state(hq_grid_t grid, hq_plasma_view* out);
 
+/* Kernel classes timed by the profiler (index into hq_profile_t arrays). */
+enum {
+  HQ_K_FINAL = 0,   /* plasma final pass: gather, AB5 step, deposit (Sec. 3.2)        */
+  HQ_K_TRIAL = 1,   /* plasma predictor-corrector trial pass                           */
+  HQ_K_DST = 2,     /* DST-I transform launches (tensor-core GEMM or FP64 FFT)         */
+  HQ_K_FIELD = 3,   /* source assembly, -grad psi, mixing, guess/shift, output copy    */
+  HQ_K_BEAM = 4,    /* beam binning, deposit, push, witness sums                       */
+  HQ_K_OTHER = 5,   /* buffer resets, plasma initialization                            */
+  HQ_K_CLASSES = 8
+};
+typedef struct {
+  double ms[HQ_K_CLASSES];        /* summed device time (CUDA events on the grid's stream) */
+  int64_t launches[HQ_K_CLASSES]; /* kernel launches issued                                 */
+} hq_profile_t;
+
+/* on != 0: from now on record a CUDA event pair around every kernel-class launch
+ * group on the grid's stream; on == 0: stop recording.  Launch counting is always
+ * on.  Either call resets the accumulators. */
+hq_status hq_profile_enable(hq_grid_t grid, int32_t on);
+
+/* Synchronizes the stream and returns the accumulated times and launch counts. */
+hq_status hq_profile_read(hq_grid_t grid, hq_profile_t* out);
+
 /* Waits for the grid's stream, then reports device status: HQ_ERR_TIMEOUT or
  * HQ_ERR_NUMERIC if a kernel flagged one (the flag is cleared), else HQ_OK.
  * removed (may be NULL) receives the number of plasma particles removed so far. */

@@ -419,18 +419,22 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
           n_slices: Optional[int] = None, record: Sequence[str] = FIELD_NAMES,
           witness: Sequence[int] = (), record_plasma_at: Sequence[int] = (),
           n0_scale: Optional[torch.Tensor] = None, radial_profile: Optional[torch.Tensor] = None,
-          ) -> SweepResult:
+          plasma_perm: Optional[torch.Tensor] = None) -> SweepResult:
     """One quasi-static sweep head -> tail (Sec. 2), slices i = 0 .. n_slices-1.
 
     Per slice (Sec. 2 steps 1-7 and the Sec. 3.2 predictor-corrector):
       deposit plasma + ions + beam(i); solve psi -> ExmBy, EypBx; Ez; Bz;
       predictor-corrector for Bx, By; final gather; push plasma to i+1.
     dt != 0 also advances every beam particle once with its own slice's fields.
+    plasma_perm (a permutation of the plasma particles) changes only the order in
+    which particle contributions are summed; results are returned in the original order.
     """
     ns = spec.nzeta if n_slices is None else n_slices
     dz = spec.dzeta
     qm = PLASMA_Q / PLASMA_M
     st = plasma_init(spec, n0_scale, radial_profile)
+    if plasma_perm is not None:
+        st = {k: v[plasma_perm] for k, v in st.items()}
     rho_ion = ion_background(spec, st)
     zero = torch.zeros(spec.ny, spec.nx, dtype=DT)
     hist = [(torch.zeros_like(st["x"]),) * 5 for _ in range(4)]  # f_{i-1} .. f_{i-4}
@@ -512,6 +516,10 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
         b2, b1 = b1, (bx, by)
     res.fields = {k: torch.stack(v) for k, v in rec.items()}
     res.removed = int((~st["alive"]).sum())
+    if plasma_perm is not None:
+        inv = torch.argsort(plasma_perm)
+        st = {k: v[inv] for k, v in st.items()}
+        res.plasma_at = {i: {k: v[inv] for k, v in s_.items()} for i, s_ in res.plasma_at.items()}
     res.plasma = st
     res.beams = beams
     res.witness = {bi: tuple(v) for bi, v in wit.items()}

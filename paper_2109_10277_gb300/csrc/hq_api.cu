@@ -56,6 +56,8 @@ void free_all(hq_grid_s* g) {
   for (int b = 0; b < kMaxBeams; ++b) {
     F(g->bins[b].bin); F(g->bins[b].count); F(g->bins[b].offset); F(g->bins[b].cursor); F(g->bins[b].perm);
   }
+  for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+  g->ev_pool.clear();
   F(g->d_profile); F(g->d_status); F(g->d_removed); F(g->d_scratch_int);
   if (g->tmaps) dst_tc_free(g);
 }
@@ -81,44 +83,87 @@ double sin_jk(int64_t j, int64_t k, int n) {
   return std::sin(M_PI * (double)m / (double)n);
 }
 
-template <typename T> void* plasma_ptr(hq_grid_s* g);
+// Counts the launches of one kernel group and, while profiling is on, brackets
+// the group with a pair of CUDA events on the grid's stream.
+struct Prof {
+  hq_grid_s* g;
+  bool on;
+  Prof(hq_grid_s* g_, int cls, int nlaunch) : g(g_), on(g_->prof_on != 0) {
+    g->launches[cls] += nlaunch;
+    if (!on) return;
+    if (g->ev_used + 2 > g->ev_pool.size()) {
+      for (int k = 0; k < 256; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+        g->ev_pool.push_back(e);
+      }
+    }
+    g->ev_class.push_back(cls);
+    cudaEventRecord(g->ev_pool[g->ev_used], g->stream);
+  }
+  ~Prof() {
+    if (!on) return;
+    cudaEventRecord(g->ev_pool[g->ev_used + 1], g->stream);
+    g->ev_used += 2;
+  }
+};
+
+void dst_solve(hq_grid_s* g, int nrhs) {
+  Prof p(g, HQ_K_DST, 4);
+  if (g->fp64) dst_solve_f64(g, nrhs, g->stream);
+  else dst_solve_tc(g, nrhs, g->stream);
+}
 
 template <typename T>
 hq_status solve_fields_impl(hq_grid_s* g, int slice) {
   cudaStream_t s = g->stream;
   void* cur = g->dep[slice & 1];
   void* prev = g->dep[(slice + 1) & 1];
-  launch_src_main<T>(g, cur, s);
-  if (g->fp64) dst_solve_f64(g, 3, s);
-  else dst_solve_tc(g, 3, s);
-  launch_finish_main<T>(g, g->solved, s);
-  launch_bguess<T>(g, s);
-  for (int m = 0; m < g->d.n_pc_iter; ++m) {
-    launch_zero<T>(g->tj, 2 * g->nnode, s);
-    launch_trial_pass<T>(g, slice, s);
-    launch_src_bperp<T>(g, cur, prev, s);
-    if (g->fp64) dst_solve_f64(g, 2, s);
-    else dst_solve_tc(g, 2, s);
-    launch_finish_bperp<T>(g, g->solved, s);
+  void* chi_prev = g->chi[(slice + 1) & 1];
+  { Prof p(g, HQ_K_FIELD, 1); launch_src_main<T>(g, cur, s); }
+  dst_solve(g, 3);
+  { Prof p(g, HQ_K_FIELD, 1); launch_finish_main<T>(g, g->solved, s); }
+  const int npc = g->d.n_pc_iter;
+  for (int m = 0; m < npc; ++m) {
+    const int last = m == npc - 1;
+    { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, s); }
+    { Prof p(g, HQ_K_FIELD, 1); launch_src_bperp<T>(g, cur, prev, chi_prev, last, s); }
+    dst_solve(g, 2);
+    { Prof p(g, HQ_K_FIELD, 1); launch_finish_bperp<T>(g, g->solved, last, s); }
   }
-  launch_bshift<T>(g, s);
+  if (npc == 0) {
+    // no predictor-corrector: B(i) is the guess; shift, clear and reset without the fused kernels
+    Prof p(g, HQ_K_FIELD, 3);
+    launch_bshift<T>(g, s);
+    launch_zero<T>(g->bjn, 2 * g->nnode, s);
+    launch_reset_dep<T>(g, prev, chi_prev, s);
+  }
   return HQ_OK;
+}
+
+// Final AB5 pass of slice `slice_from` depositing into the record `parity`, which the
+// last predictor-corrector source kernel of that slice reset to the ion background.
+template <typename T>
+void final_pass(hq_grid_s* g, int slice_from, int parity) {
+  Prof p(g, HQ_K_FINAL, 1);
+  launch_final_pass<T>(g, slice_from, g->dep[parity], g->chi[parity], g->stream);
 }
 
 template <typename T>
 void advance_impl(hq_grid_s* g, int slice) {
   cudaStream_t s = g->stream;
-  void* dst = g->dep[slice & 1];
-  void* dchi = g->chi[slice & 1];
-  launch_reset_dep<T>(g, dst, dchi, s);
   if (slice == 0) {
+    Prof p(g, HQ_K_OTHER, 8);
+    launch_reset_dep<T>(g, g->dep[0], g->chi[0], s);
     launch_plasma_init<T>(g, s);
-    launch_deposit_initial<T>(g, dst, dchi, 0, s);
+    launch_deposit_initial<T>(g, g->dep[0], g->chi[0], 0, s);
     launch_zero<T>(g->dep[1], 4 * g->nnode, s);   // J(-1) = 0 ahead of the box
     launch_zero<T>(g->bprev1, 2 * g->nnode, s);
     launch_zero<T>(g->bprev2, 2 * g->nnode, s);
+    launch_zero<T>(g->bjn, 2 * g->nnode, s);
+    launch_zero<T>(g->tj, 2 * g->nnode, s);
   } else {
-    launch_final_pass<T>(g, slice - 1, dst, dchi, s);
+    final_pass<T>(g, slice - 1, slice & 1);
   }
 }
 
@@ -156,6 +201,7 @@ hq_status beam_deposit_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int
         bb.cap = beams[b].n;
       }
       g->bound[b] = beams[b];
+      Prof p(g, HQ_K_BEAM, beams[b].n > 0 ? 3 : 1);
       launch_beam_bin(g, b, beams[b], s);
     }
     g->nbound = nb;
@@ -164,9 +210,11 @@ hq_status beam_deposit_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int
     for (int b = 0; b < nb; ++b)
       if (!same_view(beams[b], g->bound[b])) return fail(g, HQ_ERR_STATE, "beams differ from those binned at slice 0");
   }
-  launch_zero<T>(g->bjn, 2 * g->nnode, s);
+  // bjn (beam J_perp of slice i+1) was cleared at the end of the previous slice's solve
   for (int b = 0; b < nb; ++b) {
-    if (beams[b].n > 0) launch_beam_deposit<T>(g, b, beams[b], slice, g->dep[slice & 1], g->bjn, s);
+    if (beams[b].n == 0) continue;
+    Prof p(g, HQ_K_BEAM, 1);
+    launch_beam_deposit<T>(g, b, beams[b], slice, g->dep[slice & 1], g->bjn, s);
   }
   return HQ_OK;
 }
@@ -237,6 +285,9 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   gm.inv_dx = 1.0 / gm.dx; gm.inv_dy = 1.0 / gm.dy;
   gm.dzeta = (d.zeta_max - d.zeta_min) / d.nzeta;
   gm.inv_area = 1.0 / (gm.dx * gm.dy);
+  gm.inv2dx = 0.5 / gm.dx;
+  gm.inv2dy = 0.5 / gm.dy;
+  gm.inv2dz = 0.5 / gm.dzeta;
   g->last_adv = g->last_beam = g->last_solved = -1;
 
   auto bail = [&](hq_status st) {
@@ -440,6 +491,7 @@ hq_status hq_store_fields(hq_grid_t g, const hq_field_out* out, int64_t slot) {
   if (!out || slot < 0) return fail(g, HQ_ERR_ARG, "out is NULL or slot < 0");
   if (g->last_solved < 0) return fail(g, HQ_ERR_STATE, "no slice solved yet");
   const int i = g->last_solved;
+  Prof p(g, HQ_K_FIELD, 1);
   if (g->fp64) launch_store<double>(g, out, slot, g->dep[i & 1], g->chi[i & 1], g->stream);
   else launch_store<float>(g, out, slot, g->dep[i & 1], g->chi[i & 1], g->stream);
   return check_launch(g);
@@ -455,6 +507,7 @@ hq_status hq_push_beams(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, int32_
     const int k = bound_index(g, &beams[b]);
     if (k < 0) return fail(g, HQ_ERR_STATE, "beam was not binned at slice 0 of this sweep");
     if (beams[b].n == 0) continue;
+    Prof p(g, HQ_K_BEAM, 1);
     if (g->fp64) launch_beam_push<double>(g, k, beams[b], slice, dt, g->stream);
     else launch_beam_push<float>(g, k, beams[b], slice, dt, g->stream);
   }
@@ -468,6 +521,7 @@ hq_status hq_witness_accumulate(hq_grid_t g, const hq_beam_view* beam, int32_t s
   const int k = bound_index(g, beam);
   if (k < 0) return fail(g, HQ_ERR_STATE, "beam was not binned at slice 0 of this sweep");
   if (beam->n == 0) return HQ_OK;
+  Prof p(g, HQ_K_BEAM, 1);
   if (g->fp64) launch_witness<double>(g, k, *beam, slice, sums, g->stream);
   else launch_witness<float>(g, k, *beam, slice, sums, g->stream);
   return check_launch(g);
@@ -491,13 +545,8 @@ hq_status hq_sweep_step(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, double
   }
   // advance once past the tail so the plasma state matches a completed sweep
   const int nz = g->nz;
-  if (g->fp64) {
-    launch_reset_dep<double>(g, g->dep[nz & 1], g->chi[nz & 1], g->stream);
-    launch_final_pass<double>(g, nz - 1, g->dep[nz & 1], g->chi[nz & 1], g->stream);
-  } else {
-    launch_reset_dep<float>(g, g->dep[nz & 1], g->chi[nz & 1], g->stream);
-    launch_final_pass<float>(g, nz - 1, g->dep[nz & 1], g->chi[nz & 1], g->stream);
-  }
+  if (g->fp64) final_pass<double>(g, nz - 1, nz & 1);
+  else final_pass<float>(g, nz - 1, nz & 1);
   g->last_adv = nz;
   return check_launch(g);
 }
@@ -506,13 +555,12 @@ hq_status hq_poisson_solve(hq_grid_t g, const void* src, void* dst, int32_t nrhs
   if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
   if (!src || !dst || nrhs < 1 || nrhs > kMaxRhs) return fail(g, HQ_ERR_ARG, "src/dst NULL or nrhs not in 1..5");
   cudaStream_t s = g->stream;
-  if (g->fp64) {
-    launch_src_copy<double>(g, src, nrhs, s);
-    dst_solve_f64(g, nrhs, s);
-  } else {
-    launch_src_copy<float>(g, src, nrhs, s);
-    dst_solve_tc(g, nrhs, s);
+  {
+    Prof p(g, HQ_K_FIELD, 1);
+    if (g->fp64) launch_src_copy<double>(g, src, nrhs, s);
+    else launch_src_copy<float>(g, src, nrhs, s);
   }
+  dst_solve(g, nrhs);
   HQ_CUDA(g, cudaMemcpyAsync(dst, g->solved, (size_t)nrhs * g->nnode * g->tsize, cudaMemcpyDeviceToDevice, s));
   return check_launch(g);
 }
@@ -542,6 +590,32 @@ hq_status hq_sync(hq_grid_t g, int64_t* removed) {
     HQ_CUDA(g, cudaMemset(g->d_status, 0, sizeof(int)));
     if (status & DEV_TIMEOUT) return fail(g, HQ_ERR_TIMEOUT, "a bounded device wait ran out (tensor-core DST)");
     if (status & DEV_NONFINITE) return fail(g, HQ_ERR_NUMERIC, "a non-finite value reached the field solve");
+  }
+  return HQ_OK;
+}
+
+hq_status hq_profile_enable(hq_grid_t g, int32_t on) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  HQ_CUDA(g, cudaStreamSynchronize(g->stream));
+  g->prof_on = on != 0;
+  g->ev_used = 0;
+  g->ev_class.clear();
+  for (int k = 0; k < HQ_K_CLASSES; ++k) g->launches[k] = 0;
+  return HQ_OK;
+}
+
+hq_status hq_profile_read(hq_grid_t g, hq_profile_t* out) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (!out) return fail(g, HQ_ERR_ARG, "out is NULL");
+  HQ_CUDA(g, cudaStreamSynchronize(g->stream));
+  for (int k = 0; k < HQ_K_CLASSES; ++k) {
+    out->ms[k] = 0.0;
+    out->launches[k] = g->launches[k];
+  }
+  for (size_t i = 0; i < g->ev_class.size() && 2 * i + 1 < g->ev_used; ++i) {
+    float ms = 0.0f;
+    HQ_CUDA(g, cudaEventElapsedTime(&ms, g->ev_pool[2 * i], g->ev_pool[2 * i + 1]));
+    out->ms[g->ev_class[i]] += ms;
   }
   return HQ_OK;
 }

@@ -35,7 +35,11 @@ struct Geom {
   double xmin, ymin, dx, dy, inv_dx, inv_dy, dzeta;
   double xmax, ymax;
   double inv_area;  // 1 / (dx dy)
+  double inv2dx, inv2dy, inv2dz;  // 1/(2 dx), 1/(2 dy), 1/(2 dzeta): central differences
 };
+
+// Geometry constants in the kernel's arithmetic type (no per-thread FP64 division).
+template <typename T> __device__ __forceinline__ T cst(double v) { return T(v); }
 
 template <typename T> struct V4 { T a, b, c, d; };   // packed rho, jx, jy, jz
 template <typename T> struct V2 { T a, b; };          // packed jx, jy or bx, by
@@ -122,6 +126,13 @@ struct hq_grid_s {
 
   int last_adv, last_beam, last_solved;
   std::string err;
+
+  // profiling: launch counters (always) and optional CUDA event pairs per launch group
+  int64_t launches[HQ_K_CLASSES];
+  int prof_on;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_class;   // class of each recorded pair (events 2k, 2k+1)
+  size_t ev_used;
 };
 
 namespace hq {
@@ -135,10 +146,15 @@ template <typename T> void launch_final_pass(const hq_grid_s* g, int slice, void
 // fields
 template <typename T> void launch_reset_dep(const hq_grid_s* g, void* dep, void* chi, cudaStream_t s);
 template <typename T> void launch_src_main(const hq_grid_s* g, const void* dep, cudaStream_t s);
-template <typename T> void launch_src_bperp(const hq_grid_s* g, const void* dep_cur, const void* dep_prev, cudaStream_t s);
+// reads and clears the trial J_perp; reset_prev != 0: after reading, resets dep_prev to the
+// ion background (it receives the next slice's deposit)
+template <typename T> void launch_src_bperp(const hq_grid_s* g, const void* dep_cur, void* dep_prev, void* chi_prev,
+                                            int reset_prev, cudaStream_t s);
 template <typename T> void launch_src_copy(const hq_grid_s* g, const void* src, int nrhs, cudaStream_t s);
+// finish_main also sets the B_perp guess 2 B(i-1) - B(i-2)
 template <typename T> void launch_finish_main(const hq_grid_s* g, const void* res, cudaStream_t s);
-template <typename T> void launch_finish_bperp(const hq_grid_s* g, const void* res, cudaStream_t s);
+// last != 0: also shift the B_perp history and clear the beam J_perp of slice i+1
+template <typename T> void launch_finish_bperp(const hq_grid_s* g, const void* res, int last, cudaStream_t s);
 template <typename T> void launch_bguess(const hq_grid_s* g, cudaStream_t s);
 template <typename T> void launch_bshift(const hq_grid_s* g, cudaStream_t s);
 template <typename T> void launch_store(const hq_grid_s* g, const hq_field_out* out, int64_t slot, const void* dep, const void* chi, cudaStream_t s);

@@ -68,24 +68,40 @@ __device__ __forceinline__ int stencil1(double x, double x0, double dx, double* 
   return shape_weights<P, double>(j, d, w);
 }
 
+// FP32 stencil of an FP64 position: node coordinate by multiplication (no FP64
+// division), fraction rounded to FP32.
+template <int P>
+__device__ __forceinline__ int stencil1(double x, double x0, double inv_dx, float* w) {
+  const double u = (x - x0) * inv_dx;
+  const double f = floor(u);
+  return shape_weights<P, float>((int)f, (float)(u - f), w);
+}
+
+template <int P, typename T>
+__device__ __forceinline__ int stencil_t(double x, double x0, double dx, double inv_dx, T* w) {
+  if constexpr (sizeof(T) == 8) return stencil1<P>(x, x0, dx, w);
+  else return stencil1<P>(x, x0, inv_dx, w);
+}
+
 // Charge/current of the particles of slice i into dep (rho, Jx, Jy, Jz) and J_perp of
-// slice i+1 into bjn: rho = q w S / (dx dy dzeta), J = rho u / gamma.
+// slice i+1 into bjn: rho = q w S / (dx dy dzeta), J = rho u / gamma (in the field type).
 template <int P, typename T>
 __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm,
                                int slice, int nz, Geom gm, V4<T>* dep, V2<T>* bjn) {
   const int a0 = off[slice], a1 = off[slice + 1];
   const int b0 = slice + 1 < nz ? off[slice + 1] : 0, b1 = slice + 1 < nz ? off[slice + 2] : 0;
   const int na = a1 - a0, nb = b1 - b0;
-  const double rq = v.charge / (gm.dx * gm.dy * gm.dzeta);
+  const T rq = T(v.charge / (gm.dx * gm.dy * gm.dzeta));
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < na + nb; t += gridDim.x * blockDim.x) {
     const bool cur = t < na;
     const int p = perm[cur ? a0 + t : b0 + (t - na)];
-    const double ux = v.ux[p], uy = v.uy[p], uz = v.uz[p];
-    const double ig = 1.0 / sqrt(1.0 + ux * ux + uy * uy + uz * uz);
-    const double r = rq * v.w[p];
-    double wx[P + 1], wy[P + 1];
-    const int ix0 = stencil1<P>(v.x[p], gm.xmin, gm.dx, wx);
-    const int iy0 = stencil1<P>(v.y[p], gm.ymin, gm.dy, wy);
+    const T ux = T(v.ux[p]), uy = T(v.uy[p]), uz = T(v.uz[p]);
+    const T ig = T(1) / sqrt(T(1) + ux * ux + uy * uy + uz * uz);
+    const T r = rq * T(v.w[p]);
+    T wx[P + 1], wy[P + 1];
+    const int ix0 = stencil_t<P, T>(v.x[p], gm.xmin, gm.dx, gm.inv_dx, wx);
+    const int iy0 = stencil_t<P, T>(v.y[p], gm.ymin, gm.dy, gm.inv_dy, wy);
+    const T cx = ux * ig, cy = uy * ig, cz = uz * ig;
 #pragma unroll
     for (int b = 0; b <= P; ++b) {
       const int iy = iy0 + b;
@@ -94,18 +110,18 @@ __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, 
       for (int a = 0; a <= P; ++a) {
         const int ix = ix0 + a;
         if (!in_interior(ix, gm.nx)) continue;
-        const double s = wx[a] * wy[b] * r;
+        const T s = wx[a] * wy[b] * r;
         const int64_t node = (int64_t)iy * gm.nx + ix;
         if (cur) {
           V4<T>* q = dep + node;
-          atomicAdd(&q->a, T(s));
-          atomicAdd(&q->b, T(s * ux * ig));
-          atomicAdd(&q->c, T(s * uy * ig));
-          atomicAdd(&q->d, T(s * uz * ig));
+          atomicAdd(&q->a, s);
+          atomicAdd(&q->b, s * cx);
+          atomicAdd(&q->c, s * cy);
+          atomicAdd(&q->d, s * cz);
         } else {
           V2<T>* q = bjn + node;
-          atomicAdd(&q->a, T(s * ux * ig));
-          atomicAdd(&q->b, T(s * uy * ig));
+          atomicAdd(&q->a, s * cx);
+          atomicAdd(&q->b, s * cy);
         }
       }
     }
@@ -180,7 +196,8 @@ __global__ void k_beam_push(hq_beam_view v, const int32_t* __restrict__ off, con
   }
 }
 
-// sums += (q w, q w Ez, q w Ez^2) over the particles of slice i.
+// sums += (q w, q w Ez, q w Ez^2) over the particles of slice i (Ez gathered in the
+// field type, sums in FP64).
 template <int P, typename T>
 __global__ void k_witness(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm, int slice,
                           Geom gm, const T* __restrict__ gf, double* sums) {
@@ -188,10 +205,10 @@ __global__ void k_witness(hq_beam_view v, const int32_t* __restrict__ off, const
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int t = a0 + blockIdx.x * blockDim.x + threadIdx.x; t < a1; t += gridDim.x * blockDim.x) {
     const int p = perm[t];
-    double wx[P + 1], wy[P + 1];
-    const int ix0 = stencil1<P>(v.x[p], gm.xmin, gm.dx, wx);
-    const int iy0 = stencil1<P>(v.y[p], gm.ymin, gm.dy, wy);
-    double ez = 0.0;
+    T wx[P + 1], wy[P + 1];
+    const int ix0 = stencil_t<P, T>(v.x[p], gm.xmin, gm.dx, gm.inv_dx, wx);
+    const int iy0 = stencil_t<P, T>(v.y[p], gm.ymin, gm.dy, gm.inv_dy, wy);
+    T ez = T(0);
 #pragma unroll
     for (int b = 0; b <= P; ++b) {
       const int iy = iy0 + b;
@@ -200,13 +217,14 @@ __global__ void k_witness(hq_beam_view v, const int32_t* __restrict__ off, const
       for (int a = 0; a <= P; ++a) {
         const int ix = ix0 + a;
         if (!in_interior(ix, gm.nx)) continue;
-        ez += wx[a] * wy[b] * (double)gf[((int64_t)iy * gm.nx + ix) * kGF + 2];
+        ez += wx[a] * wy[b] * gf[((int64_t)iy * gm.nx + ix) * kGF + 2];
       }
     }
     const double qw = v.charge * v.w[p];
+    const double e = (double)ez;
     s0 += qw;
-    s1 += qw * ez;
-    s2 += qw * ez * ez;
+    s1 += qw * e;
+    s2 += qw * e * e;
   }
   for (int o = 16; o > 0; o >>= 1) {
     s0 += __shfl_down_sync(0xffffffffu, s0, o);

@@ -31,17 +31,25 @@ namespace hq {
 struct TensorMaps {
   CUtensorMap a0_hi, a0_lo;   // op[0] as [kMaxRhs * nyp][nxp]
   CUtensorMap a1_hi, a1_lo;   // op[1] as [kMaxRhs * nxp][nyp]
-  CUtensorMap sx_hi, sx_lo;   // [nxp][nxp]
-  CUtensorMap sy_hi, sy_lo;   // [nyp][nyp]
+  CUtensorMap sx_hi[2], sx_lo[2];   // [nxp][nxp], boxes of 128 ([0]) or 64 ([1]) rows
+  CUtensorMap sy_hi[2], sy_lo[2];   // [nyp][nyp]
 };
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
-constexpr int TILE_BYTES = BM * BK * 2;            // 16 KB per bf16 box
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;        // A_hi, A_lo, B_hi, B_lo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr uint32_t TMEM_COLS = BN;
+constexpr int BM = 128, BK = 64;
+constexpr int A_BYTES = BM * BK * 2;               // 16 KB per bf16 A box
+// Tile shape per N-tile width: 128 (3 stages of 64 KB) or 64 (4 stages of 48 KB).
+template <int BN> struct Cfg {
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // A_hi, A_lo, B_hi, B_lo
+  static constexpr int STAGES = BN == 128 ? 3 : 4;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr uint32_t TMEM_COLS = BN;
+  // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M = BM, N = BN.
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
 
 struct Epi {
   int mode;          // 0: split + transposed bf16 store; 1: scale, split, store; 2: FP32 transposed store
@@ -108,15 +116,12 @@ __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr) {
   return d;
 }
 
-// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M = BM, N = BN.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -135,10 +140,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_dst_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo, int K, Epi ep,
                int* status) {
+  using C = Cfg<BN>;
+  constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES;
+  constexpr uint32_t TMEM_COLS = C::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -178,9 +187,9 @@ __global__ void __launch_bounds__(128, 1)
       const uint32_t fb = full0 + 8 * s;
       mbar_expect_tx(fb, STAGE_BYTES);
       tma_load_2d(st, &ta_hi, kb * BK, m0, fb);
-      tma_load_2d(st + TILE_BYTES, &ta_lo, kb * BK, m0, fb);
-      tma_load_2d(st + 2 * TILE_BYTES, &tb_hi, kb * BK, n0, fb);
-      tma_load_2d(st + 3 * TILE_BYTES, &tb_lo, kb * BK, n0, fb);
+      tma_load_2d(st + A_BYTES, &ta_lo, kb * BK, m0, fb);
+      tma_load_2d(st + 2 * A_BYTES, &tb_hi, kb * BK, n0, fb);
+      tma_load_2d(st + 2 * A_BYTES + C::B_BYTES, &tb_lo, kb * BK, n0, fb);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -189,14 +198,14 @@ __global__ void __launch_bounds__(128, 1)
       if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, status)) break;
       tc_fence_after();
       const uint32_t st = base + s * STAGE_BYTES;
-      const uint64_t ah = desc_k_sw128(st), al = desc_k_sw128(st + TILE_BYTES);
-      const uint64_t bh = desc_k_sw128(st + 2 * TILE_BYTES), bl = desc_k_sw128(st + 3 * TILE_BYTES);
+      const uint64_t ah = desc_k_sw128(st), al = desc_k_sw128(st + A_BYTES);
+      const uint64_t bh = desc_k_sw128(st + 2 * A_BYTES), bl = desc_k_sw128(st + 2 * A_BYTES + C::B_BYTES);
 #pragma unroll
       for (int k = 0; k < BK / 16; ++k) {
         const uint64_t off = (uint64_t)((k * 32) >> 4);  // 16 bf16 = 32 B along K inside the swizzle row
-        mma_bf16(tmem, ah + off, bh + off, (kb | k) != 0 ? 1u : 0u);
-        mma_bf16(tmem, ah + off, bl + off, 1u);
-        mma_bf16(tmem, al + off, bh + off, 1u);
+        mma_bf16(tmem, ah + off, bh + off, C::IDESC, (kb | k) != 0 ? 1u : 0u);
+        mma_bf16(tmem, ah + off, bl + off, C::IDESC, 1u);
+        mma_bf16(tmem, al + off, bh + off, C::IDESC, 1u);
       }
       mma_commit(empty0 + 8 * s);
     }
@@ -247,10 +256,11 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
                               const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int make_map(EncodeFn enc, CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols, std::string& err) {
+int make_map(EncodeFn enc, CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols, std::string& err,
+             uint32_t box_rows = 128) {
   cuuint64_t dims[2] = {cols, rows};
   cuuint64_t strides[1] = {cols * 2};
-  cuuint32_t box[2] = {BK, 128};
+  cuuint32_t box[2] = {BK, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult rc = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -261,10 +271,18 @@ int make_map(EncodeFn enc, CUtensorMap* map, void* ptr, uint64_t rows, uint64_t 
   return 0;
 }
 
-void gemm(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl, int M, int N, int K,
-          const Epi& ep, int* status, cudaStream_t s) {
-  dim3 grid((unsigned)(M / BM), (unsigned)(N / BN));
-  k_dst_gemm<<<grid, 128, SMEM_BYTES, s>>>(ah, al, bh, bl, K, ep, status);
+// N-tile width: 64 when 128-wide tiles would leave most of the 152 SMs idle.
+inline int pick_bn(int M, int N) { return (M / BM) * (N / 128) < 152 ? 64 : 128; }
+
+void gemm(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap* bh, const CUtensorMap* bl, int M, int N,
+          int K, const Epi& ep, int* status, cudaStream_t s) {
+  if (pick_bn(M, N) == 128) {
+    dim3 grid((unsigned)(M / BM), (unsigned)(N / 128));
+    k_dst_gemm<128><<<grid, 128, Cfg<128>::SMEM_BYTES, s>>>(ah, al, bh[0], bl[0], K, ep, status);
+  } else {
+    dim3 grid((unsigned)(M / BM), (unsigned)(N / 64));
+    k_dst_gemm<64><<<grid, 128, Cfg<64>::SMEM_BYTES, s>>>(ah, al, bh[1], bl[1], K, ep, status);
+  }
 }
 
 }  // namespace
@@ -278,7 +296,10 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
     return 1;
   }
   EncodeFn enc = reinterpret_cast<EncodeFn>(fn);
-  if (cudaFuncSetAttribute(k_dst_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_dst_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128>::SMEM_BYTES) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_dst_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<64>::SMEM_BYTES) !=
+          cudaSuccess) {
     err = "cannot raise the shared-memory limit of the DST GEMM";
     return 1;
   }
@@ -290,10 +311,13 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
   bad |= make_map(enc, &t.a0_lo, g->op_lo[0], kMaxRhs * nyp, nxp, err);
   bad |= make_map(enc, &t.a1_hi, g->op_hi[1], kMaxRhs * nxp, nyp, err);
   bad |= make_map(enc, &t.a1_lo, g->op_lo[1], kMaxRhs * nxp, nyp, err);
-  bad |= make_map(enc, &t.sx_hi, g->sx_hi, nxp, nxp, err);
-  bad |= make_map(enc, &t.sx_lo, g->sx_lo, nxp, nxp, err);
-  bad |= make_map(enc, &t.sy_hi, g->sy_hi, nyp, nyp, err);
-  bad |= make_map(enc, &t.sy_lo, g->sy_lo, nyp, nyp, err);
+  for (int i = 0; i < 2; ++i) {
+    const uint32_t rows = i == 0 ? 128 : 64;
+    bad |= make_map(enc, &t.sx_hi[i], g->sx_hi, nxp, nxp, err, rows);
+    bad |= make_map(enc, &t.sx_lo[i], g->sx_lo, nxp, nxp, err, rows);
+    bad |= make_map(enc, &t.sy_hi[i], g->sy_hi, nyp, nyp, err, rows);
+    bad |= make_map(enc, &t.sy_lo[i], g->sy_lo, nyp, nyp, err, rows);
+  }
   return bad;
 }
 

@@ -36,15 +36,15 @@ struct SinkBF16 {
 
 // Central difference helpers with wall nodes (index 0 and n) reading zero; the
 // result on wall rows/columns is zero (matching the field layout convention).
-template <typename A>
-__device__ __forceinline__ auto dxc(const A& f, int iy, int ix, int nx, double inv2dx) -> decltype(f(0, 0)) {
+template <typename A, typename C>
+__device__ __forceinline__ auto dxc(const A& f, int iy, int ix, int nx, C inv2dx) -> decltype(f(0, 0)) {
   using T = decltype(f(0, 0));
   const T r = ix + 1 < nx ? f(iy, ix + 1) : T(0);
   const T l = f(iy, ix - 1);
   return (r - l) * T(inv2dx);
 }
-template <typename A>
-__device__ __forceinline__ auto dyc(const A& f, int iy, int ix, int ny, double inv2dy) -> decltype(f(0, 0)) {
+template <typename A, typename C>
+__device__ __forceinline__ auto dyc(const A& f, int iy, int ix, int ny, C inv2dy) -> decltype(f(0, 0)) {
   using T = decltype(f(0, 0));
   const T u = iy + 1 < ny ? f(iy + 1, ix) : T(0);
   const T d = f(iy - 1, ix);
@@ -70,7 +70,7 @@ __global__ void k_src_main(const V4<T>* __restrict__ dep, Geom gm, Sink sink) {
   T s0 = T(0), s1 = T(0), s2 = T(0);
   if (ix > 0 && iy > 0) {
     const V4<T> c = dep[(int64_t)iy * nx + ix];
-    const double i2x = 0.5 / gm.dx, i2y = 0.5 / gm.dy;
+    const T i2x = T(gm.inv2dx), i2y = T(gm.inv2dy);
     s0 = -(c.a - c.d);
     s1 = dxc(jx, iy, ix, nx, i2x) + dyc(jy, iy, ix, gm.ny, i2y);
     s2 = dyc(jx, iy, ix, gm.ny, i2y) - dxc(jy, iy, ix, nx, i2x);
@@ -82,23 +82,32 @@ __global__ void k_src_main(const V4<T>* __restrict__ dep, Geom gm, Sink sink) {
 
 // Bx: -dy Jz + dzeta Jy;  By: dx Jz - dzeta Jx, with dzeta J = (J(i-1) - J(i+1)) / (2 dzeta)
 // and J(i+1) = trial plasma + beam of slice i+1 (Sec. 3.2 predictor-corrector).
+// The trial J_perp is cleared after reading (ready for the next trial pass); on the
+// last iteration the slice i-1 record is reset to the ion background, ready to
+// receive the deposit of slice i+1.
 template <typename T, typename Sink>
-__global__ void k_src_bperp(const V4<T>* __restrict__ cur, const V4<T>* __restrict__ prev,
-                            const V2<T>* __restrict__ tj, const V2<T>* __restrict__ bjn, Geom gm, Sink sink) {
+__global__ void k_src_bperp(const V4<T>* __restrict__ cur, V4<T>* prev, T* chi_prev, const T* __restrict__ rho_ion,
+                            V2<T>* tj, const V2<T>* __restrict__ bjn, Geom gm, Sink sink, int reset_prev) {
   const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
   if (ix >= gm.nx) return;
   const int nx = gm.nx;
+  const int64_t o = (int64_t)iy * nx + ix;
   auto jz = [&](int y, int x) { return cur[(int64_t)y * nx + x].d; };
+  const V4<T> pv = prev[o];
+  const V2<T> t = tj[o];
   T s0 = T(0), s1 = T(0);
   if (ix > 0 && iy > 0) {
-    const int64_t o = (int64_t)iy * nx + ix;
-    const T i2z = T(0.5 / gm.dzeta);
-    const V4<T> pv = prev[o];
-    const V2<T> t = tj[o], b = bjn[o];
+    const T i2z = T(gm.inv2dz);
+    const V2<T> b = bjn[o];
     const T dzjx = (pv.b - (t.a + b.a)) * i2z;
     const T dzjy = (pv.c - (t.b + b.b)) * i2z;
-    s0 = -dyc(jz, iy, ix, gm.ny, 0.5 / gm.dy) + dzjy;
-    s1 = dxc(jz, iy, ix, nx, 0.5 / gm.dx) - dzjx;
+    s0 = -dyc(jz, iy, ix, gm.ny, T(gm.inv2dy)) + dzjy;
+    s1 = dxc(jz, iy, ix, nx, T(gm.inv2dx)) - dzjx;
+  }
+  tj[o] = V2<T>{T(0), T(0)};
+  if (reset_prev) {
+    prev[o] = V4<T>{rho_ion[o], T(0), T(0), T(0)};
+    chi_prev[o] = T(0);
   }
   sink.put(0, iy, ix, s0);
   sink.put(1, iy, ix, s1);
@@ -114,9 +123,11 @@ __global__ void k_src_copy(const T* __restrict__ src, int nrhs, Geom gm, Sink si
   }
 }
 
-// psi -> psi array and gf[0..1] = -grad psi; Ez -> gf[2]; Bz -> gf[5].
+// psi -> psi array and gf[0..1] = -grad psi; Ez -> gf[2]; Bz -> gf[5]; gf[3..4] = the
+// predictor-corrector guess B(i) = 2 B(i-1) - B(i-2).
 template <typename T>
-__global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, Geom gm, int* status) {
+__global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, const V2<T>* __restrict__ b1,
+                              const V2<T>* __restrict__ b2, Geom gm, int* status) {
   const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
   if (ix >= gm.nx) return;
   const int nx = gm.nx;
@@ -125,29 +136,42 @@ __global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, Geom gm,
   auto ps = [&](int y, int x) { return res[(int64_t)y * nx + x]; };
   T ex = T(0), ey = T(0);
   if (ix > 0 && iy > 0) {
-    ex = -dxc(ps, iy, ix, nx, 0.5 / gm.dx);
-    ey = -dyc(ps, iy, ix, gm.ny, 0.5 / gm.dy);
+    ex = -dxc(ps, iy, ix, nx, T(gm.inv2dx));
+    ey = -dyc(ps, iy, ix, gm.ny, T(gm.inv2dy));
   }
   const T p = res[o], ez = res[nn + o], bz = res[2 * nn + o];
   if (!(isfinite(p) && isfinite(ez) && isfinite(bz))) atomicOr(status, DEV_NONFINITE);
   psi[o] = p;
+  const V2<T> p1 = b1[o], p2 = b2[o];
   T* q = gf + o * kGF;
   q[0] = ex;
   q[1] = ey;
   q[2] = ez;
+  q[3] = T(2) * p1.a - p2.a;
+  q[4] = T(2) * p1.b - p2.b;
   q[5] = bz;
 }
 
-// B <- w B_solved + (1 - w) B  (predictor-corrector mixing), into gf[3..4].
+// B <- w B_solved + (1 - w) B  (predictor-corrector mixing), into gf[3..4].  After the
+// last iteration also B(i-2) <- B(i-1), B(i-1) <- B and the beam J_perp of slice i+1 is
+// cleared for the next slice's beam deposit.
 template <typename T>
-__global__ void k_finish_bperp(const T* __restrict__ res, T* gf, int64_t nn, T w, int* status) {
+__global__ void k_finish_bperp(const T* __restrict__ res, T* gf, int64_t nn, T w, int* status, int last,
+                               V2<T>* b1, V2<T>* b2, V2<T>* bjn) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nn) return;
   const T bx = res[o], by = res[nn + o];
   if (!(isfinite(bx) && isfinite(by))) atomicOr(status, DEV_NONFINITE);
   T* q = gf + o * kGF;
-  q[3] = w * bx + (T(1) - w) * q[3];
-  q[4] = w * by + (T(1) - w) * q[4];
+  const T nbx = w * bx + (T(1) - w) * q[3];
+  const T nby = w * by + (T(1) - w) * q[4];
+  q[3] = nbx;
+  q[4] = nby;
+  if (last) {
+    b2[o] = b1[o];
+    b1[o] = V2<T>{nbx, nby};
+    bjn[o] = V2<T>{T(0), T(0)};
+  }
 }
 
 // Initial guess B(i) = 2 B(i-1) - B(i-2).
@@ -221,10 +245,11 @@ void launch_src_main(const hq_grid_s* g, const void* dep, cudaStream_t s) {
   k_src_main<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const V4<T>*>(dep), g->geom, SinkOf<T>::make(g));
 }
 template <typename T>
-void launch_src_bperp(const hq_grid_s* g, const void* cur, const void* prev, cudaStream_t s) {
-  k_src_bperp<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const V4<T>*>(cur), reinterpret_cast<const V4<T>*>(prev),
-                                          reinterpret_cast<const V2<T>*>(g->tj), reinterpret_cast<const V2<T>*>(g->bjn),
-                                          g->geom, SinkOf<T>::make(g));
+void launch_src_bperp(const hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int reset_prev, cudaStream_t s) {
+  k_src_bperp<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const V4<T>*>(cur), reinterpret_cast<V4<T>*>(prev),
+                                          reinterpret_cast<T*>(chi_prev), reinterpret_cast<const T*>(g->rho_ion),
+                                          reinterpret_cast<V2<T>*>(g->tj), reinterpret_cast<const V2<T>*>(g->bjn),
+                                          g->geom, SinkOf<T>::make(g), reset_prev);
 }
 template <typename T>
 void launch_src_copy(const hq_grid_s* g, const void* src, int nrhs, cudaStream_t s) {
@@ -233,12 +258,14 @@ void launch_src_copy(const hq_grid_s* g, const void* src, int nrhs, cudaStream_t
 template <typename T>
 void launch_finish_main(const hq_grid_s* g, const void* res, cudaStream_t s) {
   k_finish_main<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const T*>(res), reinterpret_cast<T*>(g->psi),
-                                            reinterpret_cast<T*>(g->gf), g->geom, g->d_status);
+                                            reinterpret_cast<T*>(g->gf), reinterpret_cast<const V2<T>*>(g->bprev1),
+                                            reinterpret_cast<const V2<T>*>(g->bprev2), g->geom, g->d_status);
 }
 template <typename T>
-void launch_finish_bperp(const hq_grid_s* g, const void* res, cudaStream_t s) {
-  k_finish_bperp<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(reinterpret_cast<const T*>(res), reinterpret_cast<T*>(g->gf),
-                                                            g->nnode, T(g->d.pc_mix), g->d_status);
+void launch_finish_bperp(const hq_grid_s* g, const void* res, int last, cudaStream_t s) {
+  k_finish_bperp<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(
+      reinterpret_cast<const T*>(res), reinterpret_cast<T*>(g->gf), g->nnode, T(g->d.pc_mix), g->d_status, last,
+      reinterpret_cast<V2<T>*>(g->bprev1), reinterpret_cast<V2<T>*>(g->bprev2), reinterpret_cast<V2<T>*>(g->bjn));
 }
 template <typename T>
 void launch_bguess(const hq_grid_s* g, cudaStream_t s) {
@@ -265,10 +292,10 @@ void launch_zero(void* p, int64_t n, cudaStream_t s) {
 #define HQ_INST(T)                                                                              \
   template void launch_reset_dep<T>(const hq_grid_s*, void*, void*, cudaStream_t);             \
   template void launch_src_main<T>(const hq_grid_s*, const void*, cudaStream_t);               \
-  template void launch_src_bperp<T>(const hq_grid_s*, const void*, const void*, cudaStream_t); \
+  template void launch_src_bperp<T>(const hq_grid_s*, const void*, void*, void*, int, cudaStream_t); \
   template void launch_src_copy<T>(const hq_grid_s*, const void*, int, cudaStream_t);          \
   template void launch_finish_main<T>(const hq_grid_s*, const void*, cudaStream_t);            \
-  template void launch_finish_bperp<T>(const hq_grid_s*, const void*, cudaStream_t);           \
+  template void launch_finish_bperp<T>(const hq_grid_s*, const void*, int, cudaStream_t);      \
   template void launch_bguess<T>(const hq_grid_s*, cudaStream_t);                              \
   template void launch_bshift<T>(const hq_grid_s*, cudaStream_t);                              \
   template void launch_store<T>(const hq_grid_s*, const hq_field_out*, int64_t, const void*, const void*, cudaStream_t); \

@@ -22,7 +22,8 @@ STATUS = {0: "HQ_OK", 1: "HQ_ERR_ARG", 2: "HQ_ERR_CUDA", 3: "HQ_ERR_OOM", 4: "HQ
 FIELDS = ("rho", "jx", "jy", "jz", "chi", "psi", "exmby", "eypbx", "ez", "bx", "by", "bz")
 EXPORTS = ("hq_grid_create", "hq_grid_destroy", "hq_advance_slice", "hq_beam_deposit", "hq_solve_fields",
            "hq_store_fields", "hq_push_beams", "hq_witness_accumulate", "hq_sweep_step", "hq_poisson_solve",
-           "hq_plasma_state", "hq_sync", "hq_last_error")
+           "hq_plasma_state", "hq_profile_enable", "hq_profile_read", "hq_sync", "hq_last_error")
+KERNEL_CLASSES = ("final", "trial", "dst", "field", "beam", "other")
 
 
 class GridDesc(C.Structure):
@@ -42,6 +43,10 @@ class BeamView(C.Structure):
 
 class FieldOut(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in FIELDS]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_int64 * 8)]
 
 
 class PlasmaView(C.Structure):
@@ -72,6 +77,8 @@ def load() -> C.CDLL:
             "hq_sweep_step": (P, C.POINTER(BeamView), I32, D, C.POINTER(FieldOut), I32, P),
             "hq_poisson_solve": (P, P, P, I32),
             "hq_plasma_state": (P, C.POINTER(PlasmaView)),
+            "hq_profile_enable": (P, I32),
+            "hq_profile_read": (P, C.POINTER(Profile)),
             "hq_sync": (P, C.POINTER(I64)),
         }
         for name, args in sig.items():
@@ -234,6 +241,16 @@ class Grid:
         for k, ts in (("x", "<f8"), ("y", "<f8"), ("psi", "<f8"), ("ux", ft), ("uy", ft), ("w", ft), ("alive", "|u1")):
             out[k] = torch.as_tensor(_CudaArray(getattr(v, k), n, ts), device="cuda").clone()
         return out
+
+    def profile(self, on: bool) -> None:
+        """Start (on=True) or stop per-kernel-class CUDA-event timing; resets the counters."""
+        _check(load().hq_profile_enable(self.h, 1 if on else 0), self.h)
+
+    def profile_read(self) -> dict:
+        """{class: (ms, launches)} accumulated since the last profile() call."""
+        pr = Profile()
+        _check(load().hq_profile_read(self.h, C.byref(pr)), self.h)
+        return {k: (float(pr.ms[i]), int(pr.launches[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def sync(self) -> int:
         rm = C.c_int64()

@@ -156,3 +156,16 @@ def test_beam_binning_brute_force():
         members = sorted(order[off[i]:off[i + 1]].tolist())
         assert members == sorted(np.nonzero(ref == i)[0].tolist())
     assert int(off[-1]) == int((ref >= 0).sum())
+
+
+def test_plasma_permutation_only_reorders_sums():
+    """The plasma_perm option changes the summation order, not the arithmetic."""
+    g = linear_grid(nx=24, nz=16, order=2)
+    sp = O.GridSpec(**g)
+    beam = O.as_beam(I.fixed_ppc_beam(g, 0.8, 1.0, 0.3))
+    a = O.sweep(sp, [beam], record=("ez", "bx"))
+    perm = torch.as_tensor(np.random.default_rng(3).permutation(sp.nx * sp.ny))
+    b = O.sweep(sp, [beam], record=("ez", "bx"), plasma_perm=perm)
+    for k in ("ez", "bx"):
+        assert float((a.fields[k] - b.fields[k]).abs().max()) <= 1e-9 * float(a.fields[k].abs().max())
+    assert torch.allclose(a.plasma["x"], b.plasma["x"], rtol=0, atol=1e-12)
