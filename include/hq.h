@@ -159,6 +159,33 @@ hq_status hq_sweep_step(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, dou
  * nrhs x ny x nx field-type values (row/col 0 of src are ignored). */
 hq_status hq_poisson_solve(hq_grid_t grid, const void* src, void* dst, int32_t nrhs);
 
+/* Allocation-free Dirichlet Poisson solve.  The paper has no counterpart: this is
+ * an addition for callers that cannot allocate device memory.  Such callers
+ * exist: a host application that reserved the whole device memory pool up front
+ * and lets no library allocate from it, code in a latency-critical loop where a
+ * cudaMalloc or cudaFree would stall or synchronize the device, and code that is
+ * not allowed to create device objects after start-up.  This entry point solves
+ * the same problem as hq_poisson_solve on an FP32 (bf16x3 tensor-core DST-I) grid
+ * but needs no grid object and allocates nothing: its scratch is one fixed,
+ * file-scope static device array of 9 MiB + 256 bytes, which every GPU that loads
+ * libhq holds until the process exits.
+ *
+ * src, dst: DEVICE float arrays of nrhs x ny x nx, row-major, row = y (row and
+ * column 0 of src are ignored; dst has zeros there).  dx, dy: node spacings.
+ * Limits set by the static array: 8 <= nx, ny <= 512 and 1 <= nrhs <= 3; anything
+ * larger returns HQ_ERR_ARG with a message naming the limit.
+ * cuda_stream: the cudaStream_t the work is queued on (NULL = legacy stream).
+ * The first call on each device does that device's set-up (it looks up the static
+ * array's device address and raises the GEMM's shared-memory limit); make that
+ * first call before any stream capture.  A call with a new (nx, ny, dx, dy)
+ * rebuilds the sine and 1/lambda tables inside the array.  Every call shares the
+ * one array, which keeps the last call's contents: calls whose work overlaps on
+ * the GPU (several streams, several host threads) race, so the caller must
+ * serialize them.  Errors: HQ_ERR_ARG, HQ_ERR_CUDA, HQ_ERR_UNSUPPORTED (not an
+ * sm_103a device); the message is read with hq_last_error(NULL). */
+hq_status hq_poisson_solve_static(const float* src, float* dst, int32_t nx, int32_t ny, double dx, double dy,
+                                  int32_t nrhs, void* cuda_stream);
+
 /* Fills *out with views of the plasma slice (state after the last advance). */
 hq_status hq_plasma_state(hq_grid_t grid, hq_plasma_view* out);
 

@@ -233,6 +233,11 @@ hq_status check_launch(hq_grid_s* g) {
 
 }  // namespace
 
+namespace hq {
+// Error message for calls that have no grid (read back by hq_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_global_err = msg; }
+}  // namespace hq
+
 extern "C" {
 
 hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t* out) {

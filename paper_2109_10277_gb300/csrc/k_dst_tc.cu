@@ -346,3 +346,190 @@ void dst_solve_tc(hq_grid_s* g, int R, cudaStream_t s) {
 }
 
 }  // namespace hq
+
+// ---------------------------------------------------------------- allocation-free variant
+// hq_poisson_solve_static: the same tensor-core Dirichlet solve for callers that
+// cannot allocate device memory (all scratch in one file-scope static array).
+#include <map>
+#include <mutex>
+
+namespace hq {
+void set_global_error(const std::string& msg);  // defined in hq_api.cu
+
+namespace {
+
+constexpr int kStaticMaxN = 512;   // nx, ny <= 512 (so the padded extents are <= 512)
+constexpr int kStaticMaxRhs = 3;
+constexpr size_t kStaticOpBytes = (size_t)kStaticMaxRhs * kStaticMaxN * kStaticMaxN * 2;  // one bf16 operand buffer
+constexpr size_t kStaticSBytes = (size_t)kStaticMaxN * kStaticMaxN * 2;                    // one bf16 sine matrix
+constexpr size_t kStaticScaleBytes = (size_t)kStaticMaxN * kStaticMaxN * 4;                // FP32 1/lambda table
+// layout: status word (256 B) | op_hi0 op_lo0 op_hi1 op_lo1 | sx_hi sx_lo sy_hi sy_lo | scale  (9 MiB + 256 B)
+constexpr size_t kStaticBytes = 256 + 4 * kStaticOpBytes + 4 * kStaticSBytes + kStaticScaleBytes;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+struct StaticDev {
+  uint8_t* base = nullptr;   // device address of g_static_scratch on this device
+  int nx = 0, ny = 0;
+  double dx = 0.0, dy = 0.0;
+  TensorMaps maps;
+};
+std::mutex g_static_mu;
+std::map<int, StaticDev> g_static_dev;
+
+// S_x, S_y (bf16 hi/lo, zero-padded) and the scale (4/(nx ny))/lambda for one grid.
+__global__ void k_static_tables(__nv_bfloat16* sxh, __nv_bfloat16* sxl, __nv_bfloat16* syh, __nv_bfloat16* syl,
+                                float* scale, int nx, int ny, int nxp, int nyp, double dx, double dy) {
+  const int64_t tot = (int64_t)kStaticMaxN * kStaticMaxN;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / kStaticMaxN), c = (int)(t % kStaticMaxN);
+    if (r < nxp && c < nxp) {
+      const float v = (r < nx && c < nx) ? (float)sinpi((double)(((int64_t)r * c) % (2 * nx)) / nx) : 0.0f;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      sxh[(int64_t)r * nxp + c] = h;
+      sxl[(int64_t)r * nxp + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+    if (r < nyp && c < nyp) {
+      const float v = (r < ny && c < ny) ? (float)sinpi((double)(((int64_t)r * c) % (2 * ny)) / ny) : 0.0f;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      syh[(int64_t)r * nyp + c] = h;
+      syl[(int64_t)r * nyp + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+    if (r < nyp && c < nxp) {
+      float s = 0.0f;
+      if (r >= 1 && r < ny && c >= 1 && c < nx) {
+        const double sx = sinpi(c / (2.0 * nx)), sy = sinpi(r / (2.0 * ny));
+        const double lam = -(4.0 / (dx * dx)) * sx * sx - (4.0 / (dy * dy)) * sy * sy;
+        s = (float)((4.0 / ((double)nx * ny)) / lam);
+      }
+      scale[(int64_t)r * nxp + c] = s;
+    }
+  }
+}
+
+// Sources into the zero-padded split operand layout [R][nyp][nxp]; every padded entry
+// is written, so nothing left over from an earlier call of another size survives.
+__global__ void k_static_src(const float* __restrict__ src, __nv_bfloat16* hi, __nv_bfloat16* lo, int R, int nx, int ny,
+                             int nxp, int nyp) {
+  const int64_t tot = (int64_t)R * nyp * nxp;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(t % nxp);
+    const int64_t ry = t / nxp;
+    const int iy = (int)(ry % nyp), r = (int)(ry / nyp);
+    const float v = (ix >= 1 && ix < nx && iy >= 1 && iy < ny) ? src[((int64_t)r * ny + iy) * nx + ix] : 0.0f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[t] = h;
+    lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+EncodeFn static_encoder(std::string& err) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      fn == nullptr || q != cudaDriverEntryPointSuccess) {
+    err = "cuTensorMapEncodeTiled not available from the driver";
+    return nullptr;
+  }
+  return reinterpret_cast<EncodeFn>(fn);
+}
+
+hq_status static_fail(hq_status st, const std::string& msg) {
+  set_global_error(msg);
+  return st;
+}
+
+}  // namespace
+}  // namespace hq
+
+using namespace hq;
+
+extern "C" hq_status hq_poisson_solve_static(const float* src, float* dst, int32_t nx, int32_t ny, double dx, double dy,
+                                             int32_t nrhs, void* cuda_stream) {
+  if (!src || !dst) return static_fail(HQ_ERR_ARG, "hq_poisson_solve_static: src and dst must not be NULL");
+  if (nx < 8 || ny < 8 || nx > kStaticMaxN || ny > kStaticMaxN)
+    return static_fail(HQ_ERR_ARG, "hq_poisson_solve_static: nx and ny must be in 8..512 (static scratch limit)");
+  if (nrhs < 1 || nrhs > kStaticMaxRhs)
+    return static_fail(HQ_ERR_ARG, "hq_poisson_solve_static: nrhs must be in 1..3 (static scratch limit)");
+  if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
+    return static_fail(HQ_ERR_ARG, "hq_poisson_solve_static: dx and dy must be finite and positive");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return static_fail(HQ_ERR_CUDA, "hq_poisson_solve_static: no CUDA device");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  StaticDev& sd = g_static_dev[dev];
+  std::string err;
+  if (!sd.base) {
+    // once per device: resolve the static array's device address (the host-side symbol is
+    // only a stand-in) and allow the GEMM's shared-memory footprint
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess || prop.major != 10 || prop.minor != 3)
+      return static_fail(HQ_ERR_UNSUPPORTED, "hq_poisson_solve_static: needs an sm_103a (GB300) device");
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return static_fail(HQ_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+    if (cudaFuncSetAttribute(k_dst_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128>::SMEM_BYTES) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_dst_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<64>::SMEM_BYTES) !=
+            cudaSuccess)
+      return static_fail(HQ_ERR_CUDA, "hq_poisson_solve_static: cannot raise the GEMM shared-memory limit");
+    sd.base = static_cast<uint8_t*>(p);
+  }
+  uint8_t* b = sd.base;
+  int* status = reinterpret_cast<int*>(b);
+  __nv_bfloat16* op_hi0 = reinterpret_cast<__nv_bfloat16*>(b + 256);
+  __nv_bfloat16* op_lo0 = reinterpret_cast<__nv_bfloat16*>(b + 256 + kStaticOpBytes);
+  __nv_bfloat16* op_hi1 = reinterpret_cast<__nv_bfloat16*>(b + 256 + 2 * kStaticOpBytes);
+  __nv_bfloat16* op_lo1 = reinterpret_cast<__nv_bfloat16*>(b + 256 + 3 * kStaticOpBytes);
+  uint8_t* sb = b + 256 + 4 * kStaticOpBytes;
+  __nv_bfloat16* sxh = reinterpret_cast<__nv_bfloat16*>(sb);
+  __nv_bfloat16* sxl = reinterpret_cast<__nv_bfloat16*>(sb + kStaticSBytes);
+  __nv_bfloat16* syh = reinterpret_cast<__nv_bfloat16*>(sb + 2 * kStaticSBytes);
+  __nv_bfloat16* syl = reinterpret_cast<__nv_bfloat16*>(sb + 3 * kStaticSBytes);
+  float* scale = reinterpret_cast<float*>(sb + 4 * kStaticSBytes);
+  const int nxp = (nx + 127) / 128 * 128, nyp = (ny + 127) / 128 * 128;
+  if (sd.nx != nx || sd.ny != ny || sd.dx != dx || sd.dy != dy) {
+    // new geometry: rebuild the sine matrices and 1/lambda table in the static array and
+    // re-encode the tensor maps over the new padded extents (host-side, no allocation)
+    EncodeFn enc = static_encoder(err);
+    if (!enc) return static_fail(HQ_ERR_CUDA, err);
+    TensorMaps& t = sd.maps;
+    int bad = 0;
+    bad |= make_map(enc, &t.a0_hi, op_hi0, (uint64_t)kStaticMaxRhs * nyp, nxp, err);
+    bad |= make_map(enc, &t.a0_lo, op_lo0, (uint64_t)kStaticMaxRhs * nyp, nxp, err);
+    bad |= make_map(enc, &t.a1_hi, op_hi1, (uint64_t)kStaticMaxRhs * nxp, nyp, err);
+    bad |= make_map(enc, &t.a1_lo, op_lo1, (uint64_t)kStaticMaxRhs * nxp, nyp, err);
+    for (int i = 0; i < 2; ++i) {
+      const uint32_t rows = i == 0 ? 128 : 64;
+      bad |= make_map(enc, &t.sx_hi[i], sxh, nxp, nxp, err, rows);
+      bad |= make_map(enc, &t.sx_lo[i], sxl, nxp, nxp, err, rows);
+      bad |= make_map(enc, &t.sy_hi[i], syh, nyp, nyp, err, rows);
+      bad |= make_map(enc, &t.sy_lo[i], syl, nyp, nyp, err, rows);
+    }
+    if (bad) {
+      sd.nx = sd.ny = 0;
+      return static_fail(HQ_ERR_CUDA, err);
+    }
+    k_static_tables<<<256, 256, 0, s>>>(sxh, sxl, syh, syl, scale, nx, ny, nxp, nyp, dx, dy);
+    sd.nx = nx;
+    sd.ny = ny;
+    sd.dx = dx;
+    sd.dy = dy;
+  }
+  const TensorMaps& t = sd.maps;
+  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess)
+    return static_fail(HQ_ERR_CUDA, "hq_poisson_solve_static: status reset failed");
+  k_static_src<<<256, 256, 0, s>>>(src, op_hi0, op_lo0, nrhs, nx, ny, nxp, nyp);
+  Epi e{};
+  e = Epi{0, nyp, nxp, op_hi1, op_lo1, nullptr, nullptr, 0, 0};
+  gemm(t.a0_hi, t.a0_lo, t.sx_hi, t.sx_lo, nrhs * nyp, nxp, nxp, e, status, s);
+  e = Epi{1, nxp, nyp, op_hi0, op_lo0, scale, nullptr, 0, 0};
+  gemm(t.a1_hi, t.a1_lo, t.sy_hi, t.sy_lo, nrhs * nxp, nyp, nyp, e, status, s);
+  e = Epi{0, nyp, nxp, op_hi1, op_lo1, nullptr, nullptr, 0, 0};
+  gemm(t.a0_hi, t.a0_lo, t.sx_hi, t.sx_lo, nrhs * nyp, nxp, nxp, e, status, s);
+  e = Epi{2, nxp, nyp, nullptr, nullptr, nullptr, dst, nx, ny};
+  gemm(t.a1_hi, t.a1_lo, t.sy_hi, t.sy_lo, nrhs * nxp, nyp, nyp, e, status, s);
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) return static_fail(HQ_ERR_CUDA, std::string("hq_poisson_solve_static: ") + cudaGetErrorString(le));
+  return HQ_OK;
+}

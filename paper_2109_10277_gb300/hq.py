@@ -22,7 +22,8 @@ STATUS = {0: "HQ_OK", 1: "HQ_ERR_ARG", 2: "HQ_ERR_CUDA", 3: "HQ_ERR_OOM", 4: "HQ
 FIELDS = ("rho", "jx", "jy", "jz", "chi", "psi", "exmby", "eypbx", "ez", "bx", "by", "bz")
 EXPORTS = ("hq_grid_create", "hq_grid_destroy", "hq_advance_slice", "hq_beam_deposit", "hq_solve_fields",
            "hq_store_fields", "hq_push_beams", "hq_witness_accumulate", "hq_sweep_step", "hq_poisson_solve",
-           "hq_plasma_state", "hq_profile_enable", "hq_profile_read", "hq_sync", "hq_last_error")
+           "hq_plasma_state", "hq_profile_enable", "hq_profile_read", "hq_sync", "hq_last_error",
+           "hq_poisson_solve_static")
 KERNEL_CLASSES = ("final", "trial", "dst", "field", "beam", "other")
 
 
@@ -80,6 +81,7 @@ def load() -> C.CDLL:
             "hq_profile_enable": (P, I32),
             "hq_profile_read": (P, C.POINTER(Profile)),
             "hq_sync": (P, C.POINTER(I64)),
+            "hq_poisson_solve_static": (P, P, I32, I32, D, D, I32, P),
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
