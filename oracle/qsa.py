@@ -191,10 +191,14 @@ def _stencil(spec: GridSpec, x: torch.Tensor, y: torch.Tensor, order: int):
             yield idx, torch.where(valid, wx[a] * wy[b], torch.zeros_like(wx[a]))
 
 
-def deposit(spec: GridSpec, x, y, values: Sequence[torch.Tensor], order: int):
-    """Scatter per-particle `values` onto the node grid with shape `order`."""
+def deposit(spec: GridSpec, x, y, values: Sequence[torch.Tensor], order: int, reverse: bool = False):
+    """Scatter per-particle `values` onto the node grid with shape `order`.
+
+    reverse=True visits the stencil offsets in the opposite order (the same sums,
+    added in another order)."""
     outs = [torch.zeros(spec.ny * spec.nx, dtype=DT) for _ in values]
-    for idx, wgt in _stencil(spec, x, y, order):
+    stencil = list(_stencil(spec, x, y, order))
+    for idx, wgt in (stencil[::-1] if reverse else stencil):
         outs = [o.index_add(0, idx, wgt * v) for o, v in zip(outs, values)]
     return [o.reshape(spec.ny, spec.nx) for o in outs]
 
@@ -317,10 +321,10 @@ def plasma_deposit_jperp(spec: GridSpec, x, y, ux, uy, psi, w, ok, q=PLASMA_Q):
                    spec.shape_order)
 
 
-def ion_background(spec: GridSpec, st0, q=PLASMA_Q):
+def ion_background(spec: GridSpec, st0, q=PLASMA_Q, reverse: bool = False):
     """Immobile ions: minus the initial electron charge density, deposited with the same shape."""
     A = spec.dx * spec.dy
-    (rho_e,) = deposit(spec, st0["x"], st0["y"], [q * st0["w"] / A], spec.shape_order)
+    (rho_e,) = deposit(spec, st0["x"], st0["y"], [q * st0["w"] / A], spec.shape_order, reverse)
     return -rho_e
 
 
@@ -419,7 +423,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
           n_slices: Optional[int] = None, record: Sequence[str] = FIELD_NAMES,
           witness: Sequence[int] = (), record_plasma_at: Sequence[int] = (),
           n0_scale: Optional[torch.Tensor] = None, radial_profile: Optional[torch.Tensor] = None,
-          plasma_perm: Optional[torch.Tensor] = None) -> SweepResult:
+          plasma_perm: Optional[torch.Tensor] = None, reverse_ion_order: bool = False) -> SweepResult:
     """One quasi-static sweep head -> tail (Sec. 2), slices i = 0 .. n_slices-1.
 
     Per slice (Sec. 2 steps 1-7 and the Sec. 3.2 predictor-corrector):
@@ -428,6 +432,8 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     dt != 0 also advances every beam particle once with its own slice's fields.
     plasma_perm (a permutation of the plasma particles) changes only the order in
     which particle contributions are summed; results are returned in the original order.
+    reverse_ion_order sums the ion background in the opposite stencil order, so its
+    rounding no longer cancels the electrons' exactly (again the same arithmetic).
     """
     ns = spec.nzeta if n_slices is None else n_slices
     dz = spec.dzeta
@@ -435,7 +441,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     st = plasma_init(spec, n0_scale, radial_profile)
     if plasma_perm is not None:
         st = {k: v[plasma_perm] for k, v in st.items()}
-    rho_ion = ion_background(spec, st)
+    rho_ion = ion_background(spec, st, reverse=reverse_ion_order)
     zero = torch.zeros(spec.ny, spec.nx, dtype=DT)
     hist = [(torch.zeros_like(st["x"]),) * 5 for _ in range(4)]  # f_{i-1} .. f_{i-4}
     beams = [dict(b) for b in beams]

@@ -91,13 +91,15 @@ __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, 
   const int a0 = off[slice], a1 = off[slice + 1];
   const int b0 = slice + 1 < nz ? off[slice + 1] : 0, b1 = slice + 1 < nz ? off[slice + 2] : 0;
   const int na = a1 - a0, nb = b1 - b0;
-  const T rq = T(v.charge / (gm.dx * gm.dy * gm.dzeta));
+  const double vol = gm.dx * gm.dy * gm.dzeta;
+  const T rq = T(v.charge / vol);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < na + nb; t += gridDim.x * blockDim.x) {
     const bool cur = t < na;
     const int p = perm[cur ? a0 + t : b0 + (t - na)];
     const T ux = T(v.ux[p]), uy = T(v.uy[p]), uz = T(v.uz[p]);
     const T ig = T(1) / sqrt(T(1) + ux * ux + uy * uy + uz * uz);
-    const T r = rq * T(v.w[p]);
+    // FP64: (q w) / (dx dy dzeta) as in the oracle; FP32: precomputed q / volume
+    const T r = sizeof(T) == 8 ? T((v.charge * v.w[p]) / vol) : rq * T(v.w[p]);
     T wx[P + 1], wy[P + 1];
     const int ix0 = stencil_t<P, T>(v.x[p], gm.xmin, gm.dx, gm.inv_dx, wx);
     const int iy0 = stencil_t<P, T>(v.y[p], gm.ymin, gm.dy, gm.inv_dy, wy);

@@ -150,6 +150,14 @@ __device__ __forceinline__ void stencil_f64(const Geom& gm, double x, double y, 
   iy0 = shape_weights<P, T>(jy, T(fy), wy);
 }
 
+// q w / A for an electron (q = -1).  FP64 mode divides by A = dx dy as the oracle
+// does; FP32 mode multiplies by the precomputed 1/A.
+template <typename T>
+__device__ __forceinline__ T charge_density(T w, const Geom& gm) {
+  if constexpr (sizeof(T) == 8) return (T(-1.0) * w) / (gm.dx * gm.dy);
+  else return T(-1.0) * w * T(gm.inv_area);
+}
+
 // Removal rule (a reading; the paper is silent): finite, inside the open box,
 // 1 + Psi >= psi_guard.
 __device__ __forceinline__ bool state_ok(const Geom& gm, double x, double y, double opp, double guard) {
@@ -211,7 +219,7 @@ __global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* 
   T wx[P + 1], wy[P + 1];
   int ix0, iy0;
   stencil_f64<P, T>(gm, pl.x[p], pl.y[p], ix0, iy0, wx, wy);
-  const T qw = T(-1.0) * pl.w[p] * T(gm.inv_area);
+  const T qw = charge_density<T>(pl.w[p], gm);
   if (rho_ion) {
 #pragma unroll
     for (int b = 0; b <= P; ++b) {
@@ -229,9 +237,8 @@ __global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* 
   const T ux = pl.ux[p], uy = pl.uy[p];
   const T opp = T(1.0 + pl.psi[p]);
   const T g = T(1) / opp;
-  const T u2 = ux * ux + uy * uy;
-  const T gam = (T(1) + u2 + opp * opp) * T(0.5) * g;
-  const T uz = (T(1) + u2 - opp * opp) * T(0.5) * g;
+  const T gam = (T(1) + ux * ux + uy * uy + opp * opp) * T(0.5) * g;
+  const T uz = (T(1) + ux * ux + uy * uy - opp * opp) * T(0.5) * g;
   deposit_full<P, T>(dep, chi, gm.nx, gm.ny, ix0, iy0, wx, wy, qw * gam * g, qw * ux * g, qw * uy * g,
                      qw * uz * g, qw * T(-1) * g);
 }
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
     topp = T(1.0 + tpsi);
     stencil_f64<P, T>(gm, tx, ty, tix0, tiy0, twx, twy);
   }
-  const T qw = T(-1.0) * pl.w[p] * T(gm.inv_area);
+  const T qw = charge_density<T>(pl.w[p], gm);
   const T tg = T(1) / topp;
   deposit_perp<P, T>(tj, gm.nx, gm.ny, tix0, tiy0, twx, twy, qw * tux * tg, qw * tuy * tg);
 }
@@ -370,11 +377,10 @@ __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, 
     topp = T(nopp);
     stencil_f64<P, T>(gm, nxp, nyp, ix0, iy0, wx, wy);
   }
-  const T qw = T(-1.0) * pl.w[p] * T(gm.inv_area);
+  const T qw = charge_density<T>(pl.w[p], gm);
   const T g = T(1) / topp;
-  const T u2 = nux * nux + nuy * nuy;
-  const T gam = (T(1) + u2 + topp * topp) * T(0.5) * g;
-  const T uz = (T(1) + u2 - topp * topp) * T(0.5) * g;
+  const T gam = (T(1) + nux * nux + nuy * nuy + topp * topp) * T(0.5) * g;
+  const T uz = (T(1) + nux * nux + nuy * nuy - topp * topp) * T(0.5) * g;
   deposit_full<P, T>(dep, chi, gm.nx, gm.ny, ix0, iy0, wx, wy, qw * gam * g, qw * nux * g, qw * nuy * g,
                      qw * uz * g, qw * T(-1) * g);
 }
