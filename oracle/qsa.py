@@ -488,8 +488,8 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
             bys = poisson_solve(spec, sby0 - dzjx)
             nbx = spec.pc_mix * bxs + (1.0 - spec.pc_mix) * bx
             nby = spec.pc_mix * bys + (1.0 - spec.pc_mix) * by
-            num = torch.sqrt(((nbx - bx) ** 2).sum() + ((nby - by) ** 2).sum())
-            den = torch.sqrt((nbx ** 2).sum() + (nby ** 2).sum())
+            num = torch.sqrt(((nbx - bx) ** 2).sum() + ((nby - by) ** 2).sum()).detach()
+            den = torch.sqrt((nbx ** 2).sum() + (nby ** 2).sum()).detach()
             resid = float(num / den) if float(den) > 0 else 0.0
             bx, by = nbx, nby
         res.pc_residual.append(resid)
@@ -530,3 +530,14 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     res.beams = beams
     res.witness = {bi: tuple(v) for bi, v in wit.items()}
     return res
+
+
+def witness_loss(res: SweepResult, beam: int, kind: str = "mean"):
+    """Loss of the gradient workloads from the witness sums (S0, S1, S2) = sum(q w (1, Ez, Ez^2)):
+    "mean": charge-weighted mean Ez, S1/S0; "mean+rms": that plus the charge-weighted RMS spread
+    sqrt(S2/S0 - (S1/S0)^2)."""
+    s0, s1, s2 = res.witness[beam]
+    mean = s1 / s0
+    if kind == "mean":
+        return mean
+    return mean + torch.sqrt(torch.clamp(s2 / s0 - mean * mean, min=0.0))
