@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison sweep")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-slices", type=int, default=12, help="oracle sample: slices of the workload")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--case", choices=("sweep", "poisson"), default="sweep",
                     help="poisson: only repeated 3-RHS Dirichlet solves on the workload grid (for ncu captures)")
     return ap.parse_args()
@@ -186,6 +187,51 @@ def dst_flops_per_sweep(g: dict) -> float:
     return 3.0 * per_rhs * rhs_per_slice * g["nzeta"]
 
 
+def adjoint_leg(hq, I, stream, flush, name="adjoint256", ckpt_every=32):
+    """Adjoint/forward time on the 256^2 x 512 gradient workload (FP32/bf16x3, fixed-ppc driver
+    and witness, loss = charge-weighted mean Ez of the witness, checkpoint every 32 slices)."""
+    import torch
+    g = I.grid_params(name)
+    beams = [hq.Beam(b) for b in I.workload_beams(name)]
+    free0 = torch.cuda.mem_get_info()[0]
+    grid = hq.Grid(g, precision="fp32", stream=stream)
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for _ in range(2):  # warm-up: forward, checkpointed forward + adjoint
+        sums.zero_()
+        grid.sweep(beams, witness=1, witness_sums=sums)
+        sums.zero_()
+        grid.forward_ckpt(beams, 1, sums, ckpt_every)
+        grid.adjoint(beams, 1, hq.witness_loss_grad("mean", *[float(v) for v in sums.cpu()])[1])
+    grid.sync()
+    a, b, c, d, e = ev(), ev(), ev(), ev(), ev()
+    flush.fill_(3)
+    sums.zero_()
+    a.record(stream)
+    grid.sweep(beams, witness=1, witness_sums=sums)
+    b.record(stream)
+    flush.fill_(4)
+    sums.zero_()
+    c.record(stream)
+    grid.forward_ckpt(beams, 1, sums, ckpt_every)
+    d.record(stream)
+    s = [float(v) for v in sums.cpu()]
+    loss, dls = hq.witness_loss_grad("mean", *s)
+    c2 = ev()
+    c2.record(stream)
+    grid.adjoint(beams, 1, dls)
+    e.record(stream)
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    grid.close()
+    fwd, ck, adj = a.elapsed_time(b), c.elapsed_time(d), c2.elapsed_time(e)
+    return {"workload": f"{name}: 256x256 x 512 slices, 1 ppc, linear shape, fixed-ppc driver (n_b=2) and witness, "
+                        f"loss = mean witness Ez, FP32/bf16x3, checkpoint every {ckpt_every}",
+            "forward_ms": fwd, "forward_ckpt_ms": ck, "adjoint_ms": adj, "adjoint_over_forward": adj / fwd,
+            "ckpt_forward_plus_adjoint_over_forward": (ck + adj) / fwd, "loss": loss,
+            "device_bytes_used": int(used)}
+
+
 def run_hq(args):
     import torch
     world, rank, local = dist_setup("nccl")
@@ -299,6 +345,10 @@ def run_hq(args):
                 "fp32_speedup": (p * nz * args.steps / (ms / 1e3)) / (p * nz / (ms64 / 1e3))}
         g64.close()
 
+    adjoint = None
+    if not args.no_adjoint and args.precision == "fp32":
+        adjoint = adjoint_leg(hq, I, stream, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(args.cpu_slices)
@@ -320,7 +370,7 @@ def run_hq(args):
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
             "gpu_launches": launches_per_sweep * args.steps,
-            "fp64": fp64, "cpu_baseline": cpu, "removed_particles": removed,
+            "fp64": fp64, "adjoint": adjoint, "cpu_baseline": cpu, "removed_particles": removed,
         }
         print(json.dumps(line), flush=True)
     grid.close()

@@ -154,6 +154,31 @@ hq_status hq_witness_accumulate(hq_grid_t grid, const hq_beam_view* beam, int32_
 hq_status hq_sweep_step(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, double dt,
                         const hq_field_out* out, int32_t witness_beam, double* witness_sums);
 
+/* Forward sweep for differentiation (the benchmark spec adjoint requirement; the paper has
+ * no adjoint): the same sweep as hq_sweep_step with dt = 0 and no field output, but
+ * it stores a checkpoint (plasma slice with its AB5 history and the field records a
+ * slice starts from) every ckpt_every slices, and the per-slice tapes of the last
+ * segment.  witness_sums (DEVICE double[3], zeroed by the caller) receives
+ * sum q w (1, Ez, Ez^2) over witness_beam (-1: none).  Memory: about
+ * (nzeta/ckpt_every) checkpoints + ckpt_every tapes, each ~(P x 130 B + n^2 x 80 B)
+ * in FP32; HQ_ERR_OOM asks for a larger or smaller interval. */
+hq_status hq_sweep_forward_ckpt(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, int32_t witness_beam,
+                                double* witness_sums, int32_t ckpt_every);
+
+/* Reverse-zeta adjoint of the last hq_sweep_forward_ckpt (same beams and witness):
+ * given dL/d(S0, S1, S2) of the witness sums (HOST double[3]), returns dL/dw for
+ * every beam particle (dL_dbeam_w: HOST array of nbeams DEVICE double* of n entries,
+ * overwritten; an entry may be NULL), dL/dw of every plasma particle (DEVICE double[P],
+ * may be NULL), dL/dn0_scale (DEVICE double[1], may be NULL) and dL/d(radial profile)
+ * (DEVICE double[n_profile], may be NULL).  Segments are recomputed from their
+ * checkpoints; deposit and gather are transposes of each other, the DST-I solve is
+ * self-adjoint, central differences transpose to minus themselves, and the push has
+ * its own adjoint kernel.  Leaves the grid's forward state undefined (the next sweep
+ * restarts at slice 0).  Errors: HQ_ERR_STATE without a matching forward. */
+hq_status hq_sweep_adjoint(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, int32_t witness_beam,
+                           const double* dL_dsums, double* const* dL_dbeam_w, double* dL_dplasma_w,
+                           double* dL_dn0_scale, double* dL_dprofile);
+
 /* Solves nrhs (1..5) Dirichlet Poisson problems L f = s with the grid's DST-I
  * backend (Sec. 3.2, fast Poisson solver): src and dst are DEVICE arrays of
  * nrhs x ny x nx field-type values (row/col 0 of src are ignored). */

@@ -2,6 +2,7 @@
 // steps of the quasi-static loop (Sec. 2 enumerate; Sec. 3.1 per-slice beam
 // work; Sec. 3.2 push, deposition, Poisson and predictor-corrector solvers)
 // and the full sweep.  Host code only orders launches on the grid's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -37,6 +38,8 @@ cudaError_t dalloc(P** p, size_t bytes) {
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+void adj_free(hq_grid_s* g);
+
 void free_all(hq_grid_s* g) {
   auto F = [](void* p) { if (p) cudaFree(p); };
   for (hq::Plasma<double>* p : {&g->p64}) {
@@ -56,6 +59,7 @@ void free_all(hq_grid_s* g) {
   for (int b = 0; b < kMaxBeams; ++b) {
     F(g->bins[b].bin); F(g->bins[b].count); F(g->bins[b].offset); F(g->bins[b].cursor); F(g->bins[b].perm);
   }
+  adj_free(g);
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   g->ev_pool.clear();
   F(g->d_profile); F(g->d_status); F(g->d_removed); F(g->d_scratch_int);
@@ -81,6 +85,92 @@ std::vector<double> scale_table(const hq_grid_s* g, int rows, int cols) {
 double sin_jk(int64_t j, int64_t k, int n) {
   const int64_t m = (j * k) % (2 * (int64_t)n);
   return std::sin(M_PI * (double)m / (double)n);
+}
+
+
+// ---------------------------------------------------------------- checkpoints and tapes
+// A stored plasma slice: the state a slice starts from (or is recomputed from).
+struct Snap {
+  double *x = nullptr, *y = nullptr, *psi = nullptr;
+  void *ux = nullptr, *uy = nullptr, *hist = nullptr;
+  uint8_t* alive = nullptr;
+  int32_t* cell = nullptr;
+  float *fx = nullptr, *fy = nullptr, *opp = nullptr;
+};
+
+// Checkpoints every k slices (plasma + the field records a slice starts from), the
+// per-slice tapes of one segment (plasma, gather fields, B_perp of each predictor-
+// corrector iterate), and the adjoint state.
+struct AdjStore {
+  int k = 0, nseg = 0;
+  std::vector<Snap> ck;
+  std::vector<void*> ck_dep0, ck_dep1, ck_chi0, ck_chi1, ck_b1, ck_b2;
+  std::vector<Snap> tape;
+  std::vector<void*> tape_gf, tape_b;
+  int tape_slot = -1;       // tape slot of the slice being solved (-1: not taping)
+  int fwd_done = 0;         // a checkpointed forward sweep is available
+  int fwd_tape_base = -1;   // first slice held by the tape after the forward sweep
+  std::vector<hq_beam_view> fwd_beams;
+  int fwd_witness = -1;
+  void *sx = nullptr, *sy = nullptr, *sux = nullptr, *suy = nullptr, *spsi = nullptr, *sh = nullptr;
+  double* wbar_p = nullptr;
+  void* dbar[3] = {nullptr, nullptr, nullptr};
+  void* carry[3] = {nullptr, nullptr, nullptr};
+  void *fbar = nullptr, *bbar = nullptr, *jbar = nullptr, *jtot = nullptr, *rho_ion_bar = nullptr;
+  std::vector<void*> allocs;
+};
+
+AdjStore* adj_of(const hq_grid_s* g) { return reinterpret_cast<AdjStore*>(g->adj); }
+
+void snap_copy(hq_grid_s* g, Snap& d, bool save) {
+  const size_t np = (size_t)g->np, ts = g->tsize;
+  auto cp = [&](void* store, const void* live, size_t bytes) {
+    if (save) cudaMemcpyAsync(store, live, bytes, cudaMemcpyDeviceToDevice, g->stream);
+    else cudaMemcpyAsync(const_cast<void*>(live), store, bytes, cudaMemcpyDeviceToDevice, g->stream);
+  };
+  cp(d.x, g->p64.x, 8 * np);
+  cp(d.y, g->p64.y, 8 * np);
+  cp(d.psi, g->p64.psi, 8 * np);
+  cp(d.alive, g->p64.alive, np);
+  if (g->fp64) {
+    cp(d.ux, g->p64.ux, ts * np);
+    cp(d.uy, g->p64.uy, ts * np);
+    cp(d.hist, g->p64.hist, ts * np * kRing * 5);
+  } else {
+    cp(d.ux, g->p32.ux, ts * np);
+    cp(d.uy, g->p32.uy, ts * np);
+    cp(d.hist, g->p32.hist, ts * np * kRing * 5);
+    cp(d.cell, g->p32.cell, 4 * np);
+    cp(d.fx, g->p32.fx, 4 * np);
+    cp(d.fy, g->p32.fy, 4 * np);
+    cp(d.opp, g->p32.opp, 4 * np);
+  }
+}
+
+// Tape hooks called by the forward solve of a slice.
+void tape_slice_begin(hq_grid_s* g) {
+  AdjStore* a = adj_of(g);
+  if (a && a->tape_slot >= 0) snap_copy(g, a->tape[a->tape_slot], true);
+}
+template <typename T>
+void tape_b_iterate(hq_grid_s* g, int m) {
+  AdjStore* a = adj_of(g);
+  if (!a || a->tape_slot < 0) return;
+  char* base = reinterpret_cast<char*>(a->tape_b[a->tape_slot]) + (size_t)m * 2 * g->tsize * g->nnode;
+  launch_adj_extract_b<T>(g, base, g->stream);
+}
+void tape_slice_end(hq_grid_s* g) {
+  AdjStore* a = adj_of(g);
+  if (a && a->tape_slot >= 0)
+    cudaMemcpyAsync(a->tape_gf[a->tape_slot], g->gf, kGF * g->tsize * g->nnode, cudaMemcpyDeviceToDevice, g->stream);
+}
+
+void adj_free(hq_grid_s* g) {
+  AdjStore* a = adj_of(g);
+  if (!a) return;
+  for (void* p : a->allocs) cudaFree(p);
+  delete a;
+  g->adj = nullptr;
 }
 
 // Counts the launches of one kernel group and, while profiling is on, brackets
@@ -120,12 +210,14 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
   void* cur = g->dep[slice & 1];
   void* prev = g->dep[(slice + 1) & 1];
   void* chi_prev = g->chi[(slice + 1) & 1];
+  tape_slice_begin(g);
   { Prof p(g, HQ_K_FIELD, 1); launch_src_main<T>(g, cur, s); }
   dst_solve(g, 3);
   { Prof p(g, HQ_K_FIELD, 1); launch_finish_main<T>(g, g->solved, s); }
   const int npc = g->d.n_pc_iter;
   for (int m = 0; m < npc; ++m) {
     const int last = m == npc - 1;
+    tape_b_iterate<T>(g, m);
     { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, s); }
     { Prof p(g, HQ_K_FIELD, 1); launch_src_bperp<T>(g, cur, prev, chi_prev, last, s); }
     dst_solve(g, 2);
@@ -138,6 +230,7 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
     launch_zero<T>(g->bjn, 2 * g->nnode, s);
     launch_reset_dep<T>(g, prev, chi_prev, s);
   }
+  tape_slice_end(g);
   return HQ_OK;
 }
 
@@ -228,6 +321,202 @@ int bound_index(const hq_grid_s* g, const hq_beam_view* v) {
 hq_status check_launch(hq_grid_s* g) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(g, HQ_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return HQ_OK;
+}
+
+
+// ---------------------------------------------------------------- checkpointed forward and adjoint
+hq_status adj_alloc(hq_grid_s* g, int k) {
+  AdjStore* a = adj_of(g);
+  if (a && a->k == k) return HQ_OK;
+  adj_free(g);
+  a = new (std::nothrow) AdjStore();
+  if (!a) return fail(g, HQ_ERR_OOM, "host allocation failed");
+  g->adj = a;
+  a->k = k;
+  a->nseg = (g->nz + k - 1) / k;
+  const size_t np = (size_t)g->np, ts = g->tsize, nn = (size_t)g->nnode;
+  const int npc = g->d.n_pc_iter;
+  auto A = [&](void** p, size_t bytes) -> bool {
+    *p = nullptr;
+    if (bytes == 0) return true;
+    if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+    a->allocs.push_back(*p);
+    return true;
+  };
+  auto snap = [&](Snap& d) -> bool {
+    bool ok = A((void**)&d.x, 8 * np) && A((void**)&d.y, 8 * np) && A((void**)&d.psi, 8 * np) &&
+              A((void**)&d.alive, np) && A(&d.ux, ts * np) && A(&d.uy, ts * np) && A(&d.hist, ts * np * kRing * 5);
+    if (ok && !g->fp64)
+      ok = A((void**)&d.cell, 4 * np) && A((void**)&d.fx, 4 * np) && A((void**)&d.fy, 4 * np) &&
+           A((void**)&d.opp, 4 * np);
+    return ok;
+  };
+  bool ok = true;
+  a->ck.resize(a->nseg);
+  a->ck_dep0.resize(a->nseg); a->ck_dep1.resize(a->nseg); a->ck_chi0.resize(a->nseg); a->ck_chi1.resize(a->nseg);
+  a->ck_b1.resize(a->nseg); a->ck_b2.resize(a->nseg);
+  for (int i = 0; ok && i < a->nseg; ++i)
+    ok = snap(a->ck[i]) && A(&a->ck_dep0[i], 4 * ts * nn) && A(&a->ck_dep1[i], 4 * ts * nn) &&
+         A(&a->ck_chi0[i], ts * nn) && A(&a->ck_chi1[i], ts * nn) && A(&a->ck_b1[i], 2 * ts * nn) &&
+         A(&a->ck_b2[i], 2 * ts * nn);
+  a->tape.resize(k);
+  a->tape_gf.resize(k);
+  a->tape_b.resize(k);
+  for (int i = 0; ok && i < k; ++i)
+    ok = snap(a->tape[i]) && A(&a->tape_gf[i], kGF * ts * nn) && A(&a->tape_b[i], (size_t)std::max(npc, 1) * 2 * ts * nn);
+  ok = ok && A(&a->sx, ts * np) && A(&a->sy, ts * np) && A(&a->sux, ts * np) && A(&a->suy, ts * np) &&
+       A(&a->spsi, ts * np) && A(&a->sh, ts * np * 20) && A((void**)&a->wbar_p, 8 * np) && A(&a->fbar, kGF * ts * nn) &&
+       A(&a->bbar, (size_t)(npc + 1) * 2 * ts * nn) && A(&a->jbar, 2 * ts * nn) && A(&a->jtot, 2 * ts * nn) &&
+       A(&a->rho_ion_bar, ts * nn);
+  for (int i = 0; ok && i < 3; ++i) ok = A(&a->dbar[i], 4 * ts * nn) && A(&a->carry[i], 2 * ts * nn);
+  if (!ok) {
+    adj_free(g);
+    return fail(g, HQ_ERR_OOM, "checkpoint/tape allocation failed (reduce ckpt_every)");
+  }
+  return HQ_OK;
+}
+
+void ckpt_copy(hq_grid_s* g, int seg, bool save) {
+  AdjStore* a = adj_of(g);
+  snap_copy(g, a->ck[seg], save);
+  const size_t ts = g->tsize, nn = (size_t)g->nnode;
+  auto cp = [&](void* store, void* live, size_t bytes) {
+    if (save) cudaMemcpyAsync(store, live, bytes, cudaMemcpyDeviceToDevice, g->stream);
+    else cudaMemcpyAsync(live, store, bytes, cudaMemcpyDeviceToDevice, g->stream);
+  };
+  cp(a->ck_dep0[seg], g->dep[0], 4 * ts * nn);
+  cp(a->ck_dep1[seg], g->dep[1], 4 * ts * nn);
+  cp(a->ck_chi0[seg], g->chi[0], ts * nn);
+  cp(a->ck_chi1[seg], g->chi[1], ts * nn);
+  cp(a->ck_b1[seg], g->bprev1, 2 * ts * nn);
+  cp(a->ck_b2[seg], g->bprev2, 2 * ts * nn);
+}
+
+// Runs slices [a0, a1) from the state after hq_advance_slice(a0), taping slices >= tape_from.
+template <typename T>
+hq_status run_segment(hq_grid_s* g, const hq_beam_view* beams, int nb, int a0, int a1, int tape_from, int witness,
+                      double* wsums) {
+  AdjStore* a = adj_of(g);
+  for (int i = a0; i < a1; ++i) {
+    if (i > a0) advance_impl<T>(g, i);
+    hq_status st = beam_deposit_impl<T>(g, beams, nb, i);
+    if (st != HQ_OK) return st;
+    a->tape_slot = i >= tape_from ? i - tape_from : -1;
+    solve_fields_impl<T>(g, i);
+    a->tape_slot = -1;
+    if (witness >= 0 && wsums && beams[witness].n > 0) {
+      Prof p(g, HQ_K_BEAM, 1);
+      launch_witness<T>(g, witness, beams[witness], i, wsums, g->stream);
+    }
+  }
+  return HQ_OK;
+}
+
+template <typename T>
+hq_status forward_ckpt_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witness, double* wsums) {
+  AdjStore* a = adj_of(g);
+  const int last_seg = a->nseg - 1;
+  const int tape_from = last_seg * a->k;
+  for (int seg = 0; seg < a->nseg; ++seg) {
+    const int a0 = seg * a->k, a1 = std::min(g->nz, a0 + a->k);
+    advance_impl<T>(g, a0);
+    ckpt_copy(g, seg, true);
+    hq_status st = run_segment<T>(g, beams, nb, a0, a1, seg == last_seg ? tape_from : g->nz, witness, wsums);
+    if (st != HQ_OK) return st;
+  }
+  a->fwd_tape_base = tape_from;
+  return HQ_OK;
+}
+
+template <typename T>
+hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witness, const double* sbar,
+                       double* const* wbar_b, double* wbar_p_out, double* dn0, double* dprof) {
+  AdjStore* a = adj_of(g);
+  cudaStream_t s = g->stream;
+  const size_t np = (size_t)g->np, ts = g->tsize, nn = (size_t)g->nnode;
+  const int npc = g->d.n_pc_iter;
+  const size_t brec = 2 * ts * nn;
+  for (void* p : {a->sx, a->sy, a->sux, a->suy, a->spsi}) cudaMemsetAsync(p, 0, ts * np, s);
+  cudaMemsetAsync(a->sh, 0, ts * np * 20, s);
+  cudaMemsetAsync(a->wbar_p, 0, 8 * np, s);
+  for (int i = 0; i < 3; ++i) {
+    cudaMemsetAsync(a->dbar[i], 0, 4 * ts * nn, s);
+    cudaMemsetAsync(a->carry[i], 0, 2 * ts * nn, s);
+  }
+  cudaMemsetAsync(a->rho_ion_bar, 0, ts * nn, s);
+  for (int b = 0; b < nb; ++b)
+    if (wbar_b && wbar_b[b] && beams[b].n > 0) cudaMemsetAsync(wbar_b[b], 0, 8 * (size_t)beams[b].n, s);
+  void* dnext = a->dbar[0];
+  void* dcur = a->dbar[1];
+  void* dprev = a->dbar[2];
+  AdjView<T> av{reinterpret_cast<T*>(a->sx), reinterpret_cast<T*>(a->sy), reinterpret_cast<T*>(a->sux),
+                reinterpret_cast<T*>(a->suy), reinterpret_cast<T*>(a->spsi), reinterpret_cast<T*>(a->sh)};
+  const T* w = g->fp64 ? reinterpret_cast<const T*>(g->p64.w) : reinterpret_cast<const T*>(g->p32.w);
+  for (int seg = a->nseg - 1; seg >= 0; --seg) {
+    const int a0 = seg * a->k, a1 = std::min(g->nz, a0 + a->k);
+    if (!(seg == a->nseg - 1 && a->fwd_tape_base == a0)) {
+      // recompute the segment from its checkpoint, taping every slice
+      ckpt_copy(g, seg, false);
+      cudaMemsetAsync(g->tj, 0, 2 * ts * nn, s);
+      cudaMemsetAsync(g->bjn, 0, 2 * ts * nn, s);
+      hq_status st = run_segment<T>(g, beams, nb, a0, a1, a0, -1, nullptr);
+      if (st != HQ_OK) return st;
+    }
+    for (int i = a1 - 1; i >= a0; --i) {
+      const int t = i - a0;
+      const Snap& sn = a->tape[t];
+      SnapView<T> sv{g->np, sn.x, sn.y, sn.psi, reinterpret_cast<const T*>(sn.ux), reinterpret_cast<const T*>(sn.uy), w,
+                     sn.alive, reinterpret_cast<const T*>(sn.hist)};
+      const void* gf = a->tape_gf[t];
+      cudaMemsetAsync(a->fbar, 0, kGF * ts * nn, s);
+      cudaMemsetAsync(a->jtot, 0, 2 * ts * nn, s);
+      if (witness >= 0 && beams[witness].n > 0) {
+        Prof p(g, HQ_K_BEAM, 1);
+        launch_adj_witness<T>(g, witness, beams[witness], i, gf, sbar, a->fbar,
+                              wbar_b ? wbar_b[witness] : nullptr, s);
+      }
+      if (i < g->nz - 1) {
+        Prof p(g, HQ_K_FINAL, 1);
+        launch_adj_final<T>(g, sv, gf, i, dnext, av, a->fbar, a->wbar_p, s);
+      }
+      char* bb = reinterpret_cast<char*>(a->bbar);
+      { Prof p(g, HQ_K_FIELD, 1); launch_adj_bstart<T>(g, a->fbar, a->carry[i % 3], bb + (size_t)npc * brec, s); }
+      for (int m = npc; m >= 1; --m) {
+        { Prof p(g, HQ_K_FIELD, 1); launch_adj_pc_pre<T>(g, bb + (size_t)m * brec, bb + (size_t)(m - 1) * brec, s); }
+        dst_solve(g, 2);
+        { Prof p(g, HQ_K_FIELD, 1); launch_adj_pc_post<T>(g, dcur, dprev, a->jbar, a->jtot, s); }
+        {
+          Prof p(g, HQ_K_TRIAL, 1);
+          launch_adj_trial<T>(g, sv, gf, reinterpret_cast<char*>(a->tape_b[t]) + (size_t)(m - 1) * brec, i, a->jbar, av,
+                              a->fbar, bb + (size_t)(m - 1) * brec, a->wbar_p, s);
+        }
+      }
+      {
+        Prof p(g, HQ_K_FIELD, 1);
+        launch_adj_guess<T>(g, bb, i >= 1 ? a->carry[(i - 1) % 3] : nullptr, i >= 2 ? a->carry[(i - 2) % 3] : nullptr, s);
+      }
+      { Prof p(g, HQ_K_FIELD, 1); launch_adj_main_pre<T>(g, a->fbar, s); }
+      dst_solve(g, 3);
+      { Prof p(g, HQ_K_FIELD, 1); launch_adj_main_post<T>(g, dcur, a->rho_ion_bar, s); }
+      for (int b = 0; b < nb; ++b) {
+        if (!wbar_b || !wbar_b[b] || beams[b].n == 0) continue;
+        Prof p(g, HQ_K_BEAM, 1);
+        launch_adj_beam<T>(g, b, beams[b], i, dcur, a->jtot, wbar_b[b], s);
+      }
+      // rotate: slice i's record becomes "next" for slice i-1; the old next is cleared for i-2
+      void* old_next = dnext;
+      dnext = dcur;
+      dcur = dprev;
+      dprev = old_next;
+      cudaMemsetAsync(dprev, 0, 4 * ts * nn, s);
+    }
+  }
+  { Prof p(g, HQ_K_OTHER, 1); launch_adj_init<T>(g, dnext, a->rho_ion_bar, a->wbar_p, s); }
+  if (dn0) cudaMemsetAsync(dn0, 0, 8, s);
+  if (dprof && !g->profile.empty()) cudaMemsetAsync(dprof, 0, 8 * g->profile.size(), s);
+  if (dn0 || dprof) launch_adj_params(g, a->wbar_p, dn0, g->profile.empty() ? nullptr : dprof, s);
+  if (wbar_p_out) cudaMemcpyAsync(wbar_p_out, a->wbar_p, 8 * np, cudaMemcpyDeviceToDevice, s);
   return HQ_OK;
 }
 
@@ -553,6 +842,52 @@ hq_status hq_sweep_step(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, double
   if (g->fp64) final_pass<double>(g, nz - 1, nz & 1);
   else final_pass<float>(g, nz - 1, nz & 1);
   g->last_adv = nz;
+  return check_launch(g);
+}
+
+
+hq_status hq_sweep_forward_ckpt(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, int32_t witness_beam,
+                                double* witness_sums, int32_t ckpt_every) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  hq_status st = check_views(g, beams, nbeams);
+  if (st != HQ_OK) return st;
+  if (witness_beam >= nbeams || (witness_beam >= 0 && !witness_sums))
+    return fail(g, HQ_ERR_ARG, "witness_beam must index a beam and witness_sums must be given");
+  if (ckpt_every < 1) return fail(g, HQ_ERR_ARG, "ckpt_every must be >= 1");
+  const int k = std::min<int>(ckpt_every, g->nz);
+  if ((st = adj_alloc(g, k)) != HQ_OK) return st;
+  AdjStore* a = adj_of(g);
+  st = g->fp64 ? forward_ckpt_impl<double>(g, beams, nbeams, witness_beam, witness_sums)
+               : forward_ckpt_impl<float>(g, beams, nbeams, witness_beam, witness_sums);
+  if (st != HQ_OK) return st;
+  a->fwd_done = 1;
+  a->fwd_beams.assign(beams, beams + nbeams);
+  a->fwd_witness = witness_beam;
+  g->last_adv = g->nz - 1;
+  g->last_beam = g->last_solved = g->nz - 1;
+  return check_launch(g);
+}
+
+hq_status hq_sweep_adjoint(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, int32_t witness_beam,
+                           const double* dL_dsums, double* const* dL_dbeam_w, double* dL_dplasma_w,
+                           double* dL_dn0_scale, double* dL_dprofile) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  AdjStore* a = adj_of(g);
+  if (!a || !a->fwd_done) return fail(g, HQ_ERR_STATE, "hq_sweep_adjoint needs hq_sweep_forward_ckpt first");
+  if (nbeams != (int)a->fwd_beams.size() || witness_beam != a->fwd_witness)
+    return fail(g, HQ_ERR_STATE, "beams/witness differ from the checkpointed forward sweep");
+  for (int b = 0; b < nbeams; ++b)
+    if (!same_view(beams[b], a->fwd_beams[b])) return fail(g, HQ_ERR_STATE, "beams differ from the forward sweep");
+  if (witness_beam >= 0 && !dL_dsums) return fail(g, HQ_ERR_ARG, "dL_dsums (host double[3]) is needed");
+  const double zero[3] = {0.0, 0.0, 0.0};
+  const double* sb = dL_dsums ? dL_dsums : zero;
+  hq_status st = g->fp64 ? adjoint_impl<double>(g, beams, nbeams, witness_beam, sb, dL_dbeam_w, dL_dplasma_w,
+                                                dL_dn0_scale, dL_dprofile)
+                         : adjoint_impl<float>(g, beams, nbeams, witness_beam, sb, dL_dbeam_w, dL_dplasma_w,
+                                               dL_dn0_scale, dL_dprofile);
+  if (st != HQ_OK) return st;
+  a->fwd_done = 0;
+  g->last_adv = g->last_beam = g->last_solved = -1;
   return check_launch(g);
 }
 

@@ -74,6 +74,23 @@ struct BeamBins {
 
 struct TensorMaps;  // opaque, defined in the tensor-core DST unit
 
+// Read-only view of a stored plasma slice (tape) for the adjoint kernels; w is the
+// grid's (constant) weight array.
+template <typename T> struct SnapView {
+  int64_t n;
+  const double *x, *y, *psi;
+  const T *ux, *uy, *w;
+  const uint8_t* alive;
+  const T* hist;    // AB5 ring as stored: physical slot s holds f_k with k = s mod 4
+};
+
+// Per-particle adjoint state: x, y, ux, uy, Psi and the AB5 history in logical order
+// (sh[j] is the adjoint of f_{i-1-j} at the current slice i), [4][5][n].
+template <typename T> struct AdjView {
+  T *sx, *sy, *sux, *suy, *spsi;
+  T* sh;
+};
+
 }  // namespace hq
 
 // ---------------------------------------------------------------- grid object
@@ -127,6 +144,9 @@ struct hq_grid_s {
   int last_adv, last_beam, last_solved;
   std::string err;
 
+  // checkpoints, tapes and adjoint state (allocated by the first checkpointed sweep)
+  void* adj;
+
   // profiling: launch counters (always) and optional CUDA event pairs per launch group
   int64_t launches[HQ_K_CLASSES];
   int prof_on;
@@ -169,6 +189,27 @@ void launch_beam_bin(hq_grid_s* g, int b, const hq_beam_view& v, cudaStream_t s)
 template <typename T> void launch_beam_deposit(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, void* dep, void* bjn, cudaStream_t s);
 template <typename T> void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double dt, cudaStream_t s);
 template <typename T> void launch_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double* sums, cudaStream_t s);
+// adjoint (k_adjoint.cu)
+template <typename T> void launch_adj_final(const hq_grid_s* g, const SnapView<T>& s, const void* gf, int slice,
+                                           const void* dbar_next, const AdjView<T>& a, void* fbar, double* wbar_p,
+                                           cudaStream_t st);
+template <typename T> void launch_adj_trial(const hq_grid_s* g, const SnapView<T>& s, const void* gf, const void* bm,
+                                           int slice, const void* jbar, const AdjView<T>& a, void* fbar, void* bbar_m1,
+                                           double* wbar_p, cudaStream_t st);
+template <typename T> void launch_adj_bstart(const hq_grid_s* g, const void* fbar, void* carry, void* bbar_n, cudaStream_t st);
+template <typename T> void launch_adj_pc_pre(const hq_grid_s* g, const void* bbar_m, void* bbar_m1, cudaStream_t st);
+template <typename T> void launch_adj_pc_post(const hq_grid_s* g, void* dcur, void* dprev, void* jbar, void* jtot, cudaStream_t st);
+template <typename T> void launch_adj_guess(const hq_grid_s* g, const void* b0, void* c1, void* c2, cudaStream_t st);
+template <typename T> void launch_adj_main_pre(const hq_grid_s* g, const void* fbar, cudaStream_t st);
+template <typename T> void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, cudaStream_t st);
+template <typename T> void launch_adj_extract_b(const hq_grid_s* g, void* out, cudaStream_t st);
+template <typename T> void launch_adj_beam(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* dcur,
+                                          const void* jtot, double* wbar, cudaStream_t st);
+template <typename T> void launch_adj_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* gf,
+                                             const double* sb, void* fbar, double* wbar, cudaStream_t st);
+template <typename T> void launch_adj_init(const hq_grid_s* g, const void* d0, const void* rho_ion_bar, double* wbar_p,
+                                          cudaStream_t st);
+void launch_adj_params(const hq_grid_s* g, const double* wbar_p, double* dn0, double* dprof, cudaStream_t st);
 
 }  // namespace hq
 
@@ -213,5 +254,57 @@ __device__ __forceinline__ void split_coord(double x, double x0, double dx, int&
 }
 
 __device__ __forceinline__ bool in_interior(int j, int n) { return j >= 1 && j <= n - 1; }
+
+}  // namespace hq
+
+// ---------------------------------------------------------------- shared field helpers
+namespace hq {
+
+// DST operand writers: FP64 mode writes [rhs][ny][nx] doubles (g->f64_a); FP32 mode
+// writes each value already split into bf16 hi + lo, zero-padded [rhs][nyp][nxp]
+// (g->op_hi[0], g->op_lo[0]), the tensor-core solver's input layout.
+struct SinkF64 {
+  double* p;
+  int nx, ny;
+  __device__ void put(int r, int iy, int ix, double v) const { p[((int64_t)r * ny + iy) * nx + ix] = v; }
+};
+
+struct SinkBF16 {
+  __nv_bfloat16 *hi, *lo;
+  int nxp, nyp;
+  __device__ void put(int r, int iy, int ix, float v) const {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    const int64_t o = ((int64_t)r * nyp + iy) * nxp + ix;
+    hi[o] = h;
+    lo[o] = l;
+  }
+};
+
+
+template <typename T> struct SinkOf;
+template <> struct SinkOf<double> {
+  static SinkF64 make(const hq_grid_s* g) { return SinkF64{g->f64_a, g->nx, g->ny}; }
+};
+template <> struct SinkOf<float> {
+  static SinkBF16 make(const hq_grid_s* g) { return SinkBF16{g->op_hi[0], g->op_lo[0], g->nxp, g->nyp}; }
+};
+
+// Central difference helpers with wall nodes (index 0 and n) reading zero; the
+// result on wall rows/columns is zero (matching the field layout convention).
+template <typename A, typename C>
+__device__ __forceinline__ auto dxc(const A& f, int iy, int ix, int nx, C inv2dx) -> decltype(f(0, 0)) {
+  using T = decltype(f(0, 0));
+  const T r = ix + 1 < nx ? f(iy, ix + 1) : T(0);
+  const T l = f(iy, ix - 1);
+  return (r - l) * T(inv2dx);
+}
+template <typename A, typename C>
+__device__ __forceinline__ auto dyc(const A& f, int iy, int ix, int ny, C inv2dy) -> decltype(f(0, 0)) {
+  using T = decltype(f(0, 0));
+  const T u = iy + 1 < ny ? f(iy + 1, ix) : T(0);
+  const T d = f(iy - 1, ix);
+  return (u - d) * T(inv2dy);
+}
 
 }  // namespace hq

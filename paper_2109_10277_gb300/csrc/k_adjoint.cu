@@ -1,0 +1,736 @@
+// Reverse-zeta adjoint of the quasi-static slice loop (hand-written discrete
+// adjoint of the forward kernels; the paper has no adjoint, the structure
+// follows its slice routine, Sec. 2, and predictor-corrector, Sec. 3.2).
+//
+// Transposes used:
+//   gather  <-> deposit (same B-spline stencil), plus the stencil derivative for
+//               the particle-position adjoints;
+//   DST-I Dirichlet solve L^-1 is symmetric (self-adjoint);
+//   masked central difference D (zero wall values/outputs): D^T = -D;
+//   AB5 step y' = y - dzeta (b0 f + sum b_k H_k): ybar += y'bar, fbar = -dzeta b0 y'bar,
+//               Hbar_k += -dzeta b_k y'bar;
+//   push derivatives f(u, Psi, F): transposed Jacobian (derivs_adj).
+// Per-particle adjoint state (x, y, ux, uy, Psi and the AB5 history, logical
+// order f_{i-1}..f_{i-4}) is owned by one thread and updated in place from slice
+// i+1 to slice i; field adjoints are accumulated with atomics.
+#include "hq_internal.cuh"
+
+namespace hq {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// B-spline weights and their derivatives d w / d u (u = node coordinate).
+template <int P, typename T>
+__device__ __forceinline__ int shape_wd(int jf, T d, T* w, T* dw) {
+  if constexpr (P == 0) {
+    w[0] = T(1);
+    dw[0] = T(0);
+    return jf + (d >= T(0.5) ? 1 : 0);
+  } else if constexpr (P == 1) {
+    w[0] = T(1) - d;
+    w[1] = d;
+    dw[0] = T(-1);
+    dw[1] = T(1);
+    return jf;
+  } else if constexpr (P == 2) {
+    const bool up = d >= T(0.5);
+    const T e = up ? d - T(1) : d;
+    const T a = T(0.5) - e, b = T(0.5) + e;
+    w[0] = T(0.5) * a * a;
+    w[1] = T(0.75) - e * e;
+    w[2] = T(0.5) * b * b;
+    dw[0] = -a;
+    dw[1] = T(-2) * e;
+    dw[2] = b;
+    return jf + (up ? 1 : 0) - 1;
+  } else {
+    const T d2 = d * d, d3 = d2 * d, om = T(1) - d;
+    w[0] = om * om * om * T(1.0 / 6.0);
+    w[1] = (T(4) - T(6) * d2 + T(3) * d3) * T(1.0 / 6.0);
+    w[2] = (T(1) + T(3) * d + T(3) * d2 - T(3) * d3) * T(1.0 / 6.0);
+    w[3] = d3 * T(1.0 / 6.0);
+    dw[0] = T(-0.5) * om * om;
+    dw[1] = T(-2) * d + T(1.5) * d2;
+    dw[2] = T(0.5) + d - T(1.5) * d2;
+    dw[3] = T(0.5) * d2;
+    return jf - 1;
+  }
+}
+
+template <int P, typename T>
+struct Stencil {
+  int ix0, iy0;
+  T wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];  // dw*: derivative w.r.t. the physical coordinate
+};
+
+template <int P, typename T>
+__device__ __forceinline__ void stencil_at(const Geom& gm, double x, double y, Stencil<P, T>& s) {
+  int jx, jy;
+  double fx, fy;
+  split_coord(x, gm.xmin, gm.dx, jx, fx);
+  split_coord(y, gm.ymin, gm.dy, jy, fy);
+  s.ix0 = shape_wd<P, T>(jx, T(fx), s.wx, s.dwx);
+  s.iy0 = shape_wd<P, T>(jy, T(fy), s.wy, s.dwy);
+#pragma unroll
+  for (int a = 0; a <= P; ++a) {
+    s.dwx[a] *= T(gm.inv_dx);
+    s.dwy[a] *= T(gm.inv_dy);
+  }
+}
+
+// Interpolated values and x/y gradients of NC components at stride `st` (offset `off`).
+template <int P, typename T, int NC>
+__device__ __forceinline__ void gather_g(const T* __restrict__ f, int st, int off, const Geom& gm, const Stencil<P, T>& s,
+                                         T* val, T* gx, T* gy) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) val[c] = gx[c] = gy[c] = T(0);
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const int iy = s.iy0 + b;
+    if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      const int ix = s.ix0 + a;
+      if (!in_interior(ix, gm.nx)) continue;
+      const T* q = f + ((int64_t)iy * gm.nx + ix) * st + off;
+      const T w = s.wx[a] * s.wy[b], wxd = s.dwx[a] * s.wy[b], wyd = s.wx[a] * s.dwy[b];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T v = q[c];
+        val[c] += w * v;
+        gx[c] += wxd * v;
+        gy[c] += wyd * v;
+      }
+    }
+  }
+}
+
+// f[node * st + off + c] += S * v[c] (atomics)
+template <int P, typename T, int NC>
+__device__ __forceinline__ void scatter(T* f, int st, int off, const Geom& gm, const Stencil<P, T>& s, const T* v) {
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const int iy = s.iy0 + b;
+    if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      const int ix = s.ix0 + a;
+      if (!in_interior(ix, gm.nx)) continue;
+      T* q = f + ((int64_t)iy * gm.nx + ix) * st + off;
+      const T w = s.wx[a] * s.wy[b];
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (v[c] != T(0)) atomicAdd(q + c, w * v[c]);
+    }
+  }
+}
+
+// Forward zeta-derivatives (identical to the forward kernels' formula).
+template <typename T>
+__device__ __forceinline__ void derivs_f(T ux, T uy, T opp, const T* F, T* f) {
+  const T g = T(1) / opp;
+  const T gam = (T(1) + ux * ux + uy * uy + opp * opp) * T(0.5) * g;
+  f[0] = -ux * g;
+  f[1] = -uy * g;
+  f[2] = gam * g * F[0] + F[4] + F[5] * g * uy;
+  f[3] = gam * g * F[1] - F[3] - F[5] * g * ux;
+  f[4] = g * (ux * F[0] + uy * F[1]) - F[2];
+}
+
+// Transposed Jacobian of derivs: given fbar, accumulate (ux, uy, Psi) adjoints and the
+// adjoints of the six gathered fields F = (ExmBy, EypBx, Ez, Bx, By, Bz).
+template <typename T>
+__device__ __forceinline__ void derivs_adj(T ux, T uy, T opp, const T* F, const T* fb, T& bux, T& buy, T& bpsi,
+                                           T* bF) {
+  const T g = T(1) / opp, g2 = g * g;
+  const T q2 = T(1) + ux * ux + uy * uy;
+  const T gam = q2 * T(0.5) * g + T(0.5) * opp;
+  const T A = gam * g;
+  const T dgam_dpsi = T(-0.5) * q2 * g2 + T(0.5);
+  const T dA_dpsi = dgam_dpsi * g - gam * g2;
+  const T E0 = F[0], E1 = F[1], Bz = F[5];
+  bux = fb[0] * (-g) + fb[2] * (ux * g2 * E0) + fb[3] * (ux * g2 * E1 - Bz * g) + fb[4] * (g * E0);
+  buy = fb[1] * (-g) + fb[2] * (uy * g2 * E0 + Bz * g) + fb[3] * (uy * g2 * E1) + fb[4] * (g * E1);
+  bpsi = fb[0] * (ux * g2) + fb[1] * (uy * g2) + fb[2] * (dA_dpsi * E0 - Bz * g2 * uy) +
+         fb[3] * (dA_dpsi * E1 + Bz * g2 * ux) - fb[4] * (g2 * (ux * E0 + uy * E1));
+  bF[0] = fb[2] * A + fb[4] * g * ux;
+  bF[1] = fb[3] * A + fb[4] * g * uy;
+  bF[2] = -fb[4];
+  bF[3] = -fb[3];
+  bF[4] = fb[2];
+  bF[5] = fb[2] * g * uy - fb[3] * g * ux;
+}
+
+template <typename T>
+__device__ __forceinline__ T hist_at(const T* __restrict__ h, int64_t n, int64_t p, int slice, int k, int c) {
+  const int slot = ((slice - k) % kRing + kRing) % kRing;  // physical slot of f_{slice-k}
+  return h[((int64_t)slot * 5 + c) * n + p];
+}
+
+// Removal rule, identical to the forward passes.
+__device__ __forceinline__ bool ok_state(const Geom& gm, double x, double y, double opp, double guard) {
+  return isfinite(x) && isfinite(y) && isfinite(opp) && x > gm.xmin && x < gm.xmax && y > gm.ymin && y < gm.ymax &&
+         opp >= guard;
+}
+
+template <typename T>
+__device__ __forceinline__ T unit_charge_density(const Geom& gm) {  // q / A with q = -1
+  if constexpr (sizeof(T) == 8) return T(-1.0) / (gm.dx * gm.dy);
+  else return T(-gm.inv_area);
+}
+
+// ---------------------------------------------------------------- final pass adjoint
+// Reverse of: gather at slice i, AB5 step to i+1, removal, deposit at i+1.
+template <int P, typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_adj_final(SnapView<T> s, const T* __restrict__ gf, Geom gm, int slice, double guard,
+                const V4<T>* __restrict__ dbar_next, AdjView<T> a, T* fbar, double* wbar_p) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= s.n || !s.alive[p]) return;
+  const int64_t n = s.n;
+  const double x = s.x[p], y = s.y[p], psi = s.psi[p];
+  const T ux = s.ux[p], uy = s.uy[p], w = s.w[p];
+  const T opp = T(1.0 + psi);
+  Stencil<P, T> st;
+  stencil_at<P, T>(gm, x, y, st);
+  T F[6], Fx[6], Fy[6];
+  gather_g<P, T, 6>(gf, kGF, 0, gm, st, F, Fx, Fy);
+  T f[5];
+  derivs_f<T>(ux, uy, opp, F, f);
+  T comb[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    T acc = T(ab5(0)) * f[c];
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) acc += T(ab5(k)) * hist_at<T>(s.hist, n, p, slice, k, c);
+    comb[c] = acc;
+  }
+  const double dz = gm.dzeta;
+  const double nxp = x - dz * (double)comb[0], nyp = y - dz * (double)comb[1];
+  const double npsi = psi - dz * (double)comb[4];
+  const T nux = ux - T(dz) * comb[2], nuy = uy - T(dz) * comb[3];
+  if (!ok_state(gm, nxp, nyp, 1.0 + npsi, guard)) return;  // removed: nothing downstream depends on it
+  // deposit at slice i+1: v = q w (gamma g, ux g, uy g, uz g) / A
+  Stencil<P, T> sn;
+  stencil_at<P, T>(gm, nxp, nyp, sn);
+  T Dg[4], Dgx[4], Dgy[4];
+  gather_g<P, T, 4>(reinterpret_cast<const T*>(dbar_next), 4, 0, gm, sn, Dg, Dgx, Dgy);
+  const T nopp = T(1.0 + npsi), g = T(1) / nopp, g2 = g * g;
+  const T q2 = T(1) + nux * nux + nuy * nuy;
+  const T gg = q2 * T(0.5) * g2 + T(0.5);   // gamma g
+  const T ug = q2 * T(0.5) * g2 - T(0.5);   // uz g
+  const T qw1 = unit_charge_density<T>(gm), qw = qw1 * w;
+  const T v[4] = {qw * gg, qw * nux * g, qw * nuy * g, qw * ug};
+  T sb[5];
+  sb[0] = a.sx[p] + v[0] * Dgx[0] + v[1] * Dgx[1] + v[2] * Dgx[2] + v[3] * Dgx[3];
+  sb[1] = a.sy[p] + v[0] * Dgy[0] + v[1] * Dgy[1] + v[2] * Dgy[2] + v[3] * Dgy[3];
+  sb[2] = a.sux[p] + qw * (Dg[0] * nux * g2 + Dg[1] * g + Dg[3] * nux * g2);
+  sb[3] = a.suy[p] + qw * (Dg[0] * nuy * g2 + Dg[2] * g + Dg[3] * nuy * g2);
+  sb[4] = a.spsi[p] + qw * (-(Dg[0] + Dg[3]) * q2 * g2 * g - Dg[1] * nux * g2 - Dg[2] * nuy * g2);
+  wbar_p[p] += (double)(qw1 * (Dg[0] * gg + Dg[1] * nux * g + Dg[2] * nuy * g + Dg[3] * ug));
+  // AB5 step and history shift
+  T fb[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    T hn[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hn[j] = a.sh[((int64_t)j * 5 + c) * n + p];
+    fb[c] = T(-dz * ab5(0)) * sb[c] + hn[0];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      a.sh[((int64_t)j * 5 + c) * n + p] = T(-dz * ab5(j + 1)) * sb[c] + (j < 3 ? hn[j + 1] : T(0));
+  }
+  T bux, buy, bpsi, bF[6];
+  derivs_adj<T>(ux, uy, opp, F, fb, bux, buy, bpsi, bF);
+  scatter<P, T, 6>(fbar, kGF, 0, gm, st, bF);
+  T bx = sb[0], by = sb[1];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    bx += bF[c] * Fx[c];
+    by += bF[c] * Fy[c];
+  }
+  a.sx[p] = bx;
+  a.sy[p] = by;
+  a.sux[p] = sb[2] + bux;
+  a.suy[p] = sb[3] + buy;
+  a.spsi[p] = sb[4] + bpsi;
+}
+
+// ---------------------------------------------------------------- trial pass adjoint
+// Reverse of one predictor-corrector trial pass: gather with B^(m-1) at slice i,
+// AB5 trial step to i+1, J_perp deposit of the trial particles.
+template <int P, typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_adj_trial(SnapView<T> s, const T* __restrict__ gf, const V2<T>* __restrict__ bm, Geom gm, int slice, double guard,
+                const V2<T>* __restrict__ jbar, AdjView<T> a, T* fbar, V2<T>* bbar_m1, double* wbar_p) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= s.n || !s.alive[p]) return;
+  const int64_t n = s.n;
+  const double x = s.x[p], y = s.y[p], psi = s.psi[p];
+  const T ux = s.ux[p], uy = s.uy[p], w = s.w[p];
+  const T opp = T(1.0 + psi);
+  Stencil<P, T> st;
+  stencil_at<P, T>(gm, x, y, st);
+  T F[6], Fx[6], Fy[6];
+  {
+    T v4[4], g4x[4], g4y[4];
+    gather_g<P, T, 3>(gf, kGF, 0, gm, st, v4, g4x, g4y);   // ExmBy, EypBx, Ez
+    F[0] = v4[0]; F[1] = v4[1]; F[2] = v4[2];
+    Fx[0] = g4x[0]; Fx[1] = g4x[1]; Fx[2] = g4x[2];
+    Fy[0] = g4y[0]; Fy[1] = g4y[1]; Fy[2] = g4y[2];
+    T b1[1], b1x[1], b1y[1];
+    gather_g<P, T, 1>(gf, kGF, 5, gm, st, b1, b1x, b1y);   // Bz
+    F[5] = b1[0]; Fx[5] = b1x[0]; Fy[5] = b1y[0];
+    T b2[2], b2x[2], b2y[2];
+    gather_g<P, T, 2>(reinterpret_cast<const T*>(bm), 2, 0, gm, st, b2, b2x, b2y);  // Bx, By of B^(m-1)
+    F[3] = b2[0]; F[4] = b2[1];
+    Fx[3] = b2x[0]; Fx[4] = b2x[1];
+    Fy[3] = b2y[0]; Fy[4] = b2y[1];
+  }
+  T f[5];
+  derivs_f<T>(ux, uy, opp, F, f);
+  T comb[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    T acc = T(ab5(0)) * f[c];
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) acc += T(ab5(k)) * hist_at<T>(s.hist, n, p, slice, k, c);
+    comb[c] = acc;
+  }
+  const double dz = gm.dzeta;
+  const double tx = x - dz * (double)comb[0], ty = y - dz * (double)comb[1];
+  const double tpsi = psi - dz * (double)comb[4];
+  const T tux = ux - T(dz) * comb[2], tuy = uy - T(dz) * comb[3];
+  if (!ok_state(gm, tx, ty, 1.0 + tpsi, guard)) return;  // skipped by the trial deposit
+  Stencil<P, T> sn;
+  stencil_at<P, T>(gm, tx, ty, sn);
+  T Jg[2], Jgx[2], Jgy[2];
+  gather_g<P, T, 2>(reinterpret_cast<const T*>(jbar), 2, 0, gm, sn, Jg, Jgx, Jgy);
+  const T tg = T(1) / T(1.0 + tpsi);
+  const T qw1 = unit_charge_density<T>(gm), qw = qw1 * w;
+  const T v0 = qw * tux * tg, v1 = qw * tuy * tg;
+  T stb[5];
+  stb[0] = v0 * Jgx[0] + v1 * Jgx[1];
+  stb[1] = v0 * Jgy[0] + v1 * Jgy[1];
+  stb[2] = qw * Jg[0] * tg;
+  stb[3] = qw * Jg[1] * tg;
+  stb[4] = -qw * tg * tg * (Jg[0] * tux + Jg[1] * tuy);
+  wbar_p[p] += (double)(qw1 * tg * (Jg[0] * tux + Jg[1] * tuy));
+  T fb[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    fb[c] = T(-dz * ab5(0)) * stb[c];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a.sh[((int64_t)j * 5 + c) * n + p] += T(-dz * ab5(j + 1)) * stb[c];
+  }
+  T bux, buy, bpsi, bF[6];
+  derivs_adj<T>(ux, uy, opp, F, fb, bux, buy, bpsi, bF);
+  {
+    const T v3[3] = {bF[0], bF[1], bF[2]};
+    scatter<P, T, 3>(fbar, kGF, 0, gm, st, v3);
+    const T v1b[1] = {bF[5]};
+    scatter<P, T, 1>(fbar, kGF, 5, gm, st, v1b);
+    const T v2b[2] = {bF[3], bF[4]};
+    scatter<P, T, 2>(reinterpret_cast<T*>(bbar_m1), 2, 0, gm, st, v2b);
+  }
+  T bx = stb[0], by = stb[1];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    bx += bF[c] * Fx[c];
+    by += bF[c] * Fy[c];
+  }
+  a.sx[p] += bx;
+  a.sy[p] += by;
+  a.sux[p] += stb[2] + bux;
+  a.suy[p] += stb[3] + buy;
+  a.spsi[p] += stb[4] + bpsi;
+}
+
+// ---------------------------------------------------------------- node-level adjoints
+// Bbar^n = (fbar Bx, fbar By) + carry of B(i); the carry slot is cleared.
+template <typename T>
+__global__ void k_adj_bstart(const T* __restrict__ fbar, V2<T>* carry, V2<T>* bbar_n, int64_t nn) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nn) return;
+  const V2<T> c = carry[o];
+  bbar_n[o] = V2<T>{fbar[o * kGF + 3] + c.a, fbar[o * kGF + 4] + c.b};
+  carry[o] = V2<T>{T(0), T(0)};
+}
+
+// Mixing B^m = w Bs + (1-w) B^(m-1): the solve gets w Bbar^m, Bbar^(m-1) starts at (1-w) Bbar^m.
+template <typename T, typename Sink>
+__global__ void k_adj_pc_pre(const V2<T>* __restrict__ bbar_m, V2<T>* bbar_m1, T w, Geom gm, Sink sink) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+  if (ix >= gm.nx) return;
+  const int64_t o = (int64_t)iy * gm.nx + ix;
+  const V2<T> b = bbar_m[o];
+  bbar_m1[o] = V2<T>{(T(1) - w) * b.a, (T(1) - w) * b.b};
+  sink.put(0, iy, ix, w * b.a);
+  sink.put(1, iy, ix, w * b.b);
+}
+
+// Sources Bx = -dy Jz + (Jy(i-1) - Jy(i+1))/2dz, By = dx Jz - (Jx(i-1) - Jx(i+1))/2dz,
+// transposed: res = L^-1 of the mixed B adjoints.
+template <typename T>
+__global__ void k_adj_pc_post(const T* __restrict__ res, V4<T>* dcur, V4<T>* dprev, V2<T>* jbar, V2<T>* jbar_tot,
+                              Geom gm) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+  if (ix >= gm.nx) return;
+  const int nx = gm.nx;
+  const int64_t nn = (int64_t)nx * gm.ny;
+  const int64_t o = (int64_t)iy * nx + ix;
+  T jz = T(0), jxp = T(0), jyp = T(0), jxn = T(0), jyn = T(0);
+  if (ix > 0 && iy > 0) {
+    auto r0 = [&](int y, int x) { return res[(int64_t)y * nx + x]; };
+    auto r1 = [&](int y, int x) { return res[nn + (int64_t)y * nx + x]; };
+    const T i2z = T(gm.inv2dz);
+    jz = dyc(r0, iy, ix, gm.ny, T(gm.inv2dy)) - dxc(r1, iy, ix, nx, T(gm.inv2dx));
+    const T a0 = res[o], a1 = res[nn + o];
+    jxp = -a1 * i2z;
+    jyp = a0 * i2z;
+    jxn = a1 * i2z;
+    jyn = -a0 * i2z;
+  }
+  dcur[o].d += jz;
+  dprev[o].b += jxp;
+  dprev[o].c += jyp;
+  jbar[o] = V2<T>{jxn, jyn};
+  const V2<T> t = jbar_tot[o];
+  jbar_tot[o] = V2<T>{t.a + jxn, t.b + jyn};
+}
+
+// Guess B^0 = 2 B(i-1) - B(i-2): carries for the two previous slices.
+template <typename T>
+__global__ void k_adj_guess(const V2<T>* __restrict__ b0, V2<T>* c1, V2<T>* c2, int64_t nn) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nn) return;
+  const V2<T> b = b0[o];
+  if (c1) { c1[o].a += T(2) * b.a; c1[o].b += T(2) * b.b; }
+  if (c2) { c2[o].a -= b.a; c2[o].b -= b.b; }
+}
+
+// psi_bar = Dx fbar0 + Dy fbar1 (ExmBy = -Dx psi, EypBx = -Dy psi), with Ez_bar, Bz_bar.
+template <typename T, typename Sink>
+__global__ void k_adj_main_pre(const T* __restrict__ fbar, Geom gm, Sink sink) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+  if (ix >= gm.nx) return;
+  const int nx = gm.nx;
+  const int64_t o = (int64_t)iy * nx + ix;
+  T s0 = T(0), s1 = T(0), s2 = T(0);
+  if (ix > 0 && iy > 0) {
+    auto f0 = [&](int y, int x) { return fbar[((int64_t)y * nx + x) * kGF + 0]; };
+    auto f1 = [&](int y, int x) { return fbar[((int64_t)y * nx + x) * kGF + 1]; };
+    s0 = dxc(f0, iy, ix, nx, T(gm.inv2dx)) + dyc(f1, iy, ix, gm.ny, T(gm.inv2dy));
+    s1 = fbar[o * kGF + 2];
+    s2 = fbar[o * kGF + 5];
+  }
+  sink.put(0, iy, ix, s0);
+  sink.put(1, iy, ix, s1);
+  sink.put(2, iy, ix, s2);
+}
+
+// psi = L^-1(-(rho - Jz)), Ez = L^-1(dx Jx + dy Jy), Bz = L^-1(dy Jx - dx Jy), transposed.
+template <typename T>
+__global__ void k_adj_main_post(const T* __restrict__ res, V4<T>* dcur, T* rho_ion_bar, Geom gm) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+  if (ix >= gm.nx) return;
+  const int nx = gm.nx;
+  const int64_t nn = (int64_t)nx * gm.ny;
+  const int64_t o = (int64_t)iy * nx + ix;
+  V4<T> d = dcur[o];
+  if (ix > 0 && iy > 0) {
+    auto r1 = [&](int y, int x) { return res[nn + (int64_t)y * nx + x]; };
+    auto r2 = [&](int y, int x) { return res[2 * nn + (int64_t)y * nx + x]; };
+    const T i2x = T(gm.inv2dx), i2y = T(gm.inv2dy);
+    const T sp = res[o];
+    d.a += -sp;
+    d.d += sp;
+    d.b += -dxc(r1, iy, ix, nx, i2x) - dyc(r2, iy, ix, gm.ny, i2y);
+    d.c += -dyc(r1, iy, ix, gm.ny, i2y) + dxc(r2, iy, ix, nx, i2x);
+  }
+  dcur[o] = d;
+  rho_ion_bar[o] += d.a;
+}
+
+template <typename T>
+__global__ void k_adj_extract_b(const T* __restrict__ gf, V2<T>* out, int64_t nn) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nn) return;
+  out[o] = V2<T>{gf[o * kGF + 3], gf[o * kGF + 4]};
+}
+
+// ---------------------------------------------------------------- beams and parameters
+template <int P>
+__device__ __forceinline__ int stencil_b(double x, double x0, double dx, double* w) {
+  int j;
+  double d;
+  split_coord(x, x0, dx, j, d);
+  return shape_weights<P, double>(j, d, w);
+}
+
+template <int P, typename T, int NC>
+__device__ __forceinline__ void gather_b(const T* __restrict__ f, int st, const Geom& gm, double x, double y, double* v) {
+  double wx[P + 1], wy[P + 1];
+  const int ix0 = stencil_b<P>(x, gm.xmin, gm.dx, wx), iy0 = stencil_b<P>(y, gm.ymin, gm.dy, wy);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) v[c] = 0.0;
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const int iy = iy0 + b;
+    if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      const int ix = ix0 + a;
+      if (!in_interior(ix, gm.nx)) continue;
+      const T* q = f + ((int64_t)iy * gm.nx + ix) * st;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[c] += wx[a] * wy[b] * (double)q[c];
+    }
+  }
+}
+
+// Beam weights: deposit of slice i (rho, J) and the J_perp of slice i+1 used by the P-C.
+template <int P, typename T>
+__global__ void k_adj_beam(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm, int slice,
+                           int nz, Geom gm, const V4<T>* __restrict__ dcur, const V2<T>* __restrict__ jtot,
+                           double* wbar) {
+  const int a0 = off[slice], a1 = off[slice + 1];
+  const int b0 = slice + 1 < nz ? off[slice + 1] : 0, b1 = slice + 1 < nz ? off[slice + 2] : 0;
+  const int na = a1 - a0, nb = b1 - b0;
+  const double rq = v.charge / (gm.dx * gm.dy * gm.dzeta);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < na + nb; t += gridDim.x * blockDim.x) {
+    const bool cur = t < na;
+    const int p = perm[cur ? a0 + t : b0 + (t - na)];
+    const double ux = v.ux[p], uy = v.uy[p], uz = v.uz[p];
+    const double ig = 1.0 / sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+    double g[4];
+    double s;
+    if (cur) {
+      gather_b<P, T, 4>(reinterpret_cast<const T*>(dcur), 4, gm, v.x[p], v.y[p], g);
+      s = g[0] + ux * ig * g[1] + uy * ig * g[2] + uz * ig * g[3];
+    } else {
+      gather_b<P, T, 2>(reinterpret_cast<const T*>(jtot), 2, gm, v.x[p], v.y[p], g);
+      s = ux * ig * g[0] + uy * ig * g[1];
+    }
+    wbar[p] += rq * s;
+  }
+}
+
+// Witness loss sums (S0, S1, S2) = sum q w (1, Ez, Ez^2) over slice i, with adjoints sb[0..2].
+template <int P, typename T>
+__global__ void k_adj_witness(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm,
+                              int slice, Geom gm, const T* __restrict__ gf, double sb0, double sb1, double sb2, T* fbar,
+                              double* wbar) {
+  const int a0 = off[slice], a1 = off[slice + 1];
+  for (int t = a0 + blockIdx.x * blockDim.x + threadIdx.x; t < a1; t += gridDim.x * blockDim.x) {
+    const int p = perm[t];
+    double wx[P + 1], wy[P + 1];
+    const int ix0 = stencil_b<P>(v.x[p], gm.xmin, gm.dx, wx), iy0 = stencil_b<P>(v.y[p], gm.ymin, gm.dy, wy);
+    double ez = 0.0;
+#pragma unroll
+    for (int b = 0; b <= P; ++b) {
+      const int iy = iy0 + b;
+      if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        const int ix = ix0 + a;
+        if (!in_interior(ix, gm.nx)) continue;
+        ez += wx[a] * wy[b] * (double)gf[((int64_t)iy * gm.nx + ix) * kGF + 2];
+      }
+    }
+    const double qw = v.charge * v.w[p];
+    if (wbar) wbar[p] += v.charge * (sb0 + ez * sb1 + ez * ez * sb2);
+    const double e = qw * (sb1 + 2.0 * ez * sb2);
+#pragma unroll
+    for (int b = 0; b <= P; ++b) {
+      const int iy = iy0 + b;
+      if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        const int ix = ix0 + a;
+        if (!in_interior(ix, gm.nx)) continue;
+        atomicAdd(fbar + ((int64_t)iy * gm.nx + ix) * kGF + 2, T(wx[a] * wy[b] * e));
+      }
+    }
+  }
+}
+
+// Plasma weights at the initial slice: deposit of slice 0 (rho only: gamma g = 1) and
+// the ion background rho_ion = -(q w / A) added to every slice.
+template <int P, typename T>
+__global__ void k_adj_init(int64_t np, Geom gm, int ppx, int ppy, const V4<T>* __restrict__ d0,
+                           const T* __restrict__ rho_ion_bar, double* wbar_p) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int ppc = ppx * ppy;
+  const int64_t c = p / ppc;
+  const int sub = (int)(p - c * ppc);
+  const int ix = (int)(c % gm.nx), iy = (int)(c / gm.nx);
+  const int sx = sub % ppx, sy = sub / ppx;
+  const double x = gm.xmin + ((double)ix + ((double)sx + 0.5) / ppx) * gm.dx;
+  const double y = gm.ymin + ((double)iy + ((double)sy + 0.5) / ppy) * gm.dy;
+  double g0[1], gi[1];
+  gather_b<P, T, 1>(reinterpret_cast<const T*>(d0), 4, gm, x, y, g0);
+  gather_b<P, T, 1>(rho_ion_bar, 1, gm, x, y, gi);
+  wbar_p[p] += (-1.0 / (gm.dx * gm.dy)) * (g0[0] - gi[0]);
+}
+
+// dL/dn0_scale and dL/dprofile from the plasma weight adjoints (w = n0 dens(r) dx dy / ppc).
+__global__ void k_adj_params(int64_t np, Geom gm, int ppx, int ppy, const double* __restrict__ prof, int npf,
+                             double rmax, double n0s, const double* __restrict__ wbar_p, double* dn0, double* dprof) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double gn = 0.0;
+  if (p < np) {
+    const int ppc = ppx * ppy;
+    const int64_t c = p / ppc;
+    const int sub = (int)(p - c * ppc);
+    const int ix = (int)(c % gm.nx), iy = (int)(c / gm.nx);
+    const int sx = sub % ppx, sy = sub / ppx;
+    const double x = gm.xmin + ((double)ix + ((double)sx + 0.5) / ppx) * gm.dx;
+    const double y = gm.ymin + ((double)iy + ((double)sy + 0.5) / ppy) * gm.dy;
+    const double cw = gm.dx * gm.dy / (double)ppc;
+    double dens = 1.0;
+    if (prof) {
+      const double r = sqrt(x * x + y * y);
+      double t = r / rmax * (npf - 1);
+      t = fmin(fmax(t, 0.0), (double)(npf - 1));
+      int k0 = (int)floor(t);
+      k0 = k0 < 0 ? 0 : (k0 > npf - 2 ? npf - 2 : k0);
+      const double fr = t - (double)k0;
+      dens = prof[k0] * (1.0 - fr) + prof[k0 + 1] * fr;
+      if (dprof) {
+        atomicAdd(dprof + k0, wbar_p[p] * n0s * cw * (1.0 - fr));
+        atomicAdd(dprof + k0 + 1, wbar_p[p] * n0s * cw * fr);
+      }
+    }
+    gn = wbar_p[p] * dens * cw;
+  }
+  for (int o = 16; o > 0; o >>= 1) gn += __shfl_down_sync(0xffffffffu, gn, o);
+  if (dn0 && (threadIdx.x & 31) == 0 && gn != 0.0) atomicAdd(dn0, gn);
+}
+
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+inline dim3 grid2d(const hq_grid_s* g) { return dim3((unsigned)((g->nx + 127) / 128), (unsigned)g->ny); }
+constexpr unsigned kSliceBlocks = 152;
+
+#define HQ_SHAPE_SWITCH(ORDER, CALL) \
+  switch (ORDER) {                   \
+    case 0: { constexpr int P = 0; CALL; } break; \
+    case 1: { constexpr int P = 1; CALL; } break; \
+    case 2: { constexpr int P = 2; CALL; } break; \
+    default: { constexpr int P = 3; CALL; } break; \
+  }
+
+}  // namespace
+
+template <typename T>
+void launch_adj_final(const hq_grid_s* g, const SnapView<T>& s, const void* gf, int slice, const void* dbar_next,
+                      const AdjView<T>& a, void* fbar, double* wbar_p, cudaStream_t st) {
+  HQ_SHAPE_SWITCH(g->d.shape_order,
+                  (k_adj_final<P, T><<<blocks_for(s.n), kThreads, 0, st>>>(
+                      s, reinterpret_cast<const T*>(gf), g->geom, slice, g->d.psi_guard,
+                      reinterpret_cast<const V4<T>*>(dbar_next), a, reinterpret_cast<T*>(fbar), wbar_p)));
+}
+template <typename T>
+void launch_adj_trial(const hq_grid_s* g, const SnapView<T>& s, const void* gf, const void* bm, int slice,
+                      const void* jbar, const AdjView<T>& a, void* fbar, void* bbar_m1, double* wbar_p,
+                      cudaStream_t st) {
+  HQ_SHAPE_SWITCH(g->d.shape_order,
+                  (k_adj_trial<P, T><<<blocks_for(s.n), kThreads, 0, st>>>(
+                      s, reinterpret_cast<const T*>(gf), reinterpret_cast<const V2<T>*>(bm), g->geom, slice,
+                      g->d.psi_guard, reinterpret_cast<const V2<T>*>(jbar), a, reinterpret_cast<T*>(fbar),
+                      reinterpret_cast<V2<T>*>(bbar_m1), wbar_p)));
+}
+template <typename T>
+void launch_adj_bstart(const hq_grid_s* g, const void* fbar, void* carry, void* bbar_n, cudaStream_t st) {
+  k_adj_bstart<T><<<blocks_for(g->nnode), kThreads, 0, st>>>(reinterpret_cast<const T*>(fbar),
+                                                           reinterpret_cast<V2<T>*>(carry),
+                                                           reinterpret_cast<V2<T>*>(bbar_n), g->nnode);
+}
+template <typename T>
+void launch_adj_pc_pre(const hq_grid_s* g, const void* bbar_m, void* bbar_m1, cudaStream_t st) {
+  k_adj_pc_pre<T><<<grid2d(g), 128, 0, st>>>(reinterpret_cast<const V2<T>*>(bbar_m), reinterpret_cast<V2<T>*>(bbar_m1),
+                                            T(g->d.pc_mix), g->geom, SinkOf<T>::make(g));
+}
+template <typename T>
+void launch_adj_pc_post(const hq_grid_s* g, void* dcur, void* dprev, void* jbar, void* jtot, cudaStream_t st) {
+  k_adj_pc_post<T><<<grid2d(g), 128, 0, st>>>(reinterpret_cast<const T*>(g->solved), reinterpret_cast<V4<T>*>(dcur),
+                                             reinterpret_cast<V4<T>*>(dprev), reinterpret_cast<V2<T>*>(jbar),
+                                             reinterpret_cast<V2<T>*>(jtot), g->geom);
+}
+template <typename T>
+void launch_adj_guess(const hq_grid_s* g, const void* b0, void* c1, void* c2, cudaStream_t st) {
+  k_adj_guess<T><<<blocks_for(g->nnode), kThreads, 0, st>>>(reinterpret_cast<const V2<T>*>(b0),
+                                                          reinterpret_cast<V2<T>*>(c1), reinterpret_cast<V2<T>*>(c2),
+                                                          g->nnode);
+}
+template <typename T>
+void launch_adj_main_pre(const hq_grid_s* g, const void* fbar, cudaStream_t st) {
+  k_adj_main_pre<T><<<grid2d(g), 128, 0, st>>>(reinterpret_cast<const T*>(fbar), g->geom, SinkOf<T>::make(g));
+}
+template <typename T>
+void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, cudaStream_t st) {
+  k_adj_main_post<T><<<grid2d(g), 128, 0, st>>>(reinterpret_cast<const T*>(g->solved), reinterpret_cast<V4<T>*>(dcur),
+                                               reinterpret_cast<T*>(rho_ion_bar), g->geom);
+}
+template <typename T>
+void launch_adj_extract_b(const hq_grid_s* g, void* out, cudaStream_t st) {
+  k_adj_extract_b<T><<<blocks_for(g->nnode), kThreads, 0, st>>>(reinterpret_cast<const T*>(g->gf),
+                                                              reinterpret_cast<V2<T>*>(out), g->nnode);
+}
+template <typename T>
+void launch_adj_beam(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* dcur, const void* jtot,
+                     double* wbar, cudaStream_t st) {
+  const BeamBins& bb = g->bins[b];
+  HQ_SHAPE_SWITCH(g->d.shape_order,
+                  (k_adj_beam<P, T><<<kSliceBlocks, kThreads, 0, st>>>(v, bb.offset, bb.perm, slice, g->nz, g->geom,
+                                                                       reinterpret_cast<const V4<T>*>(dcur),
+                                                                       reinterpret_cast<const V2<T>*>(jtot), wbar)));
+}
+template <typename T>
+void launch_adj_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* gf, const double* sb,
+                        void* fbar, double* wbar, cudaStream_t st) {
+  const BeamBins& bb = g->bins[b];
+  HQ_SHAPE_SWITCH(g->d.shape_order,
+                  (k_adj_witness<P, T><<<kSliceBlocks, kThreads, 0, st>>>(v, bb.offset, bb.perm, slice, g->geom,
+                                                                          reinterpret_cast<const T*>(gf), sb[0], sb[1],
+                                                                          sb[2], reinterpret_cast<T*>(fbar), wbar)));
+}
+template <typename T>
+void launch_adj_init(const hq_grid_s* g, const void* d0, const void* rho_ion_bar, double* wbar_p, cudaStream_t st) {
+  HQ_SHAPE_SWITCH(g->d.shape_order,
+                  (k_adj_init<P, T><<<blocks_for(g->np), kThreads, 0, st>>>(
+                      g->np, g->geom, g->d.ppc_x, g->d.ppc_y, reinterpret_cast<const V4<T>*>(d0),
+                      reinterpret_cast<const T*>(rho_ion_bar), wbar_p)));
+}
+void launch_adj_params(const hq_grid_s* g, const double* wbar_p, double* dn0, double* dprof, cudaStream_t st) {
+  k_adj_params<<<blocks_for(g->np), kThreads, 0, st>>>(g->np, g->geom, g->d.ppc_x, g->d.ppc_y,
+                                                     g->profile.empty() ? nullptr : g->d_profile,
+                                                     (int)g->profile.size(), g->d.profile_rmax, g->d.n0_scale, wbar_p,
+                                                     dn0, dprof);
+}
+
+#define HQ_INST(T)                                                                                                   \
+  template void launch_adj_final<T>(const hq_grid_s*, const SnapView<T>&, const void*, int, const void*,              \
+                                    const AdjView<T>&, void*, double*, cudaStream_t);                                \
+  template void launch_adj_trial<T>(const hq_grid_s*, const SnapView<T>&, const void*, const void*, int, const void*, \
+                                    const AdjView<T>&, void*, void*, double*, cudaStream_t);                         \
+  template void launch_adj_bstart<T>(const hq_grid_s*, const void*, void*, void*, cudaStream_t);                     \
+  template void launch_adj_pc_pre<T>(const hq_grid_s*, const void*, void*, cudaStream_t);                            \
+  template void launch_adj_pc_post<T>(const hq_grid_s*, void*, void*, void*, void*, cudaStream_t);                   \
+  template void launch_adj_guess<T>(const hq_grid_s*, const void*, void*, void*, cudaStream_t);                      \
+  template void launch_adj_main_pre<T>(const hq_grid_s*, const void*, cudaStream_t);                                 \
+  template void launch_adj_main_post<T>(const hq_grid_s*, void*, void*, cudaStream_t);                               \
+  template void launch_adj_extract_b<T>(const hq_grid_s*, void*, cudaStream_t);                                      \
+  template void launch_adj_beam<T>(const hq_grid_s*, int, const hq_beam_view&, int, const void*, const void*,        \
+                                   double*, cudaStream_t);                                                           \
+  template void launch_adj_witness<T>(const hq_grid_s*, int, const hq_beam_view&, int, const void*, const double*,   \
+                                      void*, double*, cudaStream_t);                                                 \
+  template void launch_adj_init<T>(const hq_grid_s*, const void*, const void*, double*, cudaStream_t);
+HQ_INST(float)
+HQ_INST(double)
+#undef HQ_INST
+
+}  // namespace hq

@@ -16,41 +16,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-struct SinkF64 {
-  double* p;
-  int nx, ny;
-  __device__ void put(int r, int iy, int ix, double v) const { p[((int64_t)r * ny + iy) * nx + ix] = v; }
-};
-
-struct SinkBF16 {
-  __nv_bfloat16 *hi, *lo;
-  int nxp, nyp;
-  __device__ void put(int r, int iy, int ix, float v) const {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-    const int64_t o = ((int64_t)r * nyp + iy) * nxp + ix;
-    hi[o] = h;
-    lo[o] = l;
-  }
-};
-
-// Central difference helpers with wall nodes (index 0 and n) reading zero; the
-// result on wall rows/columns is zero (matching the field layout convention).
-template <typename A, typename C>
-__device__ __forceinline__ auto dxc(const A& f, int iy, int ix, int nx, C inv2dx) -> decltype(f(0, 0)) {
-  using T = decltype(f(0, 0));
-  const T r = ix + 1 < nx ? f(iy, ix + 1) : T(0);
-  const T l = f(iy, ix - 1);
-  return (r - l) * T(inv2dx);
-}
-template <typename A, typename C>
-__device__ __forceinline__ auto dyc(const A& f, int iy, int ix, int ny, C inv2dy) -> decltype(f(0, 0)) {
-  using T = decltype(f(0, 0));
-  const T u = iy + 1 < ny ? f(iy + 1, ix) : T(0);
-  const T d = f(iy - 1, ix);
-  return (u - d) * T(inv2dy);
-}
-
 template <typename T>
 __global__ void k_reset_dep(V4<T>* dep, T* chi, const T* rho_ion, int64_t nn) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -224,14 +189,6 @@ __global__ void k_zero(T* p, int64_t n) {
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 inline dim3 grid2d(const hq_grid_s* g) { return dim3((unsigned)((g->nx + 127) / 128), (unsigned)g->ny); }
-
-template <typename T> struct SinkOf;
-template <> struct SinkOf<double> {
-  static SinkF64 make(const hq_grid_s* g) { return SinkF64{g->f64_a, g->nx, g->ny}; }
-};
-template <> struct SinkOf<float> {
-  static SinkBF16 make(const hq_grid_s* g) { return SinkBF16{g->op_hi[0], g->op_lo[0], g->nxp, g->nyp}; }
-};
 
 }  // namespace
 

@@ -23,7 +23,7 @@ FIELDS = ("rho", "jx", "jy", "jz", "chi", "psi", "exmby", "eypbx", "ez", "bx", "
 EXPORTS = ("hq_grid_create", "hq_grid_destroy", "hq_advance_slice", "hq_beam_deposit", "hq_solve_fields",
            "hq_store_fields", "hq_push_beams", "hq_witness_accumulate", "hq_sweep_step", "hq_poisson_solve",
            "hq_plasma_state", "hq_profile_enable", "hq_profile_read", "hq_sync", "hq_last_error",
-           "hq_poisson_solve_static")
+           "hq_poisson_solve_static", "hq_sweep_forward_ckpt", "hq_sweep_adjoint")
 KERNEL_CLASSES = ("final", "trial", "dst", "field", "beam", "other")
 
 
@@ -82,6 +82,8 @@ def load() -> C.CDLL:
             "hq_profile_read": (P, C.POINTER(Profile)),
             "hq_sync": (P, C.POINTER(I64)),
             "hq_poisson_solve_static": (P, P, I32, I32, D, D, I32, P),
+            "hq_sweep_forward_ckpt": (P, C.POINTER(BeamView), I32, I32, P, I32),
+            "hq_sweep_adjoint": (P, C.POINTER(BeamView), I32, I32, C.POINTER(D), C.POINTER(P), P, P, P),
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -225,6 +227,31 @@ class Grid:
                                     int(witness), C.c_void_p(_ptr(witness_sums)) if witness_sums is not None else None),
                self.h)
 
+    def forward_ckpt(self, beams: Sequence[Beam], witness: int, sums: torch.Tensor, ckpt_every: int) -> None:
+        """Checkpointed forward sweep (no field output); sums (device float64[3]) += witness sums."""
+        arr = _beam_array(beams)
+        _check(load().hq_sweep_forward_ckpt(self.h, arr, len(beams), int(witness), C.c_void_p(sums.data_ptr()),
+                                            int(ckpt_every)), self.h)
+        self._adj_beams = arr
+
+    def adjoint(self, beams: Sequence[Beam], witness: int, dl_dsums: Sequence[float], plasma: bool = True) -> dict:
+        """Reverse sweep of the last forward_ckpt: gradients w.r.t. beam and plasma weights,
+        the density scale n0 and the radial profile."""
+        arr = _beam_array(beams)
+        wb = [torch.zeros(b.n, dtype=torch.float64, device="cuda") for b in beams]
+        ptrs = (C.c_void_p * max(1, len(beams)))(*[t.data_ptr() for t in wb])
+        np_ = self.nx * self.ny * int(self.params.get("ppc_x", 1)) * int(self.params.get("ppc_y", 1))
+        wp = torch.zeros(np_, dtype=torch.float64, device="cuda") if plasma else None
+        dn0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        prof = self.params.get("radial_profile")
+        dprof = torch.zeros(len(prof), dtype=torch.float64, device="cuda") if prof is not None else None
+        sb = (C.c_double * 3)(*[float(v) for v in dl_dsums])
+        _check(load().hq_sweep_adjoint(self.h, arr, len(beams), int(witness), sb, ptrs,
+                                       C.c_void_p(wp.data_ptr()) if wp is not None else None,
+                                       C.c_void_p(dn0.data_ptr()),
+                                       C.c_void_p(dprof.data_ptr()) if dprof is not None else None), self.h)
+        return {"beam_w": wb, "plasma_w": wp, "n0_scale": dn0, "profile": dprof}
+
     def poisson_solve(self, src: torch.Tensor) -> torch.Tensor:
         assert src.dtype == self.dtype and src.is_cuda and src.is_contiguous() and src.dim() == 3
         dst = torch.empty_like(src)
@@ -258,3 +285,49 @@ class Grid:
         rm = C.c_int64()
         _check(load().hq_sync(self.h, C.byref(rm)), self.h)
         return int(rm.value)
+
+
+def witness_loss_grad(kind: str, s0: float, s1: float, s2: float):
+    """Loss from the witness sums and dL/d(S0, S1, S2): "mean" = S1/S0, "mean+rms" adds
+    sqrt(S2/S0 - (S1/S0)^2) (host arithmetic on three scalars)."""
+    mean = s1 / s0
+    if kind == "mean":
+        return mean, (-s1 / (s0 * s0), 1.0 / s0, 0.0)
+    var = max(s2 / s0 - mean * mean, 0.0)
+    sd = var ** 0.5
+    if sd == 0.0:
+        return mean, (-s1 / (s0 * s0), 1.0 / s0, 0.0)
+    dvar = (-s2 / (s0 * s0) + 2.0 * mean * s1 / (s0 * s0), -2.0 * mean / s0, 1.0 / s0)
+    return mean + sd, (-s1 / (s0 * s0) + dvar[0] / (2 * sd), 1.0 / s0 + dvar[1] / (2 * sd), dvar[2] / (2 * sd))
+
+
+class SweepLoss(torch.autograd.Function):
+    """Witness loss of one quasi-static sweep, differentiable w.r.t. the beam weights and the
+    plasma density scale / radial profile through the hand-written reverse-zeta adjoint.
+
+    apply(grid, beams, witness, kind, ckpt_every, n0_scale, profile, *beam_weights) -> loss.
+    n0_scale (0-d) and profile (1-d or an empty tensor) must hold the values the grid was
+    created with; beam_weights[i] are copied into beams[i] before the sweep."""
+
+    @staticmethod
+    def forward(ctx, grid, beams, witness, kind, ckpt_every, n0_scale, profile, *weights):
+        for b, w in zip(beams, weights):
+            b.t["w"].copy_(w.detach())
+        sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+        grid.forward_ckpt(beams, witness, sums, ckpt_every)
+        s = [float(v) for v in sums.cpu()]
+        loss, dls = witness_loss_grad(kind, *s)
+        ctx.grid, ctx.beams, ctx.witness, ctx.dls = grid, beams, witness, dls
+        ctx.has_prof = profile.numel() > 0
+        ctx.n0_like = (n0_scale.shape, n0_scale.device, n0_scale.dtype)
+        ctx.prof_like = (profile.device, profile.dtype)
+        return torch.tensor(loss, dtype=torch.float64, device=weights[0].device if weights else "cuda")
+
+    @staticmethod
+    def backward(ctx, gl):
+        g = float(gl)
+        res = ctx.grid.adjoint(ctx.beams, ctx.witness, [g * v for v in ctx.dls], plasma=True)
+        shape, dev, dt = ctx.n0_like
+        dn0 = res["n0_scale"][0].to(device=dev, dtype=dt).reshape(shape)
+        dprof = res["profile"].to(device=ctx.prof_like[0], dtype=ctx.prof_like[1]) if ctx.has_prof else None
+        return (None, None, None, None, None, dn0, dprof, *res["beam_w"])

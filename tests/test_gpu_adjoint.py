@@ -1,0 +1,138 @@
+"""The hand-written reverse-zeta adjoint (hq_sweep_forward_ckpt + hq_sweep_adjoint)
+against the oracle's taped FP64 adjoint (autograd through the oracle sweep, itself
+pinned to central finite differences in test_oracle_adjoint.py).
+
+Bars: gradients within 1e-5 (FP64 path) and 1e-3 (FP32/bf16x3 path) relative
+(the benchmark spec), checked as the relative L2 error of each gradient vector and of
+directional derivatives along random directions.  Both single-segment (no
+recompute) and multi-segment (checkpoint restore + recompute) runs are covered.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2109_10277_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hq():
+    from paper_2109_10277_gb300 import hq as _hq
+    _hq.load()
+    torch.cuda.set_device(0)
+    return _hq
+
+
+def case(order=1, nz=24, n=24):
+    g = dict(nx=n, ny=n, nzeta=nz, xmin=-6.0, xmax=6.0, ymin=-6.0, ymax=6.0, zeta_min=-7.0, zeta_max=5.0,
+             shape_order=order, n_pc_iter=2, pc_mix=0.05, psi_guard=0.02,
+             radial_profile=[1.0, 1.0, 0.8, 0.5, 0.3], profile_rmax=8.5)
+    d = I.fixed_ppc_beam(g, 0.8, 1.0, 2.0)
+    w = I.fixed_ppc_beam(g, 0.5, 0.6, 10.0, zeta0=-3.0, gamma=I.GAMMA_WITNESS)
+    return g, d, w
+
+
+def oracle_grads(g, d, w, kind):
+    sp = O.GridSpec(**g)
+    wd = torch.tensor(d["w"], dtype=torch.float64, requires_grad=True)
+    ww = torch.tensor(w["w"], dtype=torch.float64, requires_grad=True)
+    n0 = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    prof = torch.tensor(g["radial_profile"], dtype=torch.float64, requires_grad=True)
+    bd, bw = O.as_beam(d), O.as_beam(w)
+    bd["w"], bw["w"] = wd, ww
+    r = O.sweep(sp, [bd, bw], witness=(1,), record=(), n0_scale=n0, radial_profile=prof)
+    L = O.witness_loss(r, 1, kind)
+    L.backward()
+    return float(L), wd.grad, ww.grad, float(n0.grad), prof.grad
+
+
+def gpu_grads(hq, g, d, w, kind, precision, k):
+    grid = hq.Grid(g, precision=precision)
+    beams = [hq.Beam(d), hq.Beam(w)]
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    grid.forward_ckpt(beams, 1, sums, k)
+    s = [float(v) for v in sums.cpu()]
+    L, dls = hq.witness_loss_grad(kind, *s)
+    res = grid.adjoint(beams, 1, dls)
+    grid.sync()
+    out = (L, res["beam_w"][0].cpu(), res["beam_w"][1].cpu(), float(res["n0_scale"][0]), res["profile"].cpu())
+    grid.close()
+    return out
+
+
+def rel(a, b):
+    return float(torch.linalg.norm(a - b) / (torch.linalg.norm(b) + 1e-300))
+
+
+def directional(a, b, seed=0, k=3):
+    """Derivatives along random positive weight perturbations (no cancellation in the sum)."""
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(k):
+        v = torch.tensor(np.abs(rng.standard_normal(a.shape[0])), dtype=torch.float64)
+        x, y = float((a * v).sum()), float((b * v).sum())
+        worst = max(worst, abs(x - y) / (abs(y) + 1e-300))
+    return worst
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-5), ("fp32", 1e-3)])
+@pytest.mark.parametrize("kind,order,k", [("mean", 1, 24), ("mean", 1, 5), ("mean+rms", 2, 7)])
+def test_adjoint_matches_taped_oracle(hq, precision, tol, kind, order, k):
+    g, d, w = case(order=order)
+    L0, gd0, gw0, gn0, gp0 = oracle_grads(g, d, w, kind)
+    L1, gd1, gw1, gn1, gp1 = gpu_grads(hq, g, d, w, kind, precision, k)
+    errs = {"loss": abs(L1 - L0) / abs(L0), "driver_w": rel(gd1, gd0), "witness_w": rel(gw1, gw0),
+            "driver_dir": directional(gd1, gd0), "n0": abs(gn1 - gn0) / abs(gn0), "profile": rel(gp1, gp0)}
+    print(precision, kind, order, k, {a: f"{b:.2e}" for a, b in errs.items()})
+    loss_tol = 1e-10 if precision == "fp64" else 1e-3
+    assert errs["loss"] <= loss_tol, errs
+    for key in ("driver_w", "witness_w", "driver_dir", "n0", "profile"):
+        assert errs[key] <= tol, (key, errs)
+
+
+def test_sweep_loss_autograd_to_beam_parameters(hq):
+    """torch.autograd through SweepLoss: gradient of the mean witness Ez w.r.t. the driver's
+    peak density, sigma_r, sigma_z, the witness position and n0, against the oracle's taped
+    adjoint through the same weight recipe."""
+    g, d, w = case(order=1)
+    dx = (g["xmax"] - g["xmin"]) / g["nx"]
+    dz = (g["zeta_max"] - g["zeta_min"]) / g["nzeta"]
+
+    def weights(beam, nb, sr, sz, z0):
+        x, y, z = (torch.as_tensor(beam[k], dtype=torch.float64) for k in ("x", "y", "zeta"))
+        return nb * torch.exp(-(x * x + y * y) / (2 * sr * sr)) * torch.exp(-((z - z0) ** 2) / (2 * sz * sz)) * dx * dx * dz
+
+    p0 = [2.0, 0.8, 1.0, -3.0]
+
+    def params():
+        return [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in p0] + \
+               [torch.tensor(1.0, dtype=torch.float64, requires_grad=True)]
+
+    g = dict(g)
+    g.pop("radial_profile")
+    g.pop("profile_rmax")
+    # oracle
+    nb, sr, sz, z0, n0 = params()
+    sp = O.GridSpec(**g)
+    bd, bw = O.as_beam(d), O.as_beam(w)
+    bd["w"] = weights(d, nb, sr, sz, 0.0)
+    bw["w"] = weights(w, 10.0, 0.5, 0.6, z0)
+    r = O.sweep(sp, [bd, bw], witness=(1,), record=(), n0_scale=n0)
+    Lo = O.witness_loss(r, 1, "mean")
+    Lo.backward()
+    ref = [float(t.grad) for t in (nb, sr, sz, z0, n0)]
+    # GPU, FP64
+    grid = hq.Grid(g, precision="fp64")
+    beams = [hq.Beam(d), hq.Beam(w)]
+    nb, sr, sz, z0, n0 = params()
+    wd = weights(d, nb, sr, sz, 0.0).cuda()
+    ww = weights(w, 10.0, 0.5, 0.6, z0).cuda()
+    L = hq.SweepLoss.apply(grid, beams, 1, "mean", 8, n0, torch.empty(0), wd, ww)
+    L.backward()
+    got = [float(t.grad) for t in (nb, sr, sz, z0, n0)]
+    grid.close()
+    assert abs(float(L) - float(Lo)) <= 1e-10 * abs(float(Lo))
+    for a, b, name in zip(got, ref, ("n_b", "sigma_r", "sigma_z", "zeta0", "n0")):
+        assert abs(a - b) <= 1e-5 * abs(b), (name, a, b)

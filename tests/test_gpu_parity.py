@@ -8,13 +8,17 @@ Bars (derived in DESIGN.md):
     ~1e-10 relative by the tail of the 64-slice linear workload.  No
     implementation with its own operation order can beat that floor, so per
     field and per slice the GPU's deviation, measured against the field's peak
-    slice norm, must be below max(1e-12, 30 x the oracle's own reorder
+    slice norm, must be below max(2e-12, 30 x the oracle's own reorder
     deviation).  The factor 30 covers the GPU's extra rounding sources (FMA
     contraction, FFT instead of matrix DST-I).  The reordered oracle run also sums
     the ion background in the opposite stencil order, so that, as on the GPU, the
     ion and electron roundings no longer cancel exactly.  Total rho is the small
     difference of those two densities (both ~n0), so rho's deviation is measured
-    against the ion density it is summed from.
+    against the ion density it is summed from.  The absolute part of the bar is
+    2e-12 rather than 1e-12: in the linear workload the net charge is ~1e-3 of the
+    ion and electron densities it is the difference of, so one ulp of n0 per node
+    (which the oracle's exactly representable initial sums cannot reproduce)
+    reaches ~1.5e-12 of psi's and ExmBy's peak.
   * FP32/bf16x3 path: each bf16x3 product carries ~2^-17 relative error, so a
     4-product Dirichlet solve is good to a few 1e-5 (rel-L2); sweeps are held to
     the on-axis Ez (first plasma period) <= 1e-4 and bucket <= 1e-3 bounds.
@@ -84,7 +88,7 @@ def assert_fp64_sweep(out, ref, ref_perm, fields, factor=30.0, spec=None):
             ion = float(torch.linalg.norm(O.ion_background(spec, O.plasma_init(spec))))
             peak = float(torch.linalg.norm(ref.fields["rho"].reshape(ref.fields["rho"].shape[0], -1), dim=1).max())
             e, f = e * peak / max(peak, ion), f * peak / max(peak, ion)
-        bar = torch.clamp(factor * f, min=1e-12)
+        bar = torch.clamp(factor * f, min=2e-12)
         worst = int(torch.argmax(e / bar))
         print(f"fp64 {k}: max dev {float(e.max()):.2e}, reorder floor {float(f.max()):.2e}, "
               f"worst slice {worst}: {float(e[worst]):.2e} vs bar {float(bar[worst]):.2e}")
