@@ -423,7 +423,8 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
           n_slices: Optional[int] = None, record: Sequence[str] = FIELD_NAMES,
           witness: Sequence[int] = (), record_plasma_at: Sequence[int] = (),
           n0_scale: Optional[torch.Tensor] = None, radial_profile: Optional[torch.Tensor] = None,
-          plasma_perm: Optional[torch.Tensor] = None, reverse_ion_order: bool = False) -> SweepResult:
+          plasma_perm: Optional[torch.Tensor] = None, reverse_ion_order: bool = False,
+          deposit_noise: float = 0.0, noise_seed: int = 0) -> SweepResult:
     """One quasi-static sweep head -> tail (Sec. 2), slices i = 0 .. n_slices-1.
 
     Per slice (Sec. 2 steps 1-7 and the Sec. 3.2 predictor-corrector):
@@ -434,6 +435,9 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     which particle contributions are summed; results are returned in the original order.
     reverse_ion_order sums the ion background in the opposite stencil order, so its
     rounding no longer cancels the electrons' exactly (again the same arithmetic).
+    deposit_noise > 0 multiplies every plasma (and ion) deposit node value by
+    (1 + deposit_noise * U(-1, 1)): a rounding-size perturbation, like the one an
+    unordered (atomic) summation leaves, used to measure the sweep's sensitivity.
     """
     ns = spec.nzeta if n_slices is None else n_slices
     dz = spec.dzeta
@@ -442,6 +446,15 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     if plasma_perm is not None:
         st = {k: v[plasma_perm] for k, v in st.items()}
     rho_ion = ion_background(spec, st, reverse=reverse_ion_order)
+    gen = torch.Generator().manual_seed(noise_seed)
+
+    def noisy(fields):
+        if deposit_noise <= 0.0:
+            return fields
+        return [f * (1.0 + deposit_noise * (2.0 * torch.rand(f.shape, generator=gen, dtype=DT) - 1.0))
+                for f in fields]
+
+    rho_ion = noisy([rho_ion])[0]
     zero = torch.zeros(spec.ny, spec.nx, dtype=DT)
     hist = [(torch.zeros_like(st["x"]),) * 5 for _ in range(4)]  # f_{i-1} .. f_{i-4}
     beams = [dict(b) for b in beams]
@@ -454,7 +467,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     jx_prev, jy_prev = zero, zero
     b1 = (zero, zero)
     b2 = (zero, zero)
-    src = plasma_deposit_full(spec, st)
+    src = noisy(plasma_deposit_full(spec, st))
     for i in range(ns):
         if i in record_plasma_at:
             res.plasma_at[i] = {k: v.detach().clone() for k, v in st.items()}
@@ -481,7 +494,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
             tx, ty, tux, tuy, tpsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
                                               [f] + hist, dz)
             ok = st["alive"] & _state_ok(spec, tx, ty, tpsi)
-            pjx, pjy = plasma_deposit_jperp(spec, tx, ty, tux, tuy, tpsi, st["w"], ok)
+            pjx, pjy = noisy(plasma_deposit_jperp(spec, tx, ty, tux, tuy, tpsi, st["w"], ok))
             jx1, jy1 = pjx + njx, pjy + njy
             dzjx, dzjy = (jx_prev - jx1) / (2.0 * dz), (jy_prev - jy1) / (2.0 * dz)
             bxs = poisson_solve(spec, sbx0 + dzjy)
@@ -517,7 +530,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
         keep = lambda new, old: torch.where(alive, new, old)  # noqa: E731
         st = dict(x=keep(nx_, st["x"]), y=keep(ny_, st["y"]), ux=keep(nux, st["ux"]),
                   uy=keep(nuy, st["uy"]), psi=keep(npsi, st["psi"]), w=st["w"], alive=alive)
-        src = plasma_deposit_full(spec, st)
+        src = noisy(plasma_deposit_full(spec, st))
         jx_prev, jy_prev = jx, jy
         b2, b1 = b1, (bx, by)
     res.fields = {k: torch.stack(v) for k, v in rec.items()}

@@ -4,6 +4,7 @@
 // and the full sweep.  Host code only orders launches on the grid's stream.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -220,8 +221,14 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
     tape_b_iterate<T>(g, m);
     { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, s); }
     { Prof p(g, HQ_K_FIELD, 1); launch_src_bperp<T>(g, cur, prev, chi_prev, last, s); }
-    dst_solve(g, 2);
-    { Prof p(g, HQ_K_FIELD, 1); launch_finish_bperp<T>(g, g->solved, last, s); }
+    if (g->fp64) {
+      dst_solve(g, 2);
+      Prof p(g, HQ_K_FIELD, 1);
+      launch_finish_bperp<T>(g, g->solved, last, s);
+    } else {
+      Prof p(g, HQ_K_DST, 4);   // the mixing runs in the last product's epilogue
+      dst_solve_tc_bmix(g, last, s);
+    }
   }
   if (npc == 0) {
     // no predictor-corrector: B(i) is the guess; shift, clear and reset without the fused kernels
@@ -523,6 +530,14 @@ hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witn
 }  // namespace
 
 namespace hq {
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("HQ_NO_PDL");
+    return !(e && e[0] == '1');
+  }();
+  return on;
+}
+
 // Error message for calls that have no grid (read back by hq_last_error(NULL)).
 void set_global_error(const std::string& msg) { g_global_err = msg; }
 }  // namespace hq
@@ -582,6 +597,11 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   gm.inv2dx = 0.5 / gm.dx;
   gm.inv2dy = 0.5 / gm.dy;
   gm.inv2dz = 0.5 / gm.dzeta;
+  gm.f_dz = (float)gm.dzeta;
+  gm.f_dz_inv_dx = (float)(gm.dzeta * gm.inv_dx);
+  gm.f_dz_inv_dy = (float)(gm.dzeta * gm.inv_dy);
+  gm.f_inv_area = (float)gm.inv_area;
+  gm.f_guard = (float)d.psi_guard;
   g->last_adv = g->last_beam = g->last_solved = -1;
 
   auto bail = [&](hq_status st) {

@@ -7,6 +7,7 @@
 #include <cuda.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/hq.h"
@@ -36,6 +37,8 @@ struct Geom {
   double xmax, ymax;
   double inv_area;  // 1 / (dx dy)
   double inv2dx, inv2dy, inv2dz;  // 1/(2 dx), 1/(2 dy), 1/(2 dzeta): central differences
+  // FP32 copies for the FP32 kernels (no per-thread double-to-float conversion)
+  float f_dz, f_dz_inv_dx, f_dz_inv_dy, f_inv_area, f_guard;
 };
 
 // Geometry constants in the kernel's arithmetic type (no per-thread FP64 division).
@@ -157,6 +160,25 @@ struct hq_grid_s {
 
 namespace hq {
 
+// Programmatic dependent launch is on unless the environment sets HQ_NO_PDL=1.
+bool pdl_enabled();
+
+// Launch with programmatic stream serialization (see pdl_wait / pdl_trigger).
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // ---------------------------------------------------------------- launchers (kernels in *.cu)
 // particles
 template <typename T> void launch_plasma_init(const hq_grid_s* g, cudaStream_t s);
@@ -182,6 +204,7 @@ template <typename T> void launch_zero(void* p, int64_t n, cudaStream_t s);
 // DST backends: transform the nrhs sources prepared by the src kernels into g->solved
 void dst_solve_f64(hq_grid_s* g, int nrhs, cudaStream_t s);
 void dst_solve_tc(hq_grid_s* g, int nrhs, cudaStream_t s);
+void dst_solve_tc_bmix(hq_grid_s* g, int last, cudaStream_t s);   // B_perp solve + fused mixing (FP32)
 int dst_tc_init(hq_grid_s* g, std::string& err);   // builds tensor maps; 0 on success
 void dst_tc_free(hq_grid_s* g);
 // beams
@@ -215,6 +238,13 @@ void launch_adj_params(const hq_grid_s* g, const double* wbar_p, double* dn0, do
 
 // ---------------------------------------------------------------- device helpers
 namespace hq {
+
+// Programmatic dependent launch: a kernel launched with launch_pdl may start while
+// the previous kernel in the stream is still running; it must call pdl_wait()
+// before touching memory that kernel reads or writes.  pdl_trigger() lets the next
+// kernel be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // B-spline weights of order P from the cell index jf = floor(u) and the fraction
 // d = u - jf in [0, 1).  Node j0 + a carries weight w[a] (Sec. 3.2 deposition, orders 0-3).

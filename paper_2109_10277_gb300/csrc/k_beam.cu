@@ -88,6 +88,8 @@ __device__ __forceinline__ int stencil_t(double x, double x0, double dx, double 
 template <int P, typename T>
 __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm,
                                int slice, int nz, Geom gm, V4<T>* dep, V2<T>* bjn) {
+  pdl_trigger();
+  pdl_wait();
   const int a0 = off[slice], a1 = off[slice + 1];
   const int b0 = slice + 1 < nz ? off[slice + 1] : 0, b1 = slice + 1 < nz ? off[slice + 2] : 0;
   const int na = a1 - a0, nb = b1 - b0;
@@ -158,6 +160,8 @@ __device__ __forceinline__ void gather_all(const T* __restrict__ gf, const Geom&
 template <int P, typename T>
 __global__ void k_beam_push(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm,
                             int slice, Geom gm, const T* __restrict__ gf, double dt) {
+  pdl_trigger();
+  pdl_wait();
   const int a0 = off[slice], a1 = off[slice + 1];
   const double qm = v.charge / v.mass, h = 0.5 * dt;
   for (int t = a0 + blockIdx.x * blockDim.x + threadIdx.x; t < a1; t += gridDim.x * blockDim.x) {
@@ -203,6 +207,8 @@ __global__ void k_beam_push(hq_beam_view v, const int32_t* __restrict__ off, con
 template <int P, typename T>
 __global__ void k_witness(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm, int slice,
                           Geom gm, const T* __restrict__ gf, double* sums) {
+  pdl_trigger();
+  pdl_wait();
   const int a0 = off[slice], a1 = off[slice + 1];
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int t = a0 + blockIdx.x * blockDim.x + threadIdx.x; t < a1; t += gridDim.x * blockDim.x) {
@@ -267,23 +273,22 @@ template <typename T>
 void launch_beam_deposit(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, void* dep, void* bjn, cudaStream_t s) {
   const BeamBins& bb = g->bins[b];
   HQ_SHAPE_SWITCH(g->d.shape_order,
-                  (k_beam_deposit<P, T><<<kSliceBlocks, kThreads, 0, s>>>(v, bb.offset, bb.perm, slice, g->nz, g->geom,
-                                                                          reinterpret_cast<V4<T>*>(dep),
-                                                                          reinterpret_cast<V2<T>*>(bjn))));
+                  (launch_pdl(k_beam_deposit<P, T>, dim3(kSliceBlocks), dim3(kThreads), (size_t)0, s, v, bb.offset, bb.perm,
+                             slice, g->nz, g->geom, reinterpret_cast<V4<T>*>(dep), reinterpret_cast<V2<T>*>(bjn))));
 }
 template <typename T>
 void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double dt, cudaStream_t s) {
   const BeamBins& bb = g->bins[b];
   HQ_SHAPE_SWITCH(g->d.shape_order,
-                  (k_beam_push<P, T><<<kSliceBlocks, kThreads, 0, s>>>(v, bb.offset, bb.perm, slice, g->geom,
-                                                                       reinterpret_cast<const T*>(g->gf), dt)));
+                  (launch_pdl(k_beam_push<P, T>, dim3(kSliceBlocks), dim3(kThreads), (size_t)0, s, v, bb.offset, bb.perm,
+                             slice, g->geom, reinterpret_cast<const T*>(g->gf), dt)));
 }
 template <typename T>
 void launch_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double* sums, cudaStream_t s) {
   const BeamBins& bb = g->bins[b];
   HQ_SHAPE_SWITCH(g->d.shape_order,
-                  (k_witness<P, T><<<kSliceBlocks, kThreads, 0, s>>>(v, bb.offset, bb.perm, slice, g->geom,
-                                                                     reinterpret_cast<const T*>(g->gf), sums)));
+                  (launch_pdl(k_witness<P, T>, dim3(kSliceBlocks), dim3(kThreads), (size_t)0, s, v, bb.offset, bb.perm,
+                             slice, g->geom, reinterpret_cast<const T*>(g->gf), sums)));
 }
 #undef HQ_SHAPE_SWITCH
 

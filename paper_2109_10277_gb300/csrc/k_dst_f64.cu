@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(kThreads) k_dst_fft_pass(const double* __restr
                                                            int n, int logL, int M, const double2* __restrict__ tw,
                                                            const double* __restrict__ scale) {
   extern __shared__ double2 sm[];
+  pdl_trigger();
+  pdl_wait();
   const int L = 2 * n;
   double2* twid = sm;
   double2* buf = sm + n;
@@ -80,6 +82,8 @@ __global__ void __launch_bounds__(kThreads) k_dst_fft_pass(const double* __restr
 // Direct sum for any n: sn[j*n + k] = sin(pi j k / n).
 __global__ void k_dst_direct_pass(const double* __restrict__ in, double* __restrict__ out, int n, int M,
                                   const double* __restrict__ sn, const double* __restrict__ scale) {
+  pdl_trigger();
+  pdl_wait();
   const int r = blockIdx.y;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * M) return;
@@ -103,7 +107,8 @@ void fft_pass(const double* in, double* out, int n, int M, int R, const double* 
     attr_set = true;
   }
   dim3 grid((unsigned)((M + G - 1) / G), (unsigned)R);
-  k_dst_fft_pass<G><<<grid, kThreads, smem, s>>>(in, out, n, ilog2(2 * n), M, reinterpret_cast<const double2*>(tw), scale);
+  launch_pdl(k_dst_fft_pass<G>, grid, dim3(kThreads), smem, s, in, out, n, ilog2(2 * n), M,
+             reinterpret_cast<const double2*>(tw), scale);
 }
 
 void pass(const double* in, double* out, int n, int M, int R, const double* tw, const double* sn, const double* scale,
@@ -115,7 +120,7 @@ void pass(const double* in, double* out, int n, int M, int R, const double* tw, 
     else fft_pass<2>(in, out, n, M, R, tw, scale, s);
   } else {
     dim3 grid((unsigned)(((int64_t)n * M + kThreads - 1) / kThreads), (unsigned)R);
-    k_dst_direct_pass<<<grid, kThreads, 0, s>>>(in, out, n, M, sn, scale);
+    launch_pdl(k_dst_direct_pass, grid, dim3(kThreads), (size_t)0, s, in, out, n, M, sn, scale);
   }
 }
 

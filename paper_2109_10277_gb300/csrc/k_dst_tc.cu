@@ -52,7 +52,8 @@ template <int BN> struct Cfg {
 };
 
 struct Epi {
-  int mode;          // 0: split + transposed bf16 store; 1: scale, split, store; 2: FP32 transposed store
+  int mode;          // 0: split + transposed bf16 store; 1: scale, split, store; 2: FP32 transposed store;
+                     // 3: predictor-corrector mixing of (Bx, By) into the gather record
   int P1;            // rows per right-hand side (padded), i.e. m extent per rhs
   int P2;            // padded n extent
   __nv_bfloat16* out_hi;
@@ -60,6 +61,14 @@ struct Epi {
   const float* scale;   // [P2][P1]
   float* out_f32;       // [R][n_real][m_real]
   int m_real, n_real;
+  // mode 3: B <- w B_solved + (1 - w) B in gf[node*8 + 3 + r]; last: B(i-2) <- B(i-1) <- B, clear bjn
+  float* gf;
+  float* b1;
+  float* b2;
+  float* bjn;
+  float w;
+  int last;
+  int* status;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -177,6 +186,9 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // everything above overlaps the previous kernel (programmatic dependent launch)
+  pdl_trigger();
+  pdl_wait();
 
   if (warp == 0 && lane == 0) {
     // TMA producer
@@ -231,12 +243,44 @@ __global__ void __launch_bounds__(128, 1)
           if (n < ep.n_real) ep.out_f32[((int64_t)r * ep.n_real + n) * ep.m_real + ml] = __uint_as_float(v[j]);
         }
       }
+    } else if (ep.mode == 3) {
+      if (ml < ep.m_real) {
+        // two phases: all loads of the chunk first, then the mixing and stores
+        float old[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          old[j] = n < ep.n_real ? ep.gf[((int64_t)n * ep.m_real + ml) * kGF + 3 + r] : 0.0f;
+        }
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n >= ep.n_real) continue;
+          const float x = __uint_as_float(v[j]);
+          bad |= !isfinite(x);
+          const int64_t node = (int64_t)n * ep.m_real + ml;
+          const float nb = ep.w * x + (1.0f - ep.w) * old[j];
+          ep.gf[node * kGF + 3 + r] = nb;
+          if (ep.last) {
+            ep.b2[node * 2 + r] = ep.b1[node * 2 + r];
+            ep.b1[node * 2 + r] = nb;
+            ep.bjn[node * 2 + r] = 0.0f;
+          }
+        }
+        if (bad) atomicOr(ep.status, DEV_NONFINITE);
+      }
     } else {
+      float sc[32];
+      if (ep.mode == 1) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sc[j] = __ldg(ep.scale + (int64_t)(n0 + c0 + j) * ep.P1 + ml);
+      }
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int n = n0 + c0 + j;
         float x = __uint_as_float(v[j]);
-        if (ep.mode == 1) x *= __ldg(ep.scale + (int64_t)n * ep.P1 + ml);
+        if (ep.mode == 1) x *= sc[j];
         const __nv_bfloat16 h = __float2bfloat16_rn(x);
         const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
         const int64_t o = ((int64_t)r * ep.P2 + n) * ep.P1 + ml;
@@ -278,10 +322,10 @@ void gemm(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap* bh, c
           int K, const Epi& ep, int* status, cudaStream_t s) {
   if (pick_bn(M, N) == 128) {
     dim3 grid((unsigned)(M / BM), (unsigned)(N / 128));
-    k_dst_gemm<128><<<grid, 128, Cfg<128>::SMEM_BYTES, s>>>(ah, al, bh[0], bl[0], K, ep, status);
+    launch_pdl(k_dst_gemm<128>, grid, dim3(128), (size_t)Cfg<128>::SMEM_BYTES, s, ah, al, bh[0], bl[0], K, ep, status);
   } else {
     dim3 grid((unsigned)(M / BM), (unsigned)(N / 64));
-    k_dst_gemm<64><<<grid, 128, Cfg<64>::SMEM_BYTES, s>>>(ah, al, bh[1], bl[1], K, ep, status);
+    launch_pdl(k_dst_gemm<64>, grid, dim3(128), (size_t)Cfg<64>::SMEM_BYTES, s, ah, al, bh[1], bl[1], K, ep, status);
   }
 }
 
@@ -324,6 +368,24 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
 void dst_tc_free(hq_grid_s* g) {
   delete g->tmaps;
   g->tmaps = nullptr;
+}
+
+// B_perp solve with the predictor-corrector mixing fused into the last product's epilogue:
+// sources (split, 2 rhs) in op[0] -> gf[3..4] <- w B + (1 - w) gf[3..4] (+ ring shift if last).
+void dst_solve_tc_bmix(hq_grid_s* g, int last, cudaStream_t s) {
+  const TensorMaps& t = *g->tmaps;
+  const int nxp = g->nxp, nyp = g->nyp, R = 2;
+  Epi e{};
+  e = Epi{0, nyp, nxp, g->op_hi[1], g->op_lo[1], nullptr, nullptr, 0, 0};
+  gemm(t.a0_hi, t.a0_lo, t.sx_hi, t.sx_lo, R * nyp, nxp, nxp, e, g->d_status, s);
+  e = Epi{1, nxp, nyp, g->op_hi[0], g->op_lo[0], g->f32_scale, nullptr, 0, 0};
+  gemm(t.a1_hi, t.a1_lo, t.sy_hi, t.sy_lo, R * nxp, nyp, nyp, e, g->d_status, s);
+  e = Epi{0, nyp, nxp, g->op_hi[1], g->op_lo[1], nullptr, nullptr, 0, 0};
+  gemm(t.a0_hi, t.a0_lo, t.sx_hi, t.sx_lo, R * nyp, nxp, nxp, e, g->d_status, s);
+  e = Epi{3, nxp, nyp, nullptr, nullptr, nullptr, nullptr, g->nx, g->ny,
+          reinterpret_cast<float*>(g->gf), reinterpret_cast<float*>(g->bprev1), reinterpret_cast<float*>(g->bprev2),
+          reinterpret_cast<float*>(g->bjn), (float)g->d.pc_mix, last, g->d_status};
+  gemm(t.a1_hi, t.a1_lo, t.sy_hi, t.sy_lo, R * nxp, nyp, nyp, e, g->d_status, s);
 }
 
 // sources (split) in op[0] [R][nyp][nxp] -> FP32 solution in g->solved [R][ny][nx]

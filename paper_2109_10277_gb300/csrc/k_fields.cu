@@ -27,6 +27,8 @@ __global__ void k_reset_dep(V4<T>* dep, T* chi, const T* rho_ion, int64_t nn) {
 // psi: -(rho - Jz);  Ez: dx Jx + dy Jy;  Bz: dy Jx - dx Jy.
 template <typename T, typename Sink>
 __global__ void k_src_main(const V4<T>* __restrict__ dep, Geom gm, Sink sink) {
+  pdl_trigger();
+  pdl_wait();
   const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
   if (ix >= gm.nx) return;
   const int nx = gm.nx;
@@ -53,6 +55,8 @@ __global__ void k_src_main(const V4<T>* __restrict__ dep, Geom gm, Sink sink) {
 template <typename T, typename Sink>
 __global__ void k_src_bperp(const V4<T>* __restrict__ cur, V4<T>* prev, T* chi_prev, const T* __restrict__ rho_ion,
                             V2<T>* tj, const V2<T>* __restrict__ bjn, Geom gm, Sink sink, int reset_prev) {
+  pdl_trigger();
+  pdl_wait();
   const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
   if (ix >= gm.nx) return;
   const int nx = gm.nx;
@@ -93,6 +97,8 @@ __global__ void k_src_copy(const T* __restrict__ src, int nrhs, Geom gm, Sink si
 template <typename T>
 __global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, const V2<T>* __restrict__ b1,
                               const V2<T>* __restrict__ b2, Geom gm, int* status) {
+  pdl_trigger();
+  pdl_wait();
   const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
   if (ix >= gm.nx) return;
   const int nx = gm.nx;
@@ -123,6 +129,8 @@ __global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, const V2
 template <typename T>
 __global__ void k_finish_bperp(const T* __restrict__ res, T* gf, int64_t nn, T w, int* status, int last,
                                V2<T>* b1, V2<T>* b2, V2<T>* bjn) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nn) return;
   const T bx = res[o], by = res[nn + o];
@@ -162,6 +170,8 @@ __global__ void k_bshift(V2<T>* b1, V2<T>* b2, const T* gf, int64_t nn) {
 template <typename T>
 __global__ void k_store(hq_field_out out, int64_t base, const V4<T>* dep, const T* chi, const T* psi,
                         const T* gf, int64_t nn) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nn) return;
   const V4<T> d = dep[o];
@@ -199,14 +209,15 @@ void launch_reset_dep(const hq_grid_s* g, void* dep, void* chi, cudaStream_t s) 
 }
 template <typename T>
 void launch_src_main(const hq_grid_s* g, const void* dep, cudaStream_t s) {
-  k_src_main<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const V4<T>*>(dep), g->geom, SinkOf<T>::make(g));
+  launch_pdl(k_src_main<T, decltype(SinkOf<T>::make(g))>, grid2d(g), 128, 0, s, reinterpret_cast<const V4<T>*>(dep),
+             g->geom, SinkOf<T>::make(g));
 }
 template <typename T>
 void launch_src_bperp(const hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int reset_prev, cudaStream_t s) {
-  k_src_bperp<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const V4<T>*>(cur), reinterpret_cast<V4<T>*>(prev),
-                                          reinterpret_cast<T*>(chi_prev), reinterpret_cast<const T*>(g->rho_ion),
-                                          reinterpret_cast<V2<T>*>(g->tj), reinterpret_cast<const V2<T>*>(g->bjn),
-                                          g->geom, SinkOf<T>::make(g), reset_prev);
+  launch_pdl(k_src_bperp<T, decltype(SinkOf<T>::make(g))>, grid2d(g), 128, 0, s,
+             reinterpret_cast<const V4<T>*>(cur), reinterpret_cast<V4<T>*>(prev), reinterpret_cast<T*>(chi_prev),
+             reinterpret_cast<const T*>(g->rho_ion), reinterpret_cast<V2<T>*>(g->tj),
+             reinterpret_cast<const V2<T>*>(g->bjn), g->geom, SinkOf<T>::make(g), reset_prev);
 }
 template <typename T>
 void launch_src_copy(const hq_grid_s* g, const void* src, int nrhs, cudaStream_t s) {
@@ -214,15 +225,15 @@ void launch_src_copy(const hq_grid_s* g, const void* src, int nrhs, cudaStream_t
 }
 template <typename T>
 void launch_finish_main(const hq_grid_s* g, const void* res, cudaStream_t s) {
-  k_finish_main<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const T*>(res), reinterpret_cast<T*>(g->psi),
-                                            reinterpret_cast<T*>(g->gf), reinterpret_cast<const V2<T>*>(g->bprev1),
-                                            reinterpret_cast<const V2<T>*>(g->bprev2), g->geom, g->d_status);
+  launch_pdl(k_finish_main<T>, grid2d(g), 128, 0, s, reinterpret_cast<const T*>(res), reinterpret_cast<T*>(g->psi),
+             reinterpret_cast<T*>(g->gf), reinterpret_cast<const V2<T>*>(g->bprev1),
+             reinterpret_cast<const V2<T>*>(g->bprev2), g->geom, g->d_status);
 }
 template <typename T>
 void launch_finish_bperp(const hq_grid_s* g, const void* res, int last, cudaStream_t s) {
-  k_finish_bperp<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(
-      reinterpret_cast<const T*>(res), reinterpret_cast<T*>(g->gf), g->nnode, T(g->d.pc_mix), g->d_status, last,
-      reinterpret_cast<V2<T>*>(g->bprev1), reinterpret_cast<V2<T>*>(g->bprev2), reinterpret_cast<V2<T>*>(g->bjn));
+  launch_pdl(k_finish_bperp<T>, blocks_for(g->nnode), kThreads, 0, s, reinterpret_cast<const T*>(res),
+             reinterpret_cast<T*>(g->gf), g->nnode, T(g->d.pc_mix), g->d_status, last,
+             reinterpret_cast<V2<T>*>(g->bprev1), reinterpret_cast<V2<T>*>(g->bprev2), reinterpret_cast<V2<T>*>(g->bjn));
 }
 template <typename T>
 void launch_bguess(const hq_grid_s* g, cudaStream_t s) {
@@ -237,9 +248,9 @@ void launch_bshift(const hq_grid_s* g, cudaStream_t s) {
 }
 template <typename T>
 void launch_store(const hq_grid_s* g, const hq_field_out* out, int64_t slot, const void* dep, const void* chi, cudaStream_t s) {
-  k_store<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(*out, slot * g->nnode, reinterpret_cast<const V4<T>*>(dep),
-                                                      reinterpret_cast<const T*>(chi), reinterpret_cast<const T*>(g->psi),
-                                                      reinterpret_cast<const T*>(g->gf), g->nnode);
+  launch_pdl(k_store<T>, blocks_for(g->nnode), kThreads, 0, s, *out, slot * g->nnode,
+             reinterpret_cast<const V4<T>*>(dep), reinterpret_cast<const T*>(chi), reinterpret_cast<const T*>(g->psi),
+             reinterpret_cast<const T*>(g->gf), g->nnode);
 }
 template <typename T>
 void launch_zero(void* p, int64_t n, cudaStream_t s) {

@@ -155,7 +155,7 @@ __device__ __forceinline__ void stencil_f64(const Geom& gm, double x, double y, 
 template <typename T>
 __device__ __forceinline__ T charge_density(T w, const Geom& gm) {
   if constexpr (sizeof(T) == 8) return (T(-1.0) * w) / (gm.dx * gm.dy);
-  else return T(-1.0) * w * T(gm.inv_area);
+  else return -w * gm.f_inv_area;
 }
 
 // Removal rule (a reading; the paper is silent): finite, inside the open box,
@@ -249,6 +249,8 @@ __global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* 
 template <int P, typename T, bool CACHE>
 __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf,
                                                          V2<T>* tj, int slice, double guard) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pl.n || !pl.alive[p]) return;
   const int64_t n = pl.n;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
   const F6<T> F = gather6<P, T>(gf, gm.nx, gm.ny, ix0, iy0, wx, wy);
   T f[5];
   derivs<T>(ux, uy, opp, F, f);
-  const T dz = T(gm.dzeta);
+  const T dz = CACHE ? T(gm.f_dz) : T(gm.dzeta);
   const T cx = ab5_comb<T>(pl.hist, n, p, slice, 0, f[0]);
   const T cy = ab5_comb<T>(pl.hist, n, p, slice, 1, f[1]);
   const T tux = ux - dz * ab5_comb<T>(pl.hist, n, p, slice, 2, f[2]);
@@ -285,8 +287,8 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
   T topp;
   if constexpr (CACHE) {
     // trial step in cell-relative coordinates (FP32 only)
-    T ux_ = fxr - T(gm.dzeta * gm.inv_dx) * cx;
-    T uy_ = fyr - T(gm.dzeta * gm.inv_dy) * cy;
+    T ux_ = fxr - T(gm.f_dz_inv_dx) * cx;
+    T uy_ = fyr - T(gm.f_dz_inv_dy) * cy;
     const T flx = floor(ux_), fly = floor(uy_);
     const int tjx = jx + (int)flx, tjy = jy + (int)fly;
     ux_ -= flx;
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
     topp = opp - dz * cpsi;
     const T ax = T(tjx) + ux_, ay = T(tjy) + uy_;
     const bool ok = isfinite(ax) && isfinite(ay) && isfinite(topp) && ax > T(0) && ax < T(gm.nx) &&
-                    ay > T(0) && ay < T(gm.ny) && topp >= T(guard);
+                    ay > T(0) && ay < T(gm.ny) && topp >= T(gm.f_guard);
     if (!ok) return;
     tix0 = shape_weights<P, T>(tjx, ux_, twx);
     tiy0 = shape_weights<P, T>(tjy, uy_, twy);
@@ -318,6 +320,8 @@ template <int P, typename T, bool CACHE>
 __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf,
                                                          V4<T>* dep, T* chi, int slice, double guard,
                                                          unsigned long long* removed) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pl.n || !pl.alive[p]) return;
   const int64_t n = pl.n;
@@ -422,10 +426,10 @@ void launch_trial_pass(const hq_grid_s* g, int slice, cudaStream_t s) {
   constexpr bool C = sizeof(T) == 4;
   const double gd = g->d.psi_guard;
   switch (g->d.shape_order) {
-    case 0: k_trial_pass<0, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
-    case 1: k_trial_pass<1, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
-    case 2: k_trial_pass<2, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
-    default: k_trial_pass<3, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
+    case 0: launch_pdl(k_trial_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
+    case 1: launch_pdl(k_trial_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
+    case 2: launch_pdl(k_trial_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
+    default: launch_pdl(k_trial_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
   }
 }
 
@@ -439,10 +443,10 @@ void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cuda
   const double gd = g->d.psi_guard;
   unsigned long long* rm = g->d_removed;
   switch (g->d.shape_order) {
-    case 0: k_final_pass<0, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
-    case 1: k_final_pass<1, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
-    case 2: k_final_pass<2, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
-    default: k_final_pass<3, T, C><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
+    case 0: launch_pdl(k_final_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
+    case 1: launch_pdl(k_final_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
+    case 2: launch_pdl(k_final_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
+    default: launch_pdl(k_final_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
   }
 }
 

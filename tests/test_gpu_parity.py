@@ -3,22 +3,14 @@
 Bars (derived in DESIGN.md):
   * Poisson solves, FP64: rel-L2 <= 1e-12 (a single linear operation).
   * Whole sweeps, FP64: the quasi-static sweep amplifies last-bit rounding
-    differences.  The oracle run with its plasma and beam particles in another
-    order (a different summation order only, identical arithmetic) moves Bx by
-    ~1e-10 relative by the tail of the 64-slice linear workload.  No
-    implementation with its own operation order can beat that floor, so per
-    field and per slice the GPU's deviation, measured against the field's peak
-    slice norm, must be below max(2e-12, 30 x the oracle's own reorder
-    deviation).  The factor 30 covers the GPU's extra rounding sources (FMA
-    contraction, FFT instead of matrix DST-I).  The reordered oracle run also sums
-    the ion background in the opposite stencil order, so that, as on the GPU, the
-    ion and electron roundings no longer cancel exactly.  Total rho is the small
-    difference of those two densities (both ~n0), so rho's deviation is measured
-    against the ion density it is summed from.  The absolute part of the bar is
-    2e-12 rather than 1e-12: in the linear workload the net charge is ~1e-3 of the
-    ion and electron densities it is the difference of, so one ulp of n0 per node
-    (which the oracle's exactly representable initial sums cannot reproduce)
-    reaches ~1.5e-12 of psi's and ExmBy's peak.
+    differences, and the GPU's deposits are unordered atomic sums (the GPU run
+    twice differs from itself by up to ~1e-10 of Bz's peak).  The bar is
+    measured on the oracle: a second oracle run with the particles in another
+    order, the ion background summed in reverse stencil order and every plasma
+    deposit node value perturbed by one ulp (relative 2^-52, the size of the
+    error an unordered summation leaves) gives, per field and slice, the
+    sweep's own rounding floor f (deviation over the field's peak slice norm).
+    The GPU's deviation must be below max(1e-12, 10 f).
   * FP32/bf16x3 path: each bf16x3 product carries ~2^-17 relative error, so a
     4-product Dirichlet solve is good to a few 1e-5 (rel-L2); sweeps are held to
     the on-axis Ez (first plasma period) <= 1e-4 and bucket <= 1e-3 bounds.
@@ -80,15 +72,11 @@ def plasma_perm(g, seed=1):
     return torch.as_tensor(np.random.default_rng(seed).permutation(n))
 
 
-def assert_fp64_sweep(out, ref, ref_perm, fields, factor=30.0, spec=None):
+def assert_fp64_sweep(out, ref, ref_perm, fields, factor=10.0, spec=None):
     for k in fields:
         e = peak_err(out[k], ref.fields[k])
         f = peak_err(ref_perm.fields[k], ref.fields[k])
-        if k == "rho" and spec is not None:
-            ion = float(torch.linalg.norm(O.ion_background(spec, O.plasma_init(spec))))
-            peak = float(torch.linalg.norm(ref.fields["rho"].reshape(ref.fields["rho"].shape[0], -1), dim=1).max())
-            e, f = e * peak / max(peak, ion), f * peak / max(peak, ion)
-        bar = torch.clamp(factor * f, min=2e-12)
+        bar = torch.clamp(factor * f, min=1e-12)
         worst = int(torch.argmax(e / bar))
         print(f"fp64 {k}: max dev {float(e.max()):.2e}, reorder floor {float(f.max()):.2e}, "
               f"worst slice {worst}: {float(e[worst]):.2e} vs bar {float(bar[worst]):.2e}")
@@ -156,7 +144,7 @@ def test_sweep_fp64_linear64_full_size(hq):
     sp = O.GridSpec(**g)
     ref = O.sweep(sp, [O.as_beam(b) for b in beams])
     ref_perm = O.sweep(sp, [O.as_beam(b) for b in reordered(beams)], plasma_perm=plasma_perm(g),
-                     reverse_ion_order=True)
+                     reverse_ion_order=True, deposit_noise=2.0 ** -52)
     out, st, removed, _, _ = run_gpu(hq, g, beams, "fp64")
     assert_fp64_sweep(out, ref, ref_perm, O.FIELD_NAMES, spec=sp)
     for k in ("x", "y", "psi", "ux", "uy"):
@@ -178,7 +166,7 @@ def test_sweep_fp64_ragged(hq, order, ppc, profile):
     sp = O.GridSpec(**g)
     ref = O.sweep(sp, [O.as_beam(b) for b in beams])
     ref_perm = O.sweep(sp, [O.as_beam(b) for b in reordered(beams)], plasma_perm=plasma_perm(g),
-                     reverse_ion_order=True)
+                     reverse_ion_order=True, deposit_noise=2.0 ** -52)
     out, st, removed, _, _ = run_gpu(hq, g, beams, "fp64")
     assert_fp64_sweep(out, ref, ref_perm, O.FIELD_NAMES, spec=sp)
     assert removed == ref.removed
@@ -192,7 +180,7 @@ def test_beam_push_and_witness_fp64(hq):
     perm = [np.random.default_rng(0).permutation(len(b["x"])) for b in beams]
     ref_perm = O.sweep(sp, [O.as_beam(b) for b in reordered(beams)], dt=5.0, witness=(1,), record=("ez",),
                        plasma_perm=plasma_perm(g),
-                     reverse_ion_order=True)
+                     reverse_ion_order=True, deposit_noise=2.0 ** -52)
     out, st, removed, hb, sums = run_gpu(hq, g, beams, "fp64", fields=("ez",), dt=5.0, witness=1)
     assert_fp64_sweep(out, ref, ref_perm, ("ez",))
     for bi in range(2):
@@ -305,7 +293,7 @@ def test_blowout512_head_full_size(hq):
     ref = O.sweep(sp, [O.as_beam(b) for b in beams], n_slices=nsamp, record=rec)
     ref_perm = O.sweep(sp, [O.as_beam(b) for b in reordered(beams)], n_slices=nsamp, record=rec,
                        plasma_perm=plasma_perm(g),
-                     reverse_ion_order=True)
+                     reverse_ion_order=True, deposit_noise=2.0 ** -52)
     assert float(ref.fields["rho"].abs().max()) > 0.1  # the beam is in the sample
     for prec in ("fp64", "fp32"):
         gg = dict(g)
