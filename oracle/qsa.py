@@ -72,6 +72,10 @@ class GridSpec:
     n_pc_iter: int = 5
     pc_mix: float = 0.05
     psi_guard: float = 0.02
+    # "float32": B-spline weights formed from an FP32 cell fraction in FP32 arithmetic
+    # (then widened).  A test knob that measures the rounding floor of a single-precision
+    # deposit/gather; the method itself is the default, FP64.
+    weight_dtype: str = "float64"
 
     @property
     def dx(self) -> float:
@@ -149,38 +153,42 @@ def ddy(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
 # Shapes, deposition and gather (Sec. 3.2: order 0 longitudinal, 0-3 transverse)
 # ----------------------------------------------------------------------------
 
-def shape_1d(u: torch.Tensor, order: int):
+def shape_1d(u: torch.Tensor, order: int, wdtype: torch.dtype = torch.float64):
     """B-spline weights of order `order` at node coordinate u (nodes at integers).
 
-    Returns (j0, [w_0..w_p]): node j0 + a carries weight w_a.
+    Returns (j0, [w_0..w_p]): node j0 + a carries weight w_a.  The cell fraction and
+    the weights are formed in `wdtype` (FP64 unless a rounding floor is being measured).
     """
+    def back(ws):
+        return [w.to(u.dtype) for w in ws]
     if order == 0:
         j0 = torch.floor(u + 0.5)
         return j0.to(torch.int64), [torch.ones_like(u)]
     if order == 1:
         j0 = torch.floor(u)
-        d = u - j0
-        return j0.to(torch.int64), [1.0 - d, d]
+        d = (u - j0).to(wdtype)
+        return j0.to(torch.int64), back([1.0 - d, d])
     if order == 2:
         jc = torch.floor(u + 0.5)
-        d = u - jc
-        return (jc - 1).to(torch.int64), [0.5 * (0.5 - d) ** 2, 0.75 - d * d, 0.5 * (0.5 + d) ** 2]
+        d = (u - jc).to(wdtype)
+        return (jc - 1).to(torch.int64), back([0.5 * (0.5 - d) ** 2, 0.75 - d * d, 0.5 * (0.5 + d) ** 2])
     if order == 3:
         jf = torch.floor(u)
-        d = u - jf
-        return (jf - 1).to(torch.int64), [
+        d = (u - jf).to(wdtype)
+        return (jf - 1).to(torch.int64), back([
             (1.0 - d) ** 3 / 6.0,
             (4.0 - 6.0 * d * d + 3.0 * d ** 3) / 6.0,
             (1.0 + 3.0 * d + 3.0 * d * d - 3.0 * d ** 3) / 6.0,
             d ** 3 / 6.0,
-        ]
+        ])
     raise ValueError("shape order must be 0..3")
 
 
 def _stencil(spec: GridSpec, x: torch.Tensor, y: torch.Tensor, order: int):
     """Yield (flat node index, weight) for every stencil node; invalid nodes get weight 0."""
-    jx0, wx = shape_1d((x - spec.xmin) / spec.dx, order)
-    jy0, wy = shape_1d((y - spec.ymin) / spec.dy, order)
+    wdt = torch.float32 if spec.weight_dtype == "float32" else torch.float64
+    jx0, wx = shape_1d((x - spec.xmin) / spec.dx, order, wdt)
+    jy0, wy = shape_1d((y - spec.ymin) / spec.dy, order, wdt)
     for b in range(order + 1):
         jy = jy0 + b
         vy = (jy >= 1) & (jy <= spec.ny - 1)

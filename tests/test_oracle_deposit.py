@@ -106,3 +106,27 @@ def test_rho_minus_jz_identity():
     rho, jx, jy, jz, chi = O.plasma_deposit_full(sp, st)
     (ref,) = O.deposit(sp, x, y, [O.PLASMA_Q * st["w"] / (sp.dx * sp.dy)], 2)
     assert torch.allclose(rho - jz, ref, atol=1e-13)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_fp32_weight_knob(order):
+    """The single-precision weight knob (a rounding-floor probe): each weight is the
+    FP32 rounding of the brute-force B-spline value to within a few FP32 ulps, the
+    weights still sum to one to FP32 precision, and the default FP64 path is unchanged
+    by the knob's existence (it matches the brute force to 1e-14)."""
+    g = torch.Generator().manual_seed(11 + order)
+    u = 3.0 + 20.0 * torch.rand(400, generator=g, dtype=torch.float64)
+    for wdt, tol in ((torch.float64, 1e-14), (torch.float32, 4e-7)):
+        j0, w = O.qsa.shape_1d(u, order, wdt)
+        assert all(t.dtype == torch.float64 for t in w)
+        s = sum(w)
+        assert float((s - 1.0).abs().max()) <= (1e-14 if wdt == torch.float64 else 4e-7)
+        for a, wa in enumerate(w):
+            ref = torch.tensor([bspline(float(uu) - float(j0[i] + a), order) for i, uu in enumerate(u)],
+                               dtype=torch.float64)
+            assert float((wa - ref).abs().max()) <= tol, (wdt, a)
+    # FP32 weights are not the FP64 ones (the knob does something), but are close
+    _, w64 = O.qsa.shape_1d(u, order, torch.float64)
+    _, w32 = O.qsa.shape_1d(u, order, torch.float32)
+    d = max(float((a - b).abs().max()) for a, b in zip(w32, w64))
+    assert 0.0 < d <= 4e-7
