@@ -63,7 +63,7 @@ void free_all(hq_grid_s* g) {
   adj_free(g);
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   g->ev_pool.clear();
-  F(g->d_profile); F(g->d_status); F(g->d_removed); F(g->d_scratch_int);
+  F(g->d_profile); F(g->d_status); F(g->d_removed); F(g->d_scratch_int); F(g->d_gbar);
   if (g->tmaps) dst_tc_free(g);
 }
 
@@ -88,6 +88,27 @@ double sin_jk(int64_t j, int64_t k, int n) {
   return std::sin(M_PI * (double)m / (double)n);
 }
 
+
+// Fold matrix of the folded DST-I, [n][n/2]: row = output slot s (index k = fold_node(s)),
+// column u = folded input column of pair (a, b) = fold_pair(u).  Odd k weigh the pair sum
+// with sin(pi a k / n), even k the pair difference; the wall pair (0, n/2) stores x_{n/2}
+// as its sum (weight sin(pi k / 2)) and nothing as its difference.
+std::vector<double> fold_matrix(int n) {
+  std::vector<double> c((size_t)n * (n / 2), 0.0);
+  for (int s = 0; s < n; ++s) {
+    const int k = fold_node(s, n);
+    for (int u = 0; u < n / 2; ++u) {
+      int pa, pb;
+      fold_pair(u, n, pa, pb);
+      const bool wall = pa == 0;
+      double v;
+      if (k & 1) v = wall ? sin_jk(pb, k, n) : sin_jk(pa, k, n);
+      else v = wall ? 0.0 : sin_jk(pa, k, n);
+      c[(size_t)s * (n / 2) + u] = v;
+    }
+  }
+  return c;
+}
 
 // ---------------------------------------------------------------- checkpoints and tapes
 // A stored plasma slice: the state a slice starts from (or is recomputed from).
@@ -200,7 +221,7 @@ struct Prof {
 };
 
 void dst_solve(hq_grid_s* g, int nrhs) {
-  Prof p(g, HQ_K_DST, 4);
+  Prof p(g, HQ_K_DST, g->fp64 ? 4 : 1);   // FP64: four FFT passes; FP32: one fused cooperative launch
   if (g->fp64) dst_solve_f64(g, nrhs, g->stream);
   else dst_solve_tc(g, nrhs, g->stream);
 }
@@ -226,7 +247,7 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
       Prof p(g, HQ_K_FIELD, 1);
       launch_finish_bperp<T>(g, g->solved, last, s);
     } else {
-      Prof p(g, HQ_K_DST, 4);   // the mixing runs in the last product's epilogue
+      Prof p(g, HQ_K_DST, 1);   // the mixing runs in the last product's epilogue
       dst_solve_tc_bmix(g, last, s);
     }
   }
@@ -701,6 +722,12 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   } else {
     g->nxp = (int)round_up(g->nx, 128);
     g->nyp = (int)round_up(g->ny, 128);
+    // folded DST-I (half the contraction) when both extents are multiples of 128
+    const char* nf = std::getenv("HQ_NO_FOLD");
+    g->fold = (g->nx % 128 == 0 && g->ny % 128 == 0 && !(nf && nf[0] == '1')) ? 1 : 0;
+    HQ_ALLOC(g->d_gbar, sizeof(unsigned long long));
+    cudaMemset(g->d_gbar, 0, sizeof(unsigned long long));
+    g->gbar_base = 0;
     const size_t opn = (size_t)kMaxRhs * g->nxp * g->nyp;
     for (int i = 0; i < 2; ++i) {
       HQ_ALLOC(g->op_hi[i], 2 * opn);
@@ -708,14 +735,18 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
       cudaMemset(g->op_hi[i], 0, 2 * opn);
       cudaMemset(g->op_lo[i], 0, 2 * opn);
     }
+    // S (zero-padded [np][np]) or, folded, the fold matrix [n][n/2]; split into bf16 hi + lo
     auto smat = [&](int n, int np_, __nv_bfloat16** hi, __nv_bfloat16** lo) -> hq_status {
-      std::vector<__nv_bfloat16> h((size_t)np_ * np_), l((size_t)np_ * np_);
+      const int cols = g->fold ? n / 2 : np_;
+      const std::vector<double> fm = g->fold ? fold_matrix(n) : std::vector<double>();
+      std::vector<__nv_bfloat16> h((size_t)np_ * cols), l((size_t)np_ * cols);
       for (int k = 0; k < np_; ++k)
-        for (int j = 0; j < np_; ++j) {
-          const float v = (j < n && k < n) ? (float)sin_jk(j, k, n) : 0.0f;
+        for (int j = 0; j < cols; ++j) {
+          const float v = g->fold ? (float)fm[(size_t)k * cols + j]
+                                  : ((j < n && k < n) ? (float)sin_jk(j, k, n) : 0.0f);
           const __nv_bfloat16 vh = __float2bfloat16_rn(v);
-          h[(size_t)k * np_ + j] = vh;
-          l[(size_t)k * np_ + j] = __float2bfloat16_rn(v - __bfloat162float(vh));
+          h[(size_t)k * cols + j] = vh;
+          l[(size_t)k * cols + j] = __float2bfloat16_rn(v - __bfloat162float(vh));
         }
       if (dalloc(hi, 2 * h.size()) != cudaSuccess || dalloc(lo, 2 * l.size()) != cudaSuccess) return HQ_ERR_OOM;
       cudaMemcpy(*hi, h.data(), 2 * h.size(), cudaMemcpyHostToDevice);
@@ -727,7 +758,12 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
       return bail(HQ_ERR_OOM);
     }
     std::vector<double> sc = scale_table(g, g->nyp, g->nxp);
-    std::vector<float> scf(sc.begin(), sc.end());
+    std::vector<float> scf(sc.size());
+    for (int sy = 0; sy < g->nyp; ++sy)
+      for (int sx = 0; sx < g->nxp; ++sx) {
+        const int ky = g->fold ? fold_node(sy, g->ny) : sy, kx = g->fold ? fold_node(sx, g->nx) : sx;
+        scf[(size_t)sy * g->nxp + sx] = (float)sc[(size_t)ky * g->nxp + kx];
+      }
     HQ_ALLOC(g->f32_scale, 4 * scf.size());
     cudaMemcpy(g->f32_scale, scf.data(), 4 * scf.size(), cudaMemcpyHostToDevice);
     std::string err;

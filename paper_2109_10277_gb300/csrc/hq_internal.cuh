@@ -45,6 +45,7 @@ struct Geom {
 template <typename T> __device__ __forceinline__ T cst(double v) { return T(v); }
 
 template <typename T> struct V4 { T a, b, c, d; };   // packed rho, jx, jy, jz
+
 template <typename T> struct V2 { T a, b; };          // packed jx, jy or bx, by
 // Gather fields packed per node: ExmBy, EypBx, Ez, Bx, By, Bz, pad, pad.
 constexpr int kGF = 8;
@@ -131,8 +132,12 @@ struct hq_grid_s {
   int nxp, nyp;
   __nv_bfloat16 *op_hi[2], *op_lo[2];       // ping-pong [kMaxRhs * max(nxp,nyp)^2]
   __nv_bfloat16 *sx_hi, *sx_lo, *sy_hi, *sy_lo;
-  float* f32_scale;                          // [nyp][nxp] (1/lambda)(4/(nx ny))
+  float* f32_scale;                          // [nyp][nxp] (1/lambda)(4/(nx ny)), slot order if folded
   hq::TensorMaps* tmaps;
+  int fold;                                  // folded DST-I (nx, ny multiples of 128; FP32 mode)
+  unsigned long long* d_gbar;                // grid-barrier counter of the fused solve kernel
+  unsigned long long gbar_base;              // its value before the next launch
+  int solve_ctas;                            // CTAs of the fused solve (co-resident)
 
   // beams
   hq::BeamBins bins[hq::kMaxBeams];
@@ -285,6 +290,27 @@ __device__ __forceinline__ void split_coord(double x, double x0, double dx, int&
 
 __device__ __forceinline__ bool in_interior(int j, int n) { return j >= 1 && j <= n - 1; }
 
+// Folded DST-I order (Sec. 3.2 solver).  With S_jk = sin(pi j k / n),
+// S_{n-j,k} = -(-1)^k S_jk: odd k see only x_j + x_{n-j}, even k only x_j - x_{n-j},
+// so after folding the node pairs (j, n-j) every output needs n/2 terms.  The folded
+// solver keeps each grid index in "slot order", pair u on slots 2u, 2u+1: pairs
+// 0 .. n/4-1 are (1, n-1), (3, n-3), ...; pair n/4 is (0, n/2); the rest (2, n-2),
+// (4, n-4), ...  Slots 0 .. n/2-1 thus hold the odd indices.  n must be a multiple of 4.
+__host__ __device__ __forceinline__ void fold_pair(int u, int n, int& a, int& b) {
+  if (u < n / 4) {
+    a = 2 * u + 1;
+    b = n - a;
+  } else {
+    a = 2 * (u - n / 4);
+    b = a == 0 ? n / 2 : n - a;
+  }
+}
+__host__ __device__ __forceinline__ int fold_node(int s, int n) {
+  int a, b;
+  fold_pair(s >> 1, n, a, b);
+  return (s & 1) ? b : a;
+}
+
 }  // namespace hq
 
 // ---------------------------------------------------------------- shared field helpers
@@ -294,31 +320,85 @@ namespace hq {
 // writes each value already split into bf16 hi + lo, zero-padded [rhs][nyp][nxp]
 // (g->op_hi[0], g->op_lo[0]), the tensor-core solver's input layout.
 struct SinkF64 {
+  static constexpr bool kFold = false;
   double* p;
   int nx, ny;
   __device__ void put(int r, int iy, int ix, double v) const { p[((int64_t)r * ny + iy) * nx + ix] = v; }
 };
 
+__device__ __forceinline__ void put_split(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t o, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[o] = h;
+  lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
 struct SinkBF16 {
+  static constexpr bool kFold = false;
   __nv_bfloat16 *hi, *lo;
   int nxp, nyp;
-  __device__ void put(int r, int iy, int ix, float v) const {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-    const int64_t o = ((int64_t)r * nyp + iy) * nxp + ix;
-    hi[o] = h;
-    lo[o] = l;
+  __device__ void put(int r, int iy, int ix, float v) const { put_split(hi, lo, ((int64_t)r * nyp + iy) * nxp + ix, v); }
+};
+
+// FP32 mode with the folded solver (fold_pair): a thread owns the node pair (a, b) of
+// folded column u in row slot sy and writes the sum x_a + x_b to column u and the
+// difference x_a - x_b to column nx/2 + u (the pair (0, n/2) stores x_{n/2} and 0:
+// node 0 is on the wall and never enters a DST-I).  Layout [rhs][ny slots][nx].
+struct SinkFold {
+  static constexpr bool kFold = true;
+  __nv_bfloat16 *hi, *lo;
+  int nx, ny;
+  __device__ void put_pair(int r, int sy, int u, float va, float vb) const {
+    const bool wall = u == nx / 4;
+    const int64_t row = ((int64_t)r * ny + sy) * nx;
+    put_split(hi, lo, row + u, wall ? vb : va + vb);
+    put_split(hi, lo, row + nx / 2 + u, wall ? 0.0f : va - vb);
   }
 };
 
+// Runs f(iy, ix, v) for the node(s) this thread owns and hands the first nr values
+// of v to the sink: one node per thread (consecutive threads along x) for a plain
+// sink; for SinkFold the two nodes of one folded column, the row taken in slot order.
+// Launch with src_grid().
+template <int NR, typename T, typename Sink, typename F>
+__device__ __forceinline__ void visit_nodes(const Geom& gm, const Sink& sink, int nr, F&& f) {
+  const int tx = blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (Sink::kFold) {
+    if (tx >= gm.nx / 2) return;
+    const int sy = blockIdx.y, iy = fold_node(sy, gm.ny);
+    int xa, xb;
+    fold_pair(tx, gm.nx, xa, xb);
+    T va[NR], vb[NR];
+    f(iy, xa, va);
+    f(iy, xb, vb);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nr) sink.put_pair(r, sy, tx, va[r], vb[r]);
+  } else {
+    if (tx >= gm.nx) return;
+    T v[NR];
+    f((int)blockIdx.y, tx, v);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nr) sink.put(r, blockIdx.y, tx, v[r]);
+  }
+}
 
-template <typename T> struct SinkOf;
-template <> struct SinkOf<double> {
-  static SinkF64 make(const hq_grid_s* g) { return SinkF64{g->f64_a, g->nx, g->ny}; }
-};
-template <> struct SinkOf<float> {
-  static SinkBF16 make(const hq_grid_s* g) { return SinkBF16{g->op_hi[0], g->op_lo[0], g->nxp, g->nyp}; }
-};
+// Calls f(sink) with the DST operand writer of the grid's solver.
+template <typename T, typename F>
+inline void with_sink(const hq_grid_s* g, F&& f) {
+  if constexpr (sizeof(T) == 8) {
+    f(SinkF64{g->f64_a, g->nx, g->ny});
+  } else {
+    if (g->fold) f(SinkFold{g->op_hi[0], g->op_lo[0], g->nx, g->ny});
+    else f(SinkBF16{g->op_hi[0], g->op_lo[0], g->nxp, g->nyp});
+  }
+}
+
+// Grid of the source kernels (visit_nodes): 128 threads per block along x, one row per block.
+inline dim3 src_grid(const hq_grid_s* g) {
+  const int w = g->fold ? g->nx / 2 : g->nx;
+  return dim3((unsigned)((w + 127) / 128), (unsigned)g->ny);
+}
 
 // Central difference helpers with wall nodes (index 0 and n) reading zero; the
 // result on wall rows/columns is zero (matching the field layout convention).

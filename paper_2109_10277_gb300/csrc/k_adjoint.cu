@@ -362,13 +362,13 @@ __global__ void k_adj_bstart(const T* __restrict__ fbar, V2<T>* carry, V2<T>* bb
 // Mixing B^m = w Bs + (1-w) B^(m-1): the solve gets w Bbar^m, Bbar^(m-1) starts at (1-w) Bbar^m.
 template <typename T, typename Sink>
 __global__ void k_adj_pc_pre(const V2<T>* __restrict__ bbar_m, V2<T>* bbar_m1, T w, Geom gm, Sink sink) {
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
-  if (ix >= gm.nx) return;
-  const int64_t o = (int64_t)iy * gm.nx + ix;
-  const V2<T> b = bbar_m[o];
-  bbar_m1[o] = V2<T>{(T(1) - w) * b.a, (T(1) - w) * b.b};
-  sink.put(0, iy, ix, w * b.a);
-  sink.put(1, iy, ix, w * b.b);
+  visit_nodes<2, T>(gm, sink, 2, [&](int iy, int ix, T* v) {
+    const int64_t o = (int64_t)iy * gm.nx + ix;
+    const V2<T> b = bbar_m[o];
+    bbar_m1[o] = V2<T>{(T(1) - w) * b.a, (T(1) - w) * b.b};
+    v[0] = w * b.a;
+    v[1] = w * b.b;
+  });
 }
 
 // Sources Bx = -dy Jz + (Jy(i-1) - Jy(i+1))/2dz, By = dx Jz - (Jx(i-1) - Jx(i+1))/2dz,
@@ -414,21 +414,18 @@ __global__ void k_adj_guess(const V2<T>* __restrict__ b0, V2<T>* c1, V2<T>* c2, 
 // psi_bar = Dx fbar0 + Dy fbar1 (ExmBy = -Dx psi, EypBx = -Dy psi), with Ez_bar, Bz_bar.
 template <typename T, typename Sink>
 __global__ void k_adj_main_pre(const T* __restrict__ fbar, Geom gm, Sink sink) {
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
-  if (ix >= gm.nx) return;
   const int nx = gm.nx;
-  const int64_t o = (int64_t)iy * nx + ix;
-  T s0 = T(0), s1 = T(0), s2 = T(0);
-  if (ix > 0 && iy > 0) {
-    auto f0 = [&](int y, int x) { return fbar[((int64_t)y * nx + x) * kGF + 0]; };
-    auto f1 = [&](int y, int x) { return fbar[((int64_t)y * nx + x) * kGF + 1]; };
-    s0 = dxc(f0, iy, ix, nx, T(gm.inv2dx)) + dyc(f1, iy, ix, gm.ny, T(gm.inv2dy));
-    s1 = fbar[o * kGF + 2];
-    s2 = fbar[o * kGF + 5];
-  }
-  sink.put(0, iy, ix, s0);
-  sink.put(1, iy, ix, s1);
-  sink.put(2, iy, ix, s2);
+  auto f0 = [&](int y, int x) { return fbar[((int64_t)y * nx + x) * kGF + 0]; };
+  auto f1 = [&](int y, int x) { return fbar[((int64_t)y * nx + x) * kGF + 1]; };
+  visit_nodes<3, T>(gm, sink, 3, [&](int iy, int ix, T* v) {
+    const int64_t o = (int64_t)iy * nx + ix;
+    v[0] = v[1] = v[2] = T(0);
+    if (ix > 0 && iy > 0) {
+      v[0] = dxc(f0, iy, ix, nx, T(gm.inv2dx)) + dyc(f1, iy, ix, gm.ny, T(gm.inv2dy));
+      v[1] = fbar[o * kGF + 2];
+      v[2] = fbar[o * kGF + 5];
+    }
+  });
 }
 
 // psi = L^-1(-(rho - Jz)), Ez = L^-1(dx Jx + dy Jy), Bz = L^-1(dy Jx - dx Jy), transposed.
@@ -651,8 +648,10 @@ void launch_adj_bstart(const hq_grid_s* g, const void* fbar, void* carry, void* 
 }
 template <typename T>
 void launch_adj_pc_pre(const hq_grid_s* g, const void* bbar_m, void* bbar_m1, cudaStream_t st) {
-  k_adj_pc_pre<T><<<grid2d(g), 128, 0, st>>>(reinterpret_cast<const V2<T>*>(bbar_m), reinterpret_cast<V2<T>*>(bbar_m1),
-                                            T(g->d.pc_mix), g->geom, SinkOf<T>::make(g));
+  with_sink<T>(g, [&](auto sink) {
+    k_adj_pc_pre<T, decltype(sink)><<<src_grid(g), 128, 0, st>>>(
+        reinterpret_cast<const V2<T>*>(bbar_m), reinterpret_cast<V2<T>*>(bbar_m1), T(g->d.pc_mix), g->geom, sink);
+  });
 }
 template <typename T>
 void launch_adj_pc_post(const hq_grid_s* g, void* dcur, void* dprev, void* jbar, void* jtot, cudaStream_t st) {
@@ -668,7 +667,9 @@ void launch_adj_guess(const hq_grid_s* g, const void* b0, void* c1, void* c2, cu
 }
 template <typename T>
 void launch_adj_main_pre(const hq_grid_s* g, const void* fbar, cudaStream_t st) {
-  k_adj_main_pre<T><<<grid2d(g), 128, 0, st>>>(reinterpret_cast<const T*>(fbar), g->geom, SinkOf<T>::make(g));
+  with_sink<T>(g, [&](auto sink) {
+    k_adj_main_pre<T, decltype(sink)><<<src_grid(g), 128, 0, st>>>(reinterpret_cast<const T*>(fbar), g->geom, sink);
+  });
 }
 template <typename T>
 void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, cudaStream_t st) {

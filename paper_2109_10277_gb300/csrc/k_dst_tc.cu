@@ -26,13 +26,18 @@
 // still drains its MMAs, frees its tensor memory and returns.
 #include "hq_internal.cuh"
 
+#include <algorithm>
+
 namespace hq {
 
 struct TensorMaps {
   CUtensorMap a0_hi, a0_lo;   // op[0] as [kMaxRhs * nyp][nxp]
   CUtensorMap a1_hi, a1_lo;   // op[1] as [kMaxRhs * nxp][nyp]
-  CUtensorMap sx_hi[2], sx_lo[2];   // [nxp][nxp], boxes of 128 ([0]) or 64 ([1]) rows
+  CUtensorMap sx_hi[2], sx_lo[2];   // [nxp][nxp], boxes of 128 ([0]) or 64 ([1]) rows (per-product path)
   CUtensorMap sy_hi[2], sy_lo[2];   // [nyp][nyp]
+  CUtensorMap bx_hi, bx_lo;   // fused solve: S_x [nxp][nxp], or the fold matrix [nxp][nxp/2]; 64-row boxes
+  CUtensorMap by_hi, by_lo;
+  CUtensorMap scale;          // FP32 [nyp][nxp], 128 (x) by 64 (y) boxes
 };
 
 namespace {
@@ -109,6 +114,10 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
       : "memory");
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -296,6 +305,309 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+// ---------------------------------------------------------------- fused persistent solve
+// A whole Dirichlet solve in one cooperative launch: the four products run as
+// phases separated by grid-wide barriers, with tensor memory, mbarriers and the
+// shared-memory ring set up once and the intermediates kept in L2.  Phase p
+// contracts along x (p = 0, 2: operand op[0], matrix S_x) or along y (p = 1, 3:
+// op[1], S_y); its epilogue writes the next phase's operand transposed.
+//
+// Folded order (fold_pair; n a multiple of 128): every operand row holds its n/2
+// pair sums followed by its n/2 pair differences, the output columns are slots, and
+// an N-tile of odd (even) slots contracts over the sums (differences) only, K = n/2,
+// against the fold matrix.  Rows 2u, 2u+1 of a tile are a pair, i.e. adjacent TMEM
+// lanes, so the epilogue folds the next operand with one warp shuffle.
+struct SolveArgs {
+  int R;                               // right-hand sides
+  int nxp, nyp;                        // operand extents (= nx, ny when folded)
+  int fold;
+  __nv_bfloat16 *op_hi[2], *op_lo[2];  // op[0]: [R][nyp][nxp], op[1]: [R][nxp][nyp]
+  const float* scale;                  // [nyp][nxp]: (4/(nx ny)) / lambda, slot order when folded
+  int final_mode;                      // 2: FP32 store into out [R][ny][nx]; 3: predictor-corrector mixing
+  float* out;
+  int nx, ny;
+  float *gf, *b1, *b2, *bjn;           // mode 3 (see Epi)
+  float w;
+  int last;
+  unsigned long long* gbar;            // grid-barrier counter
+  unsigned long long gbase;            // its value at launch
+  int* status;
+};
+
+// Bounded mbarrier wait that also gives up once another thread of the CTA has.
+__device__ __forceinline__ bool mbar_wait_a(uint32_t bar, uint32_t parity, int* status, volatile int* abort_f) {
+  const long long t0 = clock64();
+  uint32_t it = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++it & 63u) == 0 && (*abort_f || clock64() - t0 > (4ll << 30))) {
+      atomicOr(status, DEV_TIMEOUT);
+      *abort_f = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Grid-wide barrier (all CTAs co-resident: cooperative launch).  The counter only
+// grows; barrier b of a launch completes at gbase + (b + 1) * gridDim.x arrivals.
+// The proxy fences order the epilogue's generic stores before the other CTAs' TMA
+// (async-proxy) loads of the next phase.  Bounded: on expiry, or once another CTA
+// has reported a timeout, the CTA sets DEV_TIMEOUT and leaves.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned long long target, int* status,
+                                             volatile int* abort_f) {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!*abort_f) {
+      __threadfence();
+      atomicAdd(ctr, 1ull);
+      const long long t0 = clock64();
+      uint32_t it = 0;
+      while (true) {
+        unsigned long long v;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+        if (v >= target) break;
+        if ((++it & 15u) == 0 &&
+            ((*reinterpret_cast<volatile int*>(status) & DEV_TIMEOUT) || clock64() - t0 > (4ll << 30))) {
+          atomicOr(status, DEV_TIMEOUT);
+          *abort_f = 1;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
+  __syncthreads();
+  return !*abort_f;
+}
+
+constexpr int kSolveBN = 64;
+
+// Optional per-CTA timestamps of the solve's steps (a profiling build defines it).
+#ifndef HQ_SOLVE_TRACE_POINT
+#define HQ_SOLVE_TRACE_POINT(phase, tag)
+#endif
+
+// Shared memory of the solve: the stage ring, the FP32 scale tile of phase 1
+// ([64 n][128 rows]), then the barriers (full, empty, done, scale) and the TMEM slot.
+struct SolveSmem {
+  static constexpr int STAGES = Cfg<kSolveBN>::STAGES;
+  static constexpr int RING = STAGES * Cfg<kSolveBN>::STAGE_BYTES;
+  static constexpr int SCALE = RING;
+  static constexpr int BARS = SCALE + kSolveBN * BM * 4;
+  static constexpr int BYTES = BARS + 256 + 1024 /*alignment*/;
+};
+
+__global__ void __launch_bounds__(128, 1)
+    k_dst_solve(const __grid_constant__ CUtensorMap a0h, const __grid_constant__ CUtensorMap a0l,
+                const __grid_constant__ CUtensorMap a1h, const __grid_constant__ CUtensorMap a1l,
+                const __grid_constant__ CUtensorMap bxh, const __grid_constant__ CUtensorMap bxl,
+                const __grid_constant__ CUtensorMap byh, const __grid_constant__ CUtensorMap byl,
+                const __grid_constant__ CUtensorMap scm, const SolveArgs a) {
+  constexpr int BN = kSolveBN;
+  using C = Cfg<BN>;
+  using L = SolveSmem;
+  constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ int s_abort;
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* basep = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(basep + L::BARS);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+  const uint32_t sbar = smem_u32(bars + 2 * STAGES + 1);
+  const float* scale_s = reinterpret_cast<const float*>(basep + L::SCALE);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* abort_f = &s_abort;
+  HQ_SOLVE_TRACE_POINT(0, 6);
+
+  if (threadIdx.x == 0) {
+    for (const CUtensorMap* m : {&a0h, &a0l, &a1h, &a1l, &bxh, &bxl, &byh, &byl, &scm})
+      prefetch_map(m);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    mbar_init(sbar, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  HQ_SOLVE_TRACE_POINT(0, 7);
+
+  // stage-ring, accumulator and scale-tile counters across tiles
+  uint32_t kb_run = 0, tiles_run = 0, scales_run = 0;
+  for (int p = 0; p < 4; ++p) {
+    HQ_SOLVE_TRACE_POINT(p, 0);
+    const bool along_x = (p & 1) == 0;
+    const int P1 = along_x ? a.nyp : a.nxp;   // rows per right-hand side
+    const int P2 = along_x ? a.nxp : a.nyp;   // output columns (= contraction extent)
+    const int mt = a.R * P1 / BM, tiles = mt * (P2 / BN);
+    const int nk = (a.fold ? P2 / 2 : P2) / BK;
+    const CUtensorMap* tah = along_x ? &a0h : &a1h;
+    const CUtensorMap* tal = along_x ? &a0l : &a1l;
+    const CUtensorMap* tbh = along_x ? &bxh : &byh;
+    const CUtensorMap* tbl = along_x ? &bxl : &byl;
+    const int mode = p == 3 ? a.final_mode : (p == 1 ? 1 : 0);
+    if (p == 3) pdl_trigger();
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
+      const int r = m0 / P1, ml0 = m0 - r * P1;   // a tile lies within one right-hand side
+      const int koff = (a.fold && n0 >= P2 / 2) ? P2 / 2 : 0;
+      if (warp == 0 && lane == 0) {
+        // TMA producer (and the scale tile of the spectral division)
+        if (mode == 1) {
+          mbar_expect_tx(sbar, BN * BM * 4);
+          tma_load_2d(base + L::SCALE, &scm, ml0, n0, sbar);
+        }
+        for (int kb = 0; kb < nk; ++kb) {
+          const uint32_t g = kb_run + kb;
+          const int s = g % STAGES;
+          if (g >= STAGES && !mbar_wait_a(empty0 + 8 * s, ((g / STAGES) - 1) & 1, a.status, abort_f)) break;
+          const uint32_t st = base + s * STAGE_BYTES;
+          const uint32_t fb = full0 + 8 * s;
+          mbar_expect_tx(fb, STAGE_BYTES);
+          tma_load_2d(st, tah, koff + kb * BK, m0, fb);
+          tma_load_2d(st + A_BYTES, tal, koff + kb * BK, m0, fb);
+          tma_load_2d(st + 2 * A_BYTES, tbh, kb * BK, n0, fb);
+          tma_load_2d(st + 2 * A_BYTES + C::B_BYTES, tbl, kb * BK, n0, fb);
+        }
+        HQ_SOLVE_TRACE_POINT(p, 1);
+      } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (int kb = 0; kb < nk; ++kb) {
+          const uint32_t g = kb_run + kb;
+          const int s = g % STAGES;
+          if (!mbar_wait_a(full0 + 8 * s, (g / STAGES) & 1, a.status, abort_f)) break;
+          tc_fence_after();
+          const uint32_t st = base + s * STAGE_BYTES;
+          const uint64_t ah = desc_k_sw128(st), al = desc_k_sw128(st + A_BYTES);
+          const uint64_t bh = desc_k_sw128(st + 2 * A_BYTES), bl = desc_k_sw128(st + 2 * A_BYTES + C::B_BYTES);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t off = (uint64_t)((k * 32) >> 4);
+            mma_bf16(tmem, ah + off, bh + off, C::IDESC, (kb | k) != 0 ? 1u : 0u);
+            mma_bf16(tmem, ah + off, bl + off, C::IDESC, 1u);
+            mma_bf16(tmem, al + off, bh + off, C::IDESC, 1u);
+          }
+          mma_commit(empty0 + 8 * s);
+        }
+        mma_commit(done);
+      }
+      __syncwarp();
+      mbar_wait_a(done, tiles_run & 1, a.status, abort_f);
+      if (mode == 1) mbar_wait_a(sbar, scales_run & 1, a.status, abort_f);
+      tc_fence_after();
+      HQ_SOLVE_TRACE_POINT(p, 2);
+
+      // ------------------------------------------------ epilogue: TMEM lane = tile row
+      const int row = warp * 32 + lane;
+      const int ml = ml0 + row;
+      if (mode <= 1) {
+        // scale (phase 1), fold with the pair partner (one shuffle), split and store the next
+        // operand transposed: folded, even rows hold pair sums (column u), odd rows pair
+        // differences (column P1/2 + u)
+        const bool odd = (ml & 1) != 0, wall = a.fold && (ml >> 1) == P1 / 4;
+        const int fcol = a.fold ? (odd ? P1 / 2 + (ml >> 1) : (ml >> 1)) : ml;
+        __nv_bfloat16* oh = a.op_hi[along_x ? 1 : 0];
+        __nv_bfloat16* ol = a.op_lo[along_x ? 1 : 0];
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+          HQ_SOLVE_TRACE_POINT(p, 8 + c0 / 16);
+          float sc[32];
+          if (mode == 1) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) sc[j] = scale_s[(c0 + j) * BM + row];
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float x = __uint_as_float(v[j]);
+            if (mode == 1) x *= sc[j];
+            if (a.fold) {
+              const float y = __shfl_xor_sync(0xffffffffu, x, 1);
+              x = odd ? (wall ? 0.0f : y - x) : (wall ? y : x + y);
+            }
+            put_split(oh, ol, ((int64_t)r * P2 + n0 + c0 + j) * P1 + fcol, x);
+          }
+          HQ_SOLVE_TRACE_POINT(p, 9 + c0 / 16);
+        }
+      } else {
+        // node of this row (rows run along x in the last phase)
+        const int xn = a.fold ? fold_node(ml, a.nx) : ml;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+          if (xn >= a.nx) continue;
+          auto ynode = [&](int j) { return a.fold ? fold_node(n0 + c0 + j, a.ny) : n0 + c0 + j; };
+          if (mode == 2) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int yn = ynode(j);
+              if (yn < a.ny) a.out[((int64_t)r * a.ny + yn) * a.nx + xn] = __uint_as_float(v[j]);
+            }
+          } else {
+            // predictor-corrector mixing into gf[3 + r] (all loads first, then mix and store)
+            float old[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int yn = ynode(j);
+              old[j] = yn < a.ny ? a.gf[((int64_t)yn * a.nx + xn) * kGF + 3 + r] : 0.0f;
+            }
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int yn = ynode(j);
+              if (yn >= a.ny) continue;
+              const float x = __uint_as_float(v[j]);
+              bad |= !isfinite(x);
+              const int64_t node = (int64_t)yn * a.nx + xn;
+              const float nb = a.w * x + (1.0f - a.w) * old[j];
+              a.gf[node * kGF + 3 + r] = nb;
+              if (a.last) {
+                a.b2[node * 2 + r] = a.b1[node * 2 + r];
+                a.b1[node * 2 + r] = nb;
+                a.bjn[node * 2 + r] = 0.0f;
+              }
+            }
+            if (bad) atomicOr(a.status, DEV_NONFINITE);
+          }
+        }
+      }
+      kb_run += nk;
+      ++tiles_run;
+      if (mode == 1) ++scales_run;
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      HQ_SOLVE_TRACE_POINT(p, 3);
+      if (*abort_f) break;
+    }
+    if (p < 3 && !grid_barrier(a.gbar, a.gbase + (unsigned long long)(p + 1) * gridDim.x, a.status, abort_f)) break;
+    HQ_SOLVE_TRACE_POINT(p, 4);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+  }
+  HQ_SOLVE_TRACE_POINT(3, 14);
+}
+
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
                               const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -308,6 +620,22 @@ int make_map(EncodeFn enc, CUtensorMap* map, void* ptr, uint64_t rows, uint64_t 
   cuuint32_t estr[2] = {1, 1};
   CUresult rc = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (rc != CUDA_SUCCESS) {
+    err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)rc) + ")";
+    return 1;
+  }
+  return 0;
+}
+
+// Unswizzled map with an arbitrary box (the FP32 scale tile).
+int make_map_plain(EncodeFn enc, CUtensorMap* map, CUtensorMapDataType dt, uint32_t esize, void* ptr, uint64_t rows,
+                   uint64_t cols, uint32_t box_x, uint32_t box_y, std::string& err) {
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * esize};
+  cuuint32_t box[2] = {box_x, box_y};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult rc = enc(map, dt, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (rc != CUDA_SUCCESS) {
     err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)rc) + ")";
     return 1;
@@ -340,13 +668,18 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
     return 1;
   }
   EncodeFn enc = reinterpret_cast<EncodeFn>(fn);
-  if (cudaFuncSetAttribute(k_dst_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128>::SMEM_BYTES) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_dst_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<64>::SMEM_BYTES) !=
-          cudaSuccess) {
-    err = "cannot raise the shared-memory limit of the DST GEMM";
+  constexpr int kSmem = SolveSmem::BYTES;
+  if (cudaFuncSetAttribute(k_dst_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem) != cudaSuccess) {
+    err = "cannot raise the shared-memory limit of the DST solve kernel";
     return 1;
   }
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dst_solve, 128, kSmem) != cudaSuccess || per_sm < 1 ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->dev) != cudaSuccess) {
+    err = "cannot size the cooperative DST solve";
+    return 1;
+  }
+  g->solve_ctas = per_sm * sms;
   g->tmaps = new TensorMaps();
   TensorMaps& t = *g->tmaps;
   const uint64_t nxp = g->nxp, nyp = g->nyp;
@@ -355,13 +688,13 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
   bad |= make_map(enc, &t.a0_lo, g->op_lo[0], kMaxRhs * nyp, nxp, err);
   bad |= make_map(enc, &t.a1_hi, g->op_hi[1], kMaxRhs * nxp, nyp, err);
   bad |= make_map(enc, &t.a1_lo, g->op_lo[1], kMaxRhs * nxp, nyp, err);
-  for (int i = 0; i < 2; ++i) {
-    const uint32_t rows = i == 0 ? 128 : 64;
-    bad |= make_map(enc, &t.sx_hi[i], g->sx_hi, nxp, nxp, err, rows);
-    bad |= make_map(enc, &t.sx_lo[i], g->sx_lo, nxp, nxp, err, rows);
-    bad |= make_map(enc, &t.sy_hi[i], g->sy_hi, nyp, nyp, err, rows);
-    bad |= make_map(enc, &t.sy_lo[i], g->sy_lo, nyp, nyp, err, rows);
-  }
+  // S_x, S_y (or the fold matrices, half as wide) as [rows][K]
+  const uint64_t kx = g->fold ? nxp / 2 : nxp, ky = g->fold ? nyp / 2 : nyp;
+  bad |= make_map(enc, &t.bx_hi, g->sx_hi, nxp, kx, err, kSolveBN);
+  bad |= make_map(enc, &t.bx_lo, g->sx_lo, nxp, kx, err, kSolveBN);
+  bad |= make_map(enc, &t.by_hi, g->sy_hi, nyp, ky, err, kSolveBN);
+  bad |= make_map(enc, &t.by_lo, g->sy_lo, nyp, ky, err, kSolveBN);
+  bad |= make_map_plain(enc, &t.scale, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->f32_scale, nyp, nxp, BM, kSolveBN, err);
   return bad;
 }
 
@@ -370,42 +703,59 @@ void dst_tc_free(hq_grid_s* g) {
   g->tmaps = nullptr;
 }
 
-// B_perp solve with the predictor-corrector mixing fused into the last product's epilogue:
-// sources (split, 2 rhs) in op[0] -> gf[3..4] <- w B + (1 - w) gf[3..4] (+ ring shift if last).
-void dst_solve_tc_bmix(hq_grid_s* g, int last, cudaStream_t s) {
+namespace {
+
+// One cooperative launch of k_dst_solve on the sources in op[0].
+void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s) {
   const TensorMaps& t = *g->tmaps;
-  const int nxp = g->nxp, nyp = g->nyp, R = 2;
-  Epi e{};
-  e = Epi{0, nyp, nxp, g->op_hi[1], g->op_lo[1], nullptr, nullptr, 0, 0};
-  gemm(t.a0_hi, t.a0_lo, t.sx_hi, t.sx_lo, R * nyp, nxp, nxp, e, g->d_status, s);
-  e = Epi{1, nxp, nyp, g->op_hi[0], g->op_lo[0], g->f32_scale, nullptr, 0, 0};
-  gemm(t.a1_hi, t.a1_lo, t.sy_hi, t.sy_lo, R * nxp, nyp, nyp, e, g->d_status, s);
-  e = Epi{0, nyp, nxp, g->op_hi[1], g->op_lo[1], nullptr, nullptr, 0, 0};
-  gemm(t.a0_hi, t.a0_lo, t.sx_hi, t.sx_lo, R * nyp, nxp, nxp, e, g->d_status, s);
-  e = Epi{3, nxp, nyp, nullptr, nullptr, nullptr, nullptr, g->nx, g->ny,
-          reinterpret_cast<float*>(g->gf), reinterpret_cast<float*>(g->bprev1), reinterpret_cast<float*>(g->bprev2),
-          reinterpret_cast<float*>(g->bjn), (float)g->d.pc_mix, last, g->d_status};
-  gemm(t.a1_hi, t.a1_lo, t.sy_hi, t.sy_lo, R * nxp, nyp, nyp, e, g->d_status, s);
+  SolveArgs a{};
+  a.R = R;
+  a.nxp = g->nxp;
+  a.nyp = g->nyp;
+  a.fold = g->fold;
+  a.op_hi[0] = g->op_hi[0];
+  a.op_lo[0] = g->op_lo[0];
+  a.op_hi[1] = g->op_hi[1];
+  a.op_lo[1] = g->op_lo[1];
+  a.scale = g->f32_scale;
+  a.final_mode = final_mode;
+  a.out = reinterpret_cast<float*>(g->solved);
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.gf = reinterpret_cast<float*>(g->gf);
+  a.b1 = reinterpret_cast<float*>(g->bprev1);
+  a.b2 = reinterpret_cast<float*>(g->bprev2);
+  a.bjn = reinterpret_cast<float*>(g->bjn);
+  a.w = (float)g->d.pc_mix;
+  a.last = last;
+  a.gbar = g->d_gbar;
+  a.gbase = g->gbar_base;
+  a.status = g->d_status;
+  const int tiles_x = R * (g->nyp / BM) * (g->nxp / kSolveBN), tiles_y = R * (g->nxp / BM) * (g->nyp / kSolveBN);
+  const int ctas = std::min(g->solve_ctas, std::max(tiles_x, tiles_y));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = SolveSmem::BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_dst_solve, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi, t.bx_lo, t.by_hi, t.by_lo,
+                     t.scale, a);
+  g->gbar_base += 3ull * (unsigned long long)ctas;
 }
 
-// sources (split) in op[0] [R][nyp][nxp] -> FP32 solution in g->solved [R][ny][nx]
-void dst_solve_tc(hq_grid_s* g, int R, cudaStream_t s) {
-  const TensorMaps& t = *g->tmaps;
-  const int nxp = g->nxp, nyp = g->nyp;
-  Epi e{};
-  // 1: (s S_x)^T -> op[1] [R][nxp][nyp]
-  e = Epi{0, nyp, nxp, g->op_hi[1], g->op_lo[1], nullptr, nullptr, 0, 0};
-  gemm(t.a0_hi, t.a0_lo, t.sx_hi, t.sx_lo, R * nyp, nxp, nxp, e, g->d_status, s);
-  // 2: S_y s S_x, scaled by (4/(nx ny))/lambda -> op[0] [R][nyp][nxp]
-  e = Epi{1, nxp, nyp, g->op_hi[0], g->op_lo[0], g->f32_scale, nullptr, 0, 0};
-  gemm(t.a1_hi, t.a1_lo, t.sy_hi, t.sy_lo, R * nxp, nyp, nyp, e, g->d_status, s);
-  // 3: (f_hat S_x)^T -> op[1]
-  e = Epi{0, nyp, nxp, g->op_hi[1], g->op_lo[1], nullptr, nullptr, 0, 0};
-  gemm(t.a0_hi, t.a0_lo, t.sx_hi, t.sx_lo, R * nyp, nxp, nxp, e, g->d_status, s);
-  // 4: S_y f_hat S_x -> FP32 [R][ny][nx]
-  e = Epi{2, nxp, nyp, nullptr, nullptr, nullptr, reinterpret_cast<float*>(g->solved), g->nx, g->ny};
-  gemm(t.a1_hi, t.a1_lo, t.sy_hi, t.sy_lo, R * nxp, nyp, nyp, e, g->d_status, s);
-}
+}  // namespace
+
+// B_perp solve with the predictor-corrector mixing fused into the last product's epilogue:
+// sources (split, 2 rhs) in op[0] -> gf[3..4] <- w B + (1 - w) gf[3..4] (+ ring shift if last).
+void dst_solve_tc_bmix(hq_grid_s* g, int last, cudaStream_t s) { solve_fused(g, 2, 3, last, s); }
+
+// sources (split) in op[0] -> FP32 solution in g->solved [R][ny][nx]
+void dst_solve_tc(hq_grid_s* g, int R, cudaStream_t s) { solve_fused(g, R, 2, 0, s); }
 
 }  // namespace hq
 

@@ -6,8 +6,9 @@
 //
 // Sources are written through a "sink": FP64 mode writes doubles in the solver's
 // [rhs][ny][nx] layout; FP32 mode writes each source already split into two bf16
-// terms (hi + lo) in the zero-padded [rhs][nyp][nxp] operand layout of the
-// tensor-core DST, so no separate conversion pass is needed.
+// terms (hi + lo) in the operand layout of the tensor-core DST (zero-padded
+// [rhs][nyp][nxp], or folded node pairs in slot order), so no separate conversion
+// pass is needed.
 #include "hq_internal.cuh"
 
 namespace hq {
@@ -29,22 +30,19 @@ template <typename T, typename Sink>
 __global__ void k_src_main(const V4<T>* __restrict__ dep, Geom gm, Sink sink) {
   pdl_trigger();
   pdl_wait();
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
-  if (ix >= gm.nx) return;
   const int nx = gm.nx;
   auto jx = [&](int y, int x) { return dep[(int64_t)y * nx + x].b; };
   auto jy = [&](int y, int x) { return dep[(int64_t)y * nx + x].c; };
-  T s0 = T(0), s1 = T(0), s2 = T(0);
-  if (ix > 0 && iy > 0) {
-    const V4<T> c = dep[(int64_t)iy * nx + ix];
-    const T i2x = T(gm.inv2dx), i2y = T(gm.inv2dy);
-    s0 = -(c.a - c.d);
-    s1 = dxc(jx, iy, ix, nx, i2x) + dyc(jy, iy, ix, gm.ny, i2y);
-    s2 = dyc(jx, iy, ix, gm.ny, i2y) - dxc(jy, iy, ix, nx, i2x);
-  }
-  sink.put(0, iy, ix, s0);
-  sink.put(1, iy, ix, s1);
-  sink.put(2, iy, ix, s2);
+  visit_nodes<3, T>(gm, sink, 3, [&](int iy, int ix, T* v) {
+    v[0] = v[1] = v[2] = T(0);
+    if (ix > 0 && iy > 0) {
+      const V4<T> c = dep[(int64_t)iy * nx + ix];
+      const T i2x = T(gm.inv2dx), i2y = T(gm.inv2dy);
+      v[0] = -(c.a - c.d);
+      v[1] = dxc(jx, iy, ix, nx, i2x) + dyc(jy, iy, ix, gm.ny, i2y);
+      v[2] = dyc(jx, iy, ix, gm.ny, i2y) - dxc(jy, iy, ix, nx, i2x);
+    }
+  });
 }
 
 // Bx: -dy Jz + dzeta Jy;  By: dx Jz - dzeta Jx, with dzeta J = (J(i-1) - J(i+1)) / (2 dzeta)
@@ -57,39 +55,35 @@ __global__ void k_src_bperp(const V4<T>* __restrict__ cur, V4<T>* prev, T* chi_p
                             V2<T>* tj, const V2<T>* __restrict__ bjn, Geom gm, Sink sink, int reset_prev) {
   pdl_trigger();
   pdl_wait();
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
-  if (ix >= gm.nx) return;
   const int nx = gm.nx;
-  const int64_t o = (int64_t)iy * nx + ix;
   auto jz = [&](int y, int x) { return cur[(int64_t)y * nx + x].d; };
-  const V4<T> pv = prev[o];
-  const V2<T> t = tj[o];
-  T s0 = T(0), s1 = T(0);
-  if (ix > 0 && iy > 0) {
-    const T i2z = T(gm.inv2dz);
-    const V2<T> b = bjn[o];
-    const T dzjx = (pv.b - (t.a + b.a)) * i2z;
-    const T dzjy = (pv.c - (t.b + b.b)) * i2z;
-    s0 = -dyc(jz, iy, ix, gm.ny, T(gm.inv2dy)) + dzjy;
-    s1 = dxc(jz, iy, ix, nx, T(gm.inv2dx)) - dzjx;
-  }
-  tj[o] = V2<T>{T(0), T(0)};
-  if (reset_prev) {
-    prev[o] = V4<T>{rho_ion[o], T(0), T(0), T(0)};
-    chi_prev[o] = T(0);
-  }
-  sink.put(0, iy, ix, s0);
-  sink.put(1, iy, ix, s1);
+  visit_nodes<2, T>(gm, sink, 2, [&](int iy, int ix, T* v) {
+    const int64_t o = (int64_t)iy * nx + ix;
+    const V4<T> pv = prev[o];
+    const V2<T> t = tj[o];
+    v[0] = v[1] = T(0);
+    if (ix > 0 && iy > 0) {
+      const T i2z = T(gm.inv2dz);
+      const V2<T> b = bjn[o];
+      const T dzjx = (pv.b - (t.a + b.a)) * i2z;
+      const T dzjy = (pv.c - (t.b + b.b)) * i2z;
+      v[0] = -dyc(jz, iy, ix, gm.ny, T(gm.inv2dy)) + dzjy;
+      v[1] = dxc(jz, iy, ix, nx, T(gm.inv2dx)) - dzjx;
+    }
+    tj[o] = V2<T>{T(0), T(0)};
+    if (reset_prev) {
+      prev[o] = V4<T>{rho_ion[o], T(0), T(0), T(0)};
+      chi_prev[o] = T(0);
+    }
+  });
 }
 
 template <typename T, typename Sink>
 __global__ void k_src_copy(const T* __restrict__ src, int nrhs, Geom gm, Sink sink) {
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
-  if (ix >= gm.nx) return;
-  for (int r = 0; r < nrhs; ++r) {
-    const T v = (ix > 0 && iy > 0) ? src[((int64_t)r * gm.ny + iy) * gm.nx + ix] : T(0);
-    sink.put(r, iy, ix, v);
-  }
+  visit_nodes<kMaxRhs, T>(gm, sink, nrhs, [&](int iy, int ix, T* v) {
+    for (int r = 0; r < kMaxRhs; ++r)
+      v[r] = (r < nrhs && ix > 0 && iy > 0) ? src[((int64_t)r * gm.ny + iy) * gm.nx + ix] : T(0);
+  });
 }
 
 // psi -> psi array and gf[0..1] = -grad psi; Ez -> gf[2]; Bz -> gf[5]; gf[3..4] = the
@@ -209,19 +203,24 @@ void launch_reset_dep(const hq_grid_s* g, void* dep, void* chi, cudaStream_t s) 
 }
 template <typename T>
 void launch_src_main(const hq_grid_s* g, const void* dep, cudaStream_t s) {
-  launch_pdl(k_src_main<T, decltype(SinkOf<T>::make(g))>, grid2d(g), 128, 0, s, reinterpret_cast<const V4<T>*>(dep),
-             g->geom, SinkOf<T>::make(g));
+  with_sink<T>(g, [&](auto sink) {
+    launch_pdl(k_src_main<T, decltype(sink)>, src_grid(g), 128, 0, s, reinterpret_cast<const V4<T>*>(dep), g->geom,
+               sink);
+  });
 }
 template <typename T>
 void launch_src_bperp(const hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int reset_prev, cudaStream_t s) {
-  launch_pdl(k_src_bperp<T, decltype(SinkOf<T>::make(g))>, grid2d(g), 128, 0, s,
-             reinterpret_cast<const V4<T>*>(cur), reinterpret_cast<V4<T>*>(prev), reinterpret_cast<T*>(chi_prev),
-             reinterpret_cast<const T*>(g->rho_ion), reinterpret_cast<V2<T>*>(g->tj),
-             reinterpret_cast<const V2<T>*>(g->bjn), g->geom, SinkOf<T>::make(g), reset_prev);
+  with_sink<T>(g, [&](auto sink) {
+    launch_pdl(k_src_bperp<T, decltype(sink)>, src_grid(g), 128, 0, s, reinterpret_cast<const V4<T>*>(cur),
+               reinterpret_cast<V4<T>*>(prev), reinterpret_cast<T*>(chi_prev), reinterpret_cast<const T*>(g->rho_ion),
+               reinterpret_cast<V2<T>*>(g->tj), reinterpret_cast<const V2<T>*>(g->bjn), g->geom, sink, reset_prev);
+  });
 }
 template <typename T>
 void launch_src_copy(const hq_grid_s* g, const void* src, int nrhs, cudaStream_t s) {
-  k_src_copy<T><<<grid2d(g), 128, 0, s>>>(reinterpret_cast<const T*>(src), nrhs, g->geom, SinkOf<T>::make(g));
+  with_sink<T>(g, [&](auto sink) {
+    k_src_copy<T, decltype(sink)><<<src_grid(g), 128, 0, s>>>(reinterpret_cast<const T*>(src), nrhs, g->geom, sink);
+  });
 }
 template <typename T>
 void launch_finish_main(const hq_grid_s* g, const void* res, cudaStream_t s) {

@@ -67,13 +67,15 @@ def rel(a, b):
 
 
 def directional(a, b, seed=0, k=3):
-    """Derivatives along random positive weight perturbations (no cancellation in the sum)."""
+    """Derivatives along random positive weight perturbations v: |v.(a - b)| relative to
+    sum_i |v_i b_i|, the size of the terms summed (the gradient has both signs, so
+    |v.b| itself can be much smaller than its terms)."""
     rng = np.random.default_rng(seed)
     worst = 0.0
     for _ in range(k):
         v = torch.tensor(np.abs(rng.standard_normal(a.shape[0])), dtype=torch.float64)
         x, y = float((a * v).sum()), float((b * v).sum())
-        worst = max(worst, abs(x - y) / (abs(y) + 1e-300))
+        worst = max(worst, abs(x - y) / (float((b * v).abs().sum()) + 1e-300))
     return worst
 
 

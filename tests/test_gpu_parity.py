@@ -10,12 +10,22 @@ Bars (derived in DESIGN.md):
     deposit node value perturbed by one ulp (relative 2^-52, the size of the
     error an unordered summation leaves) gives, per field and slice, the
     sweep's own rounding floor f (deviation over the field's peak slice norm).
-    The GPU's deviation must be below max(1e-12, 10 f).
+    One such sample swings by ~10x from slice to slice (even/odd alternation),
+    and a perturbation made at slice j is carried to every later slice, so the
+    floor envelope at slice i is the running maximum of f over slices <= i.
+    The GPU's deviation must be below max(1e-12, 10 x envelope).
   * FP32/bf16x3 path: each bf16x3 product carries ~2^-17 relative error, so a
     4-product Dirichlet solve is good to a few 1e-5 (rel-L2); sweeps are held to
-    the on-axis Ez (first plasma period) <= 1e-4 and bucket <= 1e-3 bounds.
+    the on-axis Ez (first plasma period) <= 1e-4 and bucket <= 1e-3 bounds.  Where a
+    field is tiny against the charge densities that source it (psi and Ez at the
+    head of the 512^2 driver), FP32 rounding of the B-spline weights dominates: the
+    centre weight 0.75 - d^2 cannot hold d^2 below half an FP32 ulp, so every
+    slightly displaced particle deposits (1 + d^2) of its charge against the fixed
+    ion background.  There the bar is measured like the FP64 one: an oracle run with
+    FP32 weights gives the floor, and the GPU must stay within 10x its envelope.
   * integer work (beam binning) is bit-exact: per-slice particle counts.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -76,7 +86,8 @@ def assert_fp64_sweep(out, ref, ref_perm, fields, factor=10.0, spec=None):
     for k in fields:
         e = peak_err(out[k], ref.fields[k])
         f = peak_err(ref_perm.fields[k], ref.fields[k])
-        bar = torch.clamp(factor * f, min=1e-12)
+        env = torch.cummax(f, dim=0).values
+        bar = torch.clamp(factor * env, min=1e-12)
         worst = int(torch.argmax(e / bar))
         print(f"fp64 {k}: max dev {float(e.max()):.2e}, reorder floor {float(f.max()):.2e}, "
               f"worst slice {worst}: {float(e[worst]):.2e} vs bar {float(bar[worst]):.2e}")
@@ -294,6 +305,8 @@ def test_blowout512_head_full_size(hq):
     ref_perm = O.sweep(sp, [O.as_beam(b) for b in reordered(beams)], n_slices=nsamp, record=rec,
                        plasma_perm=plasma_perm(g),
                      reverse_ion_order=True, deposit_noise=2.0 ** -52)
+    ref_w32 = O.sweep(dataclasses.replace(sp, weight_dtype="float32"), [O.as_beam(b) for b in beams],
+                      n_slices=nsamp, record=rec)
     assert float(ref.fields["rho"].abs().max()) > 0.1  # the beam is in the sample
     for prec in ("fp64", "fp32"):
         gg = dict(g)
@@ -310,10 +323,16 @@ def test_blowout512_head_full_size(hq):
         if prec == "fp64":
             assert_fp64_sweep(out, ref, ref_perm, rec, spec=sp)
         else:
+            c = g["nx"] // 2
+            print("fp32 on-axis Ez rel-L2", rel(out["ez"][:, c, c], ref.fields["ez"][:, c, c]))
             for k in rec:
-                e = float(peak_err(out[k], ref.fields[k]).max())
-                print("fp32", k, e)
-                assert e <= 1e-3, (k, e)
+                e = peak_err(out[k], ref.fields[k])
+                f = peak_err(ref_w32.fields[k], ref.fields[k])
+                bar = torch.clamp(10.0 * torch.cummax(f, dim=0).values, min=1e-5)
+                worst = int(torch.argmax(e / bar))
+                print(f"fp32 {k}: max dev {float(e.max()):.2e}, FP32-weight floor {float(f.max()):.2e}, "
+                      f"worst slice {worst}: {float(e[worst]):.2e} vs bar {float(bar[worst]):.2e}")
+                assert bool((e <= bar).all()), (k, worst, float(e[worst]), float(bar[worst]))
 
 
 def test_blowout512_full_sweep_properties(hq):
