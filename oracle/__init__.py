@@ -22,5 +22,6 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   beam binning         pinned: brute-force bin membership
   beam push            pinned: uniform-B gyration, uniform-E energy gain, time reversibility
   blowout-regime physics (cfg 512^2 n_b=5): parity unpinned beyond the checks above
+  working_precision    a test knob: the same steps in another float type (rounding floors)
 """
 from .qsa import *  # noqa: F401,F403

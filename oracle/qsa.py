@@ -36,6 +36,7 @@ Readings of the paper (it is silent or only cites a reference on these points):
 """
 from __future__ import annotations
 
+import contextlib
 import math
 from dataclasses import dataclass, field
 from typing import Optional, Sequence
@@ -44,6 +45,23 @@ import torch
 
 DT = torch.float64
 DEV = torch.device("cpu")
+
+
+@contextlib.contextmanager
+def working_precision(dtype: torch.dtype):
+    """Evaluate the oracle in another floating-point type inside the block.
+
+    The method is FP64 (the default).  ``working_precision(torch.float32)`` runs the
+    same steps with every tensor in single precision: a test knob that measures the
+    single-precision rounding floor of the algorithm, against which a mixed-precision
+    implementation is judged.  Not re-entrant across threads."""
+    global DT
+    old = DT
+    DT = dtype
+    try:
+        yield
+    finally:
+        DT = old
 
 # Fifth-order Adams-Bashforth weights (Sec. 3.2 plasma push): beta_k for f_{i-k}.
 AB5 = (1901.0 / 720.0, -2774.0 / 720.0, 2616.0 / 720.0, -1274.0 / 720.0, 251.0 / 720.0)

@@ -53,7 +53,7 @@ void free_all(hq_grid_s* g) {
       F(p.ux); F(p.uy); F(p.w); F(p.hist); F(p.cell); F(p.fx); F(p.fy); F(p.opp);
     }
   }
-  for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); }
+  for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); F(g->psrc[i]); }
   F(g->rho_ion); F(g->tj); F(g->bjn); F(g->gf); F(g->psi); F(g->bprev1); F(g->bprev2); F(g->solved);
   F(g->f64_a); F(g->f64_b); F(g->f64_scale); F(g->tw_x); F(g->tw_y); F(g->sin_x); F(g->sin_y);
   F(g->sx_hi); F(g->sx_lo); F(g->sy_hi); F(g->sy_lo); F(g->f32_scale);
@@ -126,7 +126,7 @@ struct Snap {
 struct AdjStore {
   int k = 0, nseg = 0;
   std::vector<Snap> ck;
-  std::vector<void*> ck_dep0, ck_dep1, ck_chi0, ck_chi1, ck_b1, ck_b2;
+  std::vector<void*> ck_dep0, ck_dep1, ck_chi0, ck_chi1, ck_b1, ck_b2, ck_ps0, ck_ps1;
   std::vector<Snap> tape;
   std::vector<void*> tape_gf, tape_b;
   int tape_slot = -1;       // tape slot of the slice being solved (-1: not taping)
@@ -279,6 +279,7 @@ void advance_impl(hq_grid_s* g, int slice) {
     launch_plasma_init<T>(g, s);
     launch_deposit_initial<T>(g, g->dep[0], g->chi[0], 0, s);
     launch_zero<T>(g->dep[1], 4 * g->nnode, s);   // J(-1) = 0 ahead of the box
+    if (!g->fp64) launch_zero<float>(g->psrc[1], g->nnode, s);
     launch_zero<T>(g->bprev1, 2 * g->nnode, s);
     launch_zero<T>(g->bprev2, 2 * g->nnode, s);
     launch_zero<T>(g->bjn, 2 * g->nnode, s);
@@ -384,10 +385,11 @@ hq_status adj_alloc(hq_grid_s* g, int k) {
   a->ck.resize(a->nseg);
   a->ck_dep0.resize(a->nseg); a->ck_dep1.resize(a->nseg); a->ck_chi0.resize(a->nseg); a->ck_chi1.resize(a->nseg);
   a->ck_b1.resize(a->nseg); a->ck_b2.resize(a->nseg);
+  a->ck_ps0.assign(a->nseg, nullptr); a->ck_ps1.assign(a->nseg, nullptr);
   for (int i = 0; ok && i < a->nseg; ++i)
     ok = snap(a->ck[i]) && A(&a->ck_dep0[i], 4 * ts * nn) && A(&a->ck_dep1[i], 4 * ts * nn) &&
          A(&a->ck_chi0[i], ts * nn) && A(&a->ck_chi1[i], ts * nn) && A(&a->ck_b1[i], 2 * ts * nn) &&
-         A(&a->ck_b2[i], 2 * ts * nn);
+         A(&a->ck_b2[i], 2 * ts * nn) && (g->fp64 || (A(&a->ck_ps0[i], 4 * nn) && A(&a->ck_ps1[i], 4 * nn)));
   a->tape.resize(k);
   a->tape_gf.resize(k);
   a->tape_b.resize(k);
@@ -419,6 +421,10 @@ void ckpt_copy(hq_grid_s* g, int seg, bool save) {
   cp(a->ck_chi1[seg], g->chi[1], ts * nn);
   cp(a->ck_b1[seg], g->bprev1, 2 * ts * nn);
   cp(a->ck_b2[seg], g->bprev2, 2 * ts * nn);
+  if (!g->fp64) {
+    cp(a->ck_ps0[seg], g->psrc[0], 4 * nn);
+    cp(a->ck_ps1[seg], g->psrc[1], 4 * nn);
+  }
 }
 
 // Runs slices [a0, a1) from the state after hq_advance_slice(a0), taping slices >= tape_from.
@@ -658,6 +664,11 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   }
   // fields
   for (int i = 0; i < 2; ++i) { HQ_ALLOC(g->dep[i], 4 * ts * nn); HQ_ALLOC(g->chi[i], ts * nn); }
+  if (!g->fp64)
+    for (int i = 0; i < 2; ++i) {
+      HQ_ALLOC(g->psrc[i], 4 * nn);
+      cudaMemset(g->psrc[i], 0, 4 * nn);
+    }
   HQ_ALLOC(g->rho_ion, ts * nn);
   HQ_ALLOC(g->tj, 2 * ts * nn);
   HQ_ALLOC(g->bjn, 2 * ts * nn);

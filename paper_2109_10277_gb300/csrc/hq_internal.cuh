@@ -135,6 +135,7 @@ struct hq_grid_s {
   float* f32_scale;                          // [nyp][nxp] (1/lambda)(4/(nx ny)), slot order if folded
   hq::TensorMaps* tmaps;
   int fold;                                  // folded DST-I (nx, ny multiples of 128; FP32 mode)
+  float* psrc[2];                            // FP32 mode: psi source rho - J_z of dep[0], dep[1]
   unsigned long long* d_gbar;                // grid-barrier counter of the fused solve kernel
   unsigned long long gbar_base;              // its value before the next launch
   int solve_ctas;                            // CTAs of the fused solve (co-resident)
@@ -398,6 +399,18 @@ inline void with_sink(const hq_grid_s* g, F&& f) {
 inline dim3 src_grid(const hq_grid_s* g) {
   const int w = g->fold ? g->nx / 2 : g->nx;
   return dim3((unsigned)((w + 127) / 128), (unsigned)g->ny);
+}
+
+// FP32 path: the psi source rho - J_z accumulated beside a deposit record (ion-subtracted per
+// particle, see k_particles); null in FP64 mode, which forms rho - J_z from the record.
+inline float* psrc_of(const hq_grid_s* g, const void* dep) {
+  if (g->fp64) return nullptr;
+  return dep == g->dep[0] ? g->psrc[0] : dep == g->dep[1] ? g->psrc[1] : nullptr;
+}
+
+// 1 - u_z / gamma without cancellation for u_z > 0: (1 + u_perp^2) / (gamma (gamma + u_z)).
+__device__ __forceinline__ float one_minus_vz(float ux, float uy, float uz, float gamma) {
+  return uz > 0.0f ? (1.0f + ux * ux + uy * uy) / (gamma * (gamma + uz)) : 1.0f - uz / gamma;
 }
 
 // Central difference helpers with wall nodes (index 0 and n) reading zero; the

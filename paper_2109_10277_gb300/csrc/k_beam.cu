@@ -87,7 +87,7 @@ __device__ __forceinline__ int stencil_t(double x, double x0, double dx, double 
 // slice i+1 into bjn: rho = q w S / (dx dy dzeta), J = rho u / gamma (in the field type).
 template <int P, typename T>
 __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm,
-                               int slice, int nz, Geom gm, V4<T>* dep, V2<T>* bjn) {
+                               int slice, int nz, Geom gm, V4<T>* dep, V2<T>* bjn, float* ps) {
   pdl_trigger();
   pdl_wait();
   const int a0 = off[slice], a1 = off[slice + 1];
@@ -106,6 +106,9 @@ __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, 
     const int ix0 = stencil_t<P, T>(v.x[p], gm.xmin, gm.dx, gm.inv_dx, wx);
     const int iy0 = stencil_t<P, T>(v.y[p], gm.ymin, gm.dy, gm.inv_dy, wy);
     const T cx = ux * ig, cy = uy * ig, cz = uz * ig;
+    // FP32 path: this particle's share of the psi source, rho (1 - v_z), without cancellation
+    float omvz = 0.0f;
+    if constexpr (sizeof(T) == 4) omvz = one_minus_vz(ux, uy, uz, 1.0f / ig);
 #pragma unroll
     for (int b = 0; b <= P; ++b) {
       const int iy = iy0 + b;
@@ -122,6 +125,7 @@ __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, 
           atomicAdd(&q->b, s * cx);
           atomicAdd(&q->c, s * cy);
           atomicAdd(&q->d, s * cz);
+          if (ps) atomicAdd(ps + node, float(s) * omvz);
         } else {
           V2<T>* q = bjn + node;
           atomicAdd(&q->a, s * cx);
@@ -274,7 +278,8 @@ void launch_beam_deposit(const hq_grid_s* g, int b, const hq_beam_view& v, int s
   const BeamBins& bb = g->bins[b];
   HQ_SHAPE_SWITCH(g->d.shape_order,
                   (launch_pdl(k_beam_deposit<P, T>, dim3(kSliceBlocks), dim3(kThreads), (size_t)0, s, v, bb.offset, bb.perm,
-                             slice, g->nz, g->geom, reinterpret_cast<V4<T>*>(dep), reinterpret_cast<V2<T>*>(bjn))));
+                             slice, g->nz, g->geom, reinterpret_cast<V4<T>*>(dep), reinterpret_cast<V2<T>*>(bjn),
+                             psrc_of(g, dep))));
 }
 template <typename T>
 void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double dt, cudaStream_t s) {

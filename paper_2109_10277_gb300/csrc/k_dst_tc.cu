@@ -359,8 +359,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
   __syncthreads();
   if (threadIdx.x == 0) {
     if (!*abort_f) {
-      __threadfence();
-      atomicAdd(ctr, 1ull);
+      asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(ctr) : "memory");
       const long long t0 = clock64();
       uint32_t it = 0;
       while (true) {
@@ -449,13 +448,19 @@ __global__ void __launch_bounds__(128, 1)
 
   // stage-ring, accumulator and scale-tile counters across tiles
   uint32_t kb_run = 0, tiles_run = 0, scales_run = 0;
+  auto phase_geom = [&](int q, int& P1, int& P2, int& mt, int& tiles, int& nk) {
+    const bool ax = (q & 1) == 0;
+    P1 = ax ? a.nyp : a.nxp;
+    P2 = ax ? a.nxp : a.nyp;
+    mt = a.R * P1 / BM;
+    tiles = mt * (P2 / BN);
+    nk = (a.fold ? P2 / 2 : P2) / BK;
+  };
   for (int p = 0; p < 4; ++p) {
     HQ_SOLVE_TRACE_POINT(p, 0);
     const bool along_x = (p & 1) == 0;
-    const int P1 = along_x ? a.nyp : a.nxp;   // rows per right-hand side
-    const int P2 = along_x ? a.nxp : a.nyp;   // output columns (= contraction extent)
-    const int mt = a.R * P1 / BM, tiles = mt * (P2 / BN);
-    const int nk = (a.fold ? P2 / 2 : P2) / BK;
+    int P1, P2, mt, tiles, nk;   // rows per rhs, output columns (= contraction extent), tiles, K blocks
+    phase_geom(p, P1, P2, mt, tiles, nk);
     const CUtensorMap* tah = along_x ? &a0h : &a1h;
     const CUtensorMap* tal = along_x ? &a0l : &a1l;
     const CUtensorMap* tbh = along_x ? &bxh : &byh;
@@ -475,9 +480,9 @@ __global__ void __launch_bounds__(128, 1)
         for (int kb = 0; kb < nk; ++kb) {
           const uint32_t g = kb_run + kb;
           const int s = g % STAGES;
-          if (g >= STAGES && !mbar_wait_a(empty0 + 8 * s, ((g / STAGES) - 1) & 1, a.status, abort_f)) break;
           const uint32_t st = base + s * STAGE_BYTES;
           const uint32_t fb = full0 + 8 * s;
+          if (g >= STAGES && !mbar_wait_a(empty0 + 8 * s, ((g / STAGES) - 1) & 1, a.status, abort_f)) break;
           mbar_expect_tx(fb, STAGE_BYTES);
           tma_load_2d(st, tah, koff + kb * BK, m0, fb);
           tma_load_2d(st + A_BYTES, tal, koff + kb * BK, m0, fb);
@@ -743,9 +748,11 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s) 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_dst_solve, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi, t.bx_lo, t.by_hi, t.by_lo,
-                     t.scale, a);
-  g->gbar_base += 3ull * (unsigned long long)ctas;
+  // the barrier counter advances only if the kernel was launched (a launch error is
+  // reported by the caller's launch check)
+  if (cudaLaunchKernelEx(&cfg, k_dst_solve, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi, t.bx_lo, t.by_hi, t.by_lo,
+                         t.scale, a) == cudaSuccess)
+    g->gbar_base += 3ull * (unsigned long long)ctas;
 }
 
 }  // namespace

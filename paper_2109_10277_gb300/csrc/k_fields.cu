@@ -18,16 +18,18 @@ namespace {
 constexpr int kThreads = 256;
 
 template <typename T>
-__global__ void k_reset_dep(V4<T>* dep, T* chi, const T* rho_ion, int64_t nn) {
+__global__ void k_reset_dep(V4<T>* dep, T* chi, const T* rho_ion, float* ps, int64_t nn) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nn) return;
   dep[i] = V4<T>{rho_ion[i], T(0), T(0), T(0)};
   chi[i] = T(0);
+  if (ps) ps[i] = 0.0f;   // ion-subtracted: the ion background enters per particle
 }
 
-// psi: -(rho - Jz);  Ez: dx Jx + dy Jy;  Bz: dy Jx - dx Jy.
+// psi: -(rho - Jz);  Ez: dx Jx + dy Jy;  Bz: dy Jx - dx Jy.  With ps (FP32 path) the psi
+// source is the separately accumulated rho - Jz.
 template <typename T, typename Sink>
-__global__ void k_src_main(const V4<T>* __restrict__ dep, Geom gm, Sink sink) {
+__global__ void k_src_main(const V4<T>* __restrict__ dep, const float* __restrict__ ps, Geom gm, Sink sink) {
   pdl_trigger();
   pdl_wait();
   const int nx = gm.nx;
@@ -38,7 +40,7 @@ __global__ void k_src_main(const V4<T>* __restrict__ dep, Geom gm, Sink sink) {
     if (ix > 0 && iy > 0) {
       const V4<T> c = dep[(int64_t)iy * nx + ix];
       const T i2x = T(gm.inv2dx), i2y = T(gm.inv2dy);
-      v[0] = -(c.a - c.d);
+      v[0] = ps ? T(-ps[(int64_t)iy * nx + ix]) : -(c.a - c.d);
       v[1] = dxc(jx, iy, ix, nx, i2x) + dyc(jy, iy, ix, gm.ny, i2y);
       v[2] = dyc(jx, iy, ix, gm.ny, i2y) - dxc(jy, iy, ix, nx, i2x);
     }
@@ -51,8 +53,9 @@ __global__ void k_src_main(const V4<T>* __restrict__ dep, Geom gm, Sink sink) {
 // last iteration the slice i-1 record is reset to the ion background, ready to
 // receive the deposit of slice i+1.
 template <typename T, typename Sink>
-__global__ void k_src_bperp(const V4<T>* __restrict__ cur, V4<T>* prev, T* chi_prev, const T* __restrict__ rho_ion,
-                            V2<T>* tj, const V2<T>* __restrict__ bjn, Geom gm, Sink sink, int reset_prev) {
+__global__ void k_src_bperp(const V4<T>* __restrict__ cur, V4<T>* prev, T* chi_prev, float* ps_prev,
+                            const T* __restrict__ rho_ion, V2<T>* tj, const V2<T>* __restrict__ bjn, Geom gm,
+                            Sink sink, int reset_prev) {
   pdl_trigger();
   pdl_wait();
   const int nx = gm.nx;
@@ -74,6 +77,7 @@ __global__ void k_src_bperp(const V4<T>* __restrict__ cur, V4<T>* prev, T* chi_p
     if (reset_prev) {
       prev[o] = V4<T>{rho_ion[o], T(0), T(0), T(0)};
       chi_prev[o] = T(0);
+      if (ps_prev) ps_prev[o] = 0.0f;
     }
   });
 }
@@ -162,8 +166,8 @@ __global__ void k_bshift(V2<T>* b1, V2<T>* b2, const T* gf, int64_t nn) {
 }
 
 template <typename T>
-__global__ void k_store(hq_field_out out, int64_t base, const V4<T>* dep, const T* chi, const T* psi,
-                        const T* gf, int64_t nn) {
+__global__ void k_store(hq_field_out out, int64_t base, const V4<T>* dep, const float* ps, const T* chi,
+                        const T* psi, const T* gf, int64_t nn) {
   pdl_trigger();
   pdl_wait();
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -171,7 +175,9 @@ __global__ void k_store(hq_field_out out, int64_t base, const V4<T>* dep, const 
   const V4<T> d = dep[o];
   const T* q = gf + o * kGF;
   const int64_t t = base + o;
-  if (out.rho) reinterpret_cast<T*>(out.rho)[t] = d.a;
+  // FP32 path: rho = (rho - J_z) + J_z from the ion-subtracted psi source (the rho record holds
+  // the unit ion background, against which the plasma response is lost to rounding)
+  if (out.rho) reinterpret_cast<T*>(out.rho)[t] = ps ? T(ps[o]) + d.d : d.a;
   if (out.jx) reinterpret_cast<T*>(out.jx)[t] = d.b;
   if (out.jy) reinterpret_cast<T*>(out.jy)[t] = d.c;
   if (out.jz) reinterpret_cast<T*>(out.jz)[t] = d.d;
@@ -199,21 +205,23 @@ inline dim3 grid2d(const hq_grid_s* g) { return dim3((unsigned)((g->nx + 127) / 
 template <typename T>
 void launch_reset_dep(const hq_grid_s* g, void* dep, void* chi, cudaStream_t s) {
   k_reset_dep<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(reinterpret_cast<V4<T>*>(dep), reinterpret_cast<T*>(chi),
-                                                         reinterpret_cast<const T*>(g->rho_ion), g->nnode);
+                                                         reinterpret_cast<const T*>(g->rho_ion), psrc_of(g, dep),
+                                                         g->nnode);
 }
 template <typename T>
 void launch_src_main(const hq_grid_s* g, const void* dep, cudaStream_t s) {
   with_sink<T>(g, [&](auto sink) {
-    launch_pdl(k_src_main<T, decltype(sink)>, src_grid(g), 128, 0, s, reinterpret_cast<const V4<T>*>(dep), g->geom,
-               sink);
+    launch_pdl(k_src_main<T, decltype(sink)>, src_grid(g), 128, 0, s, reinterpret_cast<const V4<T>*>(dep),
+               static_cast<const float*>(psrc_of(g, dep)), g->geom, sink);
   });
 }
 template <typename T>
 void launch_src_bperp(const hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int reset_prev, cudaStream_t s) {
   with_sink<T>(g, [&](auto sink) {
     launch_pdl(k_src_bperp<T, decltype(sink)>, src_grid(g), 128, 0, s, reinterpret_cast<const V4<T>*>(cur),
-               reinterpret_cast<V4<T>*>(prev), reinterpret_cast<T*>(chi_prev), reinterpret_cast<const T*>(g->rho_ion),
-               reinterpret_cast<V2<T>*>(g->tj), reinterpret_cast<const V2<T>*>(g->bjn), g->geom, sink, reset_prev);
+               reinterpret_cast<V4<T>*>(prev), reinterpret_cast<T*>(chi_prev), psrc_of(g, prev),
+               reinterpret_cast<const T*>(g->rho_ion), reinterpret_cast<V2<T>*>(g->tj),
+               reinterpret_cast<const V2<T>*>(g->bjn), g->geom, sink, reset_prev);
   });
 }
 template <typename T>
@@ -248,8 +256,9 @@ void launch_bshift(const hq_grid_s* g, cudaStream_t s) {
 template <typename T>
 void launch_store(const hq_grid_s* g, const hq_field_out* out, int64_t slot, const void* dep, const void* chi, cudaStream_t s) {
   launch_pdl(k_store<T>, blocks_for(g->nnode), kThreads, 0, s, *out, slot * g->nnode,
-             reinterpret_cast<const V4<T>*>(dep), reinterpret_cast<const T*>(chi), reinterpret_cast<const T*>(g->psi),
-             reinterpret_cast<const T*>(g->gf), g->nnode);
+             reinterpret_cast<const V4<T>*>(dep), static_cast<const float*>(psrc_of(g, dep)),
+             reinterpret_cast<const T*>(chi), reinterpret_cast<const T*>(g->psi), reinterpret_cast<const T*>(g->gf),
+             g->nnode);
 }
 template <typename T>
 void launch_zero(void* p, int64_t n, cudaStream_t s) {

@@ -103,6 +103,16 @@ __device__ __forceinline__ T ab5_comb(const T* __restrict__ hist, int64_t n, int
   return acc;
 }
 
+// u_z = (1 + u_perp^2 - (1 + psi)^2) / (2 (1 + psi)) (the quasi-static constant of motion
+// gamma - u_z = 1 + psi).  FP64 evaluates it as written (the oracle's arithmetic); FP32 as
+// (u_perp^2 - psi (2 + psi)) g / 2 with psi (2 + psi) from the FP64 psi, since in FP32 the
+// written form subtracts numbers near 1 and loses the plasma's small u_z.
+template <typename T>
+__device__ __forceinline__ T uz_of(T ux, T uy, T opp, double psi, T g) {
+  if constexpr (sizeof(T) == 8) return (T(1) + ux * ux + uy * uy - opp * opp) * T(0.5) * g;
+  else return (ux * ux + uy * uy - T(psi * (2.0 + psi))) * T(0.5) * g;
+}
+
 template <int P, typename T>
 __device__ __forceinline__ void deposit_full(V4<T>* dep, T* chi, int nx, int ny, int ix0, int iy0,
                                              const T* wx, const T* wy, T rho, T jx, T jy, T jz, T ch) {
@@ -238,7 +248,7 @@ __global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* 
   const T opp = T(1.0 + pl.psi[p]);
   const T g = T(1) / opp;
   const T gam = (T(1) + ux * ux + uy * uy + opp * opp) * T(0.5) * g;
-  const T uz = (T(1) + ux * ux + uy * uy - opp * opp) * T(0.5) * g;
+  const T uz = uz_of<T>(ux, uy, opp, pl.psi[p], g);
   deposit_full<P, T>(dep, chi, gm.nx, gm.ny, ix0, iy0, wx, wy, qw * gam * g, qw * ux * g, qw * uy * g,
                      qw * uz * g, qw * T(-1) * g);
 }
@@ -313,17 +323,185 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
   deposit_perp<P, T>(tj, gm.nx, gm.ny, tix0, tiy0, twx, twy, qw * tux * tg, qw * tuy * tg);
 }
 
+// ---------------------------------------------------------------- FP32 psi source
+// A plasma particle's share of the psi source rho - J_z (Eq. for psi) is q w S(x): rho_p - J_zp
+// = q w (gamma - u_z) / (1 + psi) S with gamma - u_z = 1 + psi.  The FP32 path accumulates the
+// source ion-subtracted, q w (S(x) - S(x0)) with x0 the particle's initial position (the ion
+// it left behind), so the unit ion background never meets the small plasma response in an
+// FP32 sum.  When both stencils share their base node the weight differences are formed as
+// exact polynomial differences carrying the factor (x - x0); otherwise the two stencils are
+// deposited with opposite signs.  Node coordinates u = (x - x_min) / dx are FP64.
+
+// Initial node coordinates of plasma particle p (the placement of k_plasma_init).
+__device__ __forceinline__ void initial_coord(int64_t p, const Geom& gm, int ppx, int ppy, double& u0, double& v0) {
+  const int ppc = ppx * ppy;
+  const int64_t c = p / ppc;
+  const int sub = (int)(p - c * ppc);
+  u0 = (double)(c % gm.nx) + ((double)(sub % ppx) + 0.5) / ppx;
+  v0 = (double)(c / gm.nx) + ((double)(sub / ppx) + 0.5) / ppy;
+}
+
+// Weights w at u, w0 at u0 (bases b, b0) and, when b == b0, dw = w - w0 from the polynomial
+// differences (each proportional to u - u0).
+template <int P>
+__device__ __forceinline__ void weight_diff(double u, double u0, float* w, float* w0, float* dw, int& b, int& b0) {
+  const double jf = floor(u), jf0 = floor(u0);
+  const float d = (float)(u - jf), d0 = (float)(u0 - jf0);
+  b = shape_weights<P, float>((int)jf, d, w);
+  b0 = shape_weights<P, float>((int)jf0, d0, w0);
+  if (b != b0) return;
+  const float dl = (float)(u - u0);
+  if constexpr (P == 0) {
+    dw[0] = 0.0f;
+  } else if constexpr (P == 1) {
+    dw[0] = -dl;
+    dw[1] = dl;
+  } else if constexpr (P == 2) {
+    // offsets from the shared nearest node: e - e0 = u - u0
+    const float s = (d >= 0.5f ? d - 1.0f : d) + (d0 >= 0.5f ? d0 - 1.0f : d0);
+    dw[0] = -0.5f * dl * (1.0f - s);
+    dw[1] = -dl * s;
+    dw[2] = 0.5f * dl * (1.0f + s);
+  } else {
+    const float s = d + d0, q = d * d + d * d0 + d0 * d0;
+    const float a = (1.0f - d) * (1.0f - d) + (1.0f - d) * (1.0f - d0) + (1.0f - d0) * (1.0f - d0);
+    const float k = dl * (1.0f / 6.0f);
+    dw[0] = -k * a;
+    dw[1] = k * (3.0f * q - 6.0f * s);
+    dw[2] = k * (3.0f + 3.0f * s - 3.0f * q);
+    dw[3] = k * q;
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void add_stencil(float* ps, int nx, int ny, int bx, int by, const float* wx, const float* wy,
+                                            float q) {
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const int iy = by + b;
+    if (!in_interior(iy, ny)) continue;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      const int ix = bx + a;
+      if (in_interior(ix, nx)) atomicAdd(ps + (int64_t)iy * nx + ix, q * wx[a] * wy[b]);
+    }
+  }
+}
+
+// Quadratic B-spline B2(t) (t = u - node) and B2(t0 + dl) - B2(t0) for an exact dl: within one
+// polynomial piece the difference carries the factor dl; across a piece boundary tb it is split
+// there, (B2(t) - B2(tb)) + (B2(tb) - B2(t0)), with t - tb = (t0 - tb) + dl.  t0 (a start offset
+// on the half-cell lattice) and tb are exact in FP32, so every factor is formed without
+// cancellation.
+__device__ __forceinline__ int b2_piece(float t) {
+  const float a = fabsf(t);
+  return a < 0.5f ? 0 : (a < 1.5f ? (t > 0.0f ? 1 : -1) : (t > 0.0f ? 2 : -2));
+}
+__device__ __forceinline__ float b2_value(float t) {
+  const float a = fabsf(t);
+  return a < 0.5f ? 0.75f - t * t : (a < 1.5f ? 0.5f * (1.5f - a) * (1.5f - a) : 0.0f);
+}
+__device__ __forceinline__ float b2_within(float t, float t0, float dl, int pc) {
+  if (pc == 0) return -dl * (t + t0);
+  if (pc == 1 || pc == -1) return -0.5f * (pc > 0 ? dl : -dl) * (3.0f - fabsf(t) - fabsf(t0));
+  return 0.0f;
+}
+__device__ __forceinline__ float b2_diff(float t0, float dl) {
+  const float t = t0 + dl;
+  const int p = b2_piece(t), p0 = b2_piece(t0);
+  if (p == p0) return b2_within(t, t0, dl, p);
+  const float tb = (float)(p < p0 ? p : p0) + 0.5f;   // adjacent pieces: boundary at lo + 1/2
+  return b2_within(t, tb, (t0 - tb) + dl, p) + b2_within(tb, t0, tb - t0, p0);
+}
+
+// q w (S(u, v) - S(u0, v0)) into ps.
+template <int P>
+__device__ __forceinline__ void deposit_psi_src(float* ps, const Geom& gm, double u, double v, double u0, double v0,
+                                                float qw) {
+  if constexpr (P == 2) {
+    // quadratic: the cell-centred start sits on a piece boundary, so the two stencils' bases
+    // differ by one for about half the particles; difference over the 4-node union support.
+    // With |u - u0| < 1 each node's offset crosses at most one piece boundary (pieces are one
+    // cell wide), which b2_diff handles; farther moves take the two-stencil path below.
+    const int bx = (int)floor(u + 0.5) - 1, bx0 = (int)floor(u0 + 0.5) - 1;
+    const int by = (int)floor(v + 0.5) - 1, by0 = (int)floor(v0 + 0.5) - 1;
+    if (fabs(u - u0) < 1.0 && fabs(v - v0) < 1.0) {
+      const int jx = bx < bx0 ? bx : bx0, jy = by < by0 ? by : by0;
+      const float dlx = (float)(u - u0), dly = (float)(v - v0);
+      const float tx0 = (float)(u0 - (double)jx), ty0 = (float)(v0 - (double)jy);   // node jx, jy offsets
+      float wy[4], w0x[4], dwx[4], dwy[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float sx0 = tx0 - (float)k, sy0 = ty0 - (float)k;
+        w0x[k] = b2_value(sx0);
+        wy[k] = b2_value(sy0 + dly);
+        dwx[k] = b2_diff(sx0, dlx);
+        dwy[k] = b2_diff(sy0, dly);
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int iy = jy + b;
+        if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int ix = jx + a;
+          const float val = dwx[a] * wy[b] + w0x[a] * dwy[b];
+          if (val != 0.0f && in_interior(ix, gm.nx)) atomicAdd(ps + (int64_t)iy * gm.nx + ix, qw * val);
+        }
+      }
+      return;
+    }
+  }
+  float wx[P + 1], w0x[P + 1], dwx[P + 1], wy[P + 1], w0y[P + 1], dwy[P + 1];
+  int bx, bx0, by, by0;
+  weight_diff<P>(u, u0, wx, w0x, dwx, bx, bx0);
+  weight_diff<P>(v, v0, wy, w0y, dwy, by, by0);
+  if (bx == bx0 && by == by0) {
+    // S - S0 = (wx - w0x) wy + w0x (wy - w0y)
+#pragma unroll
+    for (int b = 0; b <= P; ++b) {
+      const int iy = by + b;
+      if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        const int ix = bx + a;
+        if (in_interior(ix, gm.nx)) atomicAdd(ps + (int64_t)iy * gm.nx + ix, qw * (dwx[a] * wy[b] + w0x[a] * dwy[b]));
+      }
+    }
+  } else {
+    add_stencil<P>(ps, gm.nx, gm.ny, bx, by, wx, wy, qw);
+    add_stencil<P>(ps, gm.nx, gm.ny, bx0, by0, w0x, w0y, -qw);
+  }
+}
+
+// The ion left behind by a removed particle: -q w S(u0, v0).
+template <int P>
+__device__ __forceinline__ void deposit_ion_src(float* ps, const Geom& gm, double u0, double v0, float qw) {
+  float wx[P + 1], wy[P + 1];
+  const double jx = floor(u0), jy = floor(v0);
+  const int bx = shape_weights<P, float>((int)jx, (float)(u0 - jx), wx);
+  const int by = shape_weights<P, float>((int)jy, (float)(v0 - jy), wy);
+  add_stencil<P>(ps, gm.nx, gm.ny, bx, by, wx, wy, -qw);
+}
+
 // ---------------------------------------------------------------- final pass
 // Gather with the converged fields of slice i, store f_i in the AB5 history,
 // advance to slice i+1, apply the removal rule and deposit rho, J, chi there.
 template <int P, typename T, bool CACHE>
 __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf,
-                                                         V4<T>* dep, T* chi, int slice, double guard,
-                                                         unsigned long long* removed) {
+                                                         V4<T>* dep, T* chi, float* ps, int ppx, int ppy, int slice,
+                                                         double guard, unsigned long long* removed) {
   pdl_trigger();
   pdl_wait();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= pl.n || !pl.alive[p]) return;
+  if (p >= pl.n) return;
+  double u0 = 0.0, v0 = 0.0;
+  if (ps) initial_coord(p, gm, ppx, ppy, u0, v0);
+  if (!pl.alive[p]) {
+    if constexpr (sizeof(T) == 4)
+      if (ps) deposit_ion_src<P>(ps, gm, u0, v0, charge_density<T>(pl.w[p], gm));
+    return;
+  }
   const int64_t n = pl.n;
   T wx[P + 1], wy[P + 1];
   int ix0, iy0;
@@ -357,6 +535,8 @@ __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, 
   if (!state_ok(gm, nxp, nyp, nopp, guard)) {
     pl.alive[p] = 0;
     atomicAdd(removed, 1ull);
+    if constexpr (sizeof(T) == 4)
+      if (ps) deposit_ion_src<P>(ps, gm, u0, v0, charge_density<T>(pl.w[p], gm));
     return;
   }
   pl.x[p] = nxp;
@@ -384,9 +564,11 @@ __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, 
   const T qw = charge_density<T>(pl.w[p], gm);
   const T g = T(1) / topp;
   const T gam = (T(1) + nux * nux + nuy * nuy + topp * topp) * T(0.5) * g;
-  const T uz = (T(1) + nux * nux + nuy * nuy - topp * topp) * T(0.5) * g;
+  const T uz = uz_of<T>(nux, nuy, topp, npsi, g);
   deposit_full<P, T>(dep, chi, gm.nx, gm.ny, ix0, iy0, wx, wy, qw * gam * g, qw * nux * g, qw * nuy * g,
                      qw * uz * g, qw * T(-1) * g);
+  if constexpr (sizeof(T) == 4)
+    if (ps) deposit_psi_src<P>(ps, gm, (nxp - gm.xmin) * gm.inv_dx, (nyp - gm.ymin) * gm.inv_dy, u0, v0, qw);
 }
 
 template <typename T> Plasma<T> plasma_of(const hq_grid_s* g);
@@ -442,11 +624,13 @@ void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cuda
   constexpr bool C = sizeof(T) == 4;
   const double gd = g->d.psi_guard;
   unsigned long long* rm = g->d_removed;
+  float* ps = psrc_of(g, dep);
+  const int px = g->d.ppc_x, py = g->d.ppc_y;
   switch (g->d.shape_order) {
-    case 0: launch_pdl(k_final_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
-    case 1: launch_pdl(k_final_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
-    case 2: launch_pdl(k_final_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
-    default: launch_pdl(k_final_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, slice, gd, rm); break;
+    case 0: launch_pdl(k_final_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, slice, gd, rm); break;
+    case 1: launch_pdl(k_final_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, slice, gd, rm); break;
+    case 2: launch_pdl(k_final_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, slice, gd, rm); break;
+    default: launch_pdl(k_final_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, slice, gd, rm); break;
   }
 }
 

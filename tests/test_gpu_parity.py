@@ -16,16 +16,13 @@ Bars (derived in DESIGN.md):
     The GPU's deviation must be below max(1e-12, 10 x envelope).
   * FP32/bf16x3 path: each bf16x3 product carries ~2^-17 relative error, so a
     4-product Dirichlet solve is good to a few 1e-5 (rel-L2); sweeps are held to
-    the on-axis Ez (first plasma period) <= 1e-4 and bucket <= 1e-3 bounds.  Where a
-    field is tiny against the charge densities that source it (psi and Ez at the
-    head of the 512^2 driver), FP32 rounding of the B-spline weights dominates: the
-    centre weight 0.75 - d^2 cannot hold d^2 below half an FP32 ulp, so every
-    slightly displaced particle deposits (1 + d^2) of its charge against the fixed
-    ion background.  There the bar is measured like the FP64 one: an oracle run with
-    FP32 weights gives the floor, and the GPU must stay within 10x its envelope.
+    the on-axis Ez (first plasma period) <= 1e-4 and bucket <= 1e-3 bounds.  At the
+    head of the 512^2 driver every field is held to 1e-4 of its peak, although psi
+    there (~1e-6) is the difference of unit charge densities: the FP32 path keeps
+    the psi source ion-subtracted per particle (an all-FP32 evaluation of the method,
+    printed for reference, is off by ~100% there).
   * integer work (beam binning) is bit-exact: per-slice particle counts.
 """
-import dataclasses
 import math
 
 import numpy as np
@@ -288,7 +285,7 @@ def test_sweep_fp32_blowout_reduced(hq):
     e_psi = rel(out["psi"][bucket], ref.fields["psi"][bucket])
     print("fp32 blowout128: on-axis Ez first period", e_axis, "bucket Ez", e_bucket, "psi", e_psi,
           "removed", removed, ref.removed)
-    assert e_axis <= 1e-3 and e_bucket <= 1e-2, (e_axis, e_bucket)
+    assert e_axis <= 1e-4 and e_bucket <= 1e-3, (e_axis, e_bucket)
 
 
 # ---------------------------------------------------------------- full-size workload checks
@@ -305,8 +302,8 @@ def test_blowout512_head_full_size(hq):
     ref_perm = O.sweep(sp, [O.as_beam(b) for b in reordered(beams)], n_slices=nsamp, record=rec,
                        plasma_perm=plasma_perm(g),
                      reverse_ion_order=True, deposit_noise=2.0 ** -52)
-    ref_w32 = O.sweep(dataclasses.replace(sp, weight_dtype="float32"), [O.as_beam(b) for b in beams],
-                      n_slices=nsamp, record=rec)
+    with O.working_precision(torch.float32):
+        ref_f32 = O.sweep(sp, [O.as_beam(b) for b in beams], n_slices=nsamp, record=rec)
     assert float(ref.fields["rho"].abs().max()) > 0.1  # the beam is in the sample
     for prec in ("fp64", "fp32"):
         gg = dict(g)
@@ -324,14 +321,17 @@ def test_blowout512_head_full_size(hq):
             assert_fp64_sweep(out, ref, ref_perm, rec, spec=sp)
         else:
             c = g["nx"] // 2
-            print("fp32 on-axis Ez rel-L2", rel(out["ez"][:, c, c], ref.fields["ez"][:, c, c]))
+            axis = rel(out["ez"][:, c, c], ref.fields["ez"][:, c, c])
+            axis_f = rel(ref_f32.fields["ez"][:, c, c].double(), ref.fields["ez"][:, c, c])
+            print("fp32 on-axis Ez rel-L2", axis, "all-FP32 oracle", axis_f)
+            assert axis <= 1e-4, (axis, axis_f)
             for k in rec:
                 e = peak_err(out[k], ref.fields[k])
-                f = peak_err(ref_w32.fields[k], ref.fields[k])
-                bar = torch.clamp(10.0 * torch.cummax(f, dim=0).values, min=1e-5)
+                f = peak_err(ref_f32.fields[k].double(), ref.fields[k])
+                bar = torch.full_like(e, 1e-4)
                 worst = int(torch.argmax(e / bar))
-                print(f"fp32 {k}: max dev {float(e.max()):.2e}, FP32-weight floor {float(f.max()):.2e}, "
-                      f"worst slice {worst}: {float(e[worst]):.2e} vs bar {float(bar[worst]):.2e}")
+                print(f"fp32 {k}: max dev {float(e.max()):.2e} (bar 1e-4), all-FP32 oracle {float(f.max()):.2e}, "
+                      f"worst slice {worst}: {float(e[worst]):.2e}")
                 assert bool((e <= bar).all()), (k, worst, float(e[worst]), float(bar[worst]))
 
 

@@ -169,3 +169,23 @@ def test_plasma_permutation_only_reorders_sums():
     for k in ("ez", "bx"):
         assert float((a.fields[k] - b.fields[k]).abs().max()) <= 1e-9 * float(a.fields[k].abs().max())
     assert torch.allclose(a.plasma["x"], b.plasma["x"], rtol=0, atol=1e-12)
+
+
+def test_working_precision_knob():
+    """working_precision(float32) runs the same steps in single precision (a floor probe):
+    fields come out FP32, differ from the FP64 sweep by a small nonzero amount, and the
+    default precision is restored afterwards (an FP64 rerun is bit-identical)."""
+    g = linear_grid(nx=24, nz=14, order=2)
+    sp = O.GridSpec(**g)
+    beams = [O.as_beam(I.random_beam(3000, 0.6, 0.6, 1.0, 0.8, zeta0=2.0, seed=5))]
+    ref = O.sweep(sp, beams, record=("ez", "psi"))
+    with O.working_precision(torch.float32):
+        r32 = O.sweep(sp, [O.as_beam(I.random_beam(3000, 0.6, 0.6, 1.0, 0.8, zeta0=2.0, seed=5))],
+                      record=("ez", "psi"))
+    again = O.sweep(sp, [O.as_beam(I.random_beam(3000, 0.6, 0.6, 1.0, 0.8, zeta0=2.0, seed=5))],
+                    record=("ez", "psi"))
+    for k in ("ez", "psi"):
+        assert r32.fields[k].dtype == torch.float32
+        d = float(torch.linalg.norm(r32.fields[k].double() - ref.fields[k]) / torch.linalg.norm(ref.fields[k]))
+        assert 0.0 < d < 1e-3, (k, d)
+        assert torch.equal(again.fields[k], ref.fields[k])
