@@ -179,10 +179,13 @@ def run_reference(args):
 
 def dst_flops_per_sweep(g: dict) -> float:
     """Executed bf16 flops of the tensor-core DST-I per sweep: per solve of R right-hand
-    sides, 4 products of 2 M N K with M = R x padded rows, times 3 (bf16x3)."""
+    sides, 4 products of 2 M N K with M = R x padded rows, times 3 (bf16x3).  With nx, ny
+    multiples of 128 the solve uses the folded DST-I: every output contracts over K = n/2."""
     nxp = -(-g["nx"] // 128) * 128
     nyp = -(-g["ny"] // 128) * 128
-    per_rhs = 2 * (2.0 * nyp * nxp * nxp) + 2 * (2.0 * nxp * nyp * nyp)
+    folded = g["nx"] % 128 == 0 and g["ny"] % 128 == 0
+    kx, ky = (nxp // 2, nyp // 2) if folded else (nxp, nyp)
+    per_rhs = 2 * (2.0 * nyp * nxp * kx) + 2 * (2.0 * nxp * nyp * ky)
     rhs_per_slice = 3 + 2 * g["n_pc_iter"]
     return 3.0 * per_rhs * rhs_per_slice * g["nzeta"]
 
