@@ -177,6 +177,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the current build (cold L2):
+# k_dst_solve on 512^2 with 3 rhs (the operands read once) and k_final_pass on the 512^2
+# plasma slice; the capture commands are recorded with their summaries under profiles/.
+NCU_TRAFFIC = {"dst": 5.325824e6, "final": 49.540096e6}
+
+
 def dst_flops_per_sweep(g: dict) -> float:
     """Executed bf16 flops of the tensor-core DST-I per sweep: per solve of R right-hand
     sides, 4 products of 2 M N K with M = R x padded rows, times 3 (bf16x3).  With nx, ny
@@ -317,7 +323,8 @@ def run_hq(args):
             ach = fl / (prof["dst"][0] / 1e3) / 1e12
             pk = peaks["bf16_tflops_sustained"]
             roofs["dst"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                            "traffic": None, "avg_launch_us": 1e3 * prof["dst"][0] / max(1, prof["dst"][1]),
+                            "traffic": NCU_TRAFFIC.get("dst") if g["nx"] == 512 and g["ny"] == 512 else None,
+                            "avg_launch_us": 1e3 * prof["dst"][0] / max(1, prof["dst"][1]),
                             "peak_src": f"bf16 sustained, {peak_src}"}
     for k, nb in (("trial", BYTES_TRIAL), ("final", BYTES_FINAL)):
         if prof[k][0] > 0 and args.precision == "fp32":
@@ -325,7 +332,8 @@ def run_hq(args):
             ach = nb * p * nl / (prof[k][0] / 1e3) / 1e9
             pk = peaks["hbm_gbs"]
             roofs[k] = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
-                        "traffic": None, "avg_launch_us": 1e3 * prof[k][0] / nl, "peak_src": f"hbm copy, {peak_src}"}
+                        "traffic": NCU_TRAFFIC.get(k) if g["nx"] == 512 and g["ny"] == 512 else None,
+                        "avg_launch_us": 1e3 * prof[k][0] / nl, "peak_src": f"hbm copy, {peak_src}"}
     roof = dict(roofs.get(dom, next(iter(roofs.values()), {})))
     if roof:
         roof["kernel"] = dom
