@@ -50,7 +50,7 @@ void free_all(hq_grid_s* g) {
     hq::Plasma<float>& p = g->p32;
     if (!g->fp64) {
       // x, y, psi, alive are shared with p64 storage (freed above); free the typed arrays
-      F(p.ux); F(p.uy); F(p.w); F(p.hist); F(p.cell); F(p.fx); F(p.fy); F(p.opp);
+      F(p.ux); F(p.uy); F(p.w); F(p.hist); F(p.cell); F(p.fx); F(p.fy); F(p.opp); F(p.hsum);
     }
   }
   for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); F(g->psrc[i]); }
@@ -117,7 +117,7 @@ struct Snap {
   void *ux = nullptr, *uy = nullptr, *hist = nullptr;
   uint8_t* alive = nullptr;
   int32_t* cell = nullptr;
-  float *fx = nullptr, *fy = nullptr, *opp = nullptr;
+  float *fx = nullptr, *fy = nullptr, *opp = nullptr, *hsum = nullptr;
 };
 
 // Checkpoints every k slices (plasma + the field records a slice starts from), the
@@ -166,6 +166,7 @@ void snap_copy(hq_grid_s* g, Snap& d, bool save) {
     cp(d.fx, g->p32.fx, 4 * np);
     cp(d.fy, g->p32.fy, 4 * np);
     cp(d.opp, g->p32.opp, 4 * np);
+    cp(d.hsum, g->p32.hsum, 4 * np * 5);
   }
 }
 
@@ -378,7 +379,7 @@ hq_status adj_alloc(hq_grid_s* g, int k) {
               A((void**)&d.alive, np) && A(&d.ux, ts * np) && A(&d.uy, ts * np) && A(&d.hist, ts * np * kRing * 5);
     if (ok && !g->fp64)
       ok = A((void**)&d.cell, 4 * np) && A((void**)&d.fx, 4 * np) && A((void**)&d.fy, 4 * np) &&
-           A((void**)&d.opp, 4 * np);
+           A((void**)&d.opp, 4 * np) && A((void**)&d.hsum, 4 * np * 5);
     return ok;
   };
   bool ok = true;
@@ -661,6 +662,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     HQ_ALLOC(g->p32.ux, 4 * np); HQ_ALLOC(g->p32.uy, 4 * np); HQ_ALLOC(g->p32.w, 4 * np);
     HQ_ALLOC(g->p32.hist, 4 * np * kRing * 5);
     HQ_ALLOC(g->p32.cell, 4 * np); HQ_ALLOC(g->p32.fx, 4 * np); HQ_ALLOC(g->p32.fy, 4 * np); HQ_ALLOC(g->p32.opp, 4 * np);
+    HQ_ALLOC(g->p32.hsum, 4 * np * 5);
   }
   // fields
   for (int i = 0; i < 2; ++i) { HQ_ALLOC(g->dep[i], 4 * ts * nn); HQ_ALLOC(g->chi[i], ts * nn); }

@@ -64,6 +64,10 @@ template <typename T> struct Plasma {
   float* fx;         // fractional node coordinate in x, [0, 1)
   float* fy;
   float* opp;        // 1 + Psi, formed in FP64, rounded once
+  // FP32 mode: the history part of the AB5 step of the current slice, sum_{k=1..4} beta_k
+  // f_{i-k}, [5][n]: the same for all predictor-corrector trial passes of the slice, so they
+  // read 5 values instead of the 20 of the ring (written by the final pass).
+  float* hsum;
 };
 
 // Per-beam slice binning (counting sort by slice, Sec. 3.1).

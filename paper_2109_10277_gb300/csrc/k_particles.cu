@@ -206,6 +206,8 @@ __global__ void k_plasma_init(Plasma<T> pl, Geom gm, int ppx, int ppy, const dou
   pl.w[p] = T(n0s * dens * (gm.dx * gm.dy / (double)ppc));
   pl.alive[p] = 1;
   for (int k = 0; k < kRing * 5; ++k) pl.hist[(int64_t)k * pl.n + p] = T(0);
+  if (pl.hsum)
+    for (int c = 0; c < 5; ++c) pl.hsum[(int64_t)c * pl.n + p] = 0.0f;
   if (pl.cell) {
     int jx, jy;
     double fx, fy;
@@ -287,11 +289,16 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
   T f[5];
   derivs<T>(ux, uy, opp, F, f);
   const T dz = CACHE ? T(gm.f_dz) : T(gm.dzeta);
-  const T cx = ab5_comb<T>(pl.hist, n, p, slice, 0, f[0]);
-  const T cy = ab5_comb<T>(pl.hist, n, p, slice, 1, f[1]);
-  const T tux = ux - dz * ab5_comb<T>(pl.hist, n, p, slice, 2, f[2]);
-  const T tuy = uy - dz * ab5_comb<T>(pl.hist, n, p, slice, 3, f[3]);
-  const T cpsi = ab5_comb<T>(pl.hist, n, p, slice, 4, f[4]);
+  // AB5 combination beta_0 f_i + sum_{k>=1} beta_k f_{i-k}; FP32 reads the precomputed history part
+  auto comb = [&](int c) -> T {
+    if constexpr (CACHE) return T(ab5(0)) * f[c] + T(pl.hsum[(int64_t)c * n + p]);
+    else return ab5_comb<T>(pl.hist, n, p, slice, c, f[c]);
+  };
+  const T cx = comb(0);
+  const T cy = comb(1);
+  const T tux = ux - dz * comb(2);
+  const T tuy = uy - dz * comb(3);
+  const T cpsi = comb(4);
   T twx[P + 1], twy[P + 1];
   int tix0, tiy0;
   T topp;
@@ -521,7 +528,22 @@ __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, 
   derivs<T>(ux, uy, opp, F, f);
   T comb[5];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) comb[c] = ab5_comb<T>(pl.hist, n, p, slice, c, f[c]);
+  for (int c = 0; c < 5; ++c) {
+    T h[kRing + 1];   // h[k] = f_{i-k}
+#pragma unroll
+    for (int k = 1; k <= kRing; ++k) h[k] = pl.hist[((int64_t)(((slice - k) % kRing + kRing) % kRing) * 5 + c) * n + p];
+    T acc = T(ab5(0)) * f[c];
+#pragma unroll
+    for (int k = 1; k <= kRing; ++k) acc += T(ab5(k)) * h[k];
+    comb[c] = acc;
+    if constexpr (CACHE) {
+      // history part of the next slice's step: beta_1 f_i + beta_2 f_{i-1} + ... + beta_4 f_{i-3}
+      T hn = T(ab5(1)) * f[c];
+#pragma unroll
+      for (int k = 2; k <= kRing; ++k) hn += T(ab5(k)) * h[k - 1];
+      pl.hsum[(int64_t)c * n + p] = float(hn);
+    }
+  }
   const int slot = slice % kRing;
 #pragma unroll
   for (int c = 0; c < 5; ++c) pl.hist[((int64_t)slot * 5 + c) * n + p] = f[c];
