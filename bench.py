@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-slices", type=int, default=12, help="oracle sample: slices of the workload")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the cubic1024 and adjoint512 legs and the cuFFT DST comparator")
+    ap.add_argument("--cubic-steps", type=int, default=1,
+                    help="beam time steps of the cubic1024 leg (the workload defines 10)")
     ap.add_argument("--case", choices=("sweep", "poisson"), default="sweep",
                     help="poisson: only repeated 3-RHS Dirichlet solves on the workload grid (for ncu captures)")
     return ap.parse_args()
@@ -241,6 +245,154 @@ def adjoint_leg(hq, I, stream, flush, name="adjoint256", ckpt_every=32):
             "device_bytes_used": int(used)}
 
 
+def cubic_leg(hq, I, stream, flush, steps=1):
+    """1024^2 x 1024 slices, 4 ppc (4.2M plasma particles per slice), cubic shape, driver 1e7 +
+    witness 2e6 macroparticles, beam push with dt = 20 after every slice: per-slice throughput."""
+    import torch
+    g = I.grid_params("cubic1024")
+    free0 = torch.cuda.mem_get_info()[0]
+    grid = hq.Grid(g, precision="fp32", stream=stream)
+    beams = [hq.Beam(b) for b in I.workload_beams("cubic1024")]
+    p = g["nx"] * g["ny"] * g["ppc_x"] * g["ppc_y"]
+    grid.sweep(beams, dt=20.0)   # warm-up: also the first beam time step
+    grid.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(5)
+    a.record(stream)
+    for _ in range(steps):
+        grid.sweep(beams, dt=20.0)
+    b.record(stream)
+    torch.cuda.synchronize()
+    removed = grid.sync()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    ms = a.elapsed_time(b)
+    grid.close()
+    return {"workload": "cubic1024: 1024x1024 grid on +-10 x 1024 slices over [-18, 6], 4 ppc (4,194,304 per slice), "
+                        "cubic shape, driver 1e7 (sigma_r=0.15, sigma_z=1.2, n_b=10) + witness 2e6 (zeta0=-6), "
+                        "beam push dt=20 per time step, FP32/bf16x3",
+            "time_steps": steps + 1, "timed_steps": steps, "ms_per_step": ms / steps,
+            "ms_per_slice": ms / steps / g["nzeta"],
+            "value": p * g["nzeta"] * steps / (ms / 1e3), "unit": "particle-slices/s",
+            "removed_particles": removed, "device_bytes_used": int(used)}
+
+
+def adjoint_scale_leg(hq, I, stream, flush, ckpt_every=32):
+    """adjoint512: 512^2 x 1024 slices, 2 ppc, quadratic, 256-entry radial profile, fixed-ppc driver
+    with a free 1024-entry slice current profile; loss = witness mean Ez + rms spread; one full
+    gradient: adjoint/forward time and peak device memory."""
+    import torch
+    g = I.grid_params("adjoint512")
+    free0 = torch.cuda.mem_get_info()[0]
+    grid = hq.Grid(g, precision="fp32", stream=stream)
+    bnp = I.workload_beams("adjoint512")
+    beams = [hq.Beam(b) for b in bnp]
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    sums.zero_()
+    grid.sweep(beams, witness=1, witness_sums=sums)   # warm-up
+    grid.sync()
+    a, b, c, d, e = ev(), ev(), ev(), ev(), ev()
+    flush.fill_(6)
+    sums.zero_()
+    a.record(stream)
+    grid.sweep(beams, witness=1, witness_sums=sums)
+    b.record(stream)
+    sums.zero_()
+    c.record(stream)
+    grid.forward_ckpt(beams, 1, sums, ckpt_every)
+    d.record(stream)
+    loss, dls = hq.witness_loss_grad("mean+rms", *[float(v) for v in sums.cpu()])
+    grid.sync()
+    used_fwd = free0 - torch.cuda.mem_get_info()[0]
+    e0 = ev()
+    e0.record(stream)
+    res = grid.adjoint(beams, 1, dls)
+    e.record(stream)
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    # gradient w.r.t. the driver's 1024-entry slice current profile: w_p = prof[s_p] * shape_p
+    s_idx = torch.as_tensor(bnp[0]["slice_index"], device="cuda")
+    w0 = beams[0].t["w"]
+    nz = g["nzeta"]
+    zc = g["zeta_max"] - (torch.arange(nz, device="cuda", dtype=torch.float64) + 0.5) * (
+        (g["zeta_max"] - g["zeta_min"]) / nz)
+    prof = 4.0 * torch.exp(-zc ** 2 / (2.0 * 1.4 ** 2))
+    dprof = torch.zeros(nz, dtype=torch.float64, device="cuda").index_add_(0, s_idx, res["beam_w"][0] * w0 / prof[s_idx])
+    fwd, ck, adj = a.elapsed_time(b), c.elapsed_time(d), e0.elapsed_time(e)
+    out = {"workload": "adjoint512: 512x512 x 1024 slices, 2 ppc, quadratic, 256-entry radial profile, fixed-ppc "
+                       "driver with a 1024-entry slice current profile (peak n_b=4) + witness, loss = witness mean "
+                       f"Ez + rms Ez spread, FP32/bf16x3, checkpoint every {ckpt_every}",
+           "forward_ms": fwd, "forward_ckpt_ms": ck, "adjoint_ms": adj, "adjoint_over_forward": adj / fwd,
+           "ckpt_forward_plus_adjoint_over_forward": (ck + adj) / fwd, "loss": loss,
+           "grad_norms": {"slice_profile": float(torch.linalg.norm(dprof)),
+                          "radial_profile": float(torch.linalg.norm(res["profile"])),
+                          "n0_scale": float(res["n0_scale"][0])},
+           "grads_finite": bool(torch.isfinite(dprof).all() and torch.isfinite(res["profile"]).all()),
+           "device_bytes_peak": int(used), "device_bytes_forward_ckpt": int(used_fwd)}
+    grid.close()
+    return out
+
+
+def cufft_dst_solve(src, lam_inv):
+    """Library comparator: the same Dirichlet solve through cuFFT (torch.fft): DST-I of each row via
+    the FFT of its odd extension, along x then y, scale, and the same two transforms again."""
+    import torch
+
+    def dst_rows(v):   # DST-I along the last axis, nodes 0..n-1 with node 0 on the wall
+        n = v.shape[-1]
+        ext = torch.cat([v, torch.zeros_like(v[..., :1]), -v[..., 1:].flip(-1)], dim=-1)
+        return -0.5 * torch.fft.rfft(ext, dim=-1)[..., :n].imag
+
+    t = dst_rows(src)
+    t = dst_rows(t.transpose(-1, -2)).transpose(-1, -2)
+    t = t * lam_inv
+    t = dst_rows(t)
+    return dst_rows(t.transpose(-1, -2)).transpose(-1, -2)
+
+
+def dst_comparator(hq, I, stream):
+    """Times the tensor-core Dirichlet solve (3 rhs, 512^2) against the cuFFT-based one."""
+    import math
+    import torch
+    g = I.grid_params(WORKLOAD)
+    nx, ny = g["nx"], g["ny"]
+    dx, dy = (g["xmax"] - g["xmin"]) / nx, (g["ymax"] - g["ymin"]) / ny
+    grid = hq.Grid(g, precision="fp32", stream=stream)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    src = torch.randn(3, ny, nx, device="cuda", generator=gen)
+    src[:, 0, :] = 0
+    src[:, :, 0] = 0
+    k = torch.arange(nx, device="cuda", dtype=torch.float64)
+    l = torch.arange(ny, device="cuda", dtype=torch.float64)
+    lam = -(4 / dx ** 2) * torch.sin(math.pi * k / (2 * nx)) ** 2 - (4 / dy ** 2) * torch.sin(math.pi * l[:, None] / (2 * ny)) ** 2
+    lam_inv = torch.where(lam != 0, (4.0 / (nx * ny)) / lam, torch.zeros_like(lam)).float()
+    lam_inv[0, :] = 0
+    lam_inv[:, 0] = 0
+    ours = grid.poisson_solve(src)
+    lib = cufft_dst_solve(src, lam_inv)
+    torch.cuda.synchronize()
+    agree = float(torch.linalg.norm(ours - lib) / torch.linalg.norm(lib))
+
+    def timed(fn, n=50):
+        for _ in range(5):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return 1e3 * a.elapsed_time(b) / n
+
+    us_ours = timed(lambda: grid.poisson_solve(src))
+    us_lib = timed(lambda: cufft_dst_solve(src, lam_inv))
+    grid.close()
+    return {"case": "Dirichlet solve, 512x512, 3 right-hand sides, FP32 data",
+            "tensor_core_dst_us": us_ours, "cufft_dst_us": us_lib, "rel_l2_between": agree,
+            "note": "tensor-core path: one fused cooperative launch (plus the source copy kernel); cuFFT path: "
+                    "torch.fft rfft of the odd extension, 4 batched transforms + elementwise ops"}
+
+
 def run_hq(args):
     import torch
     world, rank, local = dist_setup("nccl")
@@ -360,6 +512,18 @@ def run_hq(args):
     if not args.no_adjoint and args.precision == "fp32":
         adjoint = adjoint_leg(hq, I, stream, flush)
 
+    cubic = adjoint512 = dstcmp = None
+    if not args.no_extra and args.precision == "fp32" and rank == 0:
+        grid.close()
+        grid = None
+        torch.cuda.empty_cache()
+        cubic = cubic_leg(hq, I, stream, flush, args.cubic_steps)
+        torch.cuda.empty_cache()
+        if not args.no_adjoint:
+            adjoint512 = adjoint_scale_leg(hq, I, stream, flush)
+            torch.cuda.empty_cache()
+        dstcmp = dst_comparator(hq, I, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(args.cpu_slices)
@@ -381,10 +545,12 @@ def run_hq(args):
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
             "gpu_launches": launches_per_sweep * args.steps,
-            "fp64": fp64, "adjoint": adjoint, "cpu_baseline": cpu, "removed_particles": removed,
+            "fp64": fp64, "adjoint": adjoint, "cubic1024": cubic, "adjoint512": adjoint512,
+            "dst_comparator": dstcmp, "cpu_baseline": cpu, "removed_particles": removed,
         }
         print(json.dumps(line), flush=True)
-    grid.close()
+    if grid is not None:
+        grid.close()
 
 
 def run_poisson_case(args):

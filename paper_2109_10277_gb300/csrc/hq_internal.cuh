@@ -412,6 +412,12 @@ inline float* psrc_of(const hq_grid_s* g, const void* dep) {
   return dep == g->dep[0] ? g->psrc[0] : dep == g->dep[1] ? g->psrc[1] : nullptr;
 }
 
+template <typename T> struct SrcMain;
+template <typename T> struct SrcBperp;
+template <typename T> SrcMain<T> src_main_of(const hq_grid_s* g, const void* dep);
+template <typename T> SrcBperp<T> src_bperp_of(const hq_grid_s* g, const void* cur, void* prev, void* chi_prev,
+                                               int reset_prev);
+
 // 1 - u_z / gamma without cancellation for u_z > 0: (1 + u_perp^2) / (gamma (gamma + u_z)).
 __device__ __forceinline__ float one_minus_vz(float ux, float uy, float uz, float gamma) {
   return uz > 0.0f ? (1.0f + ux * ux + uy * uy) / (gamma * (gamma + uz)) : 1.0f - uz / gamma;
@@ -432,6 +438,83 @@ __device__ __forceinline__ auto dyc(const A& f, int iy, int ix, int ny, C inv2dy
   const T u = iy + 1 < ny ? f(iy + 1, ix) : T(0);
   const T d = f(iy - 1, ix);
   return (u - d) * T(inv2dy);
+}
+
+
+// ---------------------------------------------------------------- per-node sources
+// The field equations' sources (Sec. 2), one node at a time (visited by the source kernels
+// of k_fields.cu through the grid's operand sink).
+
+// psi: -(rho - Jz);  Ez: dx Jx + dy Jy;  Bz: dy Jx - dx Jy.  With ps (FP32 path) the psi
+// source is the separately accumulated, ion-subtracted rho - Jz.
+template <typename T> struct SrcMain {
+  static constexpr int NR = 3;
+  const V4<T>* dep;
+  const float* ps;
+  Geom gm;
+  __device__ void operator()(int iy, int ix, T* v) const {
+    const int nx = gm.nx;
+    auto jx = [&](int y, int x) { return dep[(int64_t)y * nx + x].b; };
+    auto jy = [&](int y, int x) { return dep[(int64_t)y * nx + x].c; };
+    v[0] = v[1] = v[2] = T(0);
+    if (ix > 0 && iy > 0) {
+      const V4<T> c = dep[(int64_t)iy * nx + ix];
+      const T i2x = T(gm.inv2dx), i2y = T(gm.inv2dy);
+      v[0] = ps ? T(-ps[(int64_t)iy * nx + ix]) : -(c.a - c.d);
+      v[1] = dxc(jx, iy, ix, nx, i2x) + dyc(jy, iy, ix, gm.ny, i2y);
+      v[2] = dyc(jx, iy, ix, gm.ny, i2y) - dxc(jy, iy, ix, nx, i2x);
+    }
+  }
+};
+
+// Bx: -dy Jz + dzeta Jy;  By: dx Jz - dzeta Jx, with dzeta J = (J(i-1) - J(i+1)) / (2 dzeta)
+// and J(i+1) = trial plasma + beam of slice i+1 (Sec. 3.2 predictor-corrector).  The trial
+// J_perp is cleared after reading (ready for the next trial pass); with reset_prev (the
+// last iteration) the slice i-1 record is reset to the ion background, ready to receive
+// the deposit of slice i+1.
+template <typename T> struct SrcBperp {
+  static constexpr int NR = 2;
+  const V4<T>* cur;
+  V4<T>* prev;
+  T* chi_prev;
+  float* ps_prev;
+  const T* rho_ion;
+  V2<T>* tj;
+  const V2<T>* bjn;
+  Geom gm;
+  int reset_prev;
+  __device__ void operator()(int iy, int ix, T* v) const {
+    const int nx = gm.nx;
+    auto jz = [&](int y, int x) { return cur[(int64_t)y * nx + x].d; };
+    const int64_t o = (int64_t)iy * nx + ix;
+    const V4<T> pv = prev[o];
+    const V2<T> t = tj[o];
+    v[0] = v[1] = T(0);
+    if (ix > 0 && iy > 0) {
+      const T i2z = T(gm.inv2dz);
+      const V2<T> b = bjn[o];
+      const T dzjx = (pv.b - (t.a + b.a)) * i2z;
+      const T dzjy = (pv.c - (t.b + b.b)) * i2z;
+      v[0] = -dyc(jz, iy, ix, gm.ny, T(gm.inv2dy)) + dzjy;
+      v[1] = dxc(jz, iy, ix, nx, T(gm.inv2dx)) - dzjx;
+    }
+    tj[o] = V2<T>{T(0), T(0)};
+    if (reset_prev) {
+      prev[o] = V4<T>{rho_ion[o], T(0), T(0), T(0)};
+      chi_prev[o] = T(0);
+      if (ps_prev) ps_prev[o] = 0.0f;
+    }
+  }
+};
+
+template <typename T> inline SrcMain<T> src_main_of(const hq_grid_s* g, const void* dep) {
+  return SrcMain<T>{reinterpret_cast<const V4<T>*>(dep), psrc_of(g, dep), g->geom};
+}
+template <typename T>
+inline SrcBperp<T> src_bperp_of(const hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int reset_prev) {
+  return SrcBperp<T>{reinterpret_cast<const V4<T>*>(cur), reinterpret_cast<V4<T>*>(prev), reinterpret_cast<T*>(chi_prev),
+                     psrc_of(g, prev), reinterpret_cast<const T*>(g->rho_ion), reinterpret_cast<V2<T>*>(g->tj),
+                     reinterpret_cast<const V2<T>*>(g->bjn), g->geom, reset_prev};
 }
 
 }  // namespace hq

@@ -127,6 +127,52 @@ __device__ __forceinline__ void scatter(T* f, int st, int off, const Geom& gm, c
   }
 }
 
+// Adjoints of the six gathered fields into an 8-per-node gather record (ExmBy, EypBx, Ez, Bx,
+// By, Bz, pad, pad): in FP32 two float4 vector atomics per node (the record is 32 B), in
+// FP64 one atomic per component.
+template <int P, typename T>
+__device__ __forceinline__ void scatter_gf(T* f, const Geom& gm, const Stencil<P, T>& s, const T* v) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int b = 0; b <= P; ++b) {
+      const int iy = s.iy0 + b;
+      if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        const int ix = s.ix0 + a;
+        if (!in_interior(ix, gm.nx)) continue;
+        float* q = reinterpret_cast<float*>(f) + ((int64_t)iy * gm.nx + ix) * kGF;
+        const float w = s.wx[a] * s.wy[b];
+        atomicAdd(reinterpret_cast<float4*>(q), make_float4(w * v[0], w * v[1], w * v[2], w * v[3]));
+        atomicAdd(reinterpret_cast<float4*>(q + 4), make_float4(w * v[4], w * v[5], 0.0f, 0.0f));
+      }
+    }
+  } else {
+    scatter<P, T, 6>(f, kGF, 0, gm, s, v);
+  }
+}
+
+// Adjoint pair (a, b) into a 2-per-node record: one float2 vector atomic per node in FP32.
+template <int P, typename T>
+__device__ __forceinline__ void scatter_v2(T* f, const Geom& gm, const Stencil<P, T>& s, const T* v) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int b = 0; b <= P; ++b) {
+      const int iy = s.iy0 + b;
+      if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        const int ix = s.ix0 + a;
+        if (!in_interior(ix, gm.nx)) continue;
+        const float w = s.wx[a] * s.wy[b];
+        atomicAdd(reinterpret_cast<float2*>(f) + ((int64_t)iy * gm.nx + ix), make_float2(w * v[0], w * v[1]));
+      }
+    }
+  } else {
+    scatter<P, T, 2>(f, 2, 0, gm, s, v);
+  }
+}
+
 // Forward zeta-derivatives (identical to the forward kernels' formula).
 template <typename T>
 __device__ __forceinline__ void derivs_f(T ux, T uy, T opp, const T* F, T* f) {
@@ -244,7 +290,7 @@ __global__ void __launch_bounds__(kThreads)
   }
   T bux, buy, bpsi, bF[6];
   derivs_adj<T>(ux, uy, opp, F, fb, bux, buy, bpsi, bF);
-  scatter<P, T, 6>(fbar, kGF, 0, gm, st, bF);
+  scatter_gf<P, T>(fbar, gm, st, bF);
   T bx = sb[0], by = sb[1];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
@@ -328,12 +374,11 @@ __global__ void __launch_bounds__(kThreads)
   T bux, buy, bpsi, bF[6];
   derivs_adj<T>(ux, uy, opp, F, fb, bux, buy, bpsi, bF);
   {
-    const T v3[3] = {bF[0], bF[1], bF[2]};
-    scatter<P, T, 3>(fbar, kGF, 0, gm, st, v3);
-    const T v1b[1] = {bF[5]};
-    scatter<P, T, 1>(fbar, kGF, 5, gm, st, v1b);
+    // ExmBy, EypBx, Ez, Bz into fbar; Bx, By of B^(m-1) into bbar_m1
+    const T v6[6] = {bF[0], bF[1], bF[2], T(0), T(0), bF[5]};
+    scatter_gf<P, T>(fbar, gm, st, v6);
     const T v2b[2] = {bF[3], bF[4]};
-    scatter<P, T, 2>(reinterpret_cast<T*>(bbar_m1), 2, 0, gm, st, v2b);
+    scatter_v2<P, T>(reinterpret_cast<T*>(bbar_m1), gm, st, v2b);
   }
   T bx = stb[0], by = stb[1];
 #pragma unroll

@@ -26,60 +26,20 @@ __global__ void k_reset_dep(V4<T>* dep, T* chi, const T* rho_ion, float* ps, int
   if (ps) ps[i] = 0.0f;   // ion-subtracted: the ion background enters per particle
 }
 
-// psi: -(rho - Jz);  Ez: dx Jx + dy Jy;  Bz: dy Jx - dx Jy.  With ps (FP32 path) the psi
-// source is the separately accumulated rho - Jz.
+// Source kernels: one node (or folded node pair) per thread; the arithmetic is in the
+// per-node functors SrcMain and SrcBperp.
 template <typename T, typename Sink>
-__global__ void k_src_main(const V4<T>* __restrict__ dep, const float* __restrict__ ps, Geom gm, Sink sink) {
+__global__ void k_src_main(SrcMain<T> src, Sink sink) {
   pdl_trigger();
   pdl_wait();
-  const int nx = gm.nx;
-  auto jx = [&](int y, int x) { return dep[(int64_t)y * nx + x].b; };
-  auto jy = [&](int y, int x) { return dep[(int64_t)y * nx + x].c; };
-  visit_nodes<3, T>(gm, sink, 3, [&](int iy, int ix, T* v) {
-    v[0] = v[1] = v[2] = T(0);
-    if (ix > 0 && iy > 0) {
-      const V4<T> c = dep[(int64_t)iy * nx + ix];
-      const T i2x = T(gm.inv2dx), i2y = T(gm.inv2dy);
-      v[0] = ps ? T(-ps[(int64_t)iy * nx + ix]) : -(c.a - c.d);
-      v[1] = dxc(jx, iy, ix, nx, i2x) + dyc(jy, iy, ix, gm.ny, i2y);
-      v[2] = dyc(jx, iy, ix, gm.ny, i2y) - dxc(jy, iy, ix, nx, i2x);
-    }
-  });
+  visit_nodes<3, T>(src.gm, sink, 3, src);
 }
 
-// Bx: -dy Jz + dzeta Jy;  By: dx Jz - dzeta Jx, with dzeta J = (J(i-1) - J(i+1)) / (2 dzeta)
-// and J(i+1) = trial plasma + beam of slice i+1 (Sec. 3.2 predictor-corrector).
-// The trial J_perp is cleared after reading (ready for the next trial pass); on the
-// last iteration the slice i-1 record is reset to the ion background, ready to
-// receive the deposit of slice i+1.
 template <typename T, typename Sink>
-__global__ void k_src_bperp(const V4<T>* __restrict__ cur, V4<T>* prev, T* chi_prev, float* ps_prev,
-                            const T* __restrict__ rho_ion, V2<T>* tj, const V2<T>* __restrict__ bjn, Geom gm,
-                            Sink sink, int reset_prev) {
+__global__ void k_src_bperp(SrcBperp<T> src, Sink sink) {
   pdl_trigger();
   pdl_wait();
-  const int nx = gm.nx;
-  auto jz = [&](int y, int x) { return cur[(int64_t)y * nx + x].d; };
-  visit_nodes<2, T>(gm, sink, 2, [&](int iy, int ix, T* v) {
-    const int64_t o = (int64_t)iy * nx + ix;
-    const V4<T> pv = prev[o];
-    const V2<T> t = tj[o];
-    v[0] = v[1] = T(0);
-    if (ix > 0 && iy > 0) {
-      const T i2z = T(gm.inv2dz);
-      const V2<T> b = bjn[o];
-      const T dzjx = (pv.b - (t.a + b.a)) * i2z;
-      const T dzjy = (pv.c - (t.b + b.b)) * i2z;
-      v[0] = -dyc(jz, iy, ix, gm.ny, T(gm.inv2dy)) + dzjy;
-      v[1] = dxc(jz, iy, ix, nx, T(gm.inv2dx)) - dzjx;
-    }
-    tj[o] = V2<T>{T(0), T(0)};
-    if (reset_prev) {
-      prev[o] = V4<T>{rho_ion[o], T(0), T(0), T(0)};
-      chi_prev[o] = T(0);
-      if (ps_prev) ps_prev[o] = 0.0f;
-    }
-  });
+  visit_nodes<2, T>(src.gm, sink, 2, src);
 }
 
 template <typename T, typename Sink>
@@ -211,17 +171,14 @@ void launch_reset_dep(const hq_grid_s* g, void* dep, void* chi, cudaStream_t s) 
 template <typename T>
 void launch_src_main(const hq_grid_s* g, const void* dep, cudaStream_t s) {
   with_sink<T>(g, [&](auto sink) {
-    launch_pdl(k_src_main<T, decltype(sink)>, src_grid(g), 128, 0, s, reinterpret_cast<const V4<T>*>(dep),
-               static_cast<const float*>(psrc_of(g, dep)), g->geom, sink);
+    launch_pdl(k_src_main<T, decltype(sink)>, src_grid(g), 128, 0, s, src_main_of<T>(g, dep), sink);
   });
 }
 template <typename T>
 void launch_src_bperp(const hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int reset_prev, cudaStream_t s) {
   with_sink<T>(g, [&](auto sink) {
-    launch_pdl(k_src_bperp<T, decltype(sink)>, src_grid(g), 128, 0, s, reinterpret_cast<const V4<T>*>(cur),
-               reinterpret_cast<V4<T>*>(prev), reinterpret_cast<T*>(chi_prev), psrc_of(g, prev),
-               reinterpret_cast<const T*>(g->rho_ion), reinterpret_cast<V2<T>*>(g->tj),
-               reinterpret_cast<const V2<T>*>(g->bjn), g->geom, sink, reset_prev);
+    launch_pdl(k_src_bperp<T, decltype(sink)>, src_grid(g), 128, 0, s,
+               src_bperp_of<T>(g, cur, prev, chi_prev, reset_prev), sink);
   });
 }
 template <typename T>
