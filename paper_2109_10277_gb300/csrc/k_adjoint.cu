@@ -65,12 +65,23 @@ struct Stencil {
   T wx[P + 1], wy[P + 1], dwx[P + 1], dwy[P + 1];  // dw*: derivative w.r.t. the physical coordinate
 };
 
+// FP64 forms the node coordinate by division (the oracle's arithmetic); FP32, like the FP32
+// forward, by multiplication with the cell's inverse (no FP64 division per particle).
 template <int P, typename T>
 __device__ __forceinline__ void stencil_at(const Geom& gm, double x, double y, Stencil<P, T>& s) {
   int jx, jy;
   double fx, fy;
-  split_coord(x, gm.xmin, gm.dx, jx, fx);
-  split_coord(y, gm.ymin, gm.dy, jy, fy);
+  if constexpr (sizeof(T) == 8) {
+    split_coord(x, gm.xmin, gm.dx, jx, fx);
+    split_coord(y, gm.ymin, gm.dy, jy, fy);
+  } else {
+    const double u = (x - gm.xmin) * gm.inv_dx, v = (y - gm.ymin) * gm.inv_dy;
+    const double ufl = floor(u), vfl = floor(v);
+    jx = (int)ufl;
+    jy = (int)vfl;
+    fx = u - ufl;
+    fy = v - vfl;
+  }
   s.ix0 = shape_wd<P, T>(jx, T(fx), s.wx, s.dwx);
   s.iy0 = shape_wd<P, T>(jy, T(fy), s.wy, s.dwy);
 #pragma unroll

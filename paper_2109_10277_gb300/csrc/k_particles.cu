@@ -339,13 +339,18 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
 // exact polynomial differences carrying the factor (x - x0); otherwise the two stencils are
 // deposited with opposite signs.  Node coordinates u = (x - x_min) / dx are FP64.
 
-// Initial node coordinates of plasma particle p (the placement of k_plasma_init).
-__device__ __forceinline__ void initial_coord(int64_t p, const Geom& gm, int ppx, int ppy, double& u0, double& v0) {
+// Initial node coordinates of plasma particle p (the placement of k_plasma_init; 32-bit
+// index arithmetic, the sub-cell offset by multiplication with 1/ppc per axis).
+__device__ __forceinline__ void initial_coord(int64_t p, const Geom& gm, int ppx, int ppy, double inv_ppx,
+                                              double inv_ppy, double& u0, double& v0) {
+  const int pi = (int)p;
   const int ppc = ppx * ppy;
-  const int64_t c = p / ppc;
-  const int sub = (int)(p - c * ppc);
-  u0 = (double)(c % gm.nx) + ((double)(sub % ppx) + 0.5) / ppx;
-  v0 = (double)(c / gm.nx) + ((double)(sub / ppx) + 0.5) / ppy;
+  const int c = ppc == 1 ? pi : pi / ppc;
+  const int sub = pi - c * ppc;
+  const int iy = c / gm.nx, ix = c - iy * gm.nx;
+  const int sy = ppx == 1 ? sub : sub / ppx, sx = sub - sy * ppx;
+  u0 = (double)ix + ((double)sx + 0.5) * inv_ppx;
+  v0 = (double)iy + ((double)sy + 0.5) * inv_ppy;
 }
 
 // Weights w at u, w0 at u0 (bases b, b0) and, when b == b0, dw = w - w0 from the polynomial
@@ -496,14 +501,15 @@ __device__ __forceinline__ void deposit_ion_src(float* ps, const Geom& gm, doubl
 // advance to slice i+1, apply the removal rule and deposit rho, J, chi there.
 template <int P, typename T, bool CACHE>
 __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf,
-                                                         V4<T>* dep, T* chi, float* ps, int ppx, int ppy, int slice,
-                                                         double guard, unsigned long long* removed) {
+                                                         V4<T>* dep, T* chi, float* ps, int ppx, int ppy,
+                                                         double inv_ppx, double inv_ppy, int slice, double guard,
+                                                         unsigned long long* removed) {
   pdl_trigger();
   pdl_wait();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pl.n) return;
   double u0 = 0.0, v0 = 0.0;
-  if (ps) initial_coord(p, gm, ppx, ppy, u0, v0);
+  if (ps) initial_coord(p, gm, ppx, ppy, inv_ppx, inv_ppy, u0, v0);
   if (!pl.alive[p]) {
     if constexpr (sizeof(T) == 4)
       if (ps) deposit_ion_src<P>(ps, gm, u0, v0, charge_density<T>(pl.w[p], gm));
@@ -649,10 +655,10 @@ void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cuda
   float* ps = psrc_of(g, dep);
   const int px = g->d.ppc_x, py = g->d.ppc_y;
   switch (g->d.shape_order) {
-    case 0: launch_pdl(k_final_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, slice, gd, rm); break;
-    case 1: launch_pdl(k_final_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, slice, gd, rm); break;
-    case 2: launch_pdl(k_final_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, slice, gd, rm); break;
-    default: launch_pdl(k_final_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, slice, gd, rm); break;
+    case 0: launch_pdl(k_final_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, 1.0 / px, 1.0 / py, slice, gd, rm); break;
+    case 1: launch_pdl(k_final_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, 1.0 / px, 1.0 / py, slice, gd, rm); break;
+    case 2: launch_pdl(k_final_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, 1.0 / px, 1.0 / py, slice, gd, rm); break;
+    default: launch_pdl(k_final_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, 1.0 / px, 1.0 / py, slice, gd, rm); break;
   }
 }
 
