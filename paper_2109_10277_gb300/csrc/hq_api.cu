@@ -134,7 +134,7 @@ struct AdjStore {
   int fwd_tape_base = -1;   // first slice held by the tape after the forward sweep
   std::vector<hq_beam_view> fwd_beams;
   int fwd_witness = -1;
-  void *sx = nullptr, *sy = nullptr, *sux = nullptr, *suy = nullptr, *spsi = nullptr, *sh = nullptr;
+  void *sx = nullptr, *sy = nullptr, *sux = nullptr, *suy = nullptr, *spsi = nullptr, *sh = nullptr, *sacc = nullptr;
   double* wbar_p = nullptr;
   void* dbar[3] = {nullptr, nullptr, nullptr};
   void* carry[3] = {nullptr, nullptr, nullptr};
@@ -397,7 +397,7 @@ hq_status adj_alloc(hq_grid_s* g, int k) {
   for (int i = 0; ok && i < k; ++i)
     ok = snap(a->tape[i]) && A(&a->tape_gf[i], kGF * ts * nn) && A(&a->tape_b[i], (size_t)std::max(npc, 1) * 2 * ts * nn);
   ok = ok && A(&a->sx, ts * np) && A(&a->sy, ts * np) && A(&a->sux, ts * np) && A(&a->suy, ts * np) &&
-       A(&a->spsi, ts * np) && A(&a->sh, ts * np * 20) && A((void**)&a->wbar_p, 8 * np) && A(&a->fbar, kGF * ts * nn) &&
+       A(&a->spsi, ts * np) && A(&a->sh, ts * np * 20) && A(&a->sacc, ts * np * 5) && A((void**)&a->wbar_p, 8 * np) && A(&a->fbar, kGF * ts * nn) &&
        A(&a->bbar, (size_t)(npc + 1) * 2 * ts * nn) && A(&a->jbar, 2 * ts * nn) && A(&a->jtot, 2 * ts * nn) &&
        A(&a->rho_ion_bar, ts * nn);
   for (int i = 0; ok && i < 3; ++i) ok = A(&a->dbar[i], 4 * ts * nn) && A(&a->carry[i], 2 * ts * nn);
@@ -474,6 +474,7 @@ hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witn
   const size_t brec = 2 * ts * nn;
   for (void* p : {a->sx, a->sy, a->sux, a->suy, a->spsi}) cudaMemsetAsync(p, 0, ts * np, s);
   cudaMemsetAsync(a->sh, 0, ts * np * 20, s);
+  cudaMemsetAsync(a->sacc, 0, ts * np * 5, s);
   cudaMemsetAsync(a->wbar_p, 0, 8 * np, s);
   for (int i = 0; i < 3; ++i) {
     cudaMemsetAsync(a->dbar[i], 0, 4 * ts * nn, s);
@@ -486,7 +487,8 @@ hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witn
   void* dcur = a->dbar[1];
   void* dprev = a->dbar[2];
   AdjView<T> av{reinterpret_cast<T*>(a->sx), reinterpret_cast<T*>(a->sy), reinterpret_cast<T*>(a->sux),
-                reinterpret_cast<T*>(a->suy), reinterpret_cast<T*>(a->spsi), reinterpret_cast<T*>(a->sh)};
+                reinterpret_cast<T*>(a->suy), reinterpret_cast<T*>(a->spsi), reinterpret_cast<T*>(a->sh),
+                reinterpret_cast<T*>(a->sacc)};
   const T* w = g->fp64 ? reinterpret_cast<const T*>(g->p64.w) : reinterpret_cast<const T*>(g->p32.w);
   for (int seg = a->nseg - 1; seg >= 0; --seg) {
     const int a0 = seg * a->k, a1 = std::min(g->nz, a0 + a->k);

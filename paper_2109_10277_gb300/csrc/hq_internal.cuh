@@ -97,6 +97,10 @@ template <typename T> struct SnapView {
 template <typename T> struct AdjView {
   T *sx, *sy, *sux, *suy, *spsi;
   T* sh;
+  // [5][n]: sum of the predictor-corrector trial steps' AB5-combination adjoints of the slice
+  // being reversed; their history adjoints (-dzeta beta_k times it) are folded into sh by the
+  // next final-pass adjoint, so each trial adjoint updates 5 values instead of 20.
+  T* sacc;
 };
 
 }  // namespace hq

@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(kThreads)
     comb[c] = acc;
   }
   const double dz = gm.dzeta;
+  const T mdz = T(-dz);   // -dzeta in the field type (no FP64 product per use)
   const double nxp = x - dz * (double)comb[0], nyp = y - dz * (double)comb[1];
   const double npsi = psi - dz * (double)comb[4];
   const T nux = ux - T(dz) * comb[2], nuy = uy - T(dz) * comb[3];
@@ -291,13 +292,16 @@ __global__ void __launch_bounds__(kThreads)
   T fb[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
+    // history adjoints carried from slice i+1, with the trial steps' pending share folded in
+    const T sacc = a.sacc[(int64_t)c * n + p];
+    a.sacc[(int64_t)c * n + p] = T(0);
     T hn[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) hn[j] = a.sh[((int64_t)j * 5 + c) * n + p];
-    fb[c] = T(-dz * ab5(0)) * sb[c] + hn[0];
+    for (int j = 0; j < 4; ++j) hn[j] = a.sh[((int64_t)j * 5 + c) * n + p] + (mdz * T(ab5(j + 1))) * sacc;
+    fb[c] = (mdz * T(ab5(0))) * sb[c] + hn[0];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      a.sh[((int64_t)j * 5 + c) * n + p] = T(-dz * ab5(j + 1)) * sb[c] + (j < 3 ? hn[j + 1] : T(0));
+      a.sh[((int64_t)j * 5 + c) * n + p] = (mdz * T(ab5(j + 1))) * sb[c] + (j < 3 ? hn[j + 1] : T(0));
   }
   T bux, buy, bpsi, bF[6];
   derivs_adj<T>(ux, uy, opp, F, fb, bux, buy, bpsi, bF);
@@ -357,6 +361,7 @@ __global__ void __launch_bounds__(kThreads)
     comb[c] = acc;
   }
   const double dz = gm.dzeta;
+  const T mdz = T(-dz);   // -dzeta in the field type (no FP64 product per use)
   const double tx = x - dz * (double)comb[0], ty = y - dz * (double)comb[1];
   const double tpsi = psi - dz * (double)comb[4];
   const T tux = ux - T(dz) * comb[2], tuy = uy - T(dz) * comb[3];
@@ -378,9 +383,8 @@ __global__ void __launch_bounds__(kThreads)
   T fb[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    fb[c] = T(-dz * ab5(0)) * stb[c];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) a.sh[((int64_t)j * 5 + c) * n + p] += T(-dz * ab5(j + 1)) * stb[c];
+    fb[c] = (mdz * T(ab5(0))) * stb[c];
+    a.sacc[(int64_t)c * n + p] += stb[c];   // history share: folded into sh by the next final adjoint
   }
   T bux, buy, bpsi, bF[6];
   derivs_adj<T>(ux, uy, opp, F, fb, bux, buy, bpsi, bF);
