@@ -10,6 +10,8 @@
 
 #include "hq_internal.cuh"
 
+void graph_free(hq_grid_s* g);   // the captured sweep (defined before the C entry points)
+
 using namespace hq;
 
 namespace {
@@ -61,6 +63,9 @@ void free_all(hq_grid_s* g) {
     F(g->bins[b].bin); F(g->bins[b].count); F(g->bins[b].offset); F(g->bins[b].cursor); F(g->bins[b].perm);
   }
   adj_free(g);
+  graph_free(g);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  g->cap_stream = nullptr;
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   g->ev_pool.clear();
   F(g->d_profile); F(g->d_status); F(g->d_removed); F(g->d_scratch_int); F(g->d_gbar);
@@ -572,6 +577,68 @@ bool pdl_enabled() {
 void set_global_error(const std::string& msg) { g_global_err = msg; }
 }  // namespace hq
 
+// The slice loop of one sweep (Sec. 2), issued on the grid's stream.
+hq_status sweep_body(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, double dt, const hq_field_out* out,
+                     int32_t witness_beam, double* witness_sums) {
+  hq_status st;
+  for (int i = 0; i < g->nz; ++i) {
+    if ((st = hq_advance_slice(g, i)) != HQ_OK) return st;
+    if ((st = hq_beam_deposit(g, beams, nbeams, i)) != HQ_OK) return st;
+    if ((st = hq_solve_fields(g, i)) != HQ_OK) return st;
+    if (out && (st = hq_store_fields(g, out, i)) != HQ_OK) return st;
+    if (witness_beam >= 0 && (st = hq_witness_accumulate(g, &beams[witness_beam], i, witness_sums)) != HQ_OK) return st;
+    if (dt != 0.0 && (st = hq_push_beams(g, beams, nbeams, i, dt)) != HQ_OK) return st;
+  }
+  // advance once past the tail so the plasma state matches a completed sweep
+  const int nz = g->nz;
+  if (g->fp64) final_pass<double>(g, nz - 1, nz & 1);
+  else final_pass<float>(g, nz - 1, nz & 1);
+  g->last_adv = nz;
+  return check_launch(g);
+}
+
+// A captured sweep and the arguments it was captured with (device pointers and values are
+// baked into its kernel nodes).
+struct SweepGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<hq_beam_view> beams;
+  double dt = 0.0;
+  bool has_out = false;
+  hq_field_out out{};
+  int witness = -1;
+  double* sums = nullptr;
+  bool matches(const hq_beam_view* b, int nb, double dt_, const hq_field_out* o, int w, double* s) const {
+    if ((int)beams.size() != nb || dt != dt_ || has_out != (o != nullptr) || witness != w || sums != s) return false;
+    for (int i = 0; i < nb; ++i)
+      if (!same_view(beams[i], b[i])) return false;
+    return !o || std::memcmp(&out, o, sizeof(hq_field_out)) == 0;
+  }
+};
+
+void graph_free(hq_grid_s* g) {
+  SweepGraph* sg = reinterpret_cast<SweepGraph*>(g->sweep_graph);
+  if (!sg) return;
+  if (sg->exec) cudaGraphExecDestroy(sg->exec);
+  delete sg;
+  g->sweep_graph = nullptr;
+}
+
+// Beam bin storage for the beams of a sweep, allocated ahead of a stream capture.
+hq_status reserve_bins(hq_grid_s* g, const hq_beam_view* beams, int nb) {
+  for (int b = 0; b < nb; ++b) {
+    BeamBins& bb = g->bins[b];
+    if (bb.cap >= beams[b].n) continue;
+    if (bb.bin) cudaFree(bb.bin);
+    if (bb.perm) cudaFree(bb.perm);
+    bb.bin = bb.perm = nullptr;
+    bb.cap = 0;
+    HQ_CUDA(g, dalloc(&bb.bin, sizeof(int32_t) * beams[b].n));
+    HQ_CUDA(g, dalloc(&bb.perm, sizeof(int32_t) * beams[b].n));
+    bb.cap = beams[b].n;
+  }
+  return HQ_OK;
+}
+
 extern "C" {
 
 hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t* out) {
@@ -742,7 +809,6 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     g->fold = (g->nx % 128 == 0 && g->ny % 128 == 0 && !(nf && nf[0] == '1')) ? 1 : 0;
     HQ_ALLOC(g->d_gbar, sizeof(unsigned long long));
     cudaMemset(g->d_gbar, 0, sizeof(unsigned long long));
-    g->gbar_base = 0;
     const size_t opn = (size_t)kMaxRhs * g->nxp * g->nyp;
     for (int i = 0; i < 2; ++i) {
       HQ_ALLOC(g->op_hi[i], 2 * opn);
@@ -900,19 +966,66 @@ hq_status hq_sweep_step(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, double
   if (witness_beam >= nbeams || (witness_beam >= 0 && !witness_sums))
     return fail(g, HQ_ERR_ARG, "witness_beam must index a beam and witness_sums must be given");
   if (!std::isfinite(dt)) return fail(g, HQ_ERR_ARG, "dt must be finite");
-  for (int i = 0; i < g->nz; ++i) {
-    if ((st = hq_advance_slice(g, i)) != HQ_OK) return st;
-    if ((st = hq_beam_deposit(g, beams, nbeams, i)) != HQ_OK) return st;
-    if ((st = hq_solve_fields(g, i)) != HQ_OK) return st;
-    if (out && (st = hq_store_fields(g, out, i)) != HQ_OK) return st;
-    if (witness_beam >= 0 && (st = hq_witness_accumulate(g, &beams[witness_beam], i, witness_sums)) != HQ_OK) return st;
-    if (dt != 0.0 && (st = hq_push_beams(g, beams, nbeams, i, dt)) != HQ_OK) return st;
+  // The ~20 launches per slice are replayed from a CUDA graph when possible (off while
+  // profiling, with HQ_NO_GRAPH=1, or after a capture was refused).
+  const char* ng = std::getenv("HQ_NO_GRAPH");
+  if (g->graph_off || g->prof_on || (ng && ng[0] == '1'))
+    return sweep_body(g, beams, nbeams, dt, out, witness_beam, witness_sums);
+  SweepGraph* sg = reinterpret_cast<SweepGraph*>(g->sweep_graph);
+  if (!sg || !sg->exec || !sg->matches(beams, nbeams, dt, out, witness_beam, witness_sums)) {
+    if ((st = reserve_bins(g, beams, nbeams)) != HQ_OK) return st;
+    graph_free(g);
+    if (!g->cap_stream && cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      g->cap_stream = nullptr;
+      g->graph_off = 1;
+      return sweep_body(g, beams, nbeams, dt, out, witness_beam, witness_sums);
+    }
+    // capture on the private stream (the caller's may be the legacy default stream, which
+    // cannot be captured); nothing executes during the capture
+    cudaStream_t user = g->stream;
+    g->stream = g->cap_stream;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      g->stream = user;
+      g->graph_off = 1;
+      return sweep_body(g, beams, nbeams, dt, out, witness_beam, witness_sums);
+    }
+    st = sweep_body(g, beams, nbeams, dt, out, witness_beam, witness_sums);
+    const cudaError_t ec = cudaStreamEndCapture(g->stream, &graph);
+    g->stream = user;
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = (st == HQ_OK && ec == cudaSuccess && graph) ? cudaGraphInstantiate(&exec, graph, 0)
+                                                                       : cudaErrorUnknown;
+    if (graph) cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      // not capturable here: run the sweep on the stream (the capture executed nothing)
+      cudaGetLastError();
+      g->err.clear();
+      g->graph_off = 1;
+      return sweep_body(g, beams, nbeams, dt, out, witness_beam, witness_sums);
+    }
+    sg = new (std::nothrow) SweepGraph();
+    if (!sg) {
+      cudaGraphExecDestroy(exec);
+      return fail(g, HQ_ERR_OOM, "host allocation failed");
+    }
+    sg->exec = exec;
+    sg->beams.assign(beams, beams + nbeams);
+    sg->dt = dt;
+    sg->has_out = out != nullptr;
+    if (out) sg->out = *out;
+    sg->witness = witness_beam;
+    sg->sums = witness_sums;
+    g->sweep_graph = sg;
   }
-  // advance once past the tail so the plasma state matches a completed sweep
-  const int nz = g->nz;
-  if (g->fp64) final_pass<double>(g, nz - 1, nz & 1);
-  else final_pass<float>(g, nz - 1, nz & 1);
-  g->last_adv = nz;
+  HQ_CUDA(g, cudaGraphLaunch(sg->exec, g->stream));
+  // host bookkeeping of a completed sweep (the slice-order checks of the fine-grained calls)
+  for (int b = 0; b < nbeams; ++b) g->bound[b] = beams[b];
+  g->nbound = nbeams;
+  g->last_adv = g->nz;
+  g->last_beam = g->last_solved = g->nz - 1;
   return check_launch(g);
 }
 
@@ -999,7 +1112,10 @@ hq_status hq_sync(hq_grid_t g, int64_t* removed) {
   if (removed) *removed = (int64_t)rm;
   if (status) {
     HQ_CUDA(g, cudaMemset(g->d_status, 0, sizeof(int)));
-    if (status & DEV_TIMEOUT) return fail(g, HQ_ERR_TIMEOUT, "a bounded device wait ran out (tensor-core DST)");
+    if (status & DEV_TIMEOUT) {
+      if (g->d_gbar) HQ_CUDA(g, cudaMemset(g->d_gbar, 0, sizeof(unsigned long long)));  // an aborted solve left it
+      return fail(g, HQ_ERR_TIMEOUT, "a bounded device wait ran out (tensor-core DST)");
+    }
     if (status & DEV_NONFINITE) return fail(g, HQ_ERR_NUMERIC, "a non-finite value reached the field solve");
   }
   return HQ_OK;

@@ -144,8 +144,7 @@ struct hq_grid_s {
   hq::TensorMaps* tmaps;
   int fold;                                  // folded DST-I (nx, ny multiples of 128; FP32 mode)
   float* psrc[2];                            // FP32 mode: psi source rho - J_z of dep[0], dep[1]
-  unsigned long long* d_gbar;                // grid-barrier counter of the fused solve kernel
-  unsigned long long gbar_base;              // its value before the next launch
+  unsigned long long* d_gbar;                // grid-barrier counter of the fused solve kernel (zero between launches)
   int solve_ctas;                            // CTAs of the fused solve (co-resident)
 
   // beams
@@ -163,6 +162,11 @@ struct hq_grid_s {
 
   // checkpoints, tapes and adjoint state (allocated by the first checkpointed sweep)
   void* adj;
+
+  // hq_sweep_step replayed from a CUDA graph (captured once per argument set)
+  void* sweep_graph;
+  int graph_off;       // capture failed or was refused: plain stream launches from now on
+  cudaStream_t cap_stream;   // private stream the sweep is captured on (the graph runs on `stream`)
 
   // profiling: launch counters (always) and optional CUDA event pairs per launch group
   int64_t launches[HQ_K_CLASSES];

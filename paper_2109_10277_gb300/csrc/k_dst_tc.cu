@@ -329,8 +329,7 @@ struct SolveArgs {
   float *gf, *b1, *b2, *bjn;           // mode 3 (see Epi)
   float w;
   int last;
-  unsigned long long* gbar;            // grid-barrier counter
-  unsigned long long gbase;            // its value at launch
+  unsigned long long* gbar;            // grid-barrier counter (zero at launch, reset by the last CTA)
   int* status;
 };
 
@@ -348,11 +347,13 @@ __device__ __forceinline__ bool mbar_wait_a(uint32_t bar, uint32_t parity, int* 
   return true;
 }
 
-// Grid-wide barrier (all CTAs co-resident: cooperative launch).  The counter only
-// grows; barrier b of a launch completes at gbase + (b + 1) * gridDim.x arrivals.
-// The proxy fences order the epilogue's generic stores before the other CTAs' TMA
-// (async-proxy) loads of the next phase.  Bounded: on expiry, or once another CTA
-// has reported a timeout, the CTA sets DEV_TIMEOUT and leaves.
+// Grid-wide barrier (all CTAs co-resident: cooperative launch).  The counter is zero at
+// launch and only grows within it: barrier b completes at (b + 1) * gridDim.x arrivals; after
+// the last barrier every CTA arrives once more and the last one resets the counter to zero,
+// so a launch needs no host-side state (and can be replayed from a CUDA graph).  The proxy
+// fences order the epilogue's generic stores before the other CTAs' TMA (async-proxy)
+// loads of the next phase.  Bounded: on expiry, or once another CTA has reported a
+// timeout, the CTA sets DEV_TIMEOUT and leaves.
 __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned long long target, int* status,
                                              volatile int* abort_f) {
   asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -602,8 +603,13 @@ __global__ void __launch_bounds__(128, 1)
       HQ_SOLVE_TRACE_POINT(p, 3);
       if (*abort_f) break;
     }
-    if (p < 3 && !grid_barrier(a.gbar, a.gbase + (unsigned long long)(p + 1) * gridDim.x, a.status, abort_f)) break;
+    if (p < 3 && !grid_barrier(a.gbar, (unsigned long long)(p + 1) * gridDim.x, a.status, abort_f)) break;
     HQ_SOLVE_TRACE_POINT(p, 4);
+  }
+  // exit arrival: the last CTA through resets the counter for the next launch
+  if (threadIdx.x == 0 && !*abort_f) {
+    const unsigned long long seen = atomicAdd(a.gbar, 1ull);
+    if (seen == 4ull * gridDim.x - 1ull) atomicExch(a.gbar, 0ull);
   }
   tc_fence_before();
   __syncthreads();
@@ -734,7 +740,6 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s) 
   a.w = (float)g->d.pc_mix;
   a.last = last;
   a.gbar = g->d_gbar;
-  a.gbase = g->gbar_base;
   a.status = g->d_status;
   const int tiles_x = R * (g->nyp / BM) * (g->nxp / kSolveBN), tiles_y = R * (g->nxp / BM) * (g->nyp / kSolveBN);
   const int ctas = std::min(g->solve_ctas, std::max(tiles_x, tiles_y));
@@ -748,11 +753,9 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s) 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  // the barrier counter advances only if the kernel was launched (a launch error is
-  // reported by the caller's launch check)
-  if (cudaLaunchKernelEx(&cfg, k_dst_solve, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi, t.bx_lo, t.by_hi, t.by_lo,
-                         t.scale, a) == cudaSuccess)
-    g->gbar_base += 3ull * (unsigned long long)ctas;
+  // a launch error is reported by the caller's launch check
+  cudaLaunchKernelEx(&cfg, k_dst_solve, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi, t.bx_lo, t.by_hi, t.by_lo,
+                     t.scale, a);
 }
 
 }  // namespace
