@@ -509,7 +509,7 @@ hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witn
       const int t = i - a0;
       const Snap& sn = a->tape[t];
       SnapView<T> sv{g->np, sn.x, sn.y, sn.psi, reinterpret_cast<const T*>(sn.ux), reinterpret_cast<const T*>(sn.uy), w,
-                     sn.alive, reinterpret_cast<const T*>(sn.hist)};
+                     sn.alive, reinterpret_cast<const T*>(sn.hist), g->fp64 ? nullptr : sn.hsum};
       const void* gf = a->tape_gf[t];
       cudaMemsetAsync(a->fbar, 0, kGF * ts * nn, s);
       cudaMemsetAsync(a->jtot, 0, 2 * ts * nn, s);

@@ -90,6 +90,7 @@ template <typename T> struct SnapView {
   const T *ux, *uy, *w;
   const uint8_t* alive;
   const T* hist;    // AB5 ring as stored: physical slot s holds f_k with k = s mod 4
+  const float* hsum;   // FP32: the slice's AB5 history sum [5][n] (what the trial passes used); else null
 };
 
 // Per-particle adjoint state: x, y, ux, uy, Psi and the AB5 history in logical order

@@ -355,10 +355,15 @@ __global__ void __launch_bounds__(kThreads)
   T comb[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    T acc = T(ab5(0)) * f[c];
+    if (s.hsum) {
+      // FP32: the forward trial passes' own combination, beta_0 f_i + (stored history sum)
+      comb[c] = T(ab5(0)) * f[c] + T(s.hsum[(int64_t)c * n + p]);
+    } else {
+      T acc = T(ab5(0)) * f[c];
 #pragma unroll
-    for (int k = 1; k <= 4; ++k) acc += T(ab5(k)) * hist_at<T>(s.hist, n, p, slice, k, c);
-    comb[c] = acc;
+      for (int k = 1; k <= 4; ++k) acc += T(ab5(k)) * hist_at<T>(s.hist, n, p, slice, k, c);
+      comb[c] = acc;
+    }
   }
   const double dz = gm.dzeta;
   const T mdz = T(-dz);   // -dzeta in the field type (no FP64 product per use)
