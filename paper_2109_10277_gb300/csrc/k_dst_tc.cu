@@ -27,6 +27,7 @@
 #include "hq_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace hq {
 
@@ -35,9 +36,13 @@ struct TensorMaps {
   CUtensorMap a1_hi, a1_lo;   // op[1] as [kMaxRhs * nxp][nyp]
   CUtensorMap sx_hi[2], sx_lo[2];   // [nxp][nxp], boxes of 128 ([0]) or 64 ([1]) rows (per-product path)
   CUtensorMap sy_hi[2], sy_lo[2];   // [nyp][nyp]
-  CUtensorMap bx_hi, bx_lo;   // fused solve: S_x [nxp][nxp], or the fold matrix [nxp][nxp/2]; 64-row boxes
-  CUtensorMap by_hi, by_lo;
-  CUtensorMap scale;          // FP32 [nyp][nxp], 128 (x) by 64 (y) boxes
+  // fused solve, per N-tile width ([0]: 64, [1]: 32): S_x [nxp][nxp], or the fold matrix
+  // [nxp][nxp/2], in boxes of BN rows; the FP32 scale [nyp][nxp] in 128 (x) by BN (y) boxes
+  CUtensorMap bx_hi[2], bx_lo[2];
+  CUtensorMap by_hi[2], by_lo[2];
+  CUtensorMap scale[2];
+  int ctas[2];                // co-resident CTAs of each width
+  bool wide_only;             // HQ_SOLVE_BN=64: never use the 32-wide tiles
 };
 
 namespace {
@@ -382,7 +387,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
   return !*abort_f;
 }
 
-constexpr int kSolveBN = 64;
+// N-tile widths of the fused solve: 64, or 32 when that still gives every tile its own CTA
+// (twice the tiles, so more of the SMs take part in each product).
+template <int BN> constexpr int bn_index() { return BN == 64 ? 0 : 1; }
 
 // Optional per-CTA timestamps of the solve's steps (a profiling build defines it).
 #ifndef HQ_SOLVE_TRACE_POINT
@@ -391,23 +398,23 @@ constexpr int kSolveBN = 64;
 
 // Shared memory of the solve: the stage ring, the FP32 scale tile of phase 1
 // ([64 n][128 rows]), then the barriers (full, empty, done, scale) and the TMEM slot.
-struct SolveSmem {
-  static constexpr int STAGES = Cfg<kSolveBN>::STAGES;
-  static constexpr int RING = STAGES * Cfg<kSolveBN>::STAGE_BYTES;
+template <int BN> struct SolveSmem {
+  static constexpr int STAGES = Cfg<BN>::STAGES;
+  static constexpr int RING = STAGES * Cfg<BN>::STAGE_BYTES;
   static constexpr int SCALE = RING;
-  static constexpr int BARS = SCALE + kSolveBN * BM * 4;
+  static constexpr int BARS = SCALE + BN * BM * 4;
   static constexpr int BYTES = BARS + 256 + 1024 /*alignment*/;
 };
 
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_dst_solve(const __grid_constant__ CUtensorMap a0h, const __grid_constant__ CUtensorMap a0l,
                 const __grid_constant__ CUtensorMap a1h, const __grid_constant__ CUtensorMap a1l,
                 const __grid_constant__ CUtensorMap bxh, const __grid_constant__ CUtensorMap bxl,
                 const __grid_constant__ CUtensorMap byh, const __grid_constant__ CUtensorMap byl,
                 const __grid_constant__ CUtensorMap scm, const SolveArgs a) {
-  constexpr int BN = kSolveBN;
   using C = Cfg<BN>;
-  using L = SolveSmem;
+  using L = SolveSmem<BN>;
   constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ int s_abort;
@@ -679,20 +686,29 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
     return 1;
   }
   EncodeFn enc = reinterpret_cast<EncodeFn>(fn);
-  constexpr int kSmem = SolveSmem::BYTES;
-  if (cudaFuncSetAttribute(k_dst_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem) != cudaSuccess) {
-    err = "cannot raise the shared-memory limit of the DST solve kernel";
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->dev) != cudaSuccess) {
+    err = "cannot read the SM count";
     return 1;
   }
-  int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dst_solve, 128, kSmem) != cudaSuccess || per_sm < 1 ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->dev) != cudaSuccess) {
-    err = "cannot size the cooperative DST solve";
-    return 1;
-  }
-  g->solve_ctas = per_sm * sms;
+  auto size_solve = [&](auto kern, int smem, int& ctas) {
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem) != cudaSuccess || per_sm < 1) {
+      err = "cannot size the cooperative DST solve";
+      return false;
+    }
+    ctas = per_sm * sms;
+    return true;
+  };
   g->tmaps = new TensorMaps();
   TensorMaps& t = *g->tmaps;
+  if (!size_solve(k_dst_solve<64>, SolveSmem<64>::BYTES, t.ctas[0]) ||
+      !size_solve(k_dst_solve<32>, SolveSmem<32>::BYTES, t.ctas[1]))
+    return 1;
+  g->solve_ctas = t.ctas[0];
+  const char* bn = std::getenv("HQ_SOLVE_BN");
+  t.wide_only = bn != nullptr && std::atoi(bn) == 64;
   const uint64_t nxp = g->nxp, nyp = g->nyp;
   int bad = 0;
   bad |= make_map(enc, &t.a0_hi, g->op_hi[0], kMaxRhs * nyp, nxp, err);
@@ -701,11 +717,14 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
   bad |= make_map(enc, &t.a1_lo, g->op_lo[1], kMaxRhs * nxp, nyp, err);
   // S_x, S_y (or the fold matrices, half as wide) as [rows][K]
   const uint64_t kx = g->fold ? nxp / 2 : nxp, ky = g->fold ? nyp / 2 : nyp;
-  bad |= make_map(enc, &t.bx_hi, g->sx_hi, nxp, kx, err, kSolveBN);
-  bad |= make_map(enc, &t.bx_lo, g->sx_lo, nxp, kx, err, kSolveBN);
-  bad |= make_map(enc, &t.by_hi, g->sy_hi, nyp, ky, err, kSolveBN);
-  bad |= make_map(enc, &t.by_lo, g->sy_lo, nyp, ky, err, kSolveBN);
-  bad |= make_map_plain(enc, &t.scale, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->f32_scale, nyp, nxp, BM, kSolveBN, err);
+  for (int i = 0; i < 2; ++i) {
+    const uint32_t bn = i == 0 ? 64 : 32;
+    bad |= make_map(enc, &t.bx_hi[i], g->sx_hi, nxp, kx, err, bn);
+    bad |= make_map(enc, &t.bx_lo[i], g->sx_lo, nxp, kx, err, bn);
+    bad |= make_map(enc, &t.by_hi[i], g->sy_hi, nyp, ky, err, bn);
+    bad |= make_map(enc, &t.by_lo[i], g->sy_lo, nyp, ky, err, bn);
+    bad |= make_map_plain(enc, &t.scale[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->f32_scale, nyp, nxp, BM, bn, err);
+  }
   return bad;
 }
 
@@ -741,12 +760,16 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s) 
   a.last = last;
   a.gbar = g->d_gbar;
   a.status = g->d_status;
-  const int tiles_x = R * (g->nyp / BM) * (g->nxp / kSolveBN), tiles_y = R * (g->nxp / BM) * (g->nyp / kSolveBN);
-  const int ctas = std::min(g->solve_ctas, std::max(tiles_x, tiles_y));
+  // tiles of one product (the larger of the x and y products) at N-tile width bn
+  auto tiles = [&](int bn) {
+    return std::max(R * (g->nyp / BM) * (g->nxp / bn), R * (g->nxp / BM) * (g->nyp / bn));
+  };
+  const bool narrow = !t.wide_only && tiles(32) <= t.ctas[1];
+  const int v = narrow ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.gridDim = dim3((unsigned)std::min(t.ctas[v], tiles(narrow ? 32 : 64)));
   cfg.blockDim = dim3(128);
-  cfg.dynamicSmemBytes = SolveSmem::BYTES;
+  cfg.dynamicSmemBytes = narrow ? SolveSmem<32>::BYTES : SolveSmem<64>::BYTES;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -754,8 +777,8 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s) 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   // a launch error is reported by the caller's launch check
-  cudaLaunchKernelEx(&cfg, k_dst_solve, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi, t.bx_lo, t.by_hi, t.by_lo,
-                     t.scale, a);
+  cudaLaunchKernelEx(&cfg, narrow ? k_dst_solve<32> : k_dst_solve<64>, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi[v],
+                     t.bx_lo[v], t.by_hi[v], t.by_lo[v], t.scale[v], a);
 }
 
 }  // namespace
