@@ -59,6 +59,9 @@ template <int BN> struct Cfg {
   // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M = BM, N = BN.
   static constexpr uint32_t IDESC =
       (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  // the same with N = 2 BN: B_hi and B_lo, adjacent in a stage, read as one operand
+  static constexpr uint32_t IDESC2 =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 2) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 
 struct Epi {
@@ -150,7 +153,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t* v) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -160,7 +163,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
         "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
         "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  tmem_ld32_issue(taddr, v);
+  tmem_ld_wait();
+}
+// 32 columns of a stacked accumulator: x[j] = D[c0 + j] + D[BN + c0 + j] of this thread's lane
+template <int BN>
+__device__ __forceinline__ void tmem_ld_pair(uint32_t taddr, float* x) {
+  uint32_t v[32], u[32];
+  tmem_ld32_issue(taddr, v);
+  tmem_ld32_issue(taddr + (uint32_t)BN, u);
+  tmem_ld_wait();
+#pragma unroll
+  for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]) + __uint_as_float(u[j]);
 }
 
 template <int BN>
@@ -444,7 +461,7 @@ __global__ void __launch_bounds__(128, 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -507,12 +524,13 @@ __global__ void __launch_bounds__(128, 1)
           tc_fence_after();
           const uint32_t st = base + s * STAGE_BYTES;
           const uint64_t ah = desc_k_sw128(st), al = desc_k_sw128(st + A_BYTES);
-          const uint64_t bh = desc_k_sw128(st + 2 * A_BYTES), bl = desc_k_sw128(st + 2 * A_BYTES + C::B_BYTES);
+          const uint64_t bh = desc_k_sw128(st + 2 * A_BYTES);
+          // columns [0, BN): A_hi B_hi + A_lo B_hi; columns [BN, 2 BN): A_hi B_lo (one MMA
+          // with N = 2 BN covers both A_hi products: the tensor core's cost here is per instruction)
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k) {
             const uint64_t off = (uint64_t)((k * 32) >> 4);
-            mma_bf16(tmem, ah + off, bh + off, C::IDESC, (kb | k) != 0 ? 1u : 0u);
-            mma_bf16(tmem, ah + off, bl + off, C::IDESC, 1u);
+            mma_bf16(tmem, ah + off, bh + off, C::IDESC2, (kb | k) != 0 ? 1u : 0u);
             mma_bf16(tmem, al + off, bh + off, C::IDESC, 1u);
           }
           mma_commit(empty0 + 8 * s);
@@ -538,24 +556,23 @@ __global__ void __launch_bounds__(128, 1)
         __nv_bfloat16* ol = a.op_lo[along_x ? 1 : 0];
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+          float x[32];
+          tmem_ld_pair<BN>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, x);
           HQ_SOLVE_TRACE_POINT(p, 8 + c0 / 16);
-          float sc[32];
           if (mode == 1) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) sc[j] = scale_s[(c0 + j) * BM + row];
+            for (int j = 0; j < 32; ++j) x[j] *= scale_s[(c0 + j) * BM + row];
+          }
+          if (a.fold) {
+            // all 32 exchanges first, so that the warp's shuffles overlap
+            float y[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) y[j] = __shfl_xor_sync(0xffffffffu, x[j], 1);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) x[j] = odd ? (wall ? 0.0f : y[j] - x[j]) : (wall ? y[j] : x[j] + y[j]);
           }
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            float x = __uint_as_float(v[j]);
-            if (mode == 1) x *= sc[j];
-            if (a.fold) {
-              const float y = __shfl_xor_sync(0xffffffffu, x, 1);
-              x = odd ? (wall ? 0.0f : y - x) : (wall ? y : x + y);
-            }
-            put_split(oh, ol, ((int64_t)r * P2 + n0 + c0 + j) * P1 + fcol, x);
-          }
+          for (int j = 0; j < 32; ++j) put_split(oh, ol, ((int64_t)r * P2 + n0 + c0 + j) * P1 + fcol, x[j]);
           HQ_SOLVE_TRACE_POINT(p, 9 + c0 / 16);
         }
       } else {
@@ -563,36 +580,37 @@ __global__ void __launch_bounds__(128, 1)
         const int xn = a.fold ? fold_node(ml, a.nx) : ml;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+          float x[32];
+          tmem_ld_pair<BN>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, x);
           if (xn >= a.nx) continue;
           auto ynode = [&](int j) { return a.fold ? fold_node(n0 + c0 + j, a.ny) : n0 + c0 + j; };
           if (mode == 2) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int yn = ynode(j);
-              if (yn < a.ny) a.out[((int64_t)r * a.ny + yn) * a.nx + xn] = __uint_as_float(v[j]);
+              if (yn < a.ny) a.out[((int64_t)r * a.ny + yn) * a.nx + xn] = x[j];
             }
           } else {
             // predictor-corrector mixing into gf[3 + r] (all loads first, then mix and store)
-            float old[32];
+            float old[32], prev1[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int yn = ynode(j);
-              old[j] = yn < a.ny ? a.gf[((int64_t)yn * a.nx + xn) * kGF + 3 + r] : 0.0f;
+              const int64_t node = (int64_t)yn * a.nx + xn;
+              old[j] = yn < a.ny ? a.gf[node * kGF + 3 + r] : 0.0f;
+              prev1[j] = (a.last && yn < a.ny) ? a.b1[node * 2 + r] : 0.0f;
             }
             bool bad = false;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int yn = ynode(j);
               if (yn >= a.ny) continue;
-              const float x = __uint_as_float(v[j]);
-              bad |= !isfinite(x);
+              bad |= !isfinite(x[j]);
               const int64_t node = (int64_t)yn * a.nx + xn;
-              const float nb = a.w * x + (1.0f - a.w) * old[j];
+              const float nb = a.w * x[j] + (1.0f - a.w) * old[j];
               a.gf[node * kGF + 3 + r] = nb;
               if (a.last) {
-                a.b2[node * 2 + r] = a.b1[node * 2 + r];
+                a.b2[node * 2 + r] = prev1[j];
                 a.b1[node * 2 + r] = nb;
                 a.bjn[node * 2 + r] = 0.0f;
               }
@@ -621,7 +639,7 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
   }
   HQ_SOLVE_TRACE_POINT(3, 14);
 }
