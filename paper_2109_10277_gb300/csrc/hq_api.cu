@@ -699,6 +699,11 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   gm.f_dz_inv_dy = (float)(gm.dzeta * gm.inv_dy);
   gm.f_inv_area = (float)gm.inv_area;
   gm.f_guard = (float)d.psi_guard;
+  gm.f_inv_dx = (float)gm.inv_dx;
+  gm.f_inv_dy = (float)gm.inv_dy;
+  gm.f_inv2dx = (float)gm.inv2dx;
+  gm.f_inv2dy = (float)gm.inv2dy;
+  gm.f_inv2dz = (float)gm.inv2dz;
   g->last_adv = g->last_beam = g->last_solved = -1;
 
   auto bail = [&](hq_status st) {

@@ -39,10 +39,15 @@ struct Geom {
   double inv2dx, inv2dy, inv2dz;  // 1/(2 dx), 1/(2 dy), 1/(2 dzeta): central differences
   // FP32 copies for the FP32 kernels (no per-thread double-to-float conversion)
   float f_dz, f_dz_inv_dx, f_dz_inv_dy, f_inv_area, f_guard;
+  float f_inv_dx, f_inv_dy, f_inv2dx, f_inv2dy, f_inv2dz;
 };
 
-// Geometry constants in the kernel's arithmetic type (no per-thread FP64 division).
-template <typename T> __device__ __forceinline__ T cst(double v) { return T(v); }
+// A geometry constant in the kernel's arithmetic type: FP32 kernels take the host-rounded
+// copy (on this GPU every FP64 conversion is an instruction of the slow FP64 pipe).
+template <typename T> __device__ __forceinline__ T gsel(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return d;
+}
 
 template <typename T> struct V4 { T a, b, c, d; };   // packed rho, jx, jy, jz
 
@@ -468,7 +473,7 @@ template <typename T> struct SrcMain {
     v[0] = v[1] = v[2] = T(0);
     if (ix > 0 && iy > 0) {
       const V4<T> c = dep[(int64_t)iy * nx + ix];
-      const T i2x = T(gm.inv2dx), i2y = T(gm.inv2dy);
+      const T i2x = gsel<T>(gm.inv2dx, gm.f_inv2dx), i2y = gsel<T>(gm.inv2dy, gm.f_inv2dy);
       v[0] = ps ? T(-ps[(int64_t)iy * nx + ix]) : -(c.a - c.d);
       v[1] = dxc(jx, iy, ix, nx, i2x) + dyc(jy, iy, ix, gm.ny, i2y);
       v[2] = dyc(jx, iy, ix, gm.ny, i2y) - dxc(jy, iy, ix, nx, i2x);
@@ -500,12 +505,12 @@ template <typename T> struct SrcBperp {
     const V2<T> t = tj[o];
     v[0] = v[1] = T(0);
     if (ix > 0 && iy > 0) {
-      const T i2z = T(gm.inv2dz);
+      const T i2z = gsel<T>(gm.inv2dz, gm.f_inv2dz);
       const V2<T> b = bjn[o];
       const T dzjx = (pv.b - (t.a + b.a)) * i2z;
       const T dzjy = (pv.c - (t.b + b.b)) * i2z;
-      v[0] = -dyc(jz, iy, ix, gm.ny, T(gm.inv2dy)) + dzjy;
-      v[1] = dxc(jz, iy, ix, nx, T(gm.inv2dx)) - dzjx;
+      v[0] = -dyc(jz, iy, ix, gm.ny, gsel<T>(gm.inv2dy, gm.f_inv2dy)) + dzjy;
+      v[1] = dxc(jz, iy, ix, nx, gsel<T>(gm.inv2dx, gm.f_inv2dx)) - dzjx;
     }
     tj[o] = V2<T>{T(0), T(0)};
     if (reset_prev) {

@@ -86,8 +86,8 @@ __device__ __forceinline__ void stencil_at(const Geom& gm, double x, double y, S
   s.iy0 = shape_wd<P, T>(jy, T(fy), s.wy, s.dwy);
 #pragma unroll
   for (int a = 0; a <= P; ++a) {
-    s.dwx[a] *= T(gm.inv_dx);
-    s.dwy[a] *= T(gm.inv_dy);
+    s.dwx[a] *= gsel<T>(gm.inv_dx, gm.f_inv_dx);
+    s.dwy[a] *= gsel<T>(gm.inv_dy, gm.f_inv_dy);
   }
 }
 
@@ -265,10 +265,10 @@ __global__ void __launch_bounds__(kThreads)
     comb[c] = acc;
   }
   const double dz = gm.dzeta;
-  const T mdz = T(-dz);   // -dzeta in the field type (no FP64 product per use)
+  const T mdz = -gsel<T>(dz, gm.f_dz);   // -dzeta in the field type (no FP64 product per use)
   const double nxp = x - dz * (double)comb[0], nyp = y - dz * (double)comb[1];
   const double npsi = psi - dz * (double)comb[4];
-  const T nux = ux - T(dz) * comb[2], nuy = uy - T(dz) * comb[3];
+  const T nux = ux + mdz * comb[2], nuy = uy + mdz * comb[3];
   if (!ok_state(gm, nxp, nyp, 1.0 + npsi, guard)) return;  // removed: nothing downstream depends on it
   // deposit at slice i+1: v = q w (gamma g, ux g, uy g, uz g) / A
   Stencil<P, T> sn;
@@ -366,10 +366,10 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   const double dz = gm.dzeta;
-  const T mdz = T(-dz);   // -dzeta in the field type (no FP64 product per use)
+  const T mdz = -gsel<T>(dz, gm.f_dz);   // -dzeta in the field type (no FP64 product per use)
   const double tx = x - dz * (double)comb[0], ty = y - dz * (double)comb[1];
   const double tpsi = psi - dz * (double)comb[4];
-  const T tux = ux - T(dz) * comb[2], tuy = uy - T(dz) * comb[3];
+  const T tux = ux + mdz * comb[2], tuy = uy + mdz * comb[3];
   if (!ok_state(gm, tx, ty, 1.0 + tpsi, guard)) return;  // skipped by the trial deposit
   Stencil<P, T> sn;
   stencil_at<P, T>(gm, tx, ty, sn);
@@ -450,8 +450,8 @@ __global__ void k_adj_pc_post(const T* __restrict__ res, V4<T>* dcur, V4<T>* dpr
   if (ix > 0 && iy > 0) {
     auto r0 = [&](int y, int x) { return res[(int64_t)y * nx + x]; };
     auto r1 = [&](int y, int x) { return res[nn + (int64_t)y * nx + x]; };
-    const T i2z = T(gm.inv2dz);
-    jz = dyc(r0, iy, ix, gm.ny, T(gm.inv2dy)) - dxc(r1, iy, ix, nx, T(gm.inv2dx));
+    const T i2z = gsel<T>(gm.inv2dz, gm.f_inv2dz);
+    jz = dyc(r0, iy, ix, gm.ny, gsel<T>(gm.inv2dy, gm.f_inv2dy)) - dxc(r1, iy, ix, nx, gsel<T>(gm.inv2dx, gm.f_inv2dx));
     const T a0 = res[o], a1 = res[nn + o];
     jxp = -a1 * i2z;
     jyp = a0 * i2z;
@@ -486,7 +486,7 @@ __global__ void k_adj_main_pre(const T* __restrict__ fbar, Geom gm, Sink sink) {
     const int64_t o = (int64_t)iy * nx + ix;
     v[0] = v[1] = v[2] = T(0);
     if (ix > 0 && iy > 0) {
-      v[0] = dxc(f0, iy, ix, nx, T(gm.inv2dx)) + dyc(f1, iy, ix, gm.ny, T(gm.inv2dy));
+      v[0] = dxc(f0, iy, ix, nx, gsel<T>(gm.inv2dx, gm.f_inv2dx)) + dyc(f1, iy, ix, gm.ny, gsel<T>(gm.inv2dy, gm.f_inv2dy));
       v[1] = fbar[o * kGF + 2];
       v[2] = fbar[o * kGF + 5];
     }
@@ -505,7 +505,7 @@ __global__ void k_adj_main_post(const T* __restrict__ res, V4<T>* dcur, T* rho_i
   if (ix > 0 && iy > 0) {
     auto r1 = [&](int y, int x) { return res[nn + (int64_t)y * nx + x]; };
     auto r2 = [&](int y, int x) { return res[2 * nn + (int64_t)y * nx + x]; };
-    const T i2x = T(gm.inv2dx), i2y = T(gm.inv2dy);
+    const T i2x = gsel<T>(gm.inv2dx, gm.f_inv2dx), i2y = gsel<T>(gm.inv2dy, gm.f_inv2dy);
     const T sp = res[o];
     d.a += -sp;
     d.d += sp;

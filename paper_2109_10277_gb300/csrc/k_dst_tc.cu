@@ -481,20 +481,32 @@ __global__ void __launch_bounds__(128, 1)
     tiles = mt * (P2 / BN);
     nk = (a.fold ? P2 / 2 : P2) / BK;
   };
+  // both axes' geometry and this CTA's first tile, computed before the first phase (after a
+  // grid barrier they would sit on the path to the phase's first TMA issue)
+  int P1x, P2x, mtx, tilesx, nkx, P1y, P2y, mty, tilesy, nky;
+  phase_geom(0, P1x, P2x, mtx, tilesx, nkx);
+  phase_geom(1, P1y, P2y, mty, tilesy, nky);
+  const int final_mode = a.final_mode;
+  const int t0 = (int)blockIdx.x;
+  const int m0x = (t0 % mtx) * BM, n0x = (t0 / mtx) * BN, rx = m0x / P1x;
+  const int m0y = (t0 % mty) * BM, n0y = (t0 / mty) * BN, ry = m0y / P1y;
   for (int p = 0; p < 4; ++p) {
     HQ_SOLVE_TRACE_POINT(p, 0);
     const bool along_x = (p & 1) == 0;
-    int P1, P2, mt, tiles, nk;   // rows per rhs, output columns (= contraction extent), tiles, K blocks
-    phase_geom(p, P1, P2, mt, tiles, nk);
+    // rows per rhs, output columns (= contraction extent), tiles, K blocks
+    const int P1 = along_x ? P1x : P1y, P2 = along_x ? P2x : P2y, mt = along_x ? mtx : mty;
+    const int tiles = along_x ? tilesx : tilesy, nk = along_x ? nkx : nky;
     const CUtensorMap* tah = along_x ? &a0h : &a1h;
     const CUtensorMap* tal = along_x ? &a0l : &a1l;
     const CUtensorMap* tbh = along_x ? &bxh : &byh;
     const CUtensorMap* tbl = along_x ? &bxl : &byl;
-    const int mode = p == 3 ? a.final_mode : (p == 1 ? 1 : 0);
+    const int mode = p == 3 ? final_mode : (p == 1 ? 1 : 0);
     if (p == 3) pdl_trigger();
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-      const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
-      const int r = m0 / P1, ml0 = m0 - r * P1;   // a tile lies within one right-hand side
+      const bool first = tile == t0;
+      const int m0 = first ? (along_x ? m0x : m0y) : (tile % mt) * BM;
+      const int n0 = first ? (along_x ? n0x : n0y) : (tile / mt) * BN;
+      const int r = first ? (along_x ? rx : ry) : m0 / P1, ml0 = m0 - r * P1;   // a tile lies within one rhs
       const int koff = (a.fold && n0 >= P2 / 2) ? P2 / 2 : 0;
       if (warp == 0 && lane == 0) {
         // TMA producer (and the scale tile of the spectral division)
@@ -507,7 +519,9 @@ __global__ void __launch_bounds__(128, 1)
           const int s = g % STAGES;
           const uint32_t st = base + s * STAGE_BYTES;
           const uint32_t fb = full0 + 8 * s;
-          if (g >= STAGES && !mbar_wait_a(empty0 + 8 * s, ((g / STAGES) - 1) & 1, a.status, abort_f)) break;
+          // a tile starts on a drained ring (every thread waited for the previous tile's last
+          // MMA), so only a stage reused within the tile needs its release
+          if (kb >= STAGES && !mbar_wait_a(empty0 + 8 * s, ((g / STAGES) - 1) & 1, a.status, abort_f)) break;
           mbar_expect_tx(fb, STAGE_BYTES);
           tma_load_2d(st, tah, koff + kb * BK, m0, fb);
           tma_load_2d(st + A_BYTES, tal, koff + kb * BK, m0, fb);

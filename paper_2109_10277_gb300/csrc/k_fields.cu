@@ -65,8 +65,8 @@ __global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, const V2
   auto ps = [&](int y, int x) { return res[(int64_t)y * nx + x]; };
   T ex = T(0), ey = T(0);
   if (ix > 0 && iy > 0) {
-    ex = -dxc(ps, iy, ix, nx, T(gm.inv2dx));
-    ey = -dyc(ps, iy, ix, gm.ny, T(gm.inv2dy));
+    ex = -dxc(ps, iy, ix, nx, gsel<T>(gm.inv2dx, gm.f_inv2dx));
+    ey = -dyc(ps, iy, ix, gm.ny, gsel<T>(gm.inv2dy, gm.f_inv2dy));
   }
   const T p = res[o], ez = res[nn + o], bz = res[2 * nn + o];
   if (!(isfinite(p) && isfinite(ez) && isfinite(bz))) atomicOr(status, DEV_NONFINITE);

@@ -337,32 +337,64 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
 // it left behind), so the unit ion background never meets the small plasma response in an
 // FP32 sum.  When both stencils share their base node the weight differences are formed as
 // exact polynomial differences carrying the factor (x - x0); otherwise the two stencils are
-// deposited with opposite signs.  Node coordinates u = (x - x_min) / dx are FP64.
+// deposited with opposite signs.  Node coordinates u = (x - x_min) / dx enter split as cell +
+// fraction; only the move u - u0 is formed from the FP64 fractions.
 
-// Initial node coordinates of plasma particle p (the placement of k_plasma_init; 32-bit
-// index arithmetic, the sub-cell offset by multiplication with 1/ppc per axis).
-__device__ __forceinline__ void initial_coord(int64_t p, const Geom& gm, int ppx, int ppy, double inv_ppx,
-                                              double inv_ppy, double& u0, double& v0) {
+// Plasma particles per cell per axis, with the FP32 and FP64 reciprocals.
+struct PpcInfo {
+  int px, py;
+  int pow2;   // both powers of two: the sub-cell offsets are exact in FP32
+  float finv_x, finv_y;
+  double inv_x, inv_y;
+};
+
+// Start (ion) node coordinate of plasma particle p, split as cell + fraction: u0 = cx + fx,
+// v0 = cy + fy (the placement of k_plasma_init: 32-bit index arithmetic, the sub-cell offset
+// (s + 1/2) / ppc).  With ppc a power of two the FP32 fraction is exact and the FP64 copy its
+// widening (one conversion); otherwise the FP64 fraction is computed and rounded.  On this
+// GPU every FP64 instruction issues on a slow pipe, so the split keeps them to a minimum.
+struct Start {
+  int cx, cy;
+  float fx, fy;
+  double dfx, dfy;
+};
+__device__ __forceinline__ Start start_coord(int64_t p, const Geom& gm, const PpcInfo& pc) {
   const int pi = (int)p;
-  const int ppc = ppx * ppy;
+  const int ppc = pc.px * pc.py;
   const int c = ppc == 1 ? pi : pi / ppc;
   const int sub = pi - c * ppc;
-  const int iy = c / gm.nx, ix = c - iy * gm.nx;
-  const int sy = ppx == 1 ? sub : sub / ppx, sx = sub - sy * ppx;
-  u0 = (double)ix + ((double)sx + 0.5) * inv_ppx;
-  v0 = (double)iy + ((double)sy + 0.5) * inv_ppy;
+  Start s;
+  s.cy = c / gm.nx;
+  s.cx = c - s.cy * gm.nx;
+  const int sy = pc.px == 1 ? sub : sub / pc.px, sx = sub - sy * pc.px;
+  if (pc.pow2) {
+    s.fx = ((float)sx + 0.5f) * pc.finv_x;
+    s.fy = ((float)sy + 0.5f) * pc.finv_y;
+    s.dfx = (double)s.fx;
+    s.dfy = (double)s.fy;
+  } else {
+    s.dfx = ((double)sx + 0.5) * pc.inv_x;
+    s.dfy = ((double)sy + 0.5) * pc.inv_y;
+    s.fx = (float)s.dfx;
+    s.fy = (float)s.dfy;
+  }
+  return s;
 }
 
-// Weights w at u, w0 at u0 (bases b, b0) and, when b == b0, dw = w - w0 from the polynomial
-// differences (each proportional to u - u0).
+// u - u0 in FP32 for u = j + df (df the FP64 fraction) and the start j0 + df0: the FP64
+// fraction difference is exact, so a small move keeps its full relative precision.
+__device__ __forceinline__ float move_of(int j, double df, int j0, double df0) {
+  return (float)(j - j0) + (float)(df - df0);
+}
+
+// Weights w at u = j + d, w0 at u0 = j0 + d0 (bases b, b0) and, when b == b0, dw = w - w0 from
+// the polynomial differences (each proportional to dl = u - u0).
 template <int P>
-__device__ __forceinline__ void weight_diff(double u, double u0, float* w, float* w0, float* dw, int& b, int& b0) {
-  const double jf = floor(u), jf0 = floor(u0);
-  const float d = (float)(u - jf), d0 = (float)(u0 - jf0);
-  b = shape_weights<P, float>((int)jf, d, w);
-  b0 = shape_weights<P, float>((int)jf0, d0, w0);
+__device__ __forceinline__ void weight_diff(int j, float d, int j0, float d0, float dl, float* w, float* w0, float* dw,
+                                            int& b, int& b0) {
+  b = shape_weights<P, float>(j, d, w);
+  b0 = shape_weights<P, float>(j0, d0, w0);
   if (b != b0) return;
-  const float dl = (float)(u - u0);
   if constexpr (P == 0) {
     dw[0] = 0.0f;
   } else if constexpr (P == 1) {
@@ -426,21 +458,23 @@ __device__ __forceinline__ float b2_diff(float t0, float dl) {
   return b2_within(t, tb, (t0 - tb) + dl, p) + b2_within(tb, t0, tb - t0, p0);
 }
 
-// q w (S(u, v) - S(u0, v0)) into ps.
+// q w (S(u, v) - S(u0, v0)) into ps; the new position u = jx + fx (FP32 fraction fx, FP64 dfx),
+// v = jy + fy, and the start s0.
 template <int P>
-__device__ __forceinline__ void deposit_psi_src(float* ps, const Geom& gm, double u, double v, double u0, double v0,
-                                                float qw) {
+__device__ __forceinline__ void deposit_psi_src(float* ps, const Geom& gm, int jx, float fx, double dfx, int jy, float fy,
+                                                double dfy, const Start& s0, float qw) {
+  const float dlx = move_of(jx, dfx, s0.cx, s0.dfx), dly = move_of(jy, dfy, s0.cy, s0.dfy);
   if constexpr (P == 2) {
     // quadratic: the cell-centred start sits on a piece boundary, so the two stencils' bases
     // differ by one for about half the particles; difference over the 4-node union support.
     // With |u - u0| < 1 each node's offset crosses at most one piece boundary (pieces are one
     // cell wide), which b2_diff handles; farther moves take the two-stencil path below.
-    const int bx = (int)floor(u + 0.5) - 1, bx0 = (int)floor(u0 + 0.5) - 1;
-    const int by = (int)floor(v + 0.5) - 1, by0 = (int)floor(v0 + 0.5) - 1;
-    if (fabs(u - u0) < 1.0 && fabs(v - v0) < 1.0) {
-      const int jx = bx < bx0 ? bx : bx0, jy = by < by0 ? by : by0;
-      const float dlx = (float)(u - u0), dly = (float)(v - v0);
-      const float tx0 = (float)(u0 - (double)jx), ty0 = (float)(v0 - (double)jy);   // node jx, jy offsets
+    // Nearest-node bases: floor(u + 1/2) - 1 = j + [f >= 1/2] - 1.
+    const int bx = jx + (fx >= 0.5f ? 1 : 0) - 1, bx0 = s0.cx + (s0.fx >= 0.5f ? 1 : 0) - 1;
+    const int by = jy + (fy >= 0.5f ? 1 : 0) - 1, by0 = s0.cy + (s0.fy >= 0.5f ? 1 : 0) - 1;
+    if (fabsf(dlx) < 1.0f && fabsf(dly) < 1.0f) {
+      const int ux = bx < bx0 ? bx : bx0, uy = by < by0 ? by : by0;
+      const float tx0 = (float)(s0.cx - ux) + s0.fx, ty0 = (float)(s0.cy - uy) + s0.fy;   // u0 - ux, v0 - uy
       float wy[4], w0x[4], dwx[4], dwy[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -452,11 +486,11 @@ __device__ __forceinline__ void deposit_psi_src(float* ps, const Geom& gm, doubl
       }
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const int iy = jy + b;
+        const int iy = uy + b;
         if (!in_interior(iy, gm.ny)) continue;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          const int ix = jx + a;
+          const int ix = ux + a;
           const float val = dwx[a] * wy[b] + w0x[a] * dwy[b];
           if (val != 0.0f && in_interior(ix, gm.nx)) atomicAdd(ps + (int64_t)iy * gm.nx + ix, qw * val);
         }
@@ -466,8 +500,8 @@ __device__ __forceinline__ void deposit_psi_src(float* ps, const Geom& gm, doubl
   }
   float wx[P + 1], w0x[P + 1], dwx[P + 1], wy[P + 1], w0y[P + 1], dwy[P + 1];
   int bx, bx0, by, by0;
-  weight_diff<P>(u, u0, wx, w0x, dwx, bx, bx0);
-  weight_diff<P>(v, v0, wy, w0y, dwy, by, by0);
+  weight_diff<P>(jx, fx, s0.cx, s0.fx, dlx, wx, w0x, dwx, bx, bx0);
+  weight_diff<P>(jy, fy, s0.cy, s0.fy, dly, wy, w0y, dwy, by, by0);
   if (bx == bx0 && by == by0) {
     // S - S0 = (wx - w0x) wy + w0x (wy - w0y)
 #pragma unroll
@@ -488,11 +522,10 @@ __device__ __forceinline__ void deposit_psi_src(float* ps, const Geom& gm, doubl
 
 // The ion left behind by a removed particle: -q w S(u0, v0).
 template <int P>
-__device__ __forceinline__ void deposit_ion_src(float* ps, const Geom& gm, double u0, double v0, float qw) {
+__device__ __forceinline__ void deposit_ion_src(float* ps, const Geom& gm, const Start& s0, float qw) {
   float wx[P + 1], wy[P + 1];
-  const double jx = floor(u0), jy = floor(v0);
-  const int bx = shape_weights<P, float>((int)jx, (float)(u0 - jx), wx);
-  const int by = shape_weights<P, float>((int)jy, (float)(v0 - jy), wy);
+  const int bx = shape_weights<P, float>(s0.cx, s0.fx, wx);
+  const int by = shape_weights<P, float>(s0.cy, s0.fy, wy);
   add_stencil<P>(ps, gm.nx, gm.ny, bx, by, wx, wy, -qw);
 }
 
@@ -501,18 +534,17 @@ __device__ __forceinline__ void deposit_ion_src(float* ps, const Geom& gm, doubl
 // advance to slice i+1, apply the removal rule and deposit rho, J, chi there.
 template <int P, typename T, bool CACHE>
 __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf,
-                                                         V4<T>* dep, T* chi, float* ps, int ppx, int ppy,
-                                                         double inv_ppx, double inv_ppy, int slice, double guard,
-                                                         unsigned long long* removed) {
+                                                         V4<T>* dep, T* chi, float* ps, PpcInfo pc, int slice,
+                                                         double guard, unsigned long long* removed) {
   pdl_trigger();
   pdl_wait();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pl.n) return;
-  double u0 = 0.0, v0 = 0.0;
-  if (ps) initial_coord(p, gm, ppx, ppy, inv_ppx, inv_ppy, u0, v0);
+  Start s0{};
+  if (ps) s0 = start_coord(p, gm, pc);
   if (!pl.alive[p]) {
     if constexpr (sizeof(T) == 4)
-      if (ps) deposit_ion_src<P>(ps, gm, u0, v0, charge_density<T>(pl.w[p], gm));
+      if (ps) deposit_ion_src<P>(ps, gm, s0, charge_density<T>(pl.w[p], gm));
     return;
   }
   const int64_t n = pl.n;
@@ -557,14 +589,14 @@ __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, 
   const double nxp = pl.x[p] - dz * (double)comb[0];
   const double nyp = pl.y[p] - dz * (double)comb[1];
   const double npsi = pl.psi[p] - dz * (double)comb[4];
-  const T nux = ux - T(dz) * comb[2];
-  const T nuy = uy - T(dz) * comb[3];
+  const T nux = ux - gsel<T>(dz, gm.f_dz) * comb[2];
+  const T nuy = uy - gsel<T>(dz, gm.f_dz) * comb[3];
   const double nopp = 1.0 + npsi;
   if (!state_ok(gm, nxp, nyp, nopp, guard)) {
     pl.alive[p] = 0;
     atomicAdd(removed, 1ull);
     if constexpr (sizeof(T) == 4)
-      if (ps) deposit_ion_src<P>(ps, gm, u0, v0, charge_density<T>(pl.w[p], gm));
+      if (ps) deposit_ion_src<P>(ps, gm, s0, charge_density<T>(pl.w[p], gm));
     return;
   }
   pl.x[p] = nxp;
@@ -573,11 +605,18 @@ __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, 
   pl.ux[p] = nux;
   pl.uy[p] = nuy;
   T topp;
+  int jx = 0, jy = 0;           // FP32 path: cell, FP64 and FP32 fraction of the new position
+  double dfx = 0.0, dfy = 0.0;
+  float frx = 0.0f, fry = 0.0f;
   if constexpr (CACHE) {
     const double ux_ = (nxp - gm.xmin) * gm.inv_dx, uy_ = (nyp - gm.ymin) * gm.inv_dy;
     const double flx = floor(ux_), fly = floor(uy_);
-    const int jx = (int)flx, jy = (int)fly;
-    const float frx = (float)(ux_ - flx), fry = (float)(uy_ - fly);
+    jx = (int)flx;
+    jy = (int)fly;
+    dfx = ux_ - flx;
+    dfy = uy_ - fly;
+    frx = (float)dfx;
+    fry = (float)dfy;
     pl.cell[p] = (jy << 16) | jx;
     pl.fx[p] = frx;
     pl.fy[p] = fry;
@@ -595,8 +634,8 @@ __global__ void __launch_bounds__(kThreads) k_final_pass(Plasma<T> pl, Geom gm, 
   const T uz = uz_of<T>(nux, nuy, topp, npsi, g);
   deposit_full<P, T>(dep, chi, gm.nx, gm.ny, ix0, iy0, wx, wy, qw * gam * g, qw * nux * g, qw * nuy * g,
                      qw * uz * g, qw * T(-1) * g);
-  if constexpr (sizeof(T) == 4)
-    if (ps) deposit_psi_src<P>(ps, gm, (nxp - gm.xmin) * gm.inv_dx, (nyp - gm.ymin) * gm.inv_dy, u0, v0, qw);
+  if constexpr (CACHE)
+    if (ps) deposit_psi_src<P>(ps, gm, jx, frx, dfx, jy, fry, dfy, s0, qw);
 }
 
 template <typename T> Plasma<T> plasma_of(const hq_grid_s* g);
@@ -653,12 +692,19 @@ void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cuda
   const double gd = g->d.psi_guard;
   unsigned long long* rm = g->d_removed;
   float* ps = psrc_of(g, dep);
-  const int px = g->d.ppc_x, py = g->d.ppc_y;
+  PpcInfo pc;
+  pc.px = g->d.ppc_x;
+  pc.py = g->d.ppc_y;
+  pc.pow2 = (pc.px & (pc.px - 1)) == 0 && (pc.py & (pc.py - 1)) == 0;
+  pc.inv_x = 1.0 / pc.px;
+  pc.inv_y = 1.0 / pc.py;
+  pc.finv_x = (float)pc.inv_x;
+  pc.finv_y = (float)pc.inv_y;
   switch (g->d.shape_order) {
-    case 0: launch_pdl(k_final_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, 1.0 / px, 1.0 / py, slice, gd, rm); break;
-    case 1: launch_pdl(k_final_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, 1.0 / px, 1.0 / py, slice, gd, rm); break;
-    case 2: launch_pdl(k_final_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, 1.0 / px, 1.0 / py, slice, gd, rm); break;
-    default: launch_pdl(k_final_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, px, py, 1.0 / px, 1.0 / py, slice, gd, rm); break;
+    case 0: launch_pdl(k_final_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, pc, slice, gd, rm); break;
+    case 1: launch_pdl(k_final_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, pc, slice, gd, rm); break;
+    case 2: launch_pdl(k_final_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, pc, slice, gd, rm); break;
+    default: launch_pdl(k_final_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, pc, slice, gd, rm); break;
   }
 }
 
