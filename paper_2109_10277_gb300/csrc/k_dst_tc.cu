@@ -169,15 +169,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
   tmem_ld32_issue(taddr, v);
   tmem_ld_wait();
 }
-// 32 columns of a stacked accumulator: x[j] = D[c0 + j] + D[BN + c0 + j] of this thread's lane
-template <int BN>
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+// W (16 or 32) columns of a stacked accumulator: x[j] = D[c0 + j] + D[BN + c0 + j] of this
+// thread's lane
+template <int BN, int W>
 __device__ __forceinline__ void tmem_ld_pair(uint32_t taddr, float* x) {
-  uint32_t v[32], u[32];
-  tmem_ld32_issue(taddr, v);
-  tmem_ld32_issue(taddr + (uint32_t)BN, u);
+  uint32_t v[W], u[W];
+  if constexpr (W == 32) {
+    tmem_ld32_issue(taddr, v);
+    tmem_ld32_issue(taddr + (uint32_t)BN, u);
+  } else {
+    static_assert(W == 16, "16 or 32 columns");
+    tmem_ld16_issue(taddr, v);
+    tmem_ld16_issue(taddr + (uint32_t)BN, u);
+  }
   tmem_ld_wait();
 #pragma unroll
-  for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]) + __uint_as_float(u[j]);
+  for (int j = 0; j < W; ++j) x[j] = __uint_as_float(v[j]) + __uint_as_float(u[j]);
 }
 
 template <int BN>
@@ -407,6 +422,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
 // N-tile widths of the fused solve: 64, or 32 when that still gives every tile its own CTA
 // (twice the tiles, so more of the SMs take part in each product).
 template <int BN> constexpr int bn_index() { return BN == 64 ? 0 : 1; }
+constexpr int kSolveThreads = 256;   // warps 0, 1: TMA producer, MMA issuer; all 8: epilogue
 
 // Optional per-CTA timestamps of the solve's steps (a profiling build defines it).
 #ifndef HQ_SOLVE_TRACE_POINT
@@ -424,7 +440,7 @@ template <int BN> struct SolveSmem {
 };
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kSolveThreads, 1)
     k_dst_solve(const __grid_constant__ CUtensorMap a0h, const __grid_constant__ CUtensorMap a0l,
                 const __grid_constant__ CUtensorMap a1h, const __grid_constant__ CUtensorMap a1l,
                 const __grid_constant__ CUtensorMap bxh, const __grid_constant__ CUtensorMap bxl,
@@ -557,9 +573,14 @@ __global__ void __launch_bounds__(128, 1)
       tc_fence_after();
       HQ_SOLVE_TRACE_POINT(p, 2);
 
-      // ------------------------------------------------ epilogue: TMEM lane = tile row
-      const int row = warp * 32 + lane;
+      // ------------------------------------------------ epilogue: TMEM lane = tile row; the
+      // two warpgroups take one half of the columns each (a warp reads the lanes of its
+      // quarter of the tile, warp % 4)
+      constexpr int CH = BN / 2;
+      const int row = (warp & 3) * 32 + lane;
       const int ml = ml0 + row;
+      const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+      const int c0 = (warp >> 2) * CH;
       if (mode <= 1) {
         // scale (phase 1), fold with the pair partner (one shuffle), split and store the next
         // operand transposed: folded, even rows hold pair sums (column u), odd rows pair
@@ -568,47 +589,44 @@ __global__ void __launch_bounds__(128, 1)
         const int fcol = a.fold ? (odd ? P1 / 2 + (ml >> 1) : (ml >> 1)) : ml;
         __nv_bfloat16* oh = a.op_hi[along_x ? 1 : 0];
         __nv_bfloat16* ol = a.op_lo[along_x ? 1 : 0];
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          float x[32];
-          tmem_ld_pair<BN>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, x);
-          HQ_SOLVE_TRACE_POINT(p, 8 + c0 / 16);
+        {
+          float x[CH];
+          tmem_ld_pair<BN, CH>(tl + (uint32_t)c0, x);
+          HQ_SOLVE_TRACE_POINT(p, 8);
           if (mode == 1) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) x[j] *= scale_s[(c0 + j) * BM + row];
+            for (int j = 0; j < CH; ++j) x[j] *= scale_s[(c0 + j) * BM + row];
           }
           if (a.fold) {
-            // all 32 exchanges first, so that the warp's shuffles overlap
-            float y[32];
+            // all exchanges first, so that the warp's shuffles overlap
+            float y[CH];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) y[j] = __shfl_xor_sync(0xffffffffu, x[j], 1);
+            for (int j = 0; j < CH; ++j) y[j] = __shfl_xor_sync(0xffffffffu, x[j], 1);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) x[j] = odd ? (wall ? 0.0f : y[j] - x[j]) : (wall ? y[j] : x[j] + y[j]);
+            for (int j = 0; j < CH; ++j) x[j] = odd ? (wall ? 0.0f : y[j] - x[j]) : (wall ? y[j] : x[j] + y[j]);
           }
 #pragma unroll
-          for (int j = 0; j < 32; ++j) put_split(oh, ol, ((int64_t)r * P2 + n0 + c0 + j) * P1 + fcol, x[j]);
-          HQ_SOLVE_TRACE_POINT(p, 9 + c0 / 16);
+          for (int j = 0; j < CH; ++j) put_split(oh, ol, ((int64_t)r * P2 + n0 + c0 + j) * P1 + fcol, x[j]);
+          HQ_SOLVE_TRACE_POINT(p, 9);
         }
       } else {
         // node of this row (rows run along x in the last phase)
         const int xn = a.fold ? fold_node(ml, a.nx) : ml;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          float x[32];
-          tmem_ld_pair<BN>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, x);
-          if (xn >= a.nx) continue;
+        float x[CH];
+        tmem_ld_pair<BN, CH>(tl + (uint32_t)c0, x);
+        if (xn < a.nx) {
           auto ynode = [&](int j) { return a.fold ? fold_node(n0 + c0 + j, a.ny) : n0 + c0 + j; };
           if (mode == 2) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
+            for (int j = 0; j < CH; ++j) {
               const int yn = ynode(j);
               if (yn < a.ny) a.out[((int64_t)r * a.ny + yn) * a.nx + xn] = x[j];
             }
           } else {
             // predictor-corrector mixing into gf[3 + r] (all loads first, then mix and store)
-            float old[32], prev1[32];
+            float old[CH], prev1[CH];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
+            for (int j = 0; j < CH; ++j) {
               const int yn = ynode(j);
               const int64_t node = (int64_t)yn * a.nx + xn;
               old[j] = yn < a.ny ? a.gf[node * kGF + 3 + r] : 0.0f;
@@ -616,7 +634,7 @@ __global__ void __launch_bounds__(128, 1)
             }
             bool bad = false;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
+            for (int j = 0; j < CH; ++j) {
               const int yn = ynode(j);
               if (yn >= a.ny) continue;
               bad |= !isfinite(x[j]);
@@ -726,7 +744,7 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
   auto size_solve = [&](auto kern, int smem, int& ctas) {
     int per_sm = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem) != cudaSuccess || per_sm < 1) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSolveThreads, smem) != cudaSuccess || per_sm < 1) {
       err = "cannot size the cooperative DST solve";
       return false;
     }
@@ -800,7 +818,7 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s) 
   const int v = narrow ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)std::min(t.ctas[v], tiles(narrow ? 32 : 64)));
-  cfg.blockDim = dim3(128);
+  cfg.blockDim = dim3(kSolveThreads);
   cfg.dynamicSmemBytes = narrow ? SolveSmem<32>::BYTES : SolveSmem<64>::BYTES;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
