@@ -39,8 +39,9 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 # algorithmic bytes per particle of the FP32 particle passes (reads + writes)
-BYTES_TRIAL = 109   # ux, uy, w (12) + AB5 history 4x5x4 (80) + cell/frac/1+Psi cache (16) + alive (1)
-BYTES_FINAL = 201   # reads: x, y, Psi (24) + 12 + 80 + 16 + 1; writes: x, y, Psi (24), ux, uy (8), f_i (20), cache (16)
+BYTES_TRIAL = 49    # ux, uy, w (12) + AB5 history sum (20) + cell/frac/1+Psi cache (16) + alive (1)
+BYTES_FINAL = 221   # reads: x, y, Psi (24), ux, uy, w (12), AB5 history 4x5x4 (80), cache (16), alive (1);
+                    # writes: x, y, Psi (24), ux, uy (8), f_i (20), history sum (20), cache (16)
 
 
 def parse():
@@ -59,7 +60,9 @@ def parse():
     ap.add_argument("--cubic-steps", type=int, default=1,
                     help="beam time steps of the cubic1024 leg (the workload defines 10)")
     ap.add_argument("--case", choices=("sweep", "poisson"), default="sweep",
-                    help="poisson: only repeated 3-RHS Dirichlet solves on the workload grid (for ncu captures)")
+                    help="poisson: only repeated Dirichlet solves on the workload grid (for ncu captures)")
+    ap.add_argument("--rhs", type=int, default=3, choices=(1, 2, 3),
+                    help="right-hand sides per solve of the poisson case (3: the psi/Ez/Bz solve, 2: B_perp)")
     return ap.parse_args()
 
 
@@ -184,7 +187,10 @@ def run_reference(args):
 # DRAM bytes (read + write) per launch from one ncu capture of the current build (cold L2):
 # k_dst_solve on 512^2 with 3 rhs (the operands read once) and k_final_pass on the 512^2
 # plasma slice; the capture commands are recorded with their summaries under profiles/.
-NCU_TRAFFIC = {"dst": 5.325824e6, "final": 49.540096e6}
+# DRAM bytes per launch (ncu, caches flushed before each launch) on the 512^2 workload: the
+# solves as the sweep mixes them (5 two-RHS 32-wide-tile launches to 1 three-RHS one per
+# slice: 4.246 MB and 5.325 MB), the trial and final passes of one slice
+NCU_TRAFFIC = {"dst": (5 * 4.246016e6 + 5.324544e6) / 6, "trial": 23.322368e6, "final": 48.637184e6}
 
 
 def dst_flops_per_sweep(g: dict) -> float:
@@ -554,19 +560,19 @@ def run_hq(args):
 
 
 def run_poisson_case(args):
-    """A few 3-right-hand-side solves on the workload grid: the DST kernels alone."""
+    """A few Dirichlet solves of --rhs right-hand sides on the workload grid: the DST kernels alone."""
     import torch
     from paper_2109_10277_gb300 import hq
     from paper_2109_10277_gb300 import inputs as I
     g = I.grid_params(WORKLOAD)
     grid = hq.Grid(g, precision=args.precision)
     dt = torch.float32 if args.precision == "fp32" else torch.float64
-    src = torch.randn(3, g["ny"], g["nx"], dtype=dt, device="cuda")
+    src = torch.randn(args.rhs, g["ny"], g["nx"], dtype=dt, device="cuda")
     for _ in range(args.warmup + args.steps):
         grid.poisson_solve(src)
     grid.sync()
     grid.close()
-    print(json.dumps({"case": "poisson", "solves": args.warmup + args.steps}))
+    print(json.dumps({"case": "poisson", "rhs": args.rhs, "solves": args.warmup + args.steps}))
 
 
 def main():

@@ -143,7 +143,10 @@ struct AdjStore {
   double* wbar_p = nullptr;
   void* dbar[3] = {nullptr, nullptr, nullptr};
   void* carry[3] = {nullptr, nullptr, nullptr};
-  void *fbar = nullptr, *bbar = nullptr, *jbar = nullptr, *jtot = nullptr, *rho_ion_bar = nullptr;
+  // adjoints of the gathered fields of one slice: ExmBy, EypBx, Ez, Bz (4 per node, from the
+  // witness, final and trial adjoints) and Bx, By (2 per node, from the final adjoint)
+  void *tbar = nullptr, *fbar_b = nullptr;
+  void *bbar = nullptr, *jbar = nullptr, *jtot = nullptr, *rho_ion_bar = nullptr;
   std::vector<void*> allocs;
 };
 
@@ -402,7 +405,7 @@ hq_status adj_alloc(hq_grid_s* g, int k) {
   for (int i = 0; ok && i < k; ++i)
     ok = snap(a->tape[i]) && A(&a->tape_gf[i], kGF * ts * nn) && A(&a->tape_b[i], (size_t)std::max(npc, 1) * 2 * ts * nn);
   ok = ok && A(&a->sx, ts * np) && A(&a->sy, ts * np) && A(&a->sux, ts * np) && A(&a->suy, ts * np) &&
-       A(&a->spsi, ts * np) && A(&a->sh, ts * np * 20) && A(&a->sacc, ts * np * 5) && A((void**)&a->wbar_p, 8 * np) && A(&a->fbar, kGF * ts * nn) &&
+       A(&a->spsi, ts * np) && A(&a->sh, ts * np * 20) && A(&a->sacc, ts * np * 5) && A((void**)&a->wbar_p, 8 * np) && A(&a->tbar, 4 * ts * nn) && A(&a->fbar_b, 2 * ts * nn) &&
        A(&a->bbar, (size_t)(npc + 1) * 2 * ts * nn) && A(&a->jbar, 2 * ts * nn) && A(&a->jtot, 2 * ts * nn) &&
        A(&a->rho_ion_bar, ts * nn);
   for (int i = 0; ok && i < 3; ++i) ok = A(&a->dbar[i], 4 * ts * nn) && A(&a->carry[i], 2 * ts * nn);
@@ -486,6 +489,9 @@ hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witn
     cudaMemsetAsync(a->carry[i], 0, 2 * ts * nn, s);
   }
   cudaMemsetAsync(a->rho_ion_bar, 0, ts * nn, s);
+  // cleared again by their consumers (main_post, bstart) for every next slice
+  cudaMemsetAsync(a->tbar, 0, 4 * ts * nn, s);
+  cudaMemsetAsync(a->fbar_b, 0, 2 * ts * nn, s);
   for (int b = 0; b < nb; ++b)
     if (wbar_b && wbar_b[b] && beams[b].n > 0) cudaMemsetAsync(wbar_b[b], 0, 8 * (size_t)beams[b].n, s);
   void* dnext = a->dbar[0];
@@ -511,19 +517,18 @@ hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witn
       SnapView<T> sv{g->np, sn.x, sn.y, sn.psi, reinterpret_cast<const T*>(sn.ux), reinterpret_cast<const T*>(sn.uy), w,
                      sn.alive, reinterpret_cast<const T*>(sn.hist), g->fp64 ? nullptr : sn.hsum};
       const void* gf = a->tape_gf[t];
-      cudaMemsetAsync(a->fbar, 0, kGF * ts * nn, s);
       cudaMemsetAsync(a->jtot, 0, 2 * ts * nn, s);
       if (witness >= 0 && beams[witness].n > 0) {
         Prof p(g, HQ_K_BEAM, 1);
-        launch_adj_witness<T>(g, witness, beams[witness], i, gf, sbar, a->fbar,
+        launch_adj_witness<T>(g, witness, beams[witness], i, gf, sbar, a->tbar,
                               wbar_b ? wbar_b[witness] : nullptr, s);
       }
       if (i < g->nz - 1) {
         Prof p(g, HQ_K_FINAL, 1);
-        launch_adj_final<T>(g, sv, gf, i, dnext, av, a->fbar, a->wbar_p, s);
+        launch_adj_final<T>(g, sv, gf, i, dnext, av, a->tbar, a->fbar_b, a->wbar_p, s);
       }
       char* bb = reinterpret_cast<char*>(a->bbar);
-      { Prof p(g, HQ_K_FIELD, 1); launch_adj_bstart<T>(g, a->fbar, a->carry[i % 3], bb + (size_t)npc * brec, s); }
+      { Prof p(g, HQ_K_FIELD, 1); launch_adj_bstart<T>(g, a->fbar_b, a->carry[i % 3], bb + (size_t)npc * brec, s); }
       for (int m = npc; m >= 1; --m) {
         { Prof p(g, HQ_K_FIELD, 1); launch_adj_pc_pre<T>(g, bb + (size_t)m * brec, bb + (size_t)(m - 1) * brec, s); }
         dst_solve(g, 2);
@@ -531,16 +536,16 @@ hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witn
         {
           Prof p(g, HQ_K_TRIAL, 1);
           launch_adj_trial<T>(g, sv, gf, reinterpret_cast<char*>(a->tape_b[t]) + (size_t)(m - 1) * brec, i, a->jbar, av,
-                              a->fbar, bb + (size_t)(m - 1) * brec, a->wbar_p, s);
+                              a->tbar, bb + (size_t)(m - 1) * brec, a->wbar_p, s);
         }
       }
       {
         Prof p(g, HQ_K_FIELD, 1);
         launch_adj_guess<T>(g, bb, i >= 1 ? a->carry[(i - 1) % 3] : nullptr, i >= 2 ? a->carry[(i - 2) % 3] : nullptr, s);
       }
-      { Prof p(g, HQ_K_FIELD, 1); launch_adj_main_pre<T>(g, a->fbar, s); }
+      { Prof p(g, HQ_K_FIELD, 1); launch_adj_main_pre<T>(g, a->tbar, s); }
       dst_solve(g, 3);
-      { Prof p(g, HQ_K_FIELD, 1); launch_adj_main_post<T>(g, dcur, a->rho_ion_bar, s); }
+      { Prof p(g, HQ_K_FIELD, 1); launch_adj_main_post<T>(g, dcur, a->rho_ion_bar, a->tbar, s); }
       for (int b = 0; b < nb; ++b) {
         if (!wbar_b || !wbar_b[b] || beams[b].n == 0) continue;
         Prof p(g, HQ_K_BEAM, 1);

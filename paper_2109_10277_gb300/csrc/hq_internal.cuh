@@ -238,22 +238,23 @@ template <typename T> void launch_beam_push(const hq_grid_s* g, int b, const hq_
 template <typename T> void launch_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double* sums, cudaStream_t s);
 // adjoint (k_adjoint.cu)
 template <typename T> void launch_adj_final(const hq_grid_s* g, const SnapView<T>& s, const void* gf, int slice,
-                                           const void* dbar_next, const AdjView<T>& a, void* fbar, double* wbar_p,
-                                           cudaStream_t st);
-template <typename T> void launch_adj_trial(const hq_grid_s* g, const SnapView<T>& s, const void* gf, const void* bm,
-                                           int slice, const void* jbar, const AdjView<T>& a, void* fbar, void* bbar_m1,
+                                           const void* dbar_next, const AdjView<T>& a, void* tbar, void* fbar_b,
                                            double* wbar_p, cudaStream_t st);
-template <typename T> void launch_adj_bstart(const hq_grid_s* g, const void* fbar, void* carry, void* bbar_n, cudaStream_t st);
+template <typename T> void launch_adj_trial(const hq_grid_s* g, const SnapView<T>& s, const void* gf, const void* bm,
+                                           int slice, const void* jbar, const AdjView<T>& a, void* tbar, void* bbar_m1,
+                                           double* wbar_p, cudaStream_t st);
+template <typename T> void launch_adj_bstart(const hq_grid_s* g, void* fbar_b, void* carry, void* bbar_n, cudaStream_t st);
 template <typename T> void launch_adj_pc_pre(const hq_grid_s* g, const void* bbar_m, void* bbar_m1, cudaStream_t st);
 template <typename T> void launch_adj_pc_post(const hq_grid_s* g, void* dcur, void* dprev, void* jbar, void* jtot, cudaStream_t st);
 template <typename T> void launch_adj_guess(const hq_grid_s* g, const void* b0, void* c1, void* c2, cudaStream_t st);
-template <typename T> void launch_adj_main_pre(const hq_grid_s* g, const void* fbar, cudaStream_t st);
-template <typename T> void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, cudaStream_t st);
+template <typename T> void launch_adj_main_pre(const hq_grid_s* g, const void* tbar, cudaStream_t st);
+template <typename T> void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, void* tbar,
+                                               cudaStream_t st);
 template <typename T> void launch_adj_extract_b(const hq_grid_s* g, void* out, cudaStream_t st);
 template <typename T> void launch_adj_beam(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* dcur,
                                           const void* jtot, double* wbar, cudaStream_t st);
 template <typename T> void launch_adj_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* gf,
-                                             const double* sb, void* fbar, double* wbar, cudaStream_t st);
+                                             const double* sb, void* tbar, double* wbar, cudaStream_t st);
 template <typename T> void launch_adj_init(const hq_grid_s* g, const void* d0, const void* rho_ion_bar, double* wbar_p,
                                           cudaStream_t st);
 void launch_adj_params(const hq_grid_s* g, const double* wbar_p, double* dn0, double* dprof, cudaStream_t st);

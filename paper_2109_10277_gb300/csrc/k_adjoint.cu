@@ -138,11 +138,11 @@ __device__ __forceinline__ void scatter(T* f, int st, int off, const Geom& gm, c
   }
 }
 
-// Adjoints of the six gathered fields into an 8-per-node gather record (ExmBy, EypBx, Ez, Bx,
-// By, Bz, pad, pad): in FP32 two float4 vector atomics per node (the record is 32 B), in
-// FP64 one atomic per component.
+// Adjoints of ExmBy, EypBx, Ez, Bz into a 4-per-node record: one float4 vector atomic per node
+// in FP32 (a warp's 32 consecutive nodes span 512 contiguous bytes), one atomic per component
+// in FP64.
 template <int P, typename T>
-__device__ __forceinline__ void scatter_gf(T* f, const Geom& gm, const Stencil<P, T>& s, const T* v) {
+__device__ __forceinline__ void scatter_v4(T* f, const Geom& gm, const Stencil<P, T>& s, const T* v) {
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
     for (int b = 0; b <= P; ++b) {
@@ -152,14 +152,13 @@ __device__ __forceinline__ void scatter_gf(T* f, const Geom& gm, const Stencil<P
       for (int a = 0; a <= P; ++a) {
         const int ix = s.ix0 + a;
         if (!in_interior(ix, gm.nx)) continue;
-        float* q = reinterpret_cast<float*>(f) + ((int64_t)iy * gm.nx + ix) * kGF;
         const float w = s.wx[a] * s.wy[b];
-        atomicAdd(reinterpret_cast<float4*>(q), make_float4(w * v[0], w * v[1], w * v[2], w * v[3]));
-        atomicAdd(reinterpret_cast<float4*>(q + 4), make_float4(w * v[4], w * v[5], 0.0f, 0.0f));
+        atomicAdd(reinterpret_cast<float4*>(f) + ((int64_t)iy * gm.nx + ix),
+                  make_float4(w * v[0], w * v[1], w * v[2], w * v[3]));
       }
     }
   } else {
-    scatter<P, T, 6>(f, kGF, 0, gm, s, v);
+    scatter<P, T, 4>(f, 4, 0, gm, s, v);
   }
 }
 
@@ -243,7 +242,7 @@ __device__ __forceinline__ T unit_charge_density(const Geom& gm) {  // q / A wit
 template <int P, typename T>
 __global__ void __launch_bounds__(kThreads)
     k_adj_final(SnapView<T> s, const T* __restrict__ gf, Geom gm, int slice, double guard,
-                const V4<T>* __restrict__ dbar_next, AdjView<T> a, T* fbar, double* wbar_p) {
+                const V4<T>* __restrict__ dbar_next, AdjView<T> a, T* tbar, V2<T>* fbar_b, double* wbar_p) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= s.n || !s.alive[p]) return;
   const int64_t n = s.n;
@@ -305,7 +304,13 @@ __global__ void __launch_bounds__(kThreads)
   }
   T bux, buy, bpsi, bF[6];
   derivs_adj<T>(ux, uy, opp, F, fb, bux, buy, bpsi, bF);
-  scatter_gf<P, T>(fbar, gm, st, bF);
+  {
+    // ExmBy, EypBx, Ez, Bz into tbar; Bx, By into fbar_b
+    const T v4[4] = {bF[0], bF[1], bF[2], bF[5]};
+    scatter_v4<P, T>(tbar, gm, st, v4);
+    const T v2b[2] = {bF[3], bF[4]};
+    scatter_v2<P, T>(reinterpret_cast<T*>(fbar_b), gm, st, v2b);
+  }
   T bx = sb[0], by = sb[1];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
@@ -325,7 +330,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int P, typename T>
 __global__ void __launch_bounds__(kThreads)
     k_adj_trial(SnapView<T> s, const T* __restrict__ gf, const V2<T>* __restrict__ bm, Geom gm, int slice, double guard,
-                const V2<T>* __restrict__ jbar, AdjView<T> a, T* fbar, V2<T>* bbar_m1, double* wbar_p) {
+                const V2<T>* __restrict__ jbar, AdjView<T> a, T* tbar, V2<T>* bbar_m1, double* wbar_p) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= s.n || !s.alive[p]) return;
   const int64_t n = s.n;
@@ -394,9 +399,9 @@ __global__ void __launch_bounds__(kThreads)
   T bux, buy, bpsi, bF[6];
   derivs_adj<T>(ux, uy, opp, F, fb, bux, buy, bpsi, bF);
   {
-    // ExmBy, EypBx, Ez, Bz into fbar; Bx, By of B^(m-1) into bbar_m1
-    const T v6[6] = {bF[0], bF[1], bF[2], T(0), T(0), bF[5]};
-    scatter_gf<P, T>(fbar, gm, st, v6);
+    // ExmBy, EypBx, Ez, Bz into tbar; Bx, By of B^(m-1) into bbar_m1
+    const T v4[4] = {bF[0], bF[1], bF[2], bF[5]};
+    scatter_v4<P, T>(tbar, gm, st, v4);
     const T v2b[2] = {bF[3], bF[4]};
     scatter_v2<P, T>(reinterpret_cast<T*>(bbar_m1), gm, st, v2b);
   }
@@ -414,14 +419,16 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------- node-level adjoints
-// Bbar^n = (fbar Bx, fbar By) + carry of B(i); the carry slot is cleared.
+// Bbar^n = (Bx, By adjoints of the final pass's gather) + carry of B(i); both are consumed
+// (cleared for the next slice).
 template <typename T>
-__global__ void k_adj_bstart(const T* __restrict__ fbar, V2<T>* carry, V2<T>* bbar_n, int64_t nn) {
+__global__ void k_adj_bstart(V2<T>* fbar_b, V2<T>* carry, V2<T>* bbar_n, int64_t nn) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nn) return;
-  const V2<T> c = carry[o];
-  bbar_n[o] = V2<T>{fbar[o * kGF + 3] + c.a, fbar[o * kGF + 4] + c.b};
+  const V2<T> c = carry[o], f = fbar_b[o];
+  bbar_n[o] = V2<T>{f.a + c.a, f.b + c.b};
   carry[o] = V2<T>{T(0), T(0)};
+  fbar_b[o] = V2<T>{T(0), T(0)};
 }
 
 // Mixing B^m = w Bs + (1-w) B^(m-1): the solve gets w Bbar^m, Bbar^(m-1) starts at (1-w) Bbar^m.
@@ -476,31 +483,34 @@ __global__ void k_adj_guess(const V2<T>* __restrict__ b0, V2<T>* c1, V2<T>* c2, 
   if (c2) { c2[o].a -= b.a; c2[o].b -= b.b; }
 }
 
-// psi_bar = Dx fbar0 + Dy fbar1 (ExmBy = -Dx psi, EypBx = -Dy psi), with Ez_bar, Bz_bar.
+// psi_bar = Dx tbar0 + Dy tbar1 (ExmBy = -Dx psi, EypBx = -Dy psi), with Ez_bar, Bz_bar: tbar
+// holds the adjoints of the gathered ExmBy, EypBx, Ez, Bz (witness, final and trial passes).
 template <typename T, typename Sink>
-__global__ void k_adj_main_pre(const T* __restrict__ fbar, Geom gm, Sink sink) {
+__global__ void k_adj_main_pre(const T* __restrict__ tbar, Geom gm, Sink sink) {
   const int nx = gm.nx;
-  auto f0 = [&](int y, int x) { return fbar[((int64_t)y * nx + x) * kGF + 0]; };
-  auto f1 = [&](int y, int x) { return fbar[((int64_t)y * nx + x) * kGF + 1]; };
+  auto f0 = [&](int y, int x) { return tbar[((int64_t)y * nx + x) * 4 + 0]; };
+  auto f1 = [&](int y, int x) { return tbar[((int64_t)y * nx + x) * 4 + 1]; };
   visit_nodes<3, T>(gm, sink, 3, [&](int iy, int ix, T* v) {
     const int64_t o = (int64_t)iy * nx + ix;
     v[0] = v[1] = v[2] = T(0);
     if (ix > 0 && iy > 0) {
       v[0] = dxc(f0, iy, ix, nx, gsel<T>(gm.inv2dx, gm.f_inv2dx)) + dyc(f1, iy, ix, gm.ny, gsel<T>(gm.inv2dy, gm.f_inv2dy));
-      v[1] = fbar[o * kGF + 2];
-      v[2] = fbar[o * kGF + 5];
+      v[1] = tbar[o * 4 + 2];
+      v[2] = tbar[o * 4 + 3];
     }
   });
 }
 
 // psi = L^-1(-(rho - Jz)), Ez = L^-1(dx Jx + dy Jy), Bz = L^-1(dy Jx - dx Jy), transposed.
+// tbar of this slice is consumed: cleared for the next slice.
 template <typename T>
-__global__ void k_adj_main_post(const T* __restrict__ res, V4<T>* dcur, T* rho_ion_bar, Geom gm) {
+__global__ void k_adj_main_post(const T* __restrict__ res, V4<T>* dcur, T* rho_ion_bar, V4<T>* tbar, Geom gm) {
   const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
   if (ix >= gm.nx) return;
   const int nx = gm.nx;
   const int64_t nn = (int64_t)nx * gm.ny;
   const int64_t o = (int64_t)iy * nx + ix;
+  tbar[o] = V4<T>{T(0), T(0), T(0), T(0)};
   V4<T> d = dcur[o];
   if (ix > 0 && iy > 0) {
     auto r1 = [&](int y, int x) { return res[nn + (int64_t)y * nx + x]; };
@@ -583,7 +593,7 @@ __global__ void k_adj_beam(hq_beam_view v, const int32_t* __restrict__ off, cons
 // Witness loss sums (S0, S1, S2) = sum q w (1, Ez, Ez^2) over slice i, with adjoints sb[0..2].
 template <int P, typename T>
 __global__ void k_adj_witness(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm,
-                              int slice, Geom gm, const T* __restrict__ gf, double sb0, double sb1, double sb2, T* fbar,
+                              int slice, Geom gm, const T* __restrict__ gf, double sb0, double sb1, double sb2, T* tbar,
                               double* wbar) {
   const int a0 = off[slice], a1 = off[slice + 1];
   for (int t = a0 + blockIdx.x * blockDim.x + threadIdx.x; t < a1; t += gridDim.x * blockDim.x) {
@@ -613,7 +623,7 @@ __global__ void k_adj_witness(hq_beam_view v, const int32_t* __restrict__ off, c
       for (int a = 0; a <= P; ++a) {
         const int ix = ix0 + a;
         if (!in_interior(ix, gm.nx)) continue;
-        atomicAdd(fbar + ((int64_t)iy * gm.nx + ix) * kGF + 2, T(wx[a] * wy[b] * e));
+        atomicAdd(tbar + ((int64_t)iy * gm.nx + ix) * 4 + 2, T(wx[a] * wy[b] * e));
       }
     }
   }
@@ -689,25 +699,26 @@ constexpr unsigned kSliceBlocks = 152;
 
 template <typename T>
 void launch_adj_final(const hq_grid_s* g, const SnapView<T>& s, const void* gf, int slice, const void* dbar_next,
-                      const AdjView<T>& a, void* fbar, double* wbar_p, cudaStream_t st) {
+                      const AdjView<T>& a, void* tbar, void* fbar_b, double* wbar_p, cudaStream_t st) {
   HQ_SHAPE_SWITCH(g->d.shape_order,
                   (k_adj_final<P, T><<<blocks_for(s.n), kThreads, 0, st>>>(
                       s, reinterpret_cast<const T*>(gf), g->geom, slice, g->d.psi_guard,
-                      reinterpret_cast<const V4<T>*>(dbar_next), a, reinterpret_cast<T*>(fbar), wbar_p)));
+                      reinterpret_cast<const V4<T>*>(dbar_next), a, reinterpret_cast<T*>(tbar),
+                      reinterpret_cast<V2<T>*>(fbar_b), wbar_p)));
 }
 template <typename T>
 void launch_adj_trial(const hq_grid_s* g, const SnapView<T>& s, const void* gf, const void* bm, int slice,
-                      const void* jbar, const AdjView<T>& a, void* fbar, void* bbar_m1, double* wbar_p,
+                      const void* jbar, const AdjView<T>& a, void* tbar, void* bbar_m1, double* wbar_p,
                       cudaStream_t st) {
   HQ_SHAPE_SWITCH(g->d.shape_order,
                   (k_adj_trial<P, T><<<blocks_for(s.n), kThreads, 0, st>>>(
                       s, reinterpret_cast<const T*>(gf), reinterpret_cast<const V2<T>*>(bm), g->geom, slice,
-                      g->d.psi_guard, reinterpret_cast<const V2<T>*>(jbar), a, reinterpret_cast<T*>(fbar),
+                      g->d.psi_guard, reinterpret_cast<const V2<T>*>(jbar), a, reinterpret_cast<T*>(tbar),
                       reinterpret_cast<V2<T>*>(bbar_m1), wbar_p)));
 }
 template <typename T>
-void launch_adj_bstart(const hq_grid_s* g, const void* fbar, void* carry, void* bbar_n, cudaStream_t st) {
-  k_adj_bstart<T><<<blocks_for(g->nnode), kThreads, 0, st>>>(reinterpret_cast<const T*>(fbar),
+void launch_adj_bstart(const hq_grid_s* g, void* fbar_b, void* carry, void* bbar_n, cudaStream_t st) {
+  k_adj_bstart<T><<<blocks_for(g->nnode), kThreads, 0, st>>>(reinterpret_cast<V2<T>*>(fbar_b),
                                                            reinterpret_cast<V2<T>*>(carry),
                                                            reinterpret_cast<V2<T>*>(bbar_n), g->nnode);
 }
@@ -731,15 +742,16 @@ void launch_adj_guess(const hq_grid_s* g, const void* b0, void* c1, void* c2, cu
                                                           g->nnode);
 }
 template <typename T>
-void launch_adj_main_pre(const hq_grid_s* g, const void* fbar, cudaStream_t st) {
+void launch_adj_main_pre(const hq_grid_s* g, const void* tbar, cudaStream_t st) {
   with_sink<T>(g, [&](auto sink) {
-    k_adj_main_pre<T, decltype(sink)><<<src_grid(g), 128, 0, st>>>(reinterpret_cast<const T*>(fbar), g->geom, sink);
+    k_adj_main_pre<T, decltype(sink)><<<src_grid(g), 128, 0, st>>>(reinterpret_cast<const T*>(tbar), g->geom, sink);
   });
 }
 template <typename T>
-void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, cudaStream_t st) {
+void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, void* tbar, cudaStream_t st) {
   k_adj_main_post<T><<<grid2d(g), 128, 0, st>>>(reinterpret_cast<const T*>(g->solved), reinterpret_cast<V4<T>*>(dcur),
-                                               reinterpret_cast<T*>(rho_ion_bar), g->geom);
+                                               reinterpret_cast<T*>(rho_ion_bar), reinterpret_cast<V4<T>*>(tbar),
+                                               g->geom);
 }
 template <typename T>
 void launch_adj_extract_b(const hq_grid_s* g, void* out, cudaStream_t st) {
@@ -757,12 +769,12 @@ void launch_adj_beam(const hq_grid_s* g, int b, const hq_beam_view& v, int slice
 }
 template <typename T>
 void launch_adj_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* gf, const double* sb,
-                        void* fbar, double* wbar, cudaStream_t st) {
+                        void* tbar, double* wbar, cudaStream_t st) {
   const BeamBins& bb = g->bins[b];
   HQ_SHAPE_SWITCH(g->d.shape_order,
                   (k_adj_witness<P, T><<<kSliceBlocks, kThreads, 0, st>>>(v, bb.offset, bb.perm, slice, g->geom,
                                                                           reinterpret_cast<const T*>(gf), sb[0], sb[1],
-                                                                          sb[2], reinterpret_cast<T*>(fbar), wbar)));
+                                                                          sb[2], reinterpret_cast<T*>(tbar), wbar)));
 }
 template <typename T>
 void launch_adj_init(const hq_grid_s* g, const void* d0, const void* rho_ion_bar, double* wbar_p, cudaStream_t st) {
@@ -780,15 +792,15 @@ void launch_adj_params(const hq_grid_s* g, const double* wbar_p, double* dn0, do
 
 #define HQ_INST(T)                                                                                                   \
   template void launch_adj_final<T>(const hq_grid_s*, const SnapView<T>&, const void*, int, const void*,              \
-                                    const AdjView<T>&, void*, double*, cudaStream_t);                                \
+                                    const AdjView<T>&, void*, void*, double*, cudaStream_t);                         \
   template void launch_adj_trial<T>(const hq_grid_s*, const SnapView<T>&, const void*, const void*, int, const void*, \
                                     const AdjView<T>&, void*, void*, double*, cudaStream_t);                         \
-  template void launch_adj_bstart<T>(const hq_grid_s*, const void*, void*, void*, cudaStream_t);                     \
+  template void launch_adj_bstart<T>(const hq_grid_s*, void*, void*, void*, cudaStream_t);                           \
   template void launch_adj_pc_pre<T>(const hq_grid_s*, const void*, void*, cudaStream_t);                            \
   template void launch_adj_pc_post<T>(const hq_grid_s*, void*, void*, void*, void*, cudaStream_t);                   \
   template void launch_adj_guess<T>(const hq_grid_s*, const void*, void*, void*, cudaStream_t);                      \
   template void launch_adj_main_pre<T>(const hq_grid_s*, const void*, cudaStream_t);                                 \
-  template void launch_adj_main_post<T>(const hq_grid_s*, void*, void*, cudaStream_t);                               \
+  template void launch_adj_main_post<T>(const hq_grid_s*, void*, void*, void*, cudaStream_t);                        \
   template void launch_adj_extract_b<T>(const hq_grid_s*, void*, cudaStream_t);                                      \
   template void launch_adj_beam<T>(const hq_grid_s*, int, const hq_beam_view&, int, const void*, const void*,        \
                                    double*, cudaStream_t);                                                           \
