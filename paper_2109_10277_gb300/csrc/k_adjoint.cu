@@ -91,7 +91,24 @@ __device__ __forceinline__ void stencil_at(const Geom& gm, double x, double y, S
   }
 }
 
-// Interpolated values and x/y gradients of NC components at stride `st` (offset `off`).
+// NC components of a node record q: FP32 records whose components start on a 16-byte (4 of
+// them) or 8-byte (2) boundary are read with one vector load.
+template <int NC, typename T>
+__device__ __forceinline__ void load_comp(const T* q, T* v) {
+  if constexpr (sizeof(T) == 4 && NC == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(q);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else if constexpr (sizeof(T) == 4 && NC == 2) {
+    const float2 a = *reinterpret_cast<const float2*>(q);
+    v[0] = a.x; v[1] = a.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = q[c];
+  }
+}
+
+// Interpolated values and x/y gradients of NC components at stride `st` (offset `off`);
+// NC of 4 or 2 with st and off multiples of NC read one vector per node in FP32.
 template <int P, typename T, int NC>
 __device__ __forceinline__ void gather_g(const T* __restrict__ f, int st, int off, const Geom& gm, const Stencil<P, T>& s,
                                          T* val, T* gx, T* gy) {
@@ -107,12 +124,13 @@ __device__ __forceinline__ void gather_g(const T* __restrict__ f, int st, int of
       if (!in_interior(ix, gm.nx)) continue;
       const T* q = f + ((int64_t)iy * gm.nx + ix) * st + off;
       const T w = s.wx[a] * s.wy[b], wxd = s.dwx[a] * s.wy[b], wyd = s.wx[a] * s.dwy[b];
+      T v[NC];
+      load_comp<NC, T>(q, v);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const T v = q[c];
-        val[c] += w * v;
-        gx[c] += wxd * v;
-        gy[c] += wyd * v;
+        val[c] += w * v[c];
+        gx[c] += wxd * v[c];
+        gy[c] += wyd * v[c];
       }
     }
   }
@@ -252,7 +270,8 @@ __global__ void __launch_bounds__(kThreads)
   Stencil<P, T> st;
   stencil_at<P, T>(gm, x, y, st);
   T F[6], Fx[6], Fy[6];
-  gather_g<P, T, 6>(gf, kGF, 0, gm, st, F, Fx, Fy);
+  gather_g<P, T, 4>(gf, kGF, 0, gm, st, F, Fx, Fy);            // ExmBy, EypBx, Ez, Bx
+  gather_g<P, T, 2>(gf, kGF, 4, gm, st, F + 4, Fx + 4, Fy + 4);  // By, Bz
   T f[5];
   derivs_f<T>(ux, uy, opp, F, f);
   T comb[5];
@@ -342,13 +361,13 @@ __global__ void __launch_bounds__(kThreads)
   T F[6], Fx[6], Fy[6];
   {
     T v4[4], g4x[4], g4y[4];
-    gather_g<P, T, 3>(gf, kGF, 0, gm, st, v4, g4x, g4y);   // ExmBy, EypBx, Ez
+    gather_g<P, T, 4>(gf, kGF, 0, gm, st, v4, g4x, g4y);   // ExmBy, EypBx, Ez (and the gather record's Bx)
     F[0] = v4[0]; F[1] = v4[1]; F[2] = v4[2];
     Fx[0] = g4x[0]; Fx[1] = g4x[1]; Fx[2] = g4x[2];
     Fy[0] = g4y[0]; Fy[1] = g4y[1]; Fy[2] = g4y[2];
-    T b1[1], b1x[1], b1y[1];
-    gather_g<P, T, 1>(gf, kGF, 5, gm, st, b1, b1x, b1y);   // Bz
-    F[5] = b1[0]; Fx[5] = b1x[0]; Fy[5] = b1y[0];
+    T b1[2], b1x[2], b1y[2];
+    gather_g<P, T, 2>(gf, kGF, 4, gm, st, b1, b1x, b1y);   // (By,) Bz
+    F[5] = b1[1]; Fx[5] = b1x[1]; Fy[5] = b1y[1];
     T b2[2], b2x[2], b2y[2];
     gather_g<P, T, 2>(reinterpret_cast<const T*>(bm), 2, 0, gm, st, b2, b2x, b2y);  // Bx, By of B^(m-1)
     F[3] = b2[0]; F[4] = b2[1];
