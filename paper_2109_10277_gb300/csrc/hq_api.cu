@@ -514,8 +514,10 @@ hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witn
     for (int i = a1 - 1; i >= a0; --i) {
       const int t = i - a0;
       const Snap& sn = a->tape[t];
+      const bool f32 = !g->fp64;
       SnapView<T> sv{g->np, sn.x, sn.y, sn.psi, reinterpret_cast<const T*>(sn.ux), reinterpret_cast<const T*>(sn.uy), w,
-                     sn.alive, reinterpret_cast<const T*>(sn.hist), g->fp64 ? nullptr : sn.hsum};
+                     sn.alive, reinterpret_cast<const T*>(sn.hist), f32 ? sn.hsum : nullptr, f32 ? sn.cell : nullptr,
+                     f32 ? sn.fx : nullptr, f32 ? sn.fy : nullptr, f32 ? sn.opp : nullptr};
       const void* gf = a->tape_gf[t];
       cudaMemsetAsync(a->jtot, 0, 2 * ts * nn, s);
       if (witness >= 0 && beams[witness].n > 0) {

@@ -96,6 +96,10 @@ template <typename T> struct SnapView {
   const uint8_t* alive;
   const T* hist;    // AB5 ring as stored: physical slot s holds f_k with k = s mod 4
   const float* hsum;   // FP32: the slice's AB5 history sum [5][n] (what the trial passes used); else null
+  // FP32: the slice's cached cell index, fractional node coordinates and 1 + Psi (what the
+  // trial passes and the final pass's gather used); else null
+  const int32_t* cell;
+  const float *fx, *fy, *opp;
 };
 
 // Per-particle adjoint state: x, y, ux, uy, Psi and the AB5 history in logical order

@@ -252,7 +252,20 @@ __device__ __forceinline__ bool ok_state(const Geom& gm, double x, double y, dou
 template <typename T>
 __device__ __forceinline__ T unit_charge_density(const Geom& gm) {  // q / A with q = -1
   if constexpr (sizeof(T) == 8) return T(-1.0) / (gm.dx * gm.dy);
-  else return T(-gm.inv_area);
+  else return -gm.f_inv_area;
+}
+
+// Stencil (weights and derivatives w.r.t. the physical coordinate) at node coordinate
+// (jx + fx, jy + fy), FP32: the cached split the forward kernels used.
+template <int P>
+__device__ __forceinline__ void stencil_split(const Geom& gm, int jx, float fx, int jy, float fy, Stencil<P, float>& s) {
+  s.ix0 = shape_wd<P, float>(jx, fx, s.wx, s.dwx);
+  s.iy0 = shape_wd<P, float>(jy, fy, s.wy, s.dwy);
+#pragma unroll
+  for (int a = 0; a <= P; ++a) {
+    s.dwx[a] *= gm.f_inv_dx;
+    s.dwy[a] *= gm.f_inv_dy;
+  }
 }
 
 // ---------------------------------------------------------------- final pass adjoint
@@ -266,9 +279,17 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t n = s.n;
   const double x = s.x[p], y = s.y[p], psi = s.psi[p];
   const T ux = s.ux[p], uy = s.uy[p], w = s.w[p];
-  const T opp = T(1.0 + psi);
+  T opp;
   Stencil<P, T> st;
-  stencil_at<P, T>(gm, x, y, st);
+  if constexpr (sizeof(T) == 4) {
+    // the forward final pass gathered at the cached cell coordinates, with the cached 1 + Psi
+    const int cell = s.cell[p];
+    stencil_split<P>(gm, cell & 0xFFFF, s.fx[p], cell >> 16, s.fy[p], st);
+    opp = s.opp[p];
+  } else {
+    stencil_at<P, T>(gm, x, y, st);
+    opp = T(1.0 + psi);
+  }
   T F[6], Fx[6], Fy[6];
   gather_g<P, T, 4>(gf, kGF, 0, gm, st, F, Fx, Fy);            // ExmBy, EypBx, Ez, Bx
   gather_g<P, T, 2>(gf, kGF, 4, gm, st, F + 4, Fx + 4, Fy + 4);  // By, Bz
@@ -353,11 +374,29 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= s.n || !s.alive[p]) return;
   const int64_t n = s.n;
-  const double x = s.x[p], y = s.y[p], psi = s.psi[p];
   const T ux = s.ux[p], uy = s.uy[p], w = s.w[p];
-  const T opp = T(1.0 + psi);
+  // the forward trial pass's own arithmetic: FP32 from the cached cell coordinates and 1 + Psi
+  // (FP32 mode), FP64 positions otherwise
+  int jx = 0, jy = 0;
+  T fxr = T(0), fyr = T(0);
+  double x = 0.0, y = 0.0, psi = 0.0;
+  T opp;
   Stencil<P, T> st;
-  stencil_at<P, T>(gm, x, y, st);
+  if constexpr (sizeof(T) == 4) {
+    const int cell = s.cell[p];
+    jx = cell & 0xFFFF;
+    jy = cell >> 16;
+    fxr = s.fx[p];
+    fyr = s.fy[p];
+    stencil_split<P>(gm, jx, fxr, jy, fyr, st);
+    opp = s.opp[p];
+  } else {
+    x = s.x[p];
+    y = s.y[p];
+    psi = s.psi[p];
+    stencil_at<P, T>(gm, x, y, st);
+    opp = T(1.0 + psi);
+  }
   T F[6], Fx[6], Fy[6];
   {
     T v4[4], g4x[4], g4y[4];
@@ -389,17 +428,35 @@ __global__ void __launch_bounds__(kThreads)
       comb[c] = acc;
     }
   }
-  const double dz = gm.dzeta;
-  const T mdz = -gsel<T>(dz, gm.f_dz);   // -dzeta in the field type (no FP64 product per use)
-  const double tx = x - dz * (double)comb[0], ty = y - dz * (double)comb[1];
-  const double tpsi = psi - dz * (double)comb[4];
+  const T mdz = -gsel<T>(gm.dzeta, gm.f_dz);   // -dzeta in the field type
   const T tux = ux + mdz * comb[2], tuy = uy + mdz * comb[3];
-  if (!ok_state(gm, tx, ty, 1.0 + tpsi, guard)) return;  // skipped by the trial deposit
+  T topp;
   Stencil<P, T> sn;
-  stencil_at<P, T>(gm, tx, ty, sn);
+  if constexpr (sizeof(T) == 4) {
+    // trial step in cell-relative coordinates, as the forward FP32 trial pass takes it
+    float ux_ = fxr - gm.f_dz_inv_dx * comb[0];
+    float uy_ = fyr - gm.f_dz_inv_dy * comb[1];
+    const float flx = floorf(ux_), fly = floorf(uy_);
+    const int tjx = jx + (int)flx, tjy = jy + (int)fly;
+    ux_ -= flx;
+    uy_ -= fly;
+    topp = opp + mdz * comb[4];
+    const float ax = (float)tjx + ux_, ay = (float)tjy + uy_;
+    const bool ok = isfinite(ax) && isfinite(ay) && isfinite(topp) && ax > 0.0f && ax < (float)gm.nx && ay > 0.0f &&
+                    ay < (float)gm.ny && topp >= gm.f_guard;
+    if (!ok) return;  // skipped by the trial deposit
+    stencil_split<P>(gm, tjx, ux_, tjy, uy_, sn);
+  } else {
+    const double dz = gm.dzeta;
+    const double tx = x - dz * (double)comb[0], ty = y - dz * (double)comb[1];
+    const double tpsi = psi - dz * (double)comb[4];
+    if (!ok_state(gm, tx, ty, 1.0 + tpsi, guard)) return;  // skipped by the trial deposit
+    topp = T(1.0 + tpsi);
+    stencil_at<P, T>(gm, tx, ty, sn);
+  }
   T Jg[2], Jgx[2], Jgy[2];
   gather_g<P, T, 2>(reinterpret_cast<const T*>(jbar), 2, 0, gm, sn, Jg, Jgx, Jgy);
-  const T tg = T(1) / T(1.0 + tpsi);
+  const T tg = T(1) / topp;
   const T qw1 = unit_charge_density<T>(gm), qw = qw1 * w;
   const T v0 = qw * tux * tg, v1 = qw * tuy * tg;
   T stb[5];
