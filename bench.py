@@ -190,7 +190,7 @@ def run_reference(args):
 # DRAM bytes per launch (ncu, caches flushed before each launch) on the 512^2 workload: the
 # solves as the sweep mixes them (5 two-RHS 32-wide-tile launches to 1 three-RHS one per
 # slice: 4.246 MB and 5.325 MB), the trial and final passes of one slice
-NCU_TRAFFIC = {"dst": (5 * 4.246016e6 + 5.324544e6) / 6, "trial": 23.322368e6, "final": 48.637184e6}
+NCU_TRAFFIC = {"dst": (5 * 4.246016e6 + 5.324544e6) / 6, "trial": 23.322112e6, "final": 48.652032e6}
 
 
 def dst_flops_per_sweep(g: dict) -> float:

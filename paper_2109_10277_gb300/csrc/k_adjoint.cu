@@ -19,7 +19,7 @@ namespace hq {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;   // as the forward particle kernels: a shorter tail of partly filled waves
 
 // B-spline weights and their derivatives d w / d u (u = node coordinate).
 template <int P, typename T>
