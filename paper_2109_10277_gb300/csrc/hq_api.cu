@@ -66,6 +66,11 @@ void free_all(hq_grid_s* g) {
   graph_free(g);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   g->cap_stream = nullptr;
+  if (g->aux_stream) cudaStreamDestroy(g->aux_stream);
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
+  g->aux_stream = nullptr;
+  g->ev_fork = g->ev_join = nullptr;
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   g->ev_pool.clear();
   F(g->d_profile); F(g->d_status); F(g->d_removed); F(g->d_scratch_int); F(g->d_gbar);
@@ -585,15 +590,58 @@ void set_global_error(const std::string& msg) { g_global_err = msg; }
 }  // namespace hq
 
 // The slice loop of one sweep (Sec. 2), issued on the grid's stream.
+// The second stream of sweep_body's fork (false: the sweep runs on the grid's stream alone).
+bool aux_ready(hq_grid_t g) {
+  if (g->aux_stream) return true;
+  const char* nf = std::getenv("HQ_NO_FORK");
+  if (nf && nf[0] == '1') return false;
+  if (cudaStreamCreateWithFlags(&g->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (g->aux_stream) cudaStreamDestroy(g->aux_stream);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
+    g->aux_stream = nullptr;
+    g->ev_fork = g->ev_join = nullptr;
+    return false;
+  }
+  return true;
+}
+
 hq_status sweep_body(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, double dt, const hq_field_out* out,
                      int32_t witness_beam, double* witness_sums) {
   hq_status st;
+  // Without a beam push, the witness sum of slice i-1 and the beam deposit of slice i do not
+  // depend on slice i's final pass (disjoint buffers, or commutative atomics into the same
+  // records), so from slice 1 on they run on a second stream beside it, forked and joined with
+  // events (a graph capture records the fork as parallel branches).  Slice 0 stays in order
+  // (the beams are binned and the records reset there).
+  const bool fork = dt == 0.0 && !g->prof_on && aux_ready(g);
+  const bool wit = witness_beam >= 0;
   for (int i = 0; i < g->nz; ++i) {
-    if ((st = hq_advance_slice(g, i)) != HQ_OK) return st;
-    if ((st = hq_beam_deposit(g, beams, nbeams, i)) != HQ_OK) return st;
+    if (fork && i > 0) {
+      cudaStream_t s = g->stream;
+      cudaEventRecord(g->ev_fork, s);
+      if ((st = hq_advance_slice(g, i)) != HQ_OK) return st;
+      cudaStreamWaitEvent(g->aux_stream, g->ev_fork, 0);
+      g->stream = g->aux_stream;
+      st = wit ? hq_witness_accumulate(g, &beams[witness_beam], i - 1, witness_sums) : HQ_OK;
+      if (st == HQ_OK) st = hq_beam_deposit(g, beams, nbeams, i);
+      cudaEventRecord(g->ev_join, g->aux_stream);
+      g->stream = s;
+      cudaStreamWaitEvent(s, g->ev_join, 0);
+      if (st != HQ_OK) return st;
+    } else {
+      if ((st = hq_advance_slice(g, i)) != HQ_OK) return st;
+      if ((st = hq_beam_deposit(g, beams, nbeams, i)) != HQ_OK) return st;
+    }
     if ((st = hq_solve_fields(g, i)) != HQ_OK) return st;
     if (out && (st = hq_store_fields(g, out, i)) != HQ_OK) return st;
-    if (witness_beam >= 0 && (st = hq_witness_accumulate(g, &beams[witness_beam], i, witness_sums)) != HQ_OK) return st;
+    // forked sweeps sum slice i's witness beside the next slice's final pass
+    if (wit && !(fork && i + 1 < g->nz) &&
+        (st = hq_witness_accumulate(g, &beams[witness_beam], i, witness_sums)) != HQ_OK)
+      return st;
     if (dt != 0.0 && (st = hq_push_beams(g, beams, nbeams, i, dt)) != HQ_OK) return st;
   }
   // advance once past the tail so the plasma state matches a completed sweep

@@ -177,6 +177,10 @@ struct hq_grid_s {
   void* sweep_graph;
   int graph_off;       // capture failed or was refused: plain stream launches from now on
   cudaStream_t cap_stream;   // private stream the sweep is captured on (the graph runs on `stream`)
+  // second stream (and fork / join events) for the per-slice launches that can run beside the
+  // final pass; created on first use
+  cudaStream_t aux_stream;
+  cudaEvent_t ev_fork, ev_join;
 
   // profiling: launch counters (always) and optional CUDA event pairs per launch group
   int64_t launches[HQ_K_CLASSES];
