@@ -206,6 +206,37 @@ def test_beam_push_and_witness_fp64(hq):
         assert abs(float(s[j]) - r) <= max(1e-12 * abs(r), 30 * abs(rp - r)), j
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_witness_sums_without_push(hq, monkeypatch, precision):
+    """Without a beam push the sweep sums slice i-1's witness on a second stream beside slice
+    i's final pass (and deposits slice i's beam there).  The witness sums equal the oracle's
+    (FP64: within the reordering floor; FP32: 1e-4) and the per-step order's (HQ_NO_FORK=1)."""
+    g = I.scaled_grid(I.grid_params("adjoint256"), 128, 128, 48)
+    beams = I.workload_beams("adjoint256", grid=g)
+    sp = O.GridSpec(**g)
+    ref = O.sweep(sp, [O.as_beam(b) for b in beams], witness=(1,), record=("ez",))
+    ref_perm = O.sweep(sp, [O.as_beam(b) for b in reordered(beams)], witness=(1,), record=("ez",),
+                       plasma_perm=plasma_perm(g), reverse_ion_order=True, deposit_noise=2.0 ** -52)
+    res = {}
+    for mode in ("fork", "steps"):
+        if mode == "steps":
+            monkeypatch.setenv("HQ_NO_FORK", "1")
+        out, _, _, _, sums = run_gpu(hq, g, beams, precision, fields=("ez",), witness=1)
+        res[mode] = (out, sums.cpu())
+        monkeypatch.delenv("HQ_NO_FORK", raising=False)
+    s0, s2 = float(ref.witness[1][0]), float(ref.witness[1][2])
+    scale = [abs(s0), math.sqrt(abs(s0 * s2)), abs(s2)]   # |sum qw Ez| <= sqrt(S0 S2)
+    for mode, (out, s) in res.items():
+        if precision == "fp64":
+            assert_fp64_sweep(out, ref, ref_perm, ("ez",))
+        for j in range(3):
+            r, rp = float(ref.witness[1][j]), float(ref_perm.witness[1][j])
+            bar = max(1e-12 * abs(r), 30 * abs(rp - r)) if precision == "fp64" else 1e-4 * scale[j]
+            print(f"{precision} witness sum {j} ({mode}): {float(s[j]):.12e} vs oracle {r:.12e}")
+            assert abs(float(s[j]) - r) <= bar, (mode, j, float(s[j]), r)
+    assert float(res["fork"][1].abs().sum()) > 0
+
+
 def test_beam_binning_is_exact(hq):
     """Integer work: per-slice particle counts of the device counting sort equal the oracle's
     (read through the witness charge sum, with a power-of-two weight so every sum is exact)."""
