@@ -592,9 +592,9 @@ void set_global_error(const std::string& msg) { g_global_err = msg; }
 // The slice loop of one sweep (Sec. 2), issued on the grid's stream.
 // The second stream of sweep_body's fork (false: the sweep runs on the grid's stream alone).
 bool aux_ready(hq_grid_t g) {
-  if (g->aux_stream) return true;
   const char* nf = std::getenv("HQ_NO_FORK");
   if (nf && nf[0] == '1') return false;
+  if (g->aux_stream) return true;
   if (cudaStreamCreateWithFlags(&g->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess) {

@@ -15,7 +15,8 @@
 // The epilogue of each product re-splits its FP32 result for the next one and
 // fuses the 1/lambda scaling (second product) or the final FP32 store (fourth).
 //
-// Kernel structure (one 128 x 128 output tile per CTA, 4 warps):
+// Per-product kernel (k_dst_gemm, one product per launch; the allocation-free entry point
+// at the end of this file runs it), one 128 x 128 output tile per CTA, 4 warps:
 //   warp 0 lane 0  TMA producer: 128B-swizzled 128x64 bf16 boxes of A_hi, A_lo,
 //                  S_hi, S_lo per stage (64 KB), 3-stage mbarrier ring;
 //   warp 1 lane 0  MMA issuer: 12 tcgen05.mma (M=128, N=128, K=16) per stage,
@@ -354,6 +355,12 @@ __global__ void __launch_bounds__(128, 1)
 // an N-tile of odd (even) slots contracts over the sums (differences) only, K = n/2,
 // against the fold matrix.  Rows 2u, 2u+1 of a tile are a pair, i.e. adjacent TMEM
 // lanes, so the epilogue folds the next operand with one warp shuffle.
+//
+// Tiles are 128 x BN (BN = 32 when every tile still gets its own CTA, else 64), one CTA
+// of 256 threads per SM: warp 0 lane 0 issues the TMA loads (A_hi, A_lo, B_hi, B_lo of a
+// 64-wide K block per stage, 4-stage ring), warp 1 lane 0 the MMAs (two per K step:
+// A_hi x [B_hi; B_lo] with N = 2 BN, A_lo x B_hi with N = BN, into a 2 BN-column TMEM
+// accumulator), and all 8 warps the epilogue, each warpgroup half of the columns.
 struct SolveArgs {
   int R;                               // right-hand sides
   int nxp, nyp;                        // operand extents (= nx, ny when folded)
