@@ -24,9 +24,10 @@
  * values are double for HQ_PREC_FP64 grids and float for HQ_PREC_FP32_BF16X3.
  * Beam arrays are always double.
  *
- * Run-time switches (environment variables, read when a grid is created or, for
- * HQ_NO_GRAPH and HQ_NO_FORK, when a sweep is issued); each turns an optimization off
- * and leaves the results unchanged up to summation order:
+ * Run-time switches (environment variables, read when a grid is created; HQ_NO_GRAPH
+ * at every hq_sweep_step, HQ_NO_FORK whenever a sweep is issued or captured, not when a
+ * captured one is replayed); each turns an optimization off and leaves the results
+ * unchanged up to summation order:
  *   HQ_NO_FOLD=1   FP32 DST-I without the folded (half-K) products
  *   HQ_SOLVE_BN=64 FP32 solves always on 128 x 64 tiles (no 128 x 32 tiles)
  *   HQ_NO_PDL=1    no programmatic dependent launch between the per-slice kernels
