@@ -38,7 +38,7 @@ WORKLOAD_DESC = ("512x512 grid on +-8 k_p^-1 x 1024 slices over zeta in [-13, 7]
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-# algorithmic bytes per particle of the FP32 particle passes (reads + writes)
+# algorithmic bytes per particle of the FP32 particle passes (particle streams read + written)
 BYTES_TRIAL = 49    # ux, uy, w (12) + AB5 history sum (20) + cell/frac/1+Psi cache (16) + alive (1)
 BYTES_FINAL = 221   # reads: x, y, Psi (24), ux, uy, w (12), AB5 history 4x5x4 (80), cache (16), alive (1);
                     # writes: x, y, Psi (24), ux, uy (8), f_i (20), history sum (20), cache (16)

@@ -165,8 +165,8 @@ hq_status hq_witness_accumulate(hq_grid_t grid, const hq_beam_view* beam, int32_
 hq_status hq_sweep_step(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, double dt,
                         const hq_field_out* out, int32_t witness_beam, double* witness_sums);
 
-/* Forward sweep for differentiation (the benchmark spec adjoint requirement; the paper has
- * no adjoint): the same sweep as hq_sweep_step with dt = 0 and no field output, but
+/* Forward sweep for differentiation (gradients are a goal the paper names, Sec. 1, with
+ * no adjoint formulation): the same sweep as hq_sweep_step with dt = 0 and no field output, but
  * it stores a checkpoint (plasma slice with its AB5 history and the field records a
  * slice starts from) every ckpt_every slices, and the per-slice tapes of the last
  * segment.  witness_sums (DEVICE double[3], zeroed by the caller) receives

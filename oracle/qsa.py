@@ -53,8 +53,8 @@ def working_precision(dtype: torch.dtype):
 
     The method is FP64 (the default).  ``working_precision(torch.float32)`` runs the
     same steps with every tensor in single precision: a test knob that measures the
-    single-precision rounding floor of the algorithm, against which a mixed-precision
-    implementation is judged.  Not re-entrant across threads."""
+    single-precision rounding floor of the algorithm, the reference point for a
+    mixed-precision implementation's error.  Not re-entrant across threads."""
     global DT
     old = DT
     DT = dtype

@@ -2,8 +2,8 @@
 against the oracle's taped FP64 adjoint (autograd through the oracle sweep, itself
 pinned to central finite differences in test_oracle_adjoint.py).
 
-Bars: gradients within 1e-5 (FP64 path) and 1e-3 (FP32/bf16x3 path) relative
-(the benchmark spec), checked as the relative L2 error of each gradient vector and of
+Bars: gradients within 1e-5 (FP64 path) and 1e-3 (FP32/bf16x3 path) relative,
+checked as the relative L2 error of each gradient vector and of
 directional derivatives along random directions.  Both single-segment (no
 recompute) and multi-segment (checkpoint restore + recompute) runs are covered.
 """

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Bars (derived in the design doc):
+Bars:
   * Poisson solves, FP64: rel-L2 <= 1e-12 (a single linear operation).
   * Whole sweeps, FP64: the quasi-static sweep amplifies last-bit rounding
     differences, and the GPU's deposits are unordered atomic sums (the GPU run
