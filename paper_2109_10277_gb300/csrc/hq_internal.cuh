@@ -155,7 +155,6 @@ struct hq_grid_s {
   int fold;                                  // folded DST-I (nx, ny multiples of 128; FP32 mode)
   float* psrc[2];                            // FP32 mode: psi source rho - J_z of dep[0], dep[1]
   unsigned long long* d_gbar;                // grid-barrier counter of the fused solve kernel (zero between launches)
-  int solve_ctas;                            // CTAs of the fused solve (co-resident)
 
   // beams
   hq::BeamBins bins[hq::kMaxBeams];

@@ -426,10 +426,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
   return !*abort_f;
 }
 
-// N-tile widths of the fused solve: 64, or 32 when that still gives every tile its own CTA
-// (twice the tiles, so more of the SMs take part in each product).
-template <int BN> constexpr int bn_index() { return BN == 64 ? 0 : 1; }
-constexpr int kSolveThreads = 256;   // warps 0, 1: TMA producer, MMA issuer; all 8: epilogue
+// The fused solve runs 256 threads per CTA (warps 0, 1: TMA producer, MMA issuer; all 8
+// warps: epilogue) on N tiles 64 wide, or 32 wide when that still gives every tile its own
+// CTA (twice the tiles, so more of the SMs take part in each product).
+constexpr int kSolveThreads = 256;
 
 // Optional per-CTA timestamps of the solve's steps (a profiling build defines it).
 #ifndef HQ_SOLVE_TRACE_POINT
@@ -437,7 +437,7 @@ constexpr int kSolveThreads = 256;   // warps 0, 1: TMA producer, MMA issuer; al
 #endif
 
 // Shared memory of the solve: the stage ring, the FP32 scale tile of phase 1
-// ([64 n][128 rows]), then the barriers (full, empty, done, scale) and the TMEM slot.
+// ([BN n][128 rows]), then the barriers (full, empty, done, scale) and the TMEM slot.
 template <int BN> struct SolveSmem {
   static constexpr int STAGES = Cfg<BN>::STAGES;
   static constexpr int RING = STAGES * Cfg<BN>::STAGE_BYTES;
@@ -763,7 +763,6 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
   if (!size_solve(k_dst_solve<64>, SolveSmem<64>::BYTES, t.ctas[0]) ||
       !size_solve(k_dst_solve<32>, SolveSmem<32>::BYTES, t.ctas[1]))
     return 1;
-  g->solve_ctas = t.ctas[0];
   const char* bn = std::getenv("HQ_SOLVE_BN");
   t.wide_only = bn != nullptr && std::atoi(bn) == 64;
   const uint64_t nxp = g->nxp, nyp = g->nyp;
