@@ -184,12 +184,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the current build (cold L2):
-# k_dst_solve on 512^2 with 3 rhs (the operands read once) and k_final_pass on the 512^2
-# plasma slice; the capture commands are recorded with their summaries under profiles/.
 # DRAM bytes per launch (ncu, caches flushed before each launch) on the 512^2 workload: the
 # solves as the sweep mixes them (5 two-RHS 32-wide-tile launches to 1 three-RHS one per
-# slice: 4.246 MB and 5.325 MB), the trial and final passes of one slice
+# slice: 4.246 MB and 5.325 MB), the trial and final passes of one slice; the capture
+# commands are recorded with their summaries under profiles/
 NCU_TRAFFIC = {"dst": (5 * 4.246016e6 + 5.324544e6) / 6, "trial": 23.322112e6, "final": 48.652032e6}
 
 
