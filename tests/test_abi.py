@@ -65,3 +65,16 @@ def test_no_device_fails_loudly(lib):
     assert not h.value
     with pytest.raises(RuntimeError):  # HQError or torch refusing the stream
         hq.Grid(dict(nx=64, ny=64, nzeta=8, xmin=-1, xmax=1, ymin=-1, ymax=1, zeta_min=0, zeta_max=1))
+
+
+def test_every_runtime_switch_is_documented():
+    """Each HQ_* environment variable the library reads is listed in include/hq.h."""
+    csrc = os.path.join(ROOT, "paper_2109_10277_gb300", "csrc")
+    read = set()
+    for f in os.listdir(csrc):
+        if f.endswith((".cu", ".cuh")):
+            read |= set(re.findall(r'getenv\("(HQ_\w+)"\)', open(os.path.join(csrc, f)).read()))
+    header = open(os.path.join(ROOT, "include", "hq.h")).read()
+    assert read, "no switches found"
+    for name in sorted(read):
+        assert re.search(rf"^\s*\*\s+{name}=", header, re.M), name
