@@ -2,7 +2,7 @@
  * hq.h -- C ABI of a GB300 (sm_103a) implementation of the quasi-static PIC
  * per-slice loop of arXiv:2109.10277 (HiPACE++), Sec. 2 and Sec. 3.
  *
- * Units are the paper's normalized units (Sec. 5, "normalized units"): lengths
+ * Units are the paper's normalized units (Sec. 6, "normalized units"): lengths
  * in 1/k_p, fields in E0 = m c omega_p / e, densities in n0, c = eps0 = mu0 = 1.
  * Plasma electrons have charge -1 and mass 1; ions are immobile.
  *
@@ -217,8 +217,14 @@ hq_status hq_poisson_solve(hq_grid_t grid, const void* src, void* dst, int32_t n
  * rebuilds the sine and 1/lambda tables inside the array.  Every call shares the
  * one array, which keeps the last call's contents: calls whose work overlaps on
  * the GPU (several streams, several host threads) race, so the caller must
- * serialize them.  Errors: HQ_ERR_ARG, HQ_ERR_CUDA, HQ_ERR_UNSUPPORTED (not an
- * sm_103a device); the message is read with hq_last_error(NULL). */
+ * serialize them.  A call made while its stream is being captured always enqueues
+ * the table build, and the next call rebuilds the tables again.  cuda_stream must
+ * belong to the current device.  The call is asynchronous: a bounded device wait
+ * that ran out (incomplete result) or a non-finite result is flagged in a status
+ * word at the start of the array, which stays set until hq_sync(NULL, ...) reports
+ * and clears it.  Errors returned directly: HQ_ERR_ARG, HQ_ERR_CUDA,
+ * HQ_ERR_UNSUPPORTED (not an sm_103a device); the message is read with
+ * hq_last_error(NULL). */
 hq_status hq_poisson_solve_static(const float* src, float* dst, int32_t nx, int32_t ny, double dx, double dy,
                                   int32_t nrhs, void* cuda_stream);
 
@@ -250,7 +256,13 @@ hq_status hq_profile_read(hq_grid_t grid, hq_profile_t* out);
 
 /* Waits for the grid's stream, then reports device status: HQ_ERR_TIMEOUT or
  * HQ_ERR_NUMERIC if a kernel flagged one (the flag is cleared), else HQ_OK.
- * removed (may be NULL) receives the number of plasma particles removed so far. */
+ * removed (may be NULL) receives the number of plasma particles removed so far.
+ * grid == NULL: waits for all work on the current device (cudaDeviceSynchronize) and
+ * reports the status of the hq_poisson_solve_static calls made on it since the last
+ * such query: HQ_ERR_TIMEOUT if a bounded wait inside one ran out (its result is
+ * then incomplete), HQ_ERR_NUMERIC if one produced a non-finite value, else HQ_OK;
+ * the flag is cleared and *removed (if given) is set to 0.  Allocates nothing.
+ * HQ_ERR_CUDA if the device cannot be synchronized (e.g. there is none). */
 hq_status hq_sync(hq_grid_t grid, int64_t* removed);
 
 /* Message for the last non-OK status on this grid (or a global message when

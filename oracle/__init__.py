@@ -20,6 +20,12 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   sweep                pinned: zero-beam invariant, symmetry, Ez ~ -d(psi)/d(zeta),
                        conservation of sum(rho - Jz), discrete linear wake
   beam binning         pinned: brute-force bin membership
+  beam deposit         pinned: rho_b = q n_b at the nodes of an affine-density lattice beam (all
+                       orders), J_b = rho_b u / gamma, slice charge of a random beam, and the
+                       linear wake built from the driver's closed-form density
+  predictor-corrector  pinned at the workloads' setting (5 iterations, mixing 0.05): linear wake
+                       within 5 % converging under dzeta and dx refinement; lag behind a converged
+                       iteration second order in dzeta
   beam push            pinned: uniform-B gyration, uniform-E energy gain, time reversibility
   blowout-regime physics (cfg 512^2 n_b=5): parity unpinned beyond the checks above
   working_precision    a test knob: the same steps in another float type (rounding floors)

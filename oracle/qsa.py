@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring): the product path never
 imports this module.
 
-Units are the paper's normalized units (Sec. 5): lengths in 1/k_p, fields in
+Units are the paper's normalized units (Sec. 6): lengths in 1/k_p, fields in
 E0 = m c omega_p / e, densities in n0, c = eps0 = mu0 = 1.  Plasma electrons have
 q = -1, M = 1; ions are immobile.
 

@@ -587,6 +587,7 @@ bool pdl_enabled() {
 
 // Error message for calls that have no grid (read back by hq_last_error(NULL)).
 void set_global_error(const std::string& msg) { g_global_err = msg; }
+hq_status static_sync();   // status of the allocation-free solves (k_dst_tc.cu)
 }  // namespace hq
 
 // The slice loop of one sweep (Sec. 2), issued on the grid's stream.
@@ -1163,7 +1164,10 @@ hq_status hq_plasma_state(hq_grid_t g, hq_plasma_view* out) {
 }
 
 hq_status hq_sync(hq_grid_t g, int64_t* removed) {
-  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (!g) {
+    if (removed) *removed = 0;
+    return static_sync();
+  }
   HQ_CUDA(g, cudaStreamSynchronize(g->stream));
   int status = 0;
   unsigned long long rm = 0;

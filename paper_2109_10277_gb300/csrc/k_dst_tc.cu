@@ -284,11 +284,15 @@ __global__ void __launch_bounds__(128, 1)
     tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
     if (ep.mode == 2) {
       if (ml < ep.m_real) {
+        bool bad = false;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + c0 + j;
-          if (n < ep.n_real) ep.out_f32[((int64_t)r * ep.n_real + n) * ep.m_real + ml] = __uint_as_float(v[j]);
+          const float x = __uint_as_float(v[j]);
+          bad |= !isfinite(x);
+          if (n < ep.n_real) ep.out_f32[((int64_t)r * ep.n_real + n) * ep.m_real + ml] = x;
         }
+        if (bad) atomicOr(status, DEV_NONFINITE);
       }
     } else if (ep.mode == 3) {
       if (ml < ep.m_real) {
@@ -870,9 +874,10 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 struct StaticDev {
   uint8_t* base = nullptr;   // device address of g_static_scratch on this device
-  int nx = 0, ny = 0;
+  int nx = 0, ny = 0;        // geometry the tables in the array hold (nx = 0: unknown, rebuild)
   double dx = 0.0, dy = 0.0;
-  TensorMaps maps;
+  TensorMaps maps;           // encoded for (map_nx, map_ny)
+  int map_nx = 0, map_ny = 0;
 };
 std::mutex g_static_mu;
 std::map<int, StaticDev> g_static_dev;
@@ -954,8 +959,17 @@ extern "C" hq_status hq_poisson_solve_static(const float* src, float* dst, int32
   if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
     return static_fail(HQ_ERR_ARG, "hq_poisson_solve_static: dx and dy must be finite and positive");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-  int dev = 0;
+  int dev = 0, sdev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return static_fail(HQ_ERR_CUDA, "hq_poisson_solve_static: no CUDA device");
+  if (cudaStreamGetDevice(s, &sdev) != cudaSuccess)
+    return static_fail(HQ_ERR_ARG, "hq_poisson_solve_static: cuda_stream is not a valid stream");
+  if (sdev != dev)
+    return static_fail(HQ_ERR_ARG, "hq_poisson_solve_static: cuda_stream belongs to device " + std::to_string(sdev) +
+                                        ", not the current device " + std::to_string(dev));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess)
+    return static_fail(HQ_ERR_CUDA, "hq_poisson_solve_static: cannot query the stream's capture state");
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
   std::lock_guard<std::mutex> lock(g_static_mu);
   StaticDev& sd = g_static_dev[dev];
   std::string err;
@@ -989,9 +1003,9 @@ extern "C" hq_status hq_poisson_solve_static(const float* src, float* dst, int32
   __nv_bfloat16* syl = reinterpret_cast<__nv_bfloat16*>(sb + 3 * kStaticSBytes);
   float* scale = reinterpret_cast<float*>(sb + 4 * kStaticSBytes);
   const int nxp = (nx + 127) / 128 * 128, nyp = (ny + 127) / 128 * 128;
-  if (sd.nx != nx || sd.ny != ny || sd.dx != dx || sd.dy != dy) {
-    // new geometry: rebuild the sine matrices and 1/lambda table in the static array and
-    // re-encode the tensor maps over the new padded extents (host-side, no allocation)
+  if (sd.map_nx != nx || sd.map_ny != ny) {
+    // new extents: re-encode the tensor maps over the new padded extents (host-side, no
+    // allocation)
     EncodeFn enc = static_encoder(err);
     if (!enc) return static_fail(HQ_ERR_CUDA, err);
     TensorMaps& t = sd.maps;
@@ -1008,18 +1022,33 @@ extern "C" hq_status hq_poisson_solve_static(const float* src, float* dst, int32
       bad |= make_map(enc, &t.sy_lo[i], syl, nyp, nyp, err, rows);
     }
     if (bad) {
+      sd.map_nx = sd.map_ny = 0;
       sd.nx = sd.ny = 0;
       return static_fail(HQ_ERR_CUDA, err);
     }
+    sd.map_nx = nx;
+    sd.map_ny = ny;
+  }
+  // The sine matrices and the 1/lambda table in the array are rebuilt for a new (nx, ny, dx,
+  // dy), and by every call made while the stream is being captured: what such a call enqueues
+  // runs later, so the array's contents can no longer be tracked here and the next call
+  // rebuilds them too.
+  if (capturing || sd.nx != nx || sd.ny != ny || sd.dx != dx || sd.dy != dy) {
+    sd.nx = sd.ny = 0;
     k_static_tables<<<256, 256, 0, s>>>(sxh, sxl, syh, syl, scale, nx, ny, nxp, nyp, dx, dy);
-    sd.nx = nx;
-    sd.ny = ny;
-    sd.dx = dx;
-    sd.dy = dy;
+    const cudaError_t te = cudaGetLastError();
+    if (te != cudaSuccess)
+      return static_fail(HQ_ERR_CUDA, std::string("hq_poisson_solve_static: table build: ") + cudaGetErrorString(te));
+    if (!capturing) {
+      sd.nx = nx;
+      sd.ny = ny;
+      sd.dx = dx;
+      sd.dy = dy;
+    }
   }
   const TensorMaps& t = sd.maps;
-  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess)
-    return static_fail(HQ_ERR_CUDA, "hq_poisson_solve_static: status reset failed");
+  // the status word at the start of the array is not cleared here: a timeout or a non-finite
+  // result stays flagged until hq_sync(NULL, ...) reads and clears it
   k_static_src<<<256, 256, 0, s>>>(src, op_hi0, op_lo0, nrhs, nx, ny, nxp, nyp);
   Epi e{};
   e = Epi{0, nyp, nxp, op_hi1, op_lo1, nullptr, nullptr, 0, 0};
@@ -1034,3 +1063,32 @@ extern "C" hq_status hq_poisson_solve_static(const float* src, float* dst, int32
   if (le != cudaSuccess) return static_fail(HQ_ERR_CUDA, std::string("hq_poisson_solve_static: ") + cudaGetErrorString(le));
   return HQ_OK;
 }
+
+namespace hq {
+// Status of the allocation-free solves on the current device (hq_sync(NULL, ...)): waits for
+// the device, reads the status word at the start of the static array and clears it.  A device
+// on which no such solve was set up reports HQ_OK.
+hq_status static_sync() {
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    return static_fail(HQ_ERR_CUDA, std::string("hq_sync(NULL): ") + cudaGetErrorString(e));
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return static_fail(HQ_ERR_CUDA, "hq_sync(NULL): no CUDA device");
+  uint8_t* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    auto it = g_static_dev.find(dev);
+    if (it != g_static_dev.end()) base = it->second.base;
+  }
+  if (!base) return HQ_OK;
+  int status = 0;
+  if (cudaMemcpy(&status, base, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return static_fail(HQ_ERR_CUDA, "hq_sync(NULL): status read failed");
+  if (!status) return HQ_OK;
+  if (cudaMemset(base, 0, sizeof(int)) != cudaSuccess) return static_fail(HQ_ERR_CUDA, "hq_sync(NULL): status reset failed");
+  if (status & DEV_TIMEOUT)
+    return static_fail(HQ_ERR_TIMEOUT, "hq_poisson_solve_static: a bounded device wait ran out");
+  return static_fail(HQ_ERR_NUMERIC, "hq_poisson_solve_static: a non-finite value reached the solution");
+}
+}  // namespace hq
