@@ -128,8 +128,43 @@ def laplace_eigs(spec: GridSpec) -> torch.Tensor:
     return ey[:, None] + ex[None, :]
 
 
+DST_ALGORITHM = "matrix"
+
+
+@contextlib.contextmanager
+def dst_algorithm(name: str):
+    """Choose how dst2 evaluates the DST-I inside the block: "matrix" (the default, the
+    transform's definition as a product with S) or "fft" (the same sums in O(n log n) per
+    row, through the FFT of the odd extension).  The two differ only in rounding order:
+    the FFT form serves the timed CPU baseline and measures how much the sweep amplifies
+    the DST's own rounding.  Not re-entrant across threads."""
+    global DST_ALGORITHM
+    old = DST_ALGORITHM
+    if name not in ("matrix", "fft"):
+        raise ValueError(name)
+    DST_ALGORITHM = name
+    try:
+        yield
+    finally:
+        DST_ALGORITHM = old
+
+
+def dst1_rows_fft(a: torch.Tensor) -> torch.Tensor:
+    """b_k = sum_{j=1}^{n-1} a_j sin(pi j k / n) along the last axis (node 0 on the wall).
+
+    The odd extension e = (a_0 .. a_{n-1}, 0, -a_{n-1} .. -a_1) of length 2n has the discrete
+    Fourier transform sum_j a_j (e^{-i pi j k/n} - e^{i pi j k/n}) = -2i sum_j a_j sin(pi j k/n)
+    (a_0 only adds a real constant), so b_k = -Im(E_k) / 2."""
+    n = a.shape[-1]
+    ext = torch.cat([a, torch.zeros_like(a[..., :1]), -a[..., 1:].flip(-1)], dim=-1)
+    return -0.5 * torch.fft.rfft(ext, dim=-1)[..., :n].imag
+
+
 def dst2(spec: GridSpec, a: torch.Tensor) -> torch.Tensor:
     """Unnormalised 2D DST-I of the interior: S_y a S_x."""
+    if DST_ALGORITHM == "fft":
+        t = dst1_rows_fft(a)                                        # a S_x: along x
+        return dst1_rows_fft(t.transpose(-1, -2)).transpose(-1, -2)  # S_y (.): along y
     return dst_matrix(spec.ny) @ a @ dst_matrix(spec.nx)
 
 
@@ -450,7 +485,8 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
           witness: Sequence[int] = (), record_plasma_at: Sequence[int] = (),
           n0_scale: Optional[torch.Tensor] = None, radial_profile: Optional[torch.Tensor] = None,
           plasma_perm: Optional[torch.Tensor] = None, reverse_ion_order: bool = False,
-          deposit_noise: float = 0.0, noise_seed: int = 0) -> SweepResult:
+          deposit_noise: float = 0.0, noise_seed: int = 0,
+          crop: Optional[Sequence[int]] = None) -> SweepResult:
     """One quasi-static sweep head -> tail (Sec. 2), slices i = 0 .. n_slices-1.
 
     Per slice (Sec. 2 steps 1-7 and the Sec. 3.2 predictor-corrector):
@@ -464,6 +500,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     deposit_noise > 0 multiplies every plasma (and ion) deposit node value by
     (1 + deposit_noise * U(-1, 1)): a rounding-size perturbation, like the one an
     unordered (atomic) summation leaves, used to measure the sweep's sensitivity.
+    crop = (y0, y1, x0, x1) records only the nodes [y0:y1, x0:x1] of each field (memory).
     """
     ns = spec.nzeta if n_slices is None else n_slices
     dz = spec.dzeta
@@ -538,7 +575,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
         out = dict(rho=rho, jx=jx, jy=jy, jz=jz, chi=chi, psi=psi, exmby=exmby, eypbx=eypbx,
                    ez=ez, bx=bx, by=by, bz=bz)
         for k in record:
-            rec[k].append(out[k])
+            rec[k].append(out[k] if crop is None else out[k][crop[0]:crop[1], crop[2]:crop[3]].clone())
         for bi in witness:
             sel = sel_of(bi, i)
             (ezw,) = gather(spec, beams[bi]["x"][sel], beams[bi]["y"][sel], (ez,), spec.shape_order)

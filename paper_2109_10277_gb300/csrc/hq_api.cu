@@ -868,6 +868,8 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     // folded DST-I (half the contraction) when both extents are multiples of 128
     const char* nf = std::getenv("HQ_NO_FOLD");
     g->fold = (g->nx % 128 == 0 && g->ny % 128 == 0 && !(nf && nf[0] == '1')) ? 1 : 0;
+    const char* fb = std::getenv("HQ_FAULT_BARRIER");
+    g->fault_barrier = (fb && fb[0] == '1') ? 1 : 0;
     HQ_ALLOC(g->d_gbar, sizeof(unsigned long long));
     cudaMemset(g->d_gbar, 0, sizeof(unsigned long long));
     const size_t opn = (size_t)kMaxRhs * g->nxp * g->nyp;

@@ -155,6 +155,7 @@ struct hq_grid_s {
   int fold;                                  // folded DST-I (nx, ny multiples of 128; FP32 mode)
   float* psrc[2];                            // FP32 mode: psi source rho - J_z of dep[0], dep[1]
   unsigned long long* d_gbar;                // grid-barrier counter of the fused solve kernel (zero between launches)
+  int fault_barrier;                         // HQ_FAULT_BARRIER=1: the solve's first grid barrier never fills
 
   // beams
   hq::BeamBins bins[hq::kMaxBeams];

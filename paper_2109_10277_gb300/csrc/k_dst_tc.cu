@@ -379,6 +379,7 @@ struct SolveArgs {
   int last;
   unsigned long long* gbar;            // grid-barrier counter (zero at launch, reset by the last CTA)
   int* status;
+  int barrier_skew;                    // added to the first barrier's target (fault injection; 0)
 };
 
 // Bounded mbarrier wait that also gives up once another thread of the CTA has.
@@ -671,7 +672,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
       HQ_SOLVE_TRACE_POINT(p, 3);
       if (*abort_f) break;
     }
-    if (p < 3 && !grid_barrier(a.gbar, (unsigned long long)(p + 1) * gridDim.x, a.status, abort_f)) break;
+    if (p < 3 &&
+        !grid_barrier(a.gbar, (unsigned long long)(p + 1) * gridDim.x + (p == 0 ? (unsigned)a.barrier_skew : 0u),
+                      a.status, abort_f))
+      break;
     HQ_SOLVE_TRACE_POINT(p, 4);
   }
   // exit arrival: the last CTA through resets the counter for the next launch
@@ -820,6 +824,7 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s) 
   a.last = last;
   a.gbar = g->d_gbar;
   a.status = g->d_status;
+  a.barrier_skew = g->fault_barrier;
   // tiles of one product (the larger of the x and y products) at N-tile width bn
   auto tiles = [&](int bn) {
     return std::max(R * (g->nyp / BM) * (g->nxp / bn), R * (g->nxp / BM) * (g->nyp / bn));

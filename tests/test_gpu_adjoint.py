@@ -138,3 +138,82 @@ def test_sweep_loss_autograd_to_beam_parameters(hq):
     assert abs(float(L) - float(Lo)) <= 1e-10 * abs(float(Lo))
     for a, b, name in zip(got, ref, ("n_b", "sigma_r", "sigma_z", "zeta0", "n0")):
         assert abs(a - b) <= 1e-5 * abs(b), (name, a, b)
+
+
+# ---------------------------------------------------------------- folded DST-I path, workload P-C count
+
+@pytest.fixture(scope="module")
+def folded_case():
+    """128^2 x 48 slices (nx, ny multiples of 128: the FP32 solves run the folded DST-I),
+    quadratic shape, the workloads' 5 predictor-corrector iterations; the oracle's taped
+    FP64 gradients, computed once."""
+    g = dict(nx=128, ny=128, nzeta=48, xmin=-6.0, xmax=6.0, ymin=-6.0, ymax=6.0, zeta_min=-7.0, zeta_max=5.0,
+             shape_order=2, n_pc_iter=5, pc_mix=0.05, psi_guard=0.02,
+             radial_profile=[1.0, 1.0, 0.8, 0.5, 0.3], profile_rmax=8.5)
+    d = I.fixed_ppc_beam(g, 0.6, 1.0, 2.0)
+    w = I.fixed_ppc_beam(g, 0.4, 0.6, 10.0, zeta0=-3.0, gamma=I.GAMMA_WITNESS)
+    return g, d, w, oracle_grads(g, d, w, "mean+rms")
+
+
+@pytest.mark.parametrize("precision,tol,bn", [("fp64", 1e-5, None), ("fp32", 1e-3, None), ("fp32", 1e-3, "64")])
+def test_adjoint_folded_path(hq, monkeypatch, folded_case, precision, tol, bn):
+    """FP32: the folded solve on 128 x 32 tiles (default) and on 128 x 64 tiles (HQ_SOLVE_BN=64),
+    two checkpoint segments (recompute); FP64 the same case through its FFT DST."""
+    g, d, w, (L0, gd0, gw0, gn0, gp0) = folded_case
+    if bn:
+        monkeypatch.setenv("HQ_SOLVE_BN", bn)
+    L1, gd1, gw1, gn1, gp1 = gpu_grads(hq, g, d, w, "mean+rms", precision, 24)
+    errs = {"loss": abs(L1 - L0) / abs(L0), "driver_w": rel(gd1, gd0), "witness_w": rel(gw1, gw0),
+            "driver_dir": directional(gd1, gd0), "n0": abs(gn1 - gn0) / abs(gn0), "profile": rel(gp1, gp0)}
+    print("folded", precision, bn, {a: f"{b:.2e}" for a, b in errs.items()})
+    assert errs["loss"] <= (1e-10 if precision == "fp64" else 1e-3), errs
+    for key in ("driver_w", "witness_w", "driver_dir", "n0", "profile"):
+        assert errs[key] <= tol, (key, errs)
+
+
+# ---------------------------------------------------------------- gradient workload's named check
+
+def test_adjoint256_small_grid_gradients_vs_central_fd(hq):
+    """The gradient workload's check at 64 x 64 x 128 (its box: +-6, zeta in [-7, 5]; linear
+    shape, 1 ppc, 5 predictor-corrector iterations): the GPU adjoint's gradient of the mean
+    witness Ez with respect to the driver's peak density, sigma_r, sigma_z, the witness zeta
+    position and the plasma density scale n0, against central finite differences of the FP64
+    oracle with step 1e-6 max(1, |p|).  Bars 1e-5 (FP64) and 1e-3 (FP32/bf16x3), relative."""
+    g = I.scaled_grid(I.grid_params("adjoint256"), 64, 64, 128)
+    d = I.fixed_ppc_beam(g, 0.2, 1.0, 2.0)
+    w = I.fixed_ppc_beam(g, 0.1, 0.3, 20.0, zeta0=-5.0, gamma=I.GAMMA_WITNESS)
+    dx = (g["xmax"] - g["xmin"]) / g["nx"]
+    dz = (g["zeta_max"] - g["zeta_min"]) / g["nzeta"]
+
+    def weights(beam, nb, sr, sz, z0):
+        x, y, z = (torch.as_tensor(beam[k], dtype=torch.float64) for k in ("x", "y", "zeta"))
+        return nb * torch.exp(-(x * x + y * y) / (2 * sr * sr)) * torch.exp(-((z - z0) ** 2) / (2 * sz * sz)) * dx * dx * dz
+
+    p0 = {"n_b": 2.0, "sigma_r": 0.2, "sigma_z": 1.0, "zeta_w": -5.0, "n0": 1.0}
+
+    def oracle_loss(p):
+        sp = O.GridSpec(**dict(g, n0_scale=p["n0"]))
+        bd, bw = O.as_beam(d), O.as_beam(w)
+        bd["w"] = weights(d, p["n_b"], p["sigma_r"], p["sigma_z"], 0.0)
+        bw["w"] = weights(w, 20.0, 0.1, 0.3, p["zeta_w"])
+        r = O.sweep(sp, [bd, bw], witness=(1,), record=())
+        return float(O.witness_loss(r, 1, "mean"))
+
+    fd = {}
+    for k, v in p0.items():
+        h = 1e-6 * max(1.0, abs(v))
+        fd[k] = (oracle_loss(dict(p0, **{k: v + h})) - oracle_loss(dict(p0, **{k: v - h}))) / (2 * h)
+    for precision, tol in (("fp64", 1e-5), ("fp32", 1e-3)):
+        grid = hq.Grid(g, precision=precision)
+        beams = [hq.Beam(d), hq.Beam(w)]
+        ps = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in p0.items()}
+        wd = weights(d, ps["n_b"], ps["sigma_r"], ps["sigma_z"], 0.0).cuda()
+        ww = weights(w, 20.0, 0.1, 0.3, ps["zeta_w"]).cuda()
+        L = hq.SweepLoss.apply(grid, beams, 1, "mean", 16, ps["n0"], torch.empty(0), wd, ww)
+        L.backward()
+        grid.close()
+        errs = {k: abs(float(ps[k].grad) - fd[k]) / abs(fd[k]) for k in p0}
+        print(precision, "gradient vs central FD:", {k: f"{float(ps[k].grad):.6e} / {fd[k]:.6e} ({errs[k]:.1e})"
+                                                      for k in p0})
+        for k in p0:
+            assert errs[k] <= tol, (precision, k, errs)

@@ -103,3 +103,17 @@ def test_central_differences_exact_on_quadratics():
     # orientation: an x-only function has no y derivative away from the wall row
     assert float(O.ddy(sp, fx)[2:-1, 1:].abs().max()) < 1e-12
     assert torch.all(O.ddx(sp, fx)[:, 0] == 0) and torch.all(O.ddx(sp, fx)[0, :] == 0)
+
+
+@pytest.mark.parametrize("nx,ny", [(16, 16), (24, 10), (64, 48)])
+def test_fft_dst_matches_matrix_dst(nx, ny):
+    """The O(n log n) DST-I (odd-extension FFT) reproduces the matrix definition."""
+    sp = spec(nx=nx, ny=ny)
+    a = torch.randn(ny, nx, generator=torch.Generator().manual_seed(nx * ny), dtype=torch.float64)
+    ref = O.dst2(sp, a)
+    with O.dst_algorithm("fft"):
+        got = O.dst2(sp, a)
+        f = O.poisson_solve(sp, a)
+    assert float((got - ref).abs().max()) <= 1e-12 * float(ref.abs().max())
+    assert float((f - O.poisson_solve(sp, a)).abs().max()) <= 1e-12 * float(f.abs().max())
+    assert O.DST_ALGORITHM == "matrix"
