@@ -34,6 +34,8 @@
  *   HQ_NO_GRAPH=1  hq_sweep_step issues its launches instead of replaying a CUDA graph
  *   HQ_NO_FORK=1   hq_sweep_step keeps the witness sums and beam deposits on the grid's
  *                  stream instead of beside the final pass on a second stream
+ *   HQ_SEPARATE_SRC=1  FP32: the psi/Ez/Bz and B_perp sources are formed by kernels of
+ *                  their own ahead of each solve instead of in the solve's first phase
  * and one switch for testing the failure path, which does change results:
  *   HQ_FAULT_BARRIER=1  (FP32 grids) the first grid barrier of every tensor-core solve
  *                  waits for one CTA more than the launch has, so its bounded wait runs

@@ -247,14 +247,25 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
   void* prev = g->dep[(slice + 1) & 1];
   void* chi_prev = g->chi[(slice + 1) & 1];
   tape_slice_begin(g);
-  { Prof p(g, HQ_K_FIELD, 1); launch_src_main<T>(g, cur, s); }
-  dst_solve(g, 3);
+  const bool fused_src = !g->fp64 && !g->sep_src;   // FP32: sources formed inside the solve launch
+  if (fused_src) {
+    Prof p(g, HQ_K_DST, 1);
+    dst_solve_tc_main(g, cur, s);
+  } else {
+    { Prof p(g, HQ_K_FIELD, 1); launch_src_main<T>(g, cur, s); }
+    dst_solve(g, 3);
+  }
   { Prof p(g, HQ_K_FIELD, 1); launch_finish_main<T>(g, g->solved, s); }
   const int npc = g->d.n_pc_iter;
   for (int m = 0; m < npc; ++m) {
     const int last = m == npc - 1;
     tape_b_iterate<T>(g, m);
     { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, s); }
+    if (fused_src) {
+      Prof p(g, HQ_K_DST, 1);   // sources, solve and the mixing in one launch
+      dst_solve_tc_bmix_src(g, cur, prev, chi_prev, last, s);
+      continue;
+    }
     { Prof p(g, HQ_K_FIELD, 1); launch_src_bperp<T>(g, cur, prev, chi_prev, last, s); }
     if (g->fp64) {
       dst_solve(g, 2);
@@ -868,6 +879,8 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     // folded DST-I (half the contraction) when both extents are multiples of 128
     const char* nf = std::getenv("HQ_NO_FOLD");
     g->fold = (g->nx % 128 == 0 && g->ny % 128 == 0 && !(nf && nf[0] == '1')) ? 1 : 0;
+    const char* ss = std::getenv("HQ_SEPARATE_SRC");
+    g->sep_src = (ss && ss[0] == '1') ? 1 : 0;
     const char* fb = std::getenv("HQ_FAULT_BARRIER");
     g->fault_barrier = (fb && fb[0] == '1') ? 1 : 0;
     HQ_ALLOC(g->d_gbar, sizeof(unsigned long long));

@@ -156,6 +156,7 @@ struct hq_grid_s {
   float* psrc[2];                            // FP32 mode: psi source rho - J_z of dep[0], dep[1]
   unsigned long long* d_gbar;                // grid-barrier counter of the fused solve kernel (zero between launches)
   int fault_barrier;                         // HQ_FAULT_BARRIER=1: the solve's first grid barrier never fills
+  int sep_src;                               // HQ_SEPARATE_SRC=1: source kernels ahead of the solve launches
 
   // beams
   hq::BeamBins bins[hq::kMaxBeams];
@@ -237,6 +238,9 @@ template <typename T> void launch_zero(void* p, int64_t n, cudaStream_t s);
 void dst_solve_f64(hq_grid_s* g, int nrhs, cudaStream_t s);
 void dst_solve_tc(hq_grid_s* g, int nrhs, cudaStream_t s);
 void dst_solve_tc_bmix(hq_grid_s* g, int last, cudaStream_t s);   // B_perp solve + fused mixing (FP32)
+// FP32 solves with the source assembly as their first phase (no separate source kernel)
+void dst_solve_tc_main(hq_grid_s* g, const void* dep, cudaStream_t s);
+void dst_solve_tc_bmix_src(hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int last, cudaStream_t s);
 int dst_tc_init(hq_grid_s* g, std::string& err);   // builds tensor maps; 0 on success
 void dst_tc_free(hq_grid_s* g);
 // beams
@@ -383,16 +387,18 @@ struct SinkFold {
   }
 };
 
-// Runs f(iy, ix, v) for the node(s) this thread owns and hands the first nr values
-// of v to the sink: one node per thread (consecutive threads along x) for a plain
-// sink; for SinkFold the two nodes of one folded column, the row taken in slot order.
-// Launch with src_grid().
+// Columns of one row of visit_one: nx/2 folded node pairs or nx nodes.
+template <typename Sink> __host__ __device__ __forceinline__ int visit_width(const Geom& gm) {
+  return Sink::kFold ? gm.nx / 2 : gm.nx;
+}
+
+// Runs f(iy, ix, v) for the node(s) of (row, tx) and hands the first nr values of v to the
+// sink: one node for a plain sink (row = iy, tx = ix); for SinkFold the two nodes of folded
+// column tx, the row taken in slot order.
 template <int NR, typename T, typename Sink, typename F>
-__device__ __forceinline__ void visit_nodes(const Geom& gm, const Sink& sink, int nr, F&& f) {
-  const int tx = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void visit_one(const Geom& gm, const Sink& sink, int nr, F&& f, int row, int tx) {
   if constexpr (Sink::kFold) {
-    if (tx >= gm.nx / 2) return;
-    const int sy = blockIdx.y, iy = fold_node(sy, gm.ny);
+    const int iy = fold_node(row, gm.ny);
     int xa, xb;
     fold_pair(tx, gm.nx, xa, xb);
     T va[NR], vb[NR];
@@ -400,15 +406,23 @@ __device__ __forceinline__ void visit_nodes(const Geom& gm, const Sink& sink, in
     f(iy, xb, vb);
 #pragma unroll
     for (int r = 0; r < NR; ++r)
-      if (r < nr) sink.put_pair(r, sy, tx, va[r], vb[r]);
+      if (r < nr) sink.put_pair(r, row, tx, va[r], vb[r]);
   } else {
-    if (tx >= gm.nx) return;
     T v[NR];
-    f((int)blockIdx.y, tx, v);
+    f(row, tx, v);
 #pragma unroll
     for (int r = 0; r < NR; ++r)
-      if (r < nr) sink.put(r, blockIdx.y, tx, v[r]);
+      if (r < nr) sink.put(r, row, tx, v[r]);
   }
+}
+
+// One (row, column) of visit_one per thread: consecutive threads along the row, one row per
+// block row.  Launch with src_grid().
+template <int NR, typename T, typename Sink, typename F>
+__device__ __forceinline__ void visit_nodes(const Geom& gm, const Sink& sink, int nr, F&& f) {
+  const int tx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tx >= visit_width<Sink>(gm)) return;
+  visit_one<NR, T>(gm, sink, nr, f, (int)blockIdx.y, tx);
 }
 
 // Calls f(sink) with the DST operand writer of the grid's solver.
@@ -472,22 +486,48 @@ __device__ __forceinline__ auto dyc(const A& f, int iy, int ix, int ny, C inv2dy
 // source is the separately accumulated, ion-subtracted rho - Jz.
 template <typename T> struct SrcMain {
   static constexpr int NR = 3;
+  static constexpr bool kEffects = false;
   const V4<T>* dep;
   const float* ps;
   Geom gm;
-  __device__ void operator()(int iy, int ix, T* v) const {
-    const int nx = gm.nx;
-    auto jx = [&](int y, int x) { return dep[(int64_t)y * nx + x].b; };
-    auto jy = [&](int y, int x) { return dep[(int64_t)y * nx + x].c; };
+  // what one node's sources read: the psi source, and Jx, Jy at the four neighbours
+  struct In {
+    T p, jxr, jxl, jxu, jxd, jyr, jyl, jyu, jyd;
+  };
+  __device__ In load(int iy, int ix) const {
+    In q{};
+    if (ix > 0 && iy > 0) {
+      const int nx = gm.nx;
+      const int64_t o = (int64_t)iy * nx + ix;
+      if (ps) {
+        q.p = T(-ps[o]);
+      } else {
+        const V4<T> c = dep[o];
+        q.p = -(c.a - c.d);
+      }
+      const bool r = ix + 1 < nx, u = iy + 1 < gm.ny;
+      q.jxr = r ? dep[o + 1].b : T(0);
+      q.jyr = r ? dep[o + 1].c : T(0);
+      q.jxl = dep[o - 1].b;
+      q.jyl = dep[o - 1].c;
+      q.jxu = u ? dep[o + nx].b : T(0);
+      q.jyu = u ? dep[o + nx].c : T(0);
+      q.jxd = dep[o - nx].b;
+      q.jyd = dep[o - nx].c;
+    }
+    return q;
+  }
+  __device__ void eval(int iy, int ix, const In& q, T* v) const {
     v[0] = v[1] = v[2] = T(0);
     if (ix > 0 && iy > 0) {
-      const V4<T> c = dep[(int64_t)iy * nx + ix];
       const T i2x = gsel<T>(gm.inv2dx, gm.f_inv2dx), i2y = gsel<T>(gm.inv2dy, gm.f_inv2dy);
-      v[0] = ps ? T(-ps[(int64_t)iy * nx + ix]) : -(c.a - c.d);
-      v[1] = dxc(jx, iy, ix, nx, i2x) + dyc(jy, iy, ix, gm.ny, i2y);
-      v[2] = dyc(jx, iy, ix, gm.ny, i2y) - dxc(jy, iy, ix, nx, i2x);
+      v[0] = q.p;
+      v[1] = (q.jxr - q.jxl) * i2x + (q.jyu - q.jyd) * i2y;
+      v[2] = (q.jxu - q.jxd) * i2y - (q.jyr - q.jyl) * i2x;
     }
   }
+  __device__ void effects(int, int) const {}
+  __device__ void operator()(int iy, int ix, T* v) const { eval(iy, ix, load(iy, ix), v); }
 };
 
 // Bx: -dy Jz + dzeta Jy;  By: dx Jz - dzeta Jx, with dzeta J = (J(i-1) - J(i+1)) / (2 dzeta)
@@ -497,6 +537,7 @@ template <typename T> struct SrcMain {
 // the deposit of slice i+1.
 template <typename T> struct SrcBperp {
   static constexpr int NR = 2;
+  static constexpr bool kEffects = true;
   const V4<T>* cur;
   V4<T>* prev;
   T* chi_prev;
@@ -506,27 +547,54 @@ template <typename T> struct SrcBperp {
   const V2<T>* bjn;
   Geom gm;
   int reset_prev;
-  __device__ void operator()(int iy, int ix, T* v) const {
-    const int nx = gm.nx;
-    auto jz = [&](int y, int x) { return cur[(int64_t)y * nx + x].d; };
-    const int64_t o = (int64_t)iy * nx + ix;
-    const V4<T> pv = prev[o];
-    const V2<T> t = tj[o];
+  // what one node's sources read: Jz at the four neighbours, J_perp of slices i-1 (record),
+  // i+1 (trial plasma) and i+1 (beam)
+  struct In {
+    T jzr, jzl, jzu, jzd, pb, pc, ta, tb, ba, bb;
+  };
+  __device__ In load(int iy, int ix) const {
+    In q{};
+    if (ix > 0 && iy > 0) {
+      const int nx = gm.nx;
+      const int64_t o = (int64_t)iy * nx + ix;
+      q.jzr = ix + 1 < nx ? cur[o + 1].d : T(0);
+      q.jzl = cur[o - 1].d;
+      q.jzu = iy + 1 < gm.ny ? cur[o + nx].d : T(0);
+      q.jzd = cur[o - nx].d;
+      const V4<T> pv = prev[o];
+      const V2<T> t = tj[o], b = bjn[o];
+      q.pb = pv.b;
+      q.pc = pv.c;
+      q.ta = t.a;
+      q.tb = t.b;
+      q.ba = b.a;
+      q.bb = b.b;
+    }
+    return q;
+  }
+  __device__ void eval(int iy, int ix, const In& q, T* v) const {
     v[0] = v[1] = T(0);
     if (ix > 0 && iy > 0) {
       const T i2z = gsel<T>(gm.inv2dz, gm.f_inv2dz);
-      const V2<T> b = bjn[o];
-      const T dzjx = (pv.b - (t.a + b.a)) * i2z;
-      const T dzjy = (pv.c - (t.b + b.b)) * i2z;
-      v[0] = -dyc(jz, iy, ix, gm.ny, gsel<T>(gm.inv2dy, gm.f_inv2dy)) + dzjy;
-      v[1] = dxc(jz, iy, ix, nx, gsel<T>(gm.inv2dx, gm.f_inv2dx)) - dzjx;
+      const T dzjx = (q.pb - (q.ta + q.ba)) * i2z;
+      const T dzjy = (q.pc - (q.tb + q.bb)) * i2z;
+      v[0] = -((q.jzu - q.jzd) * gsel<T>(gm.inv2dy, gm.f_inv2dy)) + dzjy;
+      v[1] = (q.jzr - q.jzl) * gsel<T>(gm.inv2dx, gm.f_inv2dx) - dzjx;
     }
+  }
+  // after the node's reads: clear the trial J_perp, reset the slice i-1 record if asked
+  __device__ void effects(int iy, int ix) const {
+    const int64_t o = (int64_t)iy * gm.nx + ix;
     tj[o] = V2<T>{T(0), T(0)};
     if (reset_prev) {
       prev[o] = V4<T>{rho_ion[o], T(0), T(0), T(0)};
       chi_prev[o] = T(0);
       if (ps_prev) ps_prev[o] = 0.0f;
     }
+  }
+  __device__ void operator()(int iy, int ix, T* v) const {
+    eval(iy, ix, load(iy, ix), v);
+    effects(iy, ix);
   }
 };
 

@@ -380,8 +380,60 @@ struct SolveArgs {
   unsigned long long* gbar;            // grid-barrier counter (zero at launch, reset by the last CTA)
   int* status;
   int barrier_skew;                    // added to the first barrier's target (fault injection; 0)
+  // source phase ahead of the four products: 0 none (sources already in op[0]); 1 the psi,
+  // Ez, Bz sources of a deposit record (sm); 2 the B_perp sources of the predictor-corrector (sb)
+  int pre;
+  SrcMain<float> sm;
+  SrcBperp<float> sb;
 };
 
+// Source phase: every thread of the launch takes (row, column) items of the operand writer
+// in turn (consecutive threads along a row), KB items at a time: all their reads are issued
+// before any write, then the sources are evaluated, split into op[0] and the functor's own
+// writes (clearing the trial J_perp) follow.
+template <typename Sink, typename F, int NR>
+__device__ __forceinline__ void solve_sources(const Geom& gm, const Sink& sink, const F& f) {
+  constexpr int KB = 4;
+  constexpr int NN = Sink::kFold ? 2 : 1;   // nodes per item
+  const int w = visit_width<Sink>(gm);
+  const int total = w * gm.ny;
+  const int stride = gridDim.x * blockDim.x;
+  for (int t0 = blockIdx.x * blockDim.x + threadIdx.x; t0 < total; t0 += KB * stride) {
+    int iy[KB][NN], ix[KB][NN];
+    typename F::In in[KB][NN];
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      const int t = t0 + k * stride;
+      const int row = t < total ? t / w : 0, tx = t < total ? t % w : 0;
+      if constexpr (Sink::kFold) {
+        iy[k][0] = iy[k][NN - 1] = fold_node(row, gm.ny);
+        fold_pair(tx, gm.nx, ix[k][0], ix[k][NN - 1]);
+      } else {
+        iy[k][0] = row;
+        ix[k][0] = tx;
+      }
+#pragma unroll
+      for (int j = 0; j < NN; ++j) in[k][j] = t < total ? f.load(iy[k][j], ix[k][j]) : typename F::In{};
+    }
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      const int t = t0 + k * stride;
+      if (t >= total) break;
+      float v[NN][NR];
+#pragma unroll
+      for (int j = 0; j < NN; ++j) f.eval(iy[k][j], ix[k][j], in[k][j], v[j]);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if constexpr (Sink::kFold) sink.put_pair(r, t / w, t % w, v[0][r], v[NN - 1][r]);
+        else sink.put(r, t / w, t % w, v[0][r]);
+      }
+      if constexpr (F::kEffects) {
+#pragma unroll
+        for (int j = 0; j < NN; ++j) f.effects(iy[k][j], ix[k][j]);
+      }
+    }
+  }
+}
 // Bounded mbarrier wait that also gives up once another thread of the CTA has.
 __device__ __forceinline__ bool mbar_wait_a(uint32_t bar, uint32_t parity, int* status, volatile int* abort_f) {
   const long long t0 = clock64();
@@ -436,11 +488,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
 // CTA (twice the tiles, so more of the SMs take part in each product).
 constexpr int kSolveThreads = 256;
 
-// Optional per-CTA timestamps of the solve's steps (a profiling build defines it).
-#ifndef HQ_SOLVE_TRACE_POINT
-#define HQ_SOLVE_TRACE_POINT(phase, tag)
-#endif
-
 // Shared memory of the solve: the stage ring, the FP32 scale tile of phase 1
 // ([BN n][128 rows]), then the barriers (full, empty, done, scale) and the TMEM slot.
 template <int BN> struct SolveSmem {
@@ -473,7 +520,6 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
   const float* scale_s = reinterpret_cast<const float*>(basep + L::SCALE);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_f = &s_abort;
-  HQ_SOLVE_TRACE_POINT(0, 6);
 
   if (threadIdx.x == 0) {
     for (const CUtensorMap* m : {&a0h, &a0l, &a1h, &a1l, &bxh, &bxl, &byh, &byl, &scm})
@@ -497,7 +543,6 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  HQ_SOLVE_TRACE_POINT(0, 7);
 
   // stage-ring, accumulator and scale-tile counters across tiles
   uint32_t kb_run = 0, tiles_run = 0, scales_run = 0;
@@ -518,8 +563,23 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
   const int t0 = (int)blockIdx.x;
   const int m0x = (t0 % mtx) * BM, n0x = (t0 / mtx) * BN, rx = m0x / P1x;
   const int m0y = (t0 % mty) * BM, n0y = (t0 / mty) * BN, ry = m0y / P1y;
-  for (int p = 0; p < 4; ++p) {
-    HQ_SOLVE_TRACE_POINT(p, 0);
+  // source phase (its writes reach the other CTAs' TMA loads through the barrier's proxy fences)
+  const unsigned nb0 = a.pre ? 1u : 0u;   // barriers before phase 0
+  bool go = true;
+  if (a.pre) {
+    const Geom& gm = a.pre == 1 ? a.sm.gm : a.sb.gm;
+    if (a.fold) {
+      const SinkFold sink{a.op_hi[0], a.op_lo[0], a.nx, a.ny};
+      if (a.pre == 1) solve_sources<SinkFold, SrcMain<float>, 3>(gm, sink, a.sm);
+      else solve_sources<SinkFold, SrcBperp<float>, 2>(gm, sink, a.sb);
+    } else {
+      const SinkBF16 sink{a.op_hi[0], a.op_lo[0], a.nxp, a.nyp};
+      if (a.pre == 1) solve_sources<SinkBF16, SrcMain<float>, 3>(gm, sink, a.sm);
+      else solve_sources<SinkBF16, SrcBperp<float>, 2>(gm, sink, a.sb);
+    }
+    go = grid_barrier(a.gbar, (unsigned long long)gridDim.x + (unsigned)a.barrier_skew, a.status, abort_f);
+  }
+  for (int p = 0; p < 4 && go; ++p) {
     const bool along_x = (p & 1) == 0;
     // rows per rhs, output columns (= contraction extent), tiles, K blocks
     const int P1 = along_x ? P1x : P1y, P2 = along_x ? P2x : P2y, mt = along_x ? mtx : mty;
@@ -556,7 +616,6 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
           tma_load_2d(st + 2 * A_BYTES, tbh, kb * BK, n0, fb);
           tma_load_2d(st + 2 * A_BYTES + C::B_BYTES, tbl, kb * BK, n0, fb);
         }
-        HQ_SOLVE_TRACE_POINT(p, 1);
       } else if (warp == 1 && lane == 0) {
         // MMA issuer
         for (int kb = 0; kb < nk; ++kb) {
@@ -583,7 +642,6 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
       mbar_wait_a(done, tiles_run & 1, a.status, abort_f);
       if (mode == 1) mbar_wait_a(sbar, scales_run & 1, a.status, abort_f);
       tc_fence_after();
-      HQ_SOLVE_TRACE_POINT(p, 2);
 
       // ------------------------------------------------ epilogue: TMEM lane = tile row; the
       // two warpgroups take one half of the columns each (a warp reads the lanes of its
@@ -604,7 +662,6 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
         {
           float x[CH];
           tmem_ld_pair<BN, CH>(tl + (uint32_t)c0, x);
-          HQ_SOLVE_TRACE_POINT(p, 8);
           if (mode == 1) {
 #pragma unroll
             for (int j = 0; j < CH; ++j) x[j] *= scale_s[(c0 + j) * BM + row];
@@ -619,7 +676,6 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
           }
 #pragma unroll
           for (int j = 0; j < CH; ++j) put_split(oh, ol, ((int64_t)r * P2 + n0 + c0 + j) * P1 + fcol, x[j]);
-          HQ_SOLVE_TRACE_POINT(p, 9);
         }
       } else {
         // node of this row (rows run along x in the last phase)
@@ -669,26 +725,24 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      HQ_SOLVE_TRACE_POINT(p, 3);
       if (*abort_f) break;
     }
-    if (p < 3 &&
-        !grid_barrier(a.gbar, (unsigned long long)(p + 1) * gridDim.x + (p == 0 ? (unsigned)a.barrier_skew : 0u),
-                      a.status, abort_f))
+    if (p < 3 && !grid_barrier(a.gbar,
+                               (unsigned long long)(nb0 + p + 1) * gridDim.x +
+                                   (nb0 == 0 && p == 0 ? (unsigned)a.barrier_skew : 0u),
+                               a.status, abort_f))
       break;
-    HQ_SOLVE_TRACE_POINT(p, 4);
   }
   // exit arrival: the last CTA through resets the counter for the next launch
   if (threadIdx.x == 0 && !*abort_f) {
     const unsigned long long seen = atomicAdd(a.gbar, 1ull);
-    if (seen == 4ull * gridDim.x - 1ull) atomicExch(a.gbar, 0ull);
+    if (seen == (nb0 + 4ull) * gridDim.x - 1ull) atomicExch(a.gbar, 0ull);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
   }
-  HQ_SOLVE_TRACE_POINT(3, 14);
 }
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
@@ -799,8 +853,10 @@ void dst_tc_free(hq_grid_s* g) {
 
 namespace {
 
-// One cooperative launch of k_dst_solve on the sources in op[0].
-void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s) {
+// One cooperative launch of k_dst_solve: on the sources in op[0] (pre = 0), or forming them
+// first from the deposit records (pre = 1: psi, Ez, Bz of dep_cur; pre = 2: B_perp).
+void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s, int pre = 0,
+                 const void* dep_cur = nullptr, void* dep_prev = nullptr, void* chi_prev = nullptr) {
   const TensorMaps& t = *g->tmaps;
   SolveArgs a{};
   a.R = R;
@@ -825,6 +881,9 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s) 
   a.gbar = g->d_gbar;
   a.status = g->d_status;
   a.barrier_skew = g->fault_barrier;
+  a.pre = pre;
+  if (pre == 1) a.sm = src_main_of<float>(g, dep_cur);
+  if (pre == 2) a.sb = src_bperp_of<float>(g, dep_cur, dep_prev, chi_prev, last);
   // tiles of one product (the larger of the x and y products) at N-tile width bn
   auto tiles = [&](int bn) {
     return std::max(R * (g->nyp / BM) * (g->nxp / bn), R * (g->nxp / BM) * (g->nyp / bn));
@@ -854,6 +913,14 @@ void dst_solve_tc_bmix(hq_grid_s* g, int last, cudaStream_t s) { solve_fused(g, 
 
 // sources (split) in op[0] -> FP32 solution in g->solved [R][ny][nx]
 void dst_solve_tc(hq_grid_s* g, int R, cudaStream_t s) { solve_fused(g, R, 2, 0, s); }
+
+// The same with the source kernels folded into the launch as its first phase: psi, Ez, Bz of
+// the deposit record dep -> g->solved; the B_perp sources of the predictor-corrector (which
+// clear the trial J_perp and, on the last iteration, reset dep_prev) -> mixing into gf.
+void dst_solve_tc_main(hq_grid_s* g, const void* dep, cudaStream_t s) { solve_fused(g, 3, 2, 0, s, 1, dep); }
+void dst_solve_tc_bmix_src(hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int last, cudaStream_t s) {
+  solve_fused(g, 2, 3, last, s, 2, cur, prev, chi_prev);
+}
 
 }  // namespace hq
 
