@@ -30,6 +30,8 @@
  * unchanged up to summation order:
  *   HQ_NO_FOLD=1   FP32 DST-I without the folded (half-K) products
  *   HQ_SOLVE_BN=64 FP32 solves always on 128 x 64 tiles (no 128 x 32 tiles)
+ *   HQ_NO_RS=1     FP32 square grids of 256 or 512 cells: the solve streams the fold matrix
+ *                  per tile instead of keeping each CTA's slice of it in shared memory
  *   HQ_NO_PDL=1    no programmatic dependent launch between the per-slice kernels
  *   HQ_NO_GRAPH=1  hq_sweep_step issues its launches instead of replaying a CUDA graph
  *   HQ_NO_FORK=1   hq_sweep_step keeps the witness sums and beam deposits on the grid's

@@ -56,7 +56,7 @@ void free_all(hq_grid_s* g) {
     }
   }
   for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); F(g->psrc[i]); }
-  F(g->rho_ion); F(g->tj); F(g->bjn); F(g->gf); F(g->psi); F(g->bprev1); F(g->bprev2); F(g->solved);
+  F(g->rho_ion); F(g->tj); F(g->bjn); F(g->gf); F(g->bm); F(g->psi); F(g->bprev1); F(g->solved);
   F(g->f64_a); F(g->f64_b); F(g->f64_scale); F(g->tw_x); F(g->tw_y); F(g->sin_x); F(g->sin_y);
   F(g->sx_hi); F(g->sx_lo); F(g->sy_hi); F(g->sy_lo); F(g->f32_scale);
   for (int b = 0; b < kMaxBeams; ++b) {
@@ -188,17 +188,21 @@ void tape_slice_begin(hq_grid_s* g) {
   AdjStore* a = adj_of(g);
   if (a && a->tape_slot >= 0) snap_copy(g, a->tape[a->tape_slot], true);
 }
-template <typename T>
 void tape_b_iterate(hq_grid_s* g, int m) {
   AdjStore* a = adj_of(g);
   if (!a || a->tape_slot < 0) return;
   char* base = reinterpret_cast<char*>(a->tape_b[a->tape_slot]) + (size_t)m * 2 * g->tsize * g->nnode;
-  launch_adj_extract_b<T>(g, base, g->stream);
+  cudaMemcpyAsync(base, g->bm, 2 * g->tsize * g->nnode, cudaMemcpyDeviceToDevice, g->stream);
 }
+// the slice's converged gather record followed by its converged B_perp record
 void tape_slice_end(hq_grid_s* g) {
   AdjStore* a = adj_of(g);
-  if (a && a->tape_slot >= 0)
-    cudaMemcpyAsync(a->tape_gf[a->tape_slot], g->gf, kGF * g->tsize * g->nnode, cudaMemcpyDeviceToDevice, g->stream);
+  if (a && a->tape_slot >= 0) {
+    const size_t gfb = kGF * g->tsize * g->nnode;
+    char* t = reinterpret_cast<char*>(a->tape_gf[a->tape_slot]);
+    cudaMemcpyAsync(t, g->gf, gfb, cudaMemcpyDeviceToDevice, g->stream);
+    cudaMemcpyAsync(t + gfb, g->bm, 2 * g->tsize * g->nnode, cudaMemcpyDeviceToDevice, g->stream);
+  }
 }
 
 void adj_free(hq_grid_s* g) {
@@ -255,11 +259,11 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
     { Prof p(g, HQ_K_FIELD, 1); launch_src_main<T>(g, cur, s); }
     dst_solve(g, 3);
   }
-  { Prof p(g, HQ_K_FIELD, 1); launch_finish_main<T>(g, g->solved, s); }
+  { Prof p(g, HQ_K_FIELD, 1); launch_finish_main<T>(g, g->solved, slice == 0, s); }
   const int npc = g->d.n_pc_iter;
   for (int m = 0; m < npc; ++m) {
     const int last = m == npc - 1;
-    tape_b_iterate<T>(g, m);
+    tape_b_iterate(g, m);
     { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, s); }
     if (fused_src) {
       Prof p(g, HQ_K_DST, 1);   // sources, solve and the mixing in one launch
@@ -270,16 +274,15 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
     if (g->fp64) {
       dst_solve(g, 2);
       Prof p(g, HQ_K_FIELD, 1);
-      launch_finish_bperp<T>(g, g->solved, last, s);
+      launch_finish_bperp<T>(g, g->solved, s);
     } else {
       Prof p(g, HQ_K_DST, 1);   // the mixing runs in the last product's epilogue
       dst_solve_tc_bmix(g, last, s);
     }
   }
   if (npc == 0) {
-    // no predictor-corrector: B(i) is the guess; shift, clear and reset without the fused kernels
-    Prof p(g, HQ_K_FIELD, 3);
-    launch_bshift<T>(g, s);
+    // no predictor-corrector: B(i) is the guess; clear and reset without the source kernels
+    Prof p(g, HQ_K_FIELD, 2);
     launch_zero<T>(g->bjn, 2 * g->nnode, s);
     launch_reset_dep<T>(g, prev, chi_prev, s);
   }
@@ -306,7 +309,6 @@ void advance_impl(hq_grid_s* g, int slice) {
     launch_zero<T>(g->dep[1], 4 * g->nnode, s);   // J(-1) = 0 ahead of the box
     if (!g->fp64) launch_zero<float>(g->psrc[1], g->nnode, s);
     launch_zero<T>(g->bprev1, 2 * g->nnode, s);
-    launch_zero<T>(g->bprev2, 2 * g->nnode, s);
     launch_zero<T>(g->bjn, 2 * g->nnode, s);
     launch_zero<T>(g->tj, 2 * g->nnode, s);
   } else {
@@ -419,7 +421,7 @@ hq_status adj_alloc(hq_grid_s* g, int k) {
   a->tape_gf.resize(k);
   a->tape_b.resize(k);
   for (int i = 0; ok && i < k; ++i)
-    ok = snap(a->tape[i]) && A(&a->tape_gf[i], kGF * ts * nn) && A(&a->tape_b[i], (size_t)std::max(npc, 1) * 2 * ts * nn);
+    ok = snap(a->tape[i]) && A(&a->tape_gf[i], (kGF + 2) * ts * nn) && A(&a->tape_b[i], (size_t)std::max(npc, 1) * 2 * ts * nn);
   ok = ok && A(&a->sx, ts * np) && A(&a->sy, ts * np) && A(&a->sux, ts * np) && A(&a->suy, ts * np) &&
        A(&a->spsi, ts * np) && A(&a->sh, ts * np * 20) && A(&a->sacc, ts * np * 5) && A((void**)&a->wbar_p, 8 * np) && A(&a->tbar, 4 * ts * nn) && A(&a->fbar_b, 2 * ts * nn) &&
        A(&a->bbar, (size_t)(npc + 1) * 2 * ts * nn) && A(&a->jbar, 2 * ts * nn) && A(&a->jtot, 2 * ts * nn) &&
@@ -444,8 +446,9 @@ void ckpt_copy(hq_grid_s* g, int seg, bool save) {
   cp(a->ck_dep1[seg], g->dep[1], 4 * ts * nn);
   cp(a->ck_chi0[seg], g->chi[0], ts * nn);
   cp(a->ck_chi1[seg], g->chi[1], ts * nn);
-  cp(a->ck_b1[seg], g->bprev1, 2 * ts * nn);
-  cp(a->ck_b2[seg], g->bprev2, 2 * ts * nn);
+  // B_perp of the two previous slices: B(i-1) still in the B_perp record, B(i-2) in bprev1
+  cp(a->ck_b1[seg], g->bm, 2 * ts * nn);
+  cp(a->ck_b2[seg], g->bprev1, 2 * ts * nn);
   if (!g->fp64) {
     cp(a->ck_ps0[seg], g->psrc[0], 4 * nn);
     cp(a->ck_ps1[seg], g->psrc[1], 4 * nn);
@@ -816,9 +819,9 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   HQ_ALLOC(g->tj, 2 * ts * nn);
   HQ_ALLOC(g->bjn, 2 * ts * nn);
   HQ_ALLOC(g->gf, kGF * ts * nn);
+  HQ_ALLOC(g->bm, 2 * ts * nn);
   HQ_ALLOC(g->psi, ts * nn);
   HQ_ALLOC(g->bprev1, 2 * ts * nn);
-  HQ_ALLOC(g->bprev2, 2 * ts * nn);
   HQ_ALLOC(g->solved, kMaxRhs * ts * nn);
   HQ_ALLOC(g->d_status, sizeof(int));
   HQ_ALLOC(g->d_removed, sizeof(unsigned long long));
@@ -837,7 +840,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   // zero everything the kernels accumulate into or read before writing
   for (void* p : {g->dep[0], g->dep[1]}) cudaMemset(p, 0, 4 * ts * nn);
   for (void* p : {g->chi[0], g->chi[1], g->rho_ion, g->psi}) cudaMemset(p, 0, ts * nn);
-  for (void* p : {g->tj, g->bjn, g->bprev1, g->bprev2}) cudaMemset(p, 0, 2 * ts * nn);
+  for (void* p : {g->tj, g->bjn, g->bprev1, g->bm}) cudaMemset(p, 0, 2 * ts * nn);
   cudaMemset(g->gf, 0, kGF * ts * nn);
   cudaMemset(g->solved, 0, kMaxRhs * ts * nn);
   cudaMemset(g->d_status, 0, sizeof(int));

@@ -52,8 +52,10 @@ template <typename T> __device__ __forceinline__ T gsel(double d, float f) {
 template <typename T> struct V4 { T a, b, c, d; };   // packed rho, jx, jy, jz
 
 template <typename T> struct V2 { T a, b; };          // packed jx, jy or bx, by
-// Gather fields packed per node: ExmBy, EypBx, Ez, Bx, By, Bz, pad, pad.
-constexpr int kGF = 8;
+// Gather fields packed per node: ExmBy, EypBx, Ez, Bz (one 16-byte record in FP32); the
+// transverse magnetic field Bx, By of the predictor-corrector lives in a record of its own
+// (V2 per node, hq_grid_s::bm), which the mixing updates in place.
+constexpr int kGF = 4;
 
 // Plasma slice, structure of arrays.  x, y, psi are FP64 accumulators in both
 // modes; the rest is of the field type T.
@@ -138,10 +140,12 @@ struct hq_grid_s {
   void* rho_ion;
   void* tj;            // V2: trial plasma J_perp of slice i+1
   void* bjn;           // V2: beam J_perp of slice i+1
-  void* gf;            // kGF per node (gather fields of the current slice)
+  void* gf;            // kGF per node (gather fields ExmBy, EypBx, Ez, Bz of the current slice)
+  void* bm;            // V2: Bx, By of the current slice (the predictor-corrector iterate, then converged);
+                       // until finish_main of slice i it holds the converged B_perp of slice i-1
   void* psi;
-  void* bprev1;        // V2: B_perp of slice i-1
-  void* bprev2;        // V2: B_perp of slice i-2
+  void* bprev1;        // V2: B_perp of slice i-2 until finish_main of slice i, then of slice i-1
+                       // (B_perp of slice i-1 is gf[3..4] until then)
   void* solved;        // kMaxRhs x nnode: DST results
 
   // DST, FP64: [kMaxRhs][nnode] ping-pong buffers, per-mode scale, twiddles, sine tables
@@ -226,12 +230,10 @@ template <typename T> void launch_src_main(const hq_grid_s* g, const void* dep, 
 template <typename T> void launch_src_bperp(const hq_grid_s* g, const void* dep_cur, void* dep_prev, void* chi_prev,
                                             int reset_prev, cudaStream_t s);
 template <typename T> void launch_src_copy(const hq_grid_s* g, const void* src, int nrhs, cudaStream_t s);
-// finish_main also sets the B_perp guess 2 B(i-1) - B(i-2)
-template <typename T> void launch_finish_main(const hq_grid_s* g, const void* res, cudaStream_t s);
-// last != 0: also shift the B_perp history and clear the beam J_perp of slice i+1
-template <typename T> void launch_finish_bperp(const hq_grid_s* g, const void* res, int last, cudaStream_t s);
-template <typename T> void launch_bguess(const hq_grid_s* g, cudaStream_t s);
-template <typename T> void launch_bshift(const hq_grid_s* g, cudaStream_t s);
+// finish_main also sets the B_perp guess 2 B(i-1) - B(i-2) (first: slice 0, B(-1) = 0) and
+// moves B(i-1) into bprev1
+template <typename T> void launch_finish_main(const hq_grid_s* g, const void* res, int first, cudaStream_t s);
+template <typename T> void launch_finish_bperp(const hq_grid_s* g, const void* res, cudaStream_t s);
 template <typename T> void launch_store(const hq_grid_s* g, const hq_field_out* out, int64_t slot, const void* dep, const void* chi, cudaStream_t s);
 template <typename T> void launch_zero(void* p, int64_t n, cudaStream_t s);
 // DST backends: transform the nrhs sources prepared by the src kernels into g->solved
@@ -262,7 +264,6 @@ template <typename T> void launch_adj_guess(const hq_grid_s* g, const void* b0, 
 template <typename T> void launch_adj_main_pre(const hq_grid_s* g, const void* tbar, cudaStream_t st);
 template <typename T> void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, void* tbar,
                                                cudaStream_t st);
-template <typename T> void launch_adj_extract_b(const hq_grid_s* g, void* out, cudaStream_t st);
 template <typename T> void launch_adj_beam(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* dcur,
                                           const void* jtot, double* wbar, cudaStream_t st);
 template <typename T> void launch_adj_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* gf,
@@ -534,7 +535,8 @@ template <typename T> struct SrcMain {
 // and J(i+1) = trial plasma + beam of slice i+1 (Sec. 3.2 predictor-corrector).  The trial
 // J_perp is cleared after reading (ready for the next trial pass); with reset_prev (the
 // last iteration) the slice i-1 record is reset to the ion background, ready to receive
-// the deposit of slice i+1.
+// the deposit of slice i+1, and the beam J_perp of slice i+1 is cleared for the next
+// slice's beam deposit.
 template <typename T> struct SrcBperp {
   static constexpr int NR = 2;
   static constexpr bool kEffects = true;
@@ -544,7 +546,7 @@ template <typename T> struct SrcBperp {
   float* ps_prev;
   const T* rho_ion;
   V2<T>* tj;
-  const V2<T>* bjn;
+  V2<T>* bjn;
   Geom gm;
   int reset_prev;
   // what one node's sources read: Jz at the four neighbours, J_perp of slices i-1 (record),
@@ -590,6 +592,7 @@ template <typename T> struct SrcBperp {
       prev[o] = V4<T>{rho_ion[o], T(0), T(0), T(0)};
       chi_prev[o] = T(0);
       if (ps_prev) ps_prev[o] = 0.0f;
+      bjn[o] = V2<T>{T(0), T(0)};
     }
   }
   __device__ void operator()(int iy, int ix, T* v) const {
@@ -605,7 +608,7 @@ template <typename T>
 inline SrcBperp<T> src_bperp_of(const hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int reset_prev) {
   return SrcBperp<T>{reinterpret_cast<const V4<T>*>(cur), reinterpret_cast<V4<T>*>(prev), reinterpret_cast<T*>(chi_prev),
                      psrc_of(g, prev), reinterpret_cast<const T*>(g->rho_ion), reinterpret_cast<V2<T>*>(g->tj),
-                     reinterpret_cast<const V2<T>*>(g->bjn), g->geom, reset_prev};
+                     reinterpret_cast<V2<T>*>(g->bjn), g->geom, reset_prev};
 }
 
 }  // namespace hq

@@ -291,8 +291,21 @@ __global__ void __launch_bounds__(kThreads)
     opp = T(1.0 + psi);
   }
   T F[6], Fx[6], Fy[6];
-  gather_g<P, T, 4>(gf, kGF, 0, gm, st, F, Fx, Fy);            // ExmBy, EypBx, Ez, Bx
-  gather_g<P, T, 2>(gf, kGF, 4, gm, st, F + 4, Fx + 4, Fy + 4);  // By, Bz
+  {
+    T v4[4], g4x[4], g4y[4];
+    gather_g<P, T, 4>(gf, kGF, 0, gm, st, v4, g4x, g4y);   // ExmBy, EypBx, Ez, Bz
+    T b[2], bx[2], by[2];
+    gather_g<P, T, 2>(gf + kGF * (int64_t)gm.nx * gm.ny, 2, 0, gm, st, b, bx, by);   // Bx, By (converged)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      F[c] = v4[c];
+      Fx[c] = g4x[c];
+      Fy[c] = g4y[c];
+    }
+    F[3] = b[0]; F[4] = b[1]; F[5] = v4[3];
+    Fx[3] = bx[0]; Fx[4] = bx[1]; Fx[5] = g4x[3];
+    Fy[3] = by[0]; Fy[4] = by[1]; Fy[5] = g4y[3];
+  }
   T f[5];
   derivs_f<T>(ux, uy, opp, F, f);
   T comb[5];
@@ -400,13 +413,11 @@ __global__ void __launch_bounds__(kThreads)
   T F[6], Fx[6], Fy[6];
   {
     T v4[4], g4x[4], g4y[4];
-    gather_g<P, T, 4>(gf, kGF, 0, gm, st, v4, g4x, g4y);   // ExmBy, EypBx, Ez (and the gather record's Bx)
+    gather_g<P, T, 4>(gf, kGF, 0, gm, st, v4, g4x, g4y);   // ExmBy, EypBx, Ez, Bz
     F[0] = v4[0]; F[1] = v4[1]; F[2] = v4[2];
     Fx[0] = g4x[0]; Fx[1] = g4x[1]; Fx[2] = g4x[2];
     Fy[0] = g4y[0]; Fy[1] = g4y[1]; Fy[2] = g4y[2];
-    T b1[2], b1x[2], b1y[2];
-    gather_g<P, T, 2>(gf, kGF, 4, gm, st, b1, b1x, b1y);   // (By,) Bz
-    F[5] = b1[1]; Fx[5] = b1x[1]; Fy[5] = b1y[1];
+    F[5] = v4[3]; Fx[5] = g4x[3]; Fy[5] = g4y[3];
     T b2[2], b2x[2], b2y[2];
     gather_g<P, T, 2>(reinterpret_cast<const T*>(bm), 2, 0, gm, st, b2, b2x, b2y);  // Bx, By of B^(m-1)
     F[3] = b2[0]; F[4] = b2[1];
@@ -602,12 +613,6 @@ __global__ void k_adj_main_post(const T* __restrict__ res, V4<T>* dcur, T* rho_i
   rho_ion_bar[o] += d.a;
 }
 
-template <typename T>
-__global__ void k_adj_extract_b(const T* __restrict__ gf, V2<T>* out, int64_t nn) {
-  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= nn) return;
-  out[o] = V2<T>{gf[o * kGF + 3], gf[o * kGF + 4]};
-}
 
 // ---------------------------------------------------------------- beams and parameters
 template <int P>
@@ -830,11 +835,6 @@ void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, voi
                                                g->geom);
 }
 template <typename T>
-void launch_adj_extract_b(const hq_grid_s* g, void* out, cudaStream_t st) {
-  k_adj_extract_b<T><<<blocks_for(g->nnode), kThreads, 0, st>>>(reinterpret_cast<const T*>(g->gf),
-                                                              reinterpret_cast<V2<T>*>(out), g->nnode);
-}
-template <typename T>
 void launch_adj_beam(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* dcur, const void* jtot,
                      double* wbar, cudaStream_t st) {
   const BeamBins& bb = g->bins[b];
@@ -877,7 +877,6 @@ void launch_adj_params(const hq_grid_s* g, const double* wbar_p, double* dn0, do
   template void launch_adj_guess<T>(const hq_grid_s*, const void*, void*, void*, cudaStream_t);                      \
   template void launch_adj_main_pre<T>(const hq_grid_s*, const void*, cudaStream_t);                                 \
   template void launch_adj_main_post<T>(const hq_grid_s*, void*, void*, void*, cudaStream_t);                        \
-  template void launch_adj_extract_b<T>(const hq_grid_s*, void*, cudaStream_t);                                      \
   template void launch_adj_beam<T>(const hq_grid_s*, int, const hq_beam_view&, int, const void*, const void*,        \
                                    double*, cudaStream_t);                                                           \
   template void launch_adj_witness<T>(const hq_grid_s*, int, const hq_beam_view&, int, const void*, const double*,   \

@@ -137,7 +137,8 @@ __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, 
 }
 
 template <int P, typename T>
-__device__ __forceinline__ void gather_all(const T* __restrict__ gf, const Geom& gm, double x, double y, double* F) {
+__device__ __forceinline__ void gather_all(const T* __restrict__ gf, const T* __restrict__ bm, const Geom& gm, double x,
+                                           double y, double* F) {
   double wx[P + 1], wy[P + 1];
   const int ix0 = stencil1<P>(x, gm.xmin, gm.dx, wx);
   const int iy0 = stencil1<P>(y, gm.ymin, gm.dy, wy);
@@ -151,10 +152,16 @@ __device__ __forceinline__ void gather_all(const T* __restrict__ gf, const Geom&
     for (int a = 0; a <= P; ++a) {
       const int ix = ix0 + a;
       if (!in_interior(ix, gm.nx)) continue;
-      const T* q = gf + ((int64_t)iy * gm.nx + ix) * kGF;
+      const int64_t node = (int64_t)iy * gm.nx + ix;
+      const T* q = gf + node * kGF;   // ExmBy, EypBx, Ez, Bz
+      const T* bq = bm + node * 2;    // Bx, By
       const double w = wx[a] * wy[b];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) F[c] += w * (double)q[c];
+      F[0] += w * (double)q[0];
+      F[1] += w * (double)q[1];
+      F[2] += w * (double)q[2];
+      F[3] += w * (double)bq[0];
+      F[4] += w * (double)bq[1];
+      F[5] += w * (double)q[3];
     }
   }
 }
@@ -163,7 +170,7 @@ __device__ __forceinline__ void gather_all(const T* __restrict__ gf, const Geom&
 // E = (ExmBy + By, EypBx - Bx, Ez), B = (Bx, By, Bz); zeta advances with v_z - 1.
 template <int P, typename T>
 __global__ void k_beam_push(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm,
-                            int slice, Geom gm, const T* __restrict__ gf, double dt) {
+                            int slice, Geom gm, const T* __restrict__ gf, const T* __restrict__ bm, double dt) {
   pdl_trigger();
   pdl_wait();
   const int a0 = off[slice], a1 = off[slice + 1];
@@ -176,7 +183,7 @@ __global__ void k_beam_push(hq_beam_view v, const int32_t* __restrict__ off, con
     y += h * uy * ig;
     z += h * (uz * ig - 1.0);
     double F[6];
-    gather_all<P, T>(gf, gm, x, y, F);
+    gather_all<P, T>(gf, bm, gm, x, y, F);
     const double ex = F[0] + F[4], ey = F[1] - F[3], ez = F[2];
     ux += qm * h * ex;
     uy += qm * h * ey;
@@ -286,7 +293,8 @@ void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slic
   const BeamBins& bb = g->bins[b];
   HQ_SHAPE_SWITCH(g->d.shape_order,
                   (launch_pdl(k_beam_push<P, T>, dim3(kSliceBlocks), dim3(kThreads), (size_t)0, s, v, bb.offset, bb.perm,
-                             slice, g->geom, reinterpret_cast<const T*>(g->gf), dt)));
+                             slice, g->geom, reinterpret_cast<const T*>(g->gf), reinterpret_cast<const T*>(g->bm),
+                             dt)));
 }
 template <typename T>
 void launch_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double* sums, cudaStream_t s) {

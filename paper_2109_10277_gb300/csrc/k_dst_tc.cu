@@ -44,6 +44,12 @@ struct TensorMaps {
   CUtensorMap scale[2];
   int ctas[2];                // co-resident CTAs of each width
   bool wide_only;             // HQ_SOLVE_BN=64: never use the 32-wide tiles
+  // resident fold-matrix solve (square folded grids, n = 256 or 512): the fold matrix in
+  // 128-row boxes, op[0] and op[1] in BN-row boxes ([0]: 64, [1]: 32)
+  bool rs;
+  CUtensorMap rf_hi, rf_lo;
+  CUtensorMap rx_hi[2][2], rx_lo[2][2];   // [operand][width]
+  int rs_ctas[2];
 };
 
 namespace {
@@ -66,8 +72,7 @@ template <int BN> struct Cfg {
 };
 
 struct Epi {
-  int mode;          // 0: split + transposed bf16 store; 1: scale, split, store; 2: FP32 transposed store;
-                     // 3: predictor-corrector mixing of (Bx, By) into the gather record
+  int mode;          // 0: split + transposed bf16 store; 1: scale, split, store; 2: FP32 transposed store
   int P1;            // rows per right-hand side (padded), i.e. m extent per rhs
   int P2;            // padded n extent
   __nv_bfloat16* out_hi;
@@ -75,14 +80,6 @@ struct Epi {
   const float* scale;   // [P2][P1]
   float* out_f32;       // [R][n_real][m_real]
   int m_real, n_real;
-  // mode 3: B <- w B_solved + (1 - w) B in gf[node*8 + 3 + r]; last: B(i-2) <- B(i-1) <- B, clear bjn
-  float* gf;
-  float* b1;
-  float* b2;
-  float* bjn;
-  float w;
-  int last;
-  int* status;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -294,33 +291,6 @@ __global__ void __launch_bounds__(128, 1)
         }
         if (bad) atomicOr(status, DEV_NONFINITE);
       }
-    } else if (ep.mode == 3) {
-      if (ml < ep.m_real) {
-        // two phases: all loads of the chunk first, then the mixing and stores
-        float old[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c0 + j;
-          old[j] = n < ep.n_real ? ep.gf[((int64_t)n * ep.m_real + ml) * kGF + 3 + r] : 0.0f;
-        }
-        bool bad = false;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c0 + j;
-          if (n >= ep.n_real) continue;
-          const float x = __uint_as_float(v[j]);
-          bad |= !isfinite(x);
-          const int64_t node = (int64_t)n * ep.m_real + ml;
-          const float nb = ep.w * x + (1.0f - ep.w) * old[j];
-          ep.gf[node * kGF + 3 + r] = nb;
-          if (ep.last) {
-            ep.b2[node * 2 + r] = ep.b1[node * 2 + r];
-            ep.b1[node * 2 + r] = nb;
-            ep.bjn[node * 2 + r] = 0.0f;
-          }
-        }
-        if (bad) atomicOr(ep.status, DEV_NONFINITE);
-      }
     } else {
       float sc[32];
       if (ep.mode == 1) {
@@ -374,9 +344,8 @@ struct SolveArgs {
   int final_mode;                      // 2: FP32 store into out [R][ny][nx]; 3: predictor-corrector mixing
   float* out;
   int nx, ny;
-  float *gf, *b1, *b2, *bjn;           // mode 3 (see Epi)
+  float* bm;                           // mode 3: B <- w B_solved + (1 - w) B in bm[node * 2 + r]
   float w;
-  int last;
   unsigned long long* gbar;            // grid-barrier counter (zero at launch, reset by the last CTA)
   int* status;
   int barrier_skew;                    // added to the first barrier's target (fault injection; 0)
@@ -691,14 +660,13 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
               if (yn < a.ny) a.out[((int64_t)r * a.ny + yn) * a.nx + xn] = x[j];
             }
           } else {
-            // predictor-corrector mixing into gf[3 + r] (all loads first, then mix and store)
-            float old[CH], prev1[CH];
+            // predictor-corrector mixing into bm[r] (all loads first, then mix and store)
+            float old[CH];
 #pragma unroll
             for (int j = 0; j < CH; ++j) {
               const int yn = ynode(j);
               const int64_t node = (int64_t)yn * a.nx + xn;
-              old[j] = yn < a.ny ? a.gf[node * kGF + 3 + r] : 0.0f;
-              prev1[j] = (a.last && yn < a.ny) ? a.b1[node * 2 + r] : 0.0f;
+              old[j] = yn < a.ny ? a.bm[node * 2 + r] : 0.0f;
             }
             bool bad = false;
 #pragma unroll
@@ -708,12 +676,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
               bad |= !isfinite(x[j]);
               const int64_t node = (int64_t)yn * a.nx + xn;
               const float nb = a.w * x[j] + (1.0f - a.w) * old[j];
-              a.gf[node * kGF + 3 + r] = nb;
-              if (a.last) {
-                a.b2[node * 2 + r] = prev1[j];
-                a.b1[node * 2 + r] = nb;
-                a.bjn[node * 2 + r] = 0.0f;
-              }
+              a.bm[node * 2 + r] = nb;
             }
             if (bad) atomicOr(a.status, DEV_NONFINITE);
           }
@@ -733,6 +696,258 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
                                a.status, abort_f))
       break;
   }
+  // exit arrival: the last CTA through resets the counter for the next launch
+  if (threadIdx.x == 0 && !*abort_f) {
+    const unsigned long long seen = atomicAdd(a.gbar, 1ull);
+    if (seen == (nb0 + 4ull) * gridDim.x - 1ull) atomicExch(a.gbar, 0ull);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- resident fold-matrix solve
+// The same four products for a square folded grid (nx = ny = n, n = 256 or 512) with the
+// operand roles swapped: each CTA owns one block of 128 output slots for the whole launch,
+// so its 128 x n/2 slice of the fold matrix (bf16 hi + lo, 64 or 128 KB) is loaded into
+// shared memory once, while the source phase runs, and only the data operand (BN rows of
+// the previous phase's output) is streamed per tile:
+//   D[s][c] = sum_u F[s][u] X[c][koff + u]   (A = F in shared memory, B = X streamed),
+// with koff = 0 for the odd-index slots (pair sums) and n/2 for the even ones (differences).
+// TMEM lane = output slot s, column = data row c.  The fold of the next operand pairs
+// adjacent columns of one thread (no shuffle), and each thread stores its row of the next
+// operand as contiguous 16-byte runs.  The third product writes its rows in node order, so
+// the last one's output columns are consecutive x nodes.
+template <int BN> struct RsSmem {
+  static constexpr int KB_MAX = 4;                          // folded K = n/2 <= 256
+  static constexpr int F = 0;                               // F_hi blocks 0..3, F_lo blocks 4..7
+  static constexpr int STAGE = 2 * BN * BK * 2;             // X_hi + X_lo rows of one K block
+  static constexpr int RING = 2 * KB_MAX * A_BYTES;
+  static constexpr int BARS = RING + KB_MAX * STAGE;
+  static constexpr int BYTES = BARS + 256 + 1024 /*alignment*/;
+};
+
+// bf16 hi/lo split of 8 values packed for two 16-byte stores.
+__device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * k]), h1 = __float2bfloat16_rn(v[2 * k + 1]);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * k] - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * k + 1] - __bfloat162float(h1));
+    h[k] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    l[k] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Epilogue of one thread's CH consecutive columns (data rows i0 .. i0 + CH - 1 of rhs r) of
+// output slot s.  Modes 0/1 (1: times the 1/lambda table) fold adjacent column pairs into
+// the next operand's row (r, orow) (orow = s, or its node for the third product): pair sums at column v, differences at n/2 + v (the wall
+// pair (0, n/2) keeps x_{n/2} as its sum and 0 as its difference).  Mode 2 stores the
+// solution (rows in node order: columns are consecutive x nodes), mode 3 mixes it into the
+// B_perp record.
+template <int CH>
+__device__ __forceinline__ void rs_epilogue(const SolveArgs& a, int mode, int s, int orow, int r, int i0, float* x,
+                                            __nv_bfloat16* oh, __nv_bfloat16* ol) {
+  const int n = a.nx, H = n / 2;
+  if (mode <= 1) {
+    if (mode == 1) {
+      const float4* sc = reinterpret_cast<const float4*>(a.scale + (int64_t)s * n + i0);
+#pragma unroll
+      for (int q = 0; q < CH / 4; ++q) {
+        const float4 f = __ldg(sc + q);
+        x[4 * q] *= f.x;
+        x[4 * q + 1] *= f.y;
+        x[4 * q + 2] *= f.z;
+        x[4 * q + 3] *= f.w;
+      }
+    }
+    float sum[CH / 2], dif[CH / 2];
+    const int v0 = i0 >> 1;
+#pragma unroll
+    for (int k = 0; k < CH / 2; ++k) {
+      const bool wall = v0 + k == n / 4;
+      sum[k] = wall ? x[2 * k + 1] : x[2 * k] + x[2 * k + 1];
+      dif[k] = wall ? 0.0f : x[2 * k] - x[2 * k + 1];
+    }
+    const int64_t base = ((int64_t)r * n + orow) * n;
+#pragma unroll
+    for (int k = 0; k < CH / 2; k += 8) {
+      uint4 h, l;
+      split8(sum + k, h, l);
+      *reinterpret_cast<uint4*>(oh + base + v0 + k) = h;
+      *reinterpret_cast<uint4*>(ol + base + v0 + k) = l;
+      split8(dif + k, h, l);
+      *reinterpret_cast<uint4*>(oh + base + H + v0 + k) = h;
+      *reinterpret_cast<uint4*>(ol + base + H + v0 + k) = l;
+    }
+  } else if (mode == 2) {
+    const int yn = fold_node(s, n);
+    float4* o = reinterpret_cast<float4*>(a.out + ((int64_t)r * a.ny + yn) * a.nx + i0);
+#pragma unroll
+    for (int q = 0; q < CH / 4; ++q) o[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+  } else {
+    // predictor-corrector mixing into bm[r] (all loads first, then mix and store)
+    const int yn = fold_node(s, n);
+    const int64_t node0 = (int64_t)yn * a.nx + i0;
+    float old[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      old[j] = a.bm[(node0 + j) * 2 + r];
+    }
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      bad |= !isfinite(x[j]);
+      const float nb = a.w * x[j] + (1.0f - a.w) * old[j];
+      a.bm[(node0 + j) * 2 + r] = nb;
+    }
+    if (bad) atomicOr(a.status, DEV_NONFINITE);
+  }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kSolveThreads, 1)
+    k_dst_solve_rs(const __grid_constant__ CUtensorMap fh, const __grid_constant__ CUtensorMap fl,
+                   const __grid_constant__ CUtensorMap x0h, const __grid_constant__ CUtensorMap x0l,
+                   const __grid_constant__ CUtensorMap x1h, const __grid_constant__ CUtensorMap x1l, const SolveArgs a) {
+  using L = RsSmem<BN>;
+  constexpr int STAGES = L::KB_MAX;
+  constexpr int CH = BN / 2;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ int s_abort;
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* basep = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(basep + L::BARS);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+  const uint32_t fbar = smem_u32(bars + 2 * STAGES + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* abort_f = &s_abort;
+  const int n = a.nx, H = n / 2, nk = H / BK, MB = n / BM;
+  const int mb = (int)blockIdx.x % MB, s0 = mb * BM;
+  const int koff = s0 < H ? 0 : H;          // odd slots (first half) contract over the pair sums
+  const int NT = a.R * n / BN;               // data-row tiles per product
+  const int nt0 = (int)blockIdx.x / MB, ntstep = (int)gridDim.x / MB;
+
+  if (threadIdx.x == 0) {
+    for (const CUtensorMap* m : {&fh, &fl, &x0h, &x0l, &x1h, &x1l}) prefetch_map(m);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    mbar_init(fbar, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)(2 * BN))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // this CTA's fold-matrix slice (rows s0 .. s0 + 127, all n/2 columns), resident for the launch
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(fbar, (uint32_t)(2 * nk * A_BYTES));
+    for (int kb = 0; kb < nk; ++kb) {
+      tma_load_2d(base + L::F + kb * A_BYTES, &fh, kb * BK, s0, fbar);
+      tma_load_2d(base + L::F + (STAGES + kb) * A_BYTES, &fl, kb * BK, s0, fbar);
+    }
+  }
+  const unsigned nb0 = a.pre ? 1u : 0u;
+  bool go = true;
+  if (a.pre) {
+    const SinkFold sink{a.op_hi[0], a.op_lo[0], a.nx, a.ny};
+    if (a.pre == 1) solve_sources<SinkFold, SrcMain<float>, 3>(a.sm.gm, sink, a.sm);
+    else solve_sources<SinkFold, SrcBperp<float>, 2>(a.sb.gm, sink, a.sb);
+    go = grid_barrier(a.gbar, (unsigned long long)gridDim.x + (unsigned)a.barrier_skew, a.status, abort_f);
+  }
+  uint32_t kb_run = 0, tiles_run = 0;
+  bool f_ready = false;
+  for (int p = 0; p < 4 && go; ++p) {
+    const CUtensorMap* xh = (p & 1) ? &x1h : &x0h;
+    const CUtensorMap* xl = (p & 1) ? &x1l : &x0l;
+    const int mode = p == 3 ? a.final_mode : (p == 1 ? 1 : 0);
+    for (int nt = nt0; nt < NT; nt += ntstep) {
+      const int c0 = nt * BN;
+      if (warp == 0 && lane == 0) {
+        // data-tile producer: the whole folded K of BN rows, one stage per 64-wide K block
+        for (int kb = 0; kb < nk; ++kb) {
+          const uint32_t g = kb_run + kb;
+          const int s = g % STAGES;
+          const uint32_t st = base + L::RING + s * L::STAGE;
+          const uint32_t fb = full0 + 8 * s;
+          if (g >= (uint32_t)STAGES && !mbar_wait_a(empty0 + 8 * s, ((g / STAGES) - 1) & 1, a.status, abort_f)) break;
+          mbar_expect_tx(fb, L::STAGE);
+          tma_load_2d(st, xh, koff + kb * BK, c0, fb);
+          tma_load_2d(st + BN * BK * 2, xl, koff + kb * BK, c0, fb);
+        }
+      } else if (warp == 1 && lane == 0) {
+        // MMA issuer: A = fold-matrix slice (resident), B = [X_hi; X_lo] (N = 2 BN) and X_hi
+        bool ok = f_ready || mbar_wait_a(fbar, 0, a.status, abort_f);
+        f_ready = ok;
+        for (int kb = 0; ok && kb < nk; ++kb) {
+          const uint32_t g = kb_run + kb;
+          const int s = g % STAGES;
+          if (!mbar_wait_a(full0 + 8 * s, (g / STAGES) & 1, a.status, abort_f)) break;
+          tc_fence_after();
+          const uint32_t st = base + L::RING + s * L::STAGE;
+          const uint64_t ah = desc_k_sw128(base + L::F + kb * A_BYTES);
+          const uint64_t al = desc_k_sw128(base + L::F + (STAGES + kb) * A_BYTES);
+          const uint64_t bh = desc_k_sw128(st);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t off = (uint64_t)((k * 32) >> 4);
+            mma_bf16(tmem, ah + off, bh + off, Cfg<BN>::IDESC2, (kb | k) != 0 ? 1u : 0u);
+            mma_bf16(tmem, al + off, bh + off, Cfg<BN>::IDESC, 1u);
+          }
+          mma_commit(empty0 + 8 * s);
+        }
+        mma_commit(done);
+      }
+      __syncwarp();
+      mbar_wait_a(done, tiles_run & 1, a.status, abort_f);
+      tc_fence_after();
+      // epilogue: TMEM lane = slot s0 + row, the two warpgroups take one half of the columns each
+      {
+        const int row = (warp & 3) * 32 + lane;
+        const int s = s0 + row;
+        const int half = warp >> 2;
+        const int r = c0 / n;
+        const int i0 = c0 - r * n + half * CH;
+        float x[CH];
+        tmem_ld_pair<BN, CH>(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * CH), x);
+        const int orow = p == 2 ? fold_node(s, n) : s;
+        if (!*abort_f)
+          rs_epilogue<CH>(a, mode, s, orow, r, i0, x, a.op_hi[(p + 1) & 1], a.op_lo[(p + 1) & 1]);
+      }
+      kb_run += nk;
+      ++tiles_run;
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (*abort_f) break;
+    }
+    if (*abort_f) break;
+    if (p < 3 && !grid_barrier(a.gbar,
+                               (unsigned long long)(nb0 + p + 1) * gridDim.x +
+                                   (nb0 == 0 && p == 0 ? (unsigned)a.barrier_skew : 0u),
+                               a.status, abort_f))
+      break;
+  }
+  // the fold-matrix load must have landed before the CTA leaves (a CTA without tiles, or one
+  // that gave up, may not have waited for it): a bounded wait that ignores the abort flag
+  if (threadIdx.x == 0) mbar_wait(fbar, 0, a.status);
   // exit arrival: the last CTA through resets the counter for the next launch
   if (threadIdx.x == 0 && !*abort_f) {
     const unsigned long long seen = atomicAdd(a.gbar, 1ull);
@@ -827,6 +1042,11 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
     return 1;
   const char* bn = std::getenv("HQ_SOLVE_BN");
   t.wide_only = bn != nullptr && std::atoi(bn) == 64;
+  const char* nors = std::getenv("HQ_NO_RS");
+  t.rs = g->fold && g->nx == g->ny && (g->nx == 256 || g->nx == 512) && !(nors && nors[0] == '1');
+  if (t.rs && (!size_solve(k_dst_solve_rs<64>, RsSmem<64>::BYTES, t.rs_ctas[0]) ||
+               !size_solve(k_dst_solve_rs<32>, RsSmem<32>::BYTES, t.rs_ctas[1])))
+    return 1;
   const uint64_t nxp = g->nxp, nyp = g->nyp;
   int bad = 0;
   bad |= make_map(enc, &t.a0_hi, g->op_hi[0], kMaxRhs * nyp, nxp, err);
@@ -842,6 +1062,16 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
     bad |= make_map(enc, &t.by_hi[i], g->sy_hi, nyp, ky, err, bn);
     bad |= make_map(enc, &t.by_lo[i], g->sy_lo, nyp, ky, err, bn);
     bad |= make_map_plain(enc, &t.scale[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->f32_scale, nyp, nxp, BM, bn, err);
+  }
+  if (t.rs) {
+    bad |= make_map(enc, &t.rf_hi, g->sx_hi, nxp, kx, err, 128);
+    bad |= make_map(enc, &t.rf_lo, g->sx_lo, nxp, kx, err, 128);
+    for (int o = 0; o < 2; ++o)
+      for (int i = 0; i < 2; ++i) {
+        const uint32_t bn = i == 0 ? 64 : 32;
+        bad |= make_map(enc, &t.rx_hi[o][i], g->op_hi[o], kMaxRhs * nyp, nxp, err, bn);
+        bad |= make_map(enc, &t.rx_lo[o][i], g->op_lo[o], kMaxRhs * nyp, nxp, err, bn);
+      }
   }
   return bad;
 }
@@ -872,18 +1102,36 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s, 
   a.out = reinterpret_cast<float*>(g->solved);
   a.nx = g->nx;
   a.ny = g->ny;
-  a.gf = reinterpret_cast<float*>(g->gf);
-  a.b1 = reinterpret_cast<float*>(g->bprev1);
-  a.b2 = reinterpret_cast<float*>(g->bprev2);
-  a.bjn = reinterpret_cast<float*>(g->bjn);
+  a.bm = reinterpret_cast<float*>(g->bm);
   a.w = (float)g->d.pc_mix;
-  a.last = last;
   a.gbar = g->d_gbar;
   a.status = g->d_status;
   a.barrier_skew = g->fault_barrier;
   a.pre = pre;
   if (pre == 1) a.sm = src_main_of<float>(g, dep_cur);
   if (pre == 2) a.sb = src_bperp_of<float>(g, dep_cur, dep_prev, chi_prev, last);
+  if (t.rs) {
+    // resident fold-matrix solve: MB slot blocks x (R n / BN) data-row tiles per product; the
+    // grid is a multiple of MB (a CTA keeps its slot block)
+    const int n = g->nx, MB = n / BM;
+    const int tiles32 = MB * (R * n / 32);
+    const bool narrow = !t.wide_only && tiles32 <= t.rs_ctas[1];
+    const int v = narrow ? 1 : 0;
+    const int tiles_v = MB * (R * n / (narrow ? 32 : 64));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min(tiles_v, t.rs_ctas[v] / MB * MB));
+    cfg.blockDim = dim3(kSolveThreads);
+    cfg.dynamicSmemBytes = narrow ? RsSmem<32>::BYTES : RsSmem<64>::BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, narrow ? k_dst_solve_rs<32> : k_dst_solve_rs<64>, t.rf_hi, t.rf_lo, t.rx_hi[0][v],
+                       t.rx_lo[0][v], t.rx_hi[1][v], t.rx_lo[1][v], a);
+    return;
+  }
   // tiles of one product (the larger of the x and y products) at N-tile width bn
   auto tiles = [&](int bn) {
     return std::max(R * (g->nyp / BM) * (g->nxp / bn), R * (g->nxp / BM) * (g->nyp / bn));
@@ -908,7 +1156,7 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s, 
 }  // namespace
 
 // B_perp solve with the predictor-corrector mixing fused into the last product's epilogue:
-// sources (split, 2 rhs) in op[0] -> gf[3..4] <- w B + (1 - w) gf[3..4] (+ ring shift if last).
+// sources (split, 2 rhs) in op[0] -> bm <- w B + (1 - w) bm.
 void dst_solve_tc_bmix(hq_grid_s* g, int last, cudaStream_t s) { solve_fused(g, 2, 3, last, s); }
 
 // sources (split) in op[0] -> FP32 solution in g->solved [R][ny][nx]
@@ -916,7 +1164,7 @@ void dst_solve_tc(hq_grid_s* g, int R, cudaStream_t s) { solve_fused(g, R, 2, 0,
 
 // The same with the source kernels folded into the launch as its first phase: psi, Ez, Bz of
 // the deposit record dep -> g->solved; the B_perp sources of the predictor-corrector (which
-// clear the trial J_perp and, on the last iteration, reset dep_prev) -> mixing into gf.
+// clear the trial J_perp and, on the last iteration, reset dep_prev) -> mixing into bm.
 void dst_solve_tc_main(hq_grid_s* g, const void* dep, cudaStream_t s) { solve_fused(g, 3, 2, 0, s, 1, dep); }
 void dst_solve_tc_bmix_src(hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int last, cudaStream_t s) {
   solve_fused(g, 2, 3, last, s, 2, cur, prev, chi_prev);

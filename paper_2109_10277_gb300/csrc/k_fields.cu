@@ -50,11 +50,12 @@ __global__ void k_src_copy(const T* __restrict__ src, int nrhs, Geom gm, Sink si
   });
 }
 
-// psi -> psi array and gf[0..1] = -grad psi; Ez -> gf[2]; Bz -> gf[5]; gf[3..4] = the
-// predictor-corrector guess B(i) = 2 B(i-1) - B(i-2).
+// psi -> psi array; gf = (ExmBy, EypBx) = -grad psi, Ez, Bz; bm = the predictor-corrector
+// guess B(i) = 2 B(i-1) - B(i-2).  On entry bm still holds the converged B(i-1) of the previous
+// slice (taken as zero on the first slice) and b1 holds B(i-2); on exit b1 holds B(i-1).
 template <typename T>
-__global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, const V2<T>* __restrict__ b1,
-                              const V2<T>* __restrict__ b2, Geom gm, int* status) {
+__global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, V2<T>* bm, V2<T>* b1, int first, Geom gm,
+                              int* status) {
   pdl_trigger();
   pdl_wait();
   const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
@@ -71,63 +72,33 @@ __global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, const V2
   const T p = res[o], ez = res[nn + o], bz = res[2 * nn + o];
   if (!(isfinite(p) && isfinite(ez) && isfinite(bz))) atomicOr(status, DEV_NONFINITE);
   psi[o] = p;
-  const V2<T> p1 = b1[o], p2 = b2[o];
   T* q = gf + o * kGF;
   q[0] = ex;
   q[1] = ey;
   q[2] = ez;
-  q[3] = T(2) * p1.a - p2.a;
-  q[4] = T(2) * p1.b - p2.b;
-  q[5] = bz;
+  q[3] = bz;
+  const V2<T> p1 = first ? V2<T>{T(0), T(0)} : bm[o];
+  const V2<T> p2 = b1[o];
+  bm[o] = V2<T>{T(2) * p1.a - p2.a, T(2) * p1.b - p2.b};
+  b1[o] = p1;
 }
 
-// B <- w B_solved + (1 - w) B  (predictor-corrector mixing), into gf[3..4].  After the
-// last iteration also B(i-2) <- B(i-1), B(i-1) <- B and the beam J_perp of slice i+1 is
-// cleared for the next slice's beam deposit.
+// B <- w B_solved + (1 - w) B  (predictor-corrector mixing), into bm.
 template <typename T>
-__global__ void k_finish_bperp(const T* __restrict__ res, T* gf, int64_t nn, T w, int* status, int last,
-                               V2<T>* b1, V2<T>* b2, V2<T>* bjn) {
+__global__ void k_finish_bperp(const T* __restrict__ res, V2<T>* bm, int64_t nn, T w, int* status) {
   pdl_trigger();
   pdl_wait();
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nn) return;
   const T bx = res[o], by = res[nn + o];
   if (!(isfinite(bx) && isfinite(by))) atomicOr(status, DEV_NONFINITE);
-  T* q = gf + o * kGF;
-  const T nbx = w * bx + (T(1) - w) * q[3];
-  const T nby = w * by + (T(1) - w) * q[4];
-  q[3] = nbx;
-  q[4] = nby;
-  if (last) {
-    b2[o] = b1[o];
-    b1[o] = V2<T>{nbx, nby};
-    bjn[o] = V2<T>{T(0), T(0)};
-  }
-}
-
-// Initial guess B(i) = 2 B(i-1) - B(i-2).
-template <typename T>
-__global__ void k_bguess(const V2<T>* b1, const V2<T>* b2, T* gf, int64_t nn) {
-  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= nn) return;
-  const V2<T> p1 = b1[o], p2 = b2[o];
-  T* q = gf + o * kGF;
-  q[3] = T(2) * p1.a - p2.a;
-  q[4] = T(2) * p1.b - p2.b;
-}
-
-template <typename T>
-__global__ void k_bshift(V2<T>* b1, V2<T>* b2, const T* gf, int64_t nn) {
-  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= nn) return;
-  b2[o] = b1[o];
-  const T* q = gf + o * kGF;
-  b1[o] = V2<T>{q[3], q[4]};
+  const V2<T> b = bm[o];
+  bm[o] = V2<T>{w * bx + (T(1) - w) * b.a, w * by + (T(1) - w) * b.b};
 }
 
 template <typename T>
 __global__ void k_store(hq_field_out out, int64_t base, const V4<T>* dep, const float* ps, const T* chi,
-                        const T* psi, const T* gf, int64_t nn) {
+                        const T* psi, const T* gf, const V2<T>* bm, int64_t nn) {
   pdl_trigger();
   pdl_wait();
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -146,9 +117,9 @@ __global__ void k_store(hq_field_out out, int64_t base, const V4<T>* dep, const 
   if (out.exmby) reinterpret_cast<T*>(out.exmby)[t] = q[0];
   if (out.eypbx) reinterpret_cast<T*>(out.eypbx)[t] = q[1];
   if (out.ez) reinterpret_cast<T*>(out.ez)[t] = q[2];
-  if (out.bx) reinterpret_cast<T*>(out.bx)[t] = q[3];
-  if (out.by) reinterpret_cast<T*>(out.by)[t] = q[4];
-  if (out.bz) reinterpret_cast<T*>(out.bz)[t] = q[5];
+  if (out.bx) reinterpret_cast<T*>(out.bx)[t] = bm[o].a;
+  if (out.by) reinterpret_cast<T*>(out.by)[t] = bm[o].b;
+  if (out.bz) reinterpret_cast<T*>(out.bz)[t] = q[3];
 }
 
 template <typename T>
@@ -188,33 +159,22 @@ void launch_src_copy(const hq_grid_s* g, const void* src, int nrhs, cudaStream_t
   });
 }
 template <typename T>
-void launch_finish_main(const hq_grid_s* g, const void* res, cudaStream_t s) {
+void launch_finish_main(const hq_grid_s* g, const void* res, int first, cudaStream_t s) {
   launch_pdl(k_finish_main<T>, grid2d(g), 128, 0, s, reinterpret_cast<const T*>(res), reinterpret_cast<T*>(g->psi),
-             reinterpret_cast<T*>(g->gf), reinterpret_cast<const V2<T>*>(g->bprev1),
-             reinterpret_cast<const V2<T>*>(g->bprev2), g->geom, g->d_status);
+             reinterpret_cast<T*>(g->gf), reinterpret_cast<V2<T>*>(g->bm), reinterpret_cast<V2<T>*>(g->bprev1), first,
+             g->geom, g->d_status);
 }
 template <typename T>
-void launch_finish_bperp(const hq_grid_s* g, const void* res, int last, cudaStream_t s) {
+void launch_finish_bperp(const hq_grid_s* g, const void* res, cudaStream_t s) {
   launch_pdl(k_finish_bperp<T>, blocks_for(g->nnode), kThreads, 0, s, reinterpret_cast<const T*>(res),
-             reinterpret_cast<T*>(g->gf), g->nnode, T(g->d.pc_mix), g->d_status, last,
-             reinterpret_cast<V2<T>*>(g->bprev1), reinterpret_cast<V2<T>*>(g->bprev2), reinterpret_cast<V2<T>*>(g->bjn));
-}
-template <typename T>
-void launch_bguess(const hq_grid_s* g, cudaStream_t s) {
-  k_bguess<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(reinterpret_cast<const V2<T>*>(g->bprev1),
-                                                       reinterpret_cast<const V2<T>*>(g->bprev2),
-                                                       reinterpret_cast<T*>(g->gf), g->nnode);
-}
-template <typename T>
-void launch_bshift(const hq_grid_s* g, cudaStream_t s) {
-  k_bshift<T><<<blocks_for(g->nnode), kThreads, 0, s>>>(reinterpret_cast<V2<T>*>(g->bprev1), reinterpret_cast<V2<T>*>(g->bprev2),
-                                                       reinterpret_cast<const T*>(g->gf), g->nnode);
+             reinterpret_cast<V2<T>*>(g->bm), g->nnode, T(g->d.pc_mix), g->d_status);
 }
 template <typename T>
 void launch_store(const hq_grid_s* g, const hq_field_out* out, int64_t slot, const void* dep, const void* chi, cudaStream_t s) {
   launch_pdl(k_store<T>, blocks_for(g->nnode), kThreads, 0, s, *out, slot * g->nnode,
              reinterpret_cast<const V4<T>*>(dep), static_cast<const float*>(psrc_of(g, dep)),
              reinterpret_cast<const T*>(chi), reinterpret_cast<const T*>(g->psi), reinterpret_cast<const T*>(g->gf),
+             reinterpret_cast<const V2<T>*>(g->bm),
              g->nnode);
 }
 template <typename T>
@@ -227,10 +187,8 @@ void launch_zero(void* p, int64_t n, cudaStream_t s) {
   template void launch_src_main<T>(const hq_grid_s*, const void*, cudaStream_t);               \
   template void launch_src_bperp<T>(const hq_grid_s*, const void*, void*, void*, int, cudaStream_t); \
   template void launch_src_copy<T>(const hq_grid_s*, const void*, int, cudaStream_t);          \
-  template void launch_finish_main<T>(const hq_grid_s*, const void*, cudaStream_t);            \
-  template void launch_finish_bperp<T>(const hq_grid_s*, const void*, int, cudaStream_t);      \
-  template void launch_bguess<T>(const hq_grid_s*, cudaStream_t);                              \
-  template void launch_bshift<T>(const hq_grid_s*, cudaStream_t);                              \
+  template void launch_finish_main<T>(const hq_grid_s*, const void*, int, cudaStream_t);       \
+  template void launch_finish_bperp<T>(const hq_grid_s*, const void*, cudaStream_t);           \
   template void launch_store<T>(const hq_grid_s*, const hq_field_out*, int64_t, const void*, const void*, cudaStream_t); \
   template void launch_zero<T>(void*, int64_t, cudaStream_t);
 HQ_INST(float)

@@ -41,23 +41,24 @@ __device__ __forceinline__ void atomic_add2(V2<double>* p, double a, double b) {
 // Six gathered fields: ExmBy, EypBx, Ez, Bx, By, Bz.
 template <typename T> struct F6 { T v[6]; };
 
-__device__ __forceinline__ void load_gf(const float* q, float* o) {
+// The six fields of one node: ExmBy, EypBx, Ez, Bz from the gather record, Bx, By from the
+// B_perp record; o = (ExmBy, EypBx, Ez, Bx, By, Bz).
+__device__ __forceinline__ void load_node(const float* q, const float* b, float* o) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(q));
-  const float2 b = __ldg(reinterpret_cast<const float2*>(q + 4));
-  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
+  const float2 c = __ldg(reinterpret_cast<const float2*>(b));
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = c.x; o[4] = c.y; o[5] = a.w;
 }
-__device__ __forceinline__ void load_gf(const double* q, double* o) {
-#pragma unroll
-  for (int c = 0; c < 6; c += 2) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(q + c));
-    o[c] = a.x; o[c + 1] = a.y;
-  }
+__device__ __forceinline__ void load_node(const double* q, const double* b, double* o) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(q));
+  const double2 a2 = __ldg(reinterpret_cast<const double2*>(q + 2));
+  const double2 c = __ldg(reinterpret_cast<const double2*>(b));
+  o[0] = a.x; o[1] = a.y; o[2] = a2.x; o[3] = c.x; o[4] = c.y; o[5] = a2.y;
 }
 
 // Interpolate the packed fields at a particle whose x/y stencils start at ix0/iy0.
 template <int P, typename T>
-__device__ __forceinline__ F6<T> gather6(const T* __restrict__ gf, int nx, int ny, int ix0, int iy0,
-                                         const T* wx, const T* wy) {
+__device__ __forceinline__ F6<T> gather6(const T* __restrict__ gf, const T* __restrict__ bm, int nx, int ny, int ix0,
+                                         int iy0, const T* wx, const T* wy) {
   F6<T> F;
 #pragma unroll
   for (int c = 0; c < 6; ++c) F.v[c] = T(0);
@@ -70,7 +71,8 @@ __device__ __forceinline__ F6<T> gather6(const T* __restrict__ gf, int nx, int n
       const int ix = ix0 + a;
       if (!in_interior(ix, nx)) continue;
       T q[6];
-      load_gf(gf + ((int64_t)iy * nx + ix) * kGF, q);
+      const int64_t node = (int64_t)iy * nx + ix;
+      load_node(gf + node * kGF, bm + node * 2, q);
       const T wgt = wx[a] * wy[b];
 #pragma unroll
       for (int c = 0; c < 6; ++c) F.v[c] += wgt * q[c];
@@ -261,7 +263,7 @@ __global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* 
 // Gather with B^(m-1), AB5 trial step to slice i+1, deposit J_perp of the trial
 // particles into tj (Sec. 3.2, predictor-corrector field solver).
 template <int P, typename T, bool CACHE>
-__global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf,
+__global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf, const T* __restrict__ bm,
                                                          V2<T>* tj, int slice, double guard) {
   pdl_trigger();
   pdl_wait();
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
     opp = T(1.0 + pl.psi[p]);
   }
   const T ux = pl.ux[p], uy = pl.uy[p];
-  const F6<T> F = gather6<P, T>(gf, gm.nx, gm.ny, ix0, iy0, wx, wy);
+  const F6<T> F = gather6<P, T>(gf, bm, gm.nx, gm.ny, ix0, iy0, wx, wy);
   T f[5];
   derivs<T>(ux, uy, opp, F, f);
   const T dz = CACHE ? T(gm.f_dz) : T(gm.dzeta);
@@ -542,7 +544,7 @@ template <int P, typename T> constexpr int final_min_blocks() {
 }
 
 template <int P, typename T, bool CACHE>
-__global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf,
+__global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf, const T* __restrict__ bm,
                                                          V4<T>* dep, T* chi, float* ps, PpcInfo pc, int slice,
                                                          double guard, unsigned long long* removed) {
   pdl_trigger();
@@ -570,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pa
     opp = T(1.0 + pl.psi[p]);
   }
   const T ux = pl.ux[p], uy = pl.uy[p];
-  const F6<T> F = gather6<P, T>(gf, gm.nx, gm.ny, ix0, iy0, wx, wy);
+  const F6<T> F = gather6<P, T>(gf, bm, gm.nx, gm.ny, ix0, iy0, wx, wy);
   T f[5];
   derivs<T>(ux, uy, opp, F, f);
   T comb[5];
@@ -680,14 +682,15 @@ template <typename T>
 void launch_trial_pass(const hq_grid_s* g, int slice, cudaStream_t s) {
   const unsigned nb = blocks_for(g->np);
   const T* gf = reinterpret_cast<const T*>(g->gf);
+  const T* bm = reinterpret_cast<const T*>(g->bm);
   V2<T>* tj = reinterpret_cast<V2<T>*>(g->tj);
   constexpr bool C = sizeof(T) == 4;
   const double gd = g->d.psi_guard;
   switch (g->d.shape_order) {
-    case 0: launch_pdl(k_trial_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
-    case 1: launch_pdl(k_trial_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
-    case 2: launch_pdl(k_trial_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
-    default: launch_pdl(k_trial_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, tj, slice, gd); break;
+    case 0: launch_pdl(k_trial_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, tj, slice, gd); break;
+    case 1: launch_pdl(k_trial_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, tj, slice, gd); break;
+    case 2: launch_pdl(k_trial_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, tj, slice, gd); break;
+    default: launch_pdl(k_trial_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, tj, slice, gd); break;
   }
 }
 
@@ -695,6 +698,7 @@ template <typename T>
 void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cudaStream_t s) {
   const unsigned nb = blocks_for(g->np);
   const T* gf = reinterpret_cast<const T*>(g->gf);
+  const T* bm = reinterpret_cast<const T*>(g->bm);
   V4<T>* d = reinterpret_cast<V4<T>*>(dep);
   T* c = reinterpret_cast<T*>(chi);
   constexpr bool C = sizeof(T) == 4;
@@ -710,10 +714,10 @@ void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cuda
   pc.finv_x = (float)pc.inv_x;
   pc.finv_y = (float)pc.inv_y;
   switch (g->d.shape_order) {
-    case 0: launch_pdl(k_final_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, pc, slice, gd, rm); break;
-    case 1: launch_pdl(k_final_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, pc, slice, gd, rm); break;
-    case 2: launch_pdl(k_final_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, pc, slice, gd, rm); break;
-    default: launch_pdl(k_final_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, d, c, ps, pc, slice, gd, rm); break;
+    case 0: launch_pdl(k_final_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, d, c, ps, pc, slice, gd, rm); break;
+    case 1: launch_pdl(k_final_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, d, c, ps, pc, slice, gd, rm); break;
+    case 2: launch_pdl(k_final_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, d, c, ps, pc, slice, gd, rm); break;
+    default: launch_pdl(k_final_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, d, c, ps, pc, slice, gd, rm); break;
   }
 }
 

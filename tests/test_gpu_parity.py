@@ -547,8 +547,8 @@ def test_sources_in_solve_launch_match_separate_kernels(hq, monkeypatch):
     """FP32: the psi/Ez/Bz and B_perp sources formed in the solve launch's first phase give
     the same sweep as separate source kernels (HQ_SEPARATE_SRC=1), within the run-to-run
     floor of the FP32 atomics (two sweeps of the same build)."""
-    g = I.scaled_grid(I.grid_params("blowout512"), 128, 128, 96)
-    beams = I.workload_beams("blowout512", n_driver=100_000)
+    g = I.scaled_grid(I.grid_params("linear64"), 128, 128, 64)
+    beams = [I.random_beam(100_000, 0.3, 0.3, 1.0, 0.5, energy_spread=1e-3)]
     outs = {}
     for mode in ("fused", "fused2", "separate"):
         if mode == "separate":
@@ -559,4 +559,24 @@ def test_sources_in_solve_launch_match_separate_kernels(hq, monkeypatch):
         floor = float(peak_err(outs["fused2"][k], outs["fused"][k]).max())
         dev = float(peak_err(outs["separate"][k], outs["fused"][k]).max())
         print(f"fused vs separate sources {k}: {dev:.1e} (run-to-run {floor:.1e})")
+        assert dev <= max(10 * floor, 1e-6), (k, dev, floor)
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_resident_fold_matrix_solve_matches_streamed(hq, monkeypatch, n):
+    """FP32 square grids of 256 and 512 cells run the solve that keeps each CTA's slice of the
+    fold matrix in shared memory; it gives the same sweep as the solve that streams it
+    (HQ_NO_RS=1), within the run-to-run floor of the FP32 atomics."""
+    g = I.scaled_grid(I.grid_params("linear64"), n, n, 64)
+    beams = [I.random_beam(100_000, 0.3, 0.3, 1.0, 0.5, energy_spread=1e-3)]
+    outs = {}
+    for mode in ("rs", "rs2", "streamed"):
+        if mode == "streamed":
+            monkeypatch.setenv("HQ_NO_RS", "1")
+        outs[mode] = run_gpu(hq, g, beams, "fp32", fields=("ez", "psi", "bx"))[0]
+        monkeypatch.delenv("HQ_NO_RS", raising=False)
+    for k in ("ez", "psi", "bx"):
+        floor = float(peak_err(outs["rs2"][k], outs["rs"][k]).max())
+        dev = float(peak_err(outs["streamed"][k], outs["rs"][k]).max())
+        print(f"n={n} resident vs streamed fold matrix {k}: {dev:.1e} (run-to-run {floor:.1e})")
         assert dev <= max(10 * floor, 1e-6), (k, dev, floor)
