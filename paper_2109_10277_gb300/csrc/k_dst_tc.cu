@@ -745,26 +745,18 @@ __device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
 }
 
 // Epilogue of one thread's CH consecutive columns (data rows i0 .. i0 + CH - 1 of rhs r) of
-// output slot s.  Modes 0/1 (1: times the 1/lambda table) fold adjacent column pairs into
+// output slot s.  Modes 0/1 (1: times the 1/lambda factors sc) fold adjacent column pairs into
 // the next operand's row (r, orow) (orow = s, or its node for the third product): pair sums at column v, differences at n/2 + v (the wall
 // pair (0, n/2) keeps x_{n/2} as its sum and 0 as its difference).  Mode 2 stores the
-// solution (rows in node order: columns are consecutive x nodes), mode 3 mixes it into the
-// B_perp record.
+// solution (rows in node order: columns are consecutive x nodes); mode 3 is rs_mix.
 template <int CH>
 __device__ __forceinline__ void rs_epilogue(const SolveArgs& a, int mode, int s, int orow, int r, int i0, float* x,
-                                            __nv_bfloat16* oh, __nv_bfloat16* ol) {
+                                            const float* sc, __nv_bfloat16* oh, __nv_bfloat16* ol) {
   const int n = a.nx, H = n / 2;
   if (mode <= 1) {
     if (mode == 1) {
-      const float4* sc = reinterpret_cast<const float4*>(a.scale + (int64_t)s * n + i0);
 #pragma unroll
-      for (int q = 0; q < CH / 4; ++q) {
-        const float4 f = __ldg(sc + q);
-        x[4 * q] *= f.x;
-        x[4 * q + 1] *= f.y;
-        x[4 * q + 2] *= f.z;
-        x[4 * q + 3] *= f.w;
-      }
+      for (int j = 0; j < CH; ++j) x[j] *= sc[j];
     }
     float sum[CH / 2], dif[CH / 2];
     const int v0 = i0 >> 1;
@@ -790,24 +782,90 @@ __device__ __forceinline__ void rs_epilogue(const SolveArgs& a, int mode, int s,
     float4* o = reinterpret_cast<float4*>(a.out + ((int64_t)r * a.ny + yn) * a.nx + i0);
 #pragma unroll
     for (int q = 0; q < CH / 4; ++q) o[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-  } else {
-    // predictor-corrector mixing into bm[r] (all loads first, then mix and store)
-    const int yn = fold_node(s, n);
-    const int64_t node0 = (int64_t)yn * a.nx + i0;
-    float old[CH];
-#pragma unroll
-    for (int j = 0; j < CH; ++j) {
-      old[j] = a.bm[(node0 + j) * 2 + r];
-    }
-    bool bad = false;
-#pragma unroll
-    for (int j = 0; j < CH; ++j) {
-      bad |= !isfinite(x[j]);
-      const float nb = a.w * x[j] + (1.0f - a.w) * old[j];
-      a.bm[(node0 + j) * 2 + r] = nb;
-    }
-    if (bad) atomicOr(a.status, DEV_NONFINITE);
   }
+}
+
+// Source phase of the resident fold-matrix solve (square folded grid, n <= 512): a CTA takes
+// whole rows (RPP per pass, all their reads issued first), its threads read and evaluate the
+// sources at consecutive nodes of a row (coalesced), stage them in shared memory S
+// ([RPP rows][NR][n] floats), and then write the folded pairs (x_a + x_b, x_a - x_b) of
+// consecutive folded columns.
+template <typename F, int NR>
+__device__ __forceinline__ void solve_sources_rows(const Geom& gm, const F& f, const SinkFold& sink, float* S) {
+  constexpr int NPT = 2;   // nodes per thread per row (n <= 2 x 256)
+  constexpr int RPP = 4;   // rows per pass
+  const int n = gm.nx, w = n / 2;
+  for (int sy0 = blockIdx.x; sy0 < gm.ny; sy0 += RPP * gridDim.x) {
+    typename F::In in[RPP][NPT];
+    int iy[RPP];
+#pragma unroll
+    for (int q = 0; q < RPP; ++q) {
+      const int sy = sy0 + q * gridDim.x;
+      iy[q] = sy < gm.ny ? fold_node(sy, gm.ny) : -1;
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const int x = threadIdx.x + k * kSolveThreads;
+        in[q][k] = (iy[q] >= 0 && x < n) ? f.load(iy[q], x) : typename F::In{};
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPP; ++q) {
+      if (iy[q] < 0) continue;
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const int x = threadIdx.x + k * kSolveThreads;
+        if (x >= n) continue;
+        float v[NR];
+        f.eval(iy[q], x, in[q][k], v);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) S[(q * NR + r) * n + x] = v[r];
+        if constexpr (F::kEffects) f.effects(iy[q], x);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RPP; ++q) {
+      if (iy[q] < 0) continue;
+      const int sy = sy0 + q * gridDim.x;
+      for (int u = threadIdx.x; u < w; u += kSolveThreads) {
+        int xa, xb;
+        fold_pair(u, n, xa, xb);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) sink.put_pair(r, sy, u, S[(q * NR + r) * n + xa], S[(q * NR + r) * n + xb]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Predictor-corrector mixing B <- w B_solved + (1 - w) B of one tile (128 slots of y x BN
+// consecutive x nodes from xb, component r) staged in shared memory ([128][BN + 1]): element
+// e = (row, j) is taken by thread e mod 256, so a warp covers consecutive x nodes of one row;
+// up to sixteen elements' loads are issued before their stores.
+template <int BN>
+__device__ __forceinline__ void rs_mix(const SolveArgs& a, const float* tile, int s0, int r, int xb) {
+  constexpr int LD = BN + 1, NE = BM * BN, UN = NE / kSolveThreads < 16 ? NE / kSolveThreads : 16;
+  const int n = a.nx;
+  bool bad = false;
+  for (int e0 = threadIdx.x; e0 < NE; e0 += UN * kSolveThreads) {
+    float v[UN], old[UN];
+    int64_t at[UN];
+#pragma unroll
+    for (int k = 0; k < UN; ++k) {
+      const int e = e0 + k * kSolveThreads;
+      const int row = e / BN, j = e - row * BN;
+      v[k] = e < NE ? tile[row * LD + j] : 0.0f;
+      at[k] = e < NE ? ((int64_t)fold_node(s0 + row, n) * a.nx + xb + j) * 2 + r : -1;
+      old[k] = e < NE ? a.bm[at[k]] : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < UN; ++k) {
+      if (at[k] < 0) continue;
+      bad |= !isfinite(v[k]);
+      a.bm[at[k]] = a.w * v[k] + (1.0f - a.w) * old[k];
+    }
+  }
+  if (bad) atomicOr(a.status, DEV_NONFINITE);
 }
 
 template <int BN>
@@ -867,9 +925,11 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
   const unsigned nb0 = a.pre ? 1u : 0u;
   bool go = true;
   if (a.pre) {
+    // (the stage ring is idle until the first product: it holds the staged sources)
     const SinkFold sink{a.op_hi[0], a.op_lo[0], a.nx, a.ny};
-    if (a.pre == 1) solve_sources<SinkFold, SrcMain<float>, 3>(a.sm.gm, sink, a.sm);
-    else solve_sources<SinkFold, SrcBperp<float>, 2>(a.sb.gm, sink, a.sb);
+    float* S = reinterpret_cast<float*>(basep + L::RING);   // 4 rows x 3 x 512 floats = 24 KB
+    if (a.pre == 1) solve_sources_rows<SrcMain<float>, 3>(a.sm.gm, a.sm, sink, S);
+    else solve_sources_rows<SrcBperp<float>, 2>(a.sb.gm, a.sb, sink, S);
     go = grid_barrier(a.gbar, (unsigned long long)gridDim.x + (unsigned)a.barrier_skew, a.status, abort_f);
   }
   uint32_t kb_run = 0, tiles_run = 0;
@@ -916,20 +976,42 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
         mma_commit(done);
       }
       __syncwarp();
+      // epilogue: TMEM lane = slot s0 + row, the two warpgroups take one half of the columns each
+      const int row = (warp & 3) * 32 + lane;
+      const int s = s0 + row;
+      const int half = warp >> 2;
+      const int r = c0 / n;
+      const int i0 = c0 - r * n + half * CH;
+      float sc[CH];   // the 1/lambda factors of this thread's elements, read while the MMAs run
+      if (mode == 1) {
+        const float4* q = reinterpret_cast<const float4*>(a.scale + (int64_t)s * n + i0);
+#pragma unroll
+        for (int k = 0; k < CH / 4; ++k) {
+          const float4 f = __ldg(q + k);
+          sc[4 * k] = f.x;
+          sc[4 * k + 1] = f.y;
+          sc[4 * k + 2] = f.z;
+          sc[4 * k + 3] = f.w;
+        }
+      }
       mbar_wait_a(done, tiles_run & 1, a.status, abort_f);
       tc_fence_after();
-      // epilogue: TMEM lane = slot s0 + row, the two warpgroups take one half of the columns each
       {
-        const int row = (warp & 3) * 32 + lane;
-        const int s = s0 + row;
-        const int half = warp >> 2;
-        const int r = c0 / n;
-        const int i0 = c0 - r * n + half * CH;
         float x[CH];
         tmem_ld_pair<BN, CH>(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * CH), x);
         const int orow = p == 2 ? fold_node(s, n) : s;
-        if (!*abort_f)
-          rs_epilogue<CH>(a, mode, s, orow, r, i0, x, a.op_hi[(p + 1) & 1], a.op_lo[(p + 1) & 1]);
+        if (mode == 3) {
+          // predictor-corrector mixing into bm[node][r]: the tile goes through shared memory (the
+          // drained stage ring) so that a warp updates consecutive nodes of one row
+          constexpr int LD = BN + 1;
+          float* tile = reinterpret_cast<float*>(basep + L::RING);
+#pragma unroll
+          for (int j = 0; j < CH; ++j) tile[row * LD + half * CH + j] = x[j];
+          __syncthreads();
+          if (!*abort_f) rs_mix<BN>(a, tile, s0, r, c0 - r * n);
+        } else if (!*abort_f) {
+          rs_epilogue<CH>(a, mode, s, orow, r, i0, x, sc, a.op_hi[(p + 1) & 1], a.op_lo[(p + 1) & 1]);
+        }
       }
       kb_run += nk;
       ++tiles_run;
