@@ -57,8 +57,11 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the cubic1024 and adjoint512 legs and the cuFFT DST comparator")
-    ap.add_argument("--cubic-steps", type=int, default=1,
-                    help="beam time steps of the cubic1024 leg (the workload defines 10)")
+    ap.add_argument("--cubic-steps", type=int, default=9,
+                    help="timed beam time steps of the cubic1024 leg after its first (untimed) one: "
+                         "the workload defines 10 in all")
+    ap.add_argument("--precision-steps", type=int, default=100,
+                    help="beam time steps of the FP32-vs-FP64 witness emittance leg")
     ap.add_argument("--case", choices=("sweep", "poisson"), default="sweep",
                     help="poisson: only repeated Dirichlet solves on the workload grid (for ncu captures)")
     ap.add_argument("--rhs", type=int, default=3, choices=(1, 2, 3),
@@ -259,6 +262,7 @@ def cubic_leg(hq, I, stream, flush, steps=1):
     grid = hq.Grid(g, precision="fp32", stream=stream)
     beams = [hq.Beam(b) for b in I.workload_beams("cubic1024")]
     p = g["nx"] * g["ny"] * g["ppc_x"] * g["ppc_y"]
+    m0 = grid.beam_moments(beams[1])
     grid.sweep(beams, dt=20.0)   # warm-up: also the first beam time step
     grid.sync()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -269,6 +273,7 @@ def cubic_leg(hq, I, stream, flush, steps=1):
     b.record(stream)
     torch.cuda.synchronize()
     removed = grid.sync()
+    m1 = grid.beam_moments(beams[1])
     used = free0 - torch.cuda.mem_get_info()[0]
     ms = a.elapsed_time(b)
     grid.close()
@@ -278,7 +283,50 @@ def cubic_leg(hq, I, stream, flush, steps=1):
             "time_steps": steps + 1, "timed_steps": steps, "ms_per_step": ms / steps,
             "ms_per_slice": ms / steps / g["nzeta"],
             "value": p * g["nzeta"] * steps / (ms / 1e3), "unit": "particle-slices/s",
-            "removed_particles": removed, "device_bytes_used": int(used)}
+            "removed_particles": removed,
+            "witness_eps_x_initial": hq.emittance(m0)[0], "witness_eps_x_final": hq.emittance(m1)[0], "device_bytes_used": int(used)}
+
+
+def precision_leg(hq, I, stream, steps=100, dt=20.0):
+    """Witness emittance over many beam time steps, FP32/bf16x3 against the FP64 GPU path (the
+    paper's single- vs double-precision study, Sec. 6): a driver and a witness whose centroid
+    starts one sigma off axis, `steps` time steps of dt; the witness's normalised emittance and
+    centroid from hq_beam_moments after every step."""
+    import numpy as np
+    import torch
+    g = dict(nx=128, ny=128, nzeta=128, xmin=-6.0, xmax=6.0, ymin=-6.0, ymax=6.0, zeta_min=-7.0, zeta_max=5.0,
+             shape_order=1, n_pc_iter=5, pc_mix=0.05, psi_guard=0.02)
+    driver = I.random_beam(200_000, 0.4, 0.4, 1.0, 0.5, energy_spread=1e-3)
+    wit = I.random_beam(50_000, 0.15, 0.15, 0.3, 2.0, zeta0=-3.5, gamma=I.GAMMA_WITNESS, seed=I.SEED_WITNESS)
+    rng = np.random.Generator(np.random.PCG64(7))
+    wit["x"] = wit["x"] + 0.15
+    wit["ux"] = 0.05 * rng.standard_normal(len(wit["x"]))
+    wit["uy"] = 0.05 * rng.standard_normal(len(wit["x"]))
+    res = {}
+    for prec in ("fp64", "fp32"):
+        grid = hq.Grid(g, precision=prec, stream=stream)
+        hb = [hq.Beam(driver), hq.Beam(wit)]
+        ms = [grid.beam_moments(hb[1])]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            grid.sweep(hb, dt=dt)
+            ms.append(grid.beam_moments(hb[1]))
+        b.record(stream)
+        torch.cuda.synchronize()
+        grid.close()
+        m = torch.stack(ms).cpu()
+        em = np.array([list(hq.emittance(v)) + [float(v[1] / v[0])] for v in m])
+        res[prec] = (em, a.elapsed_time(b) / steps)
+    e64, e32 = res["fp64"][0], res["fp32"][0]
+    rel = np.abs(e32 - e64) / np.abs(e64)
+    return {"workload": f"128x128 x 128 slices on +-6 x [-7, 5], 1 ppc, linear shape; driver 2e5 (sigma 0.4/1.0, n_b=0.5), "
+                        f"witness 5e4 (sigma 0.15/0.3, n_b=2, zeta0=-3.5, 1 GeV, centroid offset 0.15, u_perp spread 0.05); "
+                        f"{steps} time steps of dt={dt}",
+            "eps_x_initial": float(e64[0, 0]), "eps_x_final_fp64": float(e64[-1, 0]), "eps_x_final_fp32": float(e32[-1, 0]),
+            "rel_diff_eps_x_final": float(rel[-1, 0]), "rel_diff_eps_y_final": float(rel[-1, 1]),
+            "rel_diff_eps_max_over_steps": float(rel[:, :2].max()), "rel_diff_centroid_final": float(rel[-1, 2]),
+            "ms_per_step_fp64": res["fp64"][1], "ms_per_step_fp32": res["fp32"][1]}
 
 
 def adjoint_scale_leg(hq, I, stream, flush, ckpt_every=32):
@@ -517,7 +565,7 @@ def run_hq(args):
     if not args.no_adjoint and args.precision == "fp32":
         adjoint = adjoint_leg(hq, I, stream, flush)
 
-    cubic = adjoint512 = dstcmp = None
+    cubic = adjoint512 = dstcmp = precision = None
     if not args.no_extra and args.precision == "fp32" and rank == 0:
         grid.close()
         grid = None
@@ -528,6 +576,7 @@ def run_hq(args):
             adjoint512 = adjoint_scale_leg(hq, I, stream, flush)
             torch.cuda.empty_cache()
         dstcmp = dst_comparator(hq, I, stream)
+        precision = precision_leg(hq, I, stream, steps=args.precision_steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -551,7 +600,7 @@ def run_hq(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
             "gpu_launches": launches_per_sweep * args.steps,
             "fp64": fp64, "adjoint": adjoint, "cubic1024": cubic, "adjoint512": adjoint512,
-            "dst_comparator": dstcmp, "cpu_baseline": cpu, "removed_particles": removed,
+            "dst_comparator": dstcmp, "precision_study": precision, "cpu_baseline": cpu, "removed_particles": removed,
         }
         print(json.dumps(line), flush=True)
     if grid is not None:

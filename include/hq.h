@@ -166,6 +166,14 @@ hq_status hq_push_beams(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, int
  * `beam` (Ez gathered with the grid's shape) to sums[0..2] (DEVICE double[3]). */
 hq_status hq_witness_accumulate(hq_grid_t grid, const hq_beam_view* beam, int32_t slice, double* sums);
 
+/* Sec. 6 (precision study: the witness beam's emittance over many time steps): adds the
+ * weighted raw moments of all particles of `beam` to moments[0..10] (DEVICE double[11],
+ * zeroed by the caller): sum w, sum w x, sum w y, sum w ux, sum w uy, sum w x^2, sum w y^2,
+ * sum w ux^2, sum w uy^2, sum w x ux, sum w y uy (FP64).  The normalised rms emittance
+ * follows as eps_x^2 = <x^2><ux^2> - <x ux>^2 with centred, weight-averaged moments.
+ * Queued on the grid's stream; the beam needs no binning.  Errors: HQ_ERR_ARG. */
+hq_status hq_beam_moments(hq_grid_t grid, const hq_beam_view* beam, double* moments);
+
 /* One full quasi-static sweep head -> tail (Sec. 2, Fig. 1): for every slice,
  * advance, beam deposit, field solve, then optionally store the fields (out may be
  * NULL), push the beams (dt != 0), and accumulate witness sums (witness_beam >= 0,

@@ -457,6 +457,34 @@ def beam_push(spec: GridSpec, beam, sel, F, dt: float):
     return out
 
 
+BEAM_MOMENT_NAMES = ("w", "x", "y", "ux", "uy", "xx", "yy", "uxux", "uyuy", "xux", "yuy")
+
+
+def beam_moments(beam) -> torch.Tensor:
+    """Weighted raw moments of a beam over all its particles (Sec. 6 precision study: the
+    witness emittance): sum w, sum w x, sum w y, sum w ux, sum w uy, sum w x^2, sum w y^2,
+    sum w ux^2, sum w uy^2, sum w x ux, sum w y uy."""
+    w, x, y, ux, uy = (beam[k] for k in ("w", "x", "y", "ux", "uy"))
+    return torch.stack([w.sum(), (w * x).sum(), (w * y).sum(), (w * ux).sum(), (w * uy).sum(),
+                        (w * x * x).sum(), (w * y * y).sum(), (w * ux * ux).sum(), (w * uy * uy).sum(),
+                        (w * x * ux).sum(), (w * y * uy).sum()])
+
+
+def emittance(m) -> tuple:
+    """Normalised rms emittances (eps_x, eps_y) from beam_moments: eps_x^2 = <dx^2><dux^2> - <dx dux>^2
+    with centred, weight-averaged second moments (momenta in units of m c)."""
+    m = [float(v) for v in m]
+    W = m[0]
+    out = []
+    for a, b, aa, bb, ab in ((1, 3, 5, 7, 9), (2, 4, 6, 8, 10)):
+        ma, mb = m[a] / W, m[b] / W
+        vaa = m[aa] / W - ma * ma
+        vbb = m[bb] / W - mb * mb
+        vab = m[ab] / W - ma * mb
+        out.append(math.sqrt(max(vaa * vbb - vab * vab, 0.0)))
+    return tuple(out)
+
+
 def as_beam(arrays: dict, charge: float = -1.0, mass: float = 1.0):
     """Convert a dict of numpy/torch arrays (x, y, zeta, ux, uy, uz, w) to float64 tensors."""
     out = {k: torch.as_tensor(arrays[k], dtype=DT) for k in ("x", "y", "zeta", "ux", "uy", "uz", "w")}

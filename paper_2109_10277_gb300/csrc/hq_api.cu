@@ -1037,6 +1037,17 @@ hq_status hq_witness_accumulate(hq_grid_t g, const hq_beam_view* beam, int32_t s
   return check_launch(g);
 }
 
+hq_status hq_beam_moments(hq_grid_t g, const hq_beam_view* beam, double* moments) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (!beam || !moments) return fail(g, HQ_ERR_ARG, "beam and moments must not be NULL");
+  hq_status st = check_views(g, beam, 1);
+  if (st != HQ_OK) return st;
+  if (beam->n == 0) return HQ_OK;
+  Prof p(g, HQ_K_BEAM, 1);
+  launch_beam_moments(*beam, moments, g->stream);
+  return check_launch(g);
+}
+
 hq_status hq_sweep_step(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, double dt, const hq_field_out* out,
                         int32_t witness_beam, double* witness_sums) {
   if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");

@@ -250,6 +250,7 @@ void launch_beam_bin(hq_grid_s* g, int b, const hq_beam_view& v, cudaStream_t s)
 template <typename T> void launch_beam_deposit(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, void* dep, void* bjn, cudaStream_t s);
 template <typename T> void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double dt, cudaStream_t s);
 template <typename T> void launch_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double* sums, cudaStream_t s);
+void launch_beam_moments(const hq_beam_view& v, double* m, cudaStream_t s);   // m += 11 weighted moments
 // adjoint (k_adjoint.cu)
 template <typename T> void launch_adj_final(const hq_grid_s* g, const SnapView<T>& s, const void* gf, int slice,
                                            const void* dbar_next, const AdjView<T>& a, void* tbar, void* fbar_b,

@@ -6,6 +6,8 @@
 // atomics, an exclusive scan and a scatter into a permutation, giving the CSR
 // offsets of each slice.  The order of particles inside one slice is not fixed
 // (atomic cursor); everything downstream is a sum over the slice.
+#include <algorithm>
+
 #include "hq_internal.cuh"
 
 namespace hq {
@@ -257,6 +259,44 @@ __global__ void k_witness(hq_beam_view v, const int32_t* __restrict__ off, const
   }
 }
 
+// Weighted raw moments of a whole beam (Sec. 6 precision study: witness emittance), FP64:
+// m += (w, w x, w y, w ux, w uy, w x^2, w y^2, w ux^2, w uy^2, w x ux, w y uy); a block sums
+// its particles with warp shuffles and shared memory, then adds once per moment.
+constexpr int kMoments = 11;
+__global__ void k_beam_moments(hq_beam_view v, double* m) {
+  __shared__ double part[kThreads / 32][kMoments];
+  double a[kMoments];
+#pragma unroll
+  for (int k = 0; k < kMoments; ++k) a[k] = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < v.n; p += (int64_t)gridDim.x * blockDim.x) {
+    const double w = v.w[p], x = v.x[p], y = v.y[p], ux = v.ux[p], uy = v.uy[p];
+    a[0] += w;
+    a[1] += w * x;
+    a[2] += w * y;
+    a[3] += w * ux;
+    a[4] += w * uy;
+    a[5] += w * x * x;
+    a[6] += w * y * y;
+    a[7] += w * ux * ux;
+    a[8] += w * uy * uy;
+    a[9] += w * x * ux;
+    a[10] += w * y * uy;
+  }
+#pragma unroll
+  for (int k = 0; k < kMoments; ++k)
+    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < kMoments; ++k) part[warp][k] = a[k];
+  __syncthreads();
+  if (threadIdx.x < kMoments) {
+    double t = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) t += part[w][threadIdx.x];
+    atomicAdd(m + threadIdx.x, t);
+  }
+}
+
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 constexpr unsigned kSliceBlocks = 152;  // grid-stride launches for per-slice beam work
 
@@ -304,6 +344,11 @@ void launch_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice,
                              slice, g->geom, reinterpret_cast<const T*>(g->gf), sums)));
 }
 #undef HQ_SHAPE_SWITCH
+
+void launch_beam_moments(const hq_beam_view& v, double* m, cudaStream_t s) {
+  const unsigned nb = (unsigned)std::min<int64_t>(4 * 152, std::max<int64_t>(1, (v.n + kThreads - 1) / kThreads));
+  k_beam_moments<<<nb, kThreads, 0, s>>>(v, m);
+}
 
 template void launch_beam_deposit<float>(const hq_grid_s*, int, const hq_beam_view&, int, void*, void*, cudaStream_t);
 template void launch_beam_deposit<double>(const hq_grid_s*, int, const hq_beam_view&, int, void*, void*, cudaStream_t);

@@ -938,6 +938,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
     const CUtensorMap* xh = (p & 1) ? &x1h : &x0h;
     const CUtensorMap* xl = (p & 1) ? &x1l : &x0l;
     const int mode = p == 3 ? a.final_mode : (p == 1 ? 1 : 0);
+    if (p == 3) pdl_trigger();   // the next kernel may be scheduled (it waits for this grid's end)
     for (int nt = nt0; nt < NT; nt += ntstep) {
       const int c0 = nt * BN;
       if (warp == 0 && lane == 0) {

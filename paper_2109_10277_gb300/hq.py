@@ -23,7 +23,7 @@ FIELDS = ("rho", "jx", "jy", "jz", "chi", "psi", "exmby", "eypbx", "ez", "bx", "
 EXPORTS = ("hq_grid_create", "hq_grid_destroy", "hq_advance_slice", "hq_beam_deposit", "hq_solve_fields",
            "hq_store_fields", "hq_push_beams", "hq_witness_accumulate", "hq_sweep_step", "hq_poisson_solve",
            "hq_plasma_state", "hq_profile_enable", "hq_profile_read", "hq_sync", "hq_last_error",
-           "hq_poisson_solve_static", "hq_sweep_forward_ckpt", "hq_sweep_adjoint")
+           "hq_poisson_solve_static", "hq_sweep_forward_ckpt", "hq_sweep_adjoint", "hq_beam_moments")
 KERNEL_CLASSES = ("final", "trial", "dst", "field", "beam", "other")
 
 
@@ -84,6 +84,7 @@ def load() -> C.CDLL:
             "hq_poisson_solve_static": (P, P, I32, I32, D, D, I32, P),
             "hq_sweep_forward_ckpt": (P, C.POINTER(BeamView), I32, I32, P, I32),
             "hq_sweep_adjoint": (P, C.POINTER(BeamView), I32, I32, C.POINTER(D), C.POINTER(P), P, P, P),
+            "hq_beam_moments": (P, C.POINTER(BeamView), P),
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -252,6 +253,13 @@ class Grid:
                                        C.c_void_p(dprof.data_ptr()) if dprof is not None else None), self.h)
         return {"beam_w": wb, "plasma_w": wp, "n0_scale": dn0, "profile": dprof}
 
+    def beam_moments(self, beam: Beam) -> torch.Tensor:
+        """Weighted raw moments of a beam (device float64[11], see hq_beam_moments)."""
+        m = torch.zeros(11, dtype=torch.float64, device="cuda")
+        v = beam.view()
+        _check(load().hq_beam_moments(self.h, C.byref(v), C.c_void_p(m.data_ptr())), self.h)
+        return m
+
     def poisson_solve(self, src: torch.Tensor) -> torch.Tensor:
         assert src.dtype == self.dtype and src.is_cuda and src.is_contiguous() and src.dim() == 3
         dst = torch.empty_like(src)
@@ -285,6 +293,18 @@ class Grid:
         rm = C.c_int64()
         _check(load().hq_sync(self.h, C.byref(rm)), self.h)
         return int(rm.value)
+
+
+def emittance(moments) -> tuple:
+    """Normalised rms emittances (eps_x, eps_y) from hq_beam_moments' eleven sums (host
+    arithmetic on scalars): eps^2 = <dx^2><du^2> - <dx du>^2, centred and weight-averaged."""
+    m = [float(v) for v in moments]
+    out = []
+    for a, b, aa, bb, ab in ((1, 3, 5, 7, 9), (2, 4, 6, 8, 10)):
+        ma, mb = m[a] / m[0], m[b] / m[0]
+        vaa, vbb, vab = m[aa] / m[0] - ma * ma, m[bb] / m[0] - mb * mb, m[ab] / m[0] - ma * mb
+        out.append(max(vaa * vbb - vab * vab, 0.0) ** 0.5)
+    return tuple(out)
 
 
 def witness_loss_grad(kind: str, s0: float, s1: float, s2: float):

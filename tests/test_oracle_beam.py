@@ -99,3 +99,30 @@ def test_random_beam_slice_charge(order):
         (rho,) = O.beam_deposit_slice(sp, beam, sel, ("rho",))
         q = -2.0 * float(w[inside].sum())
         assert abs(float(rho.sum()) * vol - q) <= 1e-12 * max(1.0, abs(q)), i
+
+
+def test_beam_emittance_against_weighted_covariance():
+    """The oracle's emittance from raw moments equals sqrt(det) of numpy's weighted covariance
+    of (x, ux) and (y, uy); it is invariant under a linear shear u -> u + a x (a thin lens) and
+    under a centroid offset, and scales with the spread of the uncorrelated part."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    n = 5000
+    x = 0.3 * rng.standard_normal(n) + 0.5
+    y = 0.2 * rng.standard_normal(n) - 0.1
+    ux = 0.01 * rng.standard_normal(n) + 0.2 * x
+    uy = 0.02 * rng.standard_normal(n)
+    w = rng.uniform(0.2, 1.0, n)
+    b = O.as_beam(dict(x=x, y=y, zeta=np.zeros(n), ux=ux, uy=uy, uz=np.full(n, 1e3), w=w))
+    ex, ey = O.emittance(O.beam_moments(b))
+    for e, (a, c) in ((ex, (x, ux)), (ey, (y, uy))):
+        cov = np.cov(np.vstack([a, c]), aweights=w, bias=True)
+        assert abs(e - math.sqrt(np.linalg.det(cov))) <= 1e-10 * e
+    b2 = dict(b)
+    b2["ux"] = b["ux"] + 3.0 * b["x"]
+    b2["x"] = b["x"] + 7.0
+    ex2, _ = O.emittance(O.beam_moments(b2))
+    assert abs(ex2 - ex) <= 1e-8 * ex
+    b3 = dict(b)
+    b3["ux"] = 0.2 * b["x"] + 2.0 * (b["ux"] - 0.2 * b["x"])
+    ex3, _ = O.emittance(O.beam_moments(b3))
+    assert abs(ex3 - 2.0 * ex) <= 1e-8 * ex
