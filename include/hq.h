@@ -194,7 +194,12 @@ hq_status hq_sweep_forward_ckpt(hq_grid_t grid, hq_beam_view* beams, int32_t nbe
                                 double* witness_sums, int32_t ckpt_every);
 
 /* Reverse-zeta adjoint of the last hq_sweep_forward_ckpt (same beams and witness):
- * given dL/d(S0, S1, S2) of the witness sums (HOST double[3]), returns dL/dw for
+ * given dL/d(S0, S1, S2) of the witness sums (HOST double[3]; may be NULL without a
+ * witness) and, optionally, the adjoint seeds of per-slice output fields (dL_dfields:
+ * DEVICE arrays of nzeta x ny x nx field-type values holding dL/d(field) per slice and
+ * node, NULL members and a NULL struct meaning zero; rho, jx, jy, jz, psi, exmby, eypbx,
+ * ez, bx, by, bz are supported, chi is refused with HQ_ERR_ARG; seeds on wall nodes are
+ * ignored, the forward holds those fields at zero), returns dL/dw for
  * every beam particle (dL_dbeam_w: HOST array of nbeams DEVICE double* of n entries,
  * overwritten; an entry may be NULL), dL/dw of every plasma particle (DEVICE double[P],
  * may be NULL), dL/dn0_scale (DEVICE double[1], may be NULL) and dL/d(radial profile)
@@ -204,8 +209,8 @@ hq_status hq_sweep_forward_ckpt(hq_grid_t grid, hq_beam_view* beams, int32_t nbe
  * its own adjoint kernel.  Leaves the grid's forward state undefined (the next sweep
  * restarts at slice 0).  Errors: HQ_ERR_STATE without a matching forward. */
 hq_status hq_sweep_adjoint(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, int32_t witness_beam,
-                           const double* dL_dsums, double* const* dL_dbeam_w, double* dL_dplasma_w,
-                           double* dL_dn0_scale, double* dL_dprofile);
+                           const double* dL_dsums, const hq_field_out* dL_dfields, double* const* dL_dbeam_w,
+                           double* dL_dplasma_w, double* dL_dn0_scale, double* dL_dprofile);
 
 /* Solves nrhs (1..5) Dirichlet Poisson problems L f = s with the grid's DST-I
  * backend (Sec. 3.2, fast Poisson solver): src and dst are DEVICE arrays of

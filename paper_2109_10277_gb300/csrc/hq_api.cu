@@ -493,7 +493,8 @@ hq_status forward_ckpt_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int
 
 template <typename T>
 hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witness, const double* sbar,
-                       double* const* wbar_b, double* wbar_p_out, double* dn0, double* dprof) {
+                       const hq_field_out* seeds, double* const* wbar_b, double* wbar_p_out, double* dn0,
+                       double* dprof) {
   AdjStore* a = adj_of(g);
   cudaStream_t s = g->stream;
   const size_t np = (size_t)g->np, ts = g->tsize, nn = (size_t)g->nnode;
@@ -539,6 +540,10 @@ hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witn
                      f32 ? sn.fx : nullptr, f32 ? sn.fy : nullptr, f32 ? sn.opp : nullptr};
       const void* gf = a->tape_gf[t];
       cudaMemsetAsync(a->jtot, 0, 2 * ts * nn, s);
+      if (seeds) {
+        Prof p(g, HQ_K_FIELD, 1);
+        launch_adj_seed<T>(g, *seeds, i, a->tbar, a->fbar_b, dcur, s);
+      }
       if (witness >= 0 && beams[witness].n > 0) {
         Prof p(g, HQ_K_BEAM, 1);
         launch_adj_witness<T>(g, witness, beams[witness], i, gf, sbar, a->tbar,
@@ -564,7 +569,11 @@ hq_status adjoint_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int witn
         Prof p(g, HQ_K_FIELD, 1);
         launch_adj_guess<T>(g, bb, i >= 1 ? a->carry[(i - 1) % 3] : nullptr, i >= 2 ? a->carry[(i - 2) % 3] : nullptr, s);
       }
-      { Prof p(g, HQ_K_FIELD, 1); launch_adj_main_pre<T>(g, a->tbar, s); }
+      {
+        Prof p(g, HQ_K_FIELD, 1);
+        const void* sp = seeds && seeds->psi ? static_cast<const char*>(seeds->psi) + (size_t)i * nn * ts : nullptr;
+        launch_adj_main_pre<T>(g, a->tbar, sp, s);
+      }
       dst_solve(g, 3);
       { Prof p(g, HQ_K_FIELD, 1); launch_adj_main_post<T>(g, dcur, a->rho_ion_bar, a->tbar, s); }
       for (int b = 0; b < nb; ++b) {
@@ -1143,8 +1152,8 @@ hq_status hq_sweep_forward_ckpt(hq_grid_t g, hq_beam_view* beams, int32_t nbeams
 }
 
 hq_status hq_sweep_adjoint(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, int32_t witness_beam,
-                           const double* dL_dsums, double* const* dL_dbeam_w, double* dL_dplasma_w,
-                           double* dL_dn0_scale, double* dL_dprofile) {
+                           const double* dL_dsums, const hq_field_out* dL_dfields, double* const* dL_dbeam_w,
+                           double* dL_dplasma_w, double* dL_dn0_scale, double* dL_dprofile) {
   if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
   AdjStore* a = adj_of(g);
   if (!a || !a->fwd_done) return fail(g, HQ_ERR_STATE, "hq_sweep_adjoint needs hq_sweep_forward_ckpt first");
@@ -1153,12 +1162,13 @@ hq_status hq_sweep_adjoint(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, int
   for (int b = 0; b < nbeams; ++b)
     if (!same_view(beams[b], a->fwd_beams[b])) return fail(g, HQ_ERR_STATE, "beams differ from the forward sweep");
   if (witness_beam >= 0 && !dL_dsums) return fail(g, HQ_ERR_ARG, "dL_dsums (host double[3]) is needed");
+  if (dL_dfields && dL_dfields->chi) return fail(g, HQ_ERR_ARG, "dL_dfields->chi is not supported (chi is output only)");
   const double zero[3] = {0.0, 0.0, 0.0};
   const double* sb = dL_dsums ? dL_dsums : zero;
-  hq_status st = g->fp64 ? adjoint_impl<double>(g, beams, nbeams, witness_beam, sb, dL_dbeam_w, dL_dplasma_w,
-                                                dL_dn0_scale, dL_dprofile)
-                         : adjoint_impl<float>(g, beams, nbeams, witness_beam, sb, dL_dbeam_w, dL_dplasma_w,
-                                               dL_dn0_scale, dL_dprofile);
+  hq_status st = g->fp64 ? adjoint_impl<double>(g, beams, nbeams, witness_beam, sb, dL_dfields, dL_dbeam_w,
+                                                dL_dplasma_w, dL_dn0_scale, dL_dprofile)
+                         : adjoint_impl<float>(g, beams, nbeams, witness_beam, sb, dL_dfields, dL_dbeam_w,
+                                               dL_dplasma_w, dL_dn0_scale, dL_dprofile);
   if (st != HQ_OK) return st;
   a->fwd_done = 0;
   g->last_adv = g->last_beam = g->last_solved = -1;

@@ -262,7 +262,9 @@ template <typename T> void launch_adj_bstart(const hq_grid_s* g, void* fbar_b, v
 template <typename T> void launch_adj_pc_pre(const hq_grid_s* g, const void* bbar_m, void* bbar_m1, cudaStream_t st);
 template <typename T> void launch_adj_pc_post(const hq_grid_s* g, void* dcur, void* dprev, void* jbar, void* jtot, cudaStream_t st);
 template <typename T> void launch_adj_guess(const hq_grid_s* g, const void* b0, void* c1, void* c2, cudaStream_t st);
-template <typename T> void launch_adj_main_pre(const hq_grid_s* g, const void* tbar, cudaStream_t st);
+template <typename T> void launch_adj_main_pre(const hq_grid_s* g, const void* tbar, const void* seed_psi, cudaStream_t st);
+template <typename T> void launch_adj_seed(const hq_grid_s* g, const hq_field_out& seeds, int slice, void* tbar,
+                                           void* fbar_b, void* dcur, cudaStream_t st);
 template <typename T> void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, void* tbar,
                                                cudaStream_t st);
 template <typename T> void launch_adj_beam(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, const void* dcur,

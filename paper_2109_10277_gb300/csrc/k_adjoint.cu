@@ -573,7 +573,7 @@ __global__ void k_adj_guess(const V2<T>* __restrict__ b0, V2<T>* c1, V2<T>* c2, 
 // psi_bar = Dx tbar0 + Dy tbar1 (ExmBy = -Dx psi, EypBx = -Dy psi), with Ez_bar, Bz_bar: tbar
 // holds the adjoints of the gathered ExmBy, EypBx, Ez, Bz (witness, final and trial passes).
 template <typename T, typename Sink>
-__global__ void k_adj_main_pre(const T* __restrict__ tbar, Geom gm, Sink sink) {
+__global__ void k_adj_main_pre(const T* __restrict__ tbar, const T* __restrict__ seed_psi, Geom gm, Sink sink) {
   const int nx = gm.nx;
   auto f0 = [&](int y, int x) { return tbar[((int64_t)y * nx + x) * 4 + 0]; };
   auto f1 = [&](int y, int x) { return tbar[((int64_t)y * nx + x) * 4 + 1]; };
@@ -582,6 +582,7 @@ __global__ void k_adj_main_pre(const T* __restrict__ tbar, Geom gm, Sink sink) {
     v[0] = v[1] = v[2] = T(0);
     if (ix > 0 && iy > 0) {
       v[0] = dxc(f0, iy, ix, nx, gsel<T>(gm.inv2dx, gm.f_inv2dx)) + dyc(f1, iy, ix, gm.ny, gsel<T>(gm.inv2dy, gm.f_inv2dy));
+      if (seed_psi) v[0] += seed_psi[o];   // the caller's dL/dpsi of this slice
       v[1] = tbar[o * 4 + 2];
       v[2] = tbar[o * 4 + 3];
     }
@@ -823,10 +824,51 @@ void launch_adj_guess(const hq_grid_s* g, const void* b0, void* c1, void* c2, cu
                                                           g->nnode);
 }
 template <typename T>
-void launch_adj_main_pre(const hq_grid_s* g, const void* tbar, cudaStream_t st) {
+void launch_adj_main_pre(const hq_grid_s* g, const void* tbar, const void* seed_psi, cudaStream_t st) {
   with_sink<T>(g, [&](auto sink) {
-    k_adj_main_pre<T, decltype(sink)><<<src_grid(g), 128, 0, st>>>(reinterpret_cast<const T*>(tbar), g->geom, sink);
+    k_adj_main_pre<T, decltype(sink)><<<src_grid(g), 128, 0, st>>>(reinterpret_cast<const T*>(tbar),
+                                                                   reinterpret_cast<const T*>(seed_psi), g->geom, sink);
   });
+}
+
+// Caller's adjoint seeds of slice i's output fields (hq_sweep_adjoint's dL_dfields, each a
+// pointer to this slice's ny x nx values or null), added where the reverse sweep accumulates the
+// adjoint of that field: ExmBy, EypBx, Ez, Bz into tbar, Bx, By into fbar_b, rho, Jx, Jy, Jz into
+// the slice's deposit adjoint.  Wall nodes are fixed zeros in the forward: their seeds are ignored.
+template <typename T>
+__global__ void k_adj_seed(hq_field_out sd, int64_t off, V4<T>* tbar, V2<T>* fbar_b, V4<T>* dcur, Geom gm) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+  if (ix >= gm.nx || ix == 0 || iy == 0) return;
+  const int64_t o = (int64_t)iy * gm.nx + ix, t = off + o;
+  auto at = [&](void* p) { return p ? reinterpret_cast<const T*>(p)[t] : T(0); };
+  if (sd.exmby || sd.eypbx || sd.ez || sd.bz) {
+    V4<T> q = tbar[o];
+    q.a += at(sd.exmby);
+    q.b += at(sd.eypbx);
+    q.c += at(sd.ez);
+    q.d += at(sd.bz);
+    tbar[o] = q;
+  }
+  if (sd.bx || sd.by) {
+    V2<T> q = fbar_b[o];
+    q.a += at(sd.bx);
+    q.b += at(sd.by);
+    fbar_b[o] = q;
+  }
+  if (sd.rho || sd.jx || sd.jy || sd.jz) {
+    V4<T> q = dcur[o];
+    q.a += at(sd.rho);
+    q.b += at(sd.jx);
+    q.c += at(sd.jy);
+    q.d += at(sd.jz);
+    dcur[o] = q;
+  }
+}
+template <typename T>
+void launch_adj_seed(const hq_grid_s* g, const hq_field_out& sd, int slice, void* tbar, void* fbar_b, void* dcur,
+                     cudaStream_t st) {
+  k_adj_seed<T><<<grid2d(g), 128, 0, st>>>(sd, (int64_t)slice * g->nnode, reinterpret_cast<V4<T>*>(tbar),
+                                          reinterpret_cast<V2<T>*>(fbar_b), reinterpret_cast<V4<T>*>(dcur), g->geom);
 }
 template <typename T>
 void launch_adj_main_post(const hq_grid_s* g, void* dcur, void* rho_ion_bar, void* tbar, cudaStream_t st) {
@@ -875,7 +917,8 @@ void launch_adj_params(const hq_grid_s* g, const double* wbar_p, double* dn0, do
   template void launch_adj_pc_pre<T>(const hq_grid_s*, const void*, void*, cudaStream_t);                            \
   template void launch_adj_pc_post<T>(const hq_grid_s*, void*, void*, void*, void*, cudaStream_t);                   \
   template void launch_adj_guess<T>(const hq_grid_s*, const void*, void*, void*, cudaStream_t);                      \
-  template void launch_adj_main_pre<T>(const hq_grid_s*, const void*, cudaStream_t);                                 \
+  template void launch_adj_main_pre<T>(const hq_grid_s*, const void*, const void*, cudaStream_t);                    \
+  template void launch_adj_seed<T>(const hq_grid_s*, const hq_field_out&, int, void*, void*, void*, cudaStream_t);    \
   template void launch_adj_main_post<T>(const hq_grid_s*, void*, void*, void*, cudaStream_t);                        \
   template void launch_adj_beam<T>(const hq_grid_s*, int, const hq_beam_view&, int, const void*, const void*,        \
                                    double*, cudaStream_t);                                                           \

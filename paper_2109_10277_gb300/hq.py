@@ -83,7 +83,8 @@ def load() -> C.CDLL:
             "hq_sync": (P, C.POINTER(I64)),
             "hq_poisson_solve_static": (P, P, I32, I32, D, D, I32, P),
             "hq_sweep_forward_ckpt": (P, C.POINTER(BeamView), I32, I32, P, I32),
-            "hq_sweep_adjoint": (P, C.POINTER(BeamView), I32, I32, C.POINTER(D), C.POINTER(P), P, P, P),
+            "hq_sweep_adjoint": (P, C.POINTER(BeamView), I32, I32, C.POINTER(D), C.POINTER(FieldOut), C.POINTER(P), P, P,
+                                 P),
             "hq_beam_moments": (P, C.POINTER(BeamView), P),
         }
         for name, args in sig.items():
@@ -235,9 +236,11 @@ class Grid:
                                             int(ckpt_every)), self.h)
         self._adj_beams = arr
 
-    def adjoint(self, beams: Sequence[Beam], witness: int, dl_dsums: Sequence[float], plasma: bool = True) -> dict:
+    def adjoint(self, beams: Sequence[Beam], witness: int, dl_dsums: Optional[Sequence[float]], plasma: bool = True,
+                dl_dfields: Optional[dict] = None) -> dict:
         """Reverse sweep of the last forward_ckpt: gradients w.r.t. beam and plasma weights,
-        the density scale n0 and the radial profile."""
+        the density scale n0 and the radial profile, of a loss with dL/d(witness sums) dl_dsums
+        and, optionally, dL/d(field) seeds dl_dfields (name -> (nzeta, ny, nx) field-type tensor)."""
         arr = _beam_array(beams)
         wb = [torch.zeros(b.n, dtype=torch.float64, device="cuda") for b in beams]
         ptrs = (C.c_void_p * max(1, len(beams)))(*[t.data_ptr() for t in wb])
@@ -246,8 +249,10 @@ class Grid:
         dn0 = torch.zeros(1, dtype=torch.float64, device="cuda")
         prof = self.params.get("radial_profile")
         dprof = torch.zeros(len(prof), dtype=torch.float64, device="cuda") if prof is not None else None
-        sb = (C.c_double * 3)(*[float(v) for v in dl_dsums])
-        _check(load().hq_sweep_adjoint(self.h, arr, len(beams), int(witness), sb, ptrs,
+        sb = (C.c_double * 3)(*[float(v) for v in dl_dsums]) if dl_dsums is not None else None
+        fo = self._out(dl_dfields)
+        _check(load().hq_sweep_adjoint(self.h, arr, len(beams), int(witness), sb,
+                                       C.byref(fo) if fo is not None else None, ptrs,
                                        C.c_void_p(wp.data_ptr()) if wp is not None else None,
                                        C.c_void_p(dn0.data_ptr()),
                                        C.c_void_p(dprof.data_ptr()) if dprof is not None else None), self.h)

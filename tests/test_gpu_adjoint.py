@@ -217,3 +217,51 @@ def test_adjoint256_small_grid_gradients_vs_central_fd(hq):
                                                       for k in p0})
         for k in p0:
             assert errs[k] <= tol, (precision, k, errs)
+
+
+# ---------------------------------------------------------------- adjoint seeds of per-slice fields
+
+SEEDED = {"ez": 10, "psi": 7, "bx": 12, "by": 3, "exmby": 15, "eypbx": 5, "bz": 9, "rho": 11, "jx": 8, "jy": 6,
+          "jz": 14}
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-5), ("fp32", 1e-3)])
+def test_adjoint_of_field_seeds_matches_taped_oracle(hq, precision, tol):
+    """A loss of the per-slice fields themselves, L = sum over the seeded (field, slice) pairs of
+    sum_nodes seed * field, differentiated by hq_sweep_adjoint's dL_dfields against the taped
+    oracle (both segments recomputed: checkpoint every 5 slices).  Gradients w.r.t. the beam
+    weights, the plasma density scale and the radial profile."""
+    g, d, w = case(order=1)
+    gen = torch.Generator().manual_seed(31)
+    seeds = {k: torch.randn(g["ny"], g["nx"], generator=gen, dtype=torch.float64) for k in SEEDED}
+    # oracle
+    sp = O.GridSpec(**g)
+    wd = torch.tensor(d["w"], dtype=torch.float64, requires_grad=True)
+    ww = torch.tensor(w["w"], dtype=torch.float64, requires_grad=True)
+    n0 = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    prof = torch.tensor(g["radial_profile"], dtype=torch.float64, requires_grad=True)
+    bd, bw = O.as_beam(d), O.as_beam(w)
+    bd["w"], bw["w"] = wd, ww
+    r = O.sweep(sp, [bd, bw], record=tuple(SEEDED), n0_scale=n0, radial_profile=prof)
+    L = sum((seeds[k] * r.fields[k][i]).sum() for k, i in SEEDED.items())
+    L.backward()
+    # GPU
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    dl = {}
+    for k, i in SEEDED.items():
+        t = torch.zeros(g["nzeta"], g["ny"], g["nx"], dtype=dt)
+        t[i] = seeds[k].to(dt)
+        dl[k] = t.cuda()
+    grid = hq.Grid(g, precision=precision)
+    beams = [hq.Beam(d), hq.Beam(w)]
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    grid.forward_ckpt(beams, -1, sums, 5)
+    res = grid.adjoint(beams, -1, None, dl_dfields=dl)
+    grid.sync()
+    grid.close()
+    errs = {"driver_w": rel(res["beam_w"][0].cpu(), wd.grad), "witness_w": rel(res["beam_w"][1].cpu(), ww.grad),
+            "n0": abs(float(res["n0_scale"][0]) - float(n0.grad)) / abs(float(n0.grad)),
+            "profile": rel(res["profile"].cpu(), prof.grad)}
+    print(precision, "field seeds:", {a: f"{b:.2e}" for a, b in errs.items()})
+    for key, e in errs.items():
+        assert e <= tol, (key, errs)
