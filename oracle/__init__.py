@@ -23,6 +23,11 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   beam deposit         pinned: rho_b = q n_b at the nodes of an affine-density lattice beam (all
                        orders), J_b = rho_b u / gamma, slice charge of a random beam, and the
                        linear wake built from the driver's closed-form density
+  explicit B_perp      pinned: Laplacian/shifted DST eigenmodes, PCG against a dense solve and exact for
+                       constant chi, source terms against central differences of the deposited current
+                       along the particle equations, linear wake, agreement with a converged
+                       predictor-corrector as dzeta shrinks
+  beam moments         pinned: numpy weighted covariance, shear and offset invariance of the emittance
   predictor-corrector  pinned at the workloads' setting (5 iterations, mixing 0.05): linear wake
                        within 5 % converging under dzeta and dx refinement; lag behind a converged
                        iteration second order in dzeta

@@ -87,9 +87,10 @@ class GridSpec:
     radial_profile: Optional[Sequence[float]] = None
     profile_rmax: float = 0.0
     n0_scale: float = 1.0
-    n_pc_iter: int = 5
+    n_pc_iter: int = 5          # predictor-corrector iterations, or the explicit solver's PCG iterations
     pc_mix: float = 0.05
     psi_guard: float = 0.02
+    bperp_solver: str = "pc"    # "pc": predictor-corrector; "explicit": Helmholtz-like equation in chi
     # "float32": B-spline weights formed from an FP32 cell fraction in FP32 arithmetic
     # (then widened).  A test knob that measures the rounding floor of a single-precision
     # deposit/gather; the method itself is the default, FP64.
@@ -200,6 +201,60 @@ def ddy(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
     fp = torch.cat([f, torch.zeros_like(f[..., :1, :])], dim=-2)
     d = torch.cat([torch.zeros_like(f[..., :1, :]), (fp[..., 2:, :] - fp[..., :-2, :]) / (2.0 * spec.dy)], dim=-2)
     return d * _wall_mask(spec)
+
+
+def laplacian(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
+    """The 5-point Laplacian on interior nodes (wall nodes read 0; wall outputs are 0): the
+    operator poisson_solve inverts."""
+    fp = torch.nn.functional.pad(f, (0, 1, 0, 1))             # nodes nx, ny (wall) = 0
+    c = fp[1:-1, 1:-1]
+    lap = torch.zeros_like(f)
+    lap[1:, 1:] = ((fp[1:-1, 2:] - 2.0 * c + fp[1:-1, :-2]) / spec.dx ** 2 +
+                   (fp[2:, 1:-1] - 2.0 * c + fp[:-2, 1:-1]) / spec.dy ** 2)
+    return lap
+
+
+def shifted_solve(spec: GridSpec, s: torch.Tensor, c: float) -> torch.Tensor:
+    """f = (L - c)^{-1} s for a constant c >= 0 (DST-I with 1/(lambda - c); f = 0 on the wall)."""
+    lam = laplace_eigs(spec)
+    inv = torch.zeros_like(lam)
+    inv[1:, 1:] = 1.0 / (lam[1:, 1:] - c)
+    return (4.0 / (spec.nx * spec.ny)) * dst2(spec, dst2(spec, s) * inv)
+
+
+def helmholtz_pcg(spec: GridSpec, chi: torch.Tensor, rhs: Sequence[torch.Tensor], x0: Sequence[torch.Tensor],
+                  c: float, iters: int):
+    """Solve (L - chi) B = rhs for each right-hand side: preconditioned conjugate gradients on
+    the symmetric positive definite form (chi - L) B = -rhs, preconditioner (c - L)^{-1} (one
+    shifted DST-I solve), start x0, a fixed number of iterations `iters` (no early exit; a
+    zero residual stops the update).  Returns the iterates and the final relative residuals."""
+    mask = _wall_mask(spec)
+    A = lambda v: chi * v * mask - laplacian(spec, v)  # noqa: E731
+    P = lambda v: -shifted_solve(spec, v, c)  # noqa: E731
+    out, resid = [], []
+    for b_, x in zip(rhs, x0):
+        b = -b_ * mask
+        x = x * mask
+        r = b - A(x)
+        z = P(r)
+        p = z
+        rz = (r * z).sum()
+        for k in range(iters):
+            q = A(p)
+            pq = (p * q).sum()
+            alpha = torch.where(pq != 0, rz / torch.where(pq != 0, pq, torch.ones_like(pq)), torch.zeros_like(pq))
+            x = x + alpha * p
+            r = r - alpha * q
+            if k < iters - 1:
+                z = P(r)
+                rz_new = (r * z).sum()
+                beta = torch.where(rz != 0, rz_new / torch.where(rz != 0, rz, torch.ones_like(rz)), torch.zeros_like(rz))
+                p = z + beta * p
+                rz = rz_new
+        nb = float(torch.linalg.norm(b))
+        resid.append(float(torch.linalg.norm(b - A(x))) / nb if nb > 0 else 0.0)
+        out.append(x)
+    return out, resid
 
 
 # ----------------------------------------------------------------------------
@@ -361,6 +416,33 @@ def plasma_deposit_full(spec: GridSpec, st, q=PLASMA_Q, m=PLASMA_M):
     uz = (1.0 + st["ux"] ** 2 + st["uy"] ** 2 - opp * opp) * 0.5 * g
     qw = torch.where(st["alive"], q * st["w"], torch.zeros_like(st["w"])) / A
     vals = [qw * gam * g, qw * st["ux"] * g, qw * st["uy"] * g, qw * uz * g, qw * q * g / m]
+    return deposit(spec, st["x"], st["y"], vals, spec.shape_order)
+
+
+def explicit_sources(spec: GridSpec, st, F4, q=PLASMA_Q, m=PLASMA_M):
+    """The plasma's d(J_perp)/d(zeta) at the current slice without its B_perp part (the
+    explicit solver's source; reading: differentiate J_perp = sum q w S u_perp/((1+Psi) A) along
+    zeta with the particle equations of Sec. 3.2).  F4 = (ExmBy, EypBx, Ez, Bz) gathered at the
+    particles.  Returns the deposits (Fx, Fy, Jxx, Jxy, Jyy) with
+      Fx = sum a S [g Gx - u_x g^2 Psi'],  Gx = -(q/M)(gamma g ExmBy + Bz g u_y),
+      Fy = sum a S [g Gy - u_y g^2 Psi'],  Gy = -(q/M)(gamma g EypBx - Bz g u_x),
+      Psi' = -(q/M)(g (u_x ExmBy + u_y EypBx) - Ez),  Jab = sum a S g^2 u_a u_b,
+    a = q w / A, g = 1/(1+Psi); then d(Jx)/d(zeta) = Fx + dx Jxx + dy Jxy - (q/M) sum a S g By and
+    d(Jy)/d(zeta) = Fy + dx Jxy + dy Jyy + (q/M) sum a S g Bx (the B terms are -chi By, chi Bx)."""
+    A = spec.dx * spec.dy
+    exmby, eypbx, ez, bz = F4
+    ux, uy = st["ux"], st["uy"]
+    opp = 1.0 + st["psi"]
+    g = 1.0 / opp
+    gam = (1.0 + ux * ux + uy * uy + opp * opp) * 0.5 * g
+    qm = q / m
+    a = torch.where(st["alive"], q * st["w"], torch.zeros_like(st["w"])) / A
+    dpsi = -qm * (g * (ux * exmby + uy * eypbx) - ez)
+    gx = -qm * (gam * g * exmby + bz * g * uy)
+    gy = -qm * (gam * g * eypbx - bz * g * ux)
+    g2 = g * g
+    vals = [a * (g * gx - ux * g2 * dpsi), a * (g * gy - uy * g2 * dpsi),
+            a * g2 * ux * ux, a * g2 * ux * uy, a * g2 * uy * uy]
     return deposit(spec, st["x"], st["y"], vals, spec.shape_order)
 
 
@@ -556,6 +638,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     rec = {k: [] for k in record}
     wit = {bi: [torch.zeros((), dtype=DT)] * 3 for bi in witness}
     jx_prev, jy_prev = zero, zero
+    bj_prev = (zero, zero)   # beam J_perp of slice i-1 (explicit solver)
     b1 = (zero, zero)
     b2 = (zero, zero)
     src = noisy(plasma_deposit_full(spec, st))
@@ -564,9 +647,11 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
             res.plasma_at[i] = {k: v.detach().clone() for k, v in st.items()}
         rho, jx, jy, jz, chi = src
         rho = rho + rho_ion
+        bj_cur = (zero, zero)
         for bi, b in enumerate(beams):
             brho, bjx, bjy, bjz = beam_deposit_slice(spec, b, sel_of(bi, i))
             rho, jx, jy, jz = rho + brho, jx + bjx, jy + bjy, jz + bjz
+            bj_cur = (bj_cur[0] + bjx, bj_cur[1] + bjy)
         psi = poisson_solve(spec, -(rho - jz))
         exmby, eypbx = -ddx(spec, psi), -ddy(spec, psi)
         ez = poisson_solve(spec, ddx(spec, jx) + ddy(spec, jy))
@@ -579,7 +664,17 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
                 tjx, tjy = beam_deposit_slice(spec, b, sel_of(bi, i + 1), ("jx", "jy"))
                 njx, njy = njx + tjx, njy + tjy
         resid = 0.0
-        for _m in range(spec.n_pc_iter):
+        if spec.bperp_solver == "explicit":
+            # explicit solver: (L - chi) Bx = -dy Jz + Ty, (L - chi) By = dx Jz - Tx with T the
+            # B-independent part of d(J_perp)/d(zeta) (explicit_sources; beams by central differences)
+            F4 = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bz), spec.shape_order)
+            fx, fy, jxx, jxy, jyy = noisy(explicit_sources(spec, st, F4))
+            tx = fx + ddx(spec, jxx) + ddy(spec, jxy) + (bj_prev[0] - njx) / (2.0 * dz)
+            ty = fy + ddx(spec, jxy) + ddy(spec, jyy) + (bj_prev[1] - njy) / (2.0 * dz)
+            (bx, by), rr = helmholtz_pcg(spec, chi, (sbx0 + ty, sby0 - tx), (bx, by), spec.n0_scale,
+                                         spec.n_pc_iter)
+            resid = max(rr)
+        for _m in range(spec.n_pc_iter if spec.bperp_solver == "pc" else 0):
             F = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bx, by, bz), spec.shape_order)
             f = derivs(qm, st["ux"], st["uy"], st["psi"], F)
             tx, ty, tux, tuy, tpsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
@@ -623,6 +718,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
                   uy=keep(nuy, st["uy"]), psi=keep(npsi, st["psi"]), w=st["w"], alive=alive)
         src = noisy(plasma_deposit_full(spec, st))
         jx_prev, jy_prev = jx, jy
+        bj_prev = bj_cur
         b2, b1 = b1, (bx, by)
     res.fields = {k: torch.stack(v) for k, v in rec.items()}
     res.removed = int((~st["alive"]).sum())
