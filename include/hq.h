@@ -86,11 +86,24 @@ typedef struct {
   int32_t n_profile;
   double profile_rmax;
   double n0_scale;                  /* multiplies plasma (and ion) density            */
-  int32_t n_pc_iter;                /* predictor-corrector iterations (fixed count)   */
+  int32_t n_pc_iter;                /* predictor-corrector iterations, or the explicit
+                                       solver's conjugate-gradient iterations (fixed count) */
   double pc_mix;                    /* B <- pc_mix * B_solved + (1 - pc_mix) * B      */
   double psi_guard;                 /* particle removed when 1 + Psi < psi_guard      */
   int32_t precision;                /* hq_precision                                   */
+  int32_t bperp_solver;             /* hq_bperp_solver (0: predictor-corrector)       */
 } hq_grid_desc;
+
+/* B_perp field solver (Sec. 3.2: "predictor-corrector field solver" and "explicit field
+ * solver").  The explicit solver differentiates the deposited plasma current along zeta
+ * with the particle equations (a reading: the paper cites the equation), which turns
+ * Eq. bxby into (L - chi) Bx = -dy Jz + Ty, (L - chi) By = dx Jz - Tx with chi =
+ * sum q^2 w S / (M (1+Psi) A) and T the B-independent part of d(J_perp)/d(zeta) (plasma:
+ * deposited force and convective terms; beams: central differences of their slice
+ * deposits); it is solved by n_pc_iter preconditioned conjugate-gradient iterations
+ * (preconditioner (c - L)^{-1}, c = n0_scale, one shifted DST-I solve each) from the guess
+ * 2 B(i-1) - B(i-2).  The adjoint supports only the predictor-corrector. */
+typedef enum { HQ_BPERP_PC = 0, HQ_BPERP_EXPLICIT = 1 } hq_bperp_solver;
 
 /* One beam species, structure of arrays in DEVICE memory (double), n particles.
  * x, y, zeta and ux, uy, uz (normalized momenta) are updated in place by the

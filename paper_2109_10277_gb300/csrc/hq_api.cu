@@ -56,7 +56,8 @@ void free_all(hq_grid_s* g) {
     }
   }
   for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); F(g->psrc[i]); }
-  F(g->rho_ion); F(g->tj); F(g->bjn); F(g->gf); F(g->bm); F(g->psi); F(g->bprev1); F(g->solved);
+  F(g->rho_ion); F(g->tj); F(g->bjn); F(g->bjp); F(g->xs4); F(g->xs1); F(g->pcg_r); F(g->pcg_p); F(g->pcg_s);
+  F(g->scale_h); F(g->gf); F(g->bm); F(g->psi); F(g->bprev1); F(g->solved);
   F(g->f64_a); F(g->f64_b); F(g->f64_scale); F(g->tw_x); F(g->tw_y); F(g->sin_x); F(g->sin_y);
   F(g->sx_hi); F(g->sx_lo); F(g->sy_hi); F(g->sy_lo); F(g->f32_scale);
   for (int b = 0; b < kMaxBeams; ++b) {
@@ -77,8 +78,9 @@ void free_all(hq_grid_s* g) {
   if (g->tmaps) dst_tc_free(g);
 }
 
-// (2/nx)(2/ny) / lambda_kl for the 5-point Laplacian; zero on mode 0 (wall).
-std::vector<double> scale_table(const hq_grid_s* g, int rows, int cols) {
+// (2/nx)(2/ny) / (lambda_kl - shift) for the 5-point Laplacian L (shift 0: Poisson; shift c > 0:
+// the explicit solver's preconditioner (L - c)^{-1}); zero on mode 0 (wall).
+std::vector<double> scale_table(const hq_grid_s* g, int rows, int cols, double shift = 0.0) {
   std::vector<double> t((size_t)rows * cols, 0.0);
   const double pi = M_PI;
   for (int l = 1; l < g->ny; ++l) {
@@ -86,7 +88,7 @@ std::vector<double> scale_table(const hq_grid_s* g, int rows, int cols) {
     for (int k = 1; k < g->nx; ++k) {
       const double sx = std::sin(pi * k / (2.0 * g->nx));
       const double lam = -(4.0 / (g->geom.dx * g->geom.dx)) * sx * sx - (4.0 / (g->geom.dy * g->geom.dy)) * sy * sy;
-      t[(size_t)l * cols + k] = (4.0 / ((double)g->nx * g->ny)) / lam;
+      t[(size_t)l * cols + k] = (4.0 / ((double)g->nx * g->ny)) / (lam - shift);
     }
   }
   return t;
@@ -261,6 +263,22 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
   }
   { Prof p(g, HQ_K_FIELD, 1); launch_finish_main<T>(g, g->solved, slice == 0, s); }
   const int npc = g->d.n_pc_iter;
+  if (g->explicit_b) {
+    // explicit B_perp solver: source pass, then npc PCG iterations from the guess in bm
+    const void* chi_cur = g->chi[slice & 1];
+    { Prof p(g, HQ_K_TRIAL, 1); launch_explicit_src<T>(g, s); }
+    { Prof p(g, HQ_K_FIELD, 1); launch_pcg_init<T>(g, cur, chi_cur, prev, chi_prev, s); }
+    for (int k = 0; k < npc; ++k) {
+      {
+        Prof p(g, HQ_K_DST, g->fp64 ? 4 : 1);
+        if (g->fp64) dst_solve_f64(g, 2, s, reinterpret_cast<const double*>(g->scale_h));
+        else dst_solve_tc_shifted(g, 2, s);
+      }
+      { Prof p(g, HQ_K_FIELD, 4); launch_pcg_iter<T>(g, k, chi_cur, s); }
+    }
+    tape_slice_end(g);
+    return HQ_OK;
+  }
   for (int m = 0; m < npc; ++m) {
     const int last = m == npc - 1;
     tape_b_iterate(g, m);
@@ -302,7 +320,7 @@ template <typename T>
 void advance_impl(hq_grid_s* g, int slice) {
   cudaStream_t s = g->stream;
   if (slice == 0) {
-    Prof p(g, HQ_K_OTHER, 8);
+    Prof p(g, HQ_K_OTHER, g->bjp ? 9 : 8);
     launch_reset_dep<T>(g, g->dep[0], g->chi[0], s);
     launch_plasma_init<T>(g, s);
     launch_deposit_initial<T>(g, g->dep[0], g->chi[0], 0, s);
@@ -311,6 +329,7 @@ void advance_impl(hq_grid_s* g, int slice) {
     launch_zero<T>(g->bprev1, 2 * g->nnode, s);
     launch_zero<T>(g->bjn, 2 * g->nnode, s);
     launch_zero<T>(g->tj, 2 * g->nnode, s);
+    if (g->bjp) launch_zero<T>(g->bjp, 2 * g->nnode, s);
   } else {
     final_pass<T>(g, slice - 1, slice & 1);
   }
@@ -737,6 +756,12 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     return fail(nullptr, HQ_ERR_ARG, "pc_mix, psi_guard and n0_scale must be finite");
   if (d.precision != HQ_PREC_FP64 && d.precision != HQ_PREC_FP32_BF16X3)
     return fail(nullptr, HQ_ERR_ARG, "unknown precision");
+  if (d.bperp_solver != HQ_BPERP_PC && d.bperp_solver != HQ_BPERP_EXPLICIT)
+    return fail(nullptr, HQ_ERR_ARG, "unknown bperp_solver");
+  if (d.bperp_solver == HQ_BPERP_EXPLICIT && (d.n_pc_iter < 1 || d.n_pc_iter > kMaxPcg))
+    return fail(nullptr, HQ_ERR_ARG, "the explicit B_perp solver needs 1..64 iterations (n_pc_iter)");
+  if (d.bperp_solver == HQ_BPERP_EXPLICIT && !(d.n0_scale > 0.0))
+    return fail(nullptr, HQ_ERR_ARG, "the explicit B_perp solver needs n0_scale > 0 (its preconditioner shift)");
   if (d.radial_profile && (d.n_profile < 2 || !(d.profile_rmax > 0.0)))
     return fail(nullptr, HQ_ERR_ARG, "radial profile needs n_profile >= 2 and profile_rmax > 0");
   const int64_t np = (int64_t)d.nx * d.ny * d.ppc_x * d.ppc_y;
@@ -758,6 +783,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   g->dev = dev;
   g->fp64 = d.precision == HQ_PREC_FP64;
+  g->explicit_b = d.bperp_solver == HQ_BPERP_EXPLICIT;
   g->nx = d.nx; g->ny = d.ny; g->nz = d.nzeta;
   g->nnode = (int64_t)d.nx * d.ny;
   g->np = np;
@@ -829,6 +855,17 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   HQ_ALLOC(g->bjn, 2 * ts * nn);
   HQ_ALLOC(g->gf, kGF * ts * nn);
   HQ_ALLOC(g->bm, 2 * ts * nn);
+  if (g->explicit_b) {
+    HQ_ALLOC(g->bjp, 2 * ts * nn);
+    HQ_ALLOC(g->xs4, 4 * ts * nn);
+    HQ_ALLOC(g->xs1, ts * nn);
+    HQ_ALLOC(g->pcg_r, 2 * ts * nn);
+    HQ_ALLOC(g->pcg_p, 2 * ts * nn);
+    HQ_ALLOC(g->pcg_s, sizeof(double) * 4 * kMaxPcg * 2);
+    for (void* p : {g->bjp, g->pcg_r, g->pcg_p}) cudaMemset(p, 0, 2 * ts * nn);
+    cudaMemset(g->xs4, 0, 4 * ts * nn);
+    cudaMemset(g->xs1, 0, ts * nn);
+  }
   HQ_ALLOC(g->psi, ts * nn);
   HQ_ALLOC(g->bprev1, 2 * ts * nn);
   HQ_ALLOC(g->solved, kMaxRhs * ts * nn);
@@ -863,6 +900,11 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     std::vector<double> sc = scale_table(g, g->ny, g->nx);
     HQ_ALLOC(g->f64_scale, 8 * nn);
     cudaMemcpy(g->f64_scale, sc.data(), 8 * nn, cudaMemcpyHostToDevice);
+    if (g->explicit_b) {
+      std::vector<double> sh = scale_table(g, g->ny, g->nx, d.n0_scale);
+      HQ_ALLOC(g->scale_h, 8 * nn);
+      cudaMemcpy(g->scale_h, sh.data(), 8 * nn, cudaMemcpyHostToDevice);
+    }
     auto tables = [&](int n, double** tw, double** sn) -> hq_status {
       if (is_pow2(n)) {
         std::vector<double> t(2 * (size_t)n);
@@ -935,6 +977,16 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
       }
     HQ_ALLOC(g->f32_scale, 4 * scf.size());
     cudaMemcpy(g->f32_scale, scf.data(), 4 * scf.size(), cudaMemcpyHostToDevice);
+    if (g->explicit_b) {
+      std::vector<double> sh = scale_table(g, g->nyp, g->nxp, d.n0_scale);
+      for (int sy = 0; sy < g->nyp; ++sy)
+        for (int sx = 0; sx < g->nxp; ++sx) {
+          const int ky = g->fold ? fold_node(sy, g->ny) : sy, kx = g->fold ? fold_node(sx, g->nx) : sx;
+          scf[(size_t)sy * g->nxp + sx] = (float)sh[(size_t)ky * g->nxp + kx];
+        }
+      HQ_ALLOC(g->scale_h, 4 * scf.size());
+      cudaMemcpy(g->scale_h, scf.data(), 4 * scf.size(), cudaMemcpyHostToDevice);
+    }
     std::string err;
     if (dst_tc_init(g, err)) {
       g->err = err;
@@ -1137,6 +1189,7 @@ hq_status hq_sweep_forward_ckpt(hq_grid_t g, hq_beam_view* beams, int32_t nbeams
   if (witness_beam >= nbeams || (witness_beam >= 0 && !witness_sums))
     return fail(g, HQ_ERR_ARG, "witness_beam must index a beam and witness_sums must be given");
   if (ckpt_every < 1) return fail(g, HQ_ERR_ARG, "ckpt_every must be >= 1");
+  if (g->explicit_b) return fail(g, HQ_ERR_UNSUPPORTED, "the adjoint supports the predictor-corrector B_perp solver only");
   const int k = std::min<int>(ckpt_every, g->nz);
   if ((st = adj_alloc(g, k)) != HQ_OK) return st;
   AdjStore* a = adj_of(g);

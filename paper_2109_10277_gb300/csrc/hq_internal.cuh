@@ -23,6 +23,7 @@ enum : int {
 constexpr int kMaxBeams = 4;
 constexpr int kMaxRhs = 5;
 constexpr int kRing = 4;  // AB5 history slots f_{i-1} .. f_{i-4}
+constexpr int kMaxPcg = 64;   // explicit B_perp solver: at most this many PCG iterations
 
 // Fifth-order Adams-Bashforth weights (Sec. 3.2 plasma push): beta_k for f_{i-k}.
 __host__ __device__ constexpr double ab5(int k) {
@@ -140,6 +141,15 @@ struct hq_grid_s {
   void* rho_ion;
   void* tj;            // V2: trial plasma J_perp of slice i+1
   void* bjn;           // V2: beam J_perp of slice i+1
+  void* bjp;           // V2: beam J_perp of slice i-1 (explicit B_perp solver; null otherwise)
+  // explicit B_perp solver (bperp_solver = 1): its source records, PCG vectors and scalars
+  int explicit_b;
+  void* xs4;           // V4: Fx, Fy, Jxx, Jyy (deposited by the explicit source pass)
+  void* xs1;           // Jxy
+  void* pcg_r;         // V2: residual r
+  void* pcg_p;         // V2: search direction p
+  double* pcg_s;       // [4][kMaxPcg][2]: r.z, p.Ap per iteration and right-hand side
+  void* scale_h;       // the preconditioner's spectral factors 1/(lambda - c), like f32_scale / f64_scale
   void* gf;            // kGF per node (gather fields ExmBy, EypBx, Ez, Bz of the current slice)
   void* bm;            // V2: Bx, By of the current slice (the predictor-corrector iterate, then converged);
                        // until finish_main of slice i it holds the converged B_perp of slice i-1
@@ -237,8 +247,10 @@ template <typename T> void launch_finish_bperp(const hq_grid_s* g, const void* r
 template <typename T> void launch_store(const hq_grid_s* g, const hq_field_out* out, int64_t slot, const void* dep, const void* chi, cudaStream_t s);
 template <typename T> void launch_zero(void* p, int64_t n, cudaStream_t s);
 // DST backends: transform the nrhs sources prepared by the src kernels into g->solved
-void dst_solve_f64(hq_grid_s* g, int nrhs, cudaStream_t s);
+// scale: the spectral factors (null: the Poisson table f64_scale; scale_h: the shifted one)
+void dst_solve_f64(hq_grid_s* g, int nrhs, cudaStream_t s, const double* scale = nullptr);
 void dst_solve_tc(hq_grid_s* g, int nrhs, cudaStream_t s);
+void dst_solve_tc_shifted(hq_grid_s* g, int nrhs, cudaStream_t s);   // (L - c)^{-1}: g->scale_h
 void dst_solve_tc_bmix(hq_grid_s* g, int last, cudaStream_t s);   // B_perp solve + fused mixing (FP32)
 // FP32 solves with the source assembly as their first phase (no separate source kernel)
 void dst_solve_tc_main(hq_grid_s* g, const void* dep, cudaStream_t s);
@@ -251,6 +263,13 @@ template <typename T> void launch_beam_deposit(const hq_grid_s* g, int b, const 
 template <typename T> void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double dt, cudaStream_t s);
 template <typename T> void launch_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double* sums, cudaStream_t s);
 void launch_beam_moments(const hq_beam_view& v, double* m, cudaStream_t s);   // m += 11 weighted moments
+// explicit B_perp solver (k_explicit.cu): the particle source pass, the PCG start (right-hand
+// side, initial residual into the solver's operand writer, reset of the slice i-1 record) and
+// one PCG iteration after a shifted solve of the residual
+template <typename T> void launch_explicit_src(const hq_grid_s* g, cudaStream_t s);
+template <typename T> void launch_pcg_init(const hq_grid_s* g, const void* cur, const void* chi_cur, void* prev,
+                                           void* chi_prev, cudaStream_t s);
+template <typename T> void launch_pcg_iter(const hq_grid_s* g, int k, const void* chi_cur, cudaStream_t s);
 // adjoint (k_adjoint.cu)
 template <typename T> void launch_adj_final(const hq_grid_s* g, const SnapView<T>& s, const void* gf, int slice,
                                            const void* dbar_next, const AdjView<T>& a, void* tbar, void* fbar_b,

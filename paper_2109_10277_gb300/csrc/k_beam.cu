@@ -89,17 +89,20 @@ __device__ __forceinline__ int stencil_t(double x, double x0, double dx, double 
 // slice i+1 into bjn: rho = q w S / (dx dy dzeta), J = rho u / gamma (in the field type).
 template <int P, typename T>
 __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm,
-                               int slice, int nz, Geom gm, V4<T>* dep, V2<T>* bjn, float* ps) {
+                               int slice, int nz, Geom gm, V4<T>* dep, V2<T>* bjn, V2<T>* bjp, float* ps) {
   pdl_trigger();
   pdl_wait();
   const int a0 = off[slice], a1 = off[slice + 1];
   const int b0 = slice + 1 < nz ? off[slice + 1] : 0, b1 = slice + 1 < nz ? off[slice + 2] : 0;
-  const int na = a1 - a0, nb = b1 - b0;
+  // the explicit B_perp solver (bjp non-null) also takes the J_perp of slice i-1
+  const int c0 = bjp && slice > 0 ? off[slice - 1] : 0, c1 = bjp && slice > 0 ? off[slice] : 0;
+  const int na = a1 - a0, nb = b1 - b0, nc = c1 - c0;
   const double vol = gm.dx * gm.dy * gm.dzeta;
   const T rq = T(v.charge / vol);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < na + nb; t += gridDim.x * blockDim.x) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < na + nb + nc; t += gridDim.x * blockDim.x) {
     const bool cur = t < na;
-    const int p = perm[cur ? a0 + t : b0 + (t - na)];
+    const bool nxt = !cur && t < na + nb;
+    const int p = perm[cur ? a0 + t : (nxt ? b0 + (t - na) : c0 + (t - na - nb))];
     const T ux = T(v.ux[p]), uy = T(v.uy[p]), uz = T(v.uz[p]);
     const T ig = T(1) / sqrt(T(1) + ux * ux + uy * uy + uz * uz);
     // FP64: (q w) / (dx dy dzeta) as in the oracle; FP32: precomputed q / volume
@@ -129,7 +132,7 @@ __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, 
           atomicAdd(&q->d, s * cz);
           if (ps) atomicAdd(ps + node, float(s) * omvz);
         } else {
-          V2<T>* q = bjn + node;
+          V2<T>* q = (nxt ? bjn : bjp) + node;
           atomicAdd(&q->a, s * cx);
           atomicAdd(&q->b, s * cy);
         }
@@ -326,7 +329,7 @@ void launch_beam_deposit(const hq_grid_s* g, int b, const hq_beam_view& v, int s
   HQ_SHAPE_SWITCH(g->d.shape_order,
                   (launch_pdl(k_beam_deposit<P, T>, dim3(kSliceBlocks), dim3(kThreads), (size_t)0, s, v, bb.offset, bb.perm,
                              slice, g->nz, g->geom, reinterpret_cast<V4<T>*>(dep), reinterpret_cast<V2<T>*>(bjn),
-                             psrc_of(g, dep))));
+                             reinterpret_cast<V2<T>*>(g->bjp), psrc_of(g, dep))));
 }
 template <typename T>
 void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double dt, cudaStream_t s) {

@@ -127,12 +127,13 @@ void pass(const double* in, double* out, int n, int M, int R, const double* tw, 
 }  // namespace
 
 // sources in g->f64_a [R][ny][nx] -> solution in g->solved [R][ny][nx]
-void dst_solve_f64(hq_grid_s* g, int R, cudaStream_t s) {
+void dst_solve_f64(hq_grid_s* g, int R, cudaStream_t s, const double* scale) {
+  if (!scale) scale = g->f64_scale;
   const int nx = g->nx, ny = g->ny;
   double* a = g->f64_a;
   double* b = g->f64_b;
   pass(a, b, nx, ny, R, g->tw_x, g->sin_x, nullptr, s);      // (s S_x)^T      [R][nx][ny]
-  pass(b, a, ny, nx, R, g->tw_y, g->sin_y, g->f64_scale, s); // S_y s S_x / lambda (normalized)
+  pass(b, a, ny, nx, R, g->tw_y, g->sin_y, scale, s); // S_y s S_x / lambda (normalized)
   pass(a, b, nx, ny, R, g->tw_x, g->sin_x, nullptr, s);
   pass(b, reinterpret_cast<double*>(g->solved), ny, nx, R, g->tw_y, g->sin_y, nullptr, s);
 }

@@ -42,6 +42,7 @@ struct TensorMaps {
   CUtensorMap bx_hi[2], bx_lo[2];
   CUtensorMap by_hi[2], by_lo[2];
   CUtensorMap scale[2];
+  CUtensorMap scale_h[2];     // the shifted (Helmholtz) spectral factors, same boxes (explicit solver)
   int ctas[2];                // co-resident CTAs of each width
   bool wide_only;             // HQ_SOLVE_BN=64: never use the 32-wide tiles
   // resident fold-matrix solve (square folded grids, n = 256 or 512): the fold matrix in
@@ -1145,6 +1146,8 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
     bad |= make_map(enc, &t.by_hi[i], g->sy_hi, nyp, ky, err, bn);
     bad |= make_map(enc, &t.by_lo[i], g->sy_lo, nyp, ky, err, bn);
     bad |= make_map_plain(enc, &t.scale[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->f32_scale, nyp, nxp, BM, bn, err);
+    if (g->scale_h)
+      bad |= make_map_plain(enc, &t.scale_h[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->scale_h, nyp, nxp, BM, bn, err);
   }
   if (t.rs) {
     bad |= make_map(enc, &t.rf_hi, g->sx_hi, nxp, kx, err, 128);
@@ -1169,7 +1172,8 @@ namespace {
 // One cooperative launch of k_dst_solve: on the sources in op[0] (pre = 0), or forming them
 // first from the deposit records (pre = 1: psi, Ez, Bz of dep_cur; pre = 2: B_perp).
 void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s, int pre = 0,
-                 const void* dep_cur = nullptr, void* dep_prev = nullptr, void* chi_prev = nullptr) {
+                 const void* dep_cur = nullptr, void* dep_prev = nullptr, void* chi_prev = nullptr,
+                 bool shifted = false) {
   const TensorMaps& t = *g->tmaps;
   SolveArgs a{};
   a.R = R;
@@ -1180,7 +1184,7 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s, 
   a.op_lo[0] = g->op_lo[0];
   a.op_hi[1] = g->op_hi[1];
   a.op_lo[1] = g->op_lo[1];
-  a.scale = g->f32_scale;
+  a.scale = reinterpret_cast<const float*>(shifted ? g->scale_h : g->f32_scale);
   a.final_mode = final_mode;
   a.out = reinterpret_cast<float*>(g->solved);
   a.nx = g->nx;
@@ -1233,7 +1237,7 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s, 
   cfg.numAttrs = 1;
   // a launch error is reported by the caller's launch check
   cudaLaunchKernelEx(&cfg, narrow ? k_dst_solve<32> : k_dst_solve<64>, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi[v],
-                     t.bx_lo[v], t.by_hi[v], t.by_lo[v], t.scale[v], a);
+                     t.bx_lo[v], t.by_hi[v], t.by_lo[v], shifted ? t.scale_h[v] : t.scale[v], a);
 }
 
 }  // namespace
@@ -1244,6 +1248,9 @@ void dst_solve_tc_bmix(hq_grid_s* g, int last, cudaStream_t s) { solve_fused(g, 
 
 // sources (split) in op[0] -> FP32 solution in g->solved [R][ny][nx]
 void dst_solve_tc(hq_grid_s* g, int R, cudaStream_t s) { solve_fused(g, R, 2, 0, s); }
+void dst_solve_tc_shifted(hq_grid_s* g, int R, cudaStream_t s) {
+  solve_fused(g, R, 2, 0, s, 0, nullptr, nullptr, nullptr, true);
+}
 
 // The same with the source kernels folded into the launch as its first phase: psi, Ez, Bz of
 // the deposit record dep -> g->solved; the B_perp sources of the predictor-corrector (which
