@@ -590,6 +590,129 @@ class SweepResult:
     plasma_at: dict = field(default_factory=dict)    # slice -> plasma state at that slice
 
 
+class SliceLoop:
+    """The slice loop's state and per-slice body (Sec. 2 enumerate, Fig. 1; Sec. 3.2
+    predictor-corrector), one slice per call: the plasma slice with its AB5 history, the
+    previous slices' plasma J_perp, beam J_perp and B_perp, and the deposit of the slice
+    about to be solved.  ``sweep`` drives it over the whole box; the temporal pipeline of
+    Sec. 5.2 drives it box by box with the beam handed over from the previous time step.
+
+    Per slice i (``slice``): deposit plasma + ions + beam(i); solve psi -> ExmBy, EypBx; Ez;
+    Bz; predictor-corrector (or the explicit solver) for Bx, By; final gather; push the
+    beam particles of slice i; final AB5 step of the plasma to slice i + 1.
+    """
+
+    def __init__(self, spec: GridSpec, n0_scale: Optional[torch.Tensor] = None,
+                 radial_profile: Optional[torch.Tensor] = None, plasma_perm: Optional[torch.Tensor] = None,
+                 reverse_ion_order: bool = False, deposit_noise: float = 0.0, noise_seed: int = 0):
+        self.spec = spec
+        st = plasma_init(spec, n0_scale, radial_profile)
+        if plasma_perm is not None:
+            st = {k: v[plasma_perm] for k, v in st.items()}
+        rho_ion = ion_background(spec, st, reverse=reverse_ion_order)
+        self.gen = torch.Generator().manual_seed(noise_seed)
+        self.deposit_noise = deposit_noise
+        self.rho_ion = self.noisy([rho_ion])[0]
+        zero = torch.zeros(spec.ny, spec.nx, dtype=DT)
+        self.zero = zero
+        self.hist = [(torch.zeros_like(st["x"]),) * 5 for _ in range(4)]  # f_{i-1} .. f_{i-4}
+        self.jx_prev, self.jy_prev = zero, zero
+        self.bj_prev = (zero, zero)   # beam J_perp of slice i-1 (explicit solver)
+        self.b1 = (zero, zero)
+        self.b2 = (zero, zero)
+        self.st = st
+        self.src = self.noisy(plasma_deposit_full(spec, st))
+
+    def noisy(self, fields):
+        if self.deposit_noise <= 0.0:
+            return fields
+        return [f * (1.0 + self.deposit_noise * (2.0 * torch.rand(f.shape, generator=self.gen, dtype=DT) - 1.0))
+                for f in fields]
+
+    def slice(self, i: int, cur: Sequence[tuple], nxt: Sequence[tuple], dt: float = 0.0,
+              witness: Sequence[int] = ()):
+        """Solves slice i.  cur: (beam, sel) pairs, the beam particles `sel` of slice i (one per
+        beam); nxt: the same for slice i + 1 (their J_perp enters the predictor-corrector);
+        witness: indices into cur whose sums q w (1, Ez, Ez^2) are returned.  Returns (fields,
+        last P-C residual, cur's beams after the push of dt (unchanged for dt = 0), witness sums)."""
+        spec, zero = self.spec, self.zero
+        dz = spec.dzeta
+        qm = PLASMA_Q / PLASMA_M
+        st, hist = self.st, self.hist
+        rho, jx, jy, jz, chi = self.src
+        rho = rho + self.rho_ion
+        bj_cur = (zero, zero)
+        for b, sel in cur:
+            brho, bjx, bjy, bjz = beam_deposit_slice(spec, b, sel)
+            rho, jx, jy, jz = rho + brho, jx + bjx, jy + bjy, jz + bjz
+            bj_cur = (bj_cur[0] + bjx, bj_cur[1] + bjy)
+        psi = poisson_solve(spec, -(rho - jz))
+        exmby, eypbx = -ddx(spec, psi), -ddy(spec, psi)
+        ez = poisson_solve(spec, ddx(spec, jx) + ddy(spec, jy))
+        bz = poisson_solve(spec, ddy(spec, jx) - ddx(spec, jy))
+        b1, b2 = self.b1, self.b2
+        bx, by = 2.0 * b1[0] - b2[0], 2.0 * b1[1] - b2[1]
+        sbx0, sby0 = -ddy(spec, jz), ddx(spec, jz)
+        njx, njy = zero, zero
+        if i + 1 < spec.nzeta:
+            for b, sel in nxt:
+                tjx, tjy = beam_deposit_slice(spec, b, sel, ("jx", "jy"))
+                njx, njy = njx + tjx, njy + tjy
+        resid = 0.0
+        if spec.bperp_solver == "explicit":
+            # explicit solver: (L - chi) Bx = -dy Jz + Ty, (L - chi) By = dx Jz - Tx with T the
+            # B-independent part of d(J_perp)/d(zeta) (explicit_sources; beams by central differences)
+            F4 = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bz), spec.shape_order)
+            fx, fy, jxx, jxy, jyy = self.noisy(explicit_sources(spec, st, F4))
+            tx = fx + ddx(spec, jxx) + ddy(spec, jxy) + (self.bj_prev[0] - njx) / (2.0 * dz)
+            ty = fy + ddx(spec, jxy) + ddy(spec, jyy) + (self.bj_prev[1] - njy) / (2.0 * dz)
+            (bx, by), rr = helmholtz_pcg(spec, chi, (sbx0 + ty, sby0 - tx), (bx, by), spec.n0_scale,
+                                         spec.n_pc_iter)
+            resid = max(rr)
+        for _m in range(spec.n_pc_iter if spec.bperp_solver == "pc" else 0):
+            F = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bx, by, bz), spec.shape_order)
+            f = derivs(qm, st["ux"], st["uy"], st["psi"], F)
+            tx, ty, tux, tuy, tpsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
+                                              [f] + hist, dz)
+            ok = st["alive"] & _state_ok(spec, tx, ty, tpsi)
+            pjx, pjy = self.noisy(plasma_deposit_jperp(spec, tx, ty, tux, tuy, tpsi, st["w"], ok))
+            jx1, jy1 = pjx + njx, pjy + njy
+            dzjx, dzjy = (self.jx_prev - jx1) / (2.0 * dz), (self.jy_prev - jy1) / (2.0 * dz)
+            bxs = poisson_solve(spec, sbx0 + dzjy)
+            bys = poisson_solve(spec, sby0 - dzjx)
+            nbx = spec.pc_mix * bxs + (1.0 - spec.pc_mix) * bx
+            nby = spec.pc_mix * bys + (1.0 - spec.pc_mix) * by
+            num = torch.sqrt(((nbx - bx) ** 2).sum() + ((nby - by) ** 2).sum()).detach()
+            den = torch.sqrt((nbx ** 2).sum() + (nby ** 2).sum()).detach()
+            resid = float(num / den) if float(den) > 0 else 0.0
+            bx, by = nbx, nby
+        Fs = (exmby, eypbx, ez, bx, by, bz)
+        F = gather(spec, st["x"], st["y"], Fs, spec.shape_order)
+        f = derivs(qm, st["ux"], st["uy"], st["psi"], F)
+        out = dict(rho=rho, jx=jx, jy=jy, jz=jz, chi=chi, psi=psi, exmby=exmby, eypbx=eypbx,
+                   ez=ez, bx=bx, by=by, bz=bz)
+        wsums = []
+        for wi in witness:
+            b, sel = cur[wi]
+            (ezw,) = gather(spec, b["x"][sel], b["y"][sel], (ez,), spec.shape_order)
+            qw = b["charge"] * b["w"][sel]
+            wsums.append((qw.sum(), (qw * ezw).sum(), (qw * ezw * ezw).sum()))
+        pushed = [beam_push(spec, b, sel, Fs, dt) if dt != 0.0 else b for b, sel in cur]
+        # final AB5 step to slice i+1 with the converged fields, then removal and deposit
+        nx_, ny_, nux, nuy, npsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
+                                            [f] + hist, dz)
+        self.hist = [f] + hist[:3]
+        alive = st["alive"] & _state_ok(spec, nx_, ny_, npsi)
+        keep = lambda new, old: torch.where(alive, new, old)  # noqa: E731
+        self.st = dict(x=keep(nx_, st["x"]), y=keep(ny_, st["y"]), ux=keep(nux, st["ux"]),
+                       uy=keep(nuy, st["uy"]), psi=keep(npsi, st["psi"]), w=st["w"], alive=alive)
+        self.src = self.noisy(plasma_deposit_full(spec, self.st))
+        self.jx_prev, self.jy_prev = jx, jy
+        self.bj_prev = bj_cur
+        self.b2, self.b1 = b1, (bx, by)
+        return out, resid, pushed, wsums
+
+
 def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
           n_slices: Optional[int] = None, record: Sequence[str] = FIELD_NAMES,
           witness: Sequence[int] = (), record_plasma_at: Sequence[int] = (),
@@ -597,12 +720,10 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
           plasma_perm: Optional[torch.Tensor] = None, reverse_ion_order: bool = False,
           deposit_noise: float = 0.0, noise_seed: int = 0,
           crop: Optional[Sequence[int]] = None) -> SweepResult:
-    """One quasi-static sweep head -> tail (Sec. 2), slices i = 0 .. n_slices-1.
+    """One quasi-static sweep head -> tail (Sec. 2), slices i = 0 .. n_slices-1 (SliceLoop).
 
-    Per slice (Sec. 2 steps 1-7 and the Sec. 3.2 predictor-corrector):
-      deposit plasma + ions + beam(i); solve psi -> ExmBy, EypBx; Ez; Bz;
-      predictor-corrector for Bx, By; final gather; push plasma to i+1.
-    dt != 0 also advances every beam particle once with its own slice's fields.
+    The beams are binned by slice once, at the start (Sec. 3.1: beam particles sorted per
+    slice); dt != 0 advances every beam particle once with its own slice's fields.
     plasma_perm (a permutation of the plasma particles) changes only the order in
     which particle contributions are summed; results are returned in the original order.
     reverse_ion_order sums the ion background in the opposite stencil order, so its
@@ -613,23 +734,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     crop = (y0, y1, x0, x1) records only the nodes [y0:y1, x0:x1] of each field (memory).
     """
     ns = spec.nzeta if n_slices is None else n_slices
-    dz = spec.dzeta
-    qm = PLASMA_Q / PLASMA_M
-    st = plasma_init(spec, n0_scale, radial_profile)
-    if plasma_perm is not None:
-        st = {k: v[plasma_perm] for k, v in st.items()}
-    rho_ion = ion_background(spec, st, reverse=reverse_ion_order)
-    gen = torch.Generator().manual_seed(noise_seed)
-
-    def noisy(fields):
-        if deposit_noise <= 0.0:
-            return fields
-        return [f * (1.0 + deposit_noise * (2.0 * torch.rand(f.shape, generator=gen, dtype=DT) - 1.0))
-                for f in fields]
-
-    rho_ion = noisy([rho_ion])[0]
-    zero = torch.zeros(spec.ny, spec.nx, dtype=DT)
-    hist = [(torch.zeros_like(st["x"]),) * 5 for _ in range(4)]  # f_{i-1} .. f_{i-4}
+    loop = SliceLoop(spec, n0_scale, radial_profile, plasma_perm, reverse_ion_order, deposit_noise, noise_seed)
     beams = [dict(b) for b in beams]
     csr = [beam_csr(spec, beam_bins(spec, b["zeta"])) for b in beams]
     sel_of = lambda bi, i: csr[bi][1][csr[bi][0][i]:csr[bi][0][i + 1]]  # noqa: E731
@@ -637,89 +742,21 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     res = SweepResult()
     rec = {k: [] for k in record}
     wit = {bi: [torch.zeros((), dtype=DT)] * 3 for bi in witness}
-    jx_prev, jy_prev = zero, zero
-    bj_prev = (zero, zero)   # beam J_perp of slice i-1 (explicit solver)
-    b1 = (zero, zero)
-    b2 = (zero, zero)
-    src = noisy(plasma_deposit_full(spec, st))
+    witness = list(witness)
     for i in range(ns):
         if i in record_plasma_at:
-            res.plasma_at[i] = {k: v.detach().clone() for k, v in st.items()}
-        rho, jx, jy, jz, chi = src
-        rho = rho + rho_ion
-        bj_cur = (zero, zero)
-        for bi, b in enumerate(beams):
-            brho, bjx, bjy, bjz = beam_deposit_slice(spec, b, sel_of(bi, i))
-            rho, jx, jy, jz = rho + brho, jx + bjx, jy + bjy, jz + bjz
-            bj_cur = (bj_cur[0] + bjx, bj_cur[1] + bjy)
-        psi = poisson_solve(spec, -(rho - jz))
-        exmby, eypbx = -ddx(spec, psi), -ddy(spec, psi)
-        ez = poisson_solve(spec, ddx(spec, jx) + ddy(spec, jy))
-        bz = poisson_solve(spec, ddy(spec, jx) - ddx(spec, jy))
-        bx, by = 2.0 * b1[0] - b2[0], 2.0 * b1[1] - b2[1]
-        sbx0, sby0 = -ddy(spec, jz), ddx(spec, jz)
-        njx, njy = zero, zero
-        if i + 1 < spec.nzeta:
-            for bi, b in enumerate(beams):
-                tjx, tjy = beam_deposit_slice(spec, b, sel_of(bi, i + 1), ("jx", "jy"))
-                njx, njy = njx + tjx, njy + tjy
-        resid = 0.0
-        if spec.bperp_solver == "explicit":
-            # explicit solver: (L - chi) Bx = -dy Jz + Ty, (L - chi) By = dx Jz - Tx with T the
-            # B-independent part of d(J_perp)/d(zeta) (explicit_sources; beams by central differences)
-            F4 = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bz), spec.shape_order)
-            fx, fy, jxx, jxy, jyy = noisy(explicit_sources(spec, st, F4))
-            tx = fx + ddx(spec, jxx) + ddy(spec, jxy) + (bj_prev[0] - njx) / (2.0 * dz)
-            ty = fy + ddx(spec, jxy) + ddy(spec, jyy) + (bj_prev[1] - njy) / (2.0 * dz)
-            (bx, by), rr = helmholtz_pcg(spec, chi, (sbx0 + ty, sby0 - tx), (bx, by), spec.n0_scale,
-                                         spec.n_pc_iter)
-            resid = max(rr)
-        for _m in range(spec.n_pc_iter if spec.bperp_solver == "pc" else 0):
-            F = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bx, by, bz), spec.shape_order)
-            f = derivs(qm, st["ux"], st["uy"], st["psi"], F)
-            tx, ty, tux, tuy, tpsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
-                                              [f] + hist, dz)
-            ok = st["alive"] & _state_ok(spec, tx, ty, tpsi)
-            pjx, pjy = noisy(plasma_deposit_jperp(spec, tx, ty, tux, tuy, tpsi, st["w"], ok))
-            jx1, jy1 = pjx + njx, pjy + njy
-            dzjx, dzjy = (jx_prev - jx1) / (2.0 * dz), (jy_prev - jy1) / (2.0 * dz)
-            bxs = poisson_solve(spec, sbx0 + dzjy)
-            bys = poisson_solve(spec, sby0 - dzjx)
-            nbx = spec.pc_mix * bxs + (1.0 - spec.pc_mix) * bx
-            nby = spec.pc_mix * bys + (1.0 - spec.pc_mix) * by
-            num = torch.sqrt(((nbx - bx) ** 2).sum() + ((nby - by) ** 2).sum()).detach()
-            den = torch.sqrt((nbx ** 2).sum() + (nby ** 2).sum()).detach()
-            resid = float(num / den) if float(den) > 0 else 0.0
-            bx, by = nbx, nby
+            res.plasma_at[i] = {k: v.detach().clone() for k, v in loop.st.items()}
+        cur = [(b, sel_of(bi, i)) for bi, b in enumerate(beams)]
+        nxt = [(b, sel_of(bi, i + 1)) for bi, b in enumerate(beams)] if i + 1 < spec.nzeta else []
+        out, resid, pushed, wsums = loop.slice(i, cur, nxt, dt, witness)
         res.pc_residual.append(resid)
-        Fs = (exmby, eypbx, ez, bx, by, bz)
-        F = gather(spec, st["x"], st["y"], Fs, spec.shape_order)
-        f = derivs(qm, st["ux"], st["uy"], st["psi"], F)
-        out = dict(rho=rho, jx=jx, jy=jy, jz=jz, chi=chi, psi=psi, exmby=exmby, eypbx=eypbx,
-                   ez=ez, bx=bx, by=by, bz=bz)
         for k in record:
             rec[k].append(out[k] if crop is None else out[k][crop[0]:crop[1], crop[2]:crop[3]].clone())
-        for bi in witness:
-            sel = sel_of(bi, i)
-            (ezw,) = gather(spec, beams[bi]["x"][sel], beams[bi]["y"][sel], (ez,), spec.shape_order)
-            qw = beams[bi]["charge"] * beams[bi]["w"][sel]
+        for bi, (w0, w1, w2) in zip(witness, wsums):
             s0, s1, s2 = wit[bi]
-            wit[bi] = [s0 + qw.sum(), s1 + (qw * ezw).sum(), s2 + (qw * ezw * ezw).sum()]
-        if dt != 0.0:
-            for bi in range(len(beams)):
-                beams[bi] = beam_push(spec, beams[bi], sel_of(bi, i), Fs, dt)
-        # final AB5 step to slice i+1 with the converged fields, then removal and deposit
-        nx_, ny_, nux, nuy, npsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
-                                            [f] + hist, dz)
-        hist = [f] + hist[:3]
-        alive = st["alive"] & _state_ok(spec, nx_, ny_, npsi)
-        keep = lambda new, old: torch.where(alive, new, old)  # noqa: E731
-        st = dict(x=keep(nx_, st["x"]), y=keep(ny_, st["y"]), ux=keep(nux, st["ux"]),
-                  uy=keep(nuy, st["uy"]), psi=keep(npsi, st["psi"]), w=st["w"], alive=alive)
-        src = noisy(plasma_deposit_full(spec, st))
-        jx_prev, jy_prev = jx, jy
-        bj_prev = bj_cur
-        b2, b1 = b1, (bx, by)
+            wit[bi] = [s0 + w0, s1 + w1, s2 + w2]
+        beams = pushed
+    st = loop.st
     res.fields = {k: torch.stack(v) for k, v in rec.items()}
     res.removed = int((~st["alive"]).sum())
     if plasma_perm is not None:
