@@ -155,9 +155,13 @@ hq_status hq_advance_slice(hq_grid_t grid, int32_t slice);
 /* Sec. 2 step 3 and Sec. 3.1 (beams sorted per slice): adds the charge and
  * current of the beam particles whose zeta falls in slice i (order 0
  * longitudinally), and stores J_perp of slice i+1 for the predictor-corrector.
- * On slice 0 the beams are binned by slice (counting sort on the device); later
- * slices of the same sweep must pass the same views (HQ_ERR_STATE otherwise).
- * At most 4 beams.  Requires hq_advance_slice(i). */
+ * Views are binned by slice (counting sort on the device on their current zeta): on
+ * slice 0 all of them; on a later slice only a view not passed at the slice before
+ * (its particles must not have been pushed in this sweep), while a view passed before
+ * keeps its bins and a view no longer passed is forgotten.  So a beam can arrive box
+ * by box (Sec. 5.2 temporal pipeline): pass the next box's view on the last slice of
+ * the current one, whose J_perp(i+1) it supplies.  At most 4 views per call.  Requires
+ * hq_advance_slice(i). */
 hq_status hq_beam_deposit(hq_grid_t grid, const hq_beam_view* beams, int32_t nbeams, int32_t slice);
 
 /* Sec. 2 steps 4-7 and Sec. 3.2 (fast Poisson solver, predictor-corrector):
@@ -172,12 +176,21 @@ hq_status hq_store_fields(hq_grid_t grid, const hq_field_out* out, int64_t slot)
 
 /* Sec. 3.2 (beam pusher): advances the particles of slice i of each beam by dt
  * with a second-order drift-kick-drift step (Boris kick) in the fields of the last
- * solved slice, which must be i.  Positions and momenta are updated in place. */
+ * solved slice, which must be i.  Positions and momenta are updated in place.  Each
+ * view must have been passed to hq_beam_deposit(i) (HQ_ERR_STATE otherwise). */
 hq_status hq_push_beams(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, int32_t slice, double dt);
 
 /* Adds sum(q w), sum(q w Ez), sum(q w Ez^2) over the particles of slice i of
  * `beam` (Ez gathered with the grid's shape) to sums[0..2] (DEVICE double[3]). */
 hq_status hq_witness_accumulate(hq_grid_t grid, const hq_beam_view* beam, int32_t slice, double* sums);
+
+/* Sec. 3.1 (beam particles sorted per slice) and Sec. 5.2 (temporal pipeline: a box's
+ * particles are handed to the next time step): writes the slice of every particle of
+ * `beam` to slices[0..n) (DEVICE int32[n]) with the arithmetic hq_beam_deposit bins by,
+ * floor((zeta_max - zeta) / dzeta) in FP64: 0..nzeta-1 inside the box, -1 ahead of its
+ * head (zeta above zeta_max), nzeta behind its tail, -2 for a non-finite zeta.  Queued on
+ * the grid's stream; needs no slice state.  Errors: HQ_ERR_ARG. */
+hq_status hq_beam_slices(hq_grid_t grid, const hq_beam_view* beam, int32_t* slices);
 
 /* Sec. 6 (precision study: the witness beam's emittance over many time steps): adds the
  * weighted raw moments of all particles of `beam` to moments[0..10] (DEVICE double[11],

@@ -267,14 +267,14 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
     // explicit B_perp solver: source pass, then npc PCG iterations from the guess in bm
     const void* chi_cur = g->chi[slice & 1];
     { Prof p(g, HQ_K_TRIAL, 1); launch_explicit_src<T>(g, s); }
-    { Prof p(g, HQ_K_FIELD, 1); launch_pcg_init<T>(g, cur, chi_cur, prev, chi_prev, s); }
+    { Prof p(g, HQ_K_FIELD, 1); launch_pcg_init<T>(g, slice, cur, chi_cur, prev, chi_prev, s); }
     for (int k = 0; k < npc; ++k) {
       {
         Prof p(g, HQ_K_DST, g->fp64 ? 4 : 1);
         if (g->fp64) dst_solve_f64(g, 2, s, reinterpret_cast<const double*>(g->scale_h));
         else dst_solve_tc_shifted(g, 2, s);
       }
-      { Prof p(g, HQ_K_FIELD, 4); launch_pcg_iter<T>(g, k, chi_cur, s); }
+      { Prof p(g, HQ_K_FIELD, 4); launch_pcg_iter<T>(g, slice, k, chi_cur, s); }
     }
     tape_slice_end(g);
     return HQ_OK;
@@ -329,7 +329,7 @@ void advance_impl(hq_grid_s* g, int slice) {
     launch_zero<T>(g->bprev1, 2 * g->nnode, s);
     launch_zero<T>(g->bjn, 2 * g->nnode, s);
     launch_zero<T>(g->tj, 2 * g->nnode, s);
-    if (g->bjp) launch_zero<T>(g->bjp, 2 * g->nnode, s);
+    if (g->bjp) launch_zero<T>(g->bjp, 4 * g->nnode, s);
   } else {
     final_pass<T>(g, slice - 1, slice & 1);
   }
@@ -349,40 +349,6 @@ hq_status check_views(hq_grid_s* g, const hq_beam_view* beams, int nb) {
     if (v.n > 0 && (!v.x || !v.y || !v.zeta || !v.ux || !v.uy || !v.uz || !v.w))
       return fail(g, HQ_ERR_ARG, "beam array is NULL");
     if (!(v.mass > 0.0) || !std::isfinite(v.charge)) return fail(g, HQ_ERR_ARG, "beam charge/mass invalid");
-  }
-  return HQ_OK;
-}
-
-template <typename T>
-hq_status beam_deposit_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int slice) {
-  cudaStream_t s = g->stream;
-  if (slice == 0) {
-    for (int b = 0; b < nb; ++b) {
-      BeamBins& bb = g->bins[b];
-      if (bb.cap < beams[b].n) {
-        if (bb.bin) cudaFree(bb.bin);
-        if (bb.perm) cudaFree(bb.perm);
-        bb.bin = bb.perm = nullptr;
-        bb.cap = 0;
-        HQ_CUDA(g, dalloc(&bb.bin, sizeof(int32_t) * beams[b].n));
-        HQ_CUDA(g, dalloc(&bb.perm, sizeof(int32_t) * beams[b].n));
-        bb.cap = beams[b].n;
-      }
-      g->bound[b] = beams[b];
-      Prof p(g, HQ_K_BEAM, beams[b].n > 0 ? 3 : 1);
-      launch_beam_bin(g, b, beams[b], s);
-    }
-    g->nbound = nb;
-  } else {
-    if (nb != g->nbound) return fail(g, HQ_ERR_STATE, "beams differ from those binned at slice 0");
-    for (int b = 0; b < nb; ++b)
-      if (!same_view(beams[b], g->bound[b])) return fail(g, HQ_ERR_STATE, "beams differ from those binned at slice 0");
-  }
-  // bjn (beam J_perp of slice i+1) was cleared at the end of the previous slice's solve
-  for (int b = 0; b < nb; ++b) {
-    if (beams[b].n == 0) continue;
-    Prof p(g, HQ_K_BEAM, 1);
-    launch_beam_deposit<T>(g, b, beams[b], slice, g->dep[slice & 1], g->bjn, s);
   }
   return HQ_OK;
 }
@@ -472,6 +438,63 @@ void ckpt_copy(hq_grid_s* g, int seg, bool save) {
     cp(a->ck_ps0[seg], g->psrc[0], 4 * nn);
     cp(a->ck_ps1[seg], g->psrc[1], 4 * nn);
   }
+}
+
+// Binds view `v` to bin slot k: counting sort of its particles by slice at their current zeta.
+hq_status bind_view(hq_grid_s* g, int k, const hq_beam_view& v) {
+  BeamBins& bb = g->bins[k];
+  if (bb.cap < v.n) {
+    if (bb.bin) cudaFree(bb.bin);
+    if (bb.perm) cudaFree(bb.perm);
+    bb.bin = bb.perm = nullptr;
+    bb.cap = 0;
+    HQ_CUDA(g, dalloc(&bb.bin, sizeof(int32_t) * v.n));
+    HQ_CUDA(g, dalloc(&bb.perm, sizeof(int32_t) * v.n));
+    bb.cap = v.n;
+  }
+  g->bound[k] = v;
+  Prof p(g, HQ_K_BEAM, v.n > 0 ? 3 : 1);
+  launch_beam_bin(g, k, v, g->stream);
+  return HQ_OK;
+}
+
+template <typename T>
+hq_status beam_deposit_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int slice) {
+  cudaStream_t s = g->stream;
+  // Slice 0 bins every view for the sweep.  A later slice keeps the bins of the views it was
+  // already given (their particles of later slices have not been pushed) and bins a view it
+  // has not seen before into a slot that no view of this call holds; views missing from the
+  // call lose their slot.  This is how a beam arrives box by box (Sec. 5.2 temporal pipeline).
+  int slot[kMaxBeams];
+  hq_status st;
+  if (slice == 0) {
+    for (int b = 0; b < nb; ++b)
+      if ((st = bind_view(g, slot[b] = b, beams[b])) != HQ_OK) return st;
+    for (int k = nb; k < kMaxBeams; ++k) g->bound[k].n = -1;
+  } else {
+    bool held[kMaxBeams] = {};
+    for (int b = 0; b < nb; ++b) {
+      slot[b] = bound_index(g, &beams[b]);
+      if (slot[b] >= 0) held[slot[b]] = true;
+    }
+    for (int b = 0; b < nb; ++b) {
+      if (slot[b] >= 0) continue;
+      int k = 0;
+      while (held[k]) ++k;   // nb <= kMaxBeams views: a free slot exists
+      held[k] = true;
+      if ((st = bind_view(g, slot[b] = k, beams[b])) != HQ_OK) return st;
+    }
+    for (int k = 0; k < kMaxBeams; ++k)
+      if (!held[k]) g->bound[k].n = -1;
+  }
+  g->nbound = kMaxBeams;
+  // bjn (beam J_perp of slice i+1) was cleared at the end of the previous slice's solve
+  for (int b = 0; b < nb; ++b) {
+    if (beams[b].n == 0) continue;
+    Prof p(g, HQ_K_BEAM, 1);
+    launch_beam_deposit<T>(g, slot[b], beams[b], slice, g->dep[slice & 1], g->bjn, s);
+  }
+  return HQ_OK;
 }
 
 // Runs slices [a0, a1) from the state after hq_advance_slice(a0), taping slices >= tape_from.
@@ -856,13 +879,14 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   HQ_ALLOC(g->gf, kGF * ts * nn);
   HQ_ALLOC(g->bm, 2 * ts * nn);
   if (g->explicit_b) {
-    HQ_ALLOC(g->bjp, 2 * ts * nn);
+    HQ_ALLOC(g->bjp, 4 * ts * nn);
     HQ_ALLOC(g->xs4, 4 * ts * nn);
     HQ_ALLOC(g->xs1, ts * nn);
     HQ_ALLOC(g->pcg_r, 2 * ts * nn);
     HQ_ALLOC(g->pcg_p, 2 * ts * nn);
     HQ_ALLOC(g->pcg_s, sizeof(double) * 4 * kMaxPcg * 2);
-    for (void* p : {g->bjp, g->pcg_r, g->pcg_p}) cudaMemset(p, 0, 2 * ts * nn);
+    for (void* p : {g->pcg_r, g->pcg_p}) cudaMemset(p, 0, 2 * ts * nn);
+    cudaMemset(g->bjp, 0, 4 * ts * nn);
     cudaMemset(g->xs4, 0, 4 * ts * nn);
     cudaMemset(g->xs1, 0, ts * nn);
   }
@@ -1076,7 +1100,7 @@ hq_status hq_push_beams(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, int32_
   if (!std::isfinite(dt)) return fail(g, HQ_ERR_ARG, "dt must be finite");
   for (int b = 0; b < nbeams; ++b) {
     const int k = bound_index(g, &beams[b]);
-    if (k < 0) return fail(g, HQ_ERR_STATE, "beam was not binned at slice 0 of this sweep");
+    if (k < 0) return fail(g, HQ_ERR_STATE, "beam was not given to hq_beam_deposit in this sweep");
     if (beams[b].n == 0) continue;
     Prof p(g, HQ_K_BEAM, 1);
     if (g->fp64) launch_beam_push<double>(g, k, beams[b], slice, dt, g->stream);
@@ -1090,11 +1114,22 @@ hq_status hq_witness_accumulate(hq_grid_t g, const hq_beam_view* beam, int32_t s
   if (!beam || !sums) return fail(g, HQ_ERR_ARG, "beam and sums must not be NULL");
   if (g->last_solved != slice) return fail(g, HQ_ERR_STATE, "hq_witness_accumulate(i) needs hq_solve_fields(i)");
   const int k = bound_index(g, beam);
-  if (k < 0) return fail(g, HQ_ERR_STATE, "beam was not binned at slice 0 of this sweep");
+  if (k < 0) return fail(g, HQ_ERR_STATE, "beam was not given to hq_beam_deposit in this sweep");
   if (beam->n == 0) return HQ_OK;
   Prof p(g, HQ_K_BEAM, 1);
   if (g->fp64) launch_witness<double>(g, k, *beam, slice, sums, g->stream);
   else launch_witness<float>(g, k, *beam, slice, sums, g->stream);
+  return check_launch(g);
+}
+
+hq_status hq_beam_slices(hq_grid_t g, const hq_beam_view* beam, int32_t* slices) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (!beam || (beam->n > 0 && !slices)) return fail(g, HQ_ERR_ARG, "beam and slices must not be NULL");
+  hq_status st = check_views(g, beam, 1);
+  if (st != HQ_OK) return st;
+  if (beam->n == 0) return HQ_OK;
+  Prof p(g, HQ_K_BEAM, 1);
+  launch_beam_slices(g, *beam, slices, g->stream);
   return check_launch(g);
 }
 

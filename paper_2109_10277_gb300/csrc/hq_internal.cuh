@@ -141,7 +141,7 @@ struct hq_grid_s {
   void* rho_ion;
   void* tj;            // V2: trial plasma J_perp of slice i+1
   void* bjn;           // V2: beam J_perp of slice i+1
-  void* bjp;           // V2: beam J_perp of slice i-1 (explicit B_perp solver; null otherwise)
+  void* bjp;           // 2 x V2: beam J_perp of slices i-1 and i by slice parity (explicit B_perp solver; null otherwise)
   // explicit B_perp solver (bperp_solver = 1): its source records, PCG vectors and scalars
   int explicit_b;
   void* xs4;           // V4: Fx, Fy, Jxx, Jyy (deposited by the explicit source pass)
@@ -259,6 +259,7 @@ int dst_tc_init(hq_grid_s* g, std::string& err);   // builds tensor maps; 0 on s
 void dst_tc_free(hq_grid_s* g);
 // beams
 void launch_beam_bin(hq_grid_s* g, int b, const hq_beam_view& v, cudaStream_t s);
+void launch_beam_slices(const hq_grid_s* g, const hq_beam_view& v, int32_t* out, cudaStream_t s);
 template <typename T> void launch_beam_deposit(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, void* dep, void* bjn, cudaStream_t s);
 template <typename T> void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double dt, cudaStream_t s);
 template <typename T> void launch_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double* sums, cudaStream_t s);
@@ -267,9 +268,9 @@ void launch_beam_moments(const hq_beam_view& v, double* m, cudaStream_t s);   //
 // side, initial residual into the solver's operand writer, reset of the slice i-1 record) and
 // one PCG iteration after a shifted solve of the residual
 template <typename T> void launch_explicit_src(const hq_grid_s* g, cudaStream_t s);
-template <typename T> void launch_pcg_init(const hq_grid_s* g, const void* cur, const void* chi_cur, void* prev,
+template <typename T> void launch_pcg_init(const hq_grid_s* g, int slice, const void* cur, const void* chi_cur, void* prev,
                                            void* chi_prev, cudaStream_t s);
-template <typename T> void launch_pcg_iter(const hq_grid_s* g, int k, const void* chi_cur, cudaStream_t s);
+template <typename T> void launch_pcg_iter(const hq_grid_s* g, int slice, int k, const void* chi_cur, cudaStream_t s);
 // adjoint (k_adjoint.cu)
 template <typename T> void launch_adj_final(const hq_grid_s* g, const SnapView<T>& s, const void* gf, int slice,
                                            const void* dbar_next, const AdjView<T>& a, void* tbar, void* fbar_b,
@@ -470,6 +471,13 @@ inline dim3 src_grid(const hq_grid_s* g) {
 inline float* psrc_of(const hq_grid_s* g, const void* dep) {
   if (g->fp64) return nullptr;
   return dep == g->dep[0] ? g->psrc[0] : dep == g->dep[1] ? g->psrc[1] : nullptr;
+}
+
+// Explicit B_perp solver: the beam J_perp record of slice `slice` (parity-indexed pair; null
+// without the explicit solver).  Slice i deposits into bjp_at(i) and reads bjp_at(i - 1).
+inline void* bjp_at(const hq_grid_s* g, int slice) {
+  if (!g->bjp) return nullptr;
+  return static_cast<char*>(g->bjp) + (size_t)(slice & 1) * 2 * (g->fp64 ? 8 : 4) * (size_t)g->nnode;
 }
 
 template <typename T> struct SrcMain;

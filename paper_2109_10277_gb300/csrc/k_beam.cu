@@ -27,6 +27,15 @@ __global__ void k_bin_count(const double* __restrict__ zeta, int64_t n, double z
   if (ok) atomicAdd(count + b, 1);
 }
 
+// The slice of every particle with the binning's arithmetic: 0..nz-1 inside the box, -1 ahead
+// of its head (zeta above zeta_max), nz behind its tail, -2 not finite.
+__global__ void k_slice_of(const double* __restrict__ zeta, int64_t n, double zmax, double dz, int nz, int32_t* out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const double t = floor((zmax - zeta[p]) / dz);
+  out[p] = !isfinite(t) ? -2 : (t < 0.0 ? -1 : (t >= (double)nz ? nz : (int)t));
+}
+
 // Exclusive scan of count[0..nz) into offset[0..nz], cursor zeroed.  One block.
 __global__ void k_scan(const int32_t* __restrict__ count, int32_t* offset, int32_t* cursor, int nz) {
   __shared__ int32_t part[1024];
@@ -87,22 +96,21 @@ __device__ __forceinline__ int stencil_t(double x, double x0, double dx, double 
 
 // Charge/current of the particles of slice i into dep (rho, Jx, Jy, Jz) and J_perp of
 // slice i+1 into bjn: rho = q w S / (dx dy dzeta), J = rho u / gamma (in the field type).
+// The explicit B_perp solver (bjc non-null) also keeps the beam's own J_perp of slice i in
+// bjc, taken before the beam push moves these particles: slice i+1 reads it as J_perp(i-1).
 template <int P, typename T>
 __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm,
-                               int slice, int nz, Geom gm, V4<T>* dep, V2<T>* bjn, V2<T>* bjp, float* ps) {
+                               int slice, int nz, Geom gm, V4<T>* dep, V2<T>* bjn, V2<T>* bjc, float* ps) {
   pdl_trigger();
   pdl_wait();
   const int a0 = off[slice], a1 = off[slice + 1];
   const int b0 = slice + 1 < nz ? off[slice + 1] : 0, b1 = slice + 1 < nz ? off[slice + 2] : 0;
-  // the explicit B_perp solver (bjp non-null) also takes the J_perp of slice i-1
-  const int c0 = bjp && slice > 0 ? off[slice - 1] : 0, c1 = bjp && slice > 0 ? off[slice] : 0;
-  const int na = a1 - a0, nb = b1 - b0, nc = c1 - c0;
+  const int na = a1 - a0, nb = b1 - b0;
   const double vol = gm.dx * gm.dy * gm.dzeta;
   const T rq = T(v.charge / vol);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < na + nb + nc; t += gridDim.x * blockDim.x) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < na + nb; t += gridDim.x * blockDim.x) {
     const bool cur = t < na;
-    const bool nxt = !cur && t < na + nb;
-    const int p = perm[cur ? a0 + t : (nxt ? b0 + (t - na) : c0 + (t - na - nb))];
+    const int p = perm[cur ? a0 + t : b0 + (t - na)];
     const T ux = T(v.ux[p]), uy = T(v.uy[p]), uz = T(v.uz[p]);
     const T ig = T(1) / sqrt(T(1) + ux * ux + uy * uy + uz * uz);
     // FP64: (q w) / (dx dy dzeta) as in the oracle; FP32: precomputed q / volume
@@ -131,8 +139,12 @@ __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, 
           atomicAdd(&q->c, s * cy);
           atomicAdd(&q->d, s * cz);
           if (ps) atomicAdd(ps + node, float(s) * omvz);
+          if (bjc) {
+            atomicAdd(&bjc[node].a, s * cx);
+            atomicAdd(&bjc[node].b, s * cy);
+          }
         } else {
-          V2<T>* q = (nxt ? bjn : bjp) + node;
+          V2<T>* q = bjn + node;
           atomicAdd(&q->a, s * cx);
           atomicAdd(&q->b, s * cy);
         }
@@ -305,6 +317,10 @@ constexpr unsigned kSliceBlocks = 152;  // grid-stride launches for per-slice be
 
 }  // namespace
 
+void launch_beam_slices(const hq_grid_s* g, const hq_beam_view& v, int32_t* out, cudaStream_t s) {
+  if (v.n > 0) k_slice_of<<<blocks_for(v.n), kThreads, 0, s>>>(v.zeta, v.n, g->d.zeta_max, g->geom.dzeta, g->nz, out);
+}
+
 void launch_beam_bin(hq_grid_s* g, int b, const hq_beam_view& v, cudaStream_t s) {
   BeamBins& bb = g->bins[b];
   cudaMemsetAsync(bb.count, 0, sizeof(int32_t) * (g->nz + 1), s);
@@ -329,7 +345,7 @@ void launch_beam_deposit(const hq_grid_s* g, int b, const hq_beam_view& v, int s
   HQ_SHAPE_SWITCH(g->d.shape_order,
                   (launch_pdl(k_beam_deposit<P, T>, dim3(kSliceBlocks), dim3(kThreads), (size_t)0, s, v, bb.offset, bb.perm,
                              slice, g->nz, g->geom, reinterpret_cast<V4<T>*>(dep), reinterpret_cast<V2<T>*>(bjn),
-                             reinterpret_cast<V2<T>*>(g->bjp), psrc_of(g, dep))));
+                             reinterpret_cast<V2<T>*>(bjp_at(g, slice)), psrc_of(g, dep))));
 }
 template <typename T>
 void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double dt, cudaStream_t s) {

@@ -306,11 +306,12 @@ void launch_explicit_src(const hq_grid_s* g, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_pcg_init(const hq_grid_s* g, const void* cur, const void* chi_cur, void* prev, void* chi_prev, cudaStream_t s) {
+void launch_pcg_init(const hq_grid_s* g, int slice, const void* cur, const void* chi_cur, void* prev, void* chi_prev,
+                     cudaStream_t s) {
   cudaMemsetAsync(g->pcg_s, 0, sizeof(double) * 4 * kMaxPcg * 2, s);
   PcgInit<T> f{reinterpret_cast<const V4<T>*>(cur), reinterpret_cast<const T*>(chi_cur),
                reinterpret_cast<const V4<T>*>(g->xs4), reinterpret_cast<const T*>(g->xs1),
-               reinterpret_cast<const V2<T>*>(g->bjp), reinterpret_cast<const V2<T>*>(g->bjn),
+               reinterpret_cast<const V2<T>*>(bjp_at(g, slice + 1)), reinterpret_cast<const V2<T>*>(g->bjn),
                reinterpret_cast<const V2<T>*>(g->bm), reinterpret_cast<V2<T>*>(g->pcg_r),
                reinterpret_cast<V4<T>*>(prev), reinterpret_cast<T*>(chi_prev), psrc_of(g, prev),
                reinterpret_cast<const T*>(g->rho_ion), g->geom};
@@ -318,7 +319,7 @@ void launch_pcg_init(const hq_grid_s* g, const void* cur, const void* chi_cur, v
 }
 
 template <typename T>
-void launch_pcg_iter(const hq_grid_s* g, int k, const void* chi_cur, cudaStream_t s) {
+void launch_pcg_iter(const hq_grid_s* g, int slice, int k, const void* chi_cur, cudaStream_t s) {
   const int64_t nn = g->nnode;
   const T* solved = reinterpret_cast<const T*>(g->solved);
   const T* chi = reinterpret_cast<const T*>(chi_cur);
@@ -326,7 +327,8 @@ void launch_pcg_iter(const hq_grid_s* g, int k, const void* chi_cur, cudaStream_
   V2<T>* p = reinterpret_cast<V2<T>*>(g->pcg_p);
   k_pcg_z<T><<<blocks_for(nn, 256), 256, 0, s>>>(solved, r, pcg_at(g, 0, k), nn, k == 0,
                                                  reinterpret_cast<V4<T>*>(g->xs4), reinterpret_cast<T*>(g->xs1),
-                                                 reinterpret_cast<V2<T>*>(g->bjp), reinterpret_cast<V2<T>*>(g->bjn));
+                                                 reinterpret_cast<V2<T>*>(bjp_at(g, slice + 1)),
+                                                 reinterpret_cast<V2<T>*>(g->bjn));
   k_pcg_p<T><<<blocks_for(nn, 256), 256, 0, s>>>(solved, p, pcg_at(g, 0, k), k > 0 ? pcg_at(g, 0, k - 1) : nullptr, nn);
   const dim3 g2((unsigned)((g->nx + 127) / 128), (unsigned)g->ny);
   k_pcg_q<T><<<g2, 128, 0, s>>>(p, chi, g->geom, pcg_at(g, 1, k));
@@ -336,9 +338,9 @@ void launch_pcg_iter(const hq_grid_s* g, int k, const void* chi_cur, cudaStream_
 
 template void launch_explicit_src<float>(const hq_grid_s*, cudaStream_t);
 template void launch_explicit_src<double>(const hq_grid_s*, cudaStream_t);
-template void launch_pcg_init<float>(const hq_grid_s*, const void*, const void*, void*, void*, cudaStream_t);
-template void launch_pcg_init<double>(const hq_grid_s*, const void*, const void*, void*, void*, cudaStream_t);
-template void launch_pcg_iter<float>(const hq_grid_s*, int, const void*, cudaStream_t);
-template void launch_pcg_iter<double>(const hq_grid_s*, int, const void*, cudaStream_t);
+template void launch_pcg_init<float>(const hq_grid_s*, int, const void*, const void*, void*, void*, cudaStream_t);
+template void launch_pcg_init<double>(const hq_grid_s*, int, const void*, const void*, void*, void*, cudaStream_t);
+template void launch_pcg_iter<float>(const hq_grid_s*, int, int, const void*, cudaStream_t);
+template void launch_pcg_iter<double>(const hq_grid_s*, int, int, const void*, cudaStream_t);
 
 }  // namespace hq

@@ -23,7 +23,8 @@ FIELDS = ("rho", "jx", "jy", "jz", "chi", "psi", "exmby", "eypbx", "ez", "bx", "
 EXPORTS = ("hq_grid_create", "hq_grid_destroy", "hq_advance_slice", "hq_beam_deposit", "hq_solve_fields",
            "hq_store_fields", "hq_push_beams", "hq_witness_accumulate", "hq_sweep_step", "hq_poisson_solve",
            "hq_plasma_state", "hq_profile_enable", "hq_profile_read", "hq_sync", "hq_last_error",
-           "hq_poisson_solve_static", "hq_sweep_forward_ckpt", "hq_sweep_adjoint", "hq_beam_moments")
+           "hq_poisson_solve_static", "hq_sweep_forward_ckpt", "hq_sweep_adjoint", "hq_beam_moments",
+           "hq_beam_slices")
 KERNEL_CLASSES = ("final", "trial", "dst", "field", "beam", "other")
 
 
@@ -86,6 +87,7 @@ def load() -> C.CDLL:
             "hq_sweep_adjoint": (P, C.POINTER(BeamView), I32, I32, C.POINTER(D), C.POINTER(FieldOut), C.POINTER(P), P, P,
                                  P),
             "hq_beam_moments": (P, C.POINTER(BeamView), P),
+            "hq_beam_slices": (P, C.POINTER(BeamView), P),
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -258,6 +260,13 @@ class Grid:
                                        C.c_void_p(dn0.data_ptr()),
                                        C.c_void_p(dprof.data_ptr()) if dprof is not None else None), self.h)
         return {"beam_w": wb, "plasma_w": wp, "n0_scale": dn0, "profile": dprof}
+
+    def beam_slices(self, beam: Beam) -> torch.Tensor:
+        """Slice of every particle (int32 CUDA tensor): 0..nzeta-1 inside, -1 ahead, nzeta behind, -2 not finite."""
+        out = torch.empty(beam.n, dtype=torch.int32, device="cuda")
+        v = beam.view()
+        _check(load().hq_beam_slices(self.h, C.byref(v), C.c_void_p(out.data_ptr()) if beam.n else None), self.h)
+        return out
 
     def beam_moments(self, beam: Beam) -> torch.Tensor:
         """Weighted raw moments of a beam (device float64[11], see hq_beam_moments)."""

@@ -180,8 +180,11 @@ def test_sweep_fp64_ragged(hq, order, ppc, profile):
     assert removed == ref.removed
 
 
-def test_beam_push_and_witness_fp64(hq):
-    g = I.scaled_grid(I.grid_params("adjoint256"), 48, 48, 48)
+@pytest.mark.parametrize("solver", ["pc", "explicit"])
+def test_beam_push_and_witness_fp64(hq, solver):
+    """The beam push with both B_perp solvers (the explicit one takes the beam J_perp of slice i-1
+    from before that slice's push)."""
+    g = I.scaled_grid(I.grid_params("adjoint256"), 48, 48, 48, bperp_solver=solver)
     beams = I.workload_beams("adjoint256", grid=g)
     sp = O.GridSpec(**g)
     ref = O.sweep(sp, [O.as_beam(b) for b in beams], dt=5.0, witness=(1,), record=("ez",))
