@@ -287,6 +287,32 @@ def cubic_leg(hq, I, stream, flush, steps=1):
             "witness_eps_x_initial": hq.emittance(m0)[0], "witness_eps_x_final": hq.emittance(m1)[0], "device_bytes_used": int(used)}
 
 
+def explicit_leg(hq, I, stream, flush, iters=6):
+    """The headline workload with the explicit B_perp solver (Helmholtz-like equation in chi,
+    `iters` preconditioned conjugate-gradient iterations) instead of the predictor-corrector."""
+    import torch
+    g = dict(I.grid_params(WORKLOAD), bperp_solver="explicit", n_pc_iter=iters)
+    grid = hq.Grid(g, precision="fp32", stream=stream)
+    hb = [hq.Beam(b) for b in I.workload_beams(WORKLOAD)]
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    grid.sweep(hb, witness=0, witness_sums=sums)
+    grid.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(7)
+    sums.zero_()
+    a.record(stream)
+    grid.sweep(hb, witness=0, witness_sums=sums)
+    b.record(stream)
+    torch.cuda.synchronize()
+    removed = grid.sync()
+    grid.close()
+    ms = a.elapsed_time(b)
+    p = g["nx"] * g["ny"] * g["ppc_x"] * g["ppc_y"]
+    return {"workload": f"{WORKLOAD} with the explicit B_perp solver, {iters} PCG iterations per slice",
+            "ms_per_step": ms, "value": p * g["nzeta"] / (ms / 1e3), "unit": UNIT, "removed_particles": removed,
+            "witness_sums": [float(v) for v in sums.cpu()]}
+
+
 def precision_leg(hq, I, stream, steps=100, dt=20.0):
     """Witness emittance over many beam time steps, FP32/bf16x3 against the FP64 GPU path (the
     paper's single- vs double-precision study, Sec. 6): a driver and a witness whose centroid
@@ -565,7 +591,7 @@ def run_hq(args):
     if not args.no_adjoint and args.precision == "fp32":
         adjoint = adjoint_leg(hq, I, stream, flush)
 
-    cubic = adjoint512 = dstcmp = precision = None
+    cubic = adjoint512 = dstcmp = precision = explicit = None
     if not args.no_extra and args.precision == "fp32" and rank == 0:
         grid.close()
         grid = None
@@ -577,6 +603,7 @@ def run_hq(args):
             torch.cuda.empty_cache()
         dstcmp = dst_comparator(hq, I, stream)
         precision = precision_leg(hq, I, stream, steps=args.precision_steps)
+        explicit = explicit_leg(hq, I, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -600,7 +627,8 @@ def run_hq(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
             "gpu_launches": launches_per_sweep * args.steps,
             "fp64": fp64, "adjoint": adjoint, "cubic1024": cubic, "adjoint512": adjoint512,
-            "dst_comparator": dstcmp, "precision_study": precision, "cpu_baseline": cpu, "removed_particles": removed,
+            "dst_comparator": dstcmp, "precision_study": precision, "explicit_solver": explicit, "cpu_baseline": cpu,
+            "removed_particles": removed,
         }
         print(json.dumps(line), flush=True)
     if grid is not None:
