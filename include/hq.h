@@ -92,6 +92,10 @@ typedef struct {
   double psi_guard;                 /* particle removed when 1 + Psi < psi_guard      */
   int32_t precision;                /* hq_precision                                   */
   int32_t bperp_solver;             /* hq_bperp_solver (0: predictor-corrector)       */
+  int32_t resort_every;             /* m > 0: after the final push to slice i with i % m
+                                       == 0 the plasma slice is re-sorted by cell (stable
+                                       counting sort, Sec. 3.1); 0: never.  Refused by
+                                       hq_sweep_forward_ckpt (HQ_ERR_UNSUPPORTED)          */
 } hq_grid_desc;
 
 /* B_perp field solver (Sec. 3.2: "predictor-corrector field solver" and "explicit field
@@ -124,12 +128,16 @@ typedef struct {
 
 /* Read-only DEVICE views of the plasma slice (library-owned memory, valid until
  * hq_grid_destroy).  x, y, psi are double; ux, uy, w are of the field type;
- * alive is uint8 (0 once a particle is removed). */
+ * alive is uint8 (0 once a particle is removed).  origin (int32) gives each entry's
+ * index in the initial placement (cell-row-major, ppc_x x ppc_y sub-cells per cell) when
+ * the grid re-sorts its plasma (resort_every > 0); NULL otherwise, when entry p is
+ * particle p of that placement. */
 typedef struct {
   int64_t n;
   const double *x, *y, *psi;
   const void *ux, *uy, *w;
   const uint8_t* alive;
+  const int32_t* origin;
 } hq_plasma_view;
 
 typedef struct hq_grid_s* hq_grid_t;

@@ -55,6 +55,8 @@ void free_all(hq_grid_s* g) {
       F(p.ux); F(p.uy); F(p.w); F(p.hist); F(p.cell); F(p.fx); F(p.fy); F(p.opp); F(p.hsum);
     }
   }
+  F(g->porigin); F(g->sort_key); F(g->sort_perm); F(g->sort_count); F(g->sort_offset); F(g->sort_tsum);
+  F(g->sort_scratch);
   for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); F(g->psrc[i]); }
   F(g->rho_ion); F(g->tj); F(g->bjn); F(g->bjp); F(g->xs4); F(g->xs1); F(g->pcg_r); F(g->pcg_p); F(g->pcg_s);
   F(g->scale_h); F(g->gf); F(g->bm); F(g->psi); F(g->bprev1); F(g->solved);
@@ -332,6 +334,10 @@ void advance_impl(hq_grid_s* g, int slice) {
     if (g->bjp) launch_zero<T>(g->bjp, 4 * g->nnode, s);
   } else {
     final_pass<T>(g, slice - 1, slice & 1);
+    if (g->d.resort_every > 0 && slice % g->d.resort_every == 0) {
+      Prof p(g, HQ_K_OTHER, 8);
+      launch_resort(g, s);
+    }
   }
 }
 
@@ -785,6 +791,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     return fail(nullptr, HQ_ERR_ARG, "the explicit B_perp solver needs 1..64 iterations (n_pc_iter)");
   if (d.bperp_solver == HQ_BPERP_EXPLICIT && !(d.n0_scale > 0.0))
     return fail(nullptr, HQ_ERR_ARG, "the explicit B_perp solver needs n0_scale > 0 (its preconditioner shift)");
+  if (d.resort_every < 0) return fail(nullptr, HQ_ERR_ARG, "resort_every must be >= 0");
   if (d.radial_profile && (d.n_profile < 2 || !(d.profile_rmax > 0.0)))
     return fail(nullptr, HQ_ERR_ARG, "radial profile needs n_profile >= 2 and profile_rmax > 0");
   const int64_t np = (int64_t)d.nx * d.ny * d.ppc_x * d.ppc_y;
@@ -865,6 +872,16 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     HQ_ALLOC(g->p32.hist, 4 * np * kRing * 5);
     HQ_ALLOC(g->p32.cell, 4 * np); HQ_ALLOC(g->p32.fx, 4 * np); HQ_ALLOC(g->p32.fy, 4 * np); HQ_ALLOC(g->p32.opp, 4 * np);
     HQ_ALLOC(g->p32.hsum, 4 * np * 5);
+  }
+  if (d.resort_every > 0) {
+    HQ_ALLOC(g->porigin, 4 * np);
+    g->p64.origin = g->p32.origin = g->porigin;
+    HQ_ALLOC(g->sort_key, 4 * np);
+    HQ_ALLOC(g->sort_perm, 4 * np);
+    HQ_ALLOC(g->sort_count, 4 * (nn + 1));
+    HQ_ALLOC(g->sort_offset, 4 * (nn + 1));
+    HQ_ALLOC(g->sort_tsum, 4 * (size_t)resort_tiles(g));
+    HQ_ALLOC(g->sort_scratch, (size_t)resort_scratch_bytes(g));
   }
   // fields
   for (int i = 0; i < 2; ++i) { HQ_ALLOC(g->dep[i], 4 * ts * nn); HQ_ALLOC(g->chi[i], ts * nn); }
@@ -1225,6 +1242,7 @@ hq_status hq_sweep_forward_ckpt(hq_grid_t g, hq_beam_view* beams, int32_t nbeams
     return fail(g, HQ_ERR_ARG, "witness_beam must index a beam and witness_sums must be given");
   if (ckpt_every < 1) return fail(g, HQ_ERR_ARG, "ckpt_every must be >= 1");
   if (g->explicit_b) return fail(g, HQ_ERR_UNSUPPORTED, "the adjoint supports the predictor-corrector B_perp solver only");
+  if (g->d.resort_every > 0) return fail(g, HQ_ERR_UNSUPPORTED, "the adjoint needs the plasma in its initial order (resort_every = 0)");
   const int k = std::min<int>(ckpt_every, g->nz);
   if ((st = adj_alloc(g, k)) != HQ_OK) return st;
   AdjStore* a = adj_of(g);
@@ -1285,6 +1303,7 @@ hq_status hq_plasma_state(hq_grid_t g, hq_plasma_view* out) {
   out->y = g->p64.y;
   out->psi = g->p64.psi;
   out->alive = g->p64.alive;
+  out->origin = g->porigin;
   if (g->fp64) { out->ux = g->p64.ux; out->uy = g->p64.uy; out->w = g->p64.w; }
   else { out->ux = g->p32.ux; out->uy = g->p32.uy; out->w = g->p32.w; }
   return HQ_OK;

@@ -76,6 +76,9 @@ template <typename T> struct Plasma {
   // f_{i-k}, [5][n]: the same for all predictor-corrector trial passes of the slice, so they
   // read 5 values instead of the 20 of the ring (written by the final pass).
   float* hsum;
+  // With the re-sort (resort_every > 0): each particle's index in the initial placement (its
+  // ion's position is recomputed from it); null otherwise (the array index is that index).
+  int32_t* origin;
 };
 
 // Per-beam slice binning (counting sort by slice, Sec. 3.1).
@@ -134,6 +137,12 @@ struct hq_grid_s {
   void* plasma;        // hq::Plasma<T>* host struct (typed by fp64)
   hq::Plasma<double> p64;
   hq::Plasma<float> p32;
+  // plasma re-sort by cell every d.resort_every slices (null when off): initial index per
+  // particle (shared by p64 and p32), sort keys, counts/cursor and offsets per cell (+1 for
+  // non-finite positions), scan tile totals, the permutation, and the scratch copy
+  int32_t* porigin;
+  int32_t *sort_key, *sort_count, *sort_offset, *sort_tsum, *sort_perm;
+  void* sort_scratch;
 
   // fields (void* typed by fp64)
   void* dep[2];        // V4 per node: rho, jx, jy, jz   (ping-pong by slice parity)
@@ -260,6 +269,10 @@ void dst_tc_free(hq_grid_s* g);
 // beams
 void launch_beam_bin(hq_grid_s* g, int b, const hq_beam_view& v, cudaStream_t s);
 void launch_beam_slices(const hq_grid_s* g, const hq_beam_view& v, int32_t* out, cudaStream_t s);
+// plasma re-sort by cell (k_sort.cu); the scratch size and scan tile count for allocation
+void launch_resort(hq_grid_s* g, cudaStream_t s);
+int64_t resort_scratch_bytes(const hq_grid_s* g);
+int64_t resort_tiles(const hq_grid_s* g);
 template <typename T> void launch_beam_deposit(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, void* dep, void* bjn, cudaStream_t s);
 template <typename T> void launch_beam_push(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double dt, cudaStream_t s);
 template <typename T> void launch_witness(const hq_grid_s* g, int b, const hq_beam_view& v, int slice, double* sums, cudaStream_t s);

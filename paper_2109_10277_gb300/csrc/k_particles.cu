@@ -209,6 +209,7 @@ __global__ void k_plasma_init(Plasma<T> pl, Geom gm, int ppx, int ppy, const dou
   pl.uy[p] = T(0);
   pl.w[p] = T(n0s * dens * (gm.dx * gm.dy / (double)ppc));
   pl.alive[p] = 1;
+  if (pl.origin) pl.origin[p] = (int32_t)p;
   for (int k = 0; k < kRing * 5; ++k) pl.hist[(int64_t)k * pl.n + p] = T(0);
   if (pl.hsum)
     for (int c = 0; c < 5; ++c) pl.hsum[(int64_t)c * pl.n + p] = 0.0f;
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pa
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pl.n) return;
   Start s0{};
-  if (ps) s0 = start_coord(p, gm, pc);
+  if (ps) s0 = start_coord(pl.origin ? (int64_t)pl.origin[p] : p, gm, pc);
   if (!pl.alive[p]) {
     if constexpr (sizeof(T) == 4)
       if (ps) deposit_ion_src<P>(ps, gm, s0, charge_density<T>(pl.w[p], gm));

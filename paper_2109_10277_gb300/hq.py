@@ -35,7 +35,8 @@ class GridDesc(C.Structure):
                 ("shape_order", C.c_int32), ("ppc_x", C.c_int32), ("ppc_y", C.c_int32),
                 ("radial_profile", C.POINTER(C.c_double)), ("n_profile", C.c_int32), ("profile_rmax", C.c_double),
                 ("n0_scale", C.c_double), ("n_pc_iter", C.c_int32), ("pc_mix", C.c_double),
-                ("psi_guard", C.c_double), ("precision", C.c_int32), ("bperp_solver", C.c_int32)]
+                ("psi_guard", C.c_double), ("precision", C.c_int32), ("bperp_solver", C.c_int32),
+                ("resort_every", C.c_int32)]
 
 
 class BeamView(C.Structure):
@@ -53,7 +54,8 @@ class Profile(C.Structure):
 
 class PlasmaView(C.Structure):
     _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p), ("psi", C.c_void_p),
-                ("ux", C.c_void_p), ("uy", C.c_void_p), ("w", C.c_void_p), ("alive", C.c_void_p)]
+                ("ux", C.c_void_p), ("uy", C.c_void_p), ("w", C.c_void_p), ("alive", C.c_void_p),
+                ("origin", C.c_void_p)]
 
 
 _lib = None
@@ -167,7 +169,7 @@ class Grid:
             float(params.get("n0_scale", 1.0)), int(params.get("n_pc_iter", 5)), float(params.get("pc_mix", 0.05)),
             float(params.get("psi_guard", 0.02)),
             HQ_PREC_FP64 if precision == "fp64" else HQ_PREC_FP32_BF16X3,
-            {"pc": 0, "explicit": 1}[params.get("bperp_solver", "pc")])
+            {"pc": 0, "explicit": 1}[params.get("bperp_solver", "pc")], int(params.get("resort_every", 0)))
         self.params = dict(params)
         self.nx, self.ny, self.nzeta = d.nx, d.ny, d.nzeta
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -282,8 +284,10 @@ class Grid:
                                        src.shape[0]), self.h)
         return dst
 
-    def plasma_state(self) -> dict:
-        """Copies of the plasma slice arrays (synchronizes the grid's stream)."""
+    def plasma_state(self, initial_order: bool = True) -> dict:
+        """Copies of the plasma slice arrays (synchronizes the grid's stream).  A grid that
+        re-sorts its plasma also returns "origin" (each entry's index in the initial placement)
+        and, with initial_order, the arrays put back in that placement's order."""
         v = PlasmaView()
         _check(load().hq_plasma_state(self.h, C.byref(v)), self.h)
         self.sync()
@@ -292,6 +296,14 @@ class Grid:
         out = {}
         for k, ts in (("x", "<f8"), ("y", "<f8"), ("psi", "<f8"), ("ux", ft), ("uy", ft), ("w", ft), ("alive", "|u1")):
             out[k] = torch.as_tensor(_CudaArray(getattr(v, k), n, ts), device="cuda").clone()
+        if v.origin:
+            org = torch.as_tensor(_CudaArray(v.origin, n, "<i4"), device="cuda").clone().to(torch.int64)
+            if initial_order:
+                for k in list(out):
+                    t = torch.empty_like(out[k])
+                    t[org] = out[k]
+                    out[k] = t
+            out["origin"] = org
         return out
 
     def profile(self, on: bool) -> None:
