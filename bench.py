@@ -64,6 +64,9 @@ def parse():
                     help="beam time steps of the FP32-vs-FP64 witness emittance leg")
     ap.add_argument("--case", choices=("sweep", "poisson"), default="sweep",
                     help="poisson: only repeated Dirichlet solves on the workload grid (for ncu captures)")
+    ap.add_argument("--nzeta", type=int, default=0,
+                    help="override the workload's slice count (a short sweep of the same kernels, for ncu "
+                         "captures; the line then names the reduced workload)")
     ap.add_argument("--rhs", type=int, default=3, choices=(1, 2, 3),
                     help="right-hand sides per solve of the poisson case (3: the psi/Ez/Bz solve, 2: B_perp)")
     return ap.parse_args()
@@ -192,7 +195,9 @@ def run_reference(args):
 # solves as the sweep mixes them (5 two-RHS 32-wide-tile launches to 1 three-RHS one per
 # slice: 4.246 MB and 5.325 MB), the trial and final passes of one slice; the capture
 # commands are recorded with their summaries under profiles/
-NCU_TRAFFIC = {"dst": (5 * 4.246016e6 + 5.324544e6) / 6, "trial": 23.322112e6, "final": 48.652032e6}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of each kernel
+# (profiles/: k_dst_solve_rs R = 2 and R = 3 weighted 5:1 as in a slice, trial and final pass)
+NCU_TRAFFIC = {"dst": (5 * 16.329984e6 + 6.899712e6) / 6, "trial": 21.229568e6, "final": 46.429952e6 + 91.392e3}
 
 
 def dst_flops_per_sweep(g: dict) -> float:
@@ -483,6 +488,10 @@ def run_hq(args):
 
     g = I.grid_params(WORKLOAD)
     beams_np = I.workload_beams(WORKLOAD)
+    if args.nzeta > 0:
+        g["nzeta"] = args.nzeta   # same slice thickness window from zeta_max: the head of the box
+        g["zeta_min"] = g["zeta_max"] - args.nzeta * (I.grid_params(WORKLOAD)["zeta_max"] -
+                                                      I.grid_params(WORKLOAD)["zeta_min"]) / I.grid_params(WORKLOAD)["nzeta"]
     p = g["nx"] * g["ny"] * g["ppc_x"] * g["ppc_y"]
     nz = g["nzeta"]
     stream = torch.cuda.current_stream()
@@ -613,7 +622,8 @@ def run_hq(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}",
+            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}" + (
+                           f" (reduced: the first {nz} slices only)" if args.nzeta > 0 else ""),
                        "precision": "FP32 push/gather/deposit, FP64 x/y/Psi accumulators, bf16x3 tensor-core DST-I"
                        if args.precision == "fp32" else "FP64 everywhere, FP64 FFT DST-I",
                        "particles_per_slice": p, "slices": nz, "parallelism": f"replicas x{world}",
