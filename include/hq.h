@@ -96,6 +96,15 @@ typedef struct {
                                        == 0 the plasma slice is re-sorted by cell (stable
                                        counting sort, Sec. 3.1); 0: never.  Refused by
                                        hq_sweep_forward_ckpt (HQ_ERR_UNSUPPORTED)          */
+  int32_t deterministic;            /* 1 (FP64 precision, predictor-corrector solver only):
+                                       every plasma and beam deposit and the witness sums
+                                       accumulate in 64-bit fixed point (resolution 2^-72,
+                                       contributions and sums below 2^31 in magnitude, else
+                                       HQ_ERR_NUMERIC) with integer atomics, so a sweep's
+                                       results do not depend on the order of the atomic
+                                       additions: bitwise reproducible.  Refused by
+                                       hq_sweep_forward_ckpt (HQ_ERR_UNSUPPORTED); 0: FP64
+                                       atomics (last-bit run-to-run differences)          */
 } hq_grid_desc;
 
 /* B_perp field solver (Sec. 3.2: "predictor-corrector field solver" and "explicit field

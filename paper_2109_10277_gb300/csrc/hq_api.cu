@@ -55,6 +55,12 @@ void free_all(hq_grid_s* g) {
       F(p.ux); F(p.uy); F(p.w); F(p.hist); F(p.cell); F(p.fx); F(p.fy); F(p.opp); F(p.hsum);
     }
   }
+  if (g->det_arena) {
+    // the deposit records are carved from the arena
+    g->dep[0] = g->dep[1] = g->chi[0] = g->chi[1] = g->rho_ion = g->tj = g->bjn = nullptr;
+    F(g->det_arena);
+    F(g->det_mirror);
+  }
   F(g->porigin); F(g->sort_key); F(g->sort_perm); F(g->sort_count); F(g->sort_offset); F(g->sort_tsum);
   F(g->sort_scratch);
   for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); F(g->psrc[i]); }
@@ -285,6 +291,7 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
     const int last = m == npc - 1;
     tape_b_iterate(g, m);
     { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, s); }
+    if (g->det) launch_fx_decode(g, g->tj, 2 * g->nnode, nullptr, s);
     if (fused_src) {
       Prof p(g, HQ_K_DST, 1);   // sources, solve and the mixing in one launch
       dst_solve_tc_bmix_src(g, cur, prev, chi_prev, last, s);
@@ -316,6 +323,10 @@ template <typename T>
 void final_pass(hq_grid_s* g, int slice_from, int parity) {
   Prof p(g, HQ_K_FINAL, 1);
   launch_final_pass<T>(g, slice_from, g->dep[parity], g->chi[parity], g->stream);
+  if (g->det) {
+    launch_fx_decode(g, g->dep[parity], 4 * g->nnode, nullptr, g->stream);
+    launch_fx_decode(g, g->chi[parity], g->nnode, nullptr, g->stream);
+  }
 }
 
 template <typename T>
@@ -326,6 +337,10 @@ void advance_impl(hq_grid_s* g, int slice) {
     launch_reset_dep<T>(g, g->dep[0], g->chi[0], s);
     launch_plasma_init<T>(g, s);
     launch_deposit_initial<T>(g, g->dep[0], g->chi[0], 0, s);
+    if (g->det) {
+      launch_fx_decode(g, g->dep[0], 4 * g->nnode, nullptr, s);
+      launch_fx_decode(g, g->chi[0], g->nnode, nullptr, s);
+    }
     launch_zero<T>(g->dep[1], 4 * g->nnode, s);   // J(-1) = 0 ahead of the box
     if (!g->fp64) launch_zero<float>(g->psrc[1], g->nnode, s);
     launch_zero<T>(g->bprev1, 2 * g->nnode, s);
@@ -499,6 +514,10 @@ hq_status beam_deposit_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int
     if (beams[b].n == 0) continue;
     Prof p(g, HQ_K_BEAM, 1);
     launch_beam_deposit<T>(g, slot[b], beams[b], slice, g->dep[slice & 1], g->bjn, s);
+  }
+  if (g->det) {
+    launch_fx_decode(g, g->dep[slice & 1], 4 * g->nnode, nullptr, s);
+    launch_fx_decode(g, g->bjn, 2 * g->nnode, nullptr, s);
   }
   return HQ_OK;
 }
@@ -689,7 +708,7 @@ hq_status sweep_body(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, double dt
   // records), so from slice 1 on they run on a second stream beside it, forked and joined with
   // events (a graph capture records the fork as parallel branches).  Slice 0 stays in order
   // (the beams are binned and the records reset there).
-  const bool fork = dt == 0.0 && !g->prof_on && aux_ready(g);
+  const bool fork = dt == 0.0 && !g->prof_on && !g->det && aux_ready(g);
   const bool wit = witness_beam >= 0;
   for (int i = 0; i < g->nz; ++i) {
     if (fork && i > 0) {
@@ -792,6 +811,11 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   if (d.bperp_solver == HQ_BPERP_EXPLICIT && !(d.n0_scale > 0.0))
     return fail(nullptr, HQ_ERR_ARG, "the explicit B_perp solver needs n0_scale > 0 (its preconditioner shift)");
   if (d.resort_every < 0) return fail(nullptr, HQ_ERR_ARG, "resort_every must be >= 0");
+  if (d.deterministic != 0 && d.deterministic != 1) return fail(nullptr, HQ_ERR_ARG, "deterministic must be 0 or 1");
+  if (d.deterministic && d.precision != HQ_PREC_FP64)
+    return fail(nullptr, HQ_ERR_UNSUPPORTED, "deterministic accumulation is an FP64 mode");
+  if (d.deterministic && d.bperp_solver != HQ_BPERP_PC)
+    return fail(nullptr, HQ_ERR_UNSUPPORTED, "deterministic accumulation covers the predictor-corrector solver only");
   if (d.radial_profile && (d.n_profile < 2 || !(d.profile_rmax > 0.0)))
     return fail(nullptr, HQ_ERR_ARG, "radial profile needs n_profile >= 2 and profile_rmax > 0");
   const int64_t np = (int64_t)d.nx * d.ny * d.ppc_x * d.ppc_y;
@@ -884,15 +908,37 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     HQ_ALLOC(g->sort_scratch, (size_t)resort_scratch_bytes(g));
   }
   // fields
-  for (int i = 0; i < 2; ++i) { HQ_ALLOC(g->dep[i], 4 * ts * nn); HQ_ALLOC(g->chi[i], ts * nn); }
+  g->det = d.deterministic;
+  if (g->det) {
+    // one arena for the deposit records (and the witness accumulator), one for their
+    // fixed-point mirrors at twice the stride: mirror(e) = 2 e + geom.det
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t sz[8] = {up(32 * nn), up(32 * nn), up(8 * nn), up(8 * nn), up(8 * nn), up(16 * nn), up(16 * nn), 256};
+    size_t tot = 0;
+    for (size_t b : sz) tot += b;
+    HQ_ALLOC(g->det_arena, tot);
+    HQ_ALLOC(g->det_mirror, 2 * tot);
+    cudaMemset(g->det_arena, 0, tot);
+    cudaMemset(g->det_mirror, 0, 2 * tot);
+    char* a = static_cast<char*>(g->det_arena);
+    void** dst[8] = {&g->dep[0], &g->dep[1], &g->chi[0], &g->chi[1], &g->rho_ion, &g->tj, &g->bjn, nullptr};
+    for (int k = 0; k < 8; ++k) {
+      if (dst[k]) *dst[k] = a;
+      else g->det_wsum = reinterpret_cast<double*>(a);
+      a += sz[k];
+    }
+    g->geom.det = (int64_t)reinterpret_cast<uintptr_t>(g->det_mirror) - 2 * (int64_t)reinterpret_cast<uintptr_t>(g->det_arena);
+  } else {
+    for (int i = 0; i < 2; ++i) { HQ_ALLOC(g->dep[i], 4 * ts * nn); HQ_ALLOC(g->chi[i], ts * nn); }
+    HQ_ALLOC(g->rho_ion, ts * nn);
+    HQ_ALLOC(g->tj, 2 * ts * nn);
+    HQ_ALLOC(g->bjn, 2 * ts * nn);
+  }
   if (!g->fp64)
     for (int i = 0; i < 2; ++i) {
       HQ_ALLOC(g->psrc[i], 4 * nn);
       cudaMemset(g->psrc[i], 0, 4 * nn);
     }
-  HQ_ALLOC(g->rho_ion, ts * nn);
-  HQ_ALLOC(g->tj, 2 * ts * nn);
-  HQ_ALLOC(g->bjn, 2 * ts * nn);
   HQ_ALLOC(g->gf, kGF * ts * nn);
   HQ_ALLOC(g->bm, 2 * ts * nn);
   if (g->explicit_b) {
@@ -911,6 +957,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   HQ_ALLOC(g->bprev1, 2 * ts * nn);
   HQ_ALLOC(g->solved, kMaxRhs * ts * nn);
   HQ_ALLOC(g->d_status, sizeof(int));
+  if (g->det) g->geom.dstatus = g->d_status;   // fixed-point range overflows are reported here
   HQ_ALLOC(g->d_removed, sizeof(unsigned long long));
   for (int b = 0; b < kMaxBeams; ++b) {
     HQ_ALLOC(g->bins[b].count, sizeof(int32_t) * (g->nz + 1));
@@ -1038,6 +1085,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   if (g->fp64) {
     launch_plasma_init<double>(g, g->stream);
     launch_deposit_initial<double>(g, nullptr, nullptr, 1, g->stream);
+    if (g->det) launch_fx_decode(g, g->rho_ion, nn, nullptr, g->stream);
   } else {
     launch_plasma_init<float>(g, g->stream);
     launch_deposit_initial<float>(g, nullptr, nullptr, 1, g->stream);
@@ -1134,7 +1182,10 @@ hq_status hq_witness_accumulate(hq_grid_t g, const hq_beam_view* beam, int32_t s
   if (k < 0) return fail(g, HQ_ERR_STATE, "beam was not given to hq_beam_deposit in this sweep");
   if (beam->n == 0) return HQ_OK;
   Prof p(g, HQ_K_BEAM, 1);
-  if (g->fp64) launch_witness<double>(g, k, *beam, slice, sums, g->stream);
+  if (g->fp64) {
+    launch_witness<double>(g, k, *beam, slice, g->det ? g->det_wsum : sums, g->stream);
+    if (g->det) launch_fx_decode(g, g->det_wsum, 3, sums, g->stream);
+  }
   else launch_witness<float>(g, k, *beam, slice, sums, g->stream);
   return check_launch(g);
 }
@@ -1243,6 +1294,7 @@ hq_status hq_sweep_forward_ckpt(hq_grid_t g, hq_beam_view* beams, int32_t nbeams
   if (ckpt_every < 1) return fail(g, HQ_ERR_ARG, "ckpt_every must be >= 1");
   if (g->explicit_b) return fail(g, HQ_ERR_UNSUPPORTED, "the adjoint supports the predictor-corrector B_perp solver only");
   if (g->d.resort_every > 0) return fail(g, HQ_ERR_UNSUPPORTED, "the adjoint needs the plasma in its initial order (resort_every = 0)");
+  if (g->det) return fail(g, HQ_ERR_UNSUPPORTED, "deterministic accumulation is a forward-sweep mode");
   const int k = std::min<int>(ckpt_every, g->nz);
   if ((st = adj_alloc(g, k)) != HQ_OK) return st;
   AdjStore* a = adj_of(g);
@@ -1326,7 +1378,9 @@ hq_status hq_sync(hq_grid_t g, int64_t* removed) {
       if (g->d_gbar) HQ_CUDA(g, cudaMemset(g->d_gbar, 0, sizeof(unsigned long long)));  // an aborted solve left it
       return fail(g, HQ_ERR_TIMEOUT, "a bounded device wait ran out (tensor-core DST)");
     }
-    if (status & DEV_NONFINITE) return fail(g, HQ_ERR_NUMERIC, "a non-finite value reached the field solve");
+    if (status & DEV_NONFINITE)
+      return fail(g, HQ_ERR_NUMERIC, "a non-finite value reached the field solve, or a deterministic-mode "
+                                     "contribution left the fixed-point range");
   }
   return HQ_OK;
 }

@@ -41,6 +41,10 @@ struct Geom {
   // FP32 copies for the FP32 kernels (no per-thread double-to-float conversion)
   float f_dz, f_dz_inv_dx, f_dz_inv_dy, f_inv_area, f_guard;
   float f_inv_dx, f_inv_dy, f_inv2dx, f_inv2dy, f_inv2dz;
+  // deterministic FP64 accumulation (0: off): byte offset from twice a deposit record's
+  // address to its fixed-point mirror (see fx_add), and the status word for overflows
+  int64_t det;
+  int* dstatus;
 };
 
 // A geometry constant in the kernel's arithmetic type: FP32 kernels take the host-rounded
@@ -143,6 +147,12 @@ struct hq_grid_s {
   int32_t* porigin;
   int32_t *sort_key, *sort_count, *sort_offset, *sort_tsum, *sort_perm;
   void* sort_scratch;
+  // deterministic FP64 mode (d.deterministic): the deposit records dep[2], chi[2], tj, bjn,
+  // rho_ion and the witness accumulator det_wsum live in one arena; the fixed-point mirrors
+  // in a second one of twice its size (geom.det is their offset)
+  int det;
+  void *det_arena, *det_mirror;
+  double* det_wsum;
 
   // fields (void* typed by fp64)
   void* dep[2];        // V4 per node: rho, jx, jy, jz   (ping-pong by slice parity)
@@ -269,6 +279,9 @@ void dst_tc_free(hq_grid_s* g);
 // beams
 void launch_beam_bin(hq_grid_s* g, int b, const hq_beam_view& v, cudaStream_t s);
 void launch_beam_slices(const hq_grid_s* g, const hq_beam_view& v, int32_t* out, cudaStream_t s);
+// deterministic FP64 mode: adds the fixed-point mirrors of n elements of rec (a deposit record
+// of the arena) to rec, or to dst when given, and clears the mirrors (k_fields.cu)
+void launch_fx_decode(const hq_grid_s* g, void* rec, int64_t n, double* dst, cudaStream_t s);
 // plasma re-sort by cell (k_sort.cu); the scratch size and scan tile count for allocation
 void launch_resort(hq_grid_s* g, cudaStream_t s);
 int64_t resort_scratch_bytes(const hq_grid_s* g);
@@ -358,6 +371,34 @@ __device__ __forceinline__ void split_coord(double x, double x0, double dx, int&
 }
 
 __device__ __forceinline__ bool in_interior(int j, int n) { return j >= 1 && j <= n - 1; }
+
+// Deterministic FP64 accumulation (hq_grid_desc.deterministic).  A contribution v to an element
+// of a deposit record is split into the fixed-point pair H = floor(v 2^32), L = round((v 2^32 - H)
+// 2^40) and added with 64-bit integer atomics to the element's mirror, two words at byte address
+// 2 * (element address) + det (the mirrors of all deposit records are laid out like the records,
+// at twice the stride).  Integer sums do not depend on the order of the additions; k_fx_decode
+// later adds H 2^-32 + L 2^-72 to the element and clears the mirror.  Resolution 2^-72; |v| and
+// every partial sum must stay below 2^31 (else DEV_NONFINITE); up to 2^23 contributions per
+// element between decodes.
+__device__ __forceinline__ void fx_add(double* p, double v, int64_t det, int* status) {
+  const double s = v * 4294967296.0;
+  if (!(fabs(s) < 9.2e18)) {
+    if (status) atomicOr(status, DEV_NONFINITE);
+    return;
+  }
+  const double h = floor(s);
+  const long long hi = (long long)h;
+  const long long lo = llrint((s - h) * 1099511627776.0);
+  unsigned long long* m = reinterpret_cast<unsigned long long*>(2ull * reinterpret_cast<uintptr_t>(p) + (uint64_t)det);
+  atomicAdd(m, (unsigned long long)hi);
+  if (lo) atomicAdd(m + 1, (unsigned long long)lo);
+}
+// Deposit add: fixed point in deterministic FP64 mode, a plain atomic otherwise.
+__device__ __forceinline__ void dadd(double* p, double v, const Geom& gm) {
+  if (gm.det) fx_add(p, v, gm.det, gm.dstatus);
+  else atomicAdd(p, v);
+}
+__device__ __forceinline__ void dadd(float* p, float v, const Geom&) { atomicAdd(p, v); }
 
 // Folded DST-I order (Sec. 3.2 solver).  With S_jk = sin(pi j k / n),
 // S_{n-j,k} = -(-1)^k S_jk: odd k see only x_j + x_{n-j}, even k only x_j - x_{n-j},

@@ -134,10 +134,10 @@ __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, 
         const int64_t node = (int64_t)iy * gm.nx + ix;
         if (cur) {
           V4<T>* q = dep + node;
-          atomicAdd(&q->a, s);
-          atomicAdd(&q->b, s * cx);
-          atomicAdd(&q->c, s * cy);
-          atomicAdd(&q->d, s * cz);
+          dadd(&q->a, s, gm);
+          dadd(&q->b, s * cx, gm);
+          dadd(&q->c, s * cy, gm);
+          dadd(&q->d, s * cz, gm);
           if (ps) atomicAdd(ps + node, float(s) * omvz);
           if (bjc) {
             atomicAdd(&bjc[node].a, s * cx);
@@ -145,8 +145,8 @@ __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, 
           }
         } else {
           V2<T>* q = bjn + node;
-          atomicAdd(&q->a, s * cx);
-          atomicAdd(&q->b, s * cy);
+          dadd(&q->a, s * cx, gm);
+          dadd(&q->b, s * cy, gm);
         }
       }
     }
@@ -231,7 +231,8 @@ __global__ void k_beam_push(hq_beam_view v, const int32_t* __restrict__ off, con
 }
 
 // sums += (q w, q w Ez, q w Ez^2) over the particles of slice i (Ez gathered in the
-// field type, sums in FP64).
+// field type, sums in FP64).  Deterministic FP64 mode: every particle's terms go to the fixed-
+// point mirror of sums (the grid's witness accumulator), independent of particle order.
 template <int P, typename T>
 __global__ void k_witness(hq_beam_view v, const int32_t* __restrict__ off, const int32_t* __restrict__ perm, int slice,
                           Geom gm, const T* __restrict__ gf, double* sums) {
@@ -258,6 +259,12 @@ __global__ void k_witness(hq_beam_view v, const int32_t* __restrict__ off, const
     }
     const double qw = v.charge * v.w[p];
     const double e = (double)ez;
+    if (gm.det) {
+      fx_add(sums, qw, gm.det, gm.dstatus);
+      fx_add(sums + 1, qw * e, gm.det, gm.dstatus);
+      fx_add(sums + 2, qw * e * e, gm.det, gm.dstatus);
+      continue;
+    }
     s0 += qw;
     s1 += qw * e;
     s2 += qw * e * e;

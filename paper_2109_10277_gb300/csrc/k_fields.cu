@@ -182,6 +182,26 @@ void launch_zero(void* p, int64_t n, cudaStream_t s) {
   if (n > 0) k_zero<T><<<blocks_for(n), kThreads, 0, s>>>(reinterpret_cast<T*>(p), n);
 }
 
+// Deterministic FP64 mode: value of each element's fixed-point mirror (H 2^-32 + L 2^-72, see
+// fx_add) added to the element (or to dst[i]); the mirror is cleared.  Elements whose mirror is
+// zero are left untouched.
+__global__ void k_fx_decode(double* rec, int64_t n, int64_t det, double* dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long* m = reinterpret_cast<unsigned long long*>(2ull * reinterpret_cast<uintptr_t>(rec + i) + (uint64_t)det);
+  const long long hi = (long long)m[0], lo = (long long)m[1];
+  if ((hi | lo) == 0) return;
+  const double v = (double)hi * 0x1p-32 + (double)lo * 0x1p-72;
+  if (dst) dst[i] += v;
+  else rec[i] += v;
+  m[0] = 0ull;
+  m[1] = 0ull;
+}
+
+void launch_fx_decode(const hq_grid_s* g, void* rec, int64_t n, double* dst, cudaStream_t s) {
+  if (n > 0) k_fx_decode<<<blocks_for(n), kThreads, 0, s>>>(static_cast<double*>(rec), n, g->geom.det, dst);
+}
+
 #define HQ_INST(T)                                                                              \
   template void launch_reset_dep<T>(const hq_grid_s*, void*, void*, cudaStream_t);             \
   template void launch_src_main<T>(const hq_grid_s*, const void*, cudaStream_t);               \

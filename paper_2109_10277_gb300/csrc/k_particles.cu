@@ -21,21 +21,21 @@ namespace {
 // of partly filled waves (trial and final passes 2.4 % faster on the blowout512 sweep than 256)
 constexpr int kThreads = 128;
 
-__device__ __forceinline__ void atomic_add4(V4<float>* p, float a, float b, float c, float d) {
+__device__ __forceinline__ void atomic_add4(V4<float>* p, float a, float b, float c, float d, const Geom&) {
   atomicAdd(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
 }
-__device__ __forceinline__ void atomic_add4(V4<double>* p, double a, double b, double c, double d) {
-  atomicAdd(&p->a, a);
-  atomicAdd(&p->b, b);
-  atomicAdd(&p->c, c);
-  atomicAdd(&p->d, d);
+__device__ __forceinline__ void atomic_add4(V4<double>* p, double a, double b, double c, double d, const Geom& gm) {
+  dadd(&p->a, a, gm);
+  dadd(&p->b, b, gm);
+  dadd(&p->c, c, gm);
+  dadd(&p->d, d, gm);
 }
-__device__ __forceinline__ void atomic_add2(V2<float>* p, float a, float b) {
+__device__ __forceinline__ void atomic_add2(V2<float>* p, float a, float b, const Geom&) {
   atomicAdd(reinterpret_cast<float2*>(p), make_float2(a, b));
 }
-__device__ __forceinline__ void atomic_add2(V2<double>* p, double a, double b) {
-  atomicAdd(&p->a, a);
-  atomicAdd(&p->b, b);
+__device__ __forceinline__ void atomic_add2(V2<double>* p, double a, double b, const Geom& gm) {
+  dadd(&p->a, a, gm);
+  dadd(&p->b, b, gm);
 }
 
 // Six gathered fields: ExmBy, EypBx, Ez, Bx, By, Bz.
@@ -118,8 +118,9 @@ __device__ __forceinline__ T uz_of(T ux, T uy, T opp, double psi, T g) {
 }
 
 template <int P, typename T>
-__device__ __forceinline__ void deposit_full(V4<T>* dep, T* chi, int nx, int ny, int ix0, int iy0,
+__device__ __forceinline__ void deposit_full(V4<T>* dep, T* chi, const Geom& gm, int ix0, int iy0,
                                              const T* wx, const T* wy, T rho, T jx, T jy, T jz, T ch) {
+  const int nx = gm.nx, ny = gm.ny;
 #pragma unroll
   for (int b = 0; b <= P; ++b) {
     const int iy = iy0 + b;
@@ -130,15 +131,16 @@ __device__ __forceinline__ void deposit_full(V4<T>* dep, T* chi, int nx, int ny,
       if (!in_interior(ix, nx)) continue;
       const T wgt = wx[a] * wy[b];
       const int64_t node = (int64_t)iy * nx + ix;
-      atomic_add4(dep + node, wgt * rho, wgt * jx, wgt * jy, wgt * jz);
-      if (chi) atomicAdd(chi + node, wgt * ch);
+      atomic_add4(dep + node, wgt * rho, wgt * jx, wgt * jy, wgt * jz, gm);
+      if (chi) dadd(chi + node, wgt * ch, gm);
     }
   }
 }
 
 template <int P, typename T>
-__device__ __forceinline__ void deposit_perp(V2<T>* tj, int nx, int ny, int ix0, int iy0,
+__device__ __forceinline__ void deposit_perp(V2<T>* tj, const Geom& gm, int ix0, int iy0,
                                              const T* wx, const T* wy, T jx, T jy) {
+  const int nx = gm.nx, ny = gm.ny;
 #pragma unroll
   for (int b = 0; b <= P; ++b) {
     const int iy = iy0 + b;
@@ -148,7 +150,7 @@ __device__ __forceinline__ void deposit_perp(V2<T>* tj, int nx, int ny, int ix0,
       const int ix = ix0 + a;
       if (!in_interior(ix, nx)) continue;
       const T wgt = wx[a] * wy[b];
-      atomic_add2(tj + (int64_t)iy * nx + ix, wgt * jx, wgt * jy);
+      atomic_add2(tj + (int64_t)iy * nx + ix, wgt * jx, wgt * jy, gm);
     }
   }
 }
@@ -246,7 +248,7 @@ __global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* 
       for (int a = 0; a <= P; ++a) {
         const int ix = ix0 + a;
         if (!in_interior(ix, gm.nx)) continue;
-        atomicAdd(rho_ion + (int64_t)iy * gm.nx + ix, -(wx[a] * wy[b] * qw));
+        dadd(rho_ion + (int64_t)iy * gm.nx + ix, -(wx[a] * wy[b] * qw), gm);
       }
     }
     return;
@@ -256,7 +258,7 @@ __global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* 
   const T g = T(1) / opp;
   const T gam = (T(1) + ux * ux + uy * uy + opp * opp) * T(0.5) * g;
   const T uz = uz_of<T>(ux, uy, opp, pl.psi[p], g);
-  deposit_full<P, T>(dep, chi, gm.nx, gm.ny, ix0, iy0, wx, wy, qw * gam * g, qw * ux * g, qw * uy * g,
+  deposit_full<P, T>(dep, chi, gm, ix0, iy0, wx, wy, qw * gam * g, qw * ux * g, qw * uy * g,
                      qw * uz * g, qw * T(-1) * g);
 }
 
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
   }
   const T qw = charge_density<T>(pl.w[p], gm);
   const T tg = T(1) / topp;
-  deposit_perp<P, T>(tj, gm.nx, gm.ny, tix0, tiy0, twx, twy, qw * tux * tg, qw * tuy * tg);
+  deposit_perp<P, T>(tj, gm, tix0, tiy0, twx, twy, qw * tux * tg, qw * tuy * tg);
 }
 
 // ---------------------------------------------------------------- FP32 psi source
@@ -644,7 +646,7 @@ __global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pa
   const T g = T(1) / topp;
   const T gam = (T(1) + nux * nux + nuy * nuy + topp * topp) * T(0.5) * g;
   const T uz = uz_of<T>(nux, nuy, topp, npsi, g);
-  deposit_full<P, T>(dep, chi, gm.nx, gm.ny, ix0, iy0, wx, wy, qw * gam * g, qw * nux * g, qw * nuy * g,
+  deposit_full<P, T>(dep, chi, gm, ix0, iy0, wx, wy, qw * gam * g, qw * nux * g, qw * nuy * g,
                      qw * uz * g, qw * T(-1) * g);
   if constexpr (CACHE)
     if (ps) deposit_psi_src<P>(ps, gm, jx, frx, dfx, jy, fry, dfy, s0, qw);

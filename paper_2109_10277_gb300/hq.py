@@ -36,7 +36,7 @@ class GridDesc(C.Structure):
                 ("radial_profile", C.POINTER(C.c_double)), ("n_profile", C.c_int32), ("profile_rmax", C.c_double),
                 ("n0_scale", C.c_double), ("n_pc_iter", C.c_int32), ("pc_mix", C.c_double),
                 ("psi_guard", C.c_double), ("precision", C.c_int32), ("bperp_solver", C.c_int32),
-                ("resort_every", C.c_int32)]
+                ("resort_every", C.c_int32), ("deterministic", C.c_int32)]
 
 
 class BeamView(C.Structure):
@@ -169,7 +169,8 @@ class Grid:
             float(params.get("n0_scale", 1.0)), int(params.get("n_pc_iter", 5)), float(params.get("pc_mix", 0.05)),
             float(params.get("psi_guard", 0.02)),
             HQ_PREC_FP64 if precision == "fp64" else HQ_PREC_FP32_BF16X3,
-            {"pc": 0, "explicit": 1}[params.get("bperp_solver", "pc")], int(params.get("resort_every", 0)))
+            {"pc": 0, "explicit": 1}[params.get("bperp_solver", "pc")], int(params.get("resort_every", 0)),
+            int(params.get("deterministic", 0)))
         self.params = dict(params)
         self.nx, self.ny, self.nzeta = d.nx, d.ny, d.nzeta
         self.stream = stream if stream is not None else torch.cuda.current_stream()
