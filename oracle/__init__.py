@@ -32,6 +32,11 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                        within 5 % converging under dzeta and dx refinement; lag behind a converged
                        iteration second order in dzeta
   beam push            pinned: uniform-B gyration, uniform-E energy gain, time reversibility
+  plasma species       pinned: a split into two half-density species is exact, heavy mobile ions
+                       reproduce the immobile background, a positron plasma's wake differs at second
+                       order in n_b, mobile light ions raise the plasma frequency by sqrt(1 + m_e/M)
+  slice loop / sweep   SliceLoop.slice is the per-slice body the sweep and the temporal pipeline
+                       drive; the pipeline over CPU ranks reproduces the serial loop bit for bit
   blowout-regime physics (cfg 512^2 n_b=5): parity unpinned beyond the checks above
   working_precision    a test knob: the same steps in another float type (rounding floors)
 """

@@ -69,6 +69,23 @@ AB5 = (1901.0 / 720.0, -2774.0 / 720.0, 2616.0 / 720.0, -1274.0 / 720.0, 251.0 /
 FIELD_NAMES = ("rho", "jx", "jy", "jz", "chi", "psi", "exmby", "eypbx", "ez", "bx", "by", "bz")
 
 
+@dataclass(frozen=True)
+class Species:
+    """One plasma species (Sec. 6 feature list: plasmas of several species and profiles, ion
+    motion).  charge and mass in units of e and m_e; the push uses q/M (Sec. 3.2 plasma
+    equations), the deposits q and q^2/M.  neutralize: an immobile background of the opposite
+    charge sits at the species' initial positions (the default electron plasma's ions);
+    without it the species' own initial charge is left in the slice."""
+    charge: float = -1.0
+    mass: float = 1.0
+    n0_scale: float = 1.0
+    ppc_x: int = 1
+    ppc_y: int = 1
+    radial_profile: Optional[Sequence[float]] = None
+    profile_rmax: float = 0.0
+    neutralize: bool = True
+
+
 @dataclass
 class GridSpec:
     """Transverse Dirichlet box, zeta range and plasma/solver parameters (Sec. 2, 3.2)."""
@@ -91,6 +108,9 @@ class GridSpec:
     pc_mix: float = 0.05
     psi_guard: float = 0.02
     bperp_solver: str = "pc"    # "pc": predictor-corrector; "explicit": Helmholtz-like equation in chi
+    # plasma species; empty: one electron species (q = -1, M = 1) with immobile ions, placed by
+    # ppc_x, ppc_y, radial_profile, profile_rmax and n0_scale above
+    species: Sequence[Species] = ()
     # "float32": B-spline weights formed from an FP32 cell fraction in FP32 arithmetic
     # (then widened).  A test knob that measures the rounding floor of a single-precision
     # deposit/gather; the method itself is the default, FP64.
@@ -373,14 +393,27 @@ PLASMA_Q = -1.0
 PLASMA_M = 1.0
 
 
+def plasma_species(spec: GridSpec) -> list:
+    """The plasma species of a grid: spec.species, or the default electrons with immobile ions."""
+    if spec.species:
+        return list(spec.species)
+    return [Species(PLASMA_Q, PLASMA_M, spec.n0_scale, spec.ppc_x, spec.ppc_y, spec.radial_profile,
+                    spec.profile_rmax, True)]
+
+
 def plasma_init(spec: GridSpec, n0_scale: Optional[torch.Tensor] = None,
-                radial_profile: Optional[torch.Tensor] = None):
-    """ppc_x x ppc_y electrons per cell at sub-cell centres, at rest (Sec. 2).
+                radial_profile: Optional[torch.Tensor] = None, species: Optional[Species] = None):
+    """ppc_x x ppc_y electrons per cell at sub-cell centres, at rest (Sec. 2); with `species`,
+    that species' particles per cell, density scale and profile instead of the grid's.
 
     Ordering: cell row-major (iy, ix), then sub-particle (sy, sx).
     w = n0_scale * n(r) * dx * dy / ppc with n(r) linearly interpolated from the
     radial profile over [0, profile_rmax] (uniform if no profile).
     """
+    if species is not None:
+        spec = GridSpec(**{**spec.__dict__, "ppc_x": species.ppc_x, "ppc_y": species.ppc_y,
+                           "radial_profile": species.radial_profile, "profile_rmax": species.profile_rmax,
+                           "n0_scale": species.n0_scale, "species": ()})
     px, py = spec.ppc_x, spec.ppc_y
     iy, ix, sy, sx = torch.meshgrid(torch.arange(spec.ny), torch.arange(spec.nx),
                                     torch.arange(py), torch.arange(px), indexing="ij")
@@ -588,40 +621,70 @@ class SweepResult:
     beams: list = field(default_factory=list)        # beams after the push (dt != 0)
     witness: dict = field(default_factory=dict)      # beam index -> (sum qw, sum qw Ez, sum qw Ez^2)
     plasma_at: dict = field(default_factory=dict)    # slice -> plasma state at that slice
+    plasma_species: list = field(default_factory=list)  # every species' state after the last slice
+
+
+def _add_fields(a, b):
+    return [x + y for x, y in zip(a, b)]
+
+
+def _sum_species(parts):
+    """Componentwise sum of per-species field lists (one species: its list itself, no added zeros)."""
+    out = parts[0]
+    for p_ in parts[1:]:
+        out = _add_fields(out, p_)
+    return out
 
 
 class SliceLoop:
     """The slice loop's state and per-slice body (Sec. 2 enumerate, Fig. 1; Sec. 3.2
-    predictor-corrector), one slice per call: the plasma slice with its AB5 history, the
-    previous slices' plasma J_perp, beam J_perp and B_perp, and the deposit of the slice
-    about to be solved.  ``sweep`` drives it over the whole box; the temporal pipeline of
+    predictor-corrector), one slice per call: the plasma slice of every species with its AB5
+    history, the previous slices' plasma J_perp, beam J_perp and B_perp, and the deposit of the
+    slice about to be solved.  ``sweep`` drives it over the whole box; the temporal pipeline of
     Sec. 5.2 drives it box by box with the beam handed over from the previous time step.
 
-    Per slice i (``slice``): deposit plasma + ions + beam(i); solve psi -> ExmBy, EypBx; Ez;
-    Bz; predictor-corrector (or the explicit solver) for Bx, By; final gather; push the
-    beam particles of slice i; final AB5 step of the plasma to slice i + 1.
+    Per slice i (``slice``): deposit plasma (all species) + immobile backgrounds + beam(i);
+    solve psi -> ExmBy, EypBx; Ez; Bz; predictor-corrector (or the explicit solver) for Bx, By;
+    final gather; push the beam particles of slice i; final AB5 step of every plasma species to
+    slice i + 1 (each with its own q/M).
     """
 
     def __init__(self, spec: GridSpec, n0_scale: Optional[torch.Tensor] = None,
                  radial_profile: Optional[torch.Tensor] = None, plasma_perm: Optional[torch.Tensor] = None,
                  reverse_ion_order: bool = False, deposit_noise: float = 0.0, noise_seed: int = 0):
         self.spec = spec
-        st = plasma_init(spec, n0_scale, radial_profile)
-        if plasma_perm is not None:
-            st = {k: v[plasma_perm] for k, v in st.items()}
-        rho_ion = ion_background(spec, st, reverse=reverse_ion_order)
+        self.species = plasma_species(spec)
+        sts = []
+        for k, sp_ in enumerate(self.species):
+            st = plasma_init(spec, n0_scale, radial_profile) if not spec.species else plasma_init(spec, species=sp_)
+            if plasma_perm is not None and k == 0:
+                st = {kk: v[plasma_perm] for kk, v in st.items()}
+            sts.append(st)
+        bgs = [ion_background(spec, st, q=sp_.charge, reverse=reverse_ion_order)
+               for sp_, st in zip(self.species, sts) if sp_.neutralize]
+        rho_ion = _sum_species([[b] for b in bgs])[0] if bgs else torch.zeros(spec.ny, spec.nx, dtype=DT)
         self.gen = torch.Generator().manual_seed(noise_seed)
         self.deposit_noise = deposit_noise
         self.rho_ion = self.noisy([rho_ion])[0]
         zero = torch.zeros(spec.ny, spec.nx, dtype=DT)
         self.zero = zero
-        self.hist = [(torch.zeros_like(st["x"]),) * 5 for _ in range(4)]  # f_{i-1} .. f_{i-4}
+        # f_{i-1} .. f_{i-4} per species
+        self.hists = [[(torch.zeros_like(st["x"]),) * 5 for _ in range(4)] for st in sts]
         self.jx_prev, self.jy_prev = zero, zero
         self.bj_prev = (zero, zero)   # beam J_perp of slice i-1 (explicit solver)
         self.b1 = (zero, zero)
         self.b2 = (zero, zero)
-        self.st = st
-        self.src = self.noisy(plasma_deposit_full(spec, st))
+        self.sts = sts
+        self.src = self._deposit_full()
+
+    @property
+    def st(self):
+        """The first species' plasma state (the only one of the default plasma)."""
+        return self.sts[0]
+
+    def _deposit_full(self):
+        return self.noisy(_sum_species([plasma_deposit_full(self.spec, st, sp_.charge, sp_.mass)
+                                        for sp_, st in zip(self.species, self.sts)]))
 
     def noisy(self, fields):
         if self.deposit_noise <= 0.0:
@@ -637,8 +700,7 @@ class SliceLoop:
         last P-C residual, cur's beams after the push of dt (unchanged for dt = 0), witness sums)."""
         spec, zero = self.spec, self.zero
         dz = spec.dzeta
-        qm = PLASMA_Q / PLASMA_M
-        st, hist = self.st, self.hist
+        sts, hists, species = self.sts, self.hists, self.species
         rho, jx, jy, jz, chi = self.src
         rho = rho + self.rho_ion
         bj_cur = (zero, zero)
@@ -662,20 +724,26 @@ class SliceLoop:
         if spec.bperp_solver == "explicit":
             # explicit solver: (L - chi) Bx = -dy Jz + Ty, (L - chi) By = dx Jz - Tx with T the
             # B-independent part of d(J_perp)/d(zeta) (explicit_sources; beams by central differences)
-            F4 = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bz), spec.shape_order)
-            fx, fy, jxx, jxy, jyy = self.noisy(explicit_sources(spec, st, F4))
+            parts = []
+            for sp_, st in zip(species, sts):
+                F4 = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bz), spec.shape_order)
+                parts.append(explicit_sources(spec, st, F4, sp_.charge, sp_.mass))
+            fx, fy, jxx, jxy, jyy = self.noisy(_sum_species(parts))
             tx = fx + ddx(spec, jxx) + ddy(spec, jxy) + (self.bj_prev[0] - njx) / (2.0 * dz)
             ty = fy + ddx(spec, jxy) + ddy(spec, jyy) + (self.bj_prev[1] - njy) / (2.0 * dz)
             (bx, by), rr = helmholtz_pcg(spec, chi, (sbx0 + ty, sby0 - tx), (bx, by), spec.n0_scale,
                                          spec.n_pc_iter)
             resid = max(rr)
         for _m in range(spec.n_pc_iter if spec.bperp_solver == "pc" else 0):
-            F = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bx, by, bz), spec.shape_order)
-            f = derivs(qm, st["ux"], st["uy"], st["psi"], F)
-            tx, ty, tux, tuy, tpsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
-                                              [f] + hist, dz)
-            ok = st["alive"] & _state_ok(spec, tx, ty, tpsi)
-            pjx, pjy = self.noisy(plasma_deposit_jperp(spec, tx, ty, tux, tuy, tpsi, st["w"], ok))
+            parts = []
+            for sp_, st, hist in zip(species, sts, hists):
+                F = gather(spec, st["x"], st["y"], (exmby, eypbx, ez, bx, by, bz), spec.shape_order)
+                f = derivs(sp_.charge / sp_.mass, st["ux"], st["uy"], st["psi"], F)
+                tx, ty, tux, tuy, tpsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
+                                                  [f] + hist, dz)
+                ok = st["alive"] & _state_ok(spec, tx, ty, tpsi)
+                parts.append(plasma_deposit_jperp(spec, tx, ty, tux, tuy, tpsi, st["w"], ok, q=sp_.charge))
+            pjx, pjy = self.noisy(_sum_species(parts))
             jx1, jy1 = pjx + njx, pjy + njy
             dzjx, dzjy = (self.jx_prev - jx1) / (2.0 * dz), (self.jy_prev - jy1) / (2.0 * dz)
             bxs = poisson_solve(spec, sbx0 + dzjy)
@@ -687,8 +755,6 @@ class SliceLoop:
             resid = float(num / den) if float(den) > 0 else 0.0
             bx, by = nbx, nby
         Fs = (exmby, eypbx, ez, bx, by, bz)
-        F = gather(spec, st["x"], st["y"], Fs, spec.shape_order)
-        f = derivs(qm, st["ux"], st["uy"], st["psi"], F)
         out = dict(rho=rho, jx=jx, jy=jy, jz=jz, chi=chi, psi=psi, exmby=exmby, eypbx=eypbx,
                    ez=ez, bx=bx, by=by, bz=bz)
         wsums = []
@@ -698,15 +764,20 @@ class SliceLoop:
             qw = b["charge"] * b["w"][sel]
             wsums.append((qw.sum(), (qw * ezw).sum(), (qw * ezw * ezw).sum()))
         pushed = [beam_push(spec, b, sel, Fs, dt) if dt != 0.0 else b for b, sel in cur]
-        # final AB5 step to slice i+1 with the converged fields, then removal and deposit
-        nx_, ny_, nux, nuy, npsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
-                                            [f] + hist, dz)
-        self.hist = [f] + hist[:3]
-        alive = st["alive"] & _state_ok(spec, nx_, ny_, npsi)
-        keep = lambda new, old: torch.where(alive, new, old)  # noqa: E731
-        self.st = dict(x=keep(nx_, st["x"]), y=keep(ny_, st["y"]), ux=keep(nux, st["ux"]),
-                       uy=keep(nuy, st["uy"]), psi=keep(npsi, st["psi"]), w=st["w"], alive=alive)
-        self.src = self.noisy(plasma_deposit_full(spec, self.st))
+        # final AB5 step of every species to slice i+1 with the converged fields, removal, deposit
+        new_sts, new_hists = [], []
+        for sp_, st, hist in zip(species, sts, hists):
+            F = gather(spec, st["x"], st["y"], Fs, spec.shape_order)
+            f = derivs(sp_.charge / sp_.mass, st["ux"], st["uy"], st["psi"], F)
+            nx_, ny_, nux, nuy, npsi = ab5_step((st["x"], st["y"], st["ux"], st["uy"], st["psi"]),
+                                                [f] + hist, dz)
+            new_hists.append([f] + hist[:3])
+            alive = st["alive"] & _state_ok(spec, nx_, ny_, npsi)
+            keep = lambda new, old: torch.where(alive, new, old)  # noqa: E731
+            new_sts.append(dict(x=keep(nx_, st["x"]), y=keep(ny_, st["y"]), ux=keep(nux, st["ux"]),
+                                uy=keep(nuy, st["uy"]), psi=keep(npsi, st["psi"]), w=st["w"], alive=alive))
+        self.sts, self.hists = new_sts, new_hists
+        self.src = self._deposit_full()
         self.jx_prev, self.jy_prev = jx, jy
         self.bj_prev = bj_cur
         self.b2, self.b1 = b1, (bx, by)
@@ -758,7 +829,8 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
         beams = pushed
     st = loop.st
     res.fields = {k: torch.stack(v) for k, v in rec.items()}
-    res.removed = int((~st["alive"]).sum())
+    res.removed = sum(int((~s_["alive"]).sum()) for s_ in loop.sts)
+    res.plasma_species = [dict(s_) for s_ in loop.sts]
     if plasma_perm is not None:
         inv = torch.argsort(plasma_perm)
         st = {k: v[inv] for k, v in st.items()}

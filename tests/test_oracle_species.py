@@ -1,0 +1,101 @@
+"""Pins for the oracle's plasma species (Sec. 6 feature list: plasmas of several species and
+profiles, ion motion; the push takes each species' q/M, Sec. 3.2 plasma equations).
+
+  * splitting the electrons into two species of half the density each changes nothing: the
+    deposits of the halves add up to the whole bit for bit;
+  * electrons with mobile ions of mass 1e8 m_e and no immobile background reproduce the default
+    plasma (electrons over immobile ions) to the ions' 1/M response;
+  * a positron plasma drives the same wake as an electron plasma to first order in the beam
+    density (the linear response goes with q^2/M): the difference halves with n_b;
+  * with ions of mass 4 m_e moving too, the plasma frequency is sqrt(1 + m_e/M) times the
+    electrons' alone, which sets the wake's half-period behind a weak wide driver.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2109_10277_gb300 import inputs as I
+
+
+def grid(**kw):
+    g = dict(nx=32, ny=32, nzeta=48, xmin=-4.0, xmax=4.0, ymin=-4.0, ymax=4.0, zeta_min=-8.0, zeta_max=2.0,
+             shape_order=1, n_pc_iter=3, pc_mix=0.05, psi_guard=0.02)
+    g.update(kw)
+    return O.GridSpec(**g)
+
+
+def beam(nb, n=4000):
+    return O.as_beam(I.random_beam(n, 0.6, 0.6, 0.5, nb, zeta0=0.5))
+
+
+def rel(a, b):
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+def test_default_plasma_is_one_electron_species():
+    sp = grid(ppc_x=2, n0_scale=1.3)
+    (s,) = O.plasma_species(sp)
+    assert (s.charge, s.mass, s.n0_scale, s.ppc_x, s.ppc_y, s.neutralize) == (-1.0, 1.0, 1.3, 2, 1, True)
+    a = O.plasma_init(sp)
+    b = O.plasma_init(grid(), species=s)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_split_species_is_exact():
+    r0 = O.sweep(grid(), [beam(0.05)])
+    half = O.Species(-1.0, 1.0, 0.5)
+    r1 = O.sweep(grid(species=(half, half)), [beam(0.05)])
+    for k in O.FIELD_NAMES:
+        assert torch.equal(r0.fields[k], r1.fields[k]), k
+    for s_ in r1.plasma_species:
+        for k in ("x", "y", "ux", "uy", "psi"):
+            assert torch.equal(s_[k], r0.plasma[k]), k
+
+
+def test_heavy_mobile_ions_match_immobile_background():
+    r0 = O.sweep(grid(), [beam(0.05)])
+    sp = grid(species=(O.Species(-1.0, 1.0, neutralize=False), O.Species(1.0, 1e8, neutralize=False)))
+    r1 = O.sweep(sp, [beam(0.05)])
+    for k in ("rho", "jz", "psi", "ez", "bx", "by", "bz"):
+        assert rel(r1.fields[k], r0.fields[k]) <= 1e-6, k
+    # the ions barely move, the electrons as before
+    ions = r1.plasma_species[1]
+    x0 = O.plasma_init(sp, species=sp.species[1])["x"]
+    assert float((ions["x"] - x0).abs().max()) <= 1e-7
+    assert rel(r1.plasma_species[0]["x"], r0.plasma["x"]) <= 1e-9
+
+
+def test_positron_plasma_wake_is_second_order_in_beam_density():
+    d = {}
+    for nb in (0.02, 0.01):
+        a = O.sweep(grid(), [beam(nb)])
+        b = O.sweep(grid(species=(O.Species(1.0, 1.0),)), [beam(nb)])
+        d[nb] = {k: rel(b.fields[k], a.fields[k]) for k in ("ez", "psi", "bx")}
+    for k in ("ez", "psi", "bx"):
+        assert d[0.02][k] <= 1.0 * 0.02, (k, d)               # small: first order agrees
+        assert 1.8 <= d[0.02][k] / d[0.01][k] <= 2.2, (k, d)   # and the rest is second order
+
+
+def half_periods(sp):
+    r = O.sweep(sp, [O.as_beam(I.random_beam(8000, 1.0, 1.0, 0.3, 0.01, zeta0=0.5))], record=("ez",))
+    c = sp.nx // 2
+    ez = r.fields["ez"][:, c, c].numpy()
+    zc = sp.zeta_max - (np.arange(sp.nzeta) + 0.5) * sp.dzeta
+    idx = np.nonzero(np.sign(ez[:-1]) != np.sign(ez[1:]))[0]
+    cr = [zc[i] + (zc[i + 1] - zc[i]) * ez[i] / (ez[i] - ez[i + 1]) for i in idx if zc[i] < -2.0]
+    return -np.diff(cr)
+
+
+@pytest.mark.slow
+def test_ion_motion_raises_the_plasma_frequency():
+    g = dict(nx=32, ny=32, nzeta=160, xmin=-6.0, xmax=6.0, ymin=-6.0, ymax=6.0, zeta_min=-28.0, zeta_max=2.0)
+    e = O.Species(-1.0, 1.0, neutralize=False)
+    fixed = half_periods(grid(**g, species=(e, O.Species(1.0, 1e9, neutralize=False))))
+    light = half_periods(grid(**g, species=(e, O.Species(1.0, 4.0, neutralize=False))))
+    assert len(fixed) >= 5 and len(light) >= 5
+    ratio = float(np.mean(light[:5]) / np.mean(fixed[:5]))
+    assert ratio == pytest.approx(1.0 / math.sqrt(1.0 + 1.0 / 4.0), rel=1e-2), ratio
