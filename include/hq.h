@@ -73,6 +73,23 @@ typedef enum {
   HQ_PREC_FP32_BF16X3 = 1
 } hq_precision;
 
+/* One plasma species (Sec. 6: plasmas of several species and profiles, ion motion).  The
+ * push takes the species' q/M (Sec. 3.2 plasma equations), the deposits q (and q^2/M for chi).
+ * Placement as for the default plasma: ppc_x x ppc_y particles per cell at sub-cell centres,
+ * weight n0_scale * n(r) * dx * dy / ppc.  neutralize = 1: an immobile background of the
+ * opposite charge sits at the species' initial positions (the default electrons' ions); 0:
+ * the species' own initial charge stays in the slice (e.g. electrons and mobile ions placed
+ * alike neutralize each other). */
+typedef struct {
+  double charge, mass;              /* units of e and m_e: the default electrons are -1, 1 */
+  double n0_scale;
+  int32_t ppc_x, ppc_y;             /* 1..16 each                                          */
+  const double* radial_profile;     /* host; n_profile entries over [0, profile_rmax]; NULL = uniform */
+  int32_t n_profile;
+  double profile_rmax;
+  int32_t neutralize;               /* 0 or 1                                               */
+} hq_species_desc;
+
 /* Grid, plasma and solver description; every field is copied by hq_grid_create.
  * Sec. 2 (slice loop), Sec. 3.2 (push, deposition, Poisson and P-C solvers). */
 typedef struct {
@@ -105,6 +122,15 @@ typedef struct {
                                        additions: bitwise reproducible.  Refused by
                                        hq_sweep_forward_ckpt (HQ_ERR_UNSUPPORTED); 0: FP64
                                        atomics (last-bit run-to-run differences)          */
+  const hq_species_desc* species;   /* host array of n_species (1..4) plasma species, copied;
+                                       the plasma slice holds them one after the other
+                                       (species s from sum_{t<s} nx ny ppc_t on); with
+                                       species the grid's ppc_x, ppc_y, radial_profile,
+                                       profile_rmax and n0_scale do not place the plasma.
+                                       Not with the explicit solver, the re-sort or the
+                                       checkpointed forward (HQ_ERR_UNSUPPORTED)           */
+  int32_t n_species;                /* 0: the default electrons (q = -1, M = 1) over
+                                       immobile ions, placed by the fields above          */
 } hq_grid_desc;
 
 /* B_perp field solver (Sec. 3.2: "predictor-corrector field solver" and "explicit field

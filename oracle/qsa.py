@@ -834,6 +834,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
     if plasma_perm is not None:
         inv = torch.argsort(plasma_perm)
         st = {k: v[inv] for k, v in st.items()}
+        res.plasma_species[0] = st
         res.plasma_at = {i: {k: v[inv] for k, v in s_.items()} for i, s_ in res.plasma_at.items()}
     res.plasma = st
     res.beams = beams

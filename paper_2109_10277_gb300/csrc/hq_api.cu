@@ -61,6 +61,8 @@ void free_all(hq_grid_s* g) {
     F(g->det_arena);
     F(g->det_mirror);
   }
+  for (int k = 0; k < kMaxSpecies; ++k) F(g->d_sp_prof[k]);
+  F(g->c0);
   F(g->porigin); F(g->sort_key); F(g->sort_perm); F(g->sort_count); F(g->sort_offset); F(g->sort_tsum);
   F(g->sort_scratch);
   for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); F(g->psrc[i]); }
@@ -818,7 +820,26 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     return fail(nullptr, HQ_ERR_UNSUPPORTED, "deterministic accumulation covers the predictor-corrector solver only");
   if (d.radial_profile && (d.n_profile < 2 || !(d.profile_rmax > 0.0)))
     return fail(nullptr, HQ_ERR_ARG, "radial profile needs n_profile >= 2 and profile_rmax > 0");
-  const int64_t np = (int64_t)d.nx * d.ny * d.ppc_x * d.ppc_y;
+  if (d.n_species < 0 || d.n_species > kMaxSpecies || (d.n_species > 0 && !d.species))
+    return fail(nullptr, HQ_ERR_ARG, "n_species must be 0..4 (with a species array)");
+  for (int k = 0; k < d.n_species; ++k) {
+    const hq_species_desc& sd = d.species[k];
+    if (!std::isfinite(sd.charge) || sd.charge == 0.0 || !(sd.mass > 0.0) || !std::isfinite(sd.mass) ||
+        !std::isfinite(sd.n0_scale))
+      return fail(nullptr, HQ_ERR_ARG, "species charge must be finite and non-zero, mass positive and finite");
+    if (sd.ppc_x < 1 || sd.ppc_y < 1 || sd.ppc_x > 16 || sd.ppc_y > 16)
+      return fail(nullptr, HQ_ERR_ARG, "species ppc must be 1..16");
+    if (sd.radial_profile && (sd.n_profile < 2 || !(sd.profile_rmax > 0.0)))
+      return fail(nullptr, HQ_ERR_ARG, "species radial profile needs n_profile >= 2 and profile_rmax > 0");
+    if (sd.neutralize != 0 && sd.neutralize != 1) return fail(nullptr, HQ_ERR_ARG, "species neutralize must be 0 or 1");
+  }
+  if (d.n_species > 0 && d.bperp_solver == HQ_BPERP_EXPLICIT)
+    return fail(nullptr, HQ_ERR_UNSUPPORTED, "the explicit B_perp solver takes the default electron plasma only");
+  if (d.n_species > 0 && d.resort_every > 0)
+    return fail(nullptr, HQ_ERR_UNSUPPORTED, "the plasma re-sort takes the default electron plasma only");
+  int64_t np = 0;
+  if (d.n_species == 0) np = (int64_t)d.nx * d.ny * d.ppc_x * d.ppc_y;
+  for (int k = 0; k < d.n_species; ++k) np += (int64_t)d.nx * d.ny * d.species[k].ppc_x * d.species[k].ppc_y;
   if (np > (1LL << 31) - 1) return fail(nullptr, HQ_ERR_ARG, "too many plasma particles");
 
   int dev = 0;
@@ -834,6 +855,47 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   g->d = d;
   if (d.radial_profile) g->profile.assign(d.radial_profile, d.radial_profile + d.n_profile);
   g->d.radial_profile = nullptr;
+  // plasma species: the descriptors and their profiles are copied; the kernels' table gets the
+  // device profiles below
+  g->multi = d.n_species > 0;
+  g->species.assign(d.species, d.species + d.n_species);
+  g->sp_prof.resize(d.n_species);
+  for (int k = 0; k < d.n_species; ++k) {
+    if (d.species[k].radial_profile)
+      g->sp_prof[k].assign(d.species[k].radial_profile, d.species[k].radial_profile + d.species[k].n_profile);
+    g->species[k].radial_profile = nullptr;
+  }
+  g->d.species = nullptr;
+  {
+    SpeciesTab& t = g->sp;
+    t = SpeciesTab{};
+    const int ns = std::max(1, d.n_species);
+    t.n = ns;
+    int64_t off = 0;
+    for (int k = 0; k < ns; ++k) {
+      const bool def = d.n_species == 0;
+      const double q = def ? -1.0 : d.species[k].charge, m = def ? 1.0 : d.species[k].mass;
+      const int px = def ? d.ppc_x : d.species[k].ppc_x, py = def ? d.ppc_y : d.species[k].ppc_y;
+      t.off[k] = off;
+      off += (int64_t)d.nx * d.ny * px * py;
+      t.q[k] = q;
+      t.qm[k] = q / m;
+      t.fq[k] = (float)q;
+      t.fqm[k] = (float)(q / m);
+      t.ppx[k] = px;
+      t.ppy[k] = py;
+      t.pow2[k] = (px & (px - 1)) == 0 && (py & (py - 1)) == 0;
+      t.inv_px[k] = 1.0 / px;
+      t.inv_py[k] = 1.0 / py;
+      t.finv_px[k] = (float)t.inv_px[k];
+      t.finv_py[k] = (float)t.inv_py[k];
+      t.neutral[k] = def ? 1 : d.species[k].neutralize;
+      t.n0[k] = def ? d.n0_scale : d.species[k].n0_scale;
+      t.npf[k] = def ? 0 : (int)g->sp_prof[k].size();
+      t.rmax[k] = def ? 0.0 : d.species[k].profile_rmax;
+    }
+    for (int k = ns; k <= kMaxSpecies; ++k) t.off[k] = off;
+  }
   g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   g->dev = dev;
   g->fp64 = d.precision == HQ_PREC_FP64;
@@ -964,6 +1026,16 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     HQ_ALLOC(g->bins[b].offset, sizeof(int32_t) * (g->nz + 1));
     HQ_ALLOC(g->bins[b].cursor, sizeof(int32_t) * (g->nz + 1));
   }
+  for (int k = 0; k < d.n_species; ++k) {
+    if (g->sp_prof[k].empty()) continue;
+    HQ_ALLOC(g->d_sp_prof[k], 8 * g->sp_prof[k].size());
+    if (cudaMemcpy(g->d_sp_prof[k], g->sp_prof[k].data(), 8 * g->sp_prof[k].size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      g->err = "species profile upload failed";
+      return bail(HQ_ERR_CUDA);
+    }
+    g->sp.prof[k] = g->d_sp_prof[k];
+  }
   if (!g->profile.empty()) {
     HQ_ALLOC(g->d_profile, 8 * g->profile.size());
     if (cudaMemcpy(g->d_profile, g->profile.data(), 8 * g->profile.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -1089,6 +1161,28 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   } else {
     launch_plasma_init<float>(g, g->stream);
     launch_deposit_initial<float>(g, nullptr, nullptr, 1, g->stream);
+    bool bare = false;
+    for (int k = 0; k < d.n_species; ++k) bare |= !d.species[k].neutralize;
+    if (bare) {
+      // the initial charge of the species without a background, for the ion-subtracted psi
+      // source: summed in FP64 on the device, rounded once to FP32
+      double* c0d = nullptr;
+      HQ_ALLOC(c0d, 8 * nn);
+      cudaMemsetAsync(c0d, 0, 8 * nn, g->stream);
+      launch_species_c0(g, c0d, g->stream);
+      std::vector<double> h(nn);
+      std::vector<float> f(nn);
+      const cudaError_t ec = cudaMemcpyAsync(h.data(), c0d, 8 * nn, cudaMemcpyDeviceToHost, g->stream);
+      cudaStreamSynchronize(g->stream);
+      cudaFree(c0d);
+      if (ec != cudaSuccess) {
+        g->err = "species charge download failed";
+        return bail(HQ_ERR_CUDA);
+      }
+      for (size_t i = 0; i < nn; ++i) f[i] = (float)h[i];
+      HQ_ALLOC(g->c0, 4 * nn);
+      cudaMemcpy(g->c0, f.data(), 4 * nn, cudaMemcpyHostToDevice);
+    }
   }
   cudaError_t e = cudaStreamSynchronize(g->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -1295,6 +1389,7 @@ hq_status hq_sweep_forward_ckpt(hq_grid_t g, hq_beam_view* beams, int32_t nbeams
   if (g->explicit_b) return fail(g, HQ_ERR_UNSUPPORTED, "the adjoint supports the predictor-corrector B_perp solver only");
   if (g->d.resort_every > 0) return fail(g, HQ_ERR_UNSUPPORTED, "the adjoint needs the plasma in its initial order (resort_every = 0)");
   if (g->det) return fail(g, HQ_ERR_UNSUPPORTED, "deterministic accumulation is a forward-sweep mode");
+  if (g->multi) return fail(g, HQ_ERR_UNSUPPORTED, "the adjoint takes the default electron plasma only");
   const int k = std::min<int>(ckpt_every, g->nz);
   if ((st = adj_alloc(g, k)) != HQ_OK) return st;
   AdjStore* a = adj_of(g);

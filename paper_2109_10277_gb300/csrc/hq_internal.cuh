@@ -85,6 +85,31 @@ template <typename T> struct Plasma {
   int32_t* origin;
 };
 
+// Plasma species (hq_species_desc), as the particle kernels of a multi-species grid read them:
+// species s holds particles [off[s], off[s + 1]) of the slice.
+constexpr int kMaxSpecies = 4;
+struct SpeciesTab {
+  int n;
+  int64_t off[kMaxSpecies + 1];
+  double q[kMaxSpecies], qm[kMaxSpecies];     // charge (units of e), charge / mass (e / m_e)
+  float fq[kMaxSpecies], fqm[kMaxSpecies];
+  int ppx[kMaxSpecies], ppy[kMaxSpecies];
+  int pow2[kMaxSpecies];                      // both particle counts per cell powers of two
+  double inv_px[kMaxSpecies], inv_py[kMaxSpecies];
+  float finv_px[kMaxSpecies], finv_py[kMaxSpecies];
+  int neutral[kMaxSpecies];                   // immobile background of the opposite charge
+  double n0[kMaxSpecies];
+  const double* prof[kMaxSpecies];            // device radial profile or null
+  int npf[kMaxSpecies];
+  double rmax[kMaxSpecies];
+};
+__device__ __forceinline__ int species_of(const SpeciesTab& t, int64_t p) {
+  int s = 0;
+#pragma unroll
+  for (int k = 1; k < kMaxSpecies; ++k) s += (k < t.n && p >= t.off[k]) ? 1 : 0;
+  return s;
+}
+
 // Per-beam slice binning (counting sort by slice, Sec. 3.1).
 struct BeamBins {
   int32_t* bin;      // per particle, -1 outside the box
@@ -153,6 +178,15 @@ struct hq_grid_s {
   int det;
   void *det_arena, *det_mirror;
   double* det_wsum;
+  // plasma species (d.n_species > 0: multi = 1 and the particle kernels read sp); FP32: c0 is
+  // the initial charge of the species without a neutralizing background, sum q w S(x0) / A,
+  // added to the ion-subtracted psi source (null when every species is neutralized)
+  int multi;
+  hq::SpeciesTab sp;
+  std::vector<hq_species_desc> species;
+  std::vector<std::vector<double>> sp_prof;
+  double* d_sp_prof[hq::kMaxSpecies];
+  float* c0;
 
   // fields (void* typed by fp64)
   void* dep[2];        // V4 per node: rho, jx, jy, jz   (ping-pong by slice parity)
@@ -279,6 +313,9 @@ void dst_tc_free(hq_grid_s* g);
 // beams
 void launch_beam_bin(hq_grid_s* g, int b, const hq_beam_view& v, cudaStream_t s);
 void launch_beam_slices(const hq_grid_s* g, const hq_beam_view& v, int32_t* out, cudaStream_t s);
+// FP32 multi-species grids: sum q w S(x0) / A of the species without a neutralizing background,
+// added in FP64 into out (nnode doubles, zeroed by the caller) (k_particles.cu)
+void launch_species_c0(const hq_grid_s* g, double* out, cudaStream_t s);
 // deterministic FP64 mode: adds the fixed-point mirrors of n elements of rec (a deposit record
 // of the arena) to rec, or to dst when given, and clears the mirrors (k_fields.cu)
 void launch_fx_decode(const hq_grid_s* g, void* rec, int64_t n, double* dst, cudaStream_t s);
@@ -568,13 +605,15 @@ __device__ __forceinline__ auto dyc(const A& f, int iy, int ix, int ny, C inv2dy
 // of k_fields.cu through the grid's operand sink).
 
 // psi: -(rho - Jz);  Ez: dx Jx + dy Jy;  Bz: dy Jx - dx Jy.  With ps (FP32 path) the psi
-// source is the separately accumulated, ion-subtracted rho - Jz.
+// source is the separately accumulated, ion-subtracted rho - Jz, plus c0 (multi-species grids:
+// the initial charge of the species without a neutralizing background) when given.
 template <typename T> struct SrcMain {
   static constexpr int NR = 3;
   static constexpr bool kEffects = false;
   const V4<T>* dep;
   const float* ps;
   Geom gm;
+  const float* c0;
   // what one node's sources read: the psi source, and Jx, Jy at the four neighbours
   struct In {
     T p, jxr, jxl, jxu, jxd, jyr, jyl, jyu, jyd;
@@ -585,7 +624,7 @@ template <typename T> struct SrcMain {
       const int nx = gm.nx;
       const int64_t o = (int64_t)iy * nx + ix;
       if (ps) {
-        q.p = T(-ps[o]);
+        q.p = c0 ? T(-(ps[o] + c0[o])) : T(-ps[o]);
       } else {
         const V4<T> c = dep[o];
         q.p = -(c.a - c.d);
@@ -686,7 +725,7 @@ template <typename T> struct SrcBperp {
 };
 
 template <typename T> inline SrcMain<T> src_main_of(const hq_grid_s* g, const void* dep) {
-  return SrcMain<T>{reinterpret_cast<const V4<T>*>(dep), psrc_of(g, dep), g->geom};
+  return SrcMain<T>{reinterpret_cast<const V4<T>*>(dep), psrc_of(g, dep), g->geom, g->c0};
 }
 template <typename T>
 inline SrcBperp<T> src_bperp_of(const hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int reset_prev) {

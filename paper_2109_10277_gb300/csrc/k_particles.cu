@@ -81,9 +81,10 @@ __device__ __forceinline__ F6<T> gather6(const T* __restrict__ gf, const T* __re
   return F;
 }
 
-// zeta-derivatives of an electron (q/M = -1), Sec. 3.2; opp = 1 + Psi.
-template <typename T>
-__device__ __forceinline__ void derivs(T ux, T uy, T opp, const F6<T>& F, T* f) {
+// zeta-derivatives of a plasma particle, Sec. 3.2; opp = 1 + Psi.  Written for an electron
+// (q/M = -1); a multi-species grid (MS) scales the momentum and Psi rates by mqm = -q/M.
+template <typename T, bool MS = false>
+__device__ __forceinline__ void derivs(T ux, T uy, T opp, const F6<T>& F, T* f, T mqm = T(1)) {
   const T g = T(1) / opp;
   const T gam = (T(1) + ux * ux + uy * uy + opp * opp) * T(0.5) * g;
   const T exmby = F.v[0], eypbx = F.v[1], ez = F.v[2], bx = F.v[3], by = F.v[4], bz = F.v[5];
@@ -92,6 +93,26 @@ __device__ __forceinline__ void derivs(T ux, T uy, T opp, const F6<T>& F, T* f) 
   f[2] = gam * g * exmby + by + bz * g * uy;      // -(q/M)[...] with q/M = -1
   f[3] = gam * g * eypbx - bx - bz * g * ux;
   f[4] = g * (ux * exmby + uy * eypbx) - ez;
+  if constexpr (MS) {
+    f[2] = mqm * f[2];
+    f[3] = mqm * f[3];
+    f[4] = mqm * f[4];
+  }
+}
+
+// A particle's species constants on a multi-species grid (MS), else the electron's: -q/M,
+// q/M (the chi factor q^2/M over q) and q, in the kernel's type.
+template <typename T> struct SpC {
+  T mqm, qm, q;
+};
+template <typename T, bool MS>
+__device__ __forceinline__ SpC<T> spc_of(const SpeciesTab& tab, int s) {
+  if constexpr (MS) {
+    if constexpr (sizeof(T) == 8) return SpC<T>{T(-tab.qm[s]), T(tab.qm[s]), T(tab.q[s])};
+    else return SpC<T>{-tab.fqm[s], tab.fqm[s], tab.fq[s]};
+  } else {
+    return SpC<T>{T(1), T(-1), T(-1)};
+  }
 }
 
 // AB5 combination sum_k beta_k f_{i-k} for component c; history slots hold f_{i-1..i-4}.
@@ -166,12 +187,12 @@ __device__ __forceinline__ void stencil_f64(const Geom& gm, double x, double y, 
   iy0 = shape_weights<P, T>(jy, T(fy), wy);
 }
 
-// q w / A for an electron (q = -1).  FP64 mode divides by A = dx dy as the oracle
-// does; FP32 mode multiplies by the precomputed 1/A.
+// q w / A (an electron: q = -1).  FP64 mode divides by A = dx dy as the oracle does; FP32
+// mode multiplies by the precomputed 1/A.
 template <typename T>
-__device__ __forceinline__ T charge_density(T w, const Geom& gm) {
-  if constexpr (sizeof(T) == 8) return (T(-1.0) * w) / (gm.dx * gm.dy);
-  else return -w * gm.f_inv_area;
+__device__ __forceinline__ T charge_density(T w, const Geom& gm, T q = T(-1)) {
+  if constexpr (sizeof(T) == 8) return (q * w) / (gm.dx * gm.dy);
+  else return q * w * gm.f_inv_area;
 }
 
 // Removal rule (a reading; the paper is silent): finite, inside the open box,
@@ -182,14 +203,28 @@ __device__ __forceinline__ bool state_ok(const Geom& gm, double x, double y, dou
 }
 
 // ---------------------------------------------------------------- init
-template <typename T>
+// Placement of plasma particle p (Sec. 2: unperturbed plasma ahead of the beams): cell-row-major,
+// ppc_x x ppc_y at sub-cell centres, at rest.  A multi-species grid (MS) places each species'
+// block [off[s], off[s + 1]) with that species' particles per cell, profile and density.
+template <typename T, bool MS>
 __global__ void k_plasma_init(Plasma<T> pl, Geom gm, int ppx, int ppy, const double* prof, int npf,
-                              double rmax, double n0s) {
+                              double rmax, double n0s, SpeciesTab tab) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pl.n) return;
+  int64_t lp = p;
+  if constexpr (MS) {
+    const int s = species_of(tab, p);
+    lp = p - tab.off[s];
+    ppx = tab.ppx[s];
+    ppy = tab.ppy[s];
+    prof = tab.prof[s];
+    npf = tab.npf[s];
+    rmax = tab.rmax[s];
+    n0s = tab.n0[s];
+  }
   const int ppc = ppx * ppy;
-  const int64_t c = p / ppc;
-  const int sub = (int)(p - c * ppc);
+  const int64_t c = lp / ppc;
+  const int sub = (int)(lp - c * ppc);
   const int ix = (int)(c % gm.nx), iy = (int)(c / gm.nx);
   const int sx = sub % ppx, sy = sub / ppx;
   const double x = gm.xmin + ((double)ix + ((double)sx + 0.5) / ppx) * gm.dx;
@@ -229,16 +264,23 @@ __global__ void k_plasma_init(Plasma<T> pl, Geom gm, int ppx, int ppy, const dou
   }
 }
 
-// Deposit of the current plasma state (slice 0), or of the ion background
-// rho_ion = -(q w / A) deposited from the initial positions (ion_only).
-template <int P, typename T>
-__global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* rho_ion) {
+// Deposit of the current plasma state (slice 0), or of the immobile background
+// rho_ion = -(q w / A) deposited from the initial positions (ion_only; on a multi-species grid
+// only the species with a neutralizing background).
+template <int P, typename T, bool MS>
+__global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* rho_ion, SpeciesTab tab) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pl.n || !pl.alive[p]) return;
+  int s = 0;
+  if constexpr (MS) {
+    s = species_of(tab, p);
+    if (rho_ion && !tab.neutral[s]) return;
+  }
+  const SpC<T> sc = spc_of<T, MS>(tab, s);
   T wx[P + 1], wy[P + 1];
   int ix0, iy0;
   stencil_f64<P, T>(gm, pl.x[p], pl.y[p], ix0, iy0, wx, wy);
-  const T qw = charge_density<T>(pl.w[p], gm);
+  const T qw = charge_density<T>(pl.w[p], gm, sc.q);
   if (rho_ion) {
 #pragma unroll
     for (int b = 0; b <= P; ++b) {
@@ -259,19 +301,44 @@ __global__ void k_deposit_initial(Plasma<T> pl, Geom gm, V4<T>* dep, T* chi, T* 
   const T gam = (T(1) + ux * ux + uy * uy + opp * opp) * T(0.5) * g;
   const T uz = uz_of<T>(ux, uy, opp, pl.psi[p], g);
   deposit_full<P, T>(dep, chi, gm, ix0, iy0, wx, wy, qw * gam * g, qw * ux * g, qw * uy * g,
-                     qw * uz * g, qw * T(-1) * g);
+                     qw * uz * g, qw * sc.qm * g);
+}
+
+// FP32 multi-species grids: the initial charge of the species without a neutralizing
+// background, sum q w S(x0) / A over their particles, accumulated in FP64 (c0 of the psi source).
+template <int P>
+__global__ void k_species_c0(Plasma<float> pl, Geom gm, double* out, SpeciesTab tab) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pl.n) return;
+  const int s = species_of(tab, p);
+  if (tab.neutral[s]) return;
+  double wx[P + 1], wy[P + 1];
+  int ix0, iy0;
+  stencil_f64<P, double>(gm, pl.x[p], pl.y[p], ix0, iy0, wx, wy);
+  const double qw = tab.q[s] * (double)pl.w[p] * gm.inv_area;
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const int iy = iy0 + b;
+    if (!in_interior(iy, gm.ny)) continue;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      const int ix = ix0 + a;
+      if (in_interior(ix, gm.nx)) atomicAdd(out + (int64_t)iy * gm.nx + ix, wx[a] * wy[b] * qw);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- trial pass (predictor-corrector)
 // Gather with B^(m-1), AB5 trial step to slice i+1, deposit J_perp of the trial
 // particles into tj (Sec. 3.2, predictor-corrector field solver).
-template <int P, typename T, bool CACHE>
+template <int P, typename T, bool CACHE, bool MS>
 __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf, const T* __restrict__ bm,
-                                                         V2<T>* tj, int slice, double guard) {
+                                                         V2<T>* tj, int slice, double guard, SpeciesTab tab) {
   pdl_trigger();
   pdl_wait();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pl.n || !pl.alive[p]) return;
+  const SpC<T> sc = spc_of<T, MS>(tab, MS ? species_of(tab, p) : 0);
   const int64_t n = pl.n;
   T wx[P + 1], wy[P + 1];
   int ix0, iy0;
@@ -294,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
   const T ux = pl.ux[p], uy = pl.uy[p];
   const F6<T> F = gather6<P, T>(gf, bm, gm.nx, gm.ny, ix0, iy0, wx, wy);
   T f[5];
-  derivs<T>(ux, uy, opp, F, f);
+  derivs<T, MS>(ux, uy, opp, F, f, sc.mqm);
   const T dz = CACHE ? T(gm.f_dz) : T(gm.dzeta);
   // AB5 combination beta_0 f_i + sum_{k>=1} beta_k f_{i-k}; FP32 reads the precomputed history part
   auto comb = [&](int c) -> T {
@@ -332,7 +399,7 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
     topp = T(1.0 + tpsi);
     stencil_f64<P, T>(gm, tx, ty, tix0, tiy0, twx, twy);
   }
-  const T qw = charge_density<T>(pl.w[p], gm);
+  const T qw = charge_density<T>(pl.w[p], gm, sc.q);
   const T tg = T(1) / topp;
   deposit_perp<P, T>(tj, gm, tix0, tiy0, twx, twy, qw * tux * tg, qw * tuy * tg);
 }
@@ -546,19 +613,33 @@ template <int P, typename T> constexpr int final_min_blocks() {
   return sizeof(T) == 4 ? 65536 / ((P == 3 ? 64 : 48) * kThreads) : 1;
 }
 
-template <int P, typename T, bool CACHE>
+template <int P, typename T, bool CACHE, bool MS>
 __global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf, const T* __restrict__ bm,
                                                          V4<T>* dep, T* chi, float* ps, PpcInfo pc, int slice,
-                                                         double guard, unsigned long long* removed) {
+                                                         double guard, unsigned long long* removed, SpeciesTab tab) {
   pdl_trigger();
   pdl_wait();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pl.n) return;
+  int sp = 0;
+  int64_t lp = pl.origin ? (int64_t)pl.origin[p] : p;   // index in the initial placement (of its species)
+  if constexpr (MS) {
+    sp = species_of(tab, p);
+    lp = p - tab.off[sp];
+    pc.px = tab.ppx[sp];
+    pc.py = tab.ppy[sp];
+    pc.pow2 = tab.pow2[sp];
+    pc.inv_x = tab.inv_px[sp];
+    pc.inv_y = tab.inv_py[sp];
+    pc.finv_x = tab.finv_px[sp];
+    pc.finv_y = tab.finv_py[sp];
+  }
+  const SpC<T> sc = spc_of<T, MS>(tab, sp);
   Start s0{};
-  if (ps) s0 = start_coord(pl.origin ? (int64_t)pl.origin[p] : p, gm, pc);
+  if (ps) s0 = start_coord(lp, gm, pc);
   if (!pl.alive[p]) {
     if constexpr (sizeof(T) == 4)
-      if (ps) deposit_ion_src<P>(ps, gm, s0, charge_density<T>(pl.w[p], gm));
+      if (ps) deposit_ion_src<P>(ps, gm, s0, charge_density<T>(pl.w[p], gm, sc.q));
     return;
   }
   const int64_t n = pl.n;
@@ -577,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pa
   const T ux = pl.ux[p], uy = pl.uy[p];
   const F6<T> F = gather6<P, T>(gf, bm, gm.nx, gm.ny, ix0, iy0, wx, wy);
   T f[5];
-  derivs<T>(ux, uy, opp, F, f);
+  derivs<T, MS>(ux, uy, opp, F, f, sc.mqm);
   T comb[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
@@ -610,7 +691,7 @@ __global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pa
     pl.alive[p] = 0;
     atomicAdd(removed, 1ull);
     if constexpr (sizeof(T) == 4)
-      if (ps) deposit_ion_src<P>(ps, gm, s0, charge_density<T>(pl.w[p], gm));
+      if (ps) deposit_ion_src<P>(ps, gm, s0, charge_density<T>(pl.w[p], gm, sc.q));
     return;
   }
   pl.x[p] = nxp;
@@ -642,12 +723,12 @@ __global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pa
     topp = T(nopp);
     stencil_f64<P, T>(gm, nxp, nyp, ix0, iy0, wx, wy);
   }
-  const T qw = charge_density<T>(pl.w[p], gm);
+  const T qw = charge_density<T>(pl.w[p], gm, sc.q);
   const T g = T(1) / topp;
   const T gam = (T(1) + nux * nux + nuy * nuy + topp * topp) * T(0.5) * g;
   const T uz = uz_of<T>(nux, nuy, topp, npsi, g);
   deposit_full<P, T>(dep, chi, gm, ix0, iy0, wx, wy, qw * gam * g, qw * nux * g, qw * nuy * g,
-                     qw * uz * g, qw * T(-1) * g);
+                     qw * uz * g, qw * sc.qm * g);
   if constexpr (CACHE)
     if (ps) deposit_psi_src<P>(ps, gm, jx, frx, dfx, jy, fry, dfy, s0, qw);
 }
@@ -660,11 +741,30 @@ inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / k
 
 }  // namespace
 
+// Shape-order and species dispatch of the particle kernels: the default electron plasma runs
+// the MS = false instances (electron constants folded in), multi-species grids MS = true.
+#define HQ_PDISPATCH(ORDER, MULTI, CALL)                                                  \
+  switch ((ORDER) * 2 + ((MULTI) ? 1 : 0)) {                                                \
+    case 0: { constexpr int P = 0; constexpr bool M = false; CALL; } break;                 \
+    case 1: { constexpr int P = 0; constexpr bool M = true; CALL; } break;                  \
+    case 2: { constexpr int P = 1; constexpr bool M = false; CALL; } break;                 \
+    case 3: { constexpr int P = 1; constexpr bool M = true; CALL; } break;                  \
+    case 4: { constexpr int P = 2; constexpr bool M = false; CALL; } break;                 \
+    case 5: { constexpr int P = 2; constexpr bool M = true; CALL; } break;                  \
+    case 6: { constexpr int P = 3; constexpr bool M = false; CALL; } break;                 \
+    default: { constexpr int P = 3; constexpr bool M = true; CALL; } break;                 \
+  }
+
 template <typename T>
 void launch_plasma_init(const hq_grid_s* g, cudaStream_t s) {
-  k_plasma_init<T><<<blocks_for(g->np), kThreads, 0, s>>>(
-      plasma_of<T>(g), g->geom, g->d.ppc_x, g->d.ppc_y, g->profile.empty() ? nullptr : g->d_profile,
-      (int)g->profile.size(), g->d.profile_rmax, g->d.n0_scale);
+  const double* prof = g->profile.empty() ? nullptr : g->d_profile;
+  if (g->multi)
+    k_plasma_init<T, true><<<blocks_for(g->np), kThreads, 0, s>>>(plasma_of<T>(g), g->geom, 1, 1, nullptr, 0, 0.0,
+                                                                   0.0, g->sp);
+  else
+    k_plasma_init<T, false><<<blocks_for(g->np), kThreads, 0, s>>>(
+        plasma_of<T>(g), g->geom, g->d.ppc_x, g->d.ppc_y, prof, (int)g->profile.size(), g->d.profile_rmax,
+        g->d.n0_scale, g->sp);
 }
 
 template <typename T>
@@ -673,11 +773,17 @@ void launch_deposit_initial(const hq_grid_s* g, void* dep, void* chi, int ion_on
   V4<T>* d = reinterpret_cast<V4<T>*>(dep);
   T* c = reinterpret_cast<T*>(chi);
   T* ion = ion_only ? reinterpret_cast<T*>(g->rho_ion) : nullptr;
+  HQ_PDISPATCH(g->d.shape_order, g->multi,
+               (k_deposit_initial<P, T, M><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, d, c, ion, g->sp)));
+}
+
+void launch_species_c0(const hq_grid_s* g, double* out, cudaStream_t s) {
+  const unsigned nb = blocks_for(g->np);
   switch (g->d.shape_order) {
-    case 0: k_deposit_initial<0, T><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, d, c, ion); break;
-    case 1: k_deposit_initial<1, T><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, d, c, ion); break;
-    case 2: k_deposit_initial<2, T><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, d, c, ion); break;
-    default: k_deposit_initial<3, T><<<nb, kThreads, 0, s>>>(plasma_of<T>(g), g->geom, d, c, ion); break;
+    case 0: k_species_c0<0><<<nb, kThreads, 0, s>>>(g->p32, g->geom, out, g->sp); break;
+    case 1: k_species_c0<1><<<nb, kThreads, 0, s>>>(g->p32, g->geom, out, g->sp); break;
+    case 2: k_species_c0<2><<<nb, kThreads, 0, s>>>(g->p32, g->geom, out, g->sp); break;
+    default: k_species_c0<3><<<nb, kThreads, 0, s>>>(g->p32, g->geom, out, g->sp); break;
   }
 }
 
@@ -689,12 +795,9 @@ void launch_trial_pass(const hq_grid_s* g, int slice, cudaStream_t s) {
   V2<T>* tj = reinterpret_cast<V2<T>*>(g->tj);
   constexpr bool C = sizeof(T) == 4;
   const double gd = g->d.psi_guard;
-  switch (g->d.shape_order) {
-    case 0: launch_pdl(k_trial_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, tj, slice, gd); break;
-    case 1: launch_pdl(k_trial_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, tj, slice, gd); break;
-    case 2: launch_pdl(k_trial_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, tj, slice, gd); break;
-    default: launch_pdl(k_trial_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, tj, slice, gd); break;
-  }
+  HQ_PDISPATCH(g->d.shape_order, g->multi,
+               (launch_pdl(k_trial_pass<P, T, C, M>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, tj, slice,
+                           gd, g->sp)));
 }
 
 template <typename T>
@@ -716,13 +819,11 @@ void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cuda
   pc.inv_y = 1.0 / pc.py;
   pc.finv_x = (float)pc.inv_x;
   pc.finv_y = (float)pc.inv_y;
-  switch (g->d.shape_order) {
-    case 0: launch_pdl(k_final_pass<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, d, c, ps, pc, slice, gd, rm); break;
-    case 1: launch_pdl(k_final_pass<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, d, c, ps, pc, slice, gd, rm); break;
-    case 2: launch_pdl(k_final_pass<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, d, c, ps, pc, slice, gd, rm); break;
-    default: launch_pdl(k_final_pass<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, d, c, ps, pc, slice, gd, rm); break;
-  }
+  HQ_PDISPATCH(g->d.shape_order, g->multi,
+               (launch_pdl(k_final_pass<P, T, C, M>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, d, c, ps, pc,
+                           slice, gd, rm, g->sp)));
 }
+#undef HQ_PDISPATCH
 
 template void launch_plasma_init<float>(const hq_grid_s*, cudaStream_t);
 template void launch_plasma_init<double>(const hq_grid_s*, cudaStream_t);

@@ -28,6 +28,12 @@ EXPORTS = ("hq_grid_create", "hq_grid_destroy", "hq_advance_slice", "hq_beam_dep
 KERNEL_CLASSES = ("final", "trial", "dst", "field", "beam", "other")
 
 
+class SpeciesDesc(C.Structure):
+    _fields_ = [("charge", C.c_double), ("mass", C.c_double), ("n0_scale", C.c_double),
+                ("ppc_x", C.c_int32), ("ppc_y", C.c_int32), ("radial_profile", C.POINTER(C.c_double)),
+                ("n_profile", C.c_int32), ("profile_rmax", C.c_double), ("neutralize", C.c_int32)]
+
+
 class GridDesc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nzeta", C.c_int32),
                 ("xmin", C.c_double), ("xmax", C.c_double), ("ymin", C.c_double), ("ymax", C.c_double),
@@ -36,7 +42,8 @@ class GridDesc(C.Structure):
                 ("radial_profile", C.POINTER(C.c_double)), ("n_profile", C.c_int32), ("profile_rmax", C.c_double),
                 ("n0_scale", C.c_double), ("n_pc_iter", C.c_int32), ("pc_mix", C.c_double),
                 ("psi_guard", C.c_double), ("precision", C.c_int32), ("bperp_solver", C.c_int32),
-                ("resort_every", C.c_int32), ("deterministic", C.c_int32)]
+                ("resort_every", C.c_int32), ("deterministic", C.c_int32),
+                ("species", C.POINTER(SpeciesDesc)), ("n_species", C.c_int32)]
 
 
 class BeamView(C.Structure):
@@ -159,6 +166,20 @@ class Grid:
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         prof = params.get("radial_profile")
         self._prof = (C.c_double * len(prof))(*prof) if prof is not None else None
+        # plasma species: dicts with charge, mass, n0_scale, ppc_x, ppc_y, radial_profile,
+        # profile_rmax, neutralize (the library copies them)
+        sps = list(params.get("species") or [])
+        self._sp_prof = []
+        self._sp = (SpeciesDesc * max(1, len(sps)))()
+        for k, sp in enumerate(sps):
+            pr = sp.get("radial_profile")
+            arr = (C.c_double * len(pr))(*pr) if pr is not None else None
+            self._sp_prof.append(arr)
+            self._sp[k] = SpeciesDesc(float(sp.get("charge", -1.0)), float(sp.get("mass", 1.0)),
+                                      float(sp.get("n0_scale", 1.0)), int(sp.get("ppc_x", 1)), int(sp.get("ppc_y", 1)),
+                                      C.cast(arr, C.POINTER(C.c_double)) if arr is not None else None,
+                                      len(pr) if pr is not None else 0, float(sp.get("profile_rmax", 0.0)),
+                                      int(bool(sp.get("neutralize", True))))
         d = GridDesc(
             int(params["nx"]), int(params["ny"]), int(params["nzeta"]),
             float(params["xmin"]), float(params["xmax"]), float(params["ymin"]), float(params["ymax"]),
@@ -170,7 +191,8 @@ class Grid:
             float(params.get("psi_guard", 0.02)),
             HQ_PREC_FP64 if precision == "fp64" else HQ_PREC_FP32_BF16X3,
             {"pc": 0, "explicit": 1}[params.get("bperp_solver", "pc")], int(params.get("resort_every", 0)),
-            int(params.get("deterministic", 0)))
+            int(params.get("deterministic", 0)),
+            C.cast(self._sp, C.POINTER(SpeciesDesc)) if sps else None, len(sps))
         self.params = dict(params)
         self.nx, self.ny, self.nzeta = d.nx, d.ny, d.nzeta
         self.stream = stream if stream is not None else torch.cuda.current_stream()

@@ -80,3 +80,37 @@ def test_every_runtime_switch_is_documented():
     assert read, "no switches found"
     for name in sorted(read):
         assert re.search(rf"^\s*\*\s+{name}=", header, re.M), name
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of the C structs have the header's sizes and field offsets (compiled
+    with the host C compiler against include/hq.h)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    from paper_2109_10277_gb300 import hq
+    checks = {"hq_grid_desc": (hq.GridDesc, ("n_pc_iter", "precision", "bperp_solver", "resort_every",
+                                             "deterministic", "species", "n_species")),
+              "hq_species_desc": (hq.SpeciesDesc, ("mass", "ppc_y", "radial_profile", "neutralize")),
+              "hq_beam_view": (hq.BeamView, ("w", "charge", "mass")),
+              "hq_field_out": (hq.FieldOut, ("bz",)),
+              "hq_plasma_view": (hq.PlasmaView, ("alive", "origin"))}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "hq.h")}"',
+             "int main(void) {"]
+    for name, (_, fields) in checks.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    r = subprocess.run([cc, str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    for name, (cls, fields) in checks.items():
+        assert int(got[name]) == C.sizeof(cls), name
+        for f in fields:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
