@@ -318,6 +318,31 @@ def explicit_leg(hq, I, stream, flush, iters=6):
             "witness_sums": [float(v) for v in sums.cpu()]}
 
 
+def species_leg(hq, I, stream, flush, mass=1836.0):
+    """The headline workload with the ions moving: electrons and hydrogen ions (M = 1836 m_e) placed
+    alike, no immobile background (twice the plasma particles, the multi-species kernels)."""
+    import torch
+    sp = [dict(charge=-1.0, mass=1.0, n0_scale=1.0, ppc_x=1, ppc_y=1, neutralize=False),
+          dict(charge=1.0, mass=mass, n0_scale=1.0, ppc_x=1, ppc_y=1, neutralize=False)]
+    g = dict(I.grid_params(WORKLOAD), species=sp)
+    grid = hq.Grid(g, precision="fp32", stream=stream)
+    hb = [hq.Beam(b) for b in I.workload_beams(WORKLOAD)]
+    grid.sweep(hb)
+    grid.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(9)
+    a.record(stream)
+    grid.sweep(hb)
+    b.record(stream)
+    torch.cuda.synchronize()
+    removed = grid.sync()
+    grid.close()
+    ms = a.elapsed_time(b)
+    p = 2 * g["nx"] * g["ny"]
+    return {"workload": f"{WORKLOAD} with mobile hydrogen ions (electrons + ions, 1 ppc each, no background)",
+            "ms_per_step": ms, "value": p * g["nzeta"] / (ms / 1e3), "unit": UNIT, "removed_particles": removed}
+
+
 def precision_leg(hq, I, stream, steps=100, dt=20.0):
     """Witness emittance over many beam time steps, FP32/bf16x3 against the FP64 GPU path (the
     paper's single- vs double-precision study, Sec. 6): a driver and a witness whose centroid
@@ -592,15 +617,27 @@ def run_hq(args):
         b.record(stream)
         torch.cuda.synchronize()
         ms64 = a.elapsed_time(b)
-        fp64 = {"value": p * nz / (ms64 / 1e3), "ms_per_step": ms64,
-                "fp32_speedup": (p * nz * args.steps / (ms / 1e3)) / (p * nz / (ms64 / 1e3))}
         g64.close()
+        # the same sweep in the deterministic FP64 mode (fixed-point deposits, bitwise reproducible)
+        gdet = hq.Grid(dict(g, deterministic=1), precision="fp64", stream=stream)
+        gdet.sweep(hb, witness=0, witness_sums=sums64)
+        gdet.sync()
+        flush.fill_(2)
+        a.record(stream)
+        gdet.sweep(hb, witness=0, witness_sums=sums64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        msdet = a.elapsed_time(b)
+        gdet.close()
+        fp64 = {"value": p * nz / (ms64 / 1e3), "ms_per_step": ms64,
+                "fp32_speedup": (p * nz * args.steps / (ms / 1e3)) / (p * nz / (ms64 / 1e3)),
+                "deterministic_ms_per_step": msdet, "deterministic_over_atomic": msdet / ms64}
 
     adjoint = None
     if not args.no_adjoint and args.precision == "fp32":
         adjoint = adjoint_leg(hq, I, stream, flush)
 
-    cubic = adjoint512 = dstcmp = precision = explicit = None
+    cubic = adjoint512 = dstcmp = precision = explicit = species = None
     if not args.no_extra and args.precision == "fp32" and rank == 0:
         grid.close()
         grid = None
@@ -613,6 +650,7 @@ def run_hq(args):
         dstcmp = dst_comparator(hq, I, stream)
         precision = precision_leg(hq, I, stream, steps=args.precision_steps)
         explicit = explicit_leg(hq, I, stream, flush)
+        species = species_leg(hq, I, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -637,7 +675,8 @@ def run_hq(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
             "gpu_launches": launches_per_sweep * args.steps,
             "fp64": fp64, "adjoint": adjoint, "cubic1024": cubic, "adjoint512": adjoint512,
-            "dst_comparator": dstcmp, "precision_study": precision, "explicit_solver": explicit, "cpu_baseline": cpu,
+            "dst_comparator": dstcmp, "precision_study": precision, "explicit_solver": explicit, "ion_motion": species,
+            "cpu_baseline": cpu,
             "removed_particles": removed,
         }
         print(json.dumps(line), flush=True)
