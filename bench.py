@@ -163,6 +163,16 @@ def oracle_sample(n_slices: int) -> dict:
                       f"full 1e6-particle driver binned), FP64 torch-CPU oracle with the FFT DST-I, {dt:.1f} s"}
 
 
+def bench_config(world: int, nzeta: int = 0) -> dict:
+    """The workload a bench line measures (the same for both arms)."""
+    from paper_2109_10277_gb300 import inputs as I
+    g = I.grid_params(WORKLOAD)
+    nz = nzeta if nzeta > 0 else g["nzeta"]
+    return {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}" + (f" (reduced: the first {nz} slices only)" if nzeta > 0 else ""),
+            "particles_per_slice": g["nx"] * g["ny"] * g["ppc_x"] * g["ppc_y"], "slices": nz,
+            "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MiB write, outside the timed events)"}
+
+
 def run_reference(args):
     import torch
     world, rank, _ = dist_setup("gloo")
@@ -183,7 +193,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "sample_slices_per_step": n},
+            "config": bench_config(args.gpus), "sample_slices_per_step": n,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
                              "sample": res["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -191,10 +201,6 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-# DRAM bytes per launch (ncu, caches flushed before each launch) on the 512^2 workload: the
-# solves as the sweep mixes them (5 two-RHS 32-wide-tile launches to 1 three-RHS one per
-# slice: 4.246 MB and 5.325 MB), the trial and final passes of one slice; the capture
-# commands are recorded with their summaries under profiles/
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of each kernel
 # (profiles/: k_dst_solve_rs R = 2 and R = 3 weighted 5:1 as in a slice, trial and final pass)
 NCU_TRAFFIC = {"dst": (5 * 16.329984e6 + 6.899712e6) / 6, "trial": 21.229568e6, "final": 46.429952e6 + 91.392e3}
@@ -660,14 +666,10 @@ def run_hq(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}" + (
-                           f" (reduced: the first {nz} slices only)" if args.nzeta > 0 else ""),
-                       "precision": "FP32 push/gather/deposit, FP64 x/y/Psi accumulators, bf16x3 tensor-core DST-I"
-                       if args.precision == "fp32" else "FP64 everywhere, FP64 FFT DST-I",
-                       "particles_per_slice": p, "slices": nz, "parallelism": f"replicas x{world}",
-                       "l2": "flushed between steps (256 MiB write, outside the timed events)",
-                       "raw_particle_passes_per_s": value * (1 + g["n_pc_iter"]),
-                       "host_wall_s": t_host},
+            "config": bench_config(world, args.nzeta),
+            "precision": "FP32 push/gather/deposit, FP64 x/y/Psi accumulators, bf16x3 tensor-core DST-I"
+            if args.precision == "fp32" else "FP64 everywhere, FP64 FFT DST-I",
+            "raw_particle_passes_per_s": value * (1 + g["n_pc_iter"]), "host_wall_s": t_host,
             "roofline": roof, "rooflines": roofs,
             "kernel_ms_per_sweep": {k: round(v[0], 3) for k, v in prof.items()},
             "kernel_share": {k: round(v / tot, 4) for k, v in shares.items()},
