@@ -209,6 +209,34 @@ def test_beam_push_and_witness_fp64(hq, solver):
         assert abs(float(s[j]) - r) <= max(1e-12 * abs(r), 30 * abs(rp - r)), j
 
 
+def test_beam_push_fp32(hq):
+    """The FP32/bf16x3 path's beam push (the cubic1024 time steps): the pushed beam phase space
+    and the witness sums against the FP64 oracle, on the adjoint256 box at 64^2 (the folded DST
+    path is not needed; the push reads the FP32 gather and B_perp records).  Bars: every
+    coordinate within 1e-4 of its spread over the beam and within 1e-3 of its largest change
+    in the step (the push's own increment), the witness sums within 1e-4."""
+    g = I.scaled_grid(I.grid_params("adjoint256"), 64, 64, 64)
+    beams = I.workload_beams("adjoint256", grid=g)
+    sp = O.GridSpec(**g)
+    ref = O.sweep(sp, [O.as_beam(b) for b in beams], dt=5.0, witness=(1,), record=())
+    _, _, _, hb, sums = run_gpu(hq, g, beams, "fp32", fields=(), dt=5.0, witness=1)
+    worst = 0.0
+    for bi in range(2):
+        for k in ("x", "y", "zeta", "ux", "uy", "uz"):
+            a = hb[bi].t[k].cpu()
+            b = ref.beams[bi][k]
+            moved = float((b - torch.as_tensor(beams[bi][k])).abs().max()) + 1e-30
+            d = float((a - b).abs().max())
+            scale = float((b - b.mean()).abs().max()) + 1e-30
+            worst = max(worst, d / scale)
+            print(f"fp32 beam push beam {bi} {k}: max dev {d:.2e} of spread {scale:.2e} (moved up to {moved:.2e})")
+            assert d <= 1e-4 * scale and d <= 1e-3 * moved, (bi, k, d, scale, moved)
+    s_ = sums.cpu()
+    for j in range(3):
+        r = float(ref.witness[1][j])
+        assert abs(float(s_[j]) - r) <= 1e-4 * abs(r), (j, float(s_[j]), r)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_witness_sums_without_push(hq, monkeypatch, precision):
     """Without a beam push the sweep sums slice i-1's witness on a second stream beside slice
