@@ -251,6 +251,20 @@ hq_status hq_beam_moments(hq_grid_t grid, const hq_beam_view* beam, double* mome
 hq_status hq_sweep_step(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, double dt,
                         const hq_field_out* out, int32_t witness_beam, double* witness_sums);
 
+/* Slices [slice_begin, slice_end) of a sweep: per slice the steps of hq_sweep_step (advance, beam
+ * deposit, solve, optional store / witness sums / push) with the views `beams`; on the range's
+ * last slice the views `next` (nnext of them; may be NULL with nnext = 0) join the beam
+ * deposit, so that the J_perp of slice slice_end reaches the predictor-corrector.  This is one
+ * box of the Sec. 5.2 temporal pipeline: the box's particles in `beams`, the next box's in
+ * `next` (pass them for the box's last slice only, in a call of its own, to receive them as
+ * late as possible).  slice_begin must be 0 (a new sweep) or the previous call's slice_end;
+ * slice_end <= nzeta, nbeams + nnext <= 4; reaching nzeta advances the plasma once more as
+ * hq_sweep_step does.  Launched from the host slice by slice (no graph replay).  Errors:
+ * HQ_ERR_ARG, HQ_ERR_STATE (out of order), and those of the per-slice calls. */
+hq_status hq_sweep_slices(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, const hq_beam_view* next,
+                          int32_t nnext, int32_t slice_begin, int32_t slice_end, double dt,
+                          const hq_field_out* out, int32_t witness_beam, double* witness_sums);
+
 /* Forward sweep for differentiation (gradients are a goal the paper names, Sec. 1, with
  * no adjoint formulation): the same sweep as hq_sweep_step with dt = 0 and no field output, but
  * it stores a checkpoint (plasma slice with its AB5 history and the field records a

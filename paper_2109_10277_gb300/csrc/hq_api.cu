@@ -1378,6 +1378,44 @@ hq_status hq_sweep_step(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, double
 }
 
 
+hq_status hq_sweep_slices(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, const hq_beam_view* next,
+                          int32_t nnext, int32_t slice_begin, int32_t slice_end, double dt,
+                          const hq_field_out* out, int32_t witness_beam, double* witness_sums) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (nbeams < 0 || nnext < 0 || nbeams + nnext > kMaxBeams || (nnext > 0 && !next))
+    return fail(g, HQ_ERR_ARG, "nbeams + nnext must be 0..4 (next given when nnext > 0)");
+  hq_status st = check_views(g, beams, nbeams);
+  if (st != HQ_OK) return st;
+  if ((st = check_views(g, next, nnext)) != HQ_OK) return st;
+  if (slice_begin < 0 || slice_end > g->nz || slice_begin >= slice_end)
+    return fail(g, HQ_ERR_ARG, "need 0 <= slice_begin < slice_end <= nzeta");
+  if (slice_begin > 0 && g->last_solved != slice_begin - 1)
+    return fail(g, HQ_ERR_STATE, "slice_begin must follow the previous call's slice_end");
+  if (witness_beam >= nbeams || (witness_beam >= 0 && !witness_sums))
+    return fail(g, HQ_ERR_ARG, "witness_beam must index a beam and witness_sums must be given");
+  if (!std::isfinite(dt)) return fail(g, HQ_ERR_ARG, "dt must be finite");
+  hq_beam_view views[kMaxBeams];
+  for (int b = 0; b < nbeams; ++b) views[b] = beams[b];
+  for (int b = 0; b < nnext; ++b) views[nbeams + b] = next[b];
+  for (int i = slice_begin; i < slice_end; ++i) {
+    if ((st = hq_advance_slice(g, i)) != HQ_OK) return st;
+    const int nv = nbeams + (i == slice_end - 1 ? nnext : 0);
+    if ((st = hq_beam_deposit(g, views, nv, i)) != HQ_OK) return st;
+    if ((st = hq_solve_fields(g, i)) != HQ_OK) return st;
+    if (out && (st = hq_store_fields(g, out, i)) != HQ_OK) return st;
+    if (witness_beam >= 0 && (st = hq_witness_accumulate(g, &beams[witness_beam], i, witness_sums)) != HQ_OK)
+      return st;
+    if (dt != 0.0 && nbeams > 0 && (st = hq_push_beams(g, beams, nbeams, i, dt)) != HQ_OK) return st;
+  }
+  if (slice_end == g->nz) {
+    // advance once past the tail so the plasma state matches a completed sweep
+    if (g->fp64) final_pass<double>(g, g->nz - 1, g->nz & 1);
+    else final_pass<float>(g, g->nz - 1, g->nz & 1);
+    g->last_adv = g->nz;
+  }
+  return check_launch(g);
+}
+
 hq_status hq_sweep_forward_ckpt(hq_grid_t g, hq_beam_view* beams, int32_t nbeams, int32_t witness_beam,
                                 double* witness_sums, int32_t ckpt_every) {
   if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");

@@ -24,7 +24,7 @@ EXPORTS = ("hq_grid_create", "hq_grid_destroy", "hq_advance_slice", "hq_beam_dep
            "hq_store_fields", "hq_push_beams", "hq_witness_accumulate", "hq_sweep_step", "hq_poisson_solve",
            "hq_plasma_state", "hq_profile_enable", "hq_profile_read", "hq_sync", "hq_last_error",
            "hq_poisson_solve_static", "hq_sweep_forward_ckpt", "hq_sweep_adjoint", "hq_beam_moments",
-           "hq_beam_slices")
+           "hq_beam_slices", "hq_sweep_slices")
 KERNEL_CLASSES = ("final", "trial", "dst", "field", "beam", "other")
 
 
@@ -97,6 +97,8 @@ def load() -> C.CDLL:
                                  P),
             "hq_beam_moments": (P, C.POINTER(BeamView), P),
             "hq_beam_slices": (P, C.POINTER(BeamView), P),
+            "hq_sweep_slices": (P, C.POINTER(BeamView), C.c_int32, C.POINTER(BeamView), C.c_int32, C.c_int32,
+                                C.c_int32, C.c_double, C.POINTER(FieldOut), C.c_int32, P),
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -256,6 +258,17 @@ class Grid:
         _check(load().hq_sweep_step(self.h, arr, len(beams), float(dt), C.byref(fo) if fo is not None else None,
                                     int(witness), C.c_void_p(_ptr(witness_sums)) if witness_sums is not None else None),
                self.h)
+
+    def sweep_slices(self, beams: Sequence[Beam], begin: int, end: int, next_beams: Sequence[Beam] = (),
+                     dt: float = 0.0, out: Optional[dict] = None, witness: int = -1,
+                     witness_sums: Optional[torch.Tensor] = None) -> None:
+        """Slices [begin, end) of a sweep (hq_sweep_slices): one box of the temporal pipeline."""
+        arr = _beam_array(beams)
+        nxt = _beam_array(next_beams)
+        fo = self._out(out)
+        _check(load().hq_sweep_slices(self.h, arr, len(beams), nxt, len(next_beams), int(begin), int(end), float(dt),
+                                      C.byref(fo) if fo is not None else None, int(witness),
+                                      C.c_void_p(_ptr(witness_sums)) if witness_sums is not None else None), self.h)
 
     def forward_ckpt(self, beams: Sequence[Beam], witness: int, sums: torch.Tensor, ckpt_every: int) -> None:
         """Checkpointed forward sweep (no field output); sums (device float64[3]) += witness sums."""

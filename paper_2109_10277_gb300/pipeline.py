@@ -31,13 +31,16 @@ Readings (the paper gives the loop, not these details):
     exactly.
 
 The compute of a box is an engine (``HqEngine`` runs it on the CUDA library); the transport is
-torch.distributed point-to-point (gloo for CPU tensors, NCCL for CUDA tensors) or, for a single
-rank, an in-process queue.
+torch.distributed point-to-point (gloo for CPU tensors, NCCL for CUDA tensors), an in-process
+queue for a single rank, or, on one GPU, ranks as threads with their own CUDA streams
+(``run_streams``): consecutive time steps then run concurrently on the device, the beam
+handed over through stream events.
 """
 from __future__ import annotations
 
 import bisect
 import collections
+import threading
 from dataclasses import dataclass, field
 from typing import Callable, Dict, List, Optional, Protocol, Sequence
 
@@ -159,6 +162,49 @@ class LocalTransport:
         pass
 
 
+class StreamTransport:
+    """Ranks as threads of one process on one GPU, each with its own CUDA stream (the time steps
+    of the pipeline overlap on the device).  A message carries an event recorded on the sender's
+    stream after its payload was written; the receiver's stream waits on it.  A receive that
+    finds nothing within `timeout` seconds raises (a rank that failed or never sends)."""
+
+    def __init__(self, timeout: float = 600.0):
+        self.cv = threading.Condition()
+        self.q = collections.defaultdict(collections.deque)
+        self.timeout = timeout
+        self.failed = False
+
+    def send(self, dst, tag, counts, payload):
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.current_stream())
+        with self.cv:
+            self.q[tag].append((counts, payload, ev))
+            self.cv.notify_all()
+
+    def recv(self, src, tag, n_species, device):
+        with self.cv:
+            if not self.cv.wait_for(lambda: self.q[tag] or self.failed, timeout=self.timeout):
+                raise RuntimeError(f"pipeline: no message with tag {tag} within {self.timeout} s")
+            if self.failed and not self.q[tag]:
+                raise RuntimeError("pipeline: another rank failed")
+            counts, payload, ev = self.q[tag].popleft()
+        cur = torch.cuda.current_stream()
+        cur.wait_event(ev)
+        # the tensors were allocated on the sender's stream: keep them from being reused there
+        # before this stream has read them
+        counts.record_stream(cur)
+        payload.record_stream(cur)
+        return counts, payload
+
+    def fail(self):
+        with self.cv:
+            self.failed = True
+            self.cv.notify_all()
+
+    def flush(self):
+        pass
+
+
 class DistTransport:
     """torch.distributed point-to-point: non-blocking sends (each tensor kept alive until its send
     completes), blocking receives in the order the sender issued the messages.  The header of a
@@ -210,9 +256,9 @@ class Engine(Protocol):
 
 
 class HqEngine:
-    """Engine on the CUDA library: per slice of the box, hq_advance_slice, hq_beam_deposit (the
-    next box's particles join on the box's last slice), hq_solve_fields, hq_witness_accumulate
-    and hq_push_beams, all queued on the grid's stream."""
+    """Engine on the CUDA library: a box is hq_sweep_slices over its slices (advance, beam deposit,
+    solve, witness sums, push per slice), the next box's particles joining the beam deposit on
+    the box's last slice; everything is queued on the grid's stream."""
 
     def __init__(self, grid, species: Sequence[tuple], dt: float, witness: int = -1):
         from . import hq
@@ -239,20 +285,16 @@ class HqEngine:
 
     def run_box(self, t, k, slices, parts, next_parts):
         beams = [self._beam(s, b) for s, b in enumerate(parts)]
-        last = slices[-1]
-        for i in slices:
-            self.grid.advance(i)
-            views = beams
-            if i == last and i + 1 < self.grid.nzeta:
-                nxt = next_parts()
-                if nxt is not None:
-                    views = beams + [self._beam(s, b) for s, b in enumerate(nxt)]
-            self.grid.beam_deposit(views, i)
-            self.grid.solve(i)
-            if self.witness >= 0:
-                self.grid.witness_accumulate(beams[self.witness], i, self.sums)
-            if self.dt != 0.0:
-                self.grid.push_beams(beams, i, self.dt)
+        first, last = slices[0], slices[-1]
+        w = self.witness
+        sums = self.sums if w >= 0 else None
+        # the box's slices but its last in one library call, then the last one with the next box's
+        # particles (received as late as possible: they are needed for J_perp(i + 1) only there)
+        if last > first:
+            self.grid.sweep_slices(beams, first, last, (), self.dt, witness=w, witness_sums=sums)
+        nxt = next_parts() if last + 1 < self.grid.nzeta else None
+        nb = [self._beam(s, b) for s, b in enumerate(nxt)] if nxt is not None else []
+        self.grid.sweep_slices(beams, last, last + 1, nb, self.dt, witness=w, witness_sums=sums)
         return parts
 
     def end_step(self, t):
@@ -354,6 +396,42 @@ def run_rank(engine: Engine, plan: Plan, rank: int, transport: Transport,
             res.final = final
     transport.flush()
     return res
+
+
+def run_streams(make_engine: Callable[[int, object], Engine], plan: Plan,
+                initial: Sequence[Bunch]) -> List[RankResult]:
+    """The pipeline on one GPU: plan.world ranks as threads, rank r on its own CUDA stream with
+    the engine make_engine(r, stream) (e.g. an HqEngine over a grid created on that stream), so
+    consecutive time steps run concurrently, one box (plus a slice) apart.  `initial` (on the
+    GPU) seeds step 0.  Returns the ranks' results (rank order); re-raises a rank's error."""
+    transport = StreamTransport()
+    results: List[Optional[RankResult]] = [None] * plan.world
+    errors: List[BaseException] = []
+    device = torch.cuda.current_device()
+    ready = torch.cuda.Event()
+    ready.record(torch.cuda.current_stream())
+
+    def body(rank: int):
+        try:
+            torch.cuda.set_device(device)
+            stream = torch.cuda.Stream()
+            stream.wait_event(ready)
+            with torch.cuda.stream(stream):
+                eng = make_engine(rank, stream)
+                results[rank] = run_rank(eng, plan, rank, transport, initial if rank == 0 else None)
+                stream.synchronize()
+        except BaseException as e:  # noqa: BLE001 - reported to the caller below
+            errors.append(e)
+            transport.fail()
+
+    threads = [threading.Thread(target=body, args=(r,), name=f"pipeline-rank-{r}") for r in range(plan.world)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+    return results
 
 
 def assemble(results: Sequence[RankResult], n_species: int) -> List[Bunch]:

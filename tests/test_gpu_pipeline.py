@@ -113,3 +113,86 @@ def test_pipeline_matches_oracle(hq):
         for j in range(3):
             r, rp = float(rsums[t][j]), float(rpsums[t][j])
             assert abs(float(psums[t][j]) - r) <= max(1e-12 * abs(r), 30 * abs(rp - r)), (t, j)
+
+
+def stream_pipeline(hq, g, beams, world, n_boxes, precision="fp64"):
+    def make(rank, stream):
+        grid = hq.Grid(g, precision=precision, stream=stream)
+        return PL.HqEngine(grid, [(b["charge"], b["mass"]) for b in beams], DT, witness=1)
+    plan = PL.Plan(nzeta=g["nzeta"], n_boxes=n_boxes, n_steps=NSTEP, world=world)
+    res = PL.run_streams(make, plan, [PL.with_ids(b, "cuda") for b in beams])
+    torch.cuda.synchronize()
+    final = PL.assemble(res, 2)
+    diag = {t: d for r in res for t, d in r.diagnostics.items()}
+    return ([{k: v.cpu() for k, v in b.items()} for b in final], [diag[t]["witness_sums"].cpu() for t in range(NSTEP)])
+
+
+@pytest.mark.parametrize("world,n_boxes", [(2, 4), (3, 8)])
+def test_stream_ranks_reproduce_serial_sweeps_bitwise(hq, world, n_boxes):
+    """Time steps pipelined on one GPU (ranks as threads with their own streams), deterministic
+    FP64 mode: the beam after the last step and every step's witness sums are bit for bit those of
+    the serial loop of whole sweeps, although the steps overlap on the device."""
+    g, beams = setup("pc")
+    g = dict(g, deterministic=1)
+    pipe, psums = stream_pipeline(hq, g, beams, world, n_boxes)
+    ser, ssums = gpu_serial(hq, g, beams)
+    for s_ in range(2):
+        assert torch.equal(pipe[s_]["id"], torch.arange(len(beams[s_]["x"])))
+        for k in PL.KEYS:
+            assert torch.equal(pipe[s_][k], ser[s_][k]), (s_, k)
+    for t in range(NSTEP):
+        assert torch.equal(psums[t], ssums[t]), t
+
+
+def test_stream_ranks_fp32(hq):
+    """The same pipelined on one GPU in FP32: within the FP32 run-to-run noise of the serial loop."""
+    g, beams = setup("pc")
+    pipe, psums = stream_pipeline(hq, g, beams, 2, 4, precision="fp32")
+    grid = hq.Grid(g, precision="fp32")
+    hb = [hq.Beam(b) for b in beams]
+    for _ in range(NSTEP):
+        grid.sweep(hb, dt=DT)
+    grid.sync()
+    grid.close()
+    for s_ in range(2):
+        for k in PL.KEYS:
+            ref = hb[s_].t[k].cpu()
+            d = float((pipe[s_][k] - ref).abs().max()) / spread(ref)
+            assert d <= 1e-4, (s_, k, d)
+
+
+def test_sweep_slices_in_chunks_is_the_sweep(hq):
+    """hq_sweep_slices over consecutive ranges equals one hq_sweep_step bit for bit (deterministic
+    FP64): fields of every slice, plasma state after the tail, pushed beams; an out-of-order range
+    is refused with HQ_ERR_STATE."""
+    g, beams = setup("pc")
+    g = dict(g, deterministic=1)
+    outs = []
+    states = []
+    pushed = []
+    for chunks in ([(0, g["nzeta"])], [(0, 10), (10, 11), (11, 23), (23, g["nzeta"])]):
+        grid = hq.Grid(g, precision="fp64")
+        out = grid.alloc_out(("rho", "ez", "psi", "bx", "by"))
+        hb = [hq.Beam(b) for b in beams]
+        if len(chunks) == 1:
+            grid.sweep(hb, dt=DT, out=out)
+        else:
+            for a, b in chunks:
+                grid.sweep_slices(hb, a, b, dt=DT, out=out)
+        grid.sync()
+        outs.append(out)
+        states.append(grid.plasma_state())
+        pushed.append([{k: v.clone() for k, v in b.t.items()} for b in hb])
+        grid.close()
+    for k in outs[0]:
+        assert torch.equal(outs[0][k], outs[1][k]), k
+    for k in ("x", "y", "psi", "ux", "uy", "alive"):
+        assert torch.equal(states[0][k], states[1][k]), k
+    for a, b in zip(pushed[0], pushed[1]):
+        for k in a:
+            assert torch.equal(a[k], b[k]), k
+    grid = hq.Grid(g, precision="fp64")
+    with pytest.raises(hq.HQError) as e:
+        grid.sweep_slices([hq.Beam(beams[0])], 5, 8)
+    assert e.value.status == 6
+    grid.close()
