@@ -113,8 +113,9 @@ typedef struct {
                                        == 0 the plasma slice is re-sorted by cell (stable
                                        counting sort, Sec. 3.1); 0: never.  Refused by
                                        hq_sweep_forward_ckpt (HQ_ERR_UNSUPPORTED)          */
-  int32_t deterministic;            /* 1 (FP64 precision, predictor-corrector solver only):
-                                       every plasma and beam deposit and the witness sums
+  int32_t deterministic;            /* 1 (FP64 precision): every plasma and beam deposit
+                                       (with the explicit solver also its source deposits and
+                                       dot products, summed in a fixed order) and the witness sums
                                        accumulate in 64-bit fixed point (resolution 2^-72,
                                        contributions and sums below 2^31 in magnitude, else
                                        HQ_ERR_NUMERIC) with integer atomics, so a sweep's
@@ -127,8 +128,9 @@ typedef struct {
                                        (species s from sum_{t<s} nx ny ppc_t on); with
                                        species the grid's ppc_x, ppc_y, radial_profile,
                                        profile_rmax and n0_scale do not place the plasma.
-                                       Not with the explicit solver, the re-sort or the
-                                       checkpointed forward (HQ_ERR_UNSUPPORTED)           */
+                                       Not with the re-sort or the checkpointed forward
+                                       (HQ_ERR_UNSUPPORTED); the explicit solver's
+                                       preconditioner shift is then sum q^2 n0_scale / M  */
   int32_t n_species;                /* 0: the default electrons (q = -1, M = 1) over
                                        immobile ions, placed by the fields above          */
 } hq_grid_desc;
@@ -140,8 +142,9 @@ typedef struct {
  * sum q^2 w S / (M (1+Psi) A) and T the B-independent part of d(J_perp)/d(zeta) (plasma:
  * deposited force and convective terms; beams: central differences of their slice
  * deposits); it is solved by n_pc_iter preconditioned conjugate-gradient iterations
- * (preconditioner (c - L)^{-1}, c = n0_scale, one shifted DST-I solve each) from the guess
- * 2 B(i-1) - B(i-2).  The adjoint supports only the predictor-corrector. */
+ * (preconditioner (c - L)^{-1} with c the unperturbed chi: n0_scale, or sum q^2 n0_scale / M
+ * over the plasma species; one shifted DST-I solve each) from the guess 2 B(i-1) - B(i-2).
+ * The adjoint supports only the predictor-corrector. */
 typedef enum { HQ_BPERP_PC = 0, HQ_BPERP_EXPLICIT = 1 } hq_bperp_solver;
 
 /* One beam species, structure of arrays in DEVICE memory (double), n particles.

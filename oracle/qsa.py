@@ -242,6 +242,14 @@ def shifted_solve(spec: GridSpec, s: torch.Tensor, c: float) -> torch.Tensor:
     return (4.0 / (spec.nx * spec.ny)) * dst2(spec, dst2(spec, s) * inv)
 
 
+def explicit_shift(spec: GridSpec) -> float:
+    """The explicit solver's preconditioner shift c: the unperturbed chi, sum q^2 n0 / M over the
+    plasma species (n0_scale for the default electrons)."""
+    if not spec.species:
+        return spec.n0_scale
+    return sum(s.charge * s.charge * s.n0_scale / s.mass for s in spec.species)
+
+
 def helmholtz_pcg(spec: GridSpec, chi: torch.Tensor, rhs: Sequence[torch.Tensor], x0: Sequence[torch.Tensor],
                   c: float, iters: int):
     """Solve (L - chi) B = rhs for each right-hand side: preconditioned conjugate gradients on
@@ -731,7 +739,7 @@ class SliceLoop:
             fx, fy, jxx, jxy, jyy = self.noisy(_sum_species(parts))
             tx = fx + ddx(spec, jxx) + ddy(spec, jxy) + (self.bj_prev[0] - njx) / (2.0 * dz)
             ty = fy + ddx(spec, jxy) + ddy(spec, jyy) + (self.bj_prev[1] - njy) / (2.0 * dz)
-            (bx, by), rr = helmholtz_pcg(spec, chi, (sbx0 + ty, sby0 - tx), (bx, by), spec.n0_scale,
+            (bx, by), rr = helmholtz_pcg(spec, chi, (sbx0 + ty, sby0 - tx), (bx, by), explicit_shift(spec),
                                          spec.n_pc_iter)
             resid = max(rr)
         for _m in range(spec.n_pc_iter if spec.bperp_solver == "pc" else 0):

@@ -58,6 +58,7 @@ void free_all(hq_grid_s* g) {
   if (g->det_arena) {
     // the deposit records are carved from the arena
     g->dep[0] = g->dep[1] = g->chi[0] = g->chi[1] = g->rho_ion = g->tj = g->bjn = nullptr;
+    g->xs4 = g->xs1 = g->bjp = nullptr;
     F(g->det_arena);
     F(g->det_mirror);
   }
@@ -67,6 +68,7 @@ void free_all(hq_grid_s* g) {
   F(g->sort_scratch);
   for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); F(g->psrc[i]); }
   F(g->rho_ion); F(g->tj); F(g->bjn); F(g->bjp); F(g->xs4); F(g->xs1); F(g->pcg_r); F(g->pcg_p); F(g->pcg_s);
+  F(g->pcg_part);
   F(g->scale_h); F(g->gf); F(g->bm); F(g->psi); F(g->bprev1); F(g->solved);
   F(g->f64_a); F(g->f64_b); F(g->f64_scale); F(g->tw_x); F(g->tw_y); F(g->sin_x); F(g->sin_y);
   F(g->sx_hi); F(g->sx_lo); F(g->sy_hi); F(g->sy_lo); F(g->f32_scale);
@@ -277,6 +279,10 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
     // explicit B_perp solver: source pass, then npc PCG iterations from the guess in bm
     const void* chi_cur = g->chi[slice & 1];
     { Prof p(g, HQ_K_TRIAL, 1); launch_explicit_src<T>(g, s); }
+    if (g->det) {
+      launch_fx_decode(g, g->xs4, 4 * g->nnode, nullptr, s);
+      launch_fx_decode(g, g->xs1, g->nnode, nullptr, s);
+    }
     { Prof p(g, HQ_K_FIELD, 1); launch_pcg_init<T>(g, slice, cur, chi_cur, prev, chi_prev, s); }
     for (int k = 0; k < npc; ++k) {
       {
@@ -520,6 +526,7 @@ hq_status beam_deposit_impl(hq_grid_s* g, const hq_beam_view* beams, int nb, int
   if (g->det) {
     launch_fx_decode(g, g->dep[slice & 1], 4 * g->nnode, nullptr, s);
     launch_fx_decode(g, g->bjn, 2 * g->nnode, nullptr, s);
+    if (g->bjp) launch_fx_decode(g, bjp_at(g, slice), 2 * g->nnode, nullptr, s);
   }
   return HQ_OK;
 }
@@ -810,14 +817,21 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     return fail(nullptr, HQ_ERR_ARG, "unknown bperp_solver");
   if (d.bperp_solver == HQ_BPERP_EXPLICIT && (d.n_pc_iter < 1 || d.n_pc_iter > kMaxPcg))
     return fail(nullptr, HQ_ERR_ARG, "the explicit B_perp solver needs 1..64 iterations (n_pc_iter)");
-  if (d.bperp_solver == HQ_BPERP_EXPLICIT && !(d.n0_scale > 0.0))
-    return fail(nullptr, HQ_ERR_ARG, "the explicit B_perp solver needs n0_scale > 0 (its preconditioner shift)");
+  // the explicit solver's preconditioner shift: the unperturbed chi, n0_scale for the default
+  // electrons, sum q^2 n0 / M over the species otherwise
+  double xshift = d.n0_scale;
+  if (d.n_species > 0 && d.species) {
+    xshift = 0.0;
+    for (int k = 0; k < d.n_species && k < kMaxSpecies; ++k)
+      xshift += d.species[k].charge * d.species[k].charge * d.species[k].n0_scale / d.species[k].mass;
+  }
+  if (d.bperp_solver == HQ_BPERP_EXPLICIT && !(xshift > 0.0 && std::isfinite(xshift)))
+    return fail(nullptr, HQ_ERR_ARG, "the explicit B_perp solver needs a positive preconditioner shift "
+                                     "(n0_scale, or sum q^2 n0 / M over the species)");
   if (d.resort_every < 0) return fail(nullptr, HQ_ERR_ARG, "resort_every must be >= 0");
   if (d.deterministic != 0 && d.deterministic != 1) return fail(nullptr, HQ_ERR_ARG, "deterministic must be 0 or 1");
   if (d.deterministic && d.precision != HQ_PREC_FP64)
     return fail(nullptr, HQ_ERR_UNSUPPORTED, "deterministic accumulation is an FP64 mode");
-  if (d.deterministic && d.bperp_solver != HQ_BPERP_PC)
-    return fail(nullptr, HQ_ERR_UNSUPPORTED, "deterministic accumulation covers the predictor-corrector solver only");
   if (d.radial_profile && (d.n_profile < 2 || !(d.profile_rmax > 0.0)))
     return fail(nullptr, HQ_ERR_ARG, "radial profile needs n_profile >= 2 and profile_rmax > 0");
   if (d.n_species < 0 || d.n_species > kMaxSpecies || (d.n_species > 0 && !d.species))
@@ -833,8 +847,6 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
       return fail(nullptr, HQ_ERR_ARG, "species radial profile needs n_profile >= 2 and profile_rmax > 0");
     if (sd.neutralize != 0 && sd.neutralize != 1) return fail(nullptr, HQ_ERR_ARG, "species neutralize must be 0 or 1");
   }
-  if (d.n_species > 0 && d.bperp_solver == HQ_BPERP_EXPLICIT)
-    return fail(nullptr, HQ_ERR_UNSUPPORTED, "the explicit B_perp solver takes the default electron plasma only");
   if (d.n_species > 0 && d.resort_every > 0)
     return fail(nullptr, HQ_ERR_UNSUPPORTED, "the plasma re-sort takes the default electron plasma only");
   int64_t np = 0;
@@ -858,6 +870,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   // plasma species: the descriptors and their profiles are copied; the kernels' table gets the
   // device profiles below
   g->multi = d.n_species > 0;
+  g->xshift = xshift;
   g->species.assign(d.species, d.species + d.n_species);
   g->sp_prof.resize(d.n_species);
   for (int k = 0; k < d.n_species; ++k) {
@@ -974,8 +987,11 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   if (g->det) {
     // one arena for the deposit records (and the witness accumulator), one for their
     // fixed-point mirrors at twice the stride: mirror(e) = 2 e + geom.det
+    // (with the explicit solver also its source records xs4, xs1 and the beam J_perp pair bjp)
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t sz[8] = {up(32 * nn), up(32 * nn), up(8 * nn), up(8 * nn), up(8 * nn), up(16 * nn), up(16 * nn), 256};
+    const bool ex = g->explicit_b;
+    const size_t sz[11] = {up(32 * nn), up(32 * nn), up(8 * nn), up(8 * nn), up(8 * nn), up(16 * nn), up(16 * nn), 256,
+                           ex ? up(32 * nn) : 0, ex ? up(8 * nn) : 0, ex ? up(32 * nn) : 0};
     size_t tot = 0;
     for (size_t b : sz) tot += b;
     HQ_ALLOC(g->det_arena, tot);
@@ -983,12 +999,14 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     cudaMemset(g->det_arena, 0, tot);
     cudaMemset(g->det_mirror, 0, 2 * tot);
     char* a = static_cast<char*>(g->det_arena);
-    void** dst[8] = {&g->dep[0], &g->dep[1], &g->chi[0], &g->chi[1], &g->rho_ion, &g->tj, &g->bjn, nullptr};
-    for (int k = 0; k < 8; ++k) {
-      if (dst[k]) *dst[k] = a;
-      else g->det_wsum = reinterpret_cast<double*>(a);
+    void* wsum = nullptr;
+    void** dst[11] = {&g->dep[0], &g->dep[1], &g->chi[0], &g->chi[1], &g->rho_ion, &g->tj, &g->bjn, &wsum,
+                      &g->xs4, &g->xs1, &g->bjp};
+    for (int k = 0; k < 11; ++k) {
+      if (sz[k]) *dst[k] = a;
       a += sz[k];
     }
+    g->det_wsum = reinterpret_cast<double*>(wsum);
     g->geom.det = (int64_t)reinterpret_cast<uintptr_t>(g->det_mirror) - 2 * (int64_t)reinterpret_cast<uintptr_t>(g->det_arena);
   } else {
     for (int i = 0; i < 2; ++i) { HQ_ALLOC(g->dep[i], 4 * ts * nn); HQ_ALLOC(g->chi[i], ts * nn); }
@@ -1004,9 +1022,15 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   HQ_ALLOC(g->gf, kGF * ts * nn);
   HQ_ALLOC(g->bm, 2 * ts * nn);
   if (g->explicit_b) {
-    HQ_ALLOC(g->bjp, 4 * ts * nn);
-    HQ_ALLOC(g->xs4, 4 * ts * nn);
-    HQ_ALLOC(g->xs1, ts * nn);
+    if (!g->det) {
+      HQ_ALLOC(g->bjp, 4 * ts * nn);
+      HQ_ALLOC(g->xs4, 4 * ts * nn);
+      HQ_ALLOC(g->xs1, ts * nn);
+    } else {
+      // deterministic mode: per-block partial dot products of the PCG
+      const int64_t nb = std::max<int64_t>((nn + 255) / 256, (int64_t)((g->nx + 127) / 128) * g->ny);
+      HQ_ALLOC(g->pcg_part, 16 * nb);
+    }
     HQ_ALLOC(g->pcg_r, 2 * ts * nn);
     HQ_ALLOC(g->pcg_p, 2 * ts * nn);
     HQ_ALLOC(g->pcg_s, sizeof(double) * 4 * kMaxPcg * 2);
@@ -1061,7 +1085,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     HQ_ALLOC(g->f64_scale, 8 * nn);
     cudaMemcpy(g->f64_scale, sc.data(), 8 * nn, cudaMemcpyHostToDevice);
     if (g->explicit_b) {
-      std::vector<double> sh = scale_table(g, g->ny, g->nx, d.n0_scale);
+      std::vector<double> sh = scale_table(g, g->ny, g->nx, g->xshift);
       HQ_ALLOC(g->scale_h, 8 * nn);
       cudaMemcpy(g->scale_h, sh.data(), 8 * nn, cudaMemcpyHostToDevice);
     }
@@ -1138,7 +1162,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     HQ_ALLOC(g->f32_scale, 4 * scf.size());
     cudaMemcpy(g->f32_scale, scf.data(), 4 * scf.size(), cudaMemcpyHostToDevice);
     if (g->explicit_b) {
-      std::vector<double> sh = scale_table(g, g->nyp, g->nxp, d.n0_scale);
+      std::vector<double> sh = scale_table(g, g->nyp, g->nxp, g->xshift);
       for (int sy = 0; sy < g->nyp; ++sy)
         for (int sx = 0; sx < g->nxp; ++sx) {
           const int ky = g->fold ? fold_node(sy, g->ny) : sy, kx = g->fold ? fold_node(sx, g->nx) : sx;

@@ -182,6 +182,7 @@ struct hq_grid_s {
   // the initial charge of the species without a neutralizing background, sum q w S(x0) / A,
   // added to the ion-subtracted psi source (null when every species is neutralized)
   int multi;
+  double xshift;       // explicit B_perp solver: preconditioner shift c (the unperturbed chi)
   hq::SpeciesTab sp;
   std::vector<hq_species_desc> species;
   std::vector<std::vector<double>> sp_prof;
@@ -202,6 +203,7 @@ struct hq_grid_s {
   void* pcg_r;         // V2: residual r
   void* pcg_p;         // V2: search direction p
   double* pcg_s;       // [4][kMaxPcg][2]: r.z, p.Ap per iteration and right-hand side
+  double* pcg_part;    // deterministic mode: per-block partial dot products (else null)
   void* scale_h;       // the preconditioner's spectral factors 1/(lambda - c), like f32_scale / f64_scale
   void* gf;            // kGF per node (gather fields ExmBy, EypBx, Ez, Bz of the current slice)
   void* bm;            // V2: Bx, By of the current slice (the predictor-corrector iterate, then converged);

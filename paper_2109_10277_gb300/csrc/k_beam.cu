@@ -140,8 +140,8 @@ __global__ void k_beam_deposit(hq_beam_view v, const int32_t* __restrict__ off, 
           dadd(&q->d, s * cz, gm);
           if (ps) atomicAdd(ps + node, float(s) * omvz);
           if (bjc) {
-            atomicAdd(&bjc[node].a, s * cx);
-            atomicAdd(&bjc[node].b, s * cy);
+            dadd(&bjc[node].a, s * cx, gm);
+            dadd(&bjc[node].b, s * cy, gm);
           }
         } else {
           V2<T>* q = bjn + node;

@@ -30,13 +30,17 @@ constexpr int kThreads = 128;
 // Fx = a (g Gx - ux g^2 Psi'), Gx = -(q/M)(gamma g ExmBy + Bz g uy),
 // Fy = a (g Gy - uy g^2 Psi'), Gy = -(q/M)(gamma g EypBx - Bz g ux),
 // Jxx = a g^2 ux^2, Jxy = a g^2 ux uy, Jyy = a g^2 uy^2, deposited with the particle's shape.
-template <int P, typename T, bool CACHE>
+// Written for electrons (q = -1, q/M = -1); a multi-species grid (MS) takes each particle's
+// species constants.
+template <int P, typename T, bool CACHE, bool MS>
 __global__ void __launch_bounds__(kThreads) k_explicit_src(Plasma<T> pl, Geom gm, const T* __restrict__ gf,
-                                                           V4<T>* xs4, T* xs1) {
+                                                           V4<T>* xs4, T* xs1, SpeciesTab tab) {
   pdl_trigger();
   pdl_wait();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pl.n || !pl.alive[p]) return;
+  int sp = 0;
+  if constexpr (MS) sp = species_of(tab, p);
   T wx[P + 1], wy[P + 1];
   int ix0, iy0;
   T opp;
@@ -72,11 +76,21 @@ __global__ void __launch_bounds__(kThreads) k_explicit_src(Plasma<T> pl, Geom gm
   const T ux = pl.ux[p], uy = pl.uy[p];
   const T g = T(1) / opp;
   const T gam = (T(1) + ux * ux + uy * uy + opp * opp) * T(0.5) * g;
-  // electrons: q = -1, q/M = -1
-  const T a = sizeof(T) == 8 ? T((-1.0 * (double)pl.w[p]) / (gm.dx * gm.dy)) : -pl.w[p] * gm.f_inv_area;
-  const T dpsi = g * (ux * E[0] + uy * E[1]) - E[2];
-  const T gx = gam * g * E[0] + E[3] * g * uy;
-  const T gy = gam * g * E[1] - E[3] * g * ux;
+  // electrons: q = -1, q/M = -1; other species: a = q w / A and the rates scaled by -q/M
+  T a, dpsi, gx, gy;
+  if constexpr (MS) {
+    const T q = sizeof(T) == 8 ? T(tab.q[sp]) : T(tab.fq[sp]);
+    const T mqm = sizeof(T) == 8 ? T(-tab.qm[sp]) : T(-tab.fqm[sp]);
+    a = sizeof(T) == 8 ? T((tab.q[sp] * (double)pl.w[p]) / (gm.dx * gm.dy)) : q * pl.w[p] * gm.f_inv_area;
+    dpsi = mqm * (g * (ux * E[0] + uy * E[1]) - E[2]);
+    gx = mqm * (gam * g * E[0] + E[3] * g * uy);
+    gy = mqm * (gam * g * E[1] - E[3] * g * ux);
+  } else {
+    a = sizeof(T) == 8 ? T((-1.0 * (double)pl.w[p]) / (gm.dx * gm.dy)) : -pl.w[p] * gm.f_inv_area;
+    dpsi = g * (ux * E[0] + uy * E[1]) - E[2];
+    gx = gam * g * E[0] + E[3] * g * uy;
+    gy = gam * g * E[1] - E[3] * g * ux;
+  }
   const T g2 = g * g;
   const T fx = a * (g * gx - ux * g2 * dpsi), fy = a * (g * gy - uy * g2 * dpsi);
   const T jxx = a * g2 * ux * ux, jxy = a * g2 * ux * uy, jyy = a * g2 * uy * uy;
@@ -94,12 +108,12 @@ __global__ void __launch_bounds__(kThreads) k_explicit_src(Plasma<T> pl, Geom gm
       if constexpr (sizeof(T) == 4) {
         atomicAdd(reinterpret_cast<float4*>(q), make_float4(w * fx, w * fy, w * jxx, w * jyy));
       } else {
-        atomicAdd(&q->a, w * fx);
-        atomicAdd(&q->b, w * fy);
-        atomicAdd(&q->c, w * jxx);
-        atomicAdd(&q->d, w * jyy);
+        dadd(&q->a, w * fx, gm);
+        dadd(&q->b, w * fy, gm);
+        dadd(&q->c, w * jxx, gm);
+        dadd(&q->d, w * jyy, gm);
       }
-      atomicAdd(xs1 + node, w * jxy);
+      dadd(xs1 + node, w * jxy, gm);
     }
   }
 }
@@ -127,7 +141,9 @@ __device__ __forceinline__ V2<T> apply_A(const V2<T>* __restrict__ v, const T* _
 }
 
 // Block sum of two FP64 values, one atomic per block and value.
-__device__ __forceinline__ void block_sum2(double a, double b, double* out) {
+// Block sum of two FP64 values: one atomic per block and value into out, or (part non-null:
+// deterministic FP64 mode) the block's pair stored at part[2 * block] for k_ordered_sum2.
+__device__ __forceinline__ void block_sum2(double a, double b, double* out, double* part_out = nullptr) {
   __shared__ double part[2][32];
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
@@ -142,8 +158,32 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* out) {
   if (threadIdx.x < 2) {
     double t = 0.0;
     for (int k = 0; k < nw; ++k) t += part[threadIdx.x][k];
-    if (t != 0.0) atomicAdd(out + threadIdx.x, t);
+    if (part_out) part_out[2 * (blockIdx.y * gridDim.x + blockIdx.x) + threadIdx.x] = t;
+    else if (t != 0.0) atomicAdd(out + threadIdx.x, t);
   }
+}
+
+// out[c] = sum over the nb block pairs of part[2 b + c] in a fixed order (one block of 256
+// threads: strided partial sums in increasing b, then a fixed tree): the deterministic mode's
+// dot products.
+__global__ void k_ordered_sum2(const double* __restrict__ part, int nb, double* out) {
+  __shared__ double red[2][256];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 256) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + h];
+      red[1][threadIdx.x] += red[1][threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 2) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
 // Per-node right-hand side of the two Helmholtz-like equations and the initial residual
@@ -204,7 +244,7 @@ __global__ void k_pcg_init(PcgInit<T> f, Sink sink) {
 // clears the consumed source records.
 template <typename T>
 __global__ void k_pcg_z(const T* __restrict__ solved, const V2<T>* __restrict__ r, double* rz, int64_t nn, int first,
-                        V4<T>* xs4, T* xs1, V2<T>* bjp, V2<T>* bjn) {
+                        V4<T>* xs4, T* xs1, V2<T>* bjp, V2<T>* bjn, double* part) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double a = 0.0, b = 0.0;
   if (o < nn) {
@@ -218,7 +258,7 @@ __global__ void k_pcg_z(const T* __restrict__ solved, const V2<T>* __restrict__ 
       bjn[o] = V2<T>{T(0), T(0)};
     }
   }
-  block_sum2(a, b, rz);
+  block_sum2(a, b, rz, part);
 }
 
 // p = z + beta p, beta = rz[k] / rz[k-1] (0 on the first iteration or a zero denominator).
@@ -236,7 +276,7 @@ __global__ void k_pcg_p(const T* __restrict__ solved, V2<T>* p, const double* __
 
 // pq[k] += p . (A p)
 template <typename T>
-__global__ void k_pcg_q(const V2<T>* __restrict__ p, const T* __restrict__ chi, Geom gm, double* pq) {
+__global__ void k_pcg_q(const V2<T>* __restrict__ p, const T* __restrict__ chi, Geom gm, double* pq, double* part) {
   const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
   double a = 0.0, b = 0.0;
   if (ix < gm.nx && ix > 0 && iy > 0) {
@@ -245,7 +285,7 @@ __global__ void k_pcg_q(const V2<T>* __restrict__ p, const T* __restrict__ chi, 
     a = (double)q.a * (double)ap.a;
     b = (double)q.b * (double)ap.b;
   }
-  block_sum2(a, b, pq);
+  block_sum2(a, b, pq, part);
 }
 
 // x += alpha p, r -= alpha A p with alpha = rz[k] / pq[k] (0 for a zero denominator); the new r
@@ -297,12 +337,17 @@ void launch_explicit_src(const hq_grid_s* g, cudaStream_t s) {
   V4<T>* xs4 = reinterpret_cast<V4<T>*>(g->xs4);
   T* xs1 = reinterpret_cast<T*>(g->xs1);
   constexpr bool C = sizeof(T) == 4;
+  const SpeciesTab& t = g->sp;
+#define HQ_XS(P)                                                                                          \
+  (g->multi ? launch_pdl(k_explicit_src<P, T, C, true>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, xs4, xs1, t) \
+            : launch_pdl(k_explicit_src<P, T, C, false>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, xs4, xs1, t))
   switch (g->d.shape_order) {
-    case 0: launch_pdl(k_explicit_src<0, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, xs4, xs1); break;
-    case 1: launch_pdl(k_explicit_src<1, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, xs4, xs1); break;
-    case 2: launch_pdl(k_explicit_src<2, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, xs4, xs1); break;
-    default: launch_pdl(k_explicit_src<3, T, C>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, xs4, xs1); break;
+    case 0: HQ_XS(0); break;
+    case 1: HQ_XS(1); break;
+    case 2: HQ_XS(2); break;
+    default: HQ_XS(3); break;
   }
+#undef HQ_XS
 }
 
 template <typename T>
@@ -325,13 +370,16 @@ void launch_pcg_iter(const hq_grid_s* g, int slice, int k, const void* chi_cur, 
   const T* chi = reinterpret_cast<const T*>(chi_cur);
   V2<T>* r = reinterpret_cast<V2<T>*>(g->pcg_r);
   V2<T>* p = reinterpret_cast<V2<T>*>(g->pcg_p);
-  k_pcg_z<T><<<blocks_for(nn, 256), 256, 0, s>>>(solved, r, pcg_at(g, 0, k), nn, k == 0,
-                                                 reinterpret_cast<V4<T>*>(g->xs4), reinterpret_cast<T*>(g->xs1),
-                                                 reinterpret_cast<V2<T>*>(bjp_at(g, slice + 1)),
-                                                 reinterpret_cast<V2<T>*>(g->bjn));
+  double* part = g->pcg_part;   // deterministic mode: per-block partial dot products
+  const unsigned nbz = blocks_for(nn, 256);
+  k_pcg_z<T><<<nbz, 256, 0, s>>>(solved, r, pcg_at(g, 0, k), nn, k == 0, reinterpret_cast<V4<T>*>(g->xs4),
+                                 reinterpret_cast<T*>(g->xs1), reinterpret_cast<V2<T>*>(bjp_at(g, slice + 1)),
+                                 reinterpret_cast<V2<T>*>(g->bjn), part);
+  if (part) k_ordered_sum2<<<1, 256, 0, s>>>(part, (int)nbz, pcg_at(g, 0, k));
   k_pcg_p<T><<<blocks_for(nn, 256), 256, 0, s>>>(solved, p, pcg_at(g, 0, k), k > 0 ? pcg_at(g, 0, k - 1) : nullptr, nn);
   const dim3 g2((unsigned)((g->nx + 127) / 128), (unsigned)g->ny);
-  k_pcg_q<T><<<g2, 128, 0, s>>>(p, chi, g->geom, pcg_at(g, 1, k));
+  k_pcg_q<T><<<g2, 128, 0, s>>>(p, chi, g->geom, pcg_at(g, 1, k), part);
+  if (part) k_ordered_sum2<<<1, 256, 0, s>>>(part, (int)(g2.x * g2.y), pcg_at(g, 1, k));
   PcgStep<T> f{p, chi, reinterpret_cast<V2<T>*>(g->bm), r, pcg_at(g, 0, k), pcg_at(g, 1, k), g->geom};
   with_sink<T>(g, [&](auto sink) { k_pcg_x<T, decltype(sink)><<<src_grid(g), 128, 0, s>>>(f, sink); });
 }

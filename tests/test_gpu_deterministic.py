@@ -5,8 +5,9 @@ GPU performs the additions no longer shows in the result.
 Checked: two sweeps on separate grids give bitwise identical fields on every slice, plasma
 state, witness sums and pushed beams; the mode meets the oracle at the FP64 bars of the atomic
 path (10x the oracle's own rounding floor per field and slice, 30x for the plasma state); an
-out-of-range contribution is reported as HQ_ERR_NUMERIC by hq_sync; FP32, the explicit solver
-and the checkpointed forward refuse the mode.
+out-of-range contribution is reported as HQ_ERR_NUMERIC by hq_sync; with the explicit solver
+too (its source deposits in fixed point, its dot products in a fixed order) two runs agree bit
+for bit; FP32 and the checkpointed forward refuse the mode.
 """
 import numpy as np
 import pytest
@@ -65,6 +66,25 @@ def test_deterministic_sweeps_are_bitwise_identical(hq):
     print(f"atomic FP64 path: {diff} field values differ between two runs; deterministic mode: 0")
 
 
+def test_deterministic_explicit_solver(hq):
+    """The explicit B_perp solver in the deterministic mode (its source deposits in fixed point, its
+    dot products summed in a fixed order): two runs bitwise equal, and the oracle's bars."""
+    g, beams = setup()
+    g = dict(g, bperp_solver="explicit", n_pc_iter=4)
+    a = run(hq, g, beams)
+    b = run(hq, g, beams)
+    for k in O.FIELD_NAMES:
+        assert torch.equal(a[0][k], b[0][k]), k
+    for ba, bb in zip(a[3], b[3]):
+        for k in ba:
+            assert torch.equal(ba[k], bb[k]), k
+    sp = O.GridSpec(**{k: v for k, v in g.items() if k != "deterministic"})
+    ref = O.sweep(sp, [O.as_beam(x) for x in beams], dt=5.0, witness=(1,))
+    ref_perm = O.sweep(sp, [O.as_beam(x) for x in reordered(beams)], dt=5.0, witness=(1,),
+                       plasma_perm=plasma_perm(g), reverse_ion_order=True, deposit_noise=2.0 ** -52)
+    assert_fp64_sweep(a[0], ref, ref_perm, O.FIELD_NAMES, spec=sp)
+
+
 def test_deterministic_matches_oracle(hq):
     g, beams = setup()
     sp = O.GridSpec(**{k: v for k, v in g.items() if k != "deterministic"})
@@ -114,9 +134,6 @@ def test_deterministic_refusals(hq):
     g, beams = setup()
     with pytest.raises(hq.HQError) as e:
         hq.Grid(g, precision="fp32")
-    assert e.value.status == 7
-    with pytest.raises(hq.HQError) as e:
-        hq.Grid(dict(g, bperp_solver="explicit", n_pc_iter=4), precision="fp64")
     assert e.value.status == 7
     grid = hq.Grid(g, precision="fp64")
     sums = torch.zeros(3, dtype=torch.float64, device="cuda")

@@ -99,6 +99,29 @@ def test_species_fp32_matches_oracle(hq, case):
     assert axis <= 1e-4 and max(errs.values()) <= 1e-3, (errs, axis)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_species_explicit_solver(hq, precision):
+    """The explicit B_perp solver on electrons with mobile ions (each species' sources, the shift
+    sum q^2 n0 / M) against the oracle: FP64 at the floor-based bars, FP32 at the FP32 bars."""
+    g = dict(nx=64, ny=64, nzeta=32, xmin=-6.0, xmax=6.0, ymin=-6.0, ymax=6.0, zeta_min=-4.0, zeta_max=2.0,
+             shape_order=1, n_pc_iter=4, pc_mix=0.05, psi_guard=0.02, bperp_solver="explicit",
+             species=CASES["electrons+ions"])
+    beams = [I.random_beam(20_000, 0.5, 0.5, 0.8, 0.5, energy_spread=1e-3)]
+    sp = spec_of(g, CASES["electrons+ions"])
+    ref = O.sweep(sp, [O.as_beam(b) for b in beams])
+    out, _, _ = run(hq, g, beams, precision, O.FIELD_NAMES)
+    if precision == "fp64":
+        perm = torch.as_tensor(np.random.default_rng(2).permutation(g["nx"] * g["ny"]))
+        ref_perm = O.sweep(sp, [O.as_beam(b) for b in reordered(beams)], plasma_perm=perm,
+                           reverse_ion_order=True, deposit_noise=2.0 ** -52)
+        assert_fp64_sweep(out, ref, ref_perm, O.FIELD_NAMES, spec=sp)
+    else:
+        errs = {k: rel(out[k], ref.fields[k]) for k in ("ez", "psi", "bx", "by")}
+        axis = rel(out["ez"][:, 32, 32], ref.fields["ez"][:, 32, 32])
+        print(f"fp32 explicit electrons+ions: on-axis Ez {axis:.2e}, rel-L2 {errs}")
+        assert axis <= 1e-4 and max(errs.values()) <= 1e-3, (errs, axis)
+
+
 def test_species_initial_placement(hq):
     """Each species block of the slice starts where the oracle places that species."""
     g = dict(nx=16, ny=16, nzeta=1, xmin=-2.0, xmax=2.0, ymin=-2.0, ymax=2.0, zeta_min=-1.0, zeta_max=0.0,
@@ -116,10 +139,9 @@ def test_species_initial_placement(hq):
 def test_species_refusals(hq):
     g = dict(nx=16, ny=16, nzeta=4, xmin=-2.0, xmax=2.0, ymin=-2.0, ymax=2.0, zeta_min=-1.0, zeta_max=0.0,
              shape_order=1, n_pc_iter=2, species=CASES["electrons+ions"])
-    for extra in (dict(bperp_solver="explicit"), dict(resort_every=4)):
-        with pytest.raises(hq.HQError) as e:
-            hq.Grid(dict(g, **extra), precision="fp64")
-        assert e.value.status == 7
+    with pytest.raises(hq.HQError) as e:
+        hq.Grid(dict(g, resort_every=4), precision="fp64")
+    assert e.value.status == 7
     with pytest.raises(hq.HQError) as e:
         hq.Grid(dict(g, species=[dict(ELE, mass=0.0)]), precision="fp64")
     assert e.value.status == 1
