@@ -230,6 +230,13 @@ hq_status hq_push_beams(hq_grid_t grid, hq_beam_view* beams, int32_t nbeams, int
  * `beam` (Ez gathered with the grid's shape) to sums[0..2] (DEVICE double[3]). */
 hq_status hq_witness_accumulate(hq_grid_t grid, const hq_beam_view* beam, int32_t slice, double* sums);
 
+/* Sec. 3.2 (predictor-corrector): the relative change of B_perp in the last iteration of each
+ * slice of the last sweep, ||B_m - B_m-1|| / ||B_m|| over both components and every node (the
+ * mixing's own residual; 0 for a slice with no iteration, or with the explicit solver, which has
+ * no mixing), written to out[0..n) (HOST doubles; entries past nzeta are 0).  Synchronizes the
+ * grid's stream.  Errors: HQ_ERR_ARG. */
+hq_status hq_pc_residuals(hq_grid_t grid, double* out, int32_t n);
+
 /* Sec. 3.1 (beam particles sorted per slice) and Sec. 5.2 (temporal pipeline: a box's
  * particles are handed to the next time step): writes the slice of every particle of
  * `beam` to slices[0..n) (DEVICE int32[n]) with the arithmetic hq_beam_deposit bins by,

@@ -69,6 +69,7 @@ void free_all(hq_grid_s* g) {
   for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); F(g->psrc[i]); }
   F(g->rho_ion); F(g->tj); F(g->bjn); F(g->bjp); F(g->xs4); F(g->xs1); F(g->pcg_r); F(g->pcg_p); F(g->pcg_s);
   F(g->pcg_part);
+  F(g->d_pcres);
   F(g->scale_h); F(g->gf); F(g->bm); F(g->psi); F(g->bprev1); F(g->solved);
   F(g->f64_a); F(g->f64_b); F(g->f64_scale); F(g->tw_x); F(g->tw_y); F(g->sin_x); F(g->sin_y);
   F(g->sx_hi); F(g->sx_lo); F(g->sy_hi); F(g->sy_lo); F(g->f32_scale);
@@ -297,6 +298,8 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
   }
   for (int m = 0; m < npc; ++m) {
     const int last = m == npc - 1;
+    // the last iteration's mixing adds its residual sums to this slice's pair
+    g->pc_rsum = last && g->d_pcres ? g->d_pcres + 2 * (int64_t)slice : nullptr;
     tape_b_iterate(g, m);
     { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, s); }
     if (g->det) launch_fx_decode(g, g->tj, 2 * g->nnode, nullptr, s);
@@ -315,6 +318,7 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
       dst_solve_tc_bmix(g, last, s);
     }
   }
+  g->pc_rsum = nullptr;
   if (npc == 0) {
     // no predictor-corrector: B(i) is the guess; clear and reset without the source kernels
     Prof p(g, HQ_K_FIELD, 2);
@@ -355,6 +359,7 @@ void advance_impl(hq_grid_s* g, int slice) {
     launch_zero<T>(g->bjn, 2 * g->nnode, s);
     launch_zero<T>(g->tj, 2 * g->nnode, s);
     if (g->bjp) launch_zero<T>(g->bjp, 4 * g->nnode, s);
+    cudaMemsetAsync(g->d_pcres, 0, sizeof(double) * 2 * g->nz, s);
   } else {
     final_pass<T>(g, slice - 1, slice & 1);
     if (g->d.resort_every > 0 && slice % g->d.resort_every == 0) {
@@ -1043,6 +1048,8 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   HQ_ALLOC(g->bprev1, 2 * ts * nn);
   HQ_ALLOC(g->solved, kMaxRhs * ts * nn);
   HQ_ALLOC(g->d_status, sizeof(int));
+  HQ_ALLOC(g->d_pcres, sizeof(double) * 2 * g->nz);
+  cudaMemset(g->d_pcres, 0, sizeof(double) * 2 * g->nz);
   if (g->det) g->geom.dstatus = g->d_status;   // fixed-point range overflows are reported here
   HQ_ALLOC(g->d_removed, sizeof(unsigned long long));
   for (int b = 0; b < kMaxBeams; ++b) {
@@ -1317,6 +1324,23 @@ hq_status hq_beam_slices(hq_grid_t g, const hq_beam_view* beam, int32_t* slices)
   Prof p(g, HQ_K_BEAM, 1);
   launch_beam_slices(g, *beam, slices, g->stream);
   return check_launch(g);
+}
+
+hq_status hq_pc_residuals(hq_grid_t g, double* out, int32_t n) {
+  if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
+  if (n < 0 || (n > 0 && !out)) return fail(g, HQ_ERR_ARG, "out must hold n >= 0 doubles");
+  HQ_CUDA(g, cudaStreamSynchronize(g->stream));
+  std::vector<double> sums(2 * (size_t)g->nz);
+  HQ_CUDA(g, cudaMemcpy(sums.data(), g->d_pcres, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i) {
+    if (i >= g->nz) {
+      out[i] = 0.0;
+      continue;
+    }
+    const double num = sums[2 * (size_t)i], den = sums[2 * (size_t)i + 1];
+    out[i] = den > 0.0 ? std::sqrt(num / den) : 0.0;
+  }
+  return HQ_OK;
 }
 
 hq_status hq_beam_moments(hq_grid_t g, const hq_beam_view* beam, double* moments) {

@@ -181,6 +181,11 @@ struct hq_grid_s {
   // plasma species (d.n_species > 0: multi = 1 and the particle kernels read sp); FP32: c0 is
   // the initial charge of the species without a neutralizing background, sum q w S(x0) / A,
   // added to the ion-subtracted psi source (null when every species is neutralized)
+  // predictor-corrector residual of each slice of the last sweep (Sec. 3.2): sum (B_m - B_m-1)^2
+  // and sum B_m^2 of the last iteration's mixing, [nzeta][2]; pc_rsum points at the slice's pair
+  // while its last iteration mixes (null otherwise)
+  double* d_pcres;
+  double* pc_rsum;
   int multi;
   double xshift;       // explicit B_perp solver: preconditioner shift c (the unperturbed chi)
   hq::SpeciesTab sp;
@@ -438,6 +443,21 @@ __device__ __forceinline__ void dadd(double* p, double v, const Geom& gm) {
   else atomicAdd(p, v);
 }
 __device__ __forceinline__ void dadd(float* p, float v, const Geom&) { atomicAdd(p, v); }
+
+// Adds a thread's (sum (B_m - B_m-1)^2, sum B_m^2) of the predictor-corrector mixing to rs[0..1]:
+// warp sums, then one FP64 atomic pair per warp (rs null: nothing).  All lanes must call it.
+__device__ __forceinline__ void pc_residual_add(double* rs, double d2, double b2) {
+  if (!rs) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 += __shfl_down_sync(0xffffffffu, d2, o);
+    b2 += __shfl_down_sync(0xffffffffu, b2, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (d2 != 0.0 || b2 != 0.0)) {
+    atomicAdd(rs, d2);
+    atomicAdd(rs + 1, b2);
+  }
+}
 
 // Folded DST-I order (Sec. 3.2 solver).  With S_jk = sin(pi j k / n),
 // S_{n-j,k} = -(-1)^k S_jk: odd k see only x_j + x_{n-j}, even k only x_j - x_{n-j},

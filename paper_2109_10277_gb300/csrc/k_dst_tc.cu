@@ -347,6 +347,7 @@ struct SolveArgs {
   int nx, ny;
   float* bm;                           // mode 3: B <- w B_solved + (1 - w) B in bm[node * 2 + r]
   float w;
+  double* rsum;                        // mode 3: sum (B_new - B_old)^2, sum B_new^2 added here (or null)
   unsigned long long* gbar;            // grid-barrier counter (zero at launch, reset by the last CTA)
   int* status;
   int barrier_skew;                    // added to the first barrier's target (fault injection; 0)
@@ -652,6 +653,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
         const int xn = a.fold ? fold_node(ml, a.nx) : ml;
         float x[CH];
         tmem_ld_pair<BN, CH>(tl + (uint32_t)c0, x);
+        double d2 = 0.0, b2 = 0.0;   // mode 3: this thread's share of the predictor-corrector residual
         if (xn < a.nx) {
           auto ynode = [&](int j) { return a.fold ? fold_node(n0 + c0 + j, a.ny) : n0 + c0 + j; };
           if (mode == 2) {
@@ -678,10 +680,14 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
               const int64_t node = (int64_t)yn * a.nx + xn;
               const float nb = a.w * x[j] + (1.0f - a.w) * old[j];
               a.bm[node * 2 + r] = nb;
+              const double d = (double)nb - (double)old[j];
+              d2 += d * d;
+              b2 += (double)nb * (double)nb;
             }
             if (bad) atomicOr(a.status, DEV_NONFINITE);
           }
         }
+        if (mode == 3) pc_residual_add(a.rsum, d2, b2);   // every lane of the warp (mode is uniform)
       }
       kb_run += nk;
       ++tiles_run;
@@ -848,6 +854,7 @@ __device__ __forceinline__ void rs_mix(const SolveArgs& a, const float* tile, in
   constexpr int LD = BN + 1, NE = BM * BN, UN = NE / kSolveThreads < 16 ? NE / kSolveThreads : 16;
   const int n = a.nx;
   bool bad = false;
+  double d2 = 0.0, b2 = 0.0;
   for (int e0 = threadIdx.x; e0 < NE; e0 += UN * kSolveThreads) {
     float v[UN], old[UN];
     int64_t at[UN];
@@ -863,10 +870,15 @@ __device__ __forceinline__ void rs_mix(const SolveArgs& a, const float* tile, in
     for (int k = 0; k < UN; ++k) {
       if (at[k] < 0) continue;
       bad |= !isfinite(v[k]);
-      a.bm[at[k]] = a.w * v[k] + (1.0f - a.w) * old[k];
+      const float nb = a.w * v[k] + (1.0f - a.w) * old[k];
+      a.bm[at[k]] = nb;
+      const double d = (double)nb - (double)old[k];
+      d2 += d * d;
+      b2 += (double)nb * (double)nb;
     }
   }
   if (bad) atomicOr(a.status, DEV_NONFINITE);
+  pc_residual_add(a.rsum, d2, b2);
 }
 
 template <int BN>
@@ -1191,6 +1203,7 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s, 
   a.ny = g->ny;
   a.bm = reinterpret_cast<float*>(g->bm);
   a.w = (float)g->d.pc_mix;
+  a.rsum = g->pc_rsum;
   a.gbar = g->d_gbar;
   a.status = g->d_status;
   a.barrier_skew = g->fault_barrier;

@@ -85,15 +85,22 @@ __global__ void k_finish_main(const T* __restrict__ res, T* psi, T* gf, V2<T>* b
 
 // B <- w B_solved + (1 - w) B  (predictor-corrector mixing), into bm.
 template <typename T>
-__global__ void k_finish_bperp(const T* __restrict__ res, V2<T>* bm, int64_t nn, T w, int* status) {
+__global__ void k_finish_bperp(const T* __restrict__ res, V2<T>* bm, int64_t nn, T w, int* status, double* rsum) {
   pdl_trigger();
   pdl_wait();
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= nn) return;
-  const T bx = res[o], by = res[nn + o];
-  if (!(isfinite(bx) && isfinite(by))) atomicOr(status, DEV_NONFINITE);
-  const V2<T> b = bm[o];
-  bm[o] = V2<T>{w * bx + (T(1) - w) * b.a, w * by + (T(1) - w) * b.b};
+  double d2 = 0.0, b2 = 0.0;
+  if (o < nn) {
+    const T bx = res[o], by = res[nn + o];
+    if (!(isfinite(bx) && isfinite(by))) atomicOr(status, DEV_NONFINITE);
+    const V2<T> b = bm[o];
+    const V2<T> nb{w * bx + (T(1) - w) * b.a, w * by + (T(1) - w) * b.b};
+    bm[o] = nb;
+    const double dx = (double)nb.a - (double)b.a, dy = (double)nb.b - (double)b.b;
+    d2 = dx * dx + dy * dy;
+    b2 = (double)nb.a * (double)nb.a + (double)nb.b * (double)nb.b;
+  }
+  pc_residual_add(rsum, d2, b2);
 }
 
 template <typename T>
@@ -167,7 +174,7 @@ void launch_finish_main(const hq_grid_s* g, const void* res, int first, cudaStre
 template <typename T>
 void launch_finish_bperp(const hq_grid_s* g, const void* res, cudaStream_t s) {
   launch_pdl(k_finish_bperp<T>, blocks_for(g->nnode), kThreads, 0, s, reinterpret_cast<const T*>(res),
-             reinterpret_cast<V2<T>*>(g->bm), g->nnode, T(g->d.pc_mix), g->d_status);
+             reinterpret_cast<V2<T>*>(g->bm), g->nnode, T(g->d.pc_mix), g->d_status, g->pc_rsum);
 }
 template <typename T>
 void launch_store(const hq_grid_s* g, const hq_field_out* out, int64_t slot, const void* dep, const void* chi, cudaStream_t s) {

@@ -24,7 +24,7 @@ EXPORTS = ("hq_grid_create", "hq_grid_destroy", "hq_advance_slice", "hq_beam_dep
            "hq_store_fields", "hq_push_beams", "hq_witness_accumulate", "hq_sweep_step", "hq_poisson_solve",
            "hq_plasma_state", "hq_profile_enable", "hq_profile_read", "hq_sync", "hq_last_error",
            "hq_poisson_solve_static", "hq_sweep_forward_ckpt", "hq_sweep_adjoint", "hq_beam_moments",
-           "hq_beam_slices", "hq_sweep_slices")
+           "hq_beam_slices", "hq_sweep_slices", "hq_pc_residuals")
 KERNEL_CLASSES = ("final", "trial", "dst", "field", "beam", "other")
 
 
@@ -97,6 +97,7 @@ def load() -> C.CDLL:
                                  P),
             "hq_beam_moments": (P, C.POINTER(BeamView), P),
             "hq_beam_slices": (P, C.POINTER(BeamView), P),
+            "hq_pc_residuals": (P, C.POINTER(C.c_double), C.c_int32),
             "hq_sweep_slices": (P, C.POINTER(BeamView), C.c_int32, C.POINTER(BeamView), C.c_int32, C.c_int32,
                                 C.c_int32, C.c_double, C.POINTER(FieldOut), C.c_int32, P),
         }
@@ -298,6 +299,12 @@ class Grid:
                                        C.c_void_p(dn0.data_ptr()),
                                        C.c_void_p(dprof.data_ptr()) if dprof is not None else None), self.h)
         return {"beam_w": wb, "plasma_w": wp, "n0_scale": dn0, "profile": dprof}
+
+    def pc_residuals(self) -> list:
+        """Per slice of the last sweep: ||B_m - B_m-1|| / ||B_m|| of the last predictor-corrector iteration."""
+        out = (C.c_double * self.nzeta)()
+        _check(load().hq_pc_residuals(self.h, out, self.nzeta), self.h)
+        return list(out)
 
     def beam_slices(self, beam: Beam) -> torch.Tensor:
         """Slice of every particle (int32 CUDA tensor): 0..nzeta-1 inside, -1 ahead, nzeta behind, -2 not finite."""
