@@ -133,6 +133,9 @@ typedef struct {
                                        preconditioner shift is then sum q^2 n0_scale / M  */
   int32_t n_species;                /* 0: the default electrons (q = -1, M = 1) over
                                        immobile ions, placed by the fields above          */
+  int32_t pc_residuals;             /* 1: record the predictor-corrector residual of every
+                                       slice for hq_pc_residuals (the last iteration's
+                                       solve launch sums it: ~6 us more per slice); 0: off */
 } hq_grid_desc;
 
 /* B_perp field solver (Sec. 3.2: "predictor-corrector field solver" and "explicit field
@@ -233,8 +236,9 @@ hq_status hq_witness_accumulate(hq_grid_t grid, const hq_beam_view* beam, int32_
 /* Sec. 3.2 (predictor-corrector): the relative change of B_perp in the last iteration of each
  * slice of the last sweep, ||B_m - B_m-1|| / ||B_m|| over both components and every node (the
  * mixing's own residual; 0 for a slice with no iteration, or with the explicit solver, which has
- * no mixing), written to out[0..n) (HOST doubles; entries past nzeta are 0).  Synchronizes the
- * grid's stream.  Errors: HQ_ERR_ARG. */
+ * no mixing), written to out[0..n) (HOST doubles; entries past nzeta are 0).  Recorded only by a
+ * grid created with pc_residuals = 1 (HQ_ERR_STATE otherwise).  Synchronizes the grid's stream.
+ * Errors: HQ_ERR_ARG, HQ_ERR_STATE. */
 hq_status hq_pc_residuals(hq_grid_t grid, double* out, int32_t n);
 
 /* Sec. 3.1 (beam particles sorted per slice) and Sec. 5.2 (temporal pipeline: a box's

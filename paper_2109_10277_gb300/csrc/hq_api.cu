@@ -299,7 +299,7 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
   for (int m = 0; m < npc; ++m) {
     const int last = m == npc - 1;
     // the last iteration's mixing adds its residual sums to this slice's pair
-    g->pc_rsum = last && g->d_pcres ? g->d_pcres + 2 * (int64_t)slice : nullptr;
+    g->pc_rsum = last && g->d_pcres ? g->d_pcres + 2 * kResLanes * (int64_t)slice : nullptr;   // (opt-in)
     tape_b_iterate(g, m);
     { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, s); }
     if (g->det) launch_fx_decode(g, g->tj, 2 * g->nnode, nullptr, s);
@@ -359,7 +359,7 @@ void advance_impl(hq_grid_s* g, int slice) {
     launch_zero<T>(g->bjn, 2 * g->nnode, s);
     launch_zero<T>(g->tj, 2 * g->nnode, s);
     if (g->bjp) launch_zero<T>(g->bjp, 4 * g->nnode, s);
-    cudaMemsetAsync(g->d_pcres, 0, sizeof(double) * 2 * g->nz, s);
+    if (g->d_pcres) cudaMemsetAsync(g->d_pcres, 0, sizeof(double) * 2 * kResLanes * g->nz, s);
   } else {
     final_pass<T>(g, slice - 1, slice & 1);
     if (g->d.resort_every > 0 && slice % g->d.resort_every == 0) {
@@ -834,6 +834,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     return fail(nullptr, HQ_ERR_ARG, "the explicit B_perp solver needs a positive preconditioner shift "
                                      "(n0_scale, or sum q^2 n0 / M over the species)");
   if (d.resort_every < 0) return fail(nullptr, HQ_ERR_ARG, "resort_every must be >= 0");
+  if (d.pc_residuals != 0 && d.pc_residuals != 1) return fail(nullptr, HQ_ERR_ARG, "pc_residuals must be 0 or 1");
   if (d.deterministic != 0 && d.deterministic != 1) return fail(nullptr, HQ_ERR_ARG, "deterministic must be 0 or 1");
   if (d.deterministic && d.precision != HQ_PREC_FP64)
     return fail(nullptr, HQ_ERR_UNSUPPORTED, "deterministic accumulation is an FP64 mode");
@@ -1048,8 +1049,10 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   HQ_ALLOC(g->bprev1, 2 * ts * nn);
   HQ_ALLOC(g->solved, kMaxRhs * ts * nn);
   HQ_ALLOC(g->d_status, sizeof(int));
-  HQ_ALLOC(g->d_pcres, sizeof(double) * 2 * g->nz);
-  cudaMemset(g->d_pcres, 0, sizeof(double) * 2 * g->nz);
+  if (d.pc_residuals) {
+    HQ_ALLOC(g->d_pcres, sizeof(double) * 2 * kResLanes * g->nz);
+    cudaMemset(g->d_pcres, 0, sizeof(double) * 2 * kResLanes * g->nz);
+  }
   if (g->det) g->geom.dstatus = g->d_status;   // fixed-point range overflows are reported here
   HQ_ALLOC(g->d_removed, sizeof(unsigned long long));
   for (int b = 0; b < kMaxBeams; ++b) {
@@ -1329,15 +1332,20 @@ hq_status hq_beam_slices(hq_grid_t g, const hq_beam_view* beam, int32_t* slices)
 hq_status hq_pc_residuals(hq_grid_t g, double* out, int32_t n) {
   if (!g) return fail(nullptr, HQ_ERR_ARG, "grid is NULL");
   if (n < 0 || (n > 0 && !out)) return fail(g, HQ_ERR_ARG, "out must hold n >= 0 doubles");
+  if (!g->d_pcres) return fail(g, HQ_ERR_STATE, "the grid was created without pc_residuals = 1");
   HQ_CUDA(g, cudaStreamSynchronize(g->stream));
-  std::vector<double> sums(2 * (size_t)g->nz);
+  std::vector<double> sums(2 * kResLanes * (size_t)g->nz);
   HQ_CUDA(g, cudaMemcpy(sums.data(), g->d_pcres, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost));
   for (int i = 0; i < n; ++i) {
     if (i >= g->nz) {
       out[i] = 0.0;
       continue;
     }
-    const double num = sums[2 * (size_t)i], den = sums[2 * (size_t)i + 1];
+    double num = 0.0, den = 0.0;
+    for (int l = 0; l < kResLanes; ++l) {
+      num += sums[(2 * kResLanes * (size_t)i) + 2 * l];
+      den += sums[(2 * kResLanes * (size_t)i) + 2 * l + 1];
+    }
     out[i] = den > 0.0 ? std::sqrt(num / den) : 0.0;
   }
   return HQ_OK;

@@ -182,8 +182,8 @@ struct hq_grid_s {
   // the initial charge of the species without a neutralizing background, sum q w S(x0) / A,
   // added to the ion-subtracted psi source (null when every species is neutralized)
   // predictor-corrector residual of each slice of the last sweep (Sec. 3.2): sum (B_m - B_m-1)^2
-  // and sum B_m^2 of the last iteration's mixing, [nzeta][2]; pc_rsum points at the slice's pair
-  // while its last iteration mixes (null otherwise)
+  // and sum B_m^2 of the last iteration's mixing, [nzeta][kResLanes][2] (lanes spread the
+  // atomics); pc_rsum points at the slice's lanes while its last iteration mixes (null otherwise)
   double* d_pcres;
   double* pc_rsum;
   int multi;
@@ -444,19 +444,31 @@ __device__ __forceinline__ void dadd(double* p, double v, const Geom& gm) {
 }
 __device__ __forceinline__ void dadd(float* p, float v, const Geom&) { atomicAdd(p, v); }
 
-// Adds a thread's (sum (B_m - B_m-1)^2, sum B_m^2) of the predictor-corrector mixing to rs[0..1]:
-// warp sums, then one FP64 atomic pair per warp (rs null: nothing).  All lanes must call it.
+// Adds the block's (sum (B_m - B_m-1)^2, sum B_m^2) of the predictor-corrector mixing to the
+// slice's residual sums rs: [kResLanes][2] pairs, the block's pair chosen by its index so that
+// no address takes more than a few atomics (the host adds the lanes).  Warp shuffles, then a
+// shared-memory sum over the warps; every thread of the block must call it (it synchronizes).
+constexpr int kResLanes = 16;
 __device__ __forceinline__ void pc_residual_add(double* rs, double d2, double b2) {
-  if (!rs) return;
+  __shared__ double part[2][32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     d2 += __shfl_down_sync(0xffffffffu, d2, o);
     b2 += __shfl_down_sync(0xffffffffu, b2, o);
   }
-  if ((threadIdx.x & 31) == 0 && (d2 != 0.0 || b2 != 0.0)) {
-    atomicAdd(rs, d2);
-    atomicAdd(rs + 1, b2);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    part[0][w] = d2;
+    part[1][w] = b2;
   }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0.0;
+    for (int k = 0; k < nw; ++k) t += part[threadIdx.x][k];
+    const int lane = (int)((blockIdx.y * gridDim.x + blockIdx.x) % kResLanes);
+    if (t != 0.0) atomicAdd(rs + 2 * lane + threadIdx.x, t);
+  }
+  __syncthreads();
 }
 
 // Folded DST-I order (Sec. 3.2 solver).  With S_jk = sin(pi j k / n),

@@ -469,7 +469,7 @@ template <int BN> struct SolveSmem {
   static constexpr int BYTES = BARS + 256 + 1024 /*alignment*/;
 };
 
-template <int BN>
+template <int BN, bool RES>
 __global__ void __launch_bounds__(kSolveThreads, 1)
     k_dst_solve(const __grid_constant__ CUtensorMap a0h, const __grid_constant__ CUtensorMap a0l,
                 const __grid_constant__ CUtensorMap a1h, const __grid_constant__ CUtensorMap a1l,
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
         const int xn = a.fold ? fold_node(ml, a.nx) : ml;
         float x[CH];
         tmem_ld_pair<BN, CH>(tl + (uint32_t)c0, x);
-        double d2 = 0.0, b2 = 0.0;   // mode 3: this thread's share of the predictor-corrector residual
+        float d2 = 0.0f, b2 = 0.0f;   // mode 3 with RES: this thread's share of the residual (FP32)
         if (xn < a.nx) {
           auto ynode = [&](int j) { return a.fold ? fold_node(n0 + c0 + j, a.ny) : n0 + c0 + j; };
           if (mode == 2) {
@@ -680,14 +680,17 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
               const int64_t node = (int64_t)yn * a.nx + xn;
               const float nb = a.w * x[j] + (1.0f - a.w) * old[j];
               a.bm[node * 2 + r] = nb;
-              const double d = (double)nb - (double)old[j];
-              d2 += d * d;
-              b2 += (double)nb * (double)nb;
+              if constexpr (RES) {
+                const float d = nb - old[j];
+                d2 += d * d;
+                b2 += nb * nb;
+              }
             }
             if (bad) atomicOr(a.status, DEV_NONFINITE);
           }
         }
-        if (mode == 3) pc_residual_add(a.rsum, d2, b2);   // every lane of the warp (mode is uniform)
+        if constexpr (RES)
+          if (mode == 3) pc_residual_add(a.rsum, (double)d2, (double)b2);   // every lane (mode is uniform)
       }
       kb_run += nk;
       ++tiles_run;
@@ -849,12 +852,12 @@ __device__ __forceinline__ void solve_sources_rows(const Geom& gm, const F& f, c
 // consecutive x nodes from xb, component r) staged in shared memory ([128][BN + 1]): element
 // e = (row, j) is taken by thread e mod 256, so a warp covers consecutive x nodes of one row;
 // up to sixteen elements' loads are issued before their stores.
-template <int BN>
+template <int BN, bool RES>
 __device__ __forceinline__ void rs_mix(const SolveArgs& a, const float* tile, int s0, int r, int xb) {
   constexpr int LD = BN + 1, NE = BM * BN, UN = NE / kSolveThreads < 16 ? NE / kSolveThreads : 16;
   const int n = a.nx;
   bool bad = false;
-  double d2 = 0.0, b2 = 0.0;
+  float d2 = 0.0f, b2 = 0.0f;   // RES (the slice's last iteration): residual sums in FP32
   for (int e0 = threadIdx.x; e0 < NE; e0 += UN * kSolveThreads) {
     float v[UN], old[UN];
     int64_t at[UN];
@@ -872,16 +875,18 @@ __device__ __forceinline__ void rs_mix(const SolveArgs& a, const float* tile, in
       bad |= !isfinite(v[k]);
       const float nb = a.w * v[k] + (1.0f - a.w) * old[k];
       a.bm[at[k]] = nb;
-      const double d = (double)nb - (double)old[k];
-      d2 += d * d;
-      b2 += (double)nb * (double)nb;
+      if constexpr (RES) {
+        const float d = nb - old[k];
+        d2 += d * d;
+        b2 += nb * nb;
+      }
     }
   }
   if (bad) atomicOr(a.status, DEV_NONFINITE);
-  pc_residual_add(a.rsum, d2, b2);
+  if constexpr (RES) pc_residual_add(a.rsum, (double)d2, (double)b2);
 }
 
-template <int BN>
+template <int BN, bool RES>
 __global__ void __launch_bounds__(kSolveThreads, 1)
     k_dst_solve_rs(const __grid_constant__ CUtensorMap fh, const __grid_constant__ CUtensorMap fl,
                    const __grid_constant__ CUtensorMap x0h, const __grid_constant__ CUtensorMap x0l,
@@ -1022,7 +1027,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
 #pragma unroll
           for (int j = 0; j < CH; ++j) tile[row * LD + half * CH + j] = x[j];
           __syncthreads();
-          if (!*abort_f) rs_mix<BN>(a, tile, s0, r, c0 - r * n);
+          if (!*abort_f) rs_mix<BN, RES>(a, tile, s0, r, c0 - r * n);
         } else if (!*abort_f) {
           rs_epilogue<CH>(a, mode, s, orow, r, i0, x, sc, a.op_hi[(p + 1) & 1], a.op_lo[(p + 1) & 1]);
         }
@@ -1133,15 +1138,20 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
   };
   g->tmaps = new TensorMaps();
   TensorMaps& t = *g->tmaps;
-  if (!size_solve(k_dst_solve<64>, SolveSmem<64>::BYTES, t.ctas[0]) ||
-      !size_solve(k_dst_solve<32>, SolveSmem<32>::BYTES, t.ctas[1]))
+  int spare = 0;   // the residual-accumulating instances (the last P-C iteration): same resources
+  if (!size_solve(k_dst_solve<64, false>, SolveSmem<64>::BYTES, t.ctas[0]) ||
+      !size_solve(k_dst_solve<32, false>, SolveSmem<32>::BYTES, t.ctas[1]) ||
+      !size_solve(k_dst_solve<64, true>, SolveSmem<64>::BYTES, spare) ||
+      !size_solve(k_dst_solve<32, true>, SolveSmem<32>::BYTES, spare))
     return 1;
   const char* bn = std::getenv("HQ_SOLVE_BN");
   t.wide_only = bn != nullptr && std::atoi(bn) == 64;
   const char* nors = std::getenv("HQ_NO_RS");
   t.rs = g->fold && g->nx == g->ny && (g->nx == 256 || g->nx == 512) && !(nors && nors[0] == '1');
-  if (t.rs && (!size_solve(k_dst_solve_rs<64>, RsSmem<64>::BYTES, t.rs_ctas[0]) ||
-               !size_solve(k_dst_solve_rs<32>, RsSmem<32>::BYTES, t.rs_ctas[1])))
+  if (t.rs && (!size_solve(k_dst_solve_rs<64, false>, RsSmem<64>::BYTES, t.rs_ctas[0]) ||
+               !size_solve(k_dst_solve_rs<32, false>, RsSmem<32>::BYTES, t.rs_ctas[1]) ||
+               !size_solve(k_dst_solve_rs<64, true>, RsSmem<64>::BYTES, spare) ||
+               !size_solve(k_dst_solve_rs<32, true>, RsSmem<32>::BYTES, spare)))
     return 1;
   const uint64_t nxp = g->nxp, nyp = g->nyp;
   int bad = 0;
@@ -1228,8 +1238,9 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s, 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, narrow ? k_dst_solve_rs<32> : k_dst_solve_rs<64>, t.rf_hi, t.rf_lo, t.rx_hi[0][v],
-                       t.rx_lo[0][v], t.rx_hi[1][v], t.rx_lo[1][v], a);
+    auto kern = a.rsum ? (narrow ? k_dst_solve_rs<32, true> : k_dst_solve_rs<64, true>)
+                       : (narrow ? k_dst_solve_rs<32, false> : k_dst_solve_rs<64, false>);
+    cudaLaunchKernelEx(&cfg, kern, t.rf_hi, t.rf_lo, t.rx_hi[0][v], t.rx_lo[0][v], t.rx_hi[1][v], t.rx_lo[1][v], a);
     return;
   }
   // tiles of one product (the larger of the x and y products) at N-tile width bn
@@ -1249,8 +1260,10 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   // a launch error is reported by the caller's launch check
-  cudaLaunchKernelEx(&cfg, narrow ? k_dst_solve<32> : k_dst_solve<64>, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi[v],
-                     t.bx_lo[v], t.by_hi[v], t.by_lo[v], shifted ? t.scale_h[v] : t.scale[v], a);
+  auto kern = a.rsum ? (narrow ? k_dst_solve<32, true> : k_dst_solve<64, true>)
+                     : (narrow ? k_dst_solve<32, false> : k_dst_solve<64, false>);
+  cudaLaunchKernelEx(&cfg, kern, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi[v], t.bx_lo[v], t.by_hi[v], t.by_lo[v],
+                     shifted ? t.scale_h[v] : t.scale[v], a);
 }
 
 }  // namespace

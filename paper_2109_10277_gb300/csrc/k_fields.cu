@@ -96,11 +96,13 @@ __global__ void k_finish_bperp(const T* __restrict__ res, V2<T>* bm, int64_t nn,
     const V2<T> b = bm[o];
     const V2<T> nb{w * bx + (T(1) - w) * b.a, w * by + (T(1) - w) * b.b};
     bm[o] = nb;
-    const double dx = (double)nb.a - (double)b.a, dy = (double)nb.b - (double)b.b;
-    d2 = dx * dx + dy * dy;
-    b2 = (double)nb.a * (double)nb.a + (double)nb.b * (double)nb.b;
+    if (rsum) {
+      const T dx = nb.a - b.a, dy = nb.b - b.b;
+      d2 = (double)(dx * dx + dy * dy);
+      b2 = (double)(nb.a * nb.a + nb.b * nb.b);
+    }
   }
-  pc_residual_add(rsum, d2, b2);
+  if (rsum) pc_residual_add(rsum, d2, b2);
 }
 
 template <typename T>

@@ -43,7 +43,7 @@ class GridDesc(C.Structure):
                 ("n0_scale", C.c_double), ("n_pc_iter", C.c_int32), ("pc_mix", C.c_double),
                 ("psi_guard", C.c_double), ("precision", C.c_int32), ("bperp_solver", C.c_int32),
                 ("resort_every", C.c_int32), ("deterministic", C.c_int32),
-                ("species", C.POINTER(SpeciesDesc)), ("n_species", C.c_int32)]
+                ("species", C.POINTER(SpeciesDesc)), ("n_species", C.c_int32), ("pc_residuals", C.c_int32)]
 
 
 class BeamView(C.Structure):
@@ -195,7 +195,7 @@ class Grid:
             HQ_PREC_FP64 if precision == "fp64" else HQ_PREC_FP32_BF16X3,
             {"pc": 0, "explicit": 1}[params.get("bperp_solver", "pc")], int(params.get("resort_every", 0)),
             int(params.get("deterministic", 0)),
-            C.cast(self._sp, C.POINTER(SpeciesDesc)) if sps else None, len(sps))
+            C.cast(self._sp, C.POINTER(SpeciesDesc)) if sps else None, len(sps), int(params.get("pc_residuals", 0)))
         self.params = dict(params)
         self.nx, self.ny, self.nzeta = d.nx, d.ny, d.nzeta
         self.stream = stream if stream is not None else torch.cuda.current_stream()

@@ -92,7 +92,7 @@ def test_binding_structs_match_the_header(tmp_path):
         pytest.skip("no host C compiler")
     from paper_2109_10277_gb300 import hq
     checks = {"hq_grid_desc": (hq.GridDesc, ("n_pc_iter", "precision", "bperp_solver", "resort_every",
-                                             "deterministic", "species", "n_species")),
+                                             "deterministic", "species", "n_species", "pc_residuals")),
               "hq_species_desc": (hq.SpeciesDesc, ("mass", "ppc_y", "radial_profile", "neutralize")),
               "hq_beam_view": (hq.BeamView, ("w", "charge", "mass")),
               "hq_field_out": (hq.FieldOut, ("bz",)),

@@ -623,10 +623,15 @@ def test_pc_residuals_match_oracle(hq, precision):
     g = I.grid_params("linear64")
     beams = I.workload_beams("linear64")
     ref = O.sweep(O.GridSpec(**g), [O.as_beam(b) for b in beams], record=())
-    grid = hq.Grid(g, precision=precision)
+    grid = hq.Grid(dict(g, pc_residuals=1), precision=precision)
     grid.sweep([hq.Beam(b) for b in beams])
     got = grid.pc_residuals()
     grid.close()
+    plain = hq.Grid(g, precision=precision)   # not recorded unless asked for
+    with pytest.raises(hq.HQError) as e:
+        plain.pc_residuals()
+    assert e.value.status == 6
+    plain.close()
     tol = 1e-8 if precision == "fp64" else 1e-2
     worst = 0.0
     for i, (a, r) in enumerate(zip(got, ref.pc_residual)):
