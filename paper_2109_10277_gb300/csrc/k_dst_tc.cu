@@ -445,7 +445,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
           *abort_f = 1;
           break;
         }
-        __nanosleep(32);
       }
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");
