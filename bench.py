@@ -324,6 +324,36 @@ def explicit_leg(hq, I, stream, flush, iters=6):
             "witness_sums": [float(v) for v in sums.cpu()]}
 
 
+def tf32_leg(hq, I, stream, flush):
+    """The headline workload with TF32x3 tensor-core DST operands (HQ_PREC_FP32_TF32X3: ~21
+    significant bits per operand against bf16x3's 16, twice the operand bytes and instructions;
+    the solve streams the fold matrix)."""
+    import torch
+    g = I.grid_params(WORKLOAD)
+    grid = hq.Grid(g, precision="tf32x3", stream=stream)
+    hb = [hq.Beam(b) for b in I.workload_beams(WORKLOAD)]
+    sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+    grid.sweep(hb, witness=0, witness_sums=sums)
+    grid.sync()
+    ts = []
+    for k in range(2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(11 + k)
+        sums.zero_()
+        a.record(stream)
+        grid.sweep(hb, witness=0, witness_sums=sums)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    removed = grid.sync()
+    grid.close()
+    ms = min(ts)
+    p = g["nx"] * g["ny"] * g["ppc_x"] * g["ppc_y"]
+    return {"workload": f"{WORKLOAD} with TF32x3 DST operands", "ms_per_step": ms,
+            "value": p * g["nzeta"] / (ms / 1e3), "unit": UNIT, "removed_particles": removed,
+            "witness_sums": [float(v) for v in sums.cpu()]}
+
+
 def pipeline_leg(hq, I, steps=8, ranks=2, boxes=8, dt=6.0):
     """The temporal decomposition of Sec. 5.2 on one GPU: `steps` beam time steps of the headline
     workload (beam push Delta t = 6, the Appendix's time step), serially as graph-replayed sweeps,
@@ -688,7 +718,7 @@ def run_hq(args):
     if not args.no_adjoint and args.precision == "fp32":
         adjoint = adjoint_leg(hq, I, stream, flush)
 
-    cubic = adjoint512 = dstcmp = precision = explicit = species = pipeline = None
+    cubic = adjoint512 = dstcmp = precision = explicit = species = pipeline = tf32 = None
     if not args.no_extra and args.precision == "fp32" and rank == 0:
         grid.close()
         grid = None
@@ -702,6 +732,7 @@ def run_hq(args):
         precision = precision_leg(hq, I, stream, steps=args.precision_steps)
         explicit = explicit_leg(hq, I, stream, flush)
         species = species_leg(hq, I, stream, flush)
+        tf32 = tf32_leg(hq, I, stream, flush)
         pipeline = pipeline_leg(hq, I)
 
     cpu = None
@@ -724,7 +755,7 @@ def run_hq(args):
             "gpu_launches": launches_per_sweep * args.steps,
             "fp64": fp64, "adjoint": adjoint, "cubic1024": cubic, "adjoint512": adjoint512,
             "dst_comparator": dstcmp, "precision_study": precision, "explicit_solver": explicit, "ion_motion": species,
-            "temporal_pipeline_1gpu": pipeline,
+            "temporal_pipeline_1gpu": pipeline, "tf32x3": tf32,
             "cpu_baseline": cpu,
             "removed_particles": removed,
         }

@@ -21,7 +21,7 @@
  * Data layout: a transverse field slice is ny x nx values, row-major, row = y.
  * Node (iy, ix) sits at (xmin + ix*dx, ymin + iy*dy); nodes 0 and nx (ny) lie on
  * the Dirichlet wall, so row 0 and column 0 of every field are zero.  Field
- * values are double for HQ_PREC_FP64 grids and float for HQ_PREC_FP32_BF16X3.
+ * values are double for HQ_PREC_FP64 grids and float for the FP32 precisions.
  * Beam arrays are always double.
  *
  * Run-time switches (environment variables, read when a grid is created; HQ_NO_GRAPH
@@ -70,7 +70,14 @@ typedef enum {
   /* push/gather/deposit in FP32 with FP64 position and Psi accumulators; the DST-I
      as dense products on the tensor cores with each FP32 operand split into two
      bf16 terms (3 products, FP32 accumulation) */
-  HQ_PREC_FP32_BF16X3 = 1
+  HQ_PREC_FP32_BF16X3 = 1,
+  /* the same FP32 path with each DST operand split into two TF32 terms instead (hi = the value
+     rounded to TF32, lo = the remainder, read by the tensor core truncated to TF32): ~21
+     significant bits per operand against bf16x3's 16, at twice the operand bytes and twice
+     the tensor-core instructions (K = 8 per instruction); every grid shape takes the solve
+     that streams the sine/fold matrices (the resident-matrix solve would need 256 KB of
+     shared memory at 512^2) */
+  HQ_PREC_FP32_TF32X3 = 2
 } hq_precision;
 
 /* One plasma species (Sec. 6: plasmas of several species and profiles, ion motion).  The
@@ -187,7 +194,7 @@ typedef struct hq_grid_s* hq_grid_t;
  * transform scratch on the current device, and builds the DST tables.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Errors: HQ_ERR_ARG (bad desc), HQ_ERR_OOM, HQ_ERR_CUDA, HQ_ERR_UNSUPPORTED
- * (HQ_PREC_FP32_BF16X3 needs a compute capability 10.x device). */
+ * (the FP32 precisions need a compute capability 10.x device). */
 hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t* out);
 
 /* Frees everything the grid owns (synchronizes its stream first). NULL is a no-op. */

@@ -31,6 +31,16 @@ hq_status fail(hq_grid_s* g, hq_status st, const std::string& msg) {
                                        std::string(#call) + ": " + cudaGetErrorString(e_));        \
   } while (0)
 
+// FP32 value rounded to TF32 (11 significant bits, ties away from zero), as cvt.rna.tf32.f32
+// rounds on the device.
+float round_tf32_host(float v) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+  std::memcpy(&v, &u, 4);
+  return v;
+}
+
 template <typename P>
 cudaError_t dalloc(P** p, size_t bytes) {
   *p = nullptr;
@@ -816,7 +826,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   if (d.n_pc_iter < 0 || d.n_pc_iter > 1000) return fail(nullptr, HQ_ERR_ARG, "n_pc_iter must be 0..1000");
   if (!std::isfinite(d.pc_mix) || !std::isfinite(d.psi_guard) || !std::isfinite(d.n0_scale))
     return fail(nullptr, HQ_ERR_ARG, "pc_mix, psi_guard and n0_scale must be finite");
-  if (d.precision != HQ_PREC_FP64 && d.precision != HQ_PREC_FP32_BF16X3)
+  if (d.precision != HQ_PREC_FP64 && d.precision != HQ_PREC_FP32_BF16X3 && d.precision != HQ_PREC_FP32_TF32X3)
     return fail(nullptr, HQ_ERR_ARG, "unknown precision");
   if (d.bperp_solver != HQ_BPERP_PC && d.bperp_solver != HQ_BPERP_EXPLICIT)
     return fail(nullptr, HQ_ERR_ARG, "unknown bperp_solver");
@@ -918,6 +928,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   g->dev = dev;
   g->fp64 = d.precision == HQ_PREC_FP64;
+  g->tf32 = d.precision == HQ_PREC_FP32_TF32X3;
   g->explicit_b = d.bperp_solver == HQ_BPERP_EXPLICIT;
   g->nx = d.nx; g->ny = d.ny; g->nz = d.nzeta;
   g->nnode = (int64_t)d.nx * d.ny;
@@ -1134,28 +1145,38 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     HQ_ALLOC(g->d_gbar, sizeof(unsigned long long));
     cudaMemset(g->d_gbar, 0, sizeof(unsigned long long));
     const size_t opn = (size_t)kMaxRhs * g->nxp * g->nyp;
+    const size_t esz = g->tf32 ? 4 : 2;   // bytes per split operand element
     for (int i = 0; i < 2; ++i) {
-      HQ_ALLOC(g->op_hi[i], 2 * opn);
-      HQ_ALLOC(g->op_lo[i], 2 * opn);
-      cudaMemset(g->op_hi[i], 0, 2 * opn);
-      cudaMemset(g->op_lo[i], 0, 2 * opn);
+      HQ_ALLOC(g->op_hi[i], esz * opn);
+      HQ_ALLOC(g->op_lo[i], esz * opn);
+      cudaMemset(g->op_hi[i], 0, esz * opn);
+      cudaMemset(g->op_lo[i], 0, esz * opn);
     }
-    // S (zero-padded [np][np]) or, folded, the fold matrix [n][n/2]; split into bf16 hi + lo
-    auto smat = [&](int n, int np_, __nv_bfloat16** hi, __nv_bfloat16** lo) -> hq_status {
+    // S (zero-padded [np][np]) or, folded, the fold matrix [n][n/2]; split into hi + lo (bf16,
+    // or TF32 in FP32 words)
+    auto smat = [&](int n, int np_, void** hi, void** lo) -> hq_status {
       const int cols = g->fold ? n / 2 : np_;
       const std::vector<double> fm = g->fold ? fold_matrix(n) : std::vector<double>();
-      std::vector<__nv_bfloat16> h((size_t)np_ * cols), l((size_t)np_ * cols);
+      const size_t cnt = (size_t)np_ * cols;
+      std::vector<__nv_bfloat16> h(g->tf32 ? 0 : cnt), l(g->tf32 ? 0 : cnt);
+      std::vector<float> hf(g->tf32 ? cnt : 0), lf(g->tf32 ? cnt : 0);
       for (int k = 0; k < np_; ++k)
         for (int j = 0; j < cols; ++j) {
           const float v = g->fold ? (float)fm[(size_t)k * cols + j]
                                   : ((j < n && k < n) ? (float)sin_jk(j, k, n) : 0.0f);
-          const __nv_bfloat16 vh = __float2bfloat16_rn(v);
-          h[(size_t)k * cols + j] = vh;
-          l[(size_t)k * cols + j] = __float2bfloat16_rn(v - __bfloat162float(vh));
+          const size_t o = (size_t)k * cols + j;
+          if (g->tf32) {
+            hf[o] = round_tf32_host(v);
+            lf[o] = v - hf[o];
+          } else {
+            const __nv_bfloat16 vh = __float2bfloat16_rn(v);
+            h[o] = vh;
+            l[o] = __float2bfloat16_rn(v - __bfloat162float(vh));
+          }
         }
-      if (dalloc(hi, 2 * h.size()) != cudaSuccess || dalloc(lo, 2 * l.size()) != cudaSuccess) return HQ_ERR_OOM;
-      cudaMemcpy(*hi, h.data(), 2 * h.size(), cudaMemcpyHostToDevice);
-      cudaMemcpy(*lo, l.data(), 2 * l.size(), cudaMemcpyHostToDevice);
+      if (dalloc(hi, esz * cnt) != cudaSuccess || dalloc(lo, esz * cnt) != cudaSuccess) return HQ_ERR_OOM;
+      cudaMemcpy(*hi, g->tf32 ? (const void*)hf.data() : (const void*)h.data(), esz * cnt, cudaMemcpyHostToDevice);
+      cudaMemcpy(*lo, g->tf32 ? (const void*)lf.data() : (const void*)l.data(), esz * cnt, cudaMemcpyHostToDevice);
       return HQ_OK;
     };
     if (smat(g->nx, g->nxp, &g->sx_hi, &g->sx_lo) != HQ_OK || smat(g->ny, g->nyp, &g->sy_hi, &g->sy_lo) != HQ_OK) {

@@ -156,7 +156,8 @@ struct hq_grid_s {
   std::vector<double> profile;
   cudaStream_t stream;
   int dev;
-  int fp64;            // 1: FP64 everywhere; 0: FP32 + bf16x3 tensor-core DST
+  int fp64;            // 1: FP64 everywhere; 0: FP32 + split tensor-core DST
+  int tf32;            // FP32 mode: 1 TF32x3 operands, 0 bf16x3
   int nx, ny, nz;
   int64_t nnode, np;
   hq::Geom geom;
@@ -222,8 +223,9 @@ struct hq_grid_s {
   double *f64_a, *f64_b, *f64_scale, *tw_x, *tw_y, *sin_x, *sin_y;
   // DST, FP32/bf16x3: padded operand buffers and sine matrices
   int nxp, nyp;
-  __nv_bfloat16 *op_hi[2], *op_lo[2];       // ping-pong [kMaxRhs * max(nxp,nyp)^2]
-  __nv_bfloat16 *sx_hi, *sx_lo, *sy_hi, *sy_lo;
+  // elements: bf16, or (tf32) FP32 words holding TF32 values
+  void *op_hi[2], *op_lo[2];                // ping-pong [kMaxRhs * max(nxp,nyp)^2]
+  void *sx_hi, *sx_lo, *sy_hi, *sy_lo;
   float* f32_scale;                          // [nyp][nxp] (1/lambda)(4/(nx ny)), slot order if folded
   hq::TensorMaps* tmaps;
   int fold;                                  // folded DST-I (nx, ny multiples of 128; FP32 mode)
@@ -498,7 +500,7 @@ __host__ __device__ __forceinline__ int fold_node(int s, int n) {
 namespace hq {
 
 // DST operand writers: FP64 mode writes [rhs][ny][nx] doubles (g->f64_a); FP32 mode
-// writes each value already split into bf16 hi + lo, zero-padded [rhs][nyp][nxp]
+// writes each value already split into hi + lo (bf16 or TF32), zero-padded [rhs][nyp][nxp]
 // (g->op_hi[0], g->op_lo[0]), the tensor-core solver's input layout.
 struct SinkF64 {
   static constexpr bool kFold = false;
@@ -507,15 +509,30 @@ struct SinkF64 {
   __device__ void put(int r, int iy, int ix, double v) const { p[((int64_t)r * ny + iy) * nx + ix] = v; }
 };
 
+// The split of one FP32 value v into the tensor-core operand pair (hi, lo), v ~ hi + lo:
+// bf16 (HQ_PREC_FP32_BF16X3: hi = bf16(v), lo = bf16(v - hi), 16 significant bits), or TF32 held
+// in 32-bit words (HQ_PREC_FP32_TF32X3: hi = v rounded to 11 significant bits, lo = v - hi,
+// which the tensor core reads truncated to TF32: 21 or more significant bits).
+__device__ __forceinline__ float round_tf32(float v) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+  return __uint_as_float(u);
+}
 __device__ __forceinline__ void put_split(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t o, float v) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
   hi[o] = h;
   lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
+__device__ __forceinline__ void put_split(float* hi, float* lo, int64_t o, float v) {
+  const float h = round_tf32(v);
+  hi[o] = h;
+  lo[o] = v - h;
+}
 
-struct SinkBF16 {
+// Plain operand layout [rhs][nyp][nxp] (E: __nv_bfloat16 or float for TF32).
+template <typename E> struct SinkSplit {
   static constexpr bool kFold = false;
-  __nv_bfloat16 *hi, *lo;
+  E *hi, *lo;
   int nxp, nyp;
   __device__ void put(int r, int iy, int ix, float v) const { put_split(hi, lo, ((int64_t)r * nyp + iy) * nxp + ix, v); }
 };
@@ -524,9 +541,9 @@ struct SinkBF16 {
 // folded column u in row slot sy and writes the sum x_a + x_b to column u and the
 // difference x_a - x_b to column nx/2 + u (the pair (0, n/2) stores x_{n/2} and 0:
 // node 0 is on the wall and never enters a DST-I).  Layout [rhs][ny slots][nx].
-struct SinkFold {
+template <typename E> struct SinkFold {
   static constexpr bool kFold = true;
-  __nv_bfloat16 *hi, *lo;
+  E *hi, *lo;
   int nx, ny;
   __device__ void put_pair(int r, int sy, int u, float va, float vb) const {
     const bool wall = u == nx / 4;
@@ -580,8 +597,17 @@ inline void with_sink(const hq_grid_s* g, F&& f) {
   if constexpr (sizeof(T) == 8) {
     f(SinkF64{g->f64_a, g->nx, g->ny});
   } else {
-    if (g->fold) f(SinkFold{g->op_hi[0], g->op_lo[0], g->nx, g->ny});
-    else f(SinkBF16{g->op_hi[0], g->op_lo[0], g->nxp, g->nyp});
+    if (g->tf32) {
+      float* hi = reinterpret_cast<float*>(g->op_hi[0]);
+      float* lo = reinterpret_cast<float*>(g->op_lo[0]);
+      if (g->fold) f(SinkFold<float>{hi, lo, g->nx, g->ny});
+      else f(SinkSplit<float>{hi, lo, g->nxp, g->nyp});
+    } else {
+      __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(g->op_hi[0]);
+      __nv_bfloat16* lo = reinterpret_cast<__nv_bfloat16*>(g->op_lo[0]);
+      if (g->fold) f(SinkFold<__nv_bfloat16>{hi, lo, g->nx, g->ny});
+      else f(SinkSplit<__nv_bfloat16>{hi, lo, g->nxp, g->nyp});
+    }
   }
 }
 

@@ -55,21 +55,27 @@ struct TensorMaps {
 
 namespace {
 
+// A K block is 128 bytes of every operand row (one 128B-swizzle atom row): BK = 64 bf16
+// elements, or 32 TF32 elements held in FP32 words (the TF32x3 split); byte sizes below are
+// the same for both.
 constexpr int BM = 128, BK = 64;
-constexpr int A_BYTES = BM * BK * 2;               // 16 KB per bf16 A box
+constexpr int A_BYTES = BM * 128;                  // 16 KB per A box
+template <typename E> constexpr int kb_elems() { return 128 / (int)sizeof(E); }
 // Tile shape per N-tile width: 128 (3 stages of 64 KB) or 64 (4 stages of 48 KB).
-template <int BN> struct Cfg {
-  static constexpr int B_BYTES = BN * BK * 2;
+template <int BN, typename E = __nv_bfloat16> struct Cfg {
+  static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // A_hi, A_lo, B_hi, B_lo
   static constexpr int STAGES = BN == 128 ? 3 : 4;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
   static constexpr uint32_t TMEM_COLS = BN;
-  // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M = BM, N = BN.
+  // instruction descriptor (kind::f16 with A = B = BF16 (1), or kind::tf32 with A = B = TF32
+  // (2)): D = F32, both K-major, M = BM, N = BN
+  static constexpr uint32_t FMT = sizeof(E) == 4 ? 2u : 1u;
   static constexpr uint32_t IDESC =
-      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+      (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   // the same with N = 2 BN: B_hi and B_lo, adjacent in a stage, read as one operand
   static constexpr uint32_t IDESC2 =
-      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 2) << 17) | ((uint32_t)(BM >> 4) << 24);
+      (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(BN >> 2) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 
 struct Epi {
@@ -147,6 +153,19 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+// TF32 operands (kind::tf32, K = 8 per instruction: 32 bytes of each row, as for bf16)
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+template <typename E>
+__device__ __forceinline__ void mma_op(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  if constexpr (sizeof(E) == 4) mma_tf32(tmem_d, a, b, idesc, accum);
+  else mma_bf16(tmem_d, a, b, idesc, accum);
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -340,7 +359,7 @@ struct SolveArgs {
   int R;                               // right-hand sides
   int nxp, nyp;                        // operand extents (= nx, ny when folded)
   int fold;
-  __nv_bfloat16 *op_hi[2], *op_lo[2];  // op[0]: [R][nyp][nxp], op[1]: [R][nxp][nyp]
+  void *op_hi[2], *op_lo[2];           // op[0]: [R][nyp][nxp], op[1]: [R][nxp][nyp] (bf16 or TF32 words)
   const float* scale;                  // [nyp][nxp]: (4/(nx ny)) / lambda, slot order when folded
   int final_mode;                      // 2: FP32 store into out [R][ny][nx]; 3: predictor-corrector mixing
   float* out;
@@ -468,16 +487,17 @@ template <int BN> struct SolveSmem {
   static constexpr int BYTES = BARS + 256 + 1024 /*alignment*/;
 };
 
-template <int BN, bool RES>
+template <int BN, bool RES, typename E>
 __global__ void __launch_bounds__(kSolveThreads, 1)
     k_dst_solve(const __grid_constant__ CUtensorMap a0h, const __grid_constant__ CUtensorMap a0l,
                 const __grid_constant__ CUtensorMap a1h, const __grid_constant__ CUtensorMap a1l,
                 const __grid_constant__ CUtensorMap bxh, const __grid_constant__ CUtensorMap bxl,
                 const __grid_constant__ CUtensorMap byh, const __grid_constant__ CUtensorMap byl,
                 const __grid_constant__ CUtensorMap scm, const SolveArgs a) {
-  using C = Cfg<BN>;
+  using C = Cfg<BN, E>;
   using L = SolveSmem<BN>;
   constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES;
+  constexpr int KE = kb_elems<E>();   // elements per K block
   extern __shared__ uint8_t smem_raw[];
   __shared__ int s_abort;
   const uint32_t raw = smem_u32(smem_raw);
@@ -522,7 +542,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
     P2 = ax ? a.nxp : a.nyp;
     mt = a.R * P1 / BM;
     tiles = mt * (P2 / BN);
-    nk = (a.fold ? P2 / 2 : P2) / BK;
+    nk = (a.fold ? P2 / 2 : P2) / KE;
   };
   // both axes' geometry and this CTA's first tile, computed before the first phase (after a
   // grid barrier they would sit on the path to the phase's first TMA issue)
@@ -538,14 +558,16 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
   bool go = true;
   if (a.pre) {
     const Geom& gm = a.pre == 1 ? a.sm.gm : a.sb.gm;
+    E* hi0 = reinterpret_cast<E*>(a.op_hi[0]);
+    E* lo0 = reinterpret_cast<E*>(a.op_lo[0]);
     if (a.fold) {
-      const SinkFold sink{a.op_hi[0], a.op_lo[0], a.nx, a.ny};
-      if (a.pre == 1) solve_sources<SinkFold, SrcMain<float>, 3>(gm, sink, a.sm);
-      else solve_sources<SinkFold, SrcBperp<float>, 2>(gm, sink, a.sb);
+      const SinkFold<E> sink{hi0, lo0, a.nx, a.ny};
+      if (a.pre == 1) solve_sources<SinkFold<E>, SrcMain<float>, 3>(gm, sink, a.sm);
+      else solve_sources<SinkFold<E>, SrcBperp<float>, 2>(gm, sink, a.sb);
     } else {
-      const SinkBF16 sink{a.op_hi[0], a.op_lo[0], a.nxp, a.nyp};
-      if (a.pre == 1) solve_sources<SinkBF16, SrcMain<float>, 3>(gm, sink, a.sm);
-      else solve_sources<SinkBF16, SrcBperp<float>, 2>(gm, sink, a.sb);
+      const SinkSplit<E> sink{hi0, lo0, a.nxp, a.nyp};
+      if (a.pre == 1) solve_sources<SinkSplit<E>, SrcMain<float>, 3>(gm, sink, a.sm);
+      else solve_sources<SinkSplit<E>, SrcBperp<float>, 2>(gm, sink, a.sb);
     }
     go = grid_barrier(a.gbar, (unsigned long long)gridDim.x + (unsigned)a.barrier_skew, a.status, abort_f);
   }
@@ -581,10 +603,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
           // MMA), so only a stage reused within the tile needs its release
           if (kb >= STAGES && !mbar_wait_a(empty0 + 8 * s, ((g / STAGES) - 1) & 1, a.status, abort_f)) break;
           mbar_expect_tx(fb, STAGE_BYTES);
-          tma_load_2d(st, tah, koff + kb * BK, m0, fb);
-          tma_load_2d(st + A_BYTES, tal, koff + kb * BK, m0, fb);
-          tma_load_2d(st + 2 * A_BYTES, tbh, kb * BK, n0, fb);
-          tma_load_2d(st + 2 * A_BYTES + C::B_BYTES, tbl, kb * BK, n0, fb);
+          tma_load_2d(st, tah, koff + kb * KE, m0, fb);
+          tma_load_2d(st + A_BYTES, tal, koff + kb * KE, m0, fb);
+          tma_load_2d(st + 2 * A_BYTES, tbh, kb * KE, n0, fb);
+          tma_load_2d(st + 2 * A_BYTES + C::B_BYTES, tbl, kb * KE, n0, fb);
         }
       } else if (warp == 1 && lane == 0) {
         // MMA issuer
@@ -597,12 +619,13 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
           const uint64_t ah = desc_k_sw128(st), al = desc_k_sw128(st + A_BYTES);
           const uint64_t bh = desc_k_sw128(st + 2 * A_BYTES);
           // columns [0, BN): A_hi B_hi + A_lo B_hi; columns [BN, 2 BN): A_hi B_lo (one MMA
-          // with N = 2 BN covers both A_hi products: the tensor core's cost here is per instruction)
+          // with N = 2 BN covers both A_hi products: the tensor core's cost here is per instruction);
+          // four 32-byte K steps per block (K = 16 bf16 or 8 TF32 each)
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k) {
+          for (int k = 0; k < 4; ++k) {
             const uint64_t off = (uint64_t)((k * 32) >> 4);
-            mma_bf16(tmem, ah + off, bh + off, C::IDESC2, (kb | k) != 0 ? 1u : 0u);
-            mma_bf16(tmem, al + off, bh + off, C::IDESC, 1u);
+            mma_op<E>(tmem, ah + off, bh + off, C::IDESC2, (kb | k) != 0 ? 1u : 0u);
+            mma_op<E>(tmem, al + off, bh + off, C::IDESC, 1u);
           }
           mma_commit(empty0 + 8 * s);
         }
@@ -627,8 +650,8 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
         // differences (column P1/2 + u)
         const bool odd = (ml & 1) != 0, wall = a.fold && (ml >> 1) == P1 / 4;
         const int fcol = a.fold ? (odd ? P1 / 2 + (ml >> 1) : (ml >> 1)) : ml;
-        __nv_bfloat16* oh = a.op_hi[along_x ? 1 : 0];
-        __nv_bfloat16* ol = a.op_lo[along_x ? 1 : 0];
+        E* oh = reinterpret_cast<E*>(a.op_hi[along_x ? 1 : 0]);
+        E* ol = reinterpret_cast<E*>(a.op_lo[along_x ? 1 : 0]);
         {
           float x[CH];
           tmem_ld_pair<BN, CH>(tl + (uint32_t)c0, x);
@@ -800,7 +823,8 @@ __device__ __forceinline__ void rs_epilogue(const SolveArgs& a, int mode, int s,
 // ([RPP rows][NR][n] floats), and then write the folded pairs (x_a + x_b, x_a - x_b) of
 // consecutive folded columns.
 template <typename F, int NR>
-__device__ __forceinline__ void solve_sources_rows(const Geom& gm, const F& f, const SinkFold& sink, float* S) {
+__device__ __forceinline__ void solve_sources_rows(const Geom& gm, const F& f, const SinkFold<__nv_bfloat16>& sink,
+                                                   float* S) {
   constexpr int NPT = 2;   // nodes per thread per row (n <= 2 x 256)
   constexpr int RPP = 4;   // rows per pass
   const int n = gm.nx, w = n / 2;
@@ -943,7 +967,8 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
   bool go = true;
   if (a.pre) {
     // (the stage ring is idle until the first product: it holds the staged sources)
-    const SinkFold sink{a.op_hi[0], a.op_lo[0], a.nx, a.ny};
+    const SinkFold<__nv_bfloat16> sink{reinterpret_cast<__nv_bfloat16*>(a.op_hi[0]),
+                                       reinterpret_cast<__nv_bfloat16*>(a.op_lo[0]), a.nx, a.ny};
     float* S = reinterpret_cast<float*>(basep + L::RING);   // 4 rows x 3 x 512 floats = 24 KB
     if (a.pre == 1) solve_sources_rows<SrcMain<float>, 3>(a.sm.gm, a.sm, sink, S);
     else solve_sources_rows<SrcBperp<float>, 2>(a.sb.gm, a.sb, sink, S);
@@ -1028,7 +1053,8 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
           __syncthreads();
           if (!*abort_f) rs_mix<BN, RES>(a, tile, s0, r, c0 - r * n);
         } else if (!*abort_f) {
-          rs_epilogue<CH>(a, mode, s, orow, r, i0, x, sc, a.op_hi[(p + 1) & 1], a.op_lo[(p + 1) & 1]);
+          rs_epilogue<CH>(a, mode, s, orow, r, i0, x, sc, reinterpret_cast<__nv_bfloat16*>(a.op_hi[(p + 1) & 1]),
+                          reinterpret_cast<__nv_bfloat16*>(a.op_lo[(p + 1) & 1]));
         }
       }
       kb_run += nk;
@@ -1064,13 +1090,17 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
                               const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// A split operand [rows][cols] in 128B-swizzled boxes of one K block (128 bytes) by box_rows:
+// bf16 elements, or (tf32) FP32 words.
 int make_map(EncodeFn enc, CUtensorMap* map, void* ptr, uint64_t rows, uint64_t cols, std::string& err,
-             uint32_t box_rows = 128) {
+             uint32_t box_rows = 128, bool tf32 = false) {
+  const uint32_t es = tf32 ? 4 : 2;
   cuuint64_t dims[2] = {cols, rows};
-  cuuint64_t strides[1] = {cols * 2};
-  cuuint32_t box[2] = {BK, box_rows};
+  cuuint64_t strides[1] = {cols * es};
+  cuuint32_t box[2] = {128 / es, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult rc = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  CUresult rc = enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (rc != CUDA_SUCCESS) {
     err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)rc) + ")";
@@ -1138,15 +1168,21 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
   g->tmaps = new TensorMaps();
   TensorMaps& t = *g->tmaps;
   int spare = 0;   // the residual-accumulating instances (the last P-C iteration): same resources
-  if (!size_solve(k_dst_solve<64, false>, SolveSmem<64>::BYTES, t.ctas[0]) ||
-      !size_solve(k_dst_solve<32, false>, SolveSmem<32>::BYTES, t.ctas[1]) ||
-      !size_solve(k_dst_solve<64, true>, SolveSmem<64>::BYTES, spare) ||
-      !size_solve(k_dst_solve<32, true>, SolveSmem<32>::BYTES, spare))
+  const bool tf = g->tf32 != 0;
+  if (tf ? (!size_solve(k_dst_solve<64, false, float>, SolveSmem<64>::BYTES, t.ctas[0]) ||
+            !size_solve(k_dst_solve<32, false, float>, SolveSmem<32>::BYTES, t.ctas[1]) ||
+            !size_solve(k_dst_solve<64, true, float>, SolveSmem<64>::BYTES, spare) ||
+            !size_solve(k_dst_solve<32, true, float>, SolveSmem<32>::BYTES, spare))
+         : (!size_solve(k_dst_solve<64, false, __nv_bfloat16>, SolveSmem<64>::BYTES, t.ctas[0]) ||
+            !size_solve(k_dst_solve<32, false, __nv_bfloat16>, SolveSmem<32>::BYTES, t.ctas[1]) ||
+            !size_solve(k_dst_solve<64, true, __nv_bfloat16>, SolveSmem<64>::BYTES, spare) ||
+            !size_solve(k_dst_solve<32, true, __nv_bfloat16>, SolveSmem<32>::BYTES, spare)))
     return 1;
   const char* bn = std::getenv("HQ_SOLVE_BN");
   t.wide_only = bn != nullptr && std::atoi(bn) == 64;
   const char* nors = std::getenv("HQ_NO_RS");
-  t.rs = g->fold && g->nx == g->ny && (g->nx == 256 || g->nx == 512) && !(nors && nors[0] == '1');
+  // (the resident fold matrix is bf16: as TF32 words it would need 256 KB of shared memory at 512^2)
+  t.rs = !tf && g->fold && g->nx == g->ny && (g->nx == 256 || g->nx == 512) && !(nors && nors[0] == '1');
   if (t.rs && (!size_solve(k_dst_solve_rs<64, false>, RsSmem<64>::BYTES, t.rs_ctas[0]) ||
                !size_solve(k_dst_solve_rs<32, false>, RsSmem<32>::BYTES, t.rs_ctas[1]) ||
                !size_solve(k_dst_solve_rs<64, true>, RsSmem<64>::BYTES, spare) ||
@@ -1154,18 +1190,18 @@ int dst_tc_init(hq_grid_s* g, std::string& err) {
     return 1;
   const uint64_t nxp = g->nxp, nyp = g->nyp;
   int bad = 0;
-  bad |= make_map(enc, &t.a0_hi, g->op_hi[0], kMaxRhs * nyp, nxp, err);
-  bad |= make_map(enc, &t.a0_lo, g->op_lo[0], kMaxRhs * nyp, nxp, err);
-  bad |= make_map(enc, &t.a1_hi, g->op_hi[1], kMaxRhs * nxp, nyp, err);
-  bad |= make_map(enc, &t.a1_lo, g->op_lo[1], kMaxRhs * nxp, nyp, err);
+  bad |= make_map(enc, &t.a0_hi, g->op_hi[0], kMaxRhs * nyp, nxp, err, 128, tf);
+  bad |= make_map(enc, &t.a0_lo, g->op_lo[0], kMaxRhs * nyp, nxp, err, 128, tf);
+  bad |= make_map(enc, &t.a1_hi, g->op_hi[1], kMaxRhs * nxp, nyp, err, 128, tf);
+  bad |= make_map(enc, &t.a1_lo, g->op_lo[1], kMaxRhs * nxp, nyp, err, 128, tf);
   // S_x, S_y (or the fold matrices, half as wide) as [rows][K]
   const uint64_t kx = g->fold ? nxp / 2 : nxp, ky = g->fold ? nyp / 2 : nyp;
   for (int i = 0; i < 2; ++i) {
     const uint32_t bn = i == 0 ? 64 : 32;
-    bad |= make_map(enc, &t.bx_hi[i], g->sx_hi, nxp, kx, err, bn);
-    bad |= make_map(enc, &t.bx_lo[i], g->sx_lo, nxp, kx, err, bn);
-    bad |= make_map(enc, &t.by_hi[i], g->sy_hi, nyp, ky, err, bn);
-    bad |= make_map(enc, &t.by_lo[i], g->sy_lo, nyp, ky, err, bn);
+    bad |= make_map(enc, &t.bx_hi[i], g->sx_hi, nxp, kx, err, bn, tf);
+    bad |= make_map(enc, &t.bx_lo[i], g->sx_lo, nxp, kx, err, bn, tf);
+    bad |= make_map(enc, &t.by_hi[i], g->sy_hi, nyp, ky, err, bn, tf);
+    bad |= make_map(enc, &t.by_lo[i], g->sy_lo, nyp, ky, err, bn, tf);
     bad |= make_map_plain(enc, &t.scale[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->f32_scale, nyp, nxp, BM, bn, err);
     if (g->scale_h)
       bad |= make_map_plain(enc, &t.scale_h[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g->scale_h, nyp, nxp, BM, bn, err);
@@ -1259,8 +1295,11 @@ void solve_fused(hq_grid_s* g, int R, int final_mode, int last, cudaStream_t s, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   // a launch error is reported by the caller's launch check
-  auto kern = a.rsum ? (narrow ? k_dst_solve<32, true> : k_dst_solve<64, true>)
-                     : (narrow ? k_dst_solve<32, false> : k_dst_solve<64, false>);
+  auto kern = g->tf32 ? (a.rsum ? (narrow ? k_dst_solve<32, true, float> : k_dst_solve<64, true, float>)
+                                : (narrow ? k_dst_solve<32, false, float> : k_dst_solve<64, false, float>))
+                      : (a.rsum ? (narrow ? k_dst_solve<32, true, __nv_bfloat16> : k_dst_solve<64, true, __nv_bfloat16>)
+                                : (narrow ? k_dst_solve<32, false, __nv_bfloat16>
+                                          : k_dst_solve<64, false, __nv_bfloat16>));
   cudaLaunchKernelEx(&cfg, kern, t.a0_hi, t.a0_lo, t.a1_hi, t.a1_lo, t.bx_hi[v], t.bx_lo[v], t.by_hi[v], t.by_lo[v],
                      shifted ? t.scale_h[v] : t.scale[v], a);
 }

@@ -17,6 +17,11 @@ LIB_PATH = os.path.join(_PKG, "libhq.so")
 
 HQ_PREC_FP64 = 0
 HQ_PREC_FP32_BF16X3 = 1
+HQ_PREC_FP32_TF32X3 = 2
+# precision names of Grid: "fp64", "fp32" (= "bf16x3", the FP32 path with bf16x3 tensor-core DST
+# operands) and "tf32x3" (the same FP32 path with TF32x3 operands)
+PRECISIONS = {"fp64": HQ_PREC_FP64, "fp32": HQ_PREC_FP32_BF16X3, "bf16x3": HQ_PREC_FP32_BF16X3,
+              "tf32x3": HQ_PREC_FP32_TF32X3}
 STATUS = {0: "HQ_OK", 1: "HQ_ERR_ARG", 2: "HQ_ERR_CUDA", 3: "HQ_ERR_OOM", 4: "HQ_ERR_NUMERIC",
           5: "HQ_ERR_TIMEOUT", 6: "HQ_ERR_STATE", 7: "HQ_ERR_UNSUPPORTED"}
 FIELDS = ("rho", "jx", "jy", "jz", "chi", "psi", "exmby", "eypbx", "ez", "bx", "by", "bz")
@@ -165,6 +170,8 @@ class Grid:
 
     def __init__(self, params: dict, precision: str = "fp64", stream: Optional[torch.cuda.Stream] = None):
         lib = load()
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
         self.precision = precision
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         prof = params.get("radial_profile")
@@ -192,7 +199,7 @@ class Grid:
             len(prof) if prof is not None else 0, float(params.get("profile_rmax", 0.0)),
             float(params.get("n0_scale", 1.0)), int(params.get("n_pc_iter", 5)), float(params.get("pc_mix", 0.05)),
             float(params.get("psi_guard", 0.02)),
-            HQ_PREC_FP64 if precision == "fp64" else HQ_PREC_FP32_BF16X3,
+            PRECISIONS[precision],
             {"pc": 0, "explicit": 1}[params.get("bperp_solver", "pc")], int(params.get("resort_every", 0)),
             int(params.get("deterministic", 0)),
             C.cast(self._sp, C.POINTER(SpeciesDesc)) if sps else None, len(sps), int(params.get("pc_residuals", 0)))

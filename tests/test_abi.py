@@ -57,6 +57,24 @@ def test_bad_descriptor_is_rejected(lib):
     assert b"shape_order" in lib.hq_last_error(None)
 
 
+def test_precision_values(lib):
+    """The precisions the header declares, the binding's names for them, and an unknown value
+    refused as an argument error before any device work."""
+    from paper_2109_10277_gb300 import hq
+    text = open(os.path.join(ROOT, "include", "hq.h")).read()
+    for name, val in (("HQ_PREC_FP64", 0), ("HQ_PREC_FP32_BF16X3", 1), ("HQ_PREC_FP32_TF32X3", 2)):
+        assert re.search(rf"\b{name} = {val}\b", text), name
+        assert getattr(hq, name) == val
+    assert hq.PRECISIONS["tf32x3"] == 2 and hq.PRECISIONS["fp32"] == 1
+    d = hq.GridDesc(64, 64, 8, -1, 1, -1, 1, 0, 1, 1, 1, 1, None, 0, 0.0, 1.0, 5, 0.05, 0.02, 3)
+    h = C.c_void_p()
+    assert lib.hq_grid_create(C.byref(d), None, C.byref(h)) == 1
+    assert b"precision" in lib.hq_last_error(None)
+    with pytest.raises(ValueError):
+        hq.Grid(dict(nx=64, ny=64, nzeta=8, xmin=-1, xmax=1, ymin=-1, ymax=1, zeta_min=0, zeta_max=1),
+                precision="fp16")
+
+
 @pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU refusal")
 def test_no_device_fails_loudly(lib):
     from paper_2109_10277_gb300 import hq
