@@ -155,10 +155,12 @@ def folded_case():
     return g, d, w, oracle_grads(g, d, w, "mean+rms")
 
 
-@pytest.mark.parametrize("precision,tol,bn", [("fp64", 1e-5, None), ("fp32", 1e-3, None), ("fp32", 1e-3, "64")])
+@pytest.mark.parametrize("precision,tol,bn", [("fp64", 1e-5, None), ("fp32", 1e-3, None), ("fp32", 1e-3, "64"),
+                                               ("tf32x3", 1e-3, None)])
 def test_adjoint_folded_path(hq, monkeypatch, folded_case, precision, tol, bn):
     """FP32: the folded solve on 128 x 32 tiles (default) and on 128 x 64 tiles (HQ_SOLVE_BN=64),
-    two checkpoint segments (recompute); FP64 the same case through its FFT DST."""
+    and with TF32x3 operands; two checkpoint segments (recompute); FP64 the same case through its
+    FFT DST."""
     g, d, w, (L0, gd0, gw0, gn0, gp0) = folded_case
     if bn:
         monkeypatch.setenv("HQ_SOLVE_BN", bn)
