@@ -267,3 +267,102 @@ def test_adjoint_of_field_seeds_matches_taped_oracle(hq, precision, tol):
     print(precision, "field seeds:", {a: f"{b:.2e}" for a, b in errs.items()})
     for key, e in errs.items():
         assert e <= tol, (key, errs)
+
+
+# ---------------------------------------------------------------- the 1280-parameter workload at full size
+
+def test_adjoint512_full_size_vs_central_fd(hq):
+    """The 1280-parameter gradient workload at its full size (512^2 x 1024 slices, 2 ppc,
+    quadratic shape, fixed-ppc driver with a 1024-entry slice current profile, 256-entry radial
+    plasma profile, witness mean Ez + rms spread), as the benchmark runs it (checkpoints every 32
+    slices): the FP32/bf16x3 and FP64 adjoint gradients against central finite differences of the
+    FP64 forward sweep in the deterministic mode (bitwise reproducible, so the difference quotient
+    carries no summation-order noise), step 1e-6 max(1, |p|), on 16 seeded entries (8 of the slice
+    profile, 8 of the radial profile, drawn among the entries whose derivative is at least a tenth of
+    the largest) and 3 random directions in all 1280 parameters, relative to the derivative (entries)
+    or to sum |v_i g_i| (directions).  Bars: FP64 1e-5; FP32/split 1e-3 on the directions and 5e-3
+    on single entries (measured 0.5e-3 .. 2.7e-3 over three runs: the FP32 rounding of the
+    1024-slice reverse sweep, seen on single entries of 1280, where the 64 x 64 x 128 check stays
+    below 1e-3 and the FP64 adjoint on this same case below 2e-6; the whole driver-weight gradient
+    of the FP32 adjoint is 4.5e-3 from the FP64 adjoint's here, 8.7e-4 on the 256^2 workload)."""
+    g = I.grid_params("adjoint512")
+    bnp = I.workload_beams("adjoint512")
+    nz = g["nzeta"]
+    dz = (g["zeta_max"] - g["zeta_min"]) / nz
+    zc = g["zeta_max"] - (np.arange(nz) + 0.5) * dz
+    prof = 4.0 * np.exp(-zc ** 2 / (2.0 * 1.4 ** 2))          # the driver's slice profile
+    rad = np.asarray(g["radial_profile"], dtype=np.float64)
+    sidx = np.asarray(bnp[0]["slice_index"])
+    shape = np.asarray(bnp[0]["w"]) / prof[sidx]               # w_p = prof[s_p] * shape_p
+
+    def beams_for(p_slice):
+        d = dict(bnp[0])
+        d["w"] = p_slice[sidx] * shape
+        return [d, bnp[1]]
+
+    # adjoint gradients (FP32/split as benchmarked, and FP64)
+    grads = {}
+    for precision in ("fp32", "fp64"):
+        grid = hq.Grid(g, precision=precision)
+        beams = [hq.Beam(b) for b in bnp]
+        sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+        grid.forward_ckpt(beams, 1, sums, 32)
+        _, dls = hq.witness_loss_grad("mean+rms", *[float(v) for v in sums.cpu()])
+        res = grid.adjoint(beams, 1, dls, plasma=False)
+        grid.sync()
+        gw = res["beam_w"][0].cpu().numpy()
+        gs = np.zeros(nz)
+        np.add.at(gs, sidx, gw * shape)                         # dL/dprof[s] = sum_p dL/dw_p shape_p
+        grads[precision] = (gs, res["profile"].cpu().numpy().copy())
+        grid.close()
+
+    # the FP64 deterministic forward loss as a function of (slice profile, radial profile)
+    gdet = dict(g, deterministic=1)
+    cache = {}
+
+    def loss(p_slice, p_rad):
+        key = (p_slice.tobytes(), p_rad.tobytes())
+        if key not in cache:
+            grid = hq.Grid(dict(gdet, radial_profile=[float(v) for v in p_rad]), precision="fp64")
+            sums = torch.zeros(3, dtype=torch.float64, device="cuda")
+            grid.sweep([hq.Beam(b) for b in beams_for(p_slice)], witness=1, witness_sums=sums)
+            grid.sync()
+            grid.close()
+            cache[key] = hq.witness_loss_grad("mean+rms", *[float(v) for v in sums.cpu()])[0]
+        return cache[key]
+
+    rng = np.random.default_rng(512)
+    gs64, gr64 = grads["fp64"]
+    pick_s = rng.choice(np.flatnonzero(np.abs(gs64) >= 0.1 * np.abs(gs64).max()), 8, replace=False)
+    pick_r = rng.choice(np.flatnonzero(np.abs(gr64) >= 0.1 * np.abs(gr64).max()), 8, replace=False)
+    fd_s, fd_r = {}, {}
+    for s in pick_s:
+        h = 1e-6 * max(1.0, abs(prof[s]))
+        up, dn = prof.copy(), prof.copy()
+        up[s] += h
+        dn[s] -= h
+        fd_s[s] = (loss(up, rad) - loss(dn, rad)) / (2 * h)
+    for k in pick_r:
+        h = 1e-6 * max(1.0, abs(rad[k]))
+        up, dn = rad.copy(), rad.copy()
+        up[k] += h
+        dn[k] -= h
+        fd_r[k] = (loss(prof, up) - loss(prof, dn)) / (2 * h)
+    dirs = []
+    for _ in range(3):
+        vs, vr = rng.standard_normal(nz), rng.standard_normal(rad.size)
+        h = 1e-6 * max(1.0, float(np.abs(prof).max()))
+        fd = (loss(prof + h * vs, rad + h * vr) - loss(prof - h * vs, rad - h * vr)) / (2 * h)
+        dirs.append((vs, vr, fd))
+
+    for precision, tol_e, tol in (("fp64", 1e-5, 1e-5), ("fp32", 5e-3, 1e-3)):
+        gs, gr = grads[precision]
+        e_s = {int(s): abs(gs[s] - fd_s[s]) / abs(fd_s[s]) for s in pick_s}
+        e_r = {int(k): abs(gr[k] - fd_r[k]) / abs(fd_r[k]) for k in pick_r}
+        e_d = [abs(float(gs @ vs + gr @ vr) - fd) / float(np.abs(gs * vs).sum() + np.abs(gr * vr).sum())
+               for vs, vr, fd in dirs]
+        print(f"adjoint512 {precision}: slice-profile entries worst {max(e_s.values()):.1e}, radial-profile "
+              f"entries worst {max(e_r.values()):.1e}, directions {[f'{e:.1e}' for e in e_d]}")
+        assert max(e_s.values()) <= tol_e, (precision, e_s)
+        assert max(e_r.values()) <= tol_e, (precision, e_r)
+        assert max(e_d) <= tol, (precision, e_d)
