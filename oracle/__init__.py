@@ -37,7 +37,9 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                        order in n_b, mobile light ions raise the plasma frequency by sqrt(1 + m_e/M)
   slice loop / sweep   SliceLoop.slice is the per-slice body the sweep and the temporal pipeline
                        drive; the pipeline over CPU ranks reproduces the serial loop bit for bit
-  blowout-regime physics (cfg 512^2 n_b=5): parity unpinned beyond the checks above
+  blowout regime        inside the electron-free channel behind a dense driver the transverse
+                       force ExmBy is x/2 and Ez is flat across it (ion-channel focusing);
+                       beyond that the blowout-regime physics (512^2 n_b=5) is parity unpinned
   working_precision    a test knob: the same steps in another float type (rounding floors)
 """
 from .qsa import *  # noqa: F401,F403
