@@ -62,7 +62,7 @@ void free_all(hq_grid_s* g) {
     hq::Plasma<float>& p = g->p32;
     if (!g->fp64) {
       // x, y, psi, alive are shared with p64 storage (freed above); free the typed arrays
-      F(p.ux); F(p.uy); F(p.w); F(p.hist); F(p.cell); F(p.fx); F(p.fy); F(p.opp); F(p.hsum);
+      F(p.ux); F(p.uy); F(p.w); F(p.hist); F(p.cell); F(p.fx); F(p.fy); F(p.opp); F(p.hsum); F(p.f4);
     }
   }
   if (g->det_arena) {
@@ -311,7 +311,7 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
     // the last iteration's mixing adds its residual sums to this slice's pair
     g->pc_rsum = last && g->d_pcres ? g->d_pcres + 2 * kResLanes * (int64_t)slice : nullptr;   // (opt-in)
     tape_b_iterate(g, m);
-    { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, s); }
+    { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, m, s); }
     if (g->det) launch_fx_decode(g, g->tj, 2 * g->nnode, nullptr, s);
     if (fused_src) {
       Prof p(g, HQ_K_DST, 1);   // sources, solve and the mixing in one launch
@@ -988,6 +988,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     HQ_ALLOC(g->p32.hist, 4 * np * kRing * 5);
     HQ_ALLOC(g->p32.cell, 4 * np); HQ_ALLOC(g->p32.fx, 4 * np); HQ_ALLOC(g->p32.fy, 4 * np); HQ_ALLOC(g->p32.opp, 4 * np);
     HQ_ALLOC(g->p32.hsum, 4 * np * 5);
+    HQ_ALLOC(g->p32.f4, 16 * np);
   }
   if (d.resort_every > 0) {
     HQ_ALLOC(g->porigin, 4 * np);
@@ -1138,6 +1139,8 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     // folded DST-I (half the contraction) when both extents are multiples of 128
     const char* nf = std::getenv("HQ_NO_FOLD");
     g->fold = (g->nx % 128 == 0 && g->ny % 128 == 0 && !(nf && nf[0] == '1')) ? 1 : 0;
+    const char* nf4 = std::getenv("HQ_NO_F4CACHE");
+    g->no_f4 = nf4 && nf4[0] == '1';
     const char* ss = std::getenv("HQ_SEPARATE_SRC");
     g->sep_src = (ss && ss[0] == '1') ? 1 : 0;
     const char* fb = std::getenv("HQ_FAULT_BARRIER");

@@ -80,6 +80,9 @@ template <typename T> struct Plasma {
   // f_{i-k}, [5][n]: the same for all predictor-corrector trial passes of the slice, so they
   // read 5 values instead of the 20 of the ring (written by the final pass).
   float* hsum;
+  // FP32 mode: ExmBy, EypBx, Ez, Bz gathered at the slice's first predictor-corrector iteration,
+  // read by the later ones of the same slice (only Bx, By change between them)
+  float4* f4;
   // With the re-sort (resort_every > 0): each particle's index in the initial placement (its
   // ion's position is recomputed from it); null otherwise (the array index is that index).
   int32_t* origin;
@@ -232,6 +235,7 @@ struct hq_grid_s {
   float* psrc[2];                            // FP32 mode: psi source rho - J_z of dep[0], dep[1]
   unsigned long long* d_gbar;                // grid-barrier counter of the fused solve kernel (zero between launches)
   int fault_barrier;                         // HQ_FAULT_BARRIER=1: the solve's first grid barrier never fills
+  int no_f4;                                 // HQ_NO_F4CACHE=1: every trial pass gathers all six fields
   int sep_src;                               // HQ_SEPARATE_SRC=1: source kernels ahead of the solve launches
 
   // beams
@@ -292,7 +296,7 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // particles
 template <typename T> void launch_plasma_init(const hq_grid_s* g, cudaStream_t s);
 template <typename T> void launch_deposit_initial(const hq_grid_s* g, void* dep, void* chi, int ion_only, cudaStream_t s);
-template <typename T> void launch_trial_pass(const hq_grid_s* g, int slice, cudaStream_t s);
+template <typename T> void launch_trial_pass(const hq_grid_s* g, int slice, int iter, cudaStream_t s);
 template <typename T> void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cudaStream_t s);
 // fields
 template <typename T> void launch_reset_dep(const hq_grid_s* g, void* dep, void* chi, cudaStream_t s);

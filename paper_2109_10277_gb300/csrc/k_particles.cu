@@ -81,6 +81,29 @@ __device__ __forceinline__ F6<T> gather6(const T* __restrict__ gf, const T* __re
   return F;
 }
 
+// Bx, By alone at the same stencil, accumulated node by node exactly as gather6 does (the same
+// products and sums in the same order, so the result is bit for bit gather6's v[3], v[4]).
+template <int P>
+__device__ __forceinline__ float2 gather_bperp(const float* __restrict__ bm, int nx, int ny, int ix0, int iy0,
+                                               const float* wx, const float* wy) {
+  float bx = 0.0f, by = 0.0f;
+#pragma unroll
+  for (int b = 0; b <= P; ++b) {
+    const int iy = iy0 + b;
+    if (!in_interior(iy, ny)) continue;
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      const int ix = ix0 + a;
+      if (!in_interior(ix, nx)) continue;
+      const float2 c = __ldg(reinterpret_cast<const float2*>(bm + ((int64_t)iy * nx + ix) * 2));
+      const float wgt = wx[a] * wy[b];
+      bx += wgt * c.x;
+      by += wgt * c.y;
+    }
+  }
+  return make_float2(bx, by);
+}
+
 // zeta-derivatives of a plasma particle, Sec. 3.2; opp = 1 + Psi.  Written for an electron
 // (q/M = -1); a multi-species grid (MS) scales the momentum and Psi rates by mqm = -q/M.
 template <typename T, bool MS = false>
@@ -330,8 +353,11 @@ __global__ void k_species_c0(Plasma<float> pl, Geom gm, double* out, SpeciesTab 
 
 // ---------------------------------------------------------------- trial pass (predictor-corrector)
 // Gather with B^(m-1), AB5 trial step to slice i+1, deposit J_perp of the trial
-// particles into tj (Sec. 3.2, predictor-corrector field solver).
-template <int P, typename T, bool CACHE, bool MS>
+// particles into tj (Sec. 3.2, predictor-corrector field solver).  Within a slice only Bx, By
+// change between the iterations: the FP32 path gathers the other four fields (ExmBy, EypBx,
+// Ez, Bz) in the first iteration and keeps them per particle in pl.f4 (fmode 1), and the later
+// iterations read them back and gather Bx, By alone (FM 2); FM 0 gathers all six.
+template <int P, typename T, bool CACHE, bool MS, int FM>
 __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf, const T* __restrict__ bm,
                                                          V2<T>* tj, int slice, double guard, SpeciesTab tab) {
   pdl_trigger();
@@ -359,7 +385,15 @@ __global__ void __launch_bounds__(kThreads) k_trial_pass(Plasma<T> pl, Geom gm, 
     opp = T(1.0 + pl.psi[p]);
   }
   const T ux = pl.ux[p], uy = pl.uy[p];
-  const F6<T> F = gather6<P, T>(gf, bm, gm.nx, gm.ny, ix0, iy0, wx, wy);
+  F6<T> F;
+  if constexpr (CACHE && FM == 2) {
+    const float4 c = pl.f4[p];
+    const float2 b = gather_bperp<P>(bm, gm.nx, gm.ny, ix0, iy0, wx, wy);
+    F.v[0] = c.x; F.v[1] = c.y; F.v[2] = c.z; F.v[3] = b.x; F.v[4] = b.y; F.v[5] = c.w;
+  } else {
+    F = gather6<P, T>(gf, bm, gm.nx, gm.ny, ix0, iy0, wx, wy);
+    if constexpr (CACHE && FM == 1) pl.f4[p] = make_float4(F.v[0], F.v[1], F.v[2], F.v[5]);
+  }
   T f[5];
   derivs<T, MS>(ux, uy, opp, F, f, sc.mqm);
   const T dz = CACHE ? T(gm.f_dz) : T(gm.dzeta);
@@ -788,16 +822,23 @@ void launch_species_c0(const hq_grid_s* g, double* out, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_trial_pass(const hq_grid_s* g, int slice, cudaStream_t s) {
+void launch_trial_pass(const hq_grid_s* g, int slice, int iter, cudaStream_t s) {
   const unsigned nb = blocks_for(g->np);
+  // FP32: the first predictor-corrector iteration of a slice keeps the four static gathered
+  // fields per particle, the others read them (HQ_NO_F4CACHE=1: every pass gathers all six)
+  const int fmode = (sizeof(T) == 8 || g->no_f4) ? 0 : (iter == 0 ? 1 : 2);
   const T* gf = reinterpret_cast<const T*>(g->gf);
   const T* bm = reinterpret_cast<const T*>(g->bm);
   V2<T>* tj = reinterpret_cast<V2<T>*>(g->tj);
   constexpr bool C = sizeof(T) == 4;
   const double gd = g->d.psi_guard;
   HQ_PDISPATCH(g->d.shape_order, g->multi,
-               (launch_pdl(k_trial_pass<P, T, C, M>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, tj, slice,
-                           gd, g->sp)));
+               (fmode == 2 ? launch_pdl(k_trial_pass<P, T, C, M, C ? 2 : 0>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom,
+                                        gf, bm, tj, slice, gd, g->sp)
+                : fmode == 1 ? launch_pdl(k_trial_pass<P, T, C, M, C ? 1 : 0>, nb, kThreads, 0, s, plasma_of<T>(g),
+                                          g->geom, gf, bm, tj, slice, gd, g->sp)
+                             : launch_pdl(k_trial_pass<P, T, C, M, 0>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf,
+                                          bm, tj, slice, gd, g->sp)));
 }
 
 template <typename T>
@@ -829,8 +870,8 @@ template void launch_plasma_init<float>(const hq_grid_s*, cudaStream_t);
 template void launch_plasma_init<double>(const hq_grid_s*, cudaStream_t);
 template void launch_deposit_initial<float>(const hq_grid_s*, void*, void*, int, cudaStream_t);
 template void launch_deposit_initial<double>(const hq_grid_s*, void*, void*, int, cudaStream_t);
-template void launch_trial_pass<float>(const hq_grid_s*, int, cudaStream_t);
-template void launch_trial_pass<double>(const hq_grid_s*, int, cudaStream_t);
+template void launch_trial_pass<float>(const hq_grid_s*, int, int, cudaStream_t);
+template void launch_trial_pass<double>(const hq_grid_s*, int, int, cudaStream_t);
 template void launch_final_pass<float>(const hq_grid_s*, int, void*, void*, cudaStream_t);
 template void launch_final_pass<double>(const hq_grid_s*, int, void*, void*, cudaStream_t);
 

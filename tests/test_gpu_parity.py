@@ -616,6 +616,27 @@ def test_sources_in_solve_launch_match_separate_kernels(hq, monkeypatch):
         assert dev <= max(10 * floor, 1e-6), (k, dev, floor)
 
 
+def test_trial_field_cache_matches_full_gather(hq, monkeypatch):
+    """FP32: the predictor-corrector trial passes after a slice's first read ExmBy, EypBx, Ez, Bz
+    back from the per-particle copy the first one kept and gather Bx, By alone; the sweep matches
+    the one whose every trial pass gathers all six fields (HQ_NO_F4CACHE=1) within the run-to-run
+    floor of the FP32 atomics (quadratic shape, 2 ppc, a driver strong enough to move particles
+    across cells within the predictor-corrector)."""
+    g = dict(I.scaled_grid(I.grid_params("linear64"), 128, 128, 64), shape_order=2, ppc_x=2)
+    beams = [I.random_beam(100_000, 0.3, 0.3, 1.0, 2.0, energy_spread=1e-3)]
+    outs = {}
+    for mode in ("cached", "cached2", "full"):
+        if mode == "full":
+            monkeypatch.setenv("HQ_NO_F4CACHE", "1")
+        outs[mode] = run_gpu(hq, g, beams, "fp32", fields=("ez", "psi", "bx", "by"))[0]
+        monkeypatch.delenv("HQ_NO_F4CACHE", raising=False)
+    for k in ("ez", "psi", "bx", "by"):
+        floor = float(peak_err(outs["cached2"][k], outs["cached"][k]).max())
+        dev = float(peak_err(outs["full"][k], outs["cached"][k]).max())
+        print(f"cached vs full gather {k}: {dev:.1e} (run-to-run {floor:.1e})")
+        assert dev <= max(10 * floor, 1e-6), (k, dev, floor)
+
+
 @pytest.mark.parametrize("n", [256, 512])
 def test_resident_fold_matrix_solve_matches_streamed(hq, monkeypatch, n):
     """FP32 square grids of 256 and 512 cells run the solve that keeps each CTA's slice of the
