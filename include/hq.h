@@ -38,9 +38,10 @@
  *                  stream instead of beside the final pass on a second stream
  *   HQ_SEPARATE_SRC=1  FP32: the psi/Ez/Bz and B_perp sources are formed by kernels of
  *                  their own ahead of each solve instead of in the solve's first phase
- *   HQ_NO_F4CACHE=1  FP32: every predictor-corrector trial pass gathers all six fields (by
- *                  default the first of a slice keeps ExmBy, EypBx, Ez, Bz per particle and
- *                  the later ones gather Bx, By alone; the results are bit for bit the same)
+ *   HQ_NO_F4CACHE=1  FP32: every predictor-corrector trial pass and the final pass gather all
+ *                  six fields (by default the first trial pass of a slice keeps ExmBy, EypBx,
+ *                  Ez, Bz per particle and the later passes of the slice gather Bx, By alone;
+ *                  the gathered values are bit for bit the same)
  * and one switch for testing the failure path, which does change results:
  *   HQ_FAULT_BARRIER=1  (FP32 grids) the first grid barrier of every tensor-core solve
  *                  waits for one CTA more than the launch has, so its bounded wait runs

@@ -312,6 +312,7 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
     g->pc_rsum = last && g->d_pcres ? g->d_pcres + 2 * kResLanes * (int64_t)slice : nullptr;   // (opt-in)
     tape_b_iterate(g, m);
     { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, m, s); }
+    if (m == 0) g->f4_slice = (g->fp64 || g->no_f4) ? -1 : slice;   // the final pass may reuse it
     if (g->det) launch_fx_decode(g, g->tj, 2 * g->nnode, nullptr, s);
     if (fused_src) {
       Prof p(g, HQ_K_DST, 1);   // sources, solve and the mixing in one launch
@@ -344,7 +345,7 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
 template <typename T>
 void final_pass(hq_grid_s* g, int slice_from, int parity) {
   Prof p(g, HQ_K_FINAL, 1);
-  launch_final_pass<T>(g, slice_from, g->dep[parity], g->chi[parity], g->stream);
+  launch_final_pass<T>(g, slice_from, g->dep[parity], g->chi[parity], g->f4_slice == slice_from, g->stream);
   if (g->det) {
     launch_fx_decode(g, g->dep[parity], 4 * g->nnode, nullptr, g->stream);
     launch_fx_decode(g, g->chi[parity], g->nnode, nullptr, g->stream);
@@ -355,6 +356,7 @@ template <typename T>
 void advance_impl(hq_grid_s* g, int slice) {
   cudaStream_t s = g->stream;
   if (slice == 0) {
+    g->f4_slice = -1;
     Prof p(g, HQ_K_OTHER, g->bjp ? 9 : 8);
     launch_reset_dep<T>(g, g->dep[0], g->chi[0], s);
     launch_plasma_init<T>(g, s);
@@ -929,6 +931,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
   g->dev = dev;
   g->fp64 = d.precision == HQ_PREC_FP64;
   g->tf32 = d.precision == HQ_PREC_FP32_TF32X3;
+  g->f4_slice = -1;
   g->explicit_b = d.bperp_solver == HQ_BPERP_EXPLICIT;
   g->nx = d.nx; g->ny = d.ny; g->nz = d.nzeta;
   g->nnode = (int64_t)d.nx * d.ny;

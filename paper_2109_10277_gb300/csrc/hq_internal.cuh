@@ -236,6 +236,7 @@ struct hq_grid_s {
   unsigned long long* d_gbar;                // grid-barrier counter of the fused solve kernel (zero between launches)
   int fault_barrier;                         // HQ_FAULT_BARRIER=1: the solve's first grid barrier never fills
   int no_f4;                                 // HQ_NO_F4CACHE=1: every trial pass gathers all six fields
+  int f4_slice;                              // slice whose first trial pass filled p32.f4 (-1: none)
   int sep_src;                               // HQ_SEPARATE_SRC=1: source kernels ahead of the solve launches
 
   // beams
@@ -297,7 +298,8 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 template <typename T> void launch_plasma_init(const hq_grid_s* g, cudaStream_t s);
 template <typename T> void launch_deposit_initial(const hq_grid_s* g, void* dep, void* chi, int ion_only, cudaStream_t s);
 template <typename T> void launch_trial_pass(const hq_grid_s* g, int slice, int iter, cudaStream_t s);
-template <typename T> void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cudaStream_t s);
+template <typename T> void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, bool f4,
+                                             cudaStream_t s);
 // fields
 template <typename T> void launch_reset_dep(const hq_grid_s* g, void* dep, void* chi, cudaStream_t s);
 template <typename T> void launch_src_main(const hq_grid_s* g, const void* dep, cudaStream_t s);

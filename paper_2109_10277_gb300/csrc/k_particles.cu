@@ -647,7 +647,9 @@ template <int P, typename T> constexpr int final_min_blocks() {
   return sizeof(T) == 4 ? 65536 / ((P == 3 ? 64 : 48) * kThreads) : 1;
 }
 
-template <int P, typename T, bool CACHE, bool MS>
+// FM 2 (FP32, after a predictor-corrector whose first iteration kept the slice's ExmBy, EypBx,
+// Ez, Bz per particle in pl.f4): read those back and gather the converged Bx, By alone.
+template <int P, typename T, bool CACHE, bool MS, int FM>
 __global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pass(Plasma<T> pl, Geom gm, const T* __restrict__ gf, const T* __restrict__ bm,
                                                          V4<T>* dep, T* chi, float* ps, PpcInfo pc, int slice,
                                                          double guard, unsigned long long* removed, SpeciesTab tab) {
@@ -690,7 +692,14 @@ __global__ void __launch_bounds__(kThreads, final_min_blocks<P, T>()) k_final_pa
     opp = T(1.0 + pl.psi[p]);
   }
   const T ux = pl.ux[p], uy = pl.uy[p];
-  const F6<T> F = gather6<P, T>(gf, bm, gm.nx, gm.ny, ix0, iy0, wx, wy);
+  F6<T> F;
+  if constexpr (CACHE && FM == 2) {
+    const float4 c = pl.f4[p];
+    const float2 b = gather_bperp<P>(bm, gm.nx, gm.ny, ix0, iy0, wx, wy);
+    F.v[0] = c.x; F.v[1] = c.y; F.v[2] = c.z; F.v[3] = b.x; F.v[4] = b.y; F.v[5] = c.w;
+  } else {
+    F = gather6<P, T>(gf, bm, gm.nx, gm.ny, ix0, iy0, wx, wy);
+  }
   T f[5];
   derivs<T, MS>(ux, uy, opp, F, f, sc.mqm);
   T comb[5];
@@ -842,7 +851,7 @@ void launch_trial_pass(const hq_grid_s* g, int slice, int iter, cudaStream_t s) 
 }
 
 template <typename T>
-void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cudaStream_t s) {
+void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, bool f4, cudaStream_t s) {
   const unsigned nb = blocks_for(g->np);
   const T* gf = reinterpret_cast<const T*>(g->gf);
   const T* bm = reinterpret_cast<const T*>(g->bm);
@@ -861,8 +870,10 @@ void launch_final_pass(const hq_grid_s* g, int slice, void* dep, void* chi, cuda
   pc.finv_x = (float)pc.inv_x;
   pc.finv_y = (float)pc.inv_y;
   HQ_PDISPATCH(g->d.shape_order, g->multi,
-               (launch_pdl(k_final_pass<P, T, C, M>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm, d, c, ps, pc,
-                           slice, gd, rm, g->sp)));
+               (f4 && C ? launch_pdl(k_final_pass<P, T, C, M, C ? 2 : 0>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom,
+                                     gf, bm, d, c, ps, pc, slice, gd, rm, g->sp)
+                        : launch_pdl(k_final_pass<P, T, C, M, 0>, nb, kThreads, 0, s, plasma_of<T>(g), g->geom, gf, bm,
+                                     d, c, ps, pc, slice, gd, rm, g->sp)));
 }
 #undef HQ_PDISPATCH
 
@@ -872,7 +883,7 @@ template void launch_deposit_initial<float>(const hq_grid_s*, void*, void*, int,
 template void launch_deposit_initial<double>(const hq_grid_s*, void*, void*, int, cudaStream_t);
 template void launch_trial_pass<float>(const hq_grid_s*, int, int, cudaStream_t);
 template void launch_trial_pass<double>(const hq_grid_s*, int, int, cudaStream_t);
-template void launch_final_pass<float>(const hq_grid_s*, int, void*, void*, cudaStream_t);
-template void launch_final_pass<double>(const hq_grid_s*, int, void*, void*, cudaStream_t);
+template void launch_final_pass<float>(const hq_grid_s*, int, void*, void*, bool, cudaStream_t);
+template void launch_final_pass<double>(const hq_grid_s*, int, void*, void*, bool, cudaStream_t);
 
 }  // namespace hq

@@ -617,9 +617,9 @@ def test_sources_in_solve_launch_match_separate_kernels(hq, monkeypatch):
 
 
 def test_trial_field_cache_matches_full_gather(hq, monkeypatch):
-    """FP32: the predictor-corrector trial passes after a slice's first read ExmBy, EypBx, Ez, Bz
-    back from the per-particle copy the first one kept and gather Bx, By alone; the sweep matches
-    the one whose every trial pass gathers all six fields (HQ_NO_F4CACHE=1) within the run-to-run
+    """FP32: the predictor-corrector trial passes after a slice's first, and the final pass, read
+    ExmBy, EypBx, Ez, Bz back from the per-particle copy the first trial pass kept and gather Bx, By
+    alone; the sweep matches the one whose every pass gathers all six fields (HQ_NO_F4CACHE=1) within the run-to-run
     floor of the FP32 atomics (quadratic shape, 2 ppc, a driver strong enough to move particles
     across cells within the predictor-corrector)."""
     g = dict(I.scaled_grid(I.grid_params("linear64"), 128, 128, 64), shape_order=2, ppc_x=2)
