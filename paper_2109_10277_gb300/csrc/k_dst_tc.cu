@@ -14,6 +14,10 @@
 // a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in FP32 in tensor memory.
 // The epilogue of each product re-splits its FP32 result for the next one and
 // fuses the 1/lambda scaling (second product) or the final FP32 store (fourth).
+// Precision "TF32x3" (the fused streamed solve below, instantiated on FP32 words): a_hi =
+// a rounded to TF32 (cvt.rna), a_lo = a - a_hi, tcgen05.mma kind::tf32 (K = 8 per
+// instruction); the byte layout of every stage, box and swizzle is the bf16 one, a 128-byte
+// K block holding 32 elements instead of 64.
 //
 // Per-product kernel (k_dst_gemm, one product per launch; the allocation-free entry point
 // at the end of this file runs it), one 128 x 128 output tile per CTA, 4 warps:
@@ -352,7 +356,7 @@ __global__ void __launch_bounds__(128, 1)
 //
 // Tiles are 128 x BN (BN = 32 when every tile still gets its own CTA, else 64), one CTA
 // of 256 threads per SM: warp 0 lane 0 issues the TMA loads (A_hi, A_lo, B_hi, B_lo of a
-// 64-wide K block per stage, 4-stage ring), warp 1 lane 0 the MMAs (two per K step:
+// 128-byte K block per stage, 4-stage ring), warp 1 lane 0 the MMAs (two per K step:
 // A_hi x [B_hi; B_lo] with N = 2 BN, A_lo x B_hi with N = BN, into a 2 BN-column TMEM
 // accumulator), and all 8 warps the epilogue, each warpgroup half of the columns.
 struct SolveArgs {
