@@ -42,6 +42,10 @@
  *                  six fields (by default the first trial pass of a slice keeps ExmBy, EypBx,
  *                  Ez, Bz per particle and the later passes of the slice gather Bx, By alone;
  *                  the gathered values are bit for bit the same)
+ *   HQ_NO_SRCCACHE=1  FP32: every B_perp source phase of the predictor-corrector forms all its
+ *                  terms from the records (by default the first iteration of a slice keeps
+ *                  the part that does not depend on the trial J_perp, and the others add the
+ *                  trial term to it: the same sources up to FP32 rounding)
  * and one switch for testing the failure path, which does change results:
  *   HQ_FAULT_BARRIER=1  (FP32 grids) the first grid barrier of every tensor-core solve
  *                  waits for one CTA more than the launch has, so its bounded wait runs

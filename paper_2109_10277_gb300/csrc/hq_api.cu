@@ -77,7 +77,7 @@ void free_all(hq_grid_s* g) {
   F(g->porigin); F(g->sort_key); F(g->sort_perm); F(g->sort_count); F(g->sort_offset); F(g->sort_tsum);
   F(g->sort_scratch);
   for (int i = 0; i < 2; ++i) { F(g->dep[i]); F(g->chi[i]); F(g->op_hi[i]); F(g->op_lo[i]); F(g->psrc[i]); }
-  F(g->rho_ion); F(g->tj); F(g->bjn); F(g->bjp); F(g->xs4); F(g->xs1); F(g->pcg_r); F(g->pcg_p); F(g->pcg_s);
+  F(g->rho_ion); F(g->tj); F(g->bsrc0); F(g->bjn); F(g->bjp); F(g->xs4); F(g->xs1); F(g->pcg_r); F(g->pcg_p); F(g->pcg_s);
   F(g->pcg_part);
   F(g->d_pcres);
   F(g->scale_h); F(g->gf); F(g->bm); F(g->psi); F(g->bprev1); F(g->solved);
@@ -311,6 +311,7 @@ hq_status solve_fields_impl(hq_grid_s* g, int slice) {
     // the last iteration's mixing adds its residual sums to this slice's pair
     g->pc_rsum = last && g->d_pcres ? g->d_pcres + 2 * kResLanes * (int64_t)slice : nullptr;   // (opt-in)
     tape_b_iterate(g, m);
+    g->pc_iter = m;   // the B_perp sources of iteration 0 keep their invariant part for the others
     { Prof p(g, HQ_K_TRIAL, 1); launch_trial_pass<T>(g, slice, m, s); }
     if (m == 0) g->f4_slice = (g->fp64 || g->no_f4) ? -1 : slice;   // the final pass may reuse it
     if (g->det) launch_fx_decode(g, g->tj, 2 * g->nnode, nullptr, s);
@@ -1033,6 +1034,7 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     for (int i = 0; i < 2; ++i) { HQ_ALLOC(g->dep[i], 4 * ts * nn); HQ_ALLOC(g->chi[i], ts * nn); }
     HQ_ALLOC(g->rho_ion, ts * nn);
     HQ_ALLOC(g->tj, 2 * ts * nn);
+    if (!g->fp64) HQ_ALLOC(g->bsrc0, 8 * nn);
     HQ_ALLOC(g->bjn, 2 * ts * nn);
   }
   if (!g->fp64)
@@ -1142,6 +1144,8 @@ hq_status hq_grid_create(const hq_grid_desc* desc, void* cuda_stream, hq_grid_t*
     // folded DST-I (half the contraction) when both extents are multiples of 128
     const char* nf = std::getenv("HQ_NO_FOLD");
     g->fold = (g->nx % 128 == 0 && g->ny % 128 == 0 && !(nf && nf[0] == '1')) ? 1 : 0;
+    const char* nsc = std::getenv("HQ_NO_SRCCACHE");
+    g->no_srccache = nsc && nsc[0] == '1';
     const char* nf4 = std::getenv("HQ_NO_F4CACHE");
     g->no_f4 = nf4 && nf4[0] == '1';
     const char* ss = std::getenv("HQ_SEPARATE_SRC");

@@ -203,6 +203,9 @@ struct hq_grid_s {
   void* chi[2];
   void* rho_ion;
   void* tj;            // V2: trial plasma J_perp of slice i+1
+  float* bsrc0;        // FP32: V2 per node, the predictor-corrector-invariant part of the B_perp sources
+  int pc_iter;         // predictor-corrector iteration being issued (host side)
+  int no_srccache;     // HQ_NO_SRCCACHE=1: every B_perp source phase reads all its records
   void* bjn;           // V2: beam J_perp of slice i+1
   void* bjp;           // 2 x V2: beam J_perp of slices i-1 and i by slice parity (explicit B_perp solver; null otherwise)
   // explicit B_perp solver (bperp_solver = 1): its source records, PCG vectors and scalars
@@ -738,14 +741,28 @@ template <typename T> struct SrcBperp {
   V2<T>* bjn;
   Geom gm;
   int reset_prev;
+  // Only the trial J_perp changes between the predictor-corrector iterations of a slice: the
+  // rest, a0 = -dy Jz + (Jy(i-1) - Jy_beam(i+1)) / 2dz and a1 = dx Jz - (Jx(i-1) - Jx_beam(i+1)) / 2dz,
+  // is formed in the first iteration and kept per node in s0 (mode 1); the later ones read it
+  // back with the trial J_perp alone (mode 2).  Mode 0 (FP64, or HQ_NO_SRCCACHE=1) forms
+  // every term from the records.
+  V2<T>* s0;
+  int mode;
   // what one node's sources read: Jz at the four neighbours, J_perp of slices i-1 (record),
-  // i+1 (trial plasma) and i+1 (beam)
+  // i+1 (trial plasma) and i+1 (beam); mode 2: a0, a1 (in pb, pc) and the trial J_perp
   struct In {
     T jzr, jzl, jzu, jzd, pb, pc, ta, tb, ba, bb;
   };
   __device__ In load(int iy, int ix) const {
     In q{};
-    if (ix > 0 && iy > 0) {
+    if (ix > 0 && iy > 0 && mode == 2) {
+      const int64_t o = (int64_t)iy * gm.nx + ix;
+      const V2<T> a = s0[o], t = tj[o];
+      q.pb = a.a;
+      q.pc = a.b;
+      q.ta = t.a;
+      q.tb = t.b;
+    } else if (ix > 0 && iy > 0) {
       const int nx = gm.nx;
       const int64_t o = (int64_t)iy * nx + ix;
       q.jzr = ix + 1 < nx ? cur[o + 1].d : T(0);
@@ -767,10 +784,21 @@ template <typename T> struct SrcBperp {
     v[0] = v[1] = T(0);
     if (ix > 0 && iy > 0) {
       const T i2z = gsel<T>(gm.inv2dz, gm.f_inv2dz);
-      const T dzjx = (q.pb - (q.ta + q.ba)) * i2z;
-      const T dzjy = (q.pc - (q.tb + q.bb)) * i2z;
-      v[0] = -((q.jzu - q.jzd) * gsel<T>(gm.inv2dy, gm.f_inv2dy)) + dzjy;
-      v[1] = (q.jzr - q.jzl) * gsel<T>(gm.inv2dx, gm.f_inv2dx) - dzjx;
+      if (mode == 0) {
+        const T dzjx = (q.pb - (q.ta + q.ba)) * i2z;
+        const T dzjy = (q.pc - (q.tb + q.bb)) * i2z;
+        v[0] = -((q.jzu - q.jzd) * gsel<T>(gm.inv2dy, gm.f_inv2dy)) + dzjy;
+        v[1] = (q.jzr - q.jzl) * gsel<T>(gm.inv2dx, gm.f_inv2dx) - dzjx;
+      } else {
+        T a0 = q.pb, a1 = q.pc;
+        if (mode == 1) {
+          a0 = -((q.jzu - q.jzd) * gsel<T>(gm.inv2dy, gm.f_inv2dy)) + (q.pc - q.bb) * i2z;
+          a1 = (q.jzr - q.jzl) * gsel<T>(gm.inv2dx, gm.f_inv2dx) - (q.pb - q.ba) * i2z;
+          s0[(int64_t)iy * gm.nx + ix] = V2<T>{a0, a1};
+        }
+        v[0] = a0 - q.tb * i2z;
+        v[1] = a1 + q.ta * i2z;
+      }
     }
   }
   // after the node's reads: clear the trial J_perp, reset the slice i-1 record if asked
@@ -795,9 +823,11 @@ template <typename T> inline SrcMain<T> src_main_of(const hq_grid_s* g, const vo
 }
 template <typename T>
 inline SrcBperp<T> src_bperp_of(const hq_grid_s* g, const void* cur, void* prev, void* chi_prev, int reset_prev) {
+  const int mode = (sizeof(T) == 8 || !g->bsrc0 || g->no_srccache) ? 0 : (g->pc_iter == 0 ? 1 : 2);
   return SrcBperp<T>{reinterpret_cast<const V4<T>*>(cur), reinterpret_cast<V4<T>*>(prev), reinterpret_cast<T*>(chi_prev),
                      psrc_of(g, prev), reinterpret_cast<const T*>(g->rho_ion), reinterpret_cast<V2<T>*>(g->tj),
-                     reinterpret_cast<V2<T>*>(g->bjn), g->geom, reset_prev};
+                     reinterpret_cast<V2<T>*>(g->bjn), g->geom, reset_prev,
+                     reinterpret_cast<V2<T>*>(g->bsrc0), mode};
 }
 
 }  // namespace hq

@@ -616,24 +616,27 @@ def test_sources_in_solve_launch_match_separate_kernels(hq, monkeypatch):
         assert dev <= max(10 * floor, 1e-6), (k, dev, floor)
 
 
-def test_trial_field_cache_matches_full_gather(hq, monkeypatch):
-    """FP32: the predictor-corrector trial passes after a slice's first, and the final pass, read
-    ExmBy, EypBx, Ez, Bz back from the per-particle copy the first trial pass kept and gather Bx, By
-    alone; the sweep matches the one whose every pass gathers all six fields (HQ_NO_F4CACHE=1) within the run-to-run
-    floor of the FP32 atomics (quadratic shape, 2 ppc, a driver strong enough to move particles
-    across cells within the predictor-corrector)."""
+@pytest.mark.parametrize("switch", ["HQ_NO_F4CACHE", "HQ_NO_SRCCACHE"])
+def test_slice_caches_match_full_evaluation(hq, monkeypatch, switch):
+    """FP32, the two per-slice caches of the predictor-corrector.  HQ_NO_F4CACHE: the trial
+    passes after a slice's first, and the final pass, read ExmBy, EypBx, Ez, Bz back from the
+    per-particle copy the first trial pass kept and gather Bx, By alone.  HQ_NO_SRCCACHE: the B_perp
+    source phases after a slice's first read back the part of the sources that does not depend
+    on the trial J_perp.  With either switch set the sweep evaluates everything every time; it
+    matches the cached sweep within the run-to-run floor of the FP32 atomics (quadratic shape,
+    2 ppc, a driver strong enough to move particles across cells within the predictor-corrector)."""
     g = dict(I.scaled_grid(I.grid_params("linear64"), 128, 128, 64), shape_order=2, ppc_x=2)
     beams = [I.random_beam(100_000, 0.3, 0.3, 1.0, 2.0, energy_spread=1e-3)]
     outs = {}
     for mode in ("cached", "cached2", "full"):
         if mode == "full":
-            monkeypatch.setenv("HQ_NO_F4CACHE", "1")
+            monkeypatch.setenv(switch, "1")
         outs[mode] = run_gpu(hq, g, beams, "fp32", fields=("ez", "psi", "bx", "by"))[0]
-        monkeypatch.delenv("HQ_NO_F4CACHE", raising=False)
+        monkeypatch.delenv(switch, raising=False)
     for k in ("ez", "psi", "bx", "by"):
         floor = float(peak_err(outs["cached2"][k], outs["cached"][k]).max())
         dev = float(peak_err(outs["full"][k], outs["cached"][k]).max())
-        print(f"cached vs full gather {k}: {dev:.1e} (run-to-run {floor:.1e})")
+        print(f"{switch}: cached vs full {k}: {dev:.1e} (run-to-run {floor:.1e})")
         assert dev <= max(10 * floor, 1e-6), (k, dev, floor)
 
 
