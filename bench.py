@@ -202,9 +202,10 @@ def run_reference(args):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of each kernel
-# (profiles/: k_dst_solve_rs R = 2 and R = 3 weighted 5:1 as in a slice; the trial pass's first
-# and later iterations weighted 1:4; the final pass)
-NCU_TRAFFIC = {"dst": (5 * 16.336128e6 + (6.902016e6 + 768)) / 6, "trial": (21.229824e6 + 4 * 21.23648e6) / 5,
+# (profiles/: k_dst_solve_rs R = 3, R = 2 of the first and of the later predictor-corrector
+# iterations weighted 1:1:4 as in a slice; the trial pass's first and later iterations 1:4;
+# the final pass)
+NCU_TRAFFIC = {"dst": (6.902016e6 + 16.344832e6 + 4 * 7.961856e6) / 6, "trial": (21.229824e6 + 4 * 21.23648e6) / 5,
                "final": 46.436608e6 + 4.096e3}
 
 
