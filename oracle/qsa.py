@@ -54,7 +54,8 @@ def working_precision(dtype: torch.dtype):
     The method is FP64 (the default).  ``working_precision(torch.float32)`` runs the
     same steps with every tensor in single precision: a test knob that measures the
     single-precision rounding floor of the algorithm, the reference point for a
-    mixed-precision implementation's error.  Not re-entrant across threads."""
+    mixed-precision implementation's error.  Not re-entrant across threads.
+    A test knob (no passage of the paper): the same steps in another float type."""
     global DT
     old = DT
     DT = dtype
@@ -118,14 +119,17 @@ class GridSpec:
 
     @property
     def dx(self) -> float:
+        """Cell size in x (nx cells between the walls)."""
         return (self.xmax - self.xmin) / self.nx
 
     @property
     def dy(self) -> float:
+        """Cell size in y."""
         return (self.ymax - self.ymin) / self.ny
 
     @property
     def dzeta(self) -> float:
+        """Slice thickness (Sec. 2: the box is cut into nzeta transverse slices)."""
         return (self.zeta_max - self.zeta_min) / self.nzeta
 
 
@@ -134,14 +138,18 @@ class GridSpec:
 # ----------------------------------------------------------------------------
 
 def dst_matrix(n: int) -> torch.Tensor:
-    """S_jk = sin(pi j k / n), j, k = 0..n-1 (row/col 0 are zero): DST-I with a zero border."""
+    """S_jk = sin(pi j k / n), j, k = 0..n-1 (row/col 0 are zero): DST-I with a zero border.
+    Sec. 3.2 (Poisson solver by a DST of the first type, read as acting on the interior nodes with
+    the wall nodes zero)."""
     j = torch.arange(n, dtype=torch.int64)
     m = torch.remainder(torch.outer(j, j), 2 * n)  # exact argument reduction
     return torch.sin(math.pi * m.to(DT) / n)
 
 
 def laplace_eigs(spec: GridSpec) -> torch.Tensor:
-    """Eigenvalues lambda[l, k] of the 5-point Laplacian for DST-I mode (k in x, l in y)."""
+    """Eigenvalues lambda[l, k] of the 5-point Laplacian for DST-I mode (k in x, l in y).
+    Sec. 3.2 and Eq. psi: the 5-point Laplacian is the operator the DST-I diagonalises (a reading:
+    the paper does not name the discrete Laplacian)."""
     k = torch.arange(spec.nx, dtype=DT)
     l = torch.arange(spec.ny, dtype=DT)
     ex = -(4.0 / spec.dx ** 2) * torch.sin(math.pi * k / (2 * spec.nx)) ** 2
@@ -158,7 +166,8 @@ def dst_algorithm(name: str):
     transform's definition as a product with S) or "fft" (the same sums in O(n log n) per
     row, through the FFT of the odd extension).  The two differ only in rounding order:
     the FFT form serves the timed CPU baseline and measures how much the sweep amplifies
-    the DST's own rounding.  Not re-entrant across threads."""
+    the DST's own rounding.  Not re-entrant across threads.
+    A test knob: the same DST-I of Sec. 3.2 evaluated another way."""
     global DST_ALGORITHM
     old = DST_ALGORITHM
     if name not in ("matrix", "fft"):
@@ -175,14 +184,14 @@ def dst1_rows_fft(a: torch.Tensor) -> torch.Tensor:
 
     The odd extension e = (a_0 .. a_{n-1}, 0, -a_{n-1} .. -a_1) of length 2n has the discrete
     Fourier transform sum_j a_j (e^{-i pi j k/n} - e^{i pi j k/n}) = -2i sum_j a_j sin(pi j k/n)
-    (a_0 only adds a real constant), so b_k = -Im(E_k) / 2."""
+    (a_0 only adds a real constant), so b_k = -Im(E_k) / 2.  Sec. 3.2 (the DST-I by FFTs)."""
     n = a.shape[-1]
     ext = torch.cat([a, torch.zeros_like(a[..., :1]), -a[..., 1:].flip(-1)], dim=-1)
     return -0.5 * torch.fft.rfft(ext, dim=-1)[..., :n].imag
 
 
 def dst2(spec: GridSpec, a: torch.Tensor) -> torch.Tensor:
-    """Unnormalised 2D DST-I of the interior: S_y a S_x."""
+    """Unnormalised 2D DST-I of the interior: S_y a S_x.  Sec. 3.2 (DST-I)."""
     if DST_ALGORITHM == "fft":
         t = dst1_rows_fft(a)                                        # a S_x: along x
         return dst1_rows_fft(t.transpose(-1, -2)).transpose(-1, -2)  # S_y (.): along y
@@ -209,7 +218,9 @@ def _wall_mask(spec: GridSpec) -> torch.Tensor:
 
 
 def ddx(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
-    """Central x-derivative on interior nodes; node nx (wall) reads 0, wall outputs are 0."""
+    """Central x-derivative on interior nodes; node nx (wall) reads 0, wall outputs are 0.
+    The transverse derivatives of Eqs. exmby, ez, bz and bxby (central differences: a reading, the
+    paper does not name the stencil)."""
     fp = torch.cat([f, torch.zeros_like(f[..., :1])], dim=-1)  # columns 0..nx
     d = torch.zeros_like(f)
     d = torch.cat([d[..., :1], (fp[..., 2:] - fp[..., :-2]) / (2.0 * spec.dx)], dim=-1)
@@ -217,7 +228,9 @@ def ddx(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
 
 
 def ddy(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
-    """Central y-derivative on interior nodes; node ny (wall) reads 0, wall outputs are 0."""
+    """Central y-derivative on interior nodes; node ny (wall) reads 0, wall outputs are 0.
+    The transverse derivatives of Eqs. exmby, ez, bz and bxby (central differences: a reading, the
+    paper does not name the stencil)."""
     fp = torch.cat([f, torch.zeros_like(f[..., :1, :])], dim=-2)
     d = torch.cat([torch.zeros_like(f[..., :1, :]), (fp[..., 2:, :] - fp[..., :-2, :]) / (2.0 * spec.dy)], dim=-2)
     return d * _wall_mask(spec)
@@ -225,7 +238,7 @@ def ddy(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
 
 def laplacian(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
     """The 5-point Laplacian on interior nodes (wall nodes read 0; wall outputs are 0): the
-    operator poisson_solve inverts."""
+    operator poisson_solve inverts.  Eq. psi (the 5-point operator, a reading)."""
     fp = torch.nn.functional.pad(f, (0, 1, 0, 1))             # nodes nx, ny (wall) = 0
     c = fp[1:-1, 1:-1]
     lap = torch.zeros_like(f)
@@ -235,7 +248,9 @@ def laplacian(spec: GridSpec, f: torch.Tensor) -> torch.Tensor:
 
 
 def shifted_solve(spec: GridSpec, s: torch.Tensor, c: float) -> torch.Tensor:
-    """f = (L - c)^{-1} s for a constant c >= 0 (DST-I with 1/(lambda - c); f = 0 on the wall)."""
+    """f = (L - c)^{-1} s for a constant c >= 0 (DST-I with 1/(lambda - c); f = 0 on the wall).
+    Sec. 3.2 (explicit field solver; its equation read from Ampere's law with the plasma's
+    d/dzeta J_perp from the particle equations, the paper citing it without printing it)."""
     lam = laplace_eigs(spec)
     inv = torch.zeros_like(lam)
     inv[1:, 1:] = 1.0 / (lam[1:, 1:] - c)
@@ -244,7 +259,8 @@ def shifted_solve(spec: GridSpec, s: torch.Tensor, c: float) -> torch.Tensor:
 
 def explicit_shift(spec: GridSpec) -> float:
     """The explicit solver's preconditioner shift c: the unperturbed chi, sum q^2 n0 / M over the
-    plasma species (n0_scale for the default electrons)."""
+    plasma species (n0_scale for the default electrons).  Sec. 3.2 (explicit field solver; its equation read from Ampere's law with the plasma's
+    d/dzeta J_perp from the particle equations, the paper citing it without printing it)."""
     if not spec.species:
         return spec.n0_scale
     return sum(s.charge * s.charge * s.n0_scale / s.mass for s in spec.species)
@@ -255,7 +271,9 @@ def helmholtz_pcg(spec: GridSpec, chi: torch.Tensor, rhs: Sequence[torch.Tensor]
     """Solve (L - chi) B = rhs for each right-hand side: preconditioned conjugate gradients on
     the symmetric positive definite form (chi - L) B = -rhs, preconditioner (c - L)^{-1} (one
     shifted DST-I solve), start x0, a fixed number of iterations `iters` (no early exit; a
-    zero residual stops the update).  Returns the iterates and the final relative residuals."""
+    zero residual stops the update).  Returns the iterates and the final relative residuals.
+    Sec. 3.2 (explicit field solver: the Helmholtz-like equation, read from Ampere's law with the
+    plasma's d/dzeta J_perp from the particle equations)."""
     mask = _wall_mask(spec)
     A = lambda v: chi * v * mask - laplacian(spec, v)  # noqa: E731
     P = lambda v: -shifted_solve(spec, v, c)  # noqa: E731
@@ -294,8 +312,11 @@ def shape_1d(u: torch.Tensor, order: int, wdtype: torch.dtype = torch.float64):
 
     Returns (j0, [w_0..w_p]): node j0 + a carries weight w_a.  The cell fraction and
     the weights are formed in `wdtype` (FP64 unless a rounding floor is being measured).
+    Sec. 3.2 (deposition of orders 0-3 transversely; the same B-spline for gather and deposit, a
+    reading).
     """
     def back(ws):
+        """The weights in the coordinate's float type."""
         return [w.to(u.dtype) for w in ws]
     if order == 0:
         j0 = torch.floor(u + 0.5)
@@ -339,7 +360,7 @@ def deposit(spec: GridSpec, x, y, values: Sequence[torch.Tensor], order: int, re
     """Scatter per-particle `values` onto the node grid with shape `order`.
 
     reverse=True visits the stencil offsets in the opposite order (the same sums,
-    added in another order)."""
+    added in another order).  Sec. 3.2 (current deposition)."""
     outs = [torch.zeros(spec.ny * spec.nx, dtype=DT) for _ in values]
     stencil = list(_stencil(spec, x, y, order))
     for idx, wgt in (stencil[::-1] if reverse else stencil):
@@ -348,7 +369,8 @@ def deposit(spec: GridSpec, x, y, values: Sequence[torch.Tensor], order: int, re
 
 
 def gather(spec: GridSpec, x, y, fields: Sequence[torch.Tensor], order: int):
-    """Interpolate node `fields` to particle positions with shape `order`."""
+    """Interpolate node `fields` to particle positions with shape `order`.
+    Sec. 3.2 (field gather)."""
     flat = [f.reshape(-1) for f in fields]
     outs = [torch.zeros_like(x) for _ in fields]
     for idx, wgt in _stencil(spec, x, y, order):
@@ -364,6 +386,7 @@ def derivs(q_over_m: float, ux, uy, psi, F):
     """zeta-derivatives (dx, dy, dux, duy, dpsi) of a plasma particle.
 
     F = (ExmBy, EypBx, Ez, Bx, By, Bz) gathered at the particle; q/M in units e/m_e.
+    Sec. 3.2, Eq. 1 (the plasma particle equations).
     """
     exmby, eypbx, ez, bx, by, bz = F
     opp = 1.0 + psi
@@ -378,7 +401,8 @@ def derivs(q_over_m: float, ux, uy, psi, F):
 
 
 def ab5_step(y: Sequence[torch.Tensor], fs: Sequence[Sequence[torch.Tensor]], dzeta: float):
-    """One step zeta -> zeta - dzeta: y - dzeta * sum_k beta_k f_{i-k}; fs = [f_i, f_{i-1}, ..]."""
+    """One step zeta -> zeta - dzeta: y - dzeta * sum_k beta_k f_{i-k}; fs = [f_i, f_{i-1}, ..].
+    Sec. 3.2 (fifth-order Adams-Bashforth plasma pusher)."""
     out = []
     for c in range(len(y)):
         acc = AB5[0] * fs[0][c]
@@ -389,6 +413,8 @@ def ab5_step(y: Sequence[torch.Tensor], fs: Sequence[Sequence[torch.Tensor]], dz
 
 
 def gamma_of(ux, uy, psi):
+    """Lorentz factor of a plasma particle, gamma_p = (1 + u_perp^2 + (1 + Psi)^2) / (2 (1 + Psi))
+    (Sec. 3.2, the equation for gamma_p)."""
     opp = 1.0 + psi
     return (1.0 + ux * ux + uy * uy + opp * opp) / (2.0 * opp)
 
@@ -402,7 +428,8 @@ PLASMA_M = 1.0
 
 
 def plasma_species(spec: GridSpec) -> list:
-    """The plasma species of a grid: spec.species, or the default electrons with immobile ions."""
+    """The plasma species of a grid: spec.species, or the default electrons with immobile ions.
+    Sec. 6 (plasmas of several species, ion motion), each pushed with its q/M (Sec. 3.2)."""
     if spec.species:
         return list(spec.species)
     return [Species(PLASMA_Q, PLASMA_M, spec.n0_scale, spec.ppc_x, spec.ppc_y, spec.radial_profile,
@@ -494,7 +521,9 @@ def _state_ok(spec: GridSpec, x, y, psi):
 
 
 def plasma_deposit_jperp(spec: GridSpec, x, y, ux, uy, psi, w, ok, q=PLASMA_Q):
-    """Jx, Jy of (trial) particles; particles with ok == False contribute nothing."""
+    """Jx, Jy of (trial) particles; particles with ok == False contribute nothing.
+    Sec. 3.2 (predictor-corrector: J_perp of the trial particles; the macroparticle carries a fixed
+    flux, n = w gamma / ((1 + Psi) A), a reading)."""
     A = spec.dx * spec.dy
     one = torch.ones_like(psi)
     safe = lambda t, fill: torch.where(ok, t, fill)  # noqa: E731
@@ -506,7 +535,8 @@ def plasma_deposit_jperp(spec: GridSpec, x, y, ux, uy, psi, w, ok, q=PLASMA_Q):
 
 
 def ion_background(spec: GridSpec, st0, q=PLASMA_Q, reverse: bool = False):
-    """Immobile ions: minus the initial electron charge density, deposited with the same shape."""
+    """Immobile ions: minus the initial electron charge density, deposited with the same shape.
+    Immobile ions (Sec. 4), read as minus the initial electron density deposited with the same shape."""
     A = spec.dx * spec.dy
     (rho_e,) = deposit(spec, st0["x"], st0["y"], [q * st0["w"] / A], spec.shape_order, reverse)
     return -rho_e
@@ -517,14 +547,16 @@ def ion_background(spec: GridSpec, st0, q=PLASMA_Q, reverse: bool = False):
 # ----------------------------------------------------------------------------
 
 def beam_bins(spec: GridSpec, zeta: torch.Tensor) -> torch.Tensor:
-    """Slice index floor((zeta_max - zeta)/dzeta); -1 for particles outside [0, nzeta)."""
+    """Slice index floor((zeta_max - zeta)/dzeta); -1 for particles outside [0, nzeta).
+    Sec. 3.1 (beam particles sorted per slice), Sec. 3.2 (order 0 longitudinally)."""
     t = torch.floor((spec.zeta_max - zeta) / spec.dzeta)
     ok = torch.isfinite(t) & (t >= 0) & (t < spec.nzeta)
     return torch.where(ok, t, torch.full_like(t, -1.0)).to(torch.int64)
 
 
 def beam_csr(spec: GridSpec, bins: torch.Tensor):
-    """Counting-sort offsets: particles of slice i are order[off[i]:off[i+1]] (stable)."""
+    """Counting-sort offsets: particles of slice i are order[off[i]:off[i+1]] (stable).
+    Sec. 3.1 (beam particles sorted per slice)."""
     counts = torch.bincount(bins[bins >= 0], minlength=spec.nzeta)
     off = torch.zeros(spec.nzeta + 1, dtype=torch.int64)
     off[1:] = torch.cumsum(counts, 0)
@@ -534,7 +566,8 @@ def beam_csr(spec: GridSpec, bins: torch.Tensor):
 
 
 def beam_deposit_slice(spec: GridSpec, beam, sel: torch.Tensor, channels=("rho", "jx", "jy", "jz")):
-    """Beam rho, J of the particles `sel` (one slice): rho = q w S/(dx dy dzeta), J = rho u/gamma."""
+    """Beam rho, J of the particles `sel` (one slice): rho = q w S/(dx dy dzeta), J = rho u/gamma.
+    Sec. 3.2 (deposition, order 0 longitudinally; the per-slice units a reading)."""
     x, y = beam["x"][sel], beam["y"][sel]
     ux, uy, uz, w = beam["ux"][sel], beam["uy"][sel], beam["uz"][sel], beam["w"][sel]
     gam = torch.sqrt(1.0 + ux * ux + uy * uy + uz * uz)
@@ -548,6 +581,7 @@ def beam_push(spec: GridSpec, beam, sel, F, dt: float):
 
     F = slice fields (ExmBy, EypBx, Ez, Bx, By, Bz); E = (ExmBy + By, EypBx - Bx, Ez),
     B = (Bx, By, Bz).  zeta advances with v_z - 1.  Returns updated copies of the arrays.
+    Sec. 3.2 (second-order symplectic beam integrator, read as drift-kick-drift with a Boris kick).
     """
     qm = beam["charge"] / beam["mass"]
     x, y, z = beam["x"][sel], beam["y"][sel], beam["zeta"][sel]
@@ -555,6 +589,7 @@ def beam_push(spec: GridSpec, beam, sel, F, dt: float):
     h = 0.5 * dt
 
     def drift(x, y, z, ux, uy, uz):
+        """Half-step drift of the beam integrator (Sec. 3.2); zeta moves with v_z - 1."""
         ig = 1.0 / torch.sqrt(1.0 + ux * ux + uy * uy + uz * uz)
         return x + h * ux * ig, y + h * uy * ig, z + h * (uz * ig - 1.0)
 
@@ -595,7 +630,8 @@ def beam_moments(beam) -> torch.Tensor:
 
 def emittance(m) -> tuple:
     """Normalised rms emittances (eps_x, eps_y) from beam_moments: eps_x^2 = <dx^2><dux^2> - <dx dux>^2
-    with centred, weight-averaged second moments (momenta in units of m c)."""
+    with centred, weight-averaged second moments (momenta in units of m c).
+    Sec. 6 (the precision study's emittance; the definition a reading, the paper prints none)."""
     m = [float(v) for v in m]
     W = m[0]
     out = []
@@ -609,7 +645,8 @@ def emittance(m) -> tuple:
 
 
 def as_beam(arrays: dict, charge: float = -1.0, mass: float = 1.0):
-    """Convert a dict of numpy/torch arrays (x, y, zeta, ux, uy, uz, w) to float64 tensors."""
+    """Convert a dict of numpy/torch arrays (x, y, zeta, ux, uy, uz, w) to float64 tensors.
+    Input marshalling (no passage of the paper)."""
     out = {k: torch.as_tensor(arrays[k], dtype=DT) for k in ("x", "y", "zeta", "ux", "uy", "uz", "w")}
     out["charge"] = float(arrays.get("charge", charge))
     out["mass"] = float(arrays.get("mass", mass))
@@ -622,6 +659,7 @@ def as_beam(arrays: dict, charge: float = -1.0, mass: float = 1.0):
 
 @dataclass
 class SweepResult:
+    """What a sweep returns (the outputs of the Sec. 2 slice loop)."""
     fields: dict = field(default_factory=dict)      # name -> (n_slices, ny, nx)
     pc_residual: list = field(default_factory=list)  # per slice, last P-C iteration
     removed: int = 0
@@ -687,7 +725,8 @@ class SliceLoop:
 
     @property
     def st(self):
-        """The first species' plasma state (the only one of the default plasma)."""
+        """The first species' plasma state (the only one of the default plasma).
+        Sec. 3.2 (plasma particle state)."""
         return self.sts[0]
 
     def _deposit_full(self):
@@ -695,6 +734,7 @@ class SliceLoop:
                                         for sp_, st in zip(self.species, self.sts)]))
 
     def noisy(self, fields):
+        """A test knob: every deposited value times (1 + deposit_noise u), u uniform in [-1, 1]."""
         if self.deposit_noise <= 0.0:
             return fields
         return [f * (1.0 + self.deposit_noise * (2.0 * torch.rand(f.shape, generator=self.gen, dtype=DT) - 1.0))
@@ -705,7 +745,8 @@ class SliceLoop:
         """Solves slice i.  cur: (beam, sel) pairs, the beam particles `sel` of slice i (one per
         beam); nxt: the same for slice i + 1 (their J_perp enters the predictor-corrector);
         witness: indices into cur whose sums q w (1, Ez, Ez^2) are returned.  Returns (fields,
-        last P-C residual, cur's beams after the push of dt (unchanged for dt = 0), witness sums)."""
+        last P-C residual, cur's beams after the push of dt (unchanged for dt = 0), witness sums).
+        Sec. 2 (the per-slice routine) with Sec. 3.2 (predictor-corrector or explicit B_perp solver)."""
         spec, zero = self.spec, self.zero
         dz = spec.dzeta
         sts, hists, species = self.sts, self.hists, self.species
@@ -853,7 +894,7 @@ def sweep(spec: GridSpec, beams: Sequence[dict] = (), dt: float = 0.0,
 def witness_loss(res: SweepResult, beam: int, kind: str = "mean"):
     """Loss of the gradient workloads from the witness sums (S0, S1, S2) = sum(q w (1, Ez, Ez^2)):
     "mean": charge-weighted mean Ez, S1/S0; "mean+rms": that plus the charge-weighted RMS spread
-    sqrt(S2/S0 - (S1/S0)^2)."""
+    sqrt(S2/S0 - (S1/S0)^2).  The gradient workloads' losses (a reading: the paper prints no adjoint formulation)."""
     s0, s1, s2 = res.witness[beam]
     mean = s1 / s0
     if kind == "mean":
