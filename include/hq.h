@@ -4,7 +4,8 @@
  *
  * Units are the paper's normalized units (Sec. 6, "normalized units"): lengths
  * in 1/k_p, fields in E0 = m c omega_p / e, densities in n0, c = eps0 = mu0 = 1.
- * Plasma electrons have charge -1 and mass 1; ions are immobile.
+ * The default plasma is electrons (charge -1, mass 1) over immobile ions; hq_grid_desc.species
+ * gives plasmas of several species with their own charge and mass (mobile ions).
  *
  * Conventions for every entry point:
  *  - Pointers named "device" must point to CUDA device memory (for example the
