@@ -1,7 +1,7 @@
-"""hq_grid_create's argument checks, on the host (no device is touched before them): every
-refused descriptor returns its status (HQ_ERR_ARG = 1 for a malformed value, HQ_ERR_UNSUPPORTED
-= 7 for a valid but unsupported combination) and a message naming the field, and leaves the
-output handle NULL."""
+"""Argument checks of the C ABI that run on the host before any device work: hq_grid_create's
+(every refused descriptor returns its status, HQ_ERR_ARG = 1 for a malformed value and
+HQ_ERR_UNSUPPORTED = 7 for a valid but unsupported combination, a message naming the field,
+and a NULL handle) and hq_poisson_solve_static's."""
 import ctypes as C
 import math
 import os
@@ -126,3 +126,23 @@ def test_explicit_solver_shift_counts_the_species(lib):
     sp = (hq.SpeciesDesc * 2)(species(n0_scale=0.0), species(charge=1.0, mass=100.0, n0_scale=0.0))
     d = edit(species=C.cast(sp, C.POINTER(hq.SpeciesDesc)), n_species=2, bperp_solver=1, n0_scale=1.0)
     refuse(lib, d, ARG, "shift")
+
+
+@pytest.mark.parametrize("args,word", [
+    ((None, 16, 64, 64, 0.1, 0.1, 1), "NULL"),
+    ((16, None, 64, 64, 0.1, 0.1, 1), "NULL"),
+    ((16, 16, 7, 64, 0.1, 0.1, 1), "8..512"),
+    ((16, 16, 64, 513, 0.1, 0.1, 1), "8..512"),
+    ((16, 16, 64, 64, 0.1, 0.1, 0), "nrhs"),
+    ((16, 16, 64, 64, 0.1, 0.1, 4), "nrhs"),
+    ((16, 16, 64, 64, 0.0, 0.1, 1), "dx and dy"),
+    ((16, 16, 64, 64, 0.1, math.nan, 1), "dx and dy"),
+])
+def test_allocation_free_solve_checks_its_arguments(lib, args, word):
+    """hq_poisson_solve_static refuses out-of-range arguments with HQ_ERR_ARG before it looks at
+    the device or the (never dereferenced, here fake) pointers."""
+    src, dst, nx, ny, dx, dy, nrhs = args
+    st = lib.hq_poisson_solve_static(C.c_void_p(src) if src else None, C.c_void_p(dst) if dst else None,
+                                     nx, ny, C.c_double(dx), C.c_double(dy), nrhs, None)
+    assert st == ARG
+    assert word in lib.hq_last_error(None).decode()
