@@ -130,3 +130,34 @@ def test_fp32_weight_knob(order):
     _, w32 = O.qsa.shape_1d(u, order, torch.float32)
     d = max(float((a - b).abs().max()) for a, b in zip(w32, w64))
     assert 0.0 < d <= 4e-7
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_chi_of_the_unperturbed_plasma_is_the_explicit_shift(order):
+    """chi = sum q^2 w S g / (M A): a plasma at rest in its initial placement (g = 1) deposits the
+    density times q^2/M on every node away from the walls (the lattice's partition of unity), the
+    value explicit_shift computes from the grid parameters alone."""
+    sp = O.GridSpec(nx=24, ny=20, nzeta=2, xmin=-3.0, xmax=3.0, ymin=-2.5, ymax=2.5, zeta_min=0.0, zeta_max=1.0,
+                    shape_order=order, ppc_x=2, ppc_y=1, n0_scale=1.3)
+    st = O.plasma_init(sp)
+    *_, chi = O.plasma_deposit_full(sp, st)
+    interior = chi[3:-3, 3:-3]
+    assert float((interior - O.explicit_shift(sp)).abs().max()) <= 1e-13
+    assert O.explicit_shift(sp) == pytest.approx(1.3)
+
+
+def test_chi_over_rho_is_q_over_m_gamma_per_particle():
+    """Per particle, chi / rho = (q^2 g / M) / (q gamma g) = q / (M gamma), node by node."""
+    sp = spec(order=2)
+    g = torch.Generator().manual_seed(9)
+    for _ in range(3):
+        x, y, _ = rand_particles(sp, 1, 2.0, int(torch.randint(0, 1000, (1,), generator=g)))
+        st = dict(x=x, y=y, ux=0.4 * torch.randn(1, generator=g, dtype=torch.float64),
+                  uy=0.4 * torch.randn(1, generator=g, dtype=torch.float64),
+                  psi=torch.tensor([-0.3], dtype=torch.float64), w=torch.tensor([0.7], dtype=torch.float64),
+                  alive=torch.ones(1, dtype=torch.bool))
+        rho, _, _, _, chi = O.plasma_deposit_full(sp, st)
+        gam = float(O.gamma_of(st["ux"], st["uy"], st["psi"]))
+        nz = rho.abs() > 1e-12
+        ratio = chi[nz] / rho[nz]
+        assert torch.allclose(ratio, torch.full_like(ratio, O.PLASMA_Q / (O.PLASMA_M * gam)), rtol=1e-13, atol=0)
