@@ -161,3 +161,25 @@ def test_chi_over_rho_is_q_over_m_gamma_per_particle():
         nz = rho.abs() > 1e-12
         ratio = chi[nz] / rho[nz]
         assert torch.allclose(ratio, torch.full_like(ratio, O.PLASMA_Q / (O.PLASMA_M * gam)), rtol=1e-13, atol=0)
+
+
+def test_trial_jperp_is_the_full_deposit_of_the_valid_particles():
+    """The predictor-corrector's J_perp deposit of trial particles equals the J_perp of the full
+    deposit over the same particles, and particles flagged invalid (here with non-finite states)
+    contribute nothing."""
+    sp = spec(order=3)
+    x, y, _ = rand_particles(sp, 200, 1.5, 77)
+    g = torch.Generator().manual_seed(5)
+    ux = 0.5 * torch.randn(200, generator=g, dtype=torch.float64)
+    uy = 0.5 * torch.randn(200, generator=g, dtype=torch.float64)
+    psi = 0.6 * torch.rand(200, generator=g, dtype=torch.float64) - 0.5
+    w = torch.rand(200, generator=g, dtype=torch.float64)
+    ok = torch.rand(200, generator=g) > 0.3
+    xb, psib = x.clone(), psi.clone()
+    xb[~ok] = float("nan")
+    psib[~ok] = float("inf")
+    jx, jy = O.plasma_deposit_jperp(sp, xb, y, ux, uy, psib, w, ok)
+    st = dict(x=x, y=y, ux=ux, uy=uy, psi=psi, w=w, alive=ok)
+    _, fx, fy, _, _ = O.plasma_deposit_full(sp, st)
+    assert torch.isfinite(jx).all() and torch.isfinite(jy).all()
+    assert torch.allclose(jx, fx, rtol=0, atol=1e-13) and torch.allclose(jy, fy, rtol=0, atol=1e-13)
